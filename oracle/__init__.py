@@ -1,0 +1,299 @@
+"""Python access to the FP64 CPU oracle (``lbm_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the oracle is a plain, slow restatement of the
+D2Q9 LBGK method (eqs. (1), (2) with exact-difference forcing) and of the
+sub-volume energy/enstrophy balance diagnostic (eqs. (8)-(13), (17), (18)) of
+Tauzin et al. (2018).  Only the test-suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import it.  It shares no code with
+the CUDA library and never imports the product package.
+
+Arrays are numpy float64, C-contiguous: populations ``f[9, ny, nx]`` and
+fields ``A[ny, nx]`` (x is the fast index).  Term-field order:
+``0 LHS^E, 1..5 RHS^{E,1..5}, 6 LHS^Omega, 7..12 RHS^{Omega,1..6}``.
+Box statistics order: ``[delta^E, delta^Omega, <13 terms>]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NT = 13  # term fields
+NQ = 15  # box quantities (2 balancing errors + 13 terms)
+TERM_NAMES = ["LHS_E", "RHS_E1", "RHS_E2", "RHS_E3", "RHS_E4", "RHS_E5",
+              "LHS_Z", "RHS_Z1", "RHS_Z2", "RHS_Z3", "RHS_Z4", "RHS_Z5", "RHS_Z6"]
+QUANTITY_NAMES = ["delta_E", "delta_Z"] + TERM_NAMES
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (plain -O2, no fast-math)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            D, I, P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            lib.orc_feq.argtypes = [D, D, D, P]
+            lib.orc_force_ext.argtypes = [I, I, I, D, I, I, I, P, P]
+            lib.orc_collide_cell.argtypes = [P, D, D, D, D, P]
+            lib.orc_collide.argtypes = [I, I, D, I, D, I, D, P, P]
+            lib.orc_stream.argtypes = [I, I, P, P]
+            lib.orc_run.argtypes = [I, I, D, I, D, I, D, P, I]
+            lib.orc_run.restype = I
+            lib.orc_init.argtypes = [I, I, P, P, P, P]
+            lib.orc_moments.argtypes = [I, I, I, D, I, D, P, P, P, P, P, P]
+            lib.orc_ddx.argtypes = [I, I, P, P]
+            lib.orc_ddy.argtypes = [I, I, P, P]
+            lib.orc_bdf2.argtypes = [ctypes.c_size_t, P, P, P, P]
+            lib.orc_terms.argtypes = [I, I, D, P, P, P, P, P, P]
+            lib.orc_terms.restype = I
+            lib.orc_box_mean.argtypes = [I, I, P, I, I, I]
+            lib.orc_box_mean.restype = D
+            lib.orc_box_values.argtypes = [I, I, P, I, I, I, P]
+            lib.orc_balance_stats.argtypes = [I, I, P, P, I, P, I, P, P]
+            lib.orc_balance_stats.restype = I
+            lib.orc_terms_from_populations.argtypes = [I, I, D, I, D, I, D, P, P, P, P]
+            lib.orc_terms_from_populations.restype = I
+            lib.orc_global.argtypes = [I, I, D, I, D, I, D, P, P]
+            lib.orc_global.restype = I
+            lib.orc_objective.argtypes = [I, I, D, I, D, I, D, P, I, I, I, I, I, P]
+            lib.orc_objective.restype = I
+            lib.orc_lattice.argtypes = [P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Force:
+    """Forcing of one member: Kolmogorov amplitude F0 at wavenumber kf (in
+    units of 2 pi / N) when kind == 1, plus drag alpha on the bare momentum."""
+
+    def __init__(self, kind: int = 0, F0: float = 0.0, kf: int = 0, alpha: float = 0.0):
+        self.kind, self.F0, self.kf, self.alpha = int(kind), float(F0), int(kf), float(alpha)
+
+    def args(self):
+        return (self.kind, self.F0, self.kf, self.alpha)
+
+
+NO_FORCE = Force()
+
+
+def lattice():
+    lib = _load()
+    cx = np.zeros(9, np.int32)
+    cy = np.zeros(9, np.int32)
+    t = np.zeros(9)
+    lib.orc_lattice(_p(cx), _p(cy), _p(t))
+    return cx, cy, t
+
+
+def feq(rho: float, ux: float, uy: float) -> np.ndarray:
+    out = np.zeros(9)
+    _load().orc_feq(rho, ux, uy, _p(out))
+    return out
+
+
+def force_ext(nx, ny, force: Force, x, y):
+    fx, fy = ctypes.c_double(), ctypes.c_double()
+    _load().orc_force_ext(nx, ny, force.kind, force.F0, force.kf, x, y,
+                          ctypes.byref(fx), ctypes.byref(fy))
+    return fx.value, fy.value
+
+
+def collide_cell(f9, tau, Fex, Fey, alpha):
+    f9 = _f64(f9)
+    out = np.zeros(9)
+    _load().orc_collide_cell(_p(f9), tau, Fex, Fey, alpha, _p(out))
+    return out
+
+
+def collide(f, tau, force: Force = NO_FORCE):
+    f = _f64(f)
+    _, ny, nx = f.shape
+    out = np.empty_like(f)
+    k, F0, kf, a = force.args()
+    _load().orc_collide(nx, ny, tau, k, F0, kf, a, _p(f), _p(out))
+    return out
+
+
+def stream(f):
+    f = _f64(f)
+    _, ny, nx = f.shape
+    out = np.empty_like(f)
+    _load().orc_stream(nx, ny, _p(f), _p(out))
+    return out
+
+
+def init(rho, ux, uy):
+    rho, ux, uy = _f64(rho), _f64(ux), _f64(uy)
+    ny, nx = rho.shape
+    f = np.empty((9, ny, nx))
+    _load().orc_init(nx, ny, _p(rho), _p(ux), _p(uy), _p(f))
+    return f
+
+
+def run(f, nsteps, tau, force: Force = NO_FORCE):
+    """Return f after nsteps steps of eq. (1) (input not modified)."""
+    f = _f64(f).copy()
+    _, ny, nx = f.shape
+    k, F0, kf, a = force.args()
+    rc = _load().orc_run(nx, ny, tau, k, F0, kf, a, _p(f), int(nsteps))
+    if rc != 0:
+        raise MemoryError("oracle run failed")
+    return f
+
+
+def moments(f, force: Force = NO_FORCE):
+    """Return dict rho, jx, jy, ux, uy (u = EDM velocity (j + F/2)/rho)."""
+    f = _f64(f)
+    _, ny, nx = f.shape
+    out = {k: np.empty((ny, nx)) for k in ("rho", "jx", "jy", "ux", "uy")}
+    k, F0, kf, a = force.args()
+    _load().orc_moments(nx, ny, k, F0, kf, a, _p(f), _p(out["rho"]), _p(out["jx"]),
+                        _p(out["jy"]), _p(out["ux"]), _p(out["uy"]))
+    return out
+
+
+def ddx(A):
+    A = _f64(A)
+    ny, nx = A.shape
+    out = np.empty_like(A)
+    _load().orc_ddx(nx, ny, _p(A), _p(out))
+    return out
+
+
+def ddy(A):
+    A = _f64(A)
+    ny, nx = A.shape
+    out = np.empty_like(A)
+    _load().orc_ddy(nx, ny, _p(A), _p(out))
+    return out
+
+
+def bdf2(An, An1, An2):
+    An, An1, An2 = _f64(An), _f64(An1), _f64(An2)
+    out = np.empty_like(An)
+    _load().orc_bdf2(An.size, _p(An), _p(An1), _p(An2), _p(out))
+    return out
+
+
+def terms(tau, rho3, ux3, uy3, Fx, Fy):
+    """13 term fields from (rho, u) at levels n, n-1, n-2 and F at n."""
+    rho3 = [_f64(a) for a in rho3]
+    ux3 = [_f64(a) for a in ux3]
+    uy3 = [_f64(a) for a in uy3]
+    Fx, Fy = _f64(Fx), _f64(Fy)
+    ny, nx = Fx.shape
+    arr = (ctypes.c_void_p * 3)
+    r = arr(*[a.ctypes.data for a in rho3])
+    u = arr(*[a.ctypes.data for a in ux3])
+    v = arr(*[a.ctypes.data for a in uy3])
+    out = np.empty((NT, ny, nx))
+    rc = _load().orc_terms(nx, ny, tau, ctypes.cast(r, ctypes.c_void_p),
+                           ctypes.cast(u, ctypes.c_void_p), ctypes.cast(v, ctypes.c_void_p),
+                           _p(Fx), _p(Fy), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle terms failed")
+    return out
+
+
+def terms_from_populations(f_n, f_n1, f_n2, tau, force: Force = NO_FORCE):
+    f_n, f_n1, f_n2 = _f64(f_n), _f64(f_n1), _f64(f_n2)
+    _, ny, nx = f_n.shape
+    out = np.empty((NT, ny, nx))
+    k, F0, kf, a = force.args()
+    rc = _load().orc_terms_from_populations(nx, ny, tau, k, F0, kf, a, _p(f_n), _p(f_n1),
+                                            _p(f_n2), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle terms failed")
+    return out
+
+
+def box_mean(A, x0, y0, L):
+    A = _f64(A)
+    ny, nx = A.shape
+    return _load().orc_box_mean(nx, ny, _p(A), int(x0), int(y0), int(L))
+
+
+def box_values(terms13, x0, y0, L):
+    terms13 = _f64(terms13)
+    _, ny, nx = terms13.shape
+    out = np.empty(NQ)
+    _load().orc_box_values(nx, ny, _p(terms13), int(x0), int(y0), int(L), _p(out))
+    return out
+
+
+def balance_stats(terms13, Ls, origins=None, per_box=False):
+    """Return stats[nL, 15, 2] (mean, population std) and optionally the
+    per-box values [nL, n_boxes, 15]."""
+    terms13 = _f64(terms13)
+    _, ny, nx = terms13.shape
+    Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+    nL = len(Ls)
+    if origins is not None:
+        origins = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1, 2)
+        nb = origins.shape[0]
+        op = _p(origins)
+    else:
+        nb = nx * ny
+        op = None
+    stats = np.empty((nL, NQ, 2))
+    pb = np.empty((nL, nb, NQ)) if per_box else None
+    rc = _load().orc_balance_stats(nx, ny, _p(terms13), _p(Ls), nL, op, nb, _p(stats),
+                                   _p(pb) if per_box else None)
+    if rc != 0:
+        raise MemoryError("oracle stats failed")
+    return (stats, pb) if per_box else stats
+
+
+def global_quantities(f, tau, force: Force = NO_FORCE):
+    """[sum rho, sum jx, sum jy, <E>, <Omega>, <u.F>, <eps>]."""
+    f = _f64(f)
+    _, ny, nx = f.shape
+    out = np.empty(7)
+    k, F0, kf, a = force.args()
+    rc = _load().orc_global(nx, ny, tau, k, F0, kf, a, _p(f), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle global failed")
+    return out
+
+
+def objective(f0, tau, force: Force, n0, n1, bx, by, L):
+    """Mean over n in [n0, n1] of the L x L box average of RHS^{E,4}(n)."""
+    f0 = _f64(f0)
+    _, ny, nx = f0.shape
+    J = ctypes.c_double()
+    k, F0, kf, a = force.args()
+    rc = _load().orc_objective(nx, ny, tau, k, F0, kf, a, _p(f0), int(n0), int(n1),
+                               int(bx), int(by), int(L), ctypes.byref(J))
+    if rc != 0:
+        raise MemoryError("oracle objective failed")
+    return J.value

@@ -1,0 +1,453 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test names the passage it checks.  None of them re-derives the oracle's
+own formula: they use identities, closed forms, special cases, brute force
+and an independent symbolic derivation of the continuum balance equations.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs as li
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Lattice and equilibrium (eq. 2)
+# --------------------------------------------------------------------------
+
+def test_lattice_isotropy(orc):
+    """D2Q9 weights: sum t = 1, sum t c = 0, sum t c c = cs^2 I,
+    sum t c_a^4 = 3 cs^4, sum t cx^2 cy^2 = cs^4, opposite pairs exist."""
+    cx, cy, t = orc.lattice()
+    cs2 = 1.0 / 3.0
+    assert abs(t.sum() - 1) < 1e-15
+    assert abs((t * cx).sum()) < 1e-15 and abs((t * cy).sum()) < 1e-15
+    assert abs((t * cx * cx).sum() - cs2) < 1e-15
+    assert abs((t * cy * cy).sum() - cs2) < 1e-15
+    assert abs((t * cx * cy).sum()) < 1e-15
+    assert abs((t * cx ** 4).sum() - 3 * cs2 ** 2) < 1e-15
+    assert abs((t * cx ** 2 * cy ** 2).sum() - cs2 ** 2) < 1e-15
+    vel = set(zip(cx.tolist(), cy.tolist()))
+    assert len(vel) == 9
+    assert all((-a, -b) in vel for a, b in vel)
+
+
+def test_equilibrium_moments(orc):
+    """Eq. (2) reproduces rho, rho u and rho (cs^2 I + u u) exactly."""
+    cx, cy, _ = orc.lattice()
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        rho = rng.uniform(0.5, 2.0)
+        ux, uy = rng.uniform(-0.2, 0.2, size=2)
+        e = orc.feq(rho, ux, uy)
+        tol = 4e-16 * rho * 10
+        assert abs(e.sum() - rho) < tol
+        assert abs((cx * e).sum() - rho * ux) < tol
+        assert abs((cy * e).sum() - rho * uy) < tol
+        assert abs((cx * cx * e).sum() - rho * (1 / 3 + ux * ux)) < tol
+        assert abs((cx * cy * e).sum() - rho * ux * uy) < tol
+        assert abs((cy * cy * e).sum() - rho * (1 / 3 + uy * uy)) < tol
+
+
+# --------------------------------------------------------------------------
+# Collision with exact-difference forcing (eq. 1, Sec. 3)
+# --------------------------------------------------------------------------
+
+def test_collision_mass_and_momentum(orc):
+    """BGK conserves mass; the EDM term adds exactly F to the momentum, with
+    F = F_ext - alpha j."""
+    cx, cy, _ = orc.lattice()
+    rng = np.random.default_rng(2)
+    f = li.random_populations(1, 1, seed=3, rel_noise=0.2)[:, 0, 0]
+    for tau in (0.505, 0.6, 1.0, 1.7):
+        for _ in range(20):
+            f = f * rng.uniform(0.8, 1.2, size=9)
+            Fex, Fey = rng.uniform(-1e-3, 1e-3, size=2)
+            alpha = rng.uniform(0, 1e-2)
+            out = orc.collide_cell(f, tau, Fex, Fey, alpha)
+            jx, jy = (cx * f).sum(), (cy * f).sum()
+            assert abs(out.sum() - f.sum()) < 1e-15
+            assert abs((cx * out).sum() - (jx + Fex - alpha * jx)) < 1e-15
+            assert abs((cy * out).sum() - (jy + Fey - alpha * jy)) < 1e-15
+
+
+def test_collision_relaxes_to_equilibrium(orc):
+    """With tau = 1 and no force the post-collision state is f_eq itself;
+    an equilibrium state is a fixed point of the collision for any tau."""
+    cx, cy, _ = orc.lattice()
+    f = li.random_populations(1, 1, seed=4, rel_noise=0.1)[:, 0, 0]
+    rho = f.sum()
+    ux, uy = (cx * f).sum() / rho, (cy * f).sum() / rho
+    np.testing.assert_allclose(orc.collide_cell(f, 1.0, 0, 0, 0), orc.feq(rho, ux, uy),
+                               rtol=2e-15, atol=0)
+    e = orc.feq(1.1, 0.03, -0.02)
+    for tau in (0.51, 0.8, 2.0):
+        np.testing.assert_allclose(orc.collide_cell(e, tau, 0, 0, 0), e, rtol=2e-15, atol=0)
+
+
+def test_edm_forcing_is_difference_of_equilibria(orc):
+    """Sec. 3 EDM: starting from equilibrium at velocity u, a forced collision
+    lands on the equilibrium at u + F/rho for any tau (special case where the
+    BGK part vanishes)."""
+    rho, ux, uy = 1.05, 0.02, -0.01
+    Fx, Fy = 3e-4, -2e-4
+    e = orc.feq(rho, ux, uy)
+    for tau in (0.6, 1.3):
+        out = orc.collide_cell(e, tau, Fx, Fy, 0.0)
+        np.testing.assert_allclose(out, orc.feq(rho, ux + Fx / rho, uy + Fy / rho),
+                                   rtol=2e-15, atol=0)
+
+
+# --------------------------------------------------------------------------
+# Streaming (eq. 1, left-hand side)
+# --------------------------------------------------------------------------
+
+def test_stream_moves_each_value_by_its_velocity(orc):
+    cx, cy, _ = orc.lattice()
+    nx, ny = 7, 5
+    for l in range(9):
+        for (x, y) in [(0, 0), (6, 4), (3, 2), (6, 0), (0, 4)]:
+            f = np.zeros((9, ny, nx))
+            f[l, y, x] = 1.0
+            g = orc.stream(f)
+            assert g.sum() == 1.0
+            assert g[l, (y + cy[l]) % ny, (x + cx[l]) % nx] == 1.0
+
+
+def test_stream_is_a_permutation_with_period_n(orc):
+    """Streaming is a bijection; n steps on an n x n grid are the identity,
+    bit for bit."""
+    n = 6
+    f = li.random_populations(n, n, seed=5)
+    g = orc.stream(f)
+    for l in range(9):
+        assert np.array_equal(np.sort(g[l].ravel()), np.sort(f[l].ravel()))
+    h = f
+    for _ in range(n):
+        h = orc.stream(h)
+    assert np.array_equal(h, f)
+    assert np.array_equal(g[0], f[0])
+
+
+def test_step_conserves_mass_and_gains_total_force(orc):
+    """One step of eq. (1): total mass exact; total momentum grows by sum F."""
+    n = 12
+    force = orc.Force(1, 2e-4, 2, 3e-3)
+    f = li.random_populations(n, n, seed=6)
+    m0 = orc.moments(f, force)
+    g = orc.run(f, 1, 0.57, force)
+    m1 = orc.moments(g, force)
+    Fx = np.zeros((n, n))
+    Fy = np.zeros((n, n))
+    for y in range(n):
+        for x in range(n):
+            Fx[y, x], Fy[y, x] = orc.force_ext(n, n, force, x, y)
+    Fx -= force.alpha * m0["jx"]
+    Fy -= force.alpha * m0["jy"]
+    assert abs(m1["rho"].sum() - m0["rho"].sum()) < 1e-12
+    assert abs(m1["jx"].sum() - (m0["jx"].sum() + Fx.sum())) < 1e-13
+    assert abs(m1["jy"].sum() - (m0["jy"].sum() + Fy.sum())) < 1e-13
+
+
+def test_force_ext_is_kolmogorov(orc):
+    """Force values at a few points against the closed form."""
+    n, F0, kf = 16, 1e-3, 3
+    f = orc.Force(1, F0, kf, 0.0)
+    for (x, y) in [(0, 0), (1, 5), (15, 3), (7, 11)]:
+        fx, fy = orc.force_ext(n, n, f, x, y)
+        assert abs(fx - F0 * np.sin(2 * np.pi * kf * y / n)) < 1e-18
+        assert abs(fy - F0 * np.sin(2 * np.pi * kf * x / n)) < 1e-18
+    assert orc.force_ext(n, n, orc.NO_FORCE, 3, 3) == (0.0, 0.0)
+
+
+# --------------------------------------------------------------------------
+# Whole LBGK: viscosity of eq. (5)
+# --------------------------------------------------------------------------
+
+def _tg_rate(orc, n, tau=0.6, u0=1e-3):
+    rho, ux, uy = li.taylor_green(n, u0=u0, pressure_consistent=True)
+    f = orc.init(rho, ux, uy)
+    nu = (tau - 0.5) / 3
+    k = 2 * np.pi / n
+    T = int(0.5 / (2 * nu * k * k))
+    t1 = T // 4
+    x = 2 * np.pi * np.arange(n) / n
+    X, Y = np.meshgrid(x, x)
+    basis = np.sin(X) * np.cos(Y)
+    f1 = orc.run(f, t1, tau)
+    f2 = orc.run(f1, T - t1, tau)
+    a1 = np.sum(orc.moments(f1)["ux"] * basis) / np.sum(basis ** 2)
+    a2 = np.sum(orc.moments(f2)["ux"] * basis) / np.sum(basis ** 2)
+    return -np.log(a2 / a1) / (T - t1), 2 * nu * k * k
+
+
+def test_taylor_green_decay_rate(orc):
+    """Taylor-Green amplitude decays as exp(-2 nu k^2 t), nu = cs^2 (tau - 1/2)
+    (eq. 5), with a rate error that falls at second order in k."""
+    r32, e32 = _tg_rate(orc, 32)
+    r64, e64 = _tg_rate(orc, 64)
+    err32, err64 = abs(r32 / e32 - 1), abs(r64 / e64 - 1)
+    assert err32 < 5e-4 and err64 < 1e-4
+    assert 3.0 < err32 / err64 < 5.5
+
+
+def test_kolmogorov_laminar_amplitude_and_power_balance(orc):
+    """Steady Kolmogorov flow: velocity amplitude F0 / (nu k^2 + alpha) and,
+    globally, injected power <u.F> equals dissipation <eps> (eq. 8 at L = N:
+    the flux terms vanish and the time derivative is zero)."""
+    n, tau, kf, alpha, A = 32, 0.8, 1, 1e-3, 0.005
+    F0 = li.kolmogorov_F0(n, tau, kf, alpha, A)
+    force = orc.Force(1, F0, kf, alpha)
+    z = np.zeros((n, n))
+    f = orc.init(np.ones((n, n)), z, z)
+    rate = (tau - 0.5) / 3 * (2 * np.pi * kf / n) ** 2 + alpha
+    f = orc.run(f, int(12 / rate), tau, force)
+    m = orc.moments(f, force)
+    x = 2 * np.pi * kf * np.arange(n) / n
+    X, Y = np.meshgrid(x, x)
+    ax = np.sum(m["ux"] * np.sin(Y)) / np.sum(np.sin(Y) ** 2)
+    ay = np.sum(m["uy"] * np.sin(X)) / np.sum(np.sin(X) ** 2)
+    assert abs(ax / A - 1) < 1e-2 and abs(ay / A - 1) < 1e-2
+    g = orc.global_quantities(f, tau, force)
+    assert abs(g[5] / g[6] - 1) < 1e-2
+
+
+# --------------------------------------------------------------------------
+# Derivatives, eqs. (17), (18)
+# --------------------------------------------------------------------------
+
+def test_ddx_ddy_modified_wavenumber(orc):
+    """Eq. (18) on a periodic sine has the closed-form modified wavenumber
+    (8/5) sin k - (2/5) sin 2k + (8/105) sin 3k - (1/140) sin 4k."""
+    nx, ny = 40, 24
+    xs = np.arange(nx)
+    ys = np.arange(ny)
+    X, Y = np.meshgrid(xs, ys)
+    for m in range(1, nx // 2):
+        k = 2 * np.pi * m / nx
+        kt = 8 / 5 * np.sin(k) - 2 / 5 * np.sin(2 * k) + 8 / 105 * np.sin(3 * k) \
+            - 1 / 140 * np.sin(4 * k)
+        A = np.sin(k * X + 0.3)
+        np.testing.assert_allclose(orc.ddx(A), kt * np.cos(k * X + 0.3), rtol=0, atol=5e-14)
+        np.testing.assert_allclose(orc.ddy(A), 0 * A, rtol=0, atol=1e-15)
+    for m in range(1, ny // 2):
+        k = 2 * np.pi * m / ny
+        kt = 8 / 5 * np.sin(k) - 2 / 5 * np.sin(2 * k) + 8 / 105 * np.sin(3 * k) \
+            - 1 / 140 * np.sin(4 * k)
+        A = np.cos(k * Y - 1.1)
+        np.testing.assert_allclose(orc.ddy(A), -kt * np.sin(k * Y - 1.1), rtol=0, atol=5e-14)
+
+
+def test_ddx_exact_on_polynomials_up_to_degree_8(orc):
+    """Eq. (18) is an 8th-order centred difference: exact on polynomials of
+    degree <= 8 away from the periodic seam, not exact at degree 9."""
+    n = 40
+    x = np.arange(n, dtype=float)
+    inner = slice(4, n - 4)
+    for deg in range(0, 10):
+        p = ((x - 20.0) / 10.0) ** deg
+        dp = deg * ((x - 20.0) / 10.0) ** max(deg - 1, 0) / 10.0
+        A = np.tile(p, (3, 1))
+        got = orc.ddx(A)[1, inner]
+        err = np.max(np.abs(got - dp[inner]))
+        if deg <= 8:
+            assert err < 1e-13, (deg, err)
+        else:
+            assert err > 1e-9, (deg, err)
+        got_y = orc.ddy(A.T.copy())[inner, 1]
+        if deg <= 8:
+            assert np.max(np.abs(got_y - dp[inner])) < 1e-13
+
+
+def test_bdf2_exact_on_quadratics(orc):
+    """Eq. (17) is exact for A(t) = a + b t + c t^2 (derivative b + 2 c t_n)."""
+    rng = np.random.default_rng(7)
+    a, b, c = rng.standard_normal((3, 50))
+    tn = 17.0
+    A = lambda t: a + b * t + c * t * t  # noqa: E731
+    got = orc.bdf2(A(tn), A(tn - 1), A(tn - 2))
+    np.testing.assert_allclose(got, b + 2 * c * tn, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Balance terms, eqs. (8)-(11): independent symbolic derivation
+# --------------------------------------------------------------------------
+
+def _symbolic_terms(n, tau, t_n, wt):
+    """Continuum terms of eqs. (10)/(11) from the 3D index forms with the
+    Levi-Civita symbol, differentiated symbolically, on the grid at t_n."""
+    sp = pytest.importorskip("sympy")
+    x, y, z, t = sp.symbols("x y z t", real=True)
+    k = 2 * sp.pi / n
+    rho = 1 + sp.Rational(3, 100) * sp.cos(k * x + 2 * k * y + sp.Rational(1, 3)) * sp.cos(wt * t)
+    ux = sp.Rational(2, 100) * sp.sin(k * y - sp.Rational(1, 2) + wt * t) \
+        + sp.Rational(1, 100) * sp.cos(2 * k * x + k * y)
+    uy = sp.Rational(15, 1000) * sp.cos(k * x + sp.Rational(7, 10)) * sp.cos(wt * t) \
+        - sp.Rational(5, 1000) * sp.sin(k * x - 2 * k * y)
+    Fx = sp.Rational(3, 10000) * sp.sin(k * y) + sp.Rational(1, 10000) * sp.cos(k * x - k * y)
+    Fy = -sp.Rational(2, 10000) * sp.sin(2 * k * x) * sp.cos(k * y)
+    u = [ux, uy, sp.Integer(0)]
+    F = [Fx, Fy, sp.Integer(0)]
+    X = [x, y, z]
+    nu = sp.Rational(1, 3) * (sp.nsimplify(tau) - sp.Rational(1, 2))
+    p = rho / 3
+    d = lambda e, j: sp.diff(e, X[j])  # noqa: E731
+    eps = sp.LeviCivita
+    R3 = range(3)
+    om = [sum(eps(i, j, kk) * d(u[kk], j) for j in R3 for kk in R3) for i in R3]
+    E = rho * sum(ui * ui for ui in u) / 2
+    Om = sum(o * o for o in om) / 2
+    S = [[d(u[i], j) + d(u[j], i) for j in R3] for i in R3]
+    H = [sum(d(nu * rho * S[i][j], j) for j in R3) / rho for i in R3]
+    T = [
+        sp.diff(E, t),
+        -sum(d(E * u[j], j) for j in R3),
+        -sum(u[i] * d(p, i) for i in R3),
+        sum(u[i] * F[i] for i in R3),
+        -sum(nu * rho * S[i][j] * d(u[i], j) for i in R3 for j in R3),
+        sum(d(nu * rho * u[i] * S[i][j], j) for i in R3 for j in R3),
+        sp.diff(Om, t),
+        -sum(d(Om * u[j], j) for j in R3),
+        -Om * sum(d(u[j], j) for j in R3),
+        sum(om[i] * eps(i, j, kk) * d(F[kk] / rho, j) for i in R3 for j in R3 for kk in R3),
+        sum(H[i] * eps(i, j, kk) * d(om[kk], j) for i in R3 for j in R3 for kk in R3),
+        sum(d(eps(i, j, kk) * om[i] * H[kk], j) for i in R3 for j in R3 for kk in R3),
+        sum(om[i] * om[j] * d(u[i], j) for i in R3 for j in R3),
+    ]
+    xs = np.arange(n, dtype=float)
+    XX, YY = np.meshgrid(xs, xs)
+    args = (x, y, z, t)
+
+    def ev(e, tt):
+        fn = sp.lambdify(args, e, "numpy")
+        v = fn(XX, YY, 0.0, tt)
+        return np.broadcast_to(np.asarray(v, dtype=float), XX.shape).copy()
+
+    fields = {name: [ev(e, t_n - m) for m in range(3)]
+              for name, e in (("rho", rho), ("ux", ux), ("uy", uy))}
+    Fxy = (ev(Fx, t_n), ev(Fy, t_n))
+    return [ev(e, t_n) for e in T], fields, Fxy
+
+
+def test_terms_match_symbolic_continuum(orc):
+    """Every discrete term (eq. 18 stencils, eq. 17 in time) matches the exact
+    continuum term of eqs. (10)/(11) on a smooth field to the schemes'
+    truncation error; RHS^{Omega,6} vanishes in 2D."""
+    n, tau, wt, t_n = 128, 0.58, 2e-3, 10.0
+    exact, fl, (Fx, Fy) = _symbolic_terms(n, tau, t_n, wt)
+    got = orc.terms(tau, fl["rho"], fl["ux"], fl["uy"], Fx, Fy)
+    for q in range(13):
+        scale = max(np.max(np.abs(exact[q])), 1e-300)
+        if q == 12:
+            assert np.max(np.abs(got[q])) == 0.0
+            assert np.max(np.abs(exact[q])) < 1e-30
+            continue
+        # time derivatives carry the BDF2 error O(wt^2), space ones O(k^8)
+        tol = 1e-5 if q in (0, 6) else 2e-8
+        err = np.max(np.abs(got[q] - exact[q])) / scale
+        assert err < tol, (orc.TERM_NAMES[q], err)
+
+
+def test_divergence_terms_vanish_on_whole_domain(orc):
+    """At L = N the flux terms RHS^{E,1}, RHS^{E,5}, RHS^{O,1}, RHS^{O,5}
+    telescope to zero (centred differences on a periodic grid)."""
+    n = 32
+    fl = [li.smooth_fields(n, n, seed=s, amp=0.03) for s in range(10, 19)]
+    rho3 = [1 + fl[0], 1 + fl[1], 1 + fl[2]]
+    ux3, uy3 = fl[3:6], fl[6:9]
+    Fx = li.smooth_fields(n, n, seed=30, amp=1e-4)
+    Fy = li.smooth_fields(n, n, seed=31, amp=1e-4)
+    T = orc.terms(0.55, rho3, ux3, uy3, Fx, Fy)
+    for q in (1, 5, 7, 11):
+        assert abs(T[q].mean()) < 1e-14 * np.max(np.abs(T[q])), orc.TERM_NAMES[q]
+    assert np.all(T[12] == 0)
+
+
+# --------------------------------------------------------------------------
+# Sub-volume averages and balancing errors, eqs. (10)-(13), Table 1
+# --------------------------------------------------------------------------
+
+def test_box_mean_matches_brute_force_numpy(orc):
+    """Box averages with periodic wrap against an independent numpy sum, every
+    L and every origin on small grids (square and rectangular)."""
+    rng = np.random.default_rng(8)
+    for (ny, nx) in [(8, 8), (5, 7), (16, 12)]:
+        A = rng.standard_normal((ny, nx))
+        for L in range(1, min(nx, ny) + 1):
+            for y0 in range(ny):
+                for x0 in range(nx):
+                    ref = np.roll(np.roll(A, -y0, axis=0), -x0, axis=1)[:L, :L].mean()
+                    assert abs(orc.box_mean(A, x0, y0, L) - ref) < 1e-14
+
+
+def test_all_origin_average_equals_global_mean(orc):
+    """Averaging box means over all periodic origins gives the global mean for
+    every L; at L = N every box is the whole domain (zero spread)."""
+    n = 12
+    T = np.stack([li.smooth_fields(n, n, seed=40 + q, amp=1.0) + 0.1 * q for q in range(13)])
+    st = orc.balance_stats(T, [1, 3, 4, 12])
+    for iL in range(4):
+        np.testing.assert_allclose(st[iL, 2:, 0], T.reshape(13, -1).mean(axis=1),
+                                   rtol=0, atol=5e-14)
+    assert np.all(np.abs(st[3, 2:, 1]) < 1e-14)
+    # L = 1 boxes are single cells: spread is the population std of the field
+    np.testing.assert_allclose(st[0, 2:, 1], T.reshape(13, -1).std(axis=1), rtol=1e-12)
+
+
+def test_balancing_error_special_cases(orc):
+    """Eqs. (12), (13) on constant term fields: an exact balance gives 0, a
+    known imbalance gives imbalance / max |RHS^i|."""
+    n = 4
+    vals = np.zeros(13)
+    vals[0] = 1.0                               # LHS^E
+    vals[1:6] = [0.5, 0.25, -0.25, 0.75, -0.25]  # sums to 1
+    vals[6] = -2.0                              # LHS^O
+    vals[7:13] = [-1.0, -0.5, -0.5, 0.0, 0.0, 0.0]
+    T = np.broadcast_to(vals[:, None, None], (13, n, n)).copy()
+    v = orc.box_values(T, 1, 2, 3)
+    assert v[0] == 0.0 and v[1] == 0.0
+    np.testing.assert_allclose(v[2:], vals, rtol=0, atol=1e-15)
+    T[3] += 0.15  # RHS^{E,3}: -0.25 -> -0.10; sum 1.15; max |RHS| = 0.75
+    T[7] -= 1.0   # RHS^{O,1}: -1 -> -2; sum -3; max |RHS| = 2
+    v = orc.box_values(T, 0, 0, 2)
+    assert abs(v[0] - 0.15 / 0.75) < 1e-15
+    assert abs(v[1] - 1.0 / 2.0) < 1e-15
+    Z = np.zeros((13, n, n))
+    assert orc.box_values(Z, 0, 0, 2)[0] == 0.0
+    Z[0] = 1.0
+    assert orc.box_values(Z, 0, 0, 2)[0] == np.inf
+
+
+def test_table1_box_counts_match_paper():
+    """Number of sub-volumes per size, the paper's Table 1 (256^2 grid)."""
+    with open(os.path.join(GOLDEN, "table1_box_counts.json")) as fh:
+        g = json.load(fh)
+    for row in g["rows"]:
+        for L in row["L_examples"]:
+            assert li.table1_count(L, g["grid"]) == row["count"], L
+    o = li.table1_origins(256, 32, seed=1)
+    assert o.shape == (5000, 2) and o.min() >= 0 and o.max() <= 256 - 32
+
+
+def test_global_budget_of_decaying_run(orc):
+    """Eq. (8) integrated over the periodic domain: the flux terms vanish, so
+    d<E>/dt = -<eps> + <u.F> + <p div u>; the last (compressibility) term is
+    small at low Mach, so the first two must close the budget to a few %."""
+    n, tau = 32, 0.56
+    rho, ux, uy = li.random_phase(n, seed=3, u_rms=0.02, k_peak=3.0)
+    f = orc.init(rho, ux, uy)
+    f = orc.run(f, 200, tau)  # let the initial acoustic transient relax
+    g0 = orc.global_quantities(f, tau)
+    f1 = orc.run(f, 1, tau)
+    fm = orc.run(f, -0 + 0, tau)  # same state (no steps)
+    assert np.array_equal(fm, f)
+    f2 = orc.run(f1, 1, tau)
+    e0 = g0[3]
+    e2 = orc.global_quantities(f2, tau)[3]
+    g1 = orc.global_quantities(f1, tau)
+    dEdt = (e2 - e0) / 2.0
+    assert abs(dEdt - (-g1[6] + g1[5])) < 0.05 * abs(g1[6])
