@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the D2Q9 LBGK hot path on GB300.
+
+Workload (one bench step): the decaying 2D turbulence ensemble -- 64 members
+of 512^2, tau 0.52, FP32 deviation populations, random-phase initial fields
+(seed 1000 + member, u_rms 0.02) -- advanced by one diagnostic period of 200
+time steps (the batched stream-collide, one launch per step for all
+members, replayed from CUDA graphs), followed by the diagnostic event: the
+moment snapshots of the three last time levels and, for every member, the
+sub-volume energy/enstrophy balance (terms, summed-area tables, balancing
+errors and their statistics) at L = 2, 4, ..., 256 over all periodic
+origins.
+
+Metric: aggregate GLUPS (lattice updates per second over all members and
+GPUs, diagnostics included), plus the roofline of the dominant kernel
+(stream-collide, 72 algorithmic bytes per update), the plain single-instance
+FP64 step beside it, an end-to-end figure through the C ABI with host
+buffers, and the FP64 CPU oracle timed on a bounded sample on the host.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+(N > 1 under torch.distributed.run: members are sharded, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbm_inputs as li  # noqa: E402
+
+METRIC = "D2Q9 GLUPS & % HBM roofline, batched FP32 vs plain FP64 at ≤2e-6 err"
+BYTES_PER_LU_F32 = 72
+BYTES_PER_LU_F64 = 144
+FALLBACK_HBM_GBS = 6800.0
+PERIOD = 200           # time steps per bench step (one diagnostic period)
+PURE_STEPS = PERIOD - 3  # steps before the three snapshot levels
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1809_06735_gb300", "csrc", "lbm_step.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the stream-collide kernel from the committed
+    ncu summary, valid only while the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "step_f32_vec_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_full_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        smax = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if s[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# CPU (oracle) sample: one member, one full diagnostic period, diagnostic on
+# sampled origins.
+# ---------------------------------------------------------------------------
+
+def oracle_period_sample(member_seed: int, n_steps: int = PERIOD, origins_per_L: int = 256):
+    import oracle
+    wl = li.decaying_ensemble_workload()
+    n, tau = wl["n"], wl["tau"]
+    rho, ux, uy = li.random_phase(n, seed=member_seed, u_rms=wl["u_rms"])
+    f = oracle.init(rho, ux, uy)
+    rng = np.random.default_rng(member_seed)
+    origins = rng.integers(0, n, size=(origins_per_L, 2)).astype(np.int32)
+    t0 = time.perf_counter()
+    f_a = oracle.run(f, n_steps - 2, tau)
+    f_b = oracle.run(f_a, 1, tau)
+    f_c = oracle.run(f_b, 1, tau)
+    T = oracle.terms_from_populations(f_c, f_b, f_a, tau)
+    oracle.balance_stats(T, wl["Ls"], origins=origins)
+    dt = time.perf_counter() - t0
+    return n * n * n_steps, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    import oracle
+    oracle.build()
+    wl = li.decaying_ensemble_workload()
+    for w in range(args.warmup):
+        oracle_period_sample(wl["seed0"] + w, n_steps=20, origins_per_L=16)
+    lu, secs = 0, 0.0
+    for k in range(args.steps):
+        a, b = oracle_period_sample(wl["seed0"] + k, n_steps=20, origins_per_L=16)
+        lu += a
+        secs += b
+    v = lu / secs / 1e9
+    sample = ("per step: one 512^2 member of the 64, 20 LBM steps of the 200-step period, "
+              "then the diagnostic on 16 random origins per L (L=2..256)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload_config():
+    wl = li.decaying_ensemble_workload()
+    return {"workload": wl["name"], "members_per_gpu": wl["members"], "grid": [wl["n"], wl["n"]],
+            "tau": wl["tau"], "precision": "fp32 deviation populations, fp64 diagnostics",
+            "lbm_steps_per_step": PERIOD,
+            "diagnostic": "per step, every member: balance terms + SAT + all-origin boxes "
+                          "at L=2..256",
+            "l2": "inputs larger than L2 (1.2 GB of populations per GPU), no flush"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1809_06735_gb300 as P
+    P.load_library()
+
+    wl = li.decaying_ensemble_workload()
+    n, tau, M = wl["n"], wl["tau"], wl["members"]
+    stream = torch.cuda.current_stream(dev)
+    lat = P.Lattice([P.Member(n, n, tau)] * M, precision=32, diag_every=PERIOD,
+                    graph_steps=PURE_STEPS - 1, stream=stream, device=dev)
+    # pinned host initial fields (also the e2e inputs)
+    host = torch.empty((M, 3, n, n), dtype=torch.float64, pin_memory=True)
+    for m in range(M):
+        r, u, v = li.random_phase(n, seed=wl["seed0"] + rank * M + m, u_rms=wl["u_rms"])
+        host[m, 0].copy_(torch.from_numpy(r))
+        host[m, 1].copy_(torch.from_numpy(u))
+        host[m, 2].copy_(torch.from_numpy(v))
+    hnp = host.numpy()
+    dev_fields = host.to(dev)
+    for m in range(M):
+        lat.init_fields(m, dev_fields[m, 0], dev_fields[m, 1], dev_fields[m, 2])
+    torch.cuda.synchronize()
+    Ls = wl["Ls"]
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def bench_step(rec=None):
+        if rec is not None:
+            rec[0].record(stream)
+        lat.step(PURE_STEPS)
+        if rec is not None:
+            rec[1].record(stream)
+        lat.step(PERIOD - PURE_STEPS)
+        out = [lat.subvolume_balance(m, Ls) for m in range(M)]
+        return out
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    recs = [(ev(), ev()) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = lat.launch_count
+    t0, t1 = ev(), ev()
+    t0.record(stream)
+    stats = None
+    for k in range(args.steps):
+        stats = bench_step(recs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = lat.launch_count - launches0
+    elapsed = t0.elapsed_time(t1) / 1e3
+    pure = sum(a.elapsed_time(b) for a, b in recs) / 1e3
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    assert stats is not None and np.all(np.isfinite(stats[0][:, 2:, 0]))
+    lu_per_gpu_step = M * n * n * PERIOD
+    value = ws * lu_per_gpu_step * args.steps / elapsed / 1e9
+    kern_s = pure / (args.steps * PURE_STEPS)
+    step_glups = M * n * n / kern_s / 1e9
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_LU_F32 * M * n * n / kern_s / 1e9
+
+    # plain single-instance FP64 step on one 512^2 member
+    lat64 = P.Lattice([P.Member(n, n, tau)], precision=64, graph_steps=20, stream=stream,
+                      device=dev)
+    lat64.init_fields(0, dev_fields[0, 0], dev_fields[0, 1], dev_fields[0, 2])
+    lat64.step(40)
+    a, b = ev(), ev()
+    torch.cuda.synchronize()
+    a.record(stream)
+    lat64.step(200)
+    b.record(stream)
+    torch.cuda.synchronize()
+    fp64_s = a.elapsed_time(b) / 1e3 / 200
+    fp64_glups = n * n / fp64_s / 1e9
+    del lat64
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # initial fields of all members from pinned host memory, runs the period
+    # and reads the statistics back.
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        for m in range(M):
+            lat.init_fields(m, hnp[m, 0], hnp[m, 1], hnp[m, 2])
+        lat.step(PERIOD)
+        for m in range(M):
+            lat.subvolume_balance(m, Ls)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te
+    e2e = {"value": ws * lu_per_gpu_step * e2e_steps / te / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": int(M * 3 * n * n * 8),
+           "d2h_bytes_per_step": int(M * len(Ls) * 30 * 8),
+           "note": "init from pinned host fields + 200 steps + balance stats to host, "
+                   "per step, wall clock"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        lu, secs = oracle_period_sample(wl["seed0"])
+        cpu = {"value": lu / secs / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+               "sample": "one 512^2 member of the 64: the full 200-step period, then the "
+                         "diagnostic with 256 random origins per L (L=2..256)",
+               "seconds": secs}
+
+    if rank == 0:
+        traffic = profiled_traffic()
+        line = {
+            "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(),
+            "roofline": {"bound": "hbm", "kernel": "k_step_f32_vec", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak,
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_launch": BYTES_PER_LU_F32 * M * n * n,
+                         "avg_launch_ms": kern_s * 1e3},
+            "step_only_glups_per_gpu": step_glups,
+            "fp64_plain_single_instance": {"glups": fp64_glups, "grid": [n, n],
+                                           "ratio_batched_fp32_over_fp64": step_glups / fp64_glups},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) D2Q9 lattice Boltzmann library.
+ *
+ * The library implements, as CUDA kernels, the method of Tauzin et al.,
+ * "A numerical tool for the study of the hydrodynamic recovery of the
+ * Lattice Boltzmann Method" (Comput. & Fluids 172, 2018):
+ *   - the D2Q9 BGK time step of eq. (1) with the equilibrium of eq. (2) and
+ *     the exact-difference-method forcing named in Sec. 3, on doubly
+ *     periodic grids, for a batch ("ensemble") of independent members;
+ *   - the sub-volume (L x L box) averages of the energy and enstrophy
+ *     balance terms of eqs. (8)-(11), with eq. (17) in time and eq. (18) in
+ *     space, and the balancing errors of eqs. (12), (13), for many L;
+ *   - an adjoint (reverse-mode) step of the time step and of a box-averaged
+ *     dissipation objective (no counterpart in the paper).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: c_0 = (0,0); c_1..c_4 = (1,0), (0,1), (-1,0), (0,-1);
+ *          c_5..c_8 = (1,1), (-1,1), (-1,-1), (1,-1); weights 4/9, 1/9, 1/36;
+ *          c_s^2 = 1/3.
+ * Arrays:  row-major with x fastest.  A scalar field is double[ny][nx]; a
+ *          population array is double[9][ny][nx] in the lattice order above.
+ * State:   the public state of a member at time n is the pre-collision
+ *          population f_l(x, n) of eq. (1).  The device keeps its own
+ *          storage convention (post-collision, pull layout, FP32 deviation
+ *          g_l = f_l - t_l rho0 for precision 32); the get/set calls convert.
+ * Force:   F(x) = F_ext(x) - alpha j(x) with j = sum_l c_l f_l the bare
+ *          momentum and F_ext = F0 (sin(2 pi kf y / ny), sin(2 pi kf x / nx))
+ *          for force_kind 1 (zero for force_kind 0).  The EDM term is
+ *          F_l = f_eq_l(rho, u + F/rho) - f_eq_l(rho, u), u = j / rho.
+ * Velocity of the diagnostic: u = (j + F/2) / rho.
+ * Memory:  the caller owns every buffer.  The library never allocates device
+ *          memory: lbm_workspace_size() states how many bytes of device
+ *          memory one handle needs, and the caller passes that buffer to
+ *          lbm_create().  Pointers documented as "device" must point into
+ *          device memory of the current CUDA device; "host" pointers to
+ *          ordinary (ideally pinned) host memory.
+ * Streams: all device work of a handle is issued on the stream given in
+ *          lbm_config.cuda_stream (NULL = the legacy default stream).  Calls
+ *          return once the work is queued, except where a call is documented
+ *          as synchronising (it writes host memory).
+ * Errors:  every int-returning call returns LBM_OK (0) or a negative
+ *          LBM_ERR_* code and never throws; lbm_last_error() gives the
+ *          message.  A CUDA error inside a call is reported as LBM_ERR_CUDA.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)       /* invalid argument */
+#define LBM_ERR_WORKSPACE (-2) /* workspace too small or misaligned */
+#define LBM_ERR_CUDA (-3)      /* a CUDA call failed */
+#define LBM_ERR_HISTORY (-4)   /* fewer than 3 consecutive snapshots */
+#define LBM_ERR_DIVERGED (-5)  /* member state contains NaN/Inf or rho <= 0 */
+#define LBM_ERR_TIMEOUT (-6)   /* a bounded device wait gave up */
+
+#define LBM_NTERMS 13 /* LHS^E, RHS^{E,1..5}, LHS^Omega, RHS^{Omega,1..6} */
+#define LBM_NQUANT 15 /* delta^E, delta^Omega, then the 13 terms */
+#define LBM_NGLOBAL 7 /* see lbm_global_balance */
+
+/* One ensemble member: a doubly periodic nx x ny grid (eq. (1)). */
+typedef struct lbm_member_cfg {
+  int nx, ny;       /* grid size, each >= 1 (the vectorised FP32 kernel
+                       serves nx % 4 == 0, another kernel any nx) */
+  double tau;       /* BGK relaxation time of eq. (1); nu = (tau - 1/2)/3,
+                       eq. (5).  Must be > 0.5 */
+  double rho0;      /* reference density of the FP32 deviation storage */
+  int force_kind;   /* 0: no external force; 1: Kolmogorov force */
+  int kf;           /* Kolmogorov wavenumber, in units of 2 pi / n */
+  double F0;        /* Kolmogorov amplitude */
+  double alpha;     /* linear drag coefficient on the bare momentum */
+} lbm_member_cfg;
+
+typedef struct lbm_config {
+  int n_members;                 /* >= 1 */
+  const lbm_member_cfg *members; /* host array of n_members (copied) */
+  int precision;   /* 32: FP32 deviation populations; 64: plain FP64 */
+  int storage;     /* 0: default (double buffer); other values reserved */
+  int diag_every;  /* > 0: lbm_step records the moment snapshots of the
+                      time levels n = k*diag_every - 2, -1, 0 that the
+                      eq. (17) time derivative needs; 0: only explicit
+                      lbm_record_snapshot() calls record */
+  int graph_steps; /* > 0: lbm_step replays CUDA graphs of this many steps
+                      (rounded up to even); 0: plain launches */
+  void *cuda_stream; /* cudaStream_t of all work; NULL = default stream */
+} lbm_config;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Bytes of device workspace a handle with this configuration needs.
+ * Host-only; validates the configuration. */
+int lbm_workspace_size(const lbm_config *cfg, size_t *bytes);
+
+/* Creates a handle over a caller-owned device workspace (device pointer,
+ * 256-byte aligned, at least lbm_workspace_size() bytes, owned by the caller
+ * and kept alive until lbm_destroy).  Uploads the member table and the
+ * forcing tables; the populations are undefined until lbm_init_fields or
+ * lbm_set_populations.  *out receives the handle (host memory owned by the
+ * library, freed by lbm_destroy).  Synchronises the stream once. */
+int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes,
+               lbm_handle **out);
+
+/* Releases the host-side handle and its CUDA graphs; the workspace stays
+ * the caller's. */
+int lbm_destroy(lbm_handle *h);
+
+/* Sets member `member` (or every member when member < 0, all sharing the
+ * same fields, which then must fit each member's grid) to the equilibrium
+ * state f_l(x, 0) = f_eq_l(rho(x), u(x)) of eq. (2) and resets the step
+ * counter and snapshot history of the handle.  rho, ux, uy: double[ny][nx],
+ * host pointers if on_device == 0 (copied through the workspace; the call
+ * synchronises), device pointers otherwise. */
+int lbm_init_fields(lbm_handle *h, int member, const double *rho,
+                    const double *ux, const double *uy, int on_device);
+
+/* Advances every member by nsteps time steps of eq. (1): per cell, pull the
+ * populations from the neighbours x - c_l, take rho and j, form F, collide
+ * with the BGK operator and the EDM term, store.  When diag_every > 0 the
+ * snapshots of the required time levels are recorded on the way. */
+int lbm_step(lbm_handle *h, int nsteps);
+
+/* Current time step n of the handle (number of steps since init). */
+long long lbm_time(const lbm_handle *h);
+
+/* Number of CUDA kernels this handle has issued so far (each node of a
+ * replayed CUDA graph counts once).  Host-only. */
+long long lbm_launch_count(const lbm_handle *h);
+
+/* Records the moment snapshot (rho, j) of every member at the current time
+ * into the 3-slot history used by the eq. (17) time derivative. */
+int lbm_record_snapshot(lbm_handle *h);
+
+/* Moments of member `member` at the current time (device pointers,
+ * double[ny][nx] each, any may be NULL): rho = sum f (below eq. (2)),
+ * u = (j + F/2)/rho, and the vorticity omega = D_x u_y - D_y u_x with D the
+ * 8th-order centred difference of eq. (18). */
+int lbm_moments(lbm_handle *h, int member, double *rho, double *ux,
+                double *uy, double *omega);
+
+/* Whole-grid quantities of member `member` at the current time, in FP64
+ * (host pointer to LBM_NGLOBAL doubles; synchronises):
+ *   out[0] = sum rho, out[1] = sum j_x, out[2] = sum j_y,
+ *   out[3] = <E> = mean of rho |u|^2 / 2, out[4] = <Omega> = mean of w^2/2,
+ *   out[5] = <u . F>, out[6] = <eps> = mean of nu rho S_ij d_j u_i
+ * (u the diagnostic velocity, S_ij = d_j u_i + d_i u_j, eq. (18) stencils):
+ * the L = N case of the energy/enstrophy budget of eqs. (8)-(11). */
+int lbm_global_balance(lbm_handle *h, int member, double *out);
+
+/* Sub-volume balance of member `member` at the current time n (eqs. (8)-(13),
+ * (17), (18)), for each box size L[i] (i < nL; host array):
+ * the local terms LHS^E, RHS^{E,1..5}, LHS^Omega, RHS^{Omega,1..6} are
+ * formed from the snapshots at n, n-1, n-2 (the snapshot at n is recorded
+ * if missing; LBM_ERR_HISTORY if n-1 or n-2 is missing), averaged over L x L
+ * boxes (periodic wrap) through FP64 summed-area tables, and turned into the
+ * balancing errors delta^E, delta^Omega (0 when numerator and denominator
+ * are 0, +Inf when only the denominator is).
+ * Boxes: every one of the nx*ny periodic origins when origins == NULL, else
+ * the n_origins lower-left corners (x0, y0) in the host array
+ * origins[2*n_origins] (0 <= x0 < nx, 0 <= y0 < ny), the same for every L.
+ * Sizes with L < 1 or L > min(nx, ny) are skipped: their statistics are NaN.
+ * stats_out (host, double[nL][15][2]; synchronises): mean and population
+ * standard deviation over the boxes of the 15 quantities
+ * [delta^E, delta^Omega, LHS^E, RHS^{E,1..5}, LHS^O, RHS^{O,1..6}].
+ * per_box_out (device, double[nL][n_boxes][15], may be NULL; then every L
+ * must fit the grid, else LBM_ERR_ARG): every box. */
+int lbm_subvolume_balance(lbm_handle *h, int member, const int *L, int nL,
+                          const int *origins, int n_origins, double *stats_out,
+                          double *per_box_out);
+
+/* Public pre-collision populations f_l(x, n) of member `member` as
+ * double[9][ny][nx] (full f, also for FP32 storage).  Host pointer if
+ * on_device == 0 (the call synchronises), device pointer otherwise.
+ * get then set restores the FP64 state bit for bit. */
+int lbm_get_populations(lbm_handle *h, int member, double *f, int on_device);
+int lbm_set_populations(lbm_handle *h, int member, const double *f,
+                        int on_device);
+
+/* Divergence check of member `member` at the current time: *status = 1 if
+ * any population or density is NaN/Inf or rho <= 0, else 0.  Synchronises. */
+int lbm_member_status(lbm_handle *h, int member, int *status);
+
+/* Adjoint of one time step of member `member` (no counterpart in the paper;
+ * the differentiation of the forward model).  With the forward map
+ * f(n+1) = S(f(n); tau, F0) of eq. (1), given lambda_in = dJ/df(n+1) as
+ * double[9][ny][nx] (device), writes lambda_out = (dS/df(n))^T lambda_in
+ * + dJ_n/df(n) (device, may not alias lambda_in), where J_n is the
+ * objective term at time n: the L x L box average, origin (bx, by), of the
+ * dissipation term RHS^{E,4} of eq. (8), weighted by obj_weight (0 to omit).
+ * f_n (device, double[9][ny][nx]) is the public state at time n.  The
+ * contributions of this step to dJ/dtau and dJ/dF0 are ADDED to the FP64
+ * accumulators at the device pointers dJ_dtau and dJ_dF0.  Plain FP64
+ * (either handle precision). */
+int lbm_adjoint_step(lbm_handle *h, int member, const double *f_n,
+                     const double *lambda_in, double *lambda_out,
+                     double obj_weight, int bx, int by, int L,
+                     double *dJ_dtau, double *dJ_dF0);
+
+/* acc[0] += weight * (L x L box average, origin (bx, by), of the dissipation
+ * term RHS^{E,4} of eq. (8) of member `member` at the current time): the
+ * forward objective matching lbm_adjoint_step.  acc is a device pointer to
+ * one double. */
+int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx,
+                             int by, int L, double *acc);
+
+/* Message of the last failing call on this handle (or of the last failing
+ * handle-less call when h is NULL).  Never NULL. */
+const char *lbm_last_error(const lbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H_ */

@@ -1,0 +1,306 @@
+"""GB300 (sm_103a) D2Q9 lattice Boltzmann library with the sub-volume
+energy/enstrophy balance diagnostic of Tauzin et al. (2018).
+
+This module is a thin binding of the C ABI in ``include/lbm.h``: it marshals
+arguments and lets PyTorch provide device memory (the workspace) and the CUDA
+stream.  Every step of the method runs in the CUDA kernels of ``liblbm.so``;
+there is no Python or CPU fallback, and the import fails loudly when the
+library has not been built (``python -m paper_1809_06735_gb300.build`` or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+
+LBM_OK = 0
+ERRORS = {-1: "invalid argument", -2: "workspace", -3: "CUDA error", -4: "history missing",
+          -5: "member diverged", -6: "timeout"}
+NTERMS = 13
+NQUANT = 15
+NGLOBAL = 7
+TERM_NAMES = ["LHS_E", "RHS_E1", "RHS_E2", "RHS_E3", "RHS_E4", "RHS_E5",
+              "LHS_Z", "RHS_Z1", "RHS_Z2", "RHS_Z3", "RHS_Z4", "RHS_Z5", "RHS_Z6"]
+QUANTITY_NAMES = ["delta_E", "delta_Z"] + TERM_NAMES
+GLOBAL_NAMES = ["mass", "jx", "jy", "E", "Omega", "uF", "eps"]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lbm error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _MemberCfg(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("force_kind", ctypes.c_int), ("kf", ctypes.c_int),
+                ("F0", ctypes.c_double), ("alpha", ctypes.c_double)]
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_members", ctypes.c_int), ("members", ctypes.POINTER(_MemberCfg)),
+                ("precision", ctypes.c_int), ("storage", ctypes.c_int),
+                ("diag_every", ctypes.c_int), ("graph_steps", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``liblbm.so`` and declare the C signatures.  Raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"liblbm.so is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    I, P, D, S = ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "lbm_workspace_size": ([ctypes.POINTER(_Config), ctypes.POINTER(S)], I),
+        "lbm_create": ([ctypes.POINTER(_Config), P, S, ctypes.POINTER(P)], I),
+        "lbm_destroy": ([P], I),
+        "lbm_init_fields": ([P, I, P, P, P, I], I),
+        "lbm_step": ([P, I], I),
+        "lbm_time": ([P], ctypes.c_longlong),
+        "lbm_launch_count": ([P], ctypes.c_longlong),
+        "lbm_record_snapshot": ([P], I),
+        "lbm_moments": ([P, I, P, P, P, P], I),
+        "lbm_global_balance": ([P, I, P], I),
+        "lbm_subvolume_balance": ([P, I, P, I, P, I, P, P], I),
+        "lbm_get_populations": ([P, I, P, I], I),
+        "lbm_set_populations": ([P, I, P, I], I),
+        "lbm_member_status": ([P, I, P], I),
+        "lbm_adjoint_step": ([P, I, P, P, P, D, I, I, I, P, P], I),
+        "lbm_objective_accumulate": ([P, I, D, I, I, I, P], I),
+        "lbm_last_error": ([P], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Member:
+    """One ensemble member: an nx x ny doubly periodic grid with relaxation
+    time tau (eq. (1), nu = (tau - 1/2)/3 by eq. (5)), reference density rho0,
+    optional Kolmogorov force F0 (sin(2 pi kf y/ny), sin(2 pi kf x/nx)) and
+    linear drag alpha on the bare momentum."""
+    nx: int
+    ny: int
+    tau: float
+    rho0: float = 1.0
+    force_kind: int = 0
+    kf: int = 0
+    F0: float = 0.0
+    alpha: float = 0.0
+
+    def c(self) -> _MemberCfg:
+        return _MemberCfg(self.nx, self.ny, self.tau, self.rho0, self.force_kind, self.kf,
+                          self.F0, self.alpha)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous(), "tensors passed to the library must be contiguous"
+    return t.data_ptr()
+
+
+class Lattice:
+    """A handle over a batch of members sharing precision and stream.
+
+    ``precision`` 32 stores FP32 deviations f - t rho0 (batched vector kernel),
+    64 stores plain FP64 populations.  The workspace is one torch uint8 CUDA
+    tensor sized by ``lbm_workspace_size``; all work goes to ``stream``
+    (default: the current torch stream at construction)."""
+
+    def __init__(self, members: Sequence[Member], precision: int = 32, diag_every: int = 0,
+                 graph_steps: int = 0, stream=None, device=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.members = list(members)
+        self.precision = precision
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        arr = (_MemberCfg * len(self.members))(*[m.c() for m in self.members])
+        self._arr = arr
+        self._cfg = _Config(len(self.members), arr, precision, 0, diag_every, graph_steps,
+                            ctypes.c_void_p(self.stream.cuda_stream))
+        nbytes = ctypes.c_size_t()
+        self._check(self.lib.lbm_workspace_size(ctypes.byref(self._cfg), ctypes.byref(nbytes)))
+        self.workspace_bytes = nbytes.value
+        self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8,
+                                     device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self._check(self.lib.lbm_create(ctypes.byref(self._cfg), ctypes.c_void_p(aligned),
+                                            self.workspace_bytes, ctypes.byref(h)))
+        self.h = h
+
+    # -- plumbing -------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != LBM_OK:
+            h = getattr(self, "h", None)
+            msg = self.lib.lbm_last_error(h).decode()
+            raise LBMError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.lbm_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, a, dtype=None):
+        torch = self._torch
+        dtype = dtype or torch.float64
+        if isinstance(a, np.ndarray):
+            a = torch.from_numpy(np.ascontiguousarray(a))
+        return a.to(device=self.device, dtype=dtype).contiguous()
+
+    def _shape(self, m):
+        return self.members[m].ny, self.members[m].nx
+
+    # -- state ------------------------------------------------------------
+    def init_fields(self, member: int, rho, ux, uy):
+        """f(x, 0) = f_eq(rho(x), u(x)).  numpy arrays are passed as host
+        pointers (the library copies them), tensors as device pointers."""
+        if isinstance(rho, np.ndarray):
+            r, u, v = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
+            self._check(self.lib.lbm_init_fields(self.h, member, _ptr(r), _ptr(u), _ptr(v), 0))
+        else:
+            r, u, v = (self._dev(a) for a in (rho, ux, uy))
+            self._check(self.lib.lbm_init_fields(self.h, member, _ptr(r), _ptr(u), _ptr(v), 1))
+            self._keep = (r, u, v)
+
+    def step(self, nsteps: int = 1):
+        self._check(self.lib.lbm_step(self.h, int(nsteps)))
+
+    @property
+    def time(self) -> int:
+        return int(self.lib.lbm_time(self.h))
+
+    @property
+    def launch_count(self) -> int:
+        """Kernels issued by this handle so far (graph nodes counted)."""
+        return int(self.lib.lbm_launch_count(self.h))
+
+    def record_snapshot(self):
+        self._check(self.lib.lbm_record_snapshot(self.h))
+
+    def get_populations(self, member: int, out=None):
+        """Public pre-collision populations f[9, ny, nx] (float64, device)."""
+        ny, nx = self._shape(member)
+        if out is None:
+            out = self._torch.empty((9, ny, nx), dtype=self._torch.float64, device=self.device)
+        self._check(self.lib.lbm_get_populations(self.h, member, _ptr(out), 1))
+        return out
+
+    def get_populations_host(self, member: int) -> np.ndarray:
+        ny, nx = self._shape(member)
+        out = np.empty((9, ny, nx))
+        self._check(self.lib.lbm_get_populations(self.h, member, _ptr(out), 0))
+        return out
+
+    def set_populations(self, member: int, f):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            self._check(self.lib.lbm_set_populations(self.h, member, _ptr(f), 0))
+        else:
+            f = self._dev(f)
+            self._check(self.lib.lbm_set_populations(self.h, member, _ptr(f), 1))
+            self._keep_f = f
+
+    def member_status(self, member: int) -> int:
+        s = ctypes.c_int()
+        self._check(self.lib.lbm_member_status(self.h, member, ctypes.byref(s)))
+        return s.value
+
+    # -- diagnostics ------------------------------------------------------
+    def moments(self, member: int):
+        """rho, u = (j + F/2)/rho and omega (eq. (18)) as float64 device tensors."""
+        torch = self._torch
+        ny, nx = self._shape(member)
+        out = {k: torch.empty((ny, nx), dtype=torch.float64, device=self.device)
+               for k in ("rho", "ux", "uy", "omega")}
+        self._check(self.lib.lbm_moments(self.h, member, _ptr(out["rho"]), _ptr(out["ux"]),
+                                         _ptr(out["uy"]), _ptr(out["omega"])))
+        return out
+
+    def global_balance(self, member: int) -> np.ndarray:
+        out = np.empty(NGLOBAL)
+        self._check(self.lib.lbm_global_balance(self.h, member, _ptr(out)))
+        return out
+
+    def subvolume_balance(self, member: int, Ls, origins=None, per_box: bool = False):
+        """Statistics [nL, 15, 2] (mean, population std) of the box quantities
+        [delta^E, delta^Omega, 13 terms]; with ``per_box`` also the device
+        tensor [nL, n_boxes, 15]."""
+        Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+        nL = len(Ls)
+        ny, nx = self._shape(member)
+        if origins is not None:
+            origins = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1, 2)
+            nb = origins.shape[0]
+        else:
+            nb = nx * ny
+        stats = np.empty((nL, NQUANT, 2))
+        pb = None
+        if per_box:
+            pb = self._torch.empty((nL, nb, NQUANT), dtype=self._torch.float64,
+                                   device=self.device)
+        self._check(self.lib.lbm_subvolume_balance(
+            self.h, member, _ptr(Ls), nL, _ptr(origins) if origins is not None else None,
+            nb if origins is not None else 0, _ptr(stats), _ptr(pb)))
+        return (stats, pb) if per_box else stats
+
+    # -- adjoint ------------------------------------------------------------
+    def adjoint_step(self, member: int, f_n, lam_in, lam_out, weight: float, box, L: int,
+                     dJ_dtau, dJ_dF0):
+        """lam_out = (dS/df)^T lam_in + weight * dJ_n/df at the state f_n; adds
+        the parameter gradients of this step into dJ_dtau, dJ_dF0 (device
+        float64 scalars)."""
+        self._check(self.lib.lbm_adjoint_step(self.h, member, _ptr(f_n), _ptr(lam_in),
+                                              _ptr(lam_out), float(weight), int(box[0]),
+                                              int(box[1]), int(L), _ptr(dJ_dtau),
+                                              _ptr(dJ_dF0)))
+
+    def objective_accumulate(self, member: int, weight: float, box, L: int, acc):
+        """acc += weight * (L x L box average of RHS^{E,4} at the current time)."""
+        self._check(self.lib.lbm_objective_accumulate(self.h, member, float(weight),
+                                                      int(box[0]), int(box[1]), int(L),
+                                                      _ptr(acc)))
+
+
+def workspace_size(members: Sequence[Member], precision: int = 32, diag_every: int = 0,
+                   graph_steps: int = 0) -> int:
+    """Host-only query of the device workspace bytes for a configuration."""
+    lib = load_library()
+    arr = (_MemberCfg * len(members))(*[m.c() for m in members])
+    cfg = _Config(len(members), arr, precision, 0, diag_every, graph_steps, None)
+    n = ctypes.c_size_t()
+    rc = lib.lbm_workspace_size(ctypes.byref(cfg), ctypes.byref(n))
+    if rc != LBM_OK:
+        raise LBMError(rc, lib.lbm_last_error(None).decode())
+    return n.value

@@ -1,0 +1,648 @@
+// C ABI and host runtime of the D2Q9 library: configuration checks,
+// workspace layout, the per-member tile table of the batched stream-collide,
+// CUDA-graph replay of the step loop, the launch-shape autotuner, the
+// snapshot ring of the eq. (17) time derivative, and the diagnostic calls.
+//
+// The runtime never allocates device memory: every device buffer is carved
+// out of the caller's workspace (see lbm_workspace_size).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+
+using lbm::Member;
+using lbm::Tile;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxL = 32;          // box sizes per balance call
+constexpr int kTileW = 128;        // cells per warp row in the vector kernel
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+thread_local std::string g_last_error = "no error";
+
+struct Layout {
+  size_t members, tiles, status;
+  std::vector<size_t> pop0, pop1, fx, fy, fx64, fy64, snap;
+  size_t scratch, partials, stats, Ls, out7, origins;
+  size_t total;
+  size_t Nmax;
+  size_t scratch_fields;
+};
+
+int pitch_of(int nx, int precision) {
+  // rows start on 16-byte boundaries: 4 floats or 2 doubles
+  const int q = precision == 32 ? 4 : 2;
+  return (nx + q - 1) / q * q;
+}
+
+bool vector_eligible(const lbm_member_cfg &m, int precision) {
+  return precision == 32 && m.nx % 4 == 0;
+}
+
+int check_config(const lbm_config *cfg, std::string &err) {
+  if (!cfg) { err = "config is NULL"; return LBM_ERR_ARG; }
+  if (cfg->n_members < 1 || !cfg->members) { err = "n_members must be >= 1 with a member array"; return LBM_ERR_ARG; }
+  if (cfg->precision != 32 && cfg->precision != 64) { err = "precision must be 32 or 64"; return LBM_ERR_ARG; }
+  if (cfg->storage != 0) { err = "storage: only 0 (double buffer) is available"; return LBM_ERR_ARG; }
+  if (cfg->diag_every < 0 || cfg->graph_steps < 0) { err = "diag_every and graph_steps must be >= 0"; return LBM_ERR_ARG; }
+  for (int m = 0; m < cfg->n_members; ++m) {
+    const lbm_member_cfg &c = cfg->members[m];
+    char buf[160];
+    if (c.nx < 1 || c.ny < 1 || (long long)c.nx * c.ny > (1LL << 30)) {
+      snprintf(buf, sizeof buf, "member %d: grid %dx%d out of range", m, c.nx, c.ny);
+      err = buf; return LBM_ERR_ARG;
+    }
+    if (!(c.tau > 0.5) || !std::isfinite(c.tau)) {
+      snprintf(buf, sizeof buf, "member %d: tau must be > 0.5", m); err = buf; return LBM_ERR_ARG;
+    }
+    if (!(c.rho0 > 0) || !std::isfinite(c.rho0)) {
+      snprintf(buf, sizeof buf, "member %d: rho0 must be > 0", m); err = buf; return LBM_ERR_ARG;
+    }
+    if (c.force_kind != 0 && c.force_kind != 1) {
+      snprintf(buf, sizeof buf, "member %d: force_kind must be 0 or 1", m); err = buf; return LBM_ERR_ARG;
+    }
+    if (!std::isfinite(c.F0) || !std::isfinite(c.alpha)) {
+      snprintf(buf, sizeof buf, "member %d: F0/alpha not finite", m); err = buf; return LBM_ERR_ARG;
+    }
+  }
+  return LBM_OK;
+}
+
+Layout make_layout(const lbm_config *cfg) {
+  Layout L{};
+  const int n = cfg->n_members;
+  const size_t es = cfg->precision == 32 ? 4 : 8;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  L.members = take(sizeof(Member) * n);
+  // tile table sized for the smallest tile height (1 row)
+  size_t max_tiles = 0;
+  for (int m = 0; m < n; ++m) {
+    const lbm_member_cfg &c = cfg->members[m];
+    if (vector_eligible(c, cfg->precision))
+      max_tiles += (size_t)((c.nx + kTileW - 1) / kTileW) * c.ny;
+  }
+  L.tiles = take(sizeof(Tile) * std::max<size_t>(max_tiles, 1));
+  L.status = take(sizeof(int) * n);
+  L.Nmax = 0;
+  for (int m = 0; m < n; ++m) {
+    const lbm_member_cfg &c = cfg->members[m];
+    const size_t N = (size_t)c.nx * c.ny;
+    const size_t plane = (size_t)c.ny * pitch_of(c.nx, cfg->precision);
+    L.pop0.push_back(take(es * 9 * plane));
+    L.pop1.push_back(take(es * 9 * plane));
+    L.fx.push_back(take(es * c.ny));
+    L.fy.push_back(take(es * c.nx));
+    L.fx64.push_back(take(8 * c.ny));
+    L.fy64.push_back(take(8 * c.nx));
+    L.snap.push_back(take(8 * 9 * N));
+    L.Nmax = std::max(L.Nmax, N);
+  }
+  L.scratch_fields = lbm::kDiagFields;
+  L.scratch = take(8 * L.scratch_fields * L.Nmax);
+  L.partials = take(8 * lbm::diag_partials_needed(kMaxL));
+  L.stats = take(8 * kMaxL * 30);
+  L.Ls = take(4 * kMaxL);
+  L.out7 = take(8 * 8);
+  L.origins = take(8 * L.Nmax);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct lbm_handle {
+  lbm_config cfg;
+  std::vector<lbm_member_cfg> mcfg;
+  std::vector<Member> hm;
+  Layout lay;
+  char *ws = nullptr;
+  Member *d_members = nullptr;
+  Tile *d_tiles = nullptr;
+  int ntiles = 0;
+  std::vector<int> scalar_members;
+  int precision = 32;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int cur = 0;
+  long long t = 0;
+  long long ring_time[3] = {-1, -1, -1};
+  lbm::DiagScratch sc{};
+  lbm::LaunchCfg lc{8, 1, 0};
+  int graph_k = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long long launches = 0;  // kernels issued (graph replays count their nodes)
+  std::string err = "no error";
+};
+
+namespace {
+
+int fail(lbm_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(h, LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+char *ws_at(lbm_handle *h, size_t off) { return h->ws + off; }
+
+int build_tiles(lbm_handle *h) {
+  std::vector<Tile> tiles;
+  h->scalar_members.clear();
+  const int rows = h->lc.block_warps_y * h->lc.rows_per_warp;
+  for (int m = 0; m < (int)h->mcfg.size(); ++m) {
+    const lbm_member_cfg &c = h->mcfg[m];
+    if (!vector_eligible(c, h->precision)) {
+      h->scalar_members.push_back(m);
+      continue;
+    }
+    for (int y0 = 0; y0 < c.ny; y0 += rows)
+      for (int x0 = 0; x0 < c.nx; x0 += kTileW) tiles.push_back(Tile{m, x0, y0, 0});
+  }
+  h->ntiles = (int)tiles.size();
+  if (!tiles.empty())
+    CK(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(),
+                       cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+// One time step of every member on stream s.
+int launch_one_step(lbm_handle *h, cudaStream_t s, int cur) {
+  if (h->ntiles > 0) CK(lbm::launch_step_f32_vec(h->d_members, h->d_tiles, h->ntiles, cur, h->lc, s));
+  for (int m : h->scalar_members)
+    CK(lbm::launch_step_scalar(h->precision, h->d_members, m, h->mcfg[m].nx, h->mcfg[m].ny, cur, s));
+  return LBM_OK;
+}
+
+long long kernels_per_step(const lbm_handle *h) {
+  return (h->ntiles > 0 ? 1 : 0) + (long long)h->scalar_members.size();
+}
+
+void drop_graphs(lbm_handle *h) {
+  for (auto &g : h->graph)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+int get_graph(lbm_handle *h, int cur, cudaGraphExec_t *out) {
+  if (!h->graph[cur]) {
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int c = cur, rc = LBM_OK;
+    for (int i = 0; i < h->graph_k && rc == LBM_OK; ++i) {
+      rc = launch_one_step(h, h->cap_stream, c);
+      c ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc != LBM_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    CK(e);
+    e = cudaGraphInstantiate(&h->graph[cur], g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+  }
+  *out = h->graph[cur];
+  return LBM_OK;
+}
+
+int run_steps(lbm_handle *h, long long k) {
+  while (k > 0) {
+    if (h->graph_k > 0 && k >= h->graph_k) {
+      cudaGraphExec_t g;
+      int rc = get_graph(h, h->cur, &g);
+      if (rc) return rc;
+      CK(cudaGraphLaunch(g, h->stream));
+      h->launches += (long long)h->graph_k * kernels_per_step(h);
+      k -= h->graph_k;
+      h->t += h->graph_k;  // graph_k is even: buffer parity unchanged
+    } else {
+      int rc = launch_one_step(h, h->stream, h->cur);
+      if (rc) return rc;
+      h->launches += kernels_per_step(h);
+      h->cur ^= 1;
+      k -= 1;
+      h->t += 1;
+    }
+  }
+  return LBM_OK;
+}
+
+bool is_snap_time(const lbm_handle *h, long long t) {
+  const long long D = h->cfg.diag_every;
+  if (D <= 0) return false;
+  const long long r = t % D;
+  return r == 0 || r == D - 1 || r == D - 2;
+}
+
+double *snap_slot(lbm_handle *h, int m, int slot) {
+  const size_t N = (size_t)h->mcfg[m].nx * h->mcfg[m].ny;
+  return h->hm[m].snap + (size_t)slot * 3 * N;
+}
+
+int record(lbm_handle *h) {
+  const int slot = (int)(h->t % 3);
+  for (int m = 0; m < (int)h->mcfg.size(); ++m)
+    CK(lbm::launch_snapshot(h->precision, h->d_members, m, h->mcfg[m].nx, h->mcfg[m].ny,
+                            h->cur, snap_slot(h, m, slot), h->stream));
+  h->ring_time[slot] = h->t;
+  h->launches += (long long)h->mcfg.size();
+  return LBM_OK;
+}
+
+int check_member(lbm_handle *h, int member) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (member < 0 || member >= (int)h->mcfg.size())
+    return fail(h, LBM_ERR_ARG, "member index out of range");
+  return LBM_OK;
+}
+
+// Autotune the batched launch: time each candidate shape on the live
+// buffers without flipping the buffer parity (the state is not changed).
+int autotune(lbm_handle *h) {
+  if (h->precision != 32) return LBM_OK;
+  size_t cells = 0;
+  for (auto &c : h->mcfg)
+    if (vector_eligible(c, 32)) cells += (size_t)c.nx * c.ny;
+  if (cells < (1u << 20)) return LBM_OK;  // small ensembles: default shape
+  int dev = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  struct Cand { lbm::LaunchCfg lc; float ms; };
+  std::vector<Cand> cands;
+  for (int wy : {4, 8})
+    for (int rows : {1, 2, 4})
+      for (int per : {0, 4, 8}) cands.push_back({{wy, rows, per * nsm}, 0.f});
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 0;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    h->lc = cands[i].lc;
+    int rc = build_tiles(h);
+    if (rc) return rc;
+    for (int w = 0; w < 2; ++w) { rc = launch_one_step(h, h->stream, h->cur); if (rc) return rc; }
+    CK(cudaEventRecord(e0, h->stream));
+    for (int r = 0; r < 5; ++r) { rc = launch_one_step(h, h->stream, h->cur); if (rc) return rc; }
+    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&cands[i].ms, e0, e1));
+    if (cands[i].ms < cands[best].ms) best = (int)i;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->lc = cands[best].lc;
+  return build_tiles(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_workspace_size(const lbm_config *cfg, size_t *bytes) {
+  std::string err;
+  int rc = check_config(cfg, err);
+  if (rc) return fail(nullptr, rc, err);
+  if (!bytes) return fail(nullptr, LBM_ERR_ARG, "bytes is NULL");
+  *bytes = make_layout(cfg).total;
+  return LBM_OK;
+}
+
+int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle **out) {
+  std::string err;
+  int rc = check_config(cfg, err);
+  if (rc) return fail(nullptr, rc, err);
+  if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  Layout lay = make_layout(cfg);
+  if (!workspace || bytes < lay.total)
+    return fail(nullptr, LBM_ERR_WORKSPACE, "workspace smaller than lbm_workspace_size()");
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign != 0)
+    return fail(nullptr, LBM_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+
+  lbm_handle *h = new lbm_handle();
+  h->cfg = *cfg;
+  h->mcfg.assign(cfg->members, cfg->members + cfg->n_members);
+  h->cfg.members = h->mcfg.data();
+  h->lay = lay;
+  h->ws = static_cast<char *>(workspace);
+  h->precision = cfg->precision;
+  h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  h->graph_k = cfg->graph_steps > 0 ? (cfg->graph_steps + 1) / 2 * 2 : 0;
+  h->d_members = reinterpret_cast<Member *>(ws_at(h, lay.members));
+  h->d_tiles = reinterpret_cast<Tile *>(ws_at(h, lay.tiles));
+  h->sc.f = reinterpret_cast<double *>(ws_at(h, lay.scratch));
+  h->sc.N = lay.Nmax;
+  h->sc.partials = reinterpret_cast<double *>(ws_at(h, lay.partials));
+  h->sc.npartials = lbm::diag_partials_needed(kMaxL);
+
+  auto cleanup = [&](int code) {
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cleanup(fail(nullptr, LBM_ERR_CUDA, "cannot create the capture stream"));
+
+  const size_t es = h->precision == 32 ? 4 : 8;
+  std::vector<char> tab;
+  for (int m = 0; m < cfg->n_members; ++m) {
+    const lbm_member_cfg &c = h->mcfg[m];
+    Member M{};
+    M.nx = c.nx;
+    M.ny = c.ny;
+    M.pitch = pitch_of(c.nx, h->precision);
+    M.force_kind = c.force_kind;
+    M.kf = c.kf;
+    M.tau = c.tau;
+    M.omega = 1.0 / c.tau;
+    M.rho0 = c.rho0;
+    M.F0 = c.F0;
+    M.alpha = c.alpha;
+    M.nu = (c.tau - 0.5) / 3.0;
+    M.plane = (size_t)c.ny * M.pitch;
+    M.pop[0] = ws_at(h, lay.pop0[m]);
+    M.pop[1] = ws_at(h, lay.pop1[m]);
+    M.fx_tab = ws_at(h, lay.fx[m]);
+    M.fy_tab = ws_at(h, lay.fy[m]);
+    M.fx_tab64 = reinterpret_cast<double *>(ws_at(h, lay.fx64[m]));
+    M.fy_tab64 = reinterpret_cast<double *>(ws_at(h, lay.fy64[m]));
+    M.snap = reinterpret_cast<double *>(ws_at(h, lay.snap[m]));
+    M.status = reinterpret_cast<int *>(ws_at(h, lay.status)) + m;
+    h->hm.push_back(M);
+    // Kolmogorov tables: F_ext,x(y) = F0 sin(2 pi kf y / ny), F_ext,y(x) likewise.
+    std::vector<double> fx(c.ny, 0.0), fy(c.nx, 0.0);
+    if (c.force_kind == 1) {
+      const double pi = 3.14159265358979323846;
+      for (int y = 0; y < c.ny; ++y) fx[y] = c.F0 * std::sin(2.0 * pi * c.kf * (double)y / c.ny);
+      for (int x = 0; x < c.nx; ++x) fy[x] = c.F0 * std::sin(2.0 * pi * c.kf * (double)x / c.nx);
+    }
+    cudaStream_t s = h->stream;
+    auto put = [&](void *dst, const std::vector<double> &v) -> cudaError_t {
+      if (es == 8) return cudaMemcpyAsync(dst, v.data(), 8 * v.size(), cudaMemcpyHostToDevice, s);
+      std::vector<float> f(v.begin(), v.end());
+      cudaError_t e = cudaMemcpyAsync(dst, f.data(), 4 * f.size(), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // f is a temporary
+      return e;
+    };
+    cudaError_t e = put(M.fx_tab, fx);
+    if (e == cudaSuccess) e = put(M.fy_tab, fy);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(M.fx_tab64, fx.data(), 8 * fx.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(M.fy_tab64, fy.data(), 8 * fy.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M.pop[0], 0, es * 9 * M.plane, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M.pop[1], 0, es * 9 * M.plane, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // fx/fy are temporaries
+    if (e != cudaSuccess)
+      return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
+  }
+  cudaError_t e = cudaMemcpyAsync(h->d_members, h->hm.data(), sizeof(Member) * h->hm.size(),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws_at(h, lay.status), 0, sizeof(int) * cfg->n_members, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess)
+    return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
+  rc = build_tiles(h);
+  if (rc == LBM_OK) rc = autotune(h);
+  if (rc != LBM_OK) {
+    std::string msg = h->err;
+    return cleanup(fail(nullptr, rc, msg));
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle *h) {
+  if (!h) return LBM_OK;
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+  return LBM_OK;
+}
+
+int lbm_init_fields(lbm_handle *h, int member, const double *rho, const double *ux,
+                    const double *uy, int on_device) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (!rho || !ux || !uy) return fail(h, LBM_ERR_ARG, "rho/ux/uy must not be NULL");
+  int m0 = member, m1 = member + 1;
+  if (member < 0) { m0 = 0; m1 = (int)h->mcfg.size(); }
+  else if (member >= (int)h->mcfg.size()) return fail(h, LBM_ERR_ARG, "member index out of range");
+  const int nx = h->mcfg[m0].nx, ny = h->mcfg[m0].ny;
+  for (int m = m0; m < m1; ++m)
+    if (h->mcfg[m].nx != nx || h->mcfg[m].ny != ny)
+      return fail(h, LBM_ERR_ARG, "shared init fields need equal grids");
+  const size_t N = (size_t)nx * ny;
+  const double *r = rho, *u = ux, *v = uy;
+  if (!on_device) {
+    double *st = h->sc.f;  // staging: three scratch fields
+    CK(cudaMemcpyAsync(st, rho, 8 * N, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(st + N, ux, 8 * N, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(st + 2 * N, uy, 8 * N, cudaMemcpyHostToDevice, h->stream));
+    r = st; u = st + N; v = st + 2 * N;
+  }
+  for (int m = m0; m < m1; ++m)
+    CK(lbm::launch_init_fields(h->precision, h->d_members, m, nx, ny, r, u, v, h->cur, h->stream));
+  h->launches += m1 - m0;
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));
+  h->t = 0;
+  h->ring_time[0] = h->ring_time[1] = h->ring_time[2] = -1;
+  return LBM_OK;
+}
+
+long long lbm_time(const lbm_handle *h) { return h ? h->t : -1; }
+
+long long lbm_launch_count(const lbm_handle *h) { return h ? h->launches : -1; }
+
+int lbm_step(lbm_handle *h, int nsteps) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps must be >= 0");
+  const long long end = h->t + nsteps;
+  while (h->t < end) {
+    if (is_snap_time(h, h->t) && h->ring_time[h->t % 3] != h->t) {
+      int rc = record(h);
+      if (rc) return rc;
+    }
+    long long next = end;
+    if (h->cfg.diag_every > 0) {
+      long long s = h->t + 1;
+      while (s < end && !is_snap_time(h, s)) {
+        const long long D = h->cfg.diag_every;
+        const long long r = s % D;
+        s += (r < D - 2) ? (D - 2 - r) : 1;  // jump to the next candidate
+      }
+      next = std::min(end, s);
+    }
+    int rc = run_steps(h, next - h->t);
+    if (rc) return rc;
+  }
+  if (is_snap_time(h, h->t) && h->ring_time[h->t % 3] != h->t) return record(h);
+  return LBM_OK;
+}
+
+int lbm_record_snapshot(lbm_handle *h) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  return record(h);
+}
+
+int lbm_moments(lbm_handle *h, int member, double *rho, double *ux, double *uy,
+                double *omega) {
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  const lbm_member_cfg &c = h->mcfg[member];
+  double *snap = h->sc.f;  // scratch fields 0..2
+  CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, snap, h->stream));
+  CK(lbm::diag_moments(h->hm[member], snap, rho, ux, uy, omega, h->sc, h->stream));
+  h->launches += omega ? 3 : 2;
+  return LBM_OK;
+}
+
+int lbm_global_balance(lbm_handle *h, int member, double *out) {
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+  const lbm_member_cfg &c = h->mcfg[member];
+  double *snap = h->sc.f;
+  double *out_dev = reinterpret_cast<double *>(ws_at(h, h->lay.out7));
+  CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, snap, h->stream));
+  CK(lbm::diag_global(h->hm[member], snap, h->sc, out_dev, h->stream));
+  h->launches += 4;
+  CK(cudaMemcpyAsync(out, out_dev, 8 * LBM_NGLOBAL, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_subvolume_balance(lbm_handle *h, int member, const int *L, int nL, const int *origins,
+                          int n_origins, double *stats_out, double *per_box_out) {
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  if (!L || nL < 1 || nL > kMaxL) return fail(h, LBM_ERR_ARG, "need 1..32 box sizes");
+  if (!stats_out) return fail(h, LBM_ERR_ARG, "stats_out is NULL");
+  const lbm_member_cfg &c = h->mcfg[member];
+  const size_t N = (size_t)c.nx * c.ny;
+  if (origins) {
+    if (n_origins < 1 || (size_t)n_origins > h->lay.Nmax)
+      return fail(h, LBM_ERR_ARG, "n_origins must be in 1..max cells");
+    for (int i = 0; i < n_origins; ++i)
+      if (origins[2 * i] < 0 || origins[2 * i] >= c.nx || origins[2 * i + 1] < 0 ||
+          origins[2 * i + 1] >= c.ny)
+        return fail(h, LBM_ERR_ARG, "origin outside the grid");
+  }
+  // history n, n-1, n-2
+  const long long t = h->t;
+  if (h->ring_time[t % 3] != t) {
+    rc = record(h);
+    if (rc) return rc;
+  }
+  if (t < 2 || h->ring_time[(t - 1) % 3] != t - 1 || h->ring_time[(t - 2) % 3] != t - 2)
+    return fail(h, LBM_ERR_HISTORY, "snapshots of time n-1 and n-2 are missing");
+  std::vector<int> valid, where;
+  for (int i = 0; i < nL; ++i)
+    if (L[i] >= 1 && L[i] <= c.nx && L[i] <= c.ny) { valid.push_back(L[i]); where.push_back(i); }
+  if (per_box_out && (int)valid.size() != nL)
+    return fail(h, LBM_ERR_ARG, "per_box_out needs every box size to fit the grid");
+  for (int i = 0; i < nL * 30; ++i) stats_out[i] = NAN;
+  if (valid.empty()) return LBM_OK;
+  CK(lbm::diag_terms(h->hm[member], snap_slot(h, member, (int)(t % 3)),
+                     snap_slot(h, member, (int)((t - 1) % 3)),
+                     snap_slot(h, member, (int)((t - 2) % 3)), h->sc, h->stream));
+  int *Ls_dev = reinterpret_cast<int *>(ws_at(h, h->lay.Ls));
+  int *orig_dev = origins ? reinterpret_cast<int *>(ws_at(h, h->lay.origins)) : nullptr;
+  double *stats_dev = reinterpret_cast<double *>(ws_at(h, h->lay.stats));
+  CK(cudaMemcpyAsync(Ls_dev, valid.data(), 4 * valid.size(), cudaMemcpyHostToDevice, h->stream));
+  if (origins)
+    CK(cudaMemcpyAsync(orig_dev, origins, 8 * (size_t)n_origins, cudaMemcpyHostToDevice, h->stream));
+  const int nb = origins ? n_origins : (int)N;
+  (void)nb;
+  CK(lbm::diag_sat_and_query(h->hm[member], Ls_dev, (int)valid.size(), orig_dev, n_origins,
+                             h->sc, stats_dev, per_box_out, h->stream));
+  h->launches += 10;  // 4 term passes, 2 mean, 2 scan, query, final
+  std::vector<double> st(valid.size() * 30);
+  CK(cudaMemcpyAsync(st.data(), stats_dev, 8 * st.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t k = 0; k < valid.size(); ++k)
+    std::memcpy(stats_out + (size_t)where[k] * 30, st.data() + k * 30, 8 * 30);
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_handle *h, int member, double *f, int on_device) {
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  if (!f) return fail(h, LBM_ERR_ARG, "f is NULL");
+  const lbm_member_cfg &c = h->mcfg[member];
+  const size_t N = (size_t)c.nx * c.ny;
+  double *dst = on_device ? f : h->sc.f;
+  CK(lbm::launch_get_populations(h->precision, h->d_members, member, c.nx, c.ny, h->cur, dst, h->stream));
+  h->launches += 1;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(f, dst, 8 * 9 * N, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_handle *h, int member, const double *f, int on_device) {
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  if (!f) return fail(h, LBM_ERR_ARG, "f is NULL");
+  const lbm_member_cfg &c = h->mcfg[member];
+  const size_t N = (size_t)c.nx * c.ny;
+  const double *src = f;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(h->sc.f, f, 8 * 9 * N, cudaMemcpyHostToDevice, h->stream));
+    src = h->sc.f;
+  }
+  CK(lbm::launch_set_populations(h->precision, h->d_members, member, c.nx, c.ny, h->cur, src, h->stream));
+  h->launches += 1;
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));
+  h->ring_time[0] = h->ring_time[1] = h->ring_time[2] = -1;
+  return LBM_OK;
+}
+
+int lbm_member_status(lbm_handle *h, int member, int *status) {
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  if (!status) return fail(h, LBM_ERR_ARG, "status is NULL");
+  const lbm_member_cfg &c = h->mcfg[member];
+  CK(cudaMemsetAsync(h->hm[member].status, 0, sizeof(int), h->stream));
+  CK(lbm::launch_status(h->precision, h->d_members, member, c.nx, c.ny, h->cur, h->stream));
+  h->launches += 1;
+  CK(cudaMemcpyAsync(status, h->hm[member].status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_adjoint_step(lbm_handle *h, int member, const double *f_n, const double *lambda_in,
+                     double *lambda_out, double obj_weight, int bx, int by, int L,
+                     double *dJ_dtau, double *dJ_dF0) {
+  (void)f_n; (void)lambda_in; (void)lambda_out; (void)obj_weight; (void)bx; (void)by;
+  (void)L; (void)dJ_dtau; (void)dJ_dF0;
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  return fail(h, LBM_ERR_ARG, "adjoint step is not available in this build");
+}
+
+int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx, int by, int L,
+                             double *acc) {
+  (void)weight; (void)bx; (void)by; (void)L; (void)acc;
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  return fail(h, LBM_ERR_ARG, "objective is not available in this build");
+}
+
+const char *lbm_last_error(const lbm_handle *h) {
+  return h ? h->err.c_str() : g_last_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Internal definitions of the GB300 D2Q9 library: member table, storage
+// layout and device helpers shared by the kernels of this library.
+//
+// Storage convention (device): for member m, buffer b in {0, 1},
+//   pop[b][(l * ny + y) * pitch + x]   (SoA planes, x fastest, pitch >= nx)
+// holds the post-collision population f*_l at its ORIGIN cell x (pull
+// layout), so that the pre-collision population of eq. (1) at time n is
+//   f_l(x, n) = pop[cur][l][x - c_l]   (periodic).
+// Precision 32 stores the deviation g_l = f_l - t_l rho0 (float); precision
+// 64 stores f_l itself (double).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+constexpr int kQ = 9;
+// D2Q9 velocities and weights (order: rest, 4 axis, 4 diagonal).
+__host__ __device__ constexpr int cx_of(int l) {
+  return l == 1 || l == 5 || l == 8 ? 1 : (l == 3 || l == 6 || l == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int cy_of(int l) {
+  return l == 2 || l == 5 || l == 6 ? 1 : (l == 4 || l == 7 || l == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr double w_of(int l) {
+  return l == 0 ? 4.0 / 9.0 : (l <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+__host__ __device__ constexpr int opposite(int l) {
+  return l == 0 ? 0 : (l <= 4 ? ((l + 1) % 4) + 1 : ((l - 5 + 2) % 4) + 5);
+}
+
+// Per-member parameters, uploaded once into the workspace.
+struct Member {
+  int nx, ny, pitch;     // grid and row pitch (elements)
+  int force_kind, kf;
+  int pad0;
+  double tau, omega;     // omega = 1 / tau
+  double rho0, F0, alpha;
+  double nu;             // (tau - 1/2) / 3
+  size_t plane;          // ny * pitch
+  void *pop[2];          // population buffers
+  void *fx_tab;          // F_ext,x as function of y: [ny] (float or double)
+  void *fy_tab;          // F_ext,y as function of x: [nx]
+  double *fx_tab64;      // the same tables in double (diagnostics, adjoint)
+  double *fy_tab64;
+  double *snap;          // [3 slots][3 fields: rho, jx, jy][ny * nx]
+  int *status;           // divergence flag
+};
+
+// Tile of the batched stream-collide: member, first x, first y.
+struct Tile {
+  int member, x0, y0, pad;
+};
+
+__host__ __device__ inline int wrapi(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+}  // namespace lbm
+
+// Kernel launch wrappers (defined in the .cu files, called by lbm_api.cu).
+namespace lbm {
+struct LaunchCfg {
+  int block_warps_y;  // warps per CTA (rows per CTA pass)
+  int rows_per_warp;  // rows each warp processes per tile
+  int grid_ctas;      // 0: one CTA per tile; else persistent grid size
+};
+
+cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, int ntiles,
+                                int cur, const LaunchCfg &lc, cudaStream_t s);
+cudaError_t launch_step_scalar(int precision, const Member *d_members, int member,
+                               int nx, int ny, int cur, cudaStream_t s);
+cudaError_t launch_init_fields(int precision, const Member *d_members, int member, int nx,
+                               int ny, const double *rho, const double *ux,
+                               const double *uy, int cur, cudaStream_t s);
+cudaError_t launch_get_populations(int precision, const Member *d_members, int member,
+                                   int nx, int ny, int cur, double *f, cudaStream_t s);
+cudaError_t launch_set_populations(int precision, const Member *d_members, int member,
+                                   int nx, int ny, int cur, const double *f, cudaStream_t s);
+cudaError_t launch_snapshot(int precision, const Member *d_members, int member, int nx,
+                            int ny, int cur, double *dst, cudaStream_t s);
+cudaError_t launch_status(int precision, const Member *d_members, int member, int nx,
+                          int ny, int cur, cudaStream_t s);
+
+// Diagnostics (lbm_diag.cu).  scratch: device FP64 scratch of the handle.
+struct DiagScratch {
+  double *f;        // [nfields][N] field scratch
+  size_t N;         // cells of the largest member
+  double *partials; // reduction partials
+  size_t npartials; // capacity in doubles
+};
+constexpr int kDiagFields = 40;
+constexpr int kMaxPartialBlocks = 1024;
+
+cudaError_t diag_moments(const Member &hm, const double *snap3, double *rho, double *ux,
+                         double *uy, double *omega, const DiagScratch &sc, cudaStream_t s);
+cudaError_t diag_global(const Member &hm, const double *snap3, const DiagScratch &sc,
+                        double *out7_dev, cudaStream_t s);
+cudaError_t diag_terms(const Member &hm, const double *sn, const double *sn1,
+                       const double *sn2, const DiagScratch &sc, cudaStream_t s);
+cudaError_t diag_sat_and_query(const Member &hm, const int *Ls_dev, int nL,
+                               const int *origins_dev, int n_origins, const DiagScratch &sc,
+                               double *stats_dev, double *per_box_dev, cudaStream_t s);
+size_t diag_partials_needed(int nL);
+
+// Adjoint (lbm_adjoint.cu).
+cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_in,
+                         double *lam_out, double w, int bx, int by, int L,
+                         double *dJ_dtau, double *dJ_dF0, const DiagScratch &sc,
+                         cudaStream_t s);
+cudaError_t objective_accumulate(const Member *d_members, const Member &hm, int member,
+                                 int cur, double w, int bx, int by, int L, double *acc,
+                                 const DiagScratch &sc, cudaStream_t s);
+}  // namespace lbm

@@ -1,0 +1,181 @@
+"""GPU parity of the diagnostic (moments, whole-grid budget, sub-volume
+balance terms, balancing errors and their statistics: eqs. (8)-(13), (17),
+(18), Table 1) against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import lbm_inputs as li
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1809_06735_gb300 as P
+    P.load_library()
+    return P
+
+
+def _forced_state(orc, nx, ny, tau, force, steps, seed):
+    r = 1.0 + li.smooth_fields(nx, ny, seed, amp=0.01)
+    u = li.smooth_fields(nx, ny, seed + 1, amp=0.03)
+    v = li.smooth_fields(nx, ny, seed + 2, amp=0.03)
+    return (r, u, v), orc.run(orc.init(r, u, v), steps, tau, force)
+
+
+def test_moments_and_vorticity(P, orc):
+    nx, ny, tau = 48, 40, 0.55
+    force = orc.Force(1, 2e-4, 3, 5e-3)
+    _, f = _forced_state(orc, nx, ny, tau, force, 0, 20)
+    lat = P.Lattice([P.Member(nx, ny, tau, 1.0, 1, 3, 2e-4, 5e-3)], precision=64)
+    lat.set_populations(0, f)
+    got = {k: v.cpu().numpy() for k, v in lat.moments(0).items()}
+    m = orc.moments(f, force)
+    w = orc.ddx(m["uy"]) - orc.ddy(m["ux"])
+    for k, ref in (("rho", m["rho"]), ("ux", m["ux"]), ("uy", m["uy"]), ("omega", w)):
+        assert np.max(np.abs(got[k] - ref)) <= 1e-13 * np.max(np.abs(ref)), k
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_global_balance(P, orc, prec):
+    nx, ny, tau = 64, 48, 0.6
+    force = orc.Force(1, 1e-4, 2, 1e-4)
+    _, f = _forced_state(orc, nx, ny, tau, force, 0, 30)
+    lat = P.Lattice([P.Member(nx, ny, tau, 1.0, 1, 2, 1e-4, 1e-4)], precision=prec)
+    lat.set_populations(0, f)
+    got = lat.global_balance(0)
+    ref = orc.global_quantities(lat.get_populations_host(0), tau, force)
+    np.testing.assert_allclose(got[[0, 3, 4, 5, 6]], ref[[0, 3, 4, 5, 6]], rtol=1e-12)
+    assert abs(got[1] - ref[1]) < 1e-12 * nx * ny and abs(got[2] - ref[2]) < 1e-12 * nx * ny
+
+
+def _check_boxes(got_stats, got_pb, T, Ls, origins=None):
+    import oracle as orc
+    want, want_pb = orc.balance_stats(T, Ls, origins=origins, per_box=True)
+    term_scale = np.max(np.abs(T.reshape(13, -1)), axis=1) + 1e-300
+    for iL in range(len(Ls)):
+        # terms: relative to the field's magnitude
+        d = np.abs(got_pb[iL][:, 2:] - want_pb[iL][:, 2:]) / term_scale[None, :]
+        assert np.max(d) < 1e-12, (Ls[iL], np.max(d))
+        # balancing errors: they divide a cancelling sum by max |RHS|
+        dd = np.abs(got_pb[iL][:, :2] - want_pb[iL][:, :2])
+        assert np.max(dd) < 1e-9 * max(1.0, np.max(want_pb[iL][:, :2])), Ls[iL]
+        np.testing.assert_allclose(got_stats[iL, 2:, 0], want[iL, 2:, 0],
+                                   rtol=0, atol=1e-12 * np.max(term_scale))
+        np.testing.assert_allclose(got_stats[iL, :, 1], want[iL, :, 1], rtol=1e-7,
+                                   atol=1e-13 * np.max(term_scale))
+        np.testing.assert_allclose(got_stats[iL, :2, 0], want[iL, :2, 0], rtol=1e-8)
+
+
+def test_balance_taylor_green_64_fp64(P, orc):
+    """Plain FP64 Taylor-Green at 64^2, every periodic origin, L in {4,8,16,32}
+    at step 100 (diagnostic history 98, 99, 100)."""
+    wl = li.taylor_green_workload()
+    n, tau = wl["n"], wl["tau"]
+    rho, ux, uy = li.taylor_green(n, u0=wl["u0"])
+    lat = P.Lattice([P.Member(n, n, tau)], precision=64, diag_every=wl["diag_every"])
+    lat.init_fields(0, rho, ux, uy)
+    lat.step(100)
+    stats, pb = lat.subvolume_balance(0, wl["Ls"], per_box=True)
+    f0 = orc.init(rho, ux, uy)
+    f98 = orc.run(f0, 98, tau)
+    f99 = orc.run(f98, 1, tau)
+    f100 = orc.run(f99, 1, tau)
+    T = orc.terms_from_populations(f100, f99, f98, tau)
+    _check_boxes(stats, pb.cpu().numpy(), T, wl["Ls"])
+
+
+def test_balance_forced_ragged_origin_list(P, orc):
+    """Forced flow on a non-square grid, Table 1 random origins, sizes beyond
+    the grid skipped (NaN), FP64."""
+    nx, ny, tau = 56, 40, 0.53
+    force = orc.Force(1, 3e-4, 2, 1e-3)
+    lat = P.Lattice([P.Member(nx, ny, tau, 1.0, 1, 2, 3e-4, 1e-3)], precision=64)
+    (r, u, v), _ = _forced_state(orc, nx, ny, tau, force, 0, 40)
+    lat.init_fields(0, r, u, v)
+    lat.step(30)
+    lat.record_snapshot()
+    lat.step(1)
+    lat.record_snapshot()
+    lat.step(1)
+    origins = np.stack([np.arange(0, 300) % nx, (np.arange(0, 300) * 7) % ny], 1).astype(np.int32)
+    Ls = [1, 3, 7, 16, 40, 41, 64]
+    stats = lat.subvolume_balance(0, Ls, origins=origins)
+    assert np.all(np.isnan(stats[5:]))
+    stats_v, pb = lat.subvolume_balance(0, Ls[:5], origins=origins, per_box=True)
+    np.testing.assert_array_equal(stats[:5], stats_v)
+    f0 = orc.init(r, u, v)
+    f30 = orc.run(f0, 30, tau, force)
+    f31 = orc.run(f30, 1, tau, force)
+    f32 = orc.run(f31, 1, tau, force)
+    T = orc.terms_from_populations(f32, f31, f30, tau, force)
+    _check_boxes(stats_v, pb.cpu().numpy(), T, Ls[:5], origins=origins)
+
+
+def test_balance_history_required(P):
+    n = 16
+    lat = P.Lattice([P.Member(n, n, 0.6)], precision=64)
+    lat.init_fields(0, np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)))
+    lat.step(5)
+    with pytest.raises(P.LBMError) as e:
+        lat.subvolume_balance(0, [4])
+    assert e.value.code == -4
+
+
+def test_balance_fp32_against_fp64_oracle(P, orc):
+    """FP32 deviation populations feeding the FP64 diagnostic: the box terms
+    stay within 1e-4 relative (of each term's magnitude) of the FP64 oracle
+    over a 100-step horizon."""
+    n, tau = 64, 0.55
+    force = orc.Force(1, li.kolmogorov_F0(n, tau, 4, 1e-4, 0.03), 4, 1e-4)
+    rho, ux, uy = li.random_phase(n, seed=5, u_rms=0.02)
+    lat = P.Lattice([P.Member(n, n, tau, 1.0, 1, 4, force.F0, 1e-4)], precision=32,
+                    diag_every=100)
+    lat.init_fields(0, rho, ux, uy)
+    lat.step(100)
+    Ls = [2, 4, 8, 16, 32, 64]
+    stats, pb = lat.subvolume_balance(0, Ls, per_box=True)
+    f98 = orc.run(orc.init(rho, ux, uy), 98, tau, force)
+    f99 = orc.run(f98, 1, tau, force)
+    f100 = orc.run(f99, 1, tau, force)
+    T = orc.terms_from_populations(f100, f99, f98, tau, force)
+    want, want_pb = orc.balance_stats(T, Ls, per_box=True)
+    pb = pb.cpu().numpy()
+    scale = np.max(np.abs(T.reshape(13, -1)), axis=1) + 1e-300
+    for iL in range(len(Ls)):
+        d = np.abs(pb[iL][:, 2:] - want_pb[iL][:, 2:]) / scale[None, :]
+        assert np.max(d) < 1e-4, (Ls[iL], np.max(d))
+
+
+def test_balance_full_size_sampled(P, orc):
+    """One 512^2 member at the ensemble's box sizes L = 2..256, all origins on
+    the GPU; sampled boxes against the oracle's brute-force averages of the
+    oracle terms of the same exported states; the all-origin mean of every
+    term equals its global mean."""
+    wl = li.decaying_ensemble_workload(members=2)
+    n, tau = wl["n"], wl["tau"]
+    lat = P.Lattice([P.Member(n, n, tau)] * 2, precision=32, diag_every=wl["diag_every"],
+                    graph_steps=20)
+    for m in range(2):
+        lat.init_fields(m, *li.random_phase(n, seed=wl["seed0"] + m, u_rms=wl["u_rms"]))
+    lat.step(198)
+    f198 = lat.get_populations_host(1)
+    lat.step(1)
+    f199 = lat.get_populations_host(1)
+    lat.step(1)
+    f200 = lat.get_populations_host(1)
+    stats, pb = lat.subvolume_balance(1, wl["Ls"], per_box=True)
+    T = orc.terms_from_populations(f200, f199, f198, tau)
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, n * n, size=40)
+    pb = pb.cpu().numpy()
+    scale = np.max(np.abs(T.reshape(13, -1)), axis=1) + 1e-300
+    for iL, L in enumerate(wl["Ls"]):
+        for b in idx:
+            want = orc.box_values(T, b % n, b // n, L)
+            assert np.max(np.abs(pb[iL, b, 2:] - want[2:]) / scale) < 1e-12
+            assert abs(pb[iL, b, 0] - want[0]) < 1e-9 and abs(pb[iL, b, 1] - want[1]) < 1e-9
+        np.testing.assert_allclose(stats[iL, 2:, 0], T.reshape(13, -1).mean(axis=1), rtol=0,
+                                   atol=1e-12 * np.max(scale))
