@@ -626,19 +626,34 @@ int lbm_member_status(lbm_handle *h, int member, int *status) {
 int lbm_adjoint_step(lbm_handle *h, int member, const double *f_n, const double *lambda_in,
                      double *lambda_out, double obj_weight, int bx, int by, int L,
                      double *dJ_dtau, double *dJ_dF0) {
-  (void)f_n; (void)lambda_in; (void)lambda_out; (void)obj_weight; (void)bx; (void)by;
-  (void)L; (void)dJ_dtau; (void)dJ_dF0;
   int rc = check_member(h, member);
   if (rc) return rc;
-  return fail(h, LBM_ERR_ARG, "adjoint step is not available in this build");
+  const lbm_member_cfg &c = h->mcfg[member];
+  if (!f_n || !lambda_out) return fail(h, LBM_ERR_ARG, "f_n and lambda_out must not be NULL");
+  if (lambda_in == lambda_out) return fail(h, LBM_ERR_ARG, "lambda_out may not alias lambda_in");
+  if (!std::isfinite(obj_weight)) return fail(h, LBM_ERR_ARG, "obj_weight not finite");
+  if (obj_weight != 0.0 &&
+      (L < 1 || L > c.nx || L > c.ny || bx < 0 || bx >= c.nx || by < 0 || by >= c.ny))
+    return fail(h, LBM_ERR_ARG, "objective box outside the grid");
+  CK(lbm::adjoint_step(h->hm[member], f_n, lambda_in, lambda_out, obj_weight, bx, by, L,
+                       dJ_dtau, dJ_dF0, h->sc, h->stream));
+  h->launches += lbm::adjoint_kernel_count(obj_weight);
+  return LBM_OK;
 }
 
 int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx, int by, int L,
                              double *acc) {
-  (void)weight; (void)bx; (void)by; (void)L; (void)acc;
   int rc = check_member(h, member);
   if (rc) return rc;
-  return fail(h, LBM_ERR_ARG, "objective is not available in this build");
+  const lbm_member_cfg &c = h->mcfg[member];
+  if (!acc) return fail(h, LBM_ERR_ARG, "acc is NULL");
+  if (L < 1 || L > c.nx || L > c.ny || bx < 0 || bx >= c.nx || by < 0 || by >= c.ny)
+    return fail(h, LBM_ERR_ARG, "objective box outside the grid");
+  CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, h->sc.f,
+                          h->stream));
+  CK(lbm::objective_from_snapshot(h->hm[member], weight, bx, by, L, acc, h->sc, h->stream));
+  h->launches += 4;
+  return LBM_OK;
 }
 
 const char *lbm_last_error(const lbm_handle *h) {

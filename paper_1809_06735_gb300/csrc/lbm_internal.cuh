@@ -111,7 +111,7 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
                          double *lam_out, double w, int bx, int by, int L,
                          double *dJ_dtau, double *dJ_dF0, const DiagScratch &sc,
                          cudaStream_t s);
-cudaError_t objective_accumulate(const Member *d_members, const Member &hm, int member,
-                                 int cur, double w, int bx, int by, int L, double *acc,
-                                 const DiagScratch &sc, cudaStream_t s);
+cudaError_t objective_from_snapshot(const Member &hm, double w, int bx, int by, int L,
+                                    double *acc, const DiagScratch &sc, cudaStream_t s);
+int adjoint_kernel_count(double w);
 }  // namespace lbm

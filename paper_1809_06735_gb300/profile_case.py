@@ -1,0 +1,73 @@
+"""Small, self-contained runs of each kernel family for Nsight Compute.
+
+    python -m paper_1809_06735_gb300.profile_case step     # batched FP32 stream-collide
+    python -m paper_1809_06735_gb300.profile_case diag     # one diagnostic event, 512^2
+    python -m paper_1809_06735_gb300.profile_case fp64     # plain FP64 step, 512^2
+    python -m paper_1809_06735_gb300.profile_case adjoint  # FP64 adjoint steps, 256^2
+
+Sizes keep the working set above the L2 (so DRAM counters mean something)
+and below a few GB.  The step case creates its handle with the launch-shape
+autotuner on: 18 shapes x 7 launches = 126 launches of k_step_f32_vec come
+before the first step of the run.
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+import torch
+
+import lbm_inputs as li
+
+from . import Lattice, Member
+
+AUTOTUNE_LAUNCHES = 126
+
+
+def case_step(members=16, n=512, steps=25):
+    lat = Lattice([Member(n, n, 0.52)] * members, precision=32, graph_steps=0)
+    for m in range(members):
+        lat.init_fields(m, *li.random_phase(n, seed=1000 + m, u_rms=0.02))
+    lat.step(steps)
+    torch.cuda.synchronize()
+    print("step case done:", lat.launch_count, "launches")
+
+
+def case_diag(n=512, events=2):
+    lat = Lattice([Member(n, n, 0.52)], precision=32, diag_every=200)
+    lat.init_fields(0, *li.random_phase(n, seed=1000, u_rms=0.02))
+    Ls = li.pow2_sizes(1, 8, n)
+    for _ in range(events):
+        lat.step(200)
+        stats = lat.subvolume_balance(0, Ls)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(stats[:, 2:, 0]))
+    print("diag case done:", lat.launch_count, "launches")
+
+
+def case_fp64(n=512, steps=20):
+    lat = Lattice([Member(n, n, 0.52)], precision=64)
+    lat.init_fields(0, *li.random_phase(n, seed=1000, u_rms=0.02))
+    lat.step(steps)
+    torch.cuda.synchronize()
+    print("fp64 case done")
+
+
+def case_adjoint(n=256, steps=6):
+    F0 = li.kolmogorov_F0(n, 0.55, 4, 1e-4, 0.03)
+    lat = Lattice([Member(n, n, 0.55, 1.0, 1, 4, F0, 1e-4)], precision=64)
+    lat.init_fields(0, *li.random_phase(n, seed=0, u_rms=0.02))
+    f = lat.get_populations(0)
+    lam = torch.zeros_like(f)
+    out = torch.empty_like(f)
+    acc = torch.zeros(2, dtype=torch.float64, device=f.device)
+    for _ in range(steps):
+        lat.adjoint_step(0, f, lam, out, 1e-3, (0, 0), 16, acc[0:1], acc[1:2])
+        lam, out = out, lam
+    torch.cuda.synchronize()
+    print("adjoint case done")
+
+
+if __name__ == "__main__":
+    which = sys.argv[1] if len(sys.argv) > 1 else "step"
+    {"step": case_step, "diag": case_diag, "fp64": case_fp64, "adjoint": case_adjoint}[which]()

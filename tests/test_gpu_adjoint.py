@@ -1,0 +1,137 @@
+"""GPU checks of the hand-written adjoint (no counterpart in the paper):
+the transposed step against finite differences of the FP64 GPU forward
+(dot-product test), and the checkpointed gradients of the box-averaged
+dissipation objective against central finite differences of the FP64
+oracle (bar: 1e-6 relative)."""
+import numpy as np
+import pytest
+
+import lbm_inputs as li
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1809_06735_gb300 as P
+    P.load_library()
+    return P
+
+
+def test_adjoint_step_dot_product(P):
+    """<lam, dS(f)[d]> = <S^T lam, d> for one step, with dS[d] by central
+    differences of the FP64 GPU step (no objective term)."""
+    import torch
+    nx, ny, tau, F0, kf, alpha = 24, 20, 0.57, 2e-4, 2, 3e-3
+    lat = P.Lattice([P.Member(nx, ny, tau, 1.0, 1, kf, F0, alpha)], precision=64)
+    f = torch.from_numpy(li.random_populations(nx, ny, seed=1)).cuda()
+    rng = np.random.default_rng(2)
+    d = torch.from_numpy(rng.standard_normal((9, ny, nx))).cuda()
+    lam = torch.from_numpy(rng.standard_normal((9, ny, nx))).cuda()
+    eps = 1e-6
+
+    def S(x):
+        lat.set_populations(0, x)
+        lat.step(1)
+        return lat.get_populations(0).clone()
+
+    jv = (S(f + eps * d) - S(f - eps * d)) / (2 * eps)
+    out = torch.empty_like(lam)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dF = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lat.adjoint_step(0, f, lam, out, 0.0, (0, 0), 1, dt, dF)
+    lhs = float((lam * jv).sum())
+    rhs = float((out * d).sum())
+    assert abs(lhs - rhs) < 1e-7 * abs(rhs)
+
+    # parameter directions: tau and F0
+    def S_param(t, a):
+        l2 = P.Lattice([P.Member(nx, ny, t, 1.0, 1, kf, a, alpha)], precision=64)
+        l2.set_populations(0, f)
+        l2.step(1)
+        return l2.get_populations(0).clone()
+
+    h = 1e-6
+    dS_dtau = (S_param(tau + h, F0) - S_param(tau - h, F0)) / (2 * h)
+    dS_dF0 = (S_param(tau, F0 * (1 + 1e-3)) - S_param(tau, F0 * (1 - 1e-3))) / (2e-3 * F0)
+    assert abs(float((lam * dS_dtau).sum()) - float(dt)) < 1e-6 * abs(float(dt))
+    assert abs(float((lam * dS_dF0).sum()) - float(dF)) < 1e-6 * abs(float(dF))
+
+
+def _small_spec(precision=64):
+    from paper_1809_06735_gb300.adjoint import ObjectiveSpec
+    return ObjectiveSpec(nx=32, ny=32, kf=2, alpha=1e-3, n0=20, n1=44, box=(5, 3), L=8,
+                         precision=precision, checkpoint_every=10)
+
+
+def test_objective_forward_matches_oracle(P, orc):
+    import torch
+    from paper_1809_06735_gb300.adjoint import forward_objective
+    spec = _small_spec()
+    tau, F0 = 0.6, li.kolmogorov_F0(32, 0.6, 2, 1e-3, 0.02)
+    r, u, v = li.random_phase(32, seed=4, u_rms=0.02, k_peak=3.0)
+    f0 = orc.init(r, u, v)
+    J, _, _ = forward_objective(spec, tau, F0, torch.from_numpy(f0).cuda())
+    Jo = orc.objective(f0, tau, orc.Force(1, F0, 2, 1e-3), spec.n0, spec.n1, *spec.box, spec.L)
+    assert abs(float(J) - Jo) < 1e-12 * abs(Jo)
+
+
+def test_gradients_match_oracle_finite_differences(P, orc):
+    """dJ/dtau (h = 1e-6), dJ/dF0 (1e-3 relative step, Richardson) and a
+    directional derivative in f0 against central differences of the FP64
+    oracle objective."""
+    import torch
+    from paper_1809_06735_gb300.adjoint import box_dissipation
+    spec = _small_spec()
+    tau0, kf, alpha = 0.6, 2, 1e-3
+    F00 = li.kolmogorov_F0(32, tau0, kf, alpha, 0.02)
+    r, u, v = li.random_phase(32, seed=4, u_rms=0.02, k_peak=3.0)
+    f0 = orc.init(r, u, v)
+    tau = torch.tensor(tau0, dtype=torch.float64, requires_grad=True)
+    F0 = torch.tensor(F00, dtype=torch.float64, requires_grad=True)
+    f0t = torch.from_numpy(f0).cuda().requires_grad_(True)
+    J = box_dissipation(tau, F0, f0t, spec)
+    J.backward()
+
+    def Jo(t, a, f=f0):
+        return orc.objective(f, t, orc.Force(1, a, kf, alpha), spec.n0, spec.n1, *spec.box,
+                             spec.L)
+
+    h = 1e-6
+    fd_tau = (Jo(tau0 + h, F00) - Jo(tau0 - h, F00)) / (2 * h)
+    assert abs(float(tau.grad) - fd_tau) < 1e-6 * abs(fd_tau)
+
+    def dF(hr):
+        a = F00 * hr
+        return (Jo(tau0, F00 + a) - Jo(tau0, F00 - a)) / (2 * a)
+    fd_F0 = (4 * dF(5e-4) - dF(1e-3)) / 3
+    assert abs(float(F0.grad) - fd_F0) < 1e-6 * abs(fd_F0)
+
+    rng = np.random.default_rng(9)
+    d = rng.standard_normal(f0.shape) * 1e-3
+    eps = 1e-4
+    fd_f = (Jo(tau0, F00, f0 + eps * d) - Jo(tau0, F00, f0 - eps * d)) / (2 * eps)
+    ad_f = float((f0t.grad.cpu().numpy() * d).sum())
+    assert abs(ad_f - fd_f) < 1e-6 * abs(fd_f)
+
+
+def test_fp32_forward_gradients_close_to_fp64(P):
+    """The same gradients with the FP32 forward trajectory (adjoint in FP64)
+    stay close to the FP64 ones over this short horizon."""
+    import torch
+    from paper_1809_06735_gb300.adjoint import box_dissipation
+    r, u, v = li.random_phase(32, seed=4, u_rms=0.02, k_peak=3.0)
+    import oracle
+    f0 = torch.from_numpy(oracle.init(r, u, v)).cuda()
+    F00 = li.kolmogorov_F0(32, 0.6, 2, 1e-3, 0.02)
+    grads = []
+    for prec in (64, 32):
+        tau = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
+        F0 = torch.tensor(F00, dtype=torch.float64, requires_grad=True)
+        J = box_dissipation(tau, F0, f0, _small_spec(prec))
+        J.backward()
+        grads.append((float(tau.grad), float(F0.grad)))
+    for a, b in zip(*grads):
+        assert abs(a - b) < 1e-3 * abs(a)
