@@ -51,6 +51,17 @@ def test_global_balance(P, orc, prec):
     assert abs(got[1] - ref[1]) < 1e-12 * nx * ny and abs(got[2] - ref[2]) < 1e-12 * nx * ny
 
 
+# FP64 tolerance of the box terms, relative to each term field's largest
+# magnitude.  Both sides round differently (stencil pairing, SAT versus brute
+# force sums); the worst-conditioned term is RHS^{E,2} = -u . grad p with
+# p = rho/3: rho varies by ~1e-4 around 1, so the eq. (18) difference of p
+# cancels ~|p|/|grad p| ~ 1e5 and one-ulp input differences reach ~1e-11
+# of the term.  1e-10 keeps a 10x margin and still fails any wrong sign,
+# index, missing factor or FP32 leak (>= 1e-7).
+TERM_TOL = 1e-10
+DELTA_TOL = 1e-8
+
+
 def _check_boxes(got_stats, got_pb, T, Ls, origins=None):
     import oracle as orc
     want, want_pb = orc.balance_stats(T, Ls, origins=origins, per_box=True)
@@ -58,15 +69,16 @@ def _check_boxes(got_stats, got_pb, T, Ls, origins=None):
     for iL in range(len(Ls)):
         # terms: relative to the field's magnitude
         d = np.abs(got_pb[iL][:, 2:] - want_pb[iL][:, 2:]) / term_scale[None, :]
-        assert np.max(d) < 1e-12, (Ls[iL], np.max(d))
+        assert np.max(d) < TERM_TOL, (Ls[iL], np.argmax(np.max(d, axis=0)), np.max(d))
         # balancing errors: they divide a cancelling sum by max |RHS|
         dd = np.abs(got_pb[iL][:, :2] - want_pb[iL][:, :2])
-        assert np.max(dd) < 1e-9 * max(1.0, np.max(want_pb[iL][:, :2])), Ls[iL]
+        assert np.max(dd) < DELTA_TOL * max(1.0, np.max(want_pb[iL][:, :2])), Ls[iL]
         np.testing.assert_allclose(got_stats[iL, 2:, 0], want[iL, 2:, 0],
-                                   rtol=0, atol=1e-12 * np.max(term_scale))
-        np.testing.assert_allclose(got_stats[iL, :, 1], want[iL, :, 1], rtol=1e-7,
-                                   atol=1e-13 * np.max(term_scale))
-        np.testing.assert_allclose(got_stats[iL, :2, 0], want[iL, :2, 0], rtol=1e-8)
+                                   rtol=0, atol=TERM_TOL * np.max(term_scale))
+        np.testing.assert_allclose(got_stats[iL, 2:, 1], want[iL, 2:, 1], rtol=1e-7,
+                                   atol=TERM_TOL * np.max(term_scale))
+        np.testing.assert_allclose(got_stats[iL, :2, :], want[iL, :2, :], rtol=1e-6,
+                                   atol=DELTA_TOL)
 
 
 def test_balance_taylor_green_64_fp64(P, orc):
@@ -180,7 +192,26 @@ def test_balance_full_size_sampled(P, orc):
     for iL, L in enumerate(wl["Ls"]):
         for b in idx:
             want = orc.box_values(T, b % n, b // n, L)
-            assert np.max(np.abs(pb[iL, b, 2:] - want[2:]) / scale) < 1e-12
-            assert abs(pb[iL, b, 0] - want[0]) < 1e-9 and abs(pb[iL, b, 1] - want[1]) < 1e-9
+            assert np.max(np.abs(pb[iL, b, 2:] - want[2:]) / scale) < TERM_TOL
+            assert abs(pb[iL, b, 0] - want[0]) < DELTA_TOL and abs(pb[iL, b, 1] - want[1]) < DELTA_TOL
         np.testing.assert_allclose(stats[iL, 2:, 0], T.reshape(13, -1).mean(axis=1), rtol=0,
-                                   atol=1e-12 * np.max(scale))
+                                   atol=TERM_TOL * np.max(scale))
+
+
+def test_balance_batch_equals_per_member(P):
+    """The batched call over uneven members gives, bit for bit, the per-member
+    statistics; sizes beyond a member's grid are NaN for that member only."""
+    spec = [(32, 32, 0.6), (48, 40, 0.55), (64, 64, 0.52)]
+    lat = P.Lattice([P.Member(nx, ny, t) for nx, ny, t in spec], precision=32, diag_every=20)
+    for i, (nx, ny, _) in enumerate(spec):
+        u = li.smooth_fields(nx, ny, 50 + i, amp=0.03)
+        v = li.smooth_fields(nx, ny, 60 + i, amp=0.03)
+        lat.init_fields(i, np.ones((ny, nx)), u, v)
+    lat.step(20)
+    Ls = [2, 8, 32, 40, 64]
+    batch = lat.subvolume_balance_batch([0, 1, 2], Ls)
+    for i in range(3):
+        single = lat.subvolume_balance(i, Ls)
+        np.testing.assert_array_equal(batch[i], single)
+    assert np.all(np.isnan(batch[0, 3:])) and np.all(np.isnan(batch[1, 3:]))
+    assert np.all(np.isfinite(batch[2, :, 2:, 0]))
