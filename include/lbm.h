@@ -173,6 +173,16 @@ int lbm_subvolume_balance(lbm_handle *h, int member, const int *L, int nL,
                           const int *origins, int n_origins, double *stats_out,
                           double *per_box_out);
 
+/* The same diagnostic for the n_members members listed in the host array
+ * members[], queued back to back with a single synchronisation at the end:
+ * stats_out (host) is double[n_members][nL][15][2], each member's sizes
+ * checked against its own grid.  origins, when given, apply to every
+ * member.  No per-box output. */
+int lbm_subvolume_balance_batch(lbm_handle *h, const int *members,
+                                int n_members, const int *L, int nL,
+                                const int *origins, int n_origins,
+                                double *stats_out);
+
 /* Public pre-collision populations f_l(x, n) of member `member` as
  * double[9][ny][nx] (full f, also for FP32 storage).  Host pointer if
  * on_device == 0 (the call synchronises), device pointer otherwise.

@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_moments": ([P, I, P, P, P, P], I),
         "lbm_global_balance": ([P, I, P], I),
         "lbm_subvolume_balance": ([P, I, P, I, P, I, P, P], I),
+        "lbm_subvolume_balance_batch": ([P, P, I, P, I, P, I, P], I),
         "lbm_get_populations": ([P, I, P, I], I),
         "lbm_set_populations": ([P, I, P, I], I),
         "lbm_member_status": ([P, I, P], I),
@@ -274,6 +275,19 @@ class Lattice:
             self.h, member, _ptr(Ls), nL, _ptr(origins) if origins is not None else None,
             nb if origins is not None else 0, _ptr(stats), _ptr(pb)))
         return (stats, pb) if per_box else stats
+
+    def subvolume_balance_batch(self, members, Ls, origins=None):
+        """Statistics [n_members, nL, 15, 2] for several members, one sync."""
+        mem = np.ascontiguousarray(members, dtype=np.int32)
+        Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+        stats = np.empty((len(mem), len(Ls), NQUANT, 2))
+        if origins is not None:
+            origins = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1, 2)
+        self._check(self.lib.lbm_subvolume_balance_batch(
+            self.h, _ptr(mem), len(mem), _ptr(Ls), len(Ls),
+            _ptr(origins) if origins is not None else None,
+            origins.shape[0] if origins is not None else 0, _ptr(stats)))
+        return stats
 
     # -- adjoint ------------------------------------------------------------
     def adjoint_step(self, member: int, f_n, lam_in, lam_out, weight: float, box, L: int,

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm.so")
-SOURCES = ["lbm_step.cu", "lbm_diag.cu", "lbm_adjoint.cu", "lbm_api.cu"]
+SOURCES = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

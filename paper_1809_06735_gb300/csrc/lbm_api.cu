@@ -110,8 +110,8 @@ Layout make_layout(const lbm_config *cfg) {
   L.scratch_fields = lbm::kDiagFields;
   L.scratch = take(8 * L.scratch_fields * L.Nmax);
   L.partials = take(8 * lbm::diag_partials_needed(kMaxL));
-  L.stats = take(8 * kMaxL * 30);
-  L.Ls = take(4 * kMaxL);
+  L.stats = take(8 * (size_t)n * kMaxL * 30);
+  L.Ls = take(4 * (size_t)n * kMaxL);
   L.out7 = take(8 * 8);
   L.origins = take(8 * L.Nmax);
   L.total = off;
@@ -523,58 +523,101 @@ int lbm_global_balance(lbm_handle *h, int member, double *out) {
   return LBM_OK;
 }
 
-int lbm_subvolume_balance(lbm_handle *h, int member, const int *L, int nL, const int *origins,
-                          int n_origins, double *stats_out, double *per_box_out) {
-  int rc = check_member(h, member);
-  if (rc) return rc;
+}  // extern "C"
+
+namespace {
+
+// Queues the diagnostic of each listed member (term fields, summed-area
+// tables, box queries, statistics) and copies every member's statistics to
+// the host with one synchronisation at the end.
+int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int nL,
+                    const int *origins, int n_origins, double *stats_out,
+                    double *per_box_out) {
   if (!L || nL < 1 || nL > kMaxL) return fail(h, LBM_ERR_ARG, "need 1..32 box sizes");
   if (!stats_out) return fail(h, LBM_ERR_ARG, "stats_out is NULL");
-  const lbm_member_cfg &c = h->mcfg[member];
-  const size_t N = (size_t)c.nx * c.ny;
-  if (origins) {
-    if (n_origins < 1 || (size_t)n_origins > h->lay.Nmax)
-      return fail(h, LBM_ERR_ARG, "n_origins must be in 1..max cells");
-    for (int i = 0; i < n_origins; ++i)
-      if (origins[2 * i] < 0 || origins[2 * i] >= c.nx || origins[2 * i + 1] < 0 ||
-          origins[2 * i + 1] >= c.ny)
-        return fail(h, LBM_ERR_ARG, "origin outside the grid");
+  if (nm < 1) return fail(h, LBM_ERR_ARG, "no member given");
+  if (per_box_out && nm != 1) return fail(h, LBM_ERR_ARG, "per_box_out needs one member");
+  for (int i = 0; i < nm; ++i) {
+    int rc = check_member(h, members[i]);
+    if (rc) return rc;
+    const lbm_member_cfg &c = h->mcfg[members[i]];
+    if (origins) {
+      if (n_origins < 1 || (size_t)n_origins > h->lay.Nmax)
+        return fail(h, LBM_ERR_ARG, "n_origins must be in 1..max cells");
+      for (int k = 0; k < n_origins; ++k)
+        if (origins[2 * k] < 0 || origins[2 * k] >= c.nx || origins[2 * k + 1] < 0 ||
+            origins[2 * k + 1] >= c.ny)
+          return fail(h, LBM_ERR_ARG, "origin outside the grid");
+    }
   }
-  // history n, n-1, n-2
+  // history n, n-1, n-2 (shared clock of all members)
   const long long t = h->t;
   if (h->ring_time[t % 3] != t) {
-    rc = record(h);
+    int rc = record(h);
     if (rc) return rc;
   }
   if (t < 2 || h->ring_time[(t - 1) % 3] != t - 1 || h->ring_time[(t - 2) % 3] != t - 2)
     return fail(h, LBM_ERR_HISTORY, "snapshots of time n-1 and n-2 are missing");
-  std::vector<int> valid, where;
-  for (int i = 0; i < nL; ++i)
-    if (L[i] >= 1 && L[i] <= c.nx && L[i] <= c.ny) { valid.push_back(L[i]); where.push_back(i); }
-  if (per_box_out && (int)valid.size() != nL)
+  std::vector<std::vector<int>> valid(nm), where(nm);
+  std::vector<int> Ls_host((size_t)nm * kMaxL, 0);
+  for (int i = 0; i < nm; ++i) {
+    const lbm_member_cfg &c = h->mcfg[members[i]];
+    for (int k = 0; k < nL; ++k)
+      if (L[k] >= 1 && L[k] <= c.nx && L[k] <= c.ny) {
+        Ls_host[(size_t)i * kMaxL + valid[i].size()] = L[k];
+        valid[i].push_back(L[k]);
+        where[i].push_back(k);
+      }
+  }
+  if (per_box_out && (int)valid[0].size() != nL)
     return fail(h, LBM_ERR_ARG, "per_box_out needs every box size to fit the grid");
-  for (int i = 0; i < nL * 30; ++i) stats_out[i] = NAN;
-  if (valid.empty()) return LBM_OK;
-  CK(lbm::diag_terms(h->hm[member], snap_slot(h, member, (int)(t % 3)),
-                     snap_slot(h, member, (int)((t - 1) % 3)),
-                     snap_slot(h, member, (int)((t - 2) % 3)), h->sc, h->stream));
+  for (size_t k = 0; k < (size_t)nm * nL * 30; ++k) stats_out[k] = NAN;
   int *Ls_dev = reinterpret_cast<int *>(ws_at(h, h->lay.Ls));
   int *orig_dev = origins ? reinterpret_cast<int *>(ws_at(h, h->lay.origins)) : nullptr;
   double *stats_dev = reinterpret_cast<double *>(ws_at(h, h->lay.stats));
-  CK(cudaMemcpyAsync(Ls_dev, valid.data(), 4 * valid.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(Ls_dev, Ls_host.data(), 4 * Ls_host.size(), cudaMemcpyHostToDevice,
+                     h->stream));
   if (origins)
-    CK(cudaMemcpyAsync(orig_dev, origins, 8 * (size_t)n_origins, cudaMemcpyHostToDevice, h->stream));
-  const int nb = origins ? n_origins : (int)N;
-  (void)nb;
-  CK(lbm::diag_sat_and_query(h->hm[member], Ls_dev, (int)valid.size(), orig_dev, n_origins,
-                             h->sc, stats_dev, per_box_out, h->stream));
-  h->launches += 10;  // 4 term passes, 2 mean, 2 scan, query, final
-  std::vector<double> st(valid.size() * 30);
+    CK(cudaMemcpyAsync(orig_dev, origins, 8 * (size_t)n_origins, cudaMemcpyHostToDevice,
+                       h->stream));
+  for (int i = 0; i < nm; ++i) {
+    if (valid[i].empty()) continue;
+    const int m = members[i];
+    CK(lbm::diag_terms(h->hm[m], snap_slot(h, m, (int)(t % 3)),
+                       snap_slot(h, m, (int)((t - 1) % 3)), snap_slot(h, m, (int)((t - 2) % 3)),
+                       h->sc, h->stream));
+    CK(lbm::diag_sat_and_query(h->hm[m], Ls_dev + (size_t)i * kMaxL, (int)valid[i].size(),
+                               orig_dev, n_origins, h->sc, stats_dev + (size_t)i * kMaxL * 30,
+                               per_box_out, h->stream));
+    h->launches += 10;  // 4 term passes, 2 mean, 2 scan, query, final
+  }
+  std::vector<double> st((size_t)nm * kMaxL * 30);
   CK(cudaMemcpyAsync(st.data(), stats_dev, 8 * st.size(), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  for (size_t k = 0; k < valid.size(); ++k)
-    std::memcpy(stats_out + (size_t)where[k] * 30, st.data() + k * 30, 8 * 30);
+  for (int i = 0; i < nm; ++i)
+    for (size_t k = 0; k < valid[i].size(); ++k)
+      std::memcpy(stats_out + ((size_t)i * nL + where[i][k]) * 30,
+                  st.data() + ((size_t)i * kMaxL + k) * 30, 8 * 30);
   return LBM_OK;
 }
+
+}  // namespace
+
+int lbm_subvolume_balance(lbm_handle *h, int member, const int *L, int nL, const int *origins,
+                          int n_origins, double *stats_out, double *per_box_out) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  return balance_members(h, &member, 1, L, nL, origins, n_origins, stats_out, per_box_out);
+}
+
+int lbm_subvolume_balance_batch(lbm_handle *h, const int *members, int n_members, const int *L,
+                                int nL, const int *origins, int n_origins, double *stats_out) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (!members) return fail(h, LBM_ERR_ARG, "members is NULL");
+  return balance_members(h, members, n_members, L, nL, origins, n_origins, stats_out,
+                         nullptr);
+}
+
+extern "C" {
 
 int lbm_get_populations(lbm_handle *h, int member, double *f, int on_device) {
   int rc = check_member(h, member);

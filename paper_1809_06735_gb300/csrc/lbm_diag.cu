@@ -290,27 +290,50 @@ __global__ void __launch_bounds__(256) k_sat_rows(double *T, int nx, int ny,
   }
 }
 
-// Inclusive scan along y: one thread per (column, field), 8 rows in flight.
-__global__ void k_sat_cols(double *T, int nx, int ny, int nf) {
-  const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (size_t)nx * nf) return;
-  const int f = (int)(id / nx), x = (int)(id % nx);
+// Inclusive scan along y over a strip of 32 columns of one field: the 8
+// warps of the CTA each sum one chunk of rows, exchange the chunk totals
+// through shared memory, then rewrite their chunk as a running sum started
+// from the total of the chunks above.  Loads are coalesced across the strip.
+__global__ void __launch_bounds__(256) k_sat_cols(double *T, int nx, int ny) {
+  const int f = blockIdx.y;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int w = threadIdx.y;
+  const int chunk = (ny + 7) / 8;
+  const int y0 = min(ny, w * chunk), y1 = min(ny, y0 + chunk);
   double *col = T + (size_t)f * nx * ny + x;
-  double acc = 0.0;
-  int y = 0;
-  for (; y + 8 <= ny; y += 8) {
-    double v[8];
+  __shared__ double tot[8][32];
+  double s = 0.0;
+  if (x < nx) {
+    int y = y0;
+    for (; y + 8 <= y1; y += 8) {
+      double v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = col[(size_t)(y + k) * nx];
+      for (int k = 0; k < 8; ++k) v[k] = col[(size_t)(y + k) * nx];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      acc += v[k];
-      col[(size_t)(y + k) * nx] = acc;
+      for (int k = 0; k < 8; ++k) s += v[k];
     }
+    for (; y < y1; ++y) s += col[(size_t)y * nx];
   }
-  for (; y < ny; ++y) {
-    acc += col[(size_t)y * nx];
-    col[(size_t)y * nx] = acc;
+  tot[w][threadIdx.x] = s;
+  __syncthreads();
+  double acc = 0.0;
+  for (int k = 0; k < w; ++k) acc += tot[k][threadIdx.x];
+  if (x < nx) {
+    int y = y0;
+    for (; y + 8 <= y1; y += 8) {
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = col[(size_t)(y + k) * nx];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        acc += v[k];
+        col[(size_t)(y + k) * nx] = acc;
+      }
+    }
+    for (; y < y1; ++y) {
+      acc += col[(size_t)y * nx];
+      col[(size_t)y * nx] = acc;
+    }
   }
 }
 
@@ -330,75 +353,108 @@ __device__ __forceinline__ double Pext(const double *S, int nx, int ny, int x, i
   return v;
 }
 
-__device__ __forceinline__ double delta_of(const double *b, int nrhs) {
-  double sum = 0.0, mx = 0.0;
-  for (int i = 1; i <= nrhs; ++i) {
-    sum += b[i];
-    mx = fmax(mx, fabs(b[i]));
-  }
-  const double num = fabs(sum - b[0]);
+// Balancing error of eqs. (12), (13) from the box LHS, the running sum of
+// the RHS terms and their largest magnitude.
+__device__ __forceinline__ double delta_of(double lhs, double sum, double mx) {
+  const double num = fabs(sum - lhs);
   if (mx == 0.0) return num == 0.0 ? 0.0 : INFINITY;
   return num / mx;
 }
 
-// One thread per box: the 12 non-zero box averages (term 12 is 0), the two
-// balancing errors, shifted sums for the statistics and optionally the
-// per-box values.
-__global__ void __launch_bounds__(256) k_query(const double *T, int nx, int ny,
-                                               const double *means, const int *Ls, int nb,
-                                               const int *origins, double *partials,
-                                               double *per_box) {
+constexpr int kQStats = 28;  // [dE, dE^2, dZ, dZ^2, (d_k, d_k^2) for the 12 fields]
+
+// One thread per box: the 12 non-zero box averages (term 12, the 2D
+// vortex-stretching term, is identically 0), the two balancing errors, sums
+// of the deviations from the field means and of their squares for the
+// statistics, and optionally the per-box values.
+template <bool PER_BOX>
+__global__ void __launch_bounds__(256) k_query(const double *__restrict__ T, int nx, int ny,
+                                               const double *__restrict__ means,
+                                               const int *__restrict__ Ls, int nb,
+                                               const int *__restrict__ origins,
+                                               double *partials, double *per_box) {
   const int iL = blockIdx.y;
   const int L = Ls[iL];
   const size_t N = (size_t)nx * ny;
-  double acc[2 * 15];
-#pragma unroll
-  for (int q = 0; q < 30; ++q) acc[q] = 0.0;
-  const int tid = threadIdx.x;
   const double invA = 1.0 / ((double)L * (double)L);
-  for (int b = blockIdx.x * blockDim.x + tid; b < nb; b += gridDim.x * blockDim.x) {
+  double mean[12], s1[12], s2[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    mean[k] = means[k];
+    s1[k] = 0.0;
+    s2[k] = 0.0;
+  }
+  double dE1 = 0.0, dE2 = 0.0, dZ1 = 0.0, dZ2 = 0.0;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
     const int x0 = origins ? origins[2 * b] : b % nx;
     const int y0 = origins ? origins[2 * b + 1] : b / nx;
-    double v[15];
-#pragma unroll 4
+    double lhsE = 0.0, sumE = 0.0, maxE = 0.0, lhsZ = 0.0, sumZ = 0.0, maxZ = 0.0;
+    double *o = PER_BOX ? per_box + ((size_t)iL * nb + b) * 15 : nullptr;
+#pragma unroll
     for (int k = 0; k < 12; ++k) {
       const double *S = T + (size_t)k * N;
-      const double s = Pext(S, nx, ny, x0 + L, y0 + L) - Pext(S, nx, ny, x0, y0 + L) -
-                       Pext(S, nx, ny, x0 + L, y0) + Pext(S, nx, ny, x0, y0);
-      v[2 + k] = s * invA + means[k];
+      const double d = (Pext(S, nx, ny, x0 + L, y0 + L) - Pext(S, nx, ny, x0, y0 + L) -
+                        Pext(S, nx, ny, x0 + L, y0) + Pext(S, nx, ny, x0, y0)) * invA;
+      const double v = d + mean[k];
+      s1[k] += d;
+      s2[k] += d * d;
+      if (k == 0) {
+        lhsE = v;
+      } else if (k < 6) {
+        sumE += v;
+        maxE = fmax(maxE, fabs(v));
+      } else if (k == 6) {
+        lhsZ = v;
+      } else {
+        sumZ += v;
+        maxZ = fmax(maxZ, fabs(v));
+      }
+      if (PER_BOX) o[2 + k] = v;
     }
-    v[14] = 0.0;  // RHS^{Omega,6} = 0 in 2D
-    v[0] = delta_of(v + 2, 5);
-    v[1] = delta_of(v + 8, 6);
-    if (per_box) {
-      double *o = per_box + ((size_t)iL * nb + b) * 15;
-#pragma unroll
-      for (int q = 0; q < 15; ++q) o[q] = v[q];
-    }
-#pragma unroll
-    for (int q = 0; q < 15; ++q) {
-      const double d = v[q] - (q >= 2 && q < 14 ? means[q - 2] : 0.0);
-      acc[2 * q] += d;
-      acc[2 * q + 1] += d * d;
+    const double dE = delta_of(lhsE, sumE, maxE), dZ = delta_of(lhsZ, sumZ, maxZ);
+    dE1 += dE;
+    dE2 += dE * dE;
+    dZ1 += dZ;
+    dZ2 += dZ * dZ;
+    if (PER_BOX) {
+      o[0] = dE;
+      o[1] = dZ;
+      o[14] = 0.0;
     }
   }
-  block_sum_store<30>(acc, partials + ((size_t)iL * gridDim.x + blockIdx.x) * 30);
+  double acc[kQStats];
+  acc[0] = dE1;
+  acc[1] = dE2;
+  acc[2] = dZ1;
+  acc[3] = dZ2;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    acc[4 + 2 * k] = s1[k];
+    acc[5 + 2 * k] = s2[k];
+  }
+  block_sum_store<kQStats>(acc, partials + ((size_t)iL * gridDim.x + blockIdx.x) * kQStats);
 }
 
+// Mean and population standard deviation of the 15 quantities per size.
 __global__ void k_stats_final(const double *partials, int nblocks, const double *means,
                               int nb, int nL, double *stats) {
   const int iL = blockIdx.x, q = threadIdx.x;
   if (q >= 15) return;
-  double s1 = 0.0, s2 = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
-    s1 += partials[((size_t)iL * nblocks + b) * 30 + 2 * q];
-    s2 += partials[((size_t)iL * nblocks + b) * 30 + 2 * q + 1];
+  double mean = 0.0, sd = 0.0;
+  if (q < 14) {
+    const int i = q < 2 ? 2 * q : 4 + 2 * (q - 2);
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+      s1 += partials[((size_t)iL * nblocks + b) * kQStats + i];
+      s2 += partials[((size_t)iL * nblocks + b) * kQStats + i + 1];
+    }
+    const double m1 = s1 / nb;
+    const double shift = q >= 2 ? means[q - 2] : 0.0;
+    mean = shift + m1;
+    sd = sqrt(fmax(s2 / nb - m1 * m1, 0.0));
   }
-  const double m1 = s1 / nb;
-  const double var = fmax(s2 / nb - m1 * m1, 0.0);
-  const double shift = (q >= 2 && q < 14) ? means[q - 2] : 0.0;
-  stats[((size_t)iL * 15 + q) * 2] = shift + m1;
-  stats[((size_t)iL * 15 + q) * 2 + 1] = sqrt(var);
+  stats[((size_t)iL * 15 + q) * 2] = mean;
+  stats[((size_t)iL * 15 + q) * 2 + 1] = sd;
 }
 
 Grid grid_of(const Member &hm) {
@@ -475,21 +531,24 @@ cudaError_t diag_sat_and_query(const Member &hm, const int *Ls_dev, int nL,
   double *part_means = sc.partials;                       // [12][kMaxPartialBlocks]
   double *means = part_means + 12 * kMaxPartialBlocks;    // [12] (+4 pad)
   double *part_q = means + 16;                            // [nL][blocks][30]
-  int nb_sum = (int)((N + 255) / 256);
+  // about 16 elements per thread for the field sums
+  int nb_sum = (int)((N + 4095) / 4096);
   if (nb_sum > kMaxPartialBlocks) nb_sum = kMaxPartialBlocks;
   k_field_sums<<<dim3(nb_sum, 12), 256, 0, s>>>(T, N, part_means);
   k_field_means<<<1, 32, 0, s>>>(part_means, nb_sum, N, means, 12);
   k_sat_rows<<<dim3(ny, 12), 256, 0, s>>>(T, nx, ny, means);
-  {
-    const size_t nthreads = (size_t)nx * 12;
-    k_sat_cols<<<(unsigned)((nthreads + 127) / 128), 128, 0, s>>>(T, nx, ny, 12);
-  }
+  k_sat_cols<<<dim3((nx + 31) / 32, 12), dim3(32, 8), 0, s>>>(T, nx, ny);
   const int nbox = origins_dev ? n_origins : (int)N;
-  int qblocks = (nbox + 255) / 256;
+  // about 4 boxes per thread, at most kMaxPartialBlocks CTAs per size
+  int qblocks = (nbox + 1023) / 1024;
   if (qblocks > kMaxPartialBlocks) qblocks = kMaxPartialBlocks;
   if (qblocks < 1) qblocks = 1;
-  k_query<<<dim3(qblocks, nL), 256, 0, s>>>(T, nx, ny, means, Ls_dev, nbox, origins_dev,
-                                            part_q, per_box_dev);
+  if (per_box_dev)
+    k_query<true><<<dim3(qblocks, nL), 256, 0, s>>>(T, nx, ny, means, Ls_dev, nbox,
+                                                    origins_dev, part_q, per_box_dev);
+  else
+    k_query<false><<<dim3(qblocks, nL), 256, 0, s>>>(T, nx, ny, means, Ls_dev, nbox,
+                                                     origins_dev, part_q, nullptr);
   k_stats_final<<<nL, 32, 0, s>>>(part_q, qblocks, means, nbox, nL, stats_dev);
   return cudaGetLastError();
 }
