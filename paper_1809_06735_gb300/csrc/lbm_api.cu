@@ -373,6 +373,9 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
     M.F0 = c.F0;
     M.alpha = c.alpha;
     M.nu = (c.tau - 0.5) / 3.0;
+    M.rho0_f = (float)c.rho0;
+    M.omega_f = (float)(1.0 / c.tau);
+    M.alpha_f = (float)c.alpha;
     M.plane = (size_t)c.ny * M.pitch;
     M.pop[0] = ws_at(h, lay.pop0[m]);
     M.pop[1] = ws_at(h, lay.pop1[m]);

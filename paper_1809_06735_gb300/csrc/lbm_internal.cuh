@@ -38,6 +38,8 @@ struct Member {
   int pad0;
   double tau, omega;     // omega = 1 / tau
   double rho0, F0, alpha;
+  float rho0_f, omega_f, alpha_f;  // float copies for the FP32 kernels
+  int pad1;
   double nu;             // (tau - 1/2) / 3
   size_t plane;          // ny * pitch
   void *pop[2];          // population buffers

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) k_step_f32_vec(const Member *__restrict__
     float *__restrict__ dst = static_cast<float *>(M.pop[cur ^ 1]);
     const float *__restrict__ fxt = static_cast<const float *>(M.fx_tab);
     const float *__restrict__ fyt = static_cast<const float *>(M.fy_tab);
-    const float rho0 = (float)M.rho0, om = (float)M.omega, alpha = (float)M.alpha;
+    const float rho0 = M.rho0_f, om = M.omega_f, alpha = M.alpha_f;
     const int x = tl.x0 + 4 * lane;
     const bool active = x < nx;
     float4 fy4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -186,7 +186,7 @@ __global__ void k_step_scalar(const Member *__restrict__ members, int member, in
     f[l] = src[(size_t)l * M.plane + (size_t)ys * M.pitch + xs];
   }
   if constexpr (sizeof(T) == 4) {
-    collide_f32(f, (float)M.rho0, (float)M.omega, fx, fy, (float)M.alpha);
+    collide_f32(f, M.rho0_f, M.omega_f, fx, fy, M.alpha_f);
   } else {
     collide_f64(f, M.omega, fx, fy, M.alpha);
   }

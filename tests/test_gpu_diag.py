@@ -213,5 +213,7 @@ def test_balance_batch_equals_per_member(P):
     for i in range(3):
         single = lat.subvolume_balance(i, Ls)
         np.testing.assert_array_equal(batch[i], single)
-    assert np.all(np.isnan(batch[0, 3:])) and np.all(np.isnan(batch[1, 3:]))
+    # 32x32 fits L <= 32; 48x40 fits L <= 40; 64x64 fits every size
+    assert np.all(np.isnan(batch[0, 3:])) and np.all(np.isfinite(batch[0, :3, 2:, 0]))
+    assert np.all(np.isnan(batch[1, 4:])) and np.all(np.isfinite(batch[1, :4, 2:, 0]))
     assert np.all(np.isfinite(batch[2, :, 2:, 0]))
