@@ -218,6 +218,44 @@ int lbm_adjoint_step(lbm_handle *h, int member, const double *f_n,
 int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx,
                              int by, int L, double *acc);
 
+/* Largest grid (nx * ny cells) that lbm_global_balance_static accepts. */
+#define LBM_STATIC_MAX_CELLS (512 * 512)
+
+/* Allocation-free variant of lbm_global_balance (the paper has no
+ * counterpart; this is an interface of this library).
+ *
+ * For callers that cannot allocate device memory: for example a plug-in
+ * whose host application owns the whole device memory pool, or code that
+ * must not call cudaMalloc because it implicitly synchronises the device.
+ * Such callers cannot provide the workspace that lbm_create needs, so this
+ * entry point takes no handle: it computes the same 7 quantities as
+ * lbm_global_balance (same order, FP64) directly from caller-owned
+ * populations, using a fixed scratch array that the library holds in
+ * device memory (about 4.3 MB on every GPU that loads the library, until the
+ * process exits).
+ *
+ * f:   device pointer, double[9][ny][nx], the public pre-collision
+ *      populations f_l(x, n) (as written by lbm_get_populations).
+ * nx, ny: grid, 1 <= nx * ny <= LBM_STATIC_MAX_CELLS (larger grids return
+ *      LBM_ERR_ARG with a message; use lbm_global_balance for them).
+ * m:   host pointer to the member parameters (tau, force_kind, kf, F0,
+ *      alpha are used; rho0 is not).
+ * out: host pointer to LBM_NGLOBAL doubles; the call synchronises
+ *      cuda_stream (NULL = legacy default stream) before returning.
+ * Calls no cudaMalloc or cudaFree.  The first call on a device looks up the
+ * scratch address with cudaGetSymbolAddress; make that first call before
+ * any stream capture.  Every call on a device shares the one scratch array
+ * (which keeps the last call's contents): calls whose work overlaps on the
+ * GPU, e.g. on two streams at once, race and give wrong results.  Errors are
+ * reported through lbm_static_last_error(). */
+int lbm_global_balance_static(const double *f, int nx, int ny,
+                              const lbm_member_cfg *m, double *out,
+                              void *cuda_stream);
+
+/* Message of the last failing lbm_global_balance_static call of this host
+ * thread.  Never NULL. */
+const char *lbm_static_last_error(void);
+
 /* Message of the last failing call on this handle (or of the last failing
  * handle-less call when h is NULL).  Never NULL. */
 const char *lbm_last_error(const lbm_handle *h);
