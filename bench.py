@@ -8,8 +8,9 @@ time steps (the batched stream-collide, one launch per step for all
 members, replayed from CUDA graphs), followed by the diagnostic event: the
 moment snapshots of the three last time levels and, for every member, the
 sub-volume energy/enstrophy balance (terms, summed-area tables, balancing
-errors and their statistics) at L = 2, 4, ..., 256 over all periodic
-origins.
+errors and their statistics) at L = 2, 4, ..., 256 on the paper's Table 1
+random boxes (56000 per member).  One event over every periodic origin
+(2.1 M boxes per member) is timed beside it.
 
 Metric: aggregate GLUPS (lattice updates per second over all members and
 GPUs, diagnostics included), plus the roofline of the dominant kernel
@@ -55,6 +56,26 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
+
+
+def member_seed(seed0: int, rank: int, members_per_rank: int, m: int) -> int:
+    """Seed of member m on a rank: the ensemble is sharded by member, so each
+    rank runs its own disjoint block of seeds (weak scaling)."""
+    return seed0 + rank * members_per_rank + m
+
+
+def max_over_ranks(seconds: float) -> float:
+    """Slowest rank's time (the job's time); host-side, over the process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_glups(world_size: int, lu_per_rank_step: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: updates of all ranks over the slowest rank's time."""
+    return world_size * lu_per_rank_step * steps / seconds / 1e9
 
 
 def dist_env():
@@ -147,20 +168,30 @@ class ClockSampler:
 # sampled origins.
 # ---------------------------------------------------------------------------
 
-def oracle_period_sample(member_seed: int, n_steps: int = PERIOD, origins_per_L: int = 256):
+def table1_boxes(n, Ls, scale=1.0):
+    """The paper's Table 1 random boxes for each size (seed = L); ``scale``
+    < 1 keeps only that fraction of each list (bounded CPU samples)."""
+    out = []
+    for L in Ls:
+        o = li.table1_origins(n, L, seed=L)
+        out.append(o[:max(1, int(round(o.shape[0] * scale)))])
+    return out
+
+
+def oracle_period_sample(seed: int, n_steps: int = PERIOD, box_fraction: float = 1.0):
     import oracle
     wl = li.decaying_ensemble_workload()
     n, tau = wl["n"], wl["tau"]
-    rho, ux, uy = li.random_phase(n, seed=member_seed, u_rms=wl["u_rms"])
+    rho, ux, uy = li.random_phase(n, seed=seed, u_rms=wl["u_rms"])
     f = oracle.init(rho, ux, uy)
-    rng = np.random.default_rng(member_seed)
-    origins = rng.integers(0, n, size=(origins_per_L, 2)).astype(np.int32)
+    boxes = table1_boxes(n, wl["Ls"], box_fraction)
     t0 = time.perf_counter()
     f_a = oracle.run(f, n_steps - 2, tau)
     f_b = oracle.run(f_a, 1, tau)
     f_c = oracle.run(f_b, 1, tau)
     T = oracle.terms_from_populations(f_c, f_b, f_a, tau)
-    oracle.balance_stats(T, wl["Ls"], origins=origins)
+    for L, o in zip(wl["Ls"], boxes):
+        oracle.balance_stats(T, [L], origins=o)
     dt = time.perf_counter() - t0
     return n * n * n_steps, dt
 
@@ -177,15 +208,15 @@ def run_reference(args):
     oracle.build()
     wl = li.decaying_ensemble_workload()
     for w in range(args.warmup):
-        oracle_period_sample(wl["seed0"] + w, n_steps=20, origins_per_L=16)
+        oracle_period_sample(wl["seed0"] + w, n_steps=20, box_fraction=0.01)
     lu, secs = 0, 0.0
     for k in range(args.steps):
-        a, b = oracle_period_sample(wl["seed0"] + k, n_steps=20, origins_per_L=16)
+        a, b = oracle_period_sample(wl["seed0"] + k, n_steps=20, box_fraction=0.01)
         lu += a
         secs += b
     v = lu / secs / 1e9
     sample = ("per step: one 512^2 member of the 64, 20 LBM steps of the 200-step period, "
-              "then the diagnostic on 16 random origins per L (L=2..256)")
+              "then the diagnostic on 1% of the Table 1 random boxes per L (L=2..256)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
@@ -206,8 +237,8 @@ def workload_config():
     return {"workload": wl["name"], "members_per_gpu": wl["members"], "grid": [wl["n"], wl["n"]],
             "tau": wl["tau"], "precision": "fp32 deviation populations, fp64 diagnostics",
             "lbm_steps_per_step": PERIOD,
-            "diagnostic": "per step, every member: balance terms + SAT + all-origin boxes "
-                          "at L=2..256",
+            "diagnostic": "per step, every member: balance terms + SAT + the paper's "
+                          "Table 1 random boxes (56000 per member) at L=2..256",
             "l2": "inputs larger than L2 (1.2 GB of populations per GPU), no flush"}
 
 
@@ -234,7 +265,7 @@ def run_ours(args):
     # pinned host initial fields (also the e2e inputs)
     host = torch.empty((M, 3, n, n), dtype=torch.float64, pin_memory=True)
     for m in range(M):
-        r, u, v = li.random_phase(n, seed=wl["seed0"] + rank * M + m, u_rms=wl["u_rms"])
+        r, u, v = li.random_phase(n, seed=member_seed(wl["seed0"], rank, M, m), u_rms=wl["u_rms"])
         host[m, 0].copy_(torch.from_numpy(r))
         host[m, 1].copy_(torch.from_numpy(u))
         host[m, 2].copy_(torch.from_numpy(v))
@@ -245,6 +276,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     Ls = wl["Ls"]
     all_members = list(range(M))
+    boxes = table1_boxes(n, Ls)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -255,7 +287,7 @@ def run_ours(args):
         if rec is not None:
             rec[1].record(stream)
         lat.step(PERIOD - PURE_STEPS)
-        return lat.subvolume_balance_batch(all_members, Ls)
+        return lat.subvolume_balance_batch(all_members, Ls, origins=boxes)
 
     for _ in range(args.warmup):
         bench_step()
@@ -280,17 +312,27 @@ def run_ours(args):
     elapsed = t0.elapsed_time(t1) / 1e3
     pure = sum(a.elapsed_time(b) for a, b in recs) / 1e3
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed)
     assert stats is not None and np.all(np.isfinite(stats[:, :, 2:, 0]))
     lu_per_gpu_step = M * n * n * PERIOD
-    value = ws * lu_per_gpu_step * args.steps / elapsed / 1e9
+    value = aggregate_glups(ws, lu_per_gpu_step, args.steps, elapsed)
     kern_s = pure / (args.steps * PURE_STEPS)
     step_glups = M * n * n / kern_s / 1e9
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_LU_F32 * M * n * n / kern_s / 1e9
+
+    # one diagnostic event of all members on its own: the Table 1 boxes of the
+    # timed steps, and every periodic origin (2.1 M boxes per member)
+    diag_ms = {}
+    for key, org in (("table1_boxes", boxes), ("all_origins", None)):
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        a.record(stream)
+        st = lat.subvolume_balance_batch(all_members, Ls, origins=org)
+        b.record(stream)
+        torch.cuda.synchronize()
+        assert np.all(np.isfinite(st[:, :, 2:, 0]))
+        diag_ms[key] = a.elapsed_time(b)
 
     # plain single-instance FP64 step on one 512^2 member
     lat64 = P.Lattice([P.Member(n, n, tau)], precision=64, graph_steps=20, stream=stream,
@@ -317,7 +359,7 @@ def run_ours(args):
         for m in range(M):
             lat.init_fields(m, hnp[m, 0], hnp[m, 1], hnp[m, 2])
         lat.step(PERIOD)
-        lat.subvolume_balance_batch(all_members, Ls)
+        lat.subvolume_balance_batch(all_members, Ls, origins=boxes)
     torch.cuda.synchronize()
     te = time.perf_counter() - te
     e2e = {"value": ws * lu_per_gpu_step * e2e_steps / te / 1e9, "unit": "GLUPS",
@@ -333,7 +375,7 @@ def run_ours(args):
         lu, secs = oracle_period_sample(wl["seed0"])
         cpu = {"value": lu / secs / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
                "sample": "one 512^2 member of the 64: the full 200-step period, then the "
-                         "diagnostic with 256 random origins per L (L=2..256)",
+                         "diagnostic on the same Table 1 random boxes (L=2..256)",
                "seconds": secs}
 
     if rank == 0:
@@ -351,6 +393,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": BYTES_PER_LU_F32 * M * n * n,
                          "avg_launch_ms": kern_s * 1e3},
             "step_only_glups_per_gpu": step_glups,
+            "diagnostic_event_ms": dict(diag_ms, members=M, sizes=list(Ls)),
             "fp64_plain_single_instance": {"glups": fp64_glups, "grid": [n, n],
                                            "ratio_batched_fp32_over_fp64": step_glups / fp64_glups},
             "cpu_baseline": cpu,

@@ -88,6 +88,12 @@ typedef struct lbm_config {
                       lbm_record_snapshot() calls record */
   int graph_steps; /* > 0: lbm_step replays CUDA graphs of this many steps
                       (rounded up to even); 0: plain launches */
+  int diag_precision; /* arithmetic of the balance terms and box statistics:
+                      64 = FP64; 32 = FP32 with every cancelling quantity
+                      (time differences, pressure deviation) formed in FP64
+                      first; 0 = same as precision.  Snapshots, summed-area
+                      tables (exact 64-bit fixed point) and all reductions
+                      are exact or FP64 in both cases. */
   void *cuda_stream; /* cudaStream_t of all work; NULL = default stream */
 } lbm_config;
 
@@ -157,30 +163,33 @@ int lbm_global_balance(lbm_handle *h, int member, double *out);
  * the local terms LHS^E, RHS^{E,1..5}, LHS^Omega, RHS^{Omega,1..6} are
  * formed from the snapshots at n, n-1, n-2 (the snapshot at n is recorded
  * if missing; LBM_ERR_HISTORY if n-1 or n-2 is missing), averaged over L x L
- * boxes (periodic wrap) through FP64 summed-area tables, and turned into the
- * balancing errors delta^E, delta^Omega (0 when numerator and denominator
- * are 0, +Inf when only the denominator is).
- * Boxes: every one of the nx*ny periodic origins when origins == NULL, else
- * the n_origins lower-left corners (x0, y0) in the host array
- * origins[2*n_origins] (0 <= x0 < nx, 0 <= y0 < ny), the same for every L.
+ * boxes (periodic wrap) through exact fixed-point summed-area tables, and
+ * turned into the balancing errors delta^E, delta^Omega (0 when numerator
+ * and denominator are 0, +Inf when only the denominator is).
+ * Boxes: with origins == NULL and counts == NULL, every one of the nx*ny
+ * periodic origins for every L; otherwise counts[i] (host, >= 1) boxes for
+ * L[i], whose lower-left corners (x0, y0) are the host pairs of origins
+ * (0 <= x0 < nx, 0 <= y0 < ny), concatenated in the order of L (e.g. the
+ * paper's Table 1 random boxes).
  * Sizes with L < 1 or L > min(nx, ny) are skipped: their statistics are NaN.
  * stats_out (host, double[nL][15][2]; synchronises): mean and population
  * standard deviation over the boxes of the 15 quantities
  * [delta^E, delta^Omega, LHS^E, RHS^{E,1..5}, LHS^O, RHS^{O,1..6}].
- * per_box_out (device, double[nL][n_boxes][15], may be NULL; then every L
- * must fit the grid, else LBM_ERR_ARG): every box. */
+ * per_box_out (device, may be NULL; then every L must fit the grid, else
+ * LBM_ERR_ARG): double[rows][15], one row per box in the order of L (nL * nx
+ * * ny rows for all origins, sum(counts) rows for lists). */
 int lbm_subvolume_balance(lbm_handle *h, int member, const int *L, int nL,
-                          const int *origins, int n_origins, double *stats_out,
-                          double *per_box_out);
+                          const int *origins, const int *counts,
+                          double *stats_out, double *per_box_out);
 
 /* The same diagnostic for the n_members members listed in the host array
  * members[], queued back to back with a single synchronisation at the end:
  * stats_out (host) is double[n_members][nL][15][2], each member's sizes
- * checked against its own grid.  origins, when given, apply to every
- * member.  No per-box output. */
+ * checked against its own grid.  origins and counts, when given, apply to
+ * every member.  No per-box output. */
 int lbm_subvolume_balance_batch(lbm_handle *h, const int *members,
                                 int n_members, const int *L, int nL,
-                                const int *origins, int n_origins,
+                                const int *origins, const int *counts,
                                 double *stats_out);
 
 /* Public pre-collision populations f_l(x, n) of member `member` as

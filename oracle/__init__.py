@@ -60,6 +60,8 @@ def _load():
             lib.orc_stream.argtypes = [I, I, P, P]
             lib.orc_run.argtypes = [I, I, D, I, D, I, D, P, I]
             lib.orc_run.restype = I
+            lib.orc_run_window.argtypes = [I, I, D, I, D, I, D, P, I, I, I, I, I]
+            lib.orc_run_window.restype = I
             lib.orc_init.argtypes = [I, I, P, P, P, P]
             lib.orc_moments.argtypes = [I, I, I, D, I, D, P, P, P, P, P, P]
             lib.orc_ddx.argtypes = [I, I, P, P]
@@ -168,6 +170,20 @@ def run(f, nsteps, tau, force: Force = NO_FORCE):
     rc = _load().orc_run(nx, ny, tau, k, F0, kf, a, _p(f), int(nsteps))
     if rc != 0:
         raise MemoryError("oracle run failed")
+    return f
+
+
+def run_window(f_window, nsteps, tau, force: Force, x0, y0, NX, NY):
+    """nsteps steps of a window of a larger NX x NY periodic grid whose lower
+    left cell is the global cell (x0, y0); only cells at least nsteps cells
+    from the window's edges are valid afterwards (light cone)."""
+    f = _f64(f_window).copy()
+    _, wy, wx = f.shape
+    k, F0, kf, a = force.args()
+    rc = _load().orc_run_window(wx, wy, tau, k, F0, kf, a, _p(f), int(nsteps), int(x0),
+                                int(y0), int(NX), int(NY))
+    if rc != 0:
+        raise MemoryError("oracle window run failed")
     return f
 
 

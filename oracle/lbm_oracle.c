@@ -167,6 +167,35 @@ int orc_run(int nx, int ny, double tau, int force_kind, double F0, int kf,
   return 0;
 }
 
+/* nsteps time steps on a wx x wy window cut out of a larger NX x NY periodic
+ * grid at global offset (X0, Y0): the same collide-then-stream as orc_step,
+ * with the external force taken at the global coordinates
+ * ((X0 + i) mod NX, (Y0 + j) mod NY) and the window treated as periodic.  A
+ * step moves information by at most one cell, so after nsteps steps the
+ * window cells at least nsteps cells away from its edges hold exactly the
+ * values of the global run; the others are meaningless. */
+int orc_run_window(int wx, int wy, double tau, int force_kind, double F0, int kf,
+                   double alpha, double *f, int nsteps, int X0, int Y0, int NX,
+                   int NY) {
+  size_t plane = (size_t)wx * wy;
+  double *s = (double *)malloc(sizeof(double) * Q * plane);
+  if (!s) return -1;
+  for (int n = 0; n < nsteps; ++n) {
+    for (int y = 0; y < wy; ++y)
+      for (int x = 0; x < wx; ++x) {
+        double a[Q], b[Q], Fex, Fey;
+        for (int l = 0; l < Q; ++l) a[l] = f[l * plane + (size_t)y * wx + x];
+        orc_force_ext(NX, NY, force_kind, F0, kf, wrap(X0 + x, NX), wrap(Y0 + y, NY), &Fex,
+                      &Fey);
+        orc_collide_cell(a, tau, Fex, Fey, alpha, b);
+        for (int l = 0; l < Q; ++l) s[l * plane + (size_t)y * wx + x] = b[l];
+      }
+    orc_stream(wx, wy, s, f);
+  }
+  free(s);
+  return 0;
+}
+
 /* Initial state: f_l(x, 0) = f_eq_l(rho(x), u(x)). */
 void orc_init(int nx, int ny, const double *rho, const double *ux,
               const double *uy, double *f) {

@@ -48,7 +48,7 @@ class _Config(ctypes.Structure):
     _fields_ = [("n_members", ctypes.c_int), ("members", ctypes.POINTER(_MemberCfg)),
                 ("precision", ctypes.c_int), ("storage", ctypes.c_int),
                 ("diag_every", ctypes.c_int), ("graph_steps", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("diag_precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -74,8 +74,8 @@ def load_library(path: str = LIB_PATH):
         "lbm_record_snapshot": ([P], I),
         "lbm_moments": ([P, I, P, P, P, P], I),
         "lbm_global_balance": ([P, I, P], I),
-        "lbm_subvolume_balance": ([P, I, P, I, P, I, P, P], I),
-        "lbm_subvolume_balance_batch": ([P, P, I, P, I, P, I, P], I),
+        "lbm_subvolume_balance": ([P, I, P, I, P, P, P, P], I),
+        "lbm_subvolume_balance_batch": ([P, P, I, P, I, P, P, P], I),
         "lbm_get_populations": ([P, I, P, I], I),
         "lbm_set_populations": ([P, I, P, I], I),
         "lbm_member_status": ([P, I, P], I),
@@ -130,7 +130,7 @@ class Lattice:
     (default: the current torch stream at construction)."""
 
     def __init__(self, members: Sequence[Member], precision: int = 32, diag_every: int = 0,
-                 graph_steps: int = 0, stream=None, device=None):
+                 graph_steps: int = 0, stream=None, device=None, diag_precision: int = 0):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -141,7 +141,7 @@ class Lattice:
         arr = (_MemberCfg * len(self.members))(*[m.c() for m in self.members])
         self._arr = arr
         self._cfg = _Config(len(self.members), arr, precision, 0, diag_every, graph_steps,
-                            ctypes.c_void_p(self.stream.cuda_stream))
+                            diag_precision, ctypes.c_void_p(self.stream.cuda_stream))
         nbytes = ctypes.c_size_t()
         self._check(self.lib.lbm_workspace_size(ctypes.byref(self._cfg), ctypes.byref(nbytes)))
         self.workspace_bytes = nbytes.value
@@ -254,26 +254,40 @@ class Lattice:
         self._check(self.lib.lbm_global_balance(self.h, member, _ptr(out)))
         return out
 
+    @staticmethod
+    def _origin_lists(Ls, origins):
+        """(concatenated origins [n, 2] int32, counts [nL] int32) or (None, None).
+        ``origins``: None (all periodic origins), one [n, 2] array used for
+        every size, or a sequence of nL arrays (one per size)."""
+        if origins is None:
+            return None, None
+        if isinstance(origins, np.ndarray) or (len(origins) and np.isscalar(origins[0][0])):
+            o = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1, 2)
+            per = [o] * len(Ls)
+        else:
+            per = [np.ascontiguousarray(o, dtype=np.int32).reshape(-1, 2) for o in origins]
+            if len(per) != len(Ls):
+                raise ValueError("one origin array per box size is required")
+        counts = np.array([p.shape[0] for p in per], dtype=np.int32)
+        return np.ascontiguousarray(np.concatenate(per, axis=0)), counts
+
     def subvolume_balance(self, member: int, Ls, origins=None, per_box: bool = False):
         """Statistics [nL, 15, 2] (mean, population std) of the box quantities
         [delta^E, delta^Omega, 13 terms]; with ``per_box`` also the device
-        tensor [nL, n_boxes, 15]."""
+        tensor of every box, [rows, 15] in the order of Ls (rows = nL * nx * ny
+        for all origins).  ``origins``: see ``_origin_lists``."""
         Ls = np.ascontiguousarray(Ls, dtype=np.int32)
         nL = len(Ls)
         ny, nx = self._shape(member)
-        if origins is not None:
-            origins = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1, 2)
-            nb = origins.shape[0]
-        else:
-            nb = nx * ny
+        o, counts = self._origin_lists(Ls, origins)
+        rows = nL * nx * ny if o is None else int(counts.sum())
         stats = np.empty((nL, NQUANT, 2))
         pb = None
         if per_box:
-            pb = self._torch.empty((nL, nb, NQUANT), dtype=self._torch.float64,
+            pb = self._torch.empty((rows, NQUANT), dtype=self._torch.float64,
                                    device=self.device)
         self._check(self.lib.lbm_subvolume_balance(
-            self.h, member, _ptr(Ls), nL, _ptr(origins) if origins is not None else None,
-            nb if origins is not None else 0, _ptr(stats), _ptr(pb)))
+            self.h, member, _ptr(Ls), nL, _ptr(o), _ptr(counts), _ptr(stats), _ptr(pb)))
         return (stats, pb) if per_box else stats
 
     def subvolume_balance_batch(self, members, Ls, origins=None):
@@ -281,12 +295,9 @@ class Lattice:
         mem = np.ascontiguousarray(members, dtype=np.int32)
         Ls = np.ascontiguousarray(Ls, dtype=np.int32)
         stats = np.empty((len(mem), len(Ls), NQUANT, 2))
-        if origins is not None:
-            origins = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1, 2)
+        o, counts = self._origin_lists(Ls, origins)
         self._check(self.lib.lbm_subvolume_balance_batch(
-            self.h, _ptr(mem), len(mem), _ptr(Ls), len(Ls),
-            _ptr(origins) if origins is not None else None,
-            origins.shape[0] if origins is not None else 0, _ptr(stats)))
+            self.h, _ptr(mem), len(mem), _ptr(Ls), len(Ls), _ptr(o), _ptr(counts), _ptr(stats)))
         return stats
 
     # -- adjoint ------------------------------------------------------------
@@ -312,7 +323,7 @@ def workspace_size(members: Sequence[Member], precision: int = 32, diag_every: i
     """Host-only query of the device workspace bytes for a configuration."""
     lib = load_library()
     arr = (_MemberCfg * len(members))(*[m.c() for m in members])
-    cfg = _Config(len(members), arr, precision, 0, diag_every, graph_steps, None)
+    cfg = _Config(len(members), arr, precision, 0, diag_every, graph_steps, 0, None)
     n = ctypes.c_size_t()
     rc = lib.lbm_workspace_size(ctypes.byref(cfg), ctypes.byref(n))
     if rc != LBM_OK:

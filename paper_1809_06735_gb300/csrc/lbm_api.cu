@@ -35,6 +35,7 @@ struct Layout {
   size_t scratch, partials, stats, Ls, out7, origins;
   size_t total;
   size_t Nmax;
+  size_t origin_cap;  // boxes the origin buffer holds
   size_t scratch_fields;
 };
 
@@ -53,6 +54,7 @@ int check_config(const lbm_config *cfg, std::string &err) {
   if (cfg->n_members < 1 || !cfg->members) { err = "n_members must be >= 1 with a member array"; return LBM_ERR_ARG; }
   if (cfg->precision != 32 && cfg->precision != 64) { err = "precision must be 32 or 64"; return LBM_ERR_ARG; }
   if (cfg->storage != 0) { err = "storage: only 0 (double buffer) is available"; return LBM_ERR_ARG; }
+  if (cfg->diag_precision != 0 && cfg->diag_precision != 32 && cfg->diag_precision != 64) { err = "diag_precision must be 0, 32 or 64"; return LBM_ERR_ARG; }
   if (cfg->diag_every < 0 || cfg->graph_steps < 0) { err = "diag_every and graph_steps must be >= 0"; return LBM_ERR_ARG; }
   for (int m = 0; m < cfg->n_members; ++m) {
     const lbm_member_cfg &c = cfg->members[m];
@@ -111,9 +113,10 @@ Layout make_layout(const lbm_config *cfg) {
   L.scratch = take(8 * L.scratch_fields * L.Nmax);
   L.partials = take(8 * lbm::diag_partials_needed(kMaxL));
   L.stats = take(8 * (size_t)n * kMaxL * 30);
-  L.Ls = take(4 * (size_t)n * kMaxL);
+  L.Ls = take(4 * 4 * (size_t)n * kMaxL);  // per-size meta rows {L, boxes, offsets}
   L.out7 = take(8 * 8);
-  L.origins = take(8 * L.Nmax);
+  L.origin_cap = std::max<size_t>(4 * L.Nmax, (size_t)1 << 20);
+  L.origins = take(8 * L.origin_cap);
   L.total = off;
   return L;
 }
@@ -131,6 +134,7 @@ struct lbm_handle {
   int ntiles = 0;
   std::vector<int> scalar_members;
   int precision = 32;
+  int diag_precision = 32;  // arithmetic of the term fields and box statistics
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   int cur = 0;
@@ -340,6 +344,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
   h->lay = lay;
   h->ws = static_cast<char *>(workspace);
   h->precision = cfg->precision;
+  h->diag_precision = cfg->diag_precision ? cfg->diag_precision : cfg->precision;
   h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   h->graph_k = cfg->graph_steps > 0 ? (cfg->graph_steps + 1) / 2 * 2 : 0;
   h->d_members = reinterpret_cast<Member *>(ws_at(h, lay.members));
@@ -534,24 +539,32 @@ namespace {
 // tables, box queries, statistics) and copies every member's statistics to
 // the host with one synchronisation at the end.
 int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int nL,
-                    const int *origins, int n_origins, double *stats_out,
+                    const int *origins, const int *counts, double *stats_out,
                     double *per_box_out) {
   if (!L || nL < 1 || nL > kMaxL) return fail(h, LBM_ERR_ARG, "need 1..32 box sizes");
   if (!stats_out) return fail(h, LBM_ERR_ARG, "stats_out is NULL");
   if (nm < 1) return fail(h, LBM_ERR_ARG, "no member given");
   if (per_box_out && nm != 1) return fail(h, LBM_ERR_ARG, "per_box_out needs one member");
+  if ((origins == nullptr) != (counts == nullptr))
+    return fail(h, LBM_ERR_ARG, "origins and counts go together (both NULL: all origins)");
+  size_t total_boxes = 0;
+  if (origins) {
+    for (int i = 0; i < nL; ++i) {
+      if (counts[i] < 1) return fail(h, LBM_ERR_ARG, "every box size needs at least one box");
+      total_boxes += (size_t)counts[i];
+    }
+    if (total_boxes > h->lay.origin_cap)
+      return fail(h, LBM_ERR_ARG, "too many boxes for the origin buffer");
+  }
   for (int i = 0; i < nm; ++i) {
     int rc = check_member(h, members[i]);
     if (rc) return rc;
     const lbm_member_cfg &c = h->mcfg[members[i]];
-    if (origins) {
-      if (n_origins < 1 || (size_t)n_origins > h->lay.Nmax)
-        return fail(h, LBM_ERR_ARG, "n_origins must be in 1..max cells");
-      for (int k = 0; k < n_origins; ++k)
+    if (origins)
+      for (size_t k = 0; k < total_boxes; ++k)
         if (origins[2 * k] < 0 || origins[2 * k] >= c.nx || origins[2 * k + 1] < 0 ||
             origins[2 * k + 1] >= c.ny)
           return fail(h, LBM_ERR_ARG, "origin outside the grid");
-    }
   }
   // history n, n-1, n-2 (shared clock of all members)
   const long long t = h->t;
@@ -561,44 +574,54 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
   }
   if (t < 2 || h->ring_time[(t - 1) % 3] != t - 1 || h->ring_time[(t - 2) % 3] != t - 2)
     return fail(h, LBM_ERR_HISTORY, "snapshots of time n-1 and n-2 are missing");
-  std::vector<std::vector<int>> valid(nm), where(nm);
-  std::vector<int> Ls_host((size_t)nm * kMaxL, 0);
+  // per member: the sizes that fit its grid, with their box counts and offsets
+  std::vector<std::vector<int>> where(nm);
+  std::vector<int> meta((size_t)nm * kMaxL * 4, 0), maxb(nm, 0);
   for (int i = 0; i < nm; ++i) {
     const lbm_member_cfg &c = h->mcfg[members[i]];
-    for (int k = 0; k < nL; ++k)
-      if (L[k] >= 1 && L[k] <= c.nx && L[k] <= c.ny) {
-        Ls_host[(size_t)i * kMaxL + valid[i].size()] = L[k];
-        valid[i].push_back(L[k]);
-        where[i].push_back(k);
+    const int N = c.nx * c.ny;
+    int ooff = 0, row = 0, k = 0;
+    for (int q = 0; q < nL; ++q) {
+      const int nb = origins ? counts[q] : N;
+      if (L[q] >= 1 && L[q] <= c.nx && L[q] <= c.ny) {
+        int *mrow = &meta[((size_t)i * kMaxL + k) * 4];
+        mrow[0] = L[q];
+        mrow[1] = nb;
+        mrow[2] = origins ? ooff : -1;
+        mrow[3] = row;
+        maxb[i] = std::max(maxb[i], nb);
+        where[i].push_back(q);
+        ++k;
+      } else if (per_box_out) {
+        return fail(h, LBM_ERR_ARG, "per_box_out needs every box size to fit the grid");
       }
+      ooff += origins ? counts[q] : 0;
+      row += nb;
+    }
   }
-  if (per_box_out && (int)valid[0].size() != nL)
-    return fail(h, LBM_ERR_ARG, "per_box_out needs every box size to fit the grid");
   for (size_t k = 0; k < (size_t)nm * nL * 30; ++k) stats_out[k] = NAN;
-  int *Ls_dev = reinterpret_cast<int *>(ws_at(h, h->lay.Ls));
+  int *meta_dev = reinterpret_cast<int *>(ws_at(h, h->lay.Ls));
   int *orig_dev = origins ? reinterpret_cast<int *>(ws_at(h, h->lay.origins)) : nullptr;
   double *stats_dev = reinterpret_cast<double *>(ws_at(h, h->lay.stats));
-  CK(cudaMemcpyAsync(Ls_dev, Ls_host.data(), 4 * Ls_host.size(), cudaMemcpyHostToDevice,
-                     h->stream));
+  CK(cudaMemcpyAsync(meta_dev, meta.data(), 4 * meta.size(), cudaMemcpyHostToDevice, h->stream));
   if (origins)
-    CK(cudaMemcpyAsync(orig_dev, origins, 8 * (size_t)n_origins, cudaMemcpyHostToDevice,
-                       h->stream));
+    CK(cudaMemcpyAsync(orig_dev, origins, 8 * total_boxes, cudaMemcpyHostToDevice, h->stream));
   for (int i = 0; i < nm; ++i) {
-    if (valid[i].empty()) continue;
+    if (where[i].empty()) continue;
     const int m = members[i];
-    CK(lbm::diag_terms(h->hm[m], snap_slot(h, m, (int)(t % 3)),
+    CK(lbm::diag_terms(h->hm[m], h->diag_precision, snap_slot(h, m, (int)(t % 3)),
                        snap_slot(h, m, (int)((t - 1) % 3)), snap_slot(h, m, (int)((t - 2) % 3)),
                        h->sc, h->stream));
-    CK(lbm::diag_sat_and_query(h->hm[m], Ls_dev + (size_t)i * kMaxL, (int)valid[i].size(),
-                               orig_dev, n_origins, h->sc, stats_dev + (size_t)i * kMaxL * 30,
-                               per_box_out, h->stream));
-    h->launches += 10;  // 4 term passes, 2 mean, 2 scan, query, final
+    CK(lbm::diag_sat_and_query(h->hm[m], h->diag_precision, meta_dev + (size_t)i * kMaxL * 4,
+                               (int)where[i].size(), maxb[i], orig_dev, h->sc,
+                               stats_dev + (size_t)i * kMaxL * 30, per_box_out, h->stream));
+    h->launches += 10;  // 4 term passes, max, scales, 2 scans, query, statistics
   }
   std::vector<double> st((size_t)nm * kMaxL * 30);
   CK(cudaMemcpyAsync(st.data(), stats_dev, 8 * st.size(), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   for (int i = 0; i < nm; ++i)
-    for (size_t k = 0; k < valid[i].size(); ++k)
+    for (size_t k = 0; k < where[i].size(); ++k)
       std::memcpy(stats_out + ((size_t)i * nL + where[i][k]) * 30,
                   st.data() + ((size_t)i * kMaxL + k) * 30, 8 * 30);
   return LBM_OK;
@@ -607,17 +630,17 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
 }  // namespace
 
 int lbm_subvolume_balance(lbm_handle *h, int member, const int *L, int nL, const int *origins,
-                          int n_origins, double *stats_out, double *per_box_out) {
+                          const int *counts, double *stats_out, double *per_box_out) {
   if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
-  return balance_members(h, &member, 1, L, nL, origins, n_origins, stats_out, per_box_out);
+  return balance_members(h, &member, 1, L, nL, origins, counts, stats_out, per_box_out);
 }
 
 int lbm_subvolume_balance_batch(lbm_handle *h, const int *members, int n_members, const int *L,
-                                int nL, const int *origins, int n_origins, double *stats_out) {
+                                int nL, const int *origins, const int *counts,
+                                double *stats_out) {
   if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
   if (!members) return fail(h, LBM_ERR_ARG, "members is NULL");
-  return balance_members(h, members, n_members, L, nL, origins, n_origins, stats_out,
-                         nullptr);
+  return balance_members(h, members, n_members, L, nL, origins, counts, stats_out, nullptr);
 }
 
 extern "C" {

@@ -1,13 +1,30 @@
 // Sub-volume energy/enstrophy balance diagnostic of Tauzin et al. (2018):
 // the local terms of eqs. (8)-(11) in 2D with the eq. (18) 8th-order
 // centred differences and the eq. (17) BDF2 time derivative, their L x L box
-// averages through FP64 summed-area tables (O(1) per box and size), the
-// balancing errors of eqs. (12), (13) and their statistics per box size.
+// averages through summed-area tables (O(1) per box and size), the balancing
+// errors of eqs. (12), (13) and their statistics per box size.
 //
-// Inputs are moment snapshots (rho, j_x, j_y) in FP64, layout [3][ny*nx].
-// All diagnostic arithmetic is FP64.  Scratch layout: fields of N = nx*ny
-// doubles at sc.f + k*N (k < kDiagFields), reduction partials at
-// sc.partials.
+// Precision.  Inputs are FP64 moment snapshots (rho, j_x, j_y), layout
+// [3][ny*nx].  The term fields are computed in T = double (FP64 handles, or
+// on request) or T = float (FP32 handles): GB300 executes FP64 at a small
+// fraction of its FP32 rate, and the FP32 variant keeps its accuracy by
+// forming every cancelling quantity from FP64 differences first -- the time
+// differences u^n - u^{n-1} (so E and Omega differences, hence the eq. (17)
+// derivatives, carry relative FP32 error of the difference, not of E), and
+// the pressure gradient from rho - rho_ref.  Both variants use the same
+// formulas.
+// The summed-area tables are exact 64-bit fixed point: each field is scaled
+// by a power of two 2^e chosen from its largest magnitude so that any
+// partial sum stays below 2^62, rounded to integers once, and summed in
+// integer arithmetic; a box sum is then exact (the only error is the one
+// rounding of each cell, 2^-e, at most 2^-36 of the field's largest value on
+// a 8192^2 grid).  Box means, balancing errors and statistics are formed in
+// MT = double or float, again by handle precision; every block partial and
+// final statistic is FP64 and block-deterministic.
+//
+// Scratch (doubles of N = nx*ny cells): slots 0..2 a temporary snapshot,
+// slots 3.. the term-stage fields (each slot holds N values of T), then 12
+// slots of int64 tables; reduction partials at sc.partials.
 #include <cmath>
 #include <vector>
 
@@ -18,45 +35,47 @@ namespace lbm {
 namespace {
 
 enum Field {
-  S_RHO = 0, S_JX, S_JY,      // temporary snapshot (moments / global)
-  U0X, U0Y, U1X, U1Y, U2X, U2Y,
-  R0, FXR, FYR, PP, A1, A2, WW, B1, B2, C1, C2, G1, G2, G3, K1, K2,
-  T0,                         // T0..T11: term fields 0..11 (term 12 is 0)
-  NFIELDS = T0 + 12
+  U0X = 0, U0Y, DU01X, DU01Y, DU12X, DU12Y, DRHO, R0, FXR, FYR, A1, A2, WW, B1, B2, C1, C2,
+  G1, G2, G3, K1, K2,
+  T0,  // T0..T11: term fields 0..11 (term 12, vortex stretching, is 0 in 2D)
+  NF = T0 + 12
 };
-static_assert(NFIELDS <= kDiagFields, "scratch too small");
+constexpr int kSnapSlots = 3;
+static_assert(kSnapSlots + NF + 12 <= kDiagFields, "scratch too small");
 
 struct Grid {
   int nx, ny;
-  double nu, alpha;
+  double nu, alpha, rho_ref;
   const double *fxt, *fyt;  // F_ext,x(y), F_ext,y(x)
 };
 
-__device__ __forceinline__ int wrapn(int i, int n) {
-  return i < 0 ? i + n : (i >= n ? i - n : i);
+template <typename T>
+__host__ __device__ inline T *fld(double *base, int k, size_t N) {
+  return reinterpret_cast<T *>(base + (size_t)(kSnapSlots + k) * N);
+}
+__host__ __device__ inline long long *sat_base(double *base, size_t N) {
+  return reinterpret_cast<long long *>(base + (size_t)(kSnapSlots + NF) * N);
 }
 
-// Eq. (18) in x and y (dx = 1), periodic; paired form of the same stencil:
+__device__ __forceinline__ int wr(int i, int n) {
+  if (n >= 4) return i < 0 ? i + n : (i >= n ? i - n : i);
+  return wrapi(i, n);
+}
+
+// Eq. (18) in x and y (dx = 1), periodic, in the paired form
 // 4/5 (A+1 - A-1) - 1/5 (A+2 - A-2) + 4/105 (A+3 - A-3) - 1/280 (A+4 - A-4).
-__device__ __forceinline__ double ddx(const double *A, const Grid &g, int x, int y) {
-  const double *r = A + (size_t)y * g.nx;
-  double a[9];
-#pragma unroll
-  for (int d = -4; d <= 4; ++d) a[d + 4] = r[g.nx >= 4 ? wrapn(x + d, g.nx) : wrapi(x + d, g.nx)];
-  return 0.8 * (a[5] - a[3]) - 0.2 * (a[6] - a[2]) + (4.0 / 105.0) * (a[7] - a[1]) -
-         (1.0 / 280.0) * (a[8] - a[0]);
+template <typename T>
+__device__ __forceinline__ T Dx(const T *A, const Grid &g, int x, int y) {
+  const T *r = A + (size_t)y * g.nx;
+  auto a = [&](int d) { return r[wr(x + d, g.nx)]; };
+  return T(0.8) * (a(1) - a(-1)) - T(0.2) * (a(2) - a(-2)) +
+         T(4.0 / 105.0) * (a(3) - a(-3)) - T(1.0 / 280.0) * (a(4) - a(-4));
 }
-__device__ __forceinline__ double ddy(const double *A, const Grid &g, int x, int y) {
-  double a[9];
-#pragma unroll
-  for (int d = -4; d <= 4; ++d)
-    a[d + 4] = A[(size_t)(g.ny >= 4 ? wrapn(y + d, g.ny) : wrapi(y + d, g.ny)) * g.nx + x];
-  return 0.8 * (a[5] - a[3]) - 0.2 * (a[6] - a[2]) + (4.0 / 105.0) * (a[7] - a[1]) -
-         (1.0 / 280.0) * (a[8] - a[0]);
-}
-
-__device__ __forceinline__ double bdf2(double a0, double a1, double a2) {
-  return (3.0 * a0 - 4.0 * a1 + a2) * 0.5;  // eq. (17), dt = 1
+template <typename T>
+__device__ __forceinline__ T Dy(const T *A, const Grid &g, int x, int y) {
+  auto a = [&](int d) { return A[(size_t)wr(y + d, g.ny) * g.nx + x]; };
+  return T(0.8) * (a(1) - a(-1)) - T(0.2) * (a(2) - a(-2)) +
+         T(4.0 / 105.0) * (a(3) - a(-3)) - T(1.0 / 280.0) * (a(4) - a(-4));
 }
 
 #define CELL_INDEX                                        \
@@ -65,119 +84,119 @@ __device__ __forceinline__ double bdf2(double a0, double a1, double a2) {
   if (x >= g.nx || y >= g.ny) return;                     \
   const size_t c = (size_t)y * g.nx + x;
 
-// Velocity u = (j + F/2)/rho with F = F_ext - alpha j.
-__device__ __forceinline__ void phys_velocity(const Grid &g, int x, int y, double r, double jx,
-                                              double jy, double &ux, double &uy, double &Fx,
-                                              double &Fy) {
-  Fx = g.fxt[y] - g.alpha * jx;
-  Fy = g.fyt[x] - g.alpha * jy;
-  ux = (jx + 0.5 * Fx) / r;
-  uy = (jy + 0.5 * Fy) / r;
-}
-
-// Pass 0 (pointwise): velocities at n, n-1, n-2; LHS^E, RHS^{E,3}; fluxes
-// of E; F / rho; p.
+// Pass 0 (pointwise).  u = (j + F/2)/rho with F = F_ext - alpha j, i.e.
+// rho u = m = (1 - alpha/2) j + F_ext/2.  Differences between levels:
+// m^0 - m^1 = (1 - alpha/2)(j^0 - j^1), and
+// u^0 - u^1 = (dm - u^0 drho) / rho^1  (exact identity).
+// E^0 - E^1 = [drho |u^0|^2 + rho^1 du . (2 u^0 - du)] / 2, and
+// LHS^E = (3 (E^0 - E^1) - (E^1 - E^2)) / 2 = eq. (17).
+template <typename T>
 __global__ void k_prep(Grid g, const double *s0, const double *s1, const double *s2,
-                       double *F, size_t N) {
+                       double *base, size_t N) {
   CELL_INDEX;
-  const double *sn[3] = {s0, s1, s2};
-  double E[3], u0 = 0, v0 = 0, Fx0 = 0, Fy0 = 0;
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    const double r = sn[m][c], jx = sn[m][N + c], jy = sn[m][2 * N + c];
-    double u, v, Fx, Fy;
-    phys_velocity(g, x, y, r, jx, jy, u, v, Fx, Fy);
-    F[(U0X + 2 * m) * N + c] = u;
-    F[(U0Y + 2 * m) * N + c] = v;
-    E[m] = 0.5 * r * (u * u + v * v);
-    if (m == 0) { u0 = u; v0 = v; Fx0 = Fx; Fy0 = Fy; }
-  }
-  const double r = s0[c];
-  F[R0 * N + c] = r;
-  F[FXR * N + c] = Fx0 / r;
-  F[FYR * N + c] = Fy0 / r;
-  F[PP * N + c] = r / 3.0;  // p = cs^2 rho
-  F[A1 * N + c] = E[0] * u0;
-  F[A2 * N + c] = E[0] * v0;
-  F[(T0 + 0) * N + c] = bdf2(E[0], E[1], E[2]);  // LHS^E
-  F[(T0 + 3) * N + c] = u0 * Fx0 + v0 * Fy0;     // RHS^{E,3} = u.F
+  const double r0d = s0[c], r1d = s1[c], r2d = s2[c];
+  const double jx0d = s0[N + c], jy0d = s0[2 * N + c];
+  const T dr01 = (T)(r0d - r1d), dr12 = (T)(r1d - r2d);
+  const T djx01 = (T)(jx0d - s1[N + c]), djy01 = (T)(jy0d - s1[2 * N + c]);
+  const T djx12 = (T)(s1[N + c] - s2[N + c]), djy12 = (T)(s1[2 * N + c] - s2[2 * N + c]);
+  const T r0 = (T)r0d, r1 = (T)r1d, r2 = (T)r2d;
+  const T jx0 = (T)jx0d, jy0 = (T)jy0d;
+  const T a = (T)g.alpha, ca = T(1) - T(0.5) * a;
+  const T Fx = (T)g.fxt[y] - a * jx0, Fy = (T)g.fyt[x] - a * jy0;
+  const T u0 = (jx0 + T(0.5) * Fx) / r0, v0 = (jy0 + T(0.5) * Fy) / r0;
+  const T du01 = (ca * djx01 - u0 * dr01) / r1, dv01 = (ca * djy01 - v0 * dr01) / r1;
+  const T u1 = u0 - du01, v1 = v0 - dv01;
+  const T du12 = (ca * djx12 - u1 * dr12) / r2, dv12 = (ca * djy12 - v1 * dr12) / r2;
+  const T q0 = u0 * u0 + v0 * v0, q1 = u1 * u1 + v1 * v1;
+  const T dE01 = T(0.5) * (dr01 * q0 + r1 * (du01 * (T(2) * u0 - du01) + dv01 * (T(2) * v0 - dv01)));
+  const T dE12 = T(0.5) * (dr12 * q1 + r2 * (du12 * (T(2) * u1 - du12) + dv12 * (T(2) * v1 - dv12)));
+  const T E0 = T(0.5) * r0 * q0;
+  fld<T>(base, U0X, N)[c] = u0;
+  fld<T>(base, U0Y, N)[c] = v0;
+  fld<T>(base, DU01X, N)[c] = du01;
+  fld<T>(base, DU01Y, N)[c] = dv01;
+  fld<T>(base, DU12X, N)[c] = du12;
+  fld<T>(base, DU12Y, N)[c] = dv12;
+  fld<T>(base, DRHO, N)[c] = (T)(r0d - g.rho_ref);
+  fld<T>(base, R0, N)[c] = r0;
+  fld<T>(base, FXR, N)[c] = Fx / r0;
+  fld<T>(base, FYR, N)[c] = Fy / r0;
+  fld<T>(base, A1, N)[c] = E0 * u0;
+  fld<T>(base, A2, N)[c] = E0 * v0;
+  fld<T>(base, T0 + 0, N)[c] = T(0.5) * (T(3) * dE01 - dE12);  // LHS^E
+  fld<T>(base, T0 + 3, N)[c] = u0 * Fx + v0 * Fy;                // RHS^{E,3} = u . F
 }
 
-// Pass 1 (radius 4): vorticity at three levels, LHS^Omega, velocity
-// gradients, RHS^{E,2}, RHS^{E,4}, RHS^{O,2}, RHS^{O,3}; fluxes for pass 2.
-__global__ void k_grad(Grid g, double *F, size_t N) {
+// Pass 1 (radius 4): vorticity w = D_x u_y - D_y u_x and its level
+// differences, LHS^Omega = (3 (O^0 - O^1) - (O^1 - O^2))/2 with
+// O^0 - O^1 = dw (2 w^0 - dw)/2; velocity gradients; RHS^{E,2}
+// (grad p = grad(rho - rho_ref)/3), RHS^{E,4}, RHS^{O,2}, RHS^{O,3};
+// fluxes for pass 2.
+template <typename T>
+__global__ void k_grad(Grid g, double *base, size_t N) {
   CELL_INDEX;
-  double w[3];
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-    w[m] = ddx(F + (U0Y + 2 * m) * N, g, x, y) - ddy(F + (U0X + 2 * m) * N, g, x, y);
-  const double Om = 0.5 * w[0] * w[0];
-  F[(T0 + 6) * N + c] = bdf2(Om, 0.5 * w[1] * w[1], 0.5 * w[2] * w[2]);  // LHS^O
-  const double *U = F + U0X * N, *V = F + U0Y * N;
-  const double dxu = ddx(U, g, x, y), dyu = ddy(U, g, x, y);
-  const double dxv = ddx(V, g, x, y), dyv = ddy(V, g, x, y);
-  const double u = U[c], v = V[c], r = F[R0 * N + c];
-  const double sxx = 2.0 * dxu, sxy = dyu + dxv, syy = 2.0 * dyv;  // S_ij = d_j u_i + d_i u_j
-  const double nr = g.nu * r;
-  F[(T0 + 2) * N + c] = -(u * ddx(F + PP * N, g, x, y) + v * ddy(F + PP * N, g, x, y));
-  F[(T0 + 4) * N + c] = -nr * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
-  F[(T0 + 8) * N + c] = -Om * (dxu + dyv);
-  F[(T0 + 9) * N + c] = w[0] * (ddx(F + FYR * N, g, x, y) - ddy(F + FXR * N, g, x, y));
-  F[WW * N + c] = w[0];
-  F[B1 * N + c] = Om * u;
-  F[B2 * N + c] = Om * v;
-  F[C1 * N + c] = nr * (u * sxx + v * sxy);
-  F[C2 * N + c] = nr * (u * sxy + v * syy);
-  F[G1 * N + c] = nr * sxx;
-  F[G2 * N + c] = nr * sxy;
-  F[G3 * N + c] = nr * syy;
+  const T *U = fld<T>(base, U0X, N), *V = fld<T>(base, U0Y, N);
+  const T w0 = Dx(V, g, x, y) - Dy(U, g, x, y);
+  const T dw01 = Dx(fld<T>(base, DU01Y, N), g, x, y) - Dy(fld<T>(base, DU01X, N), g, x, y);
+  const T dw12 = Dx(fld<T>(base, DU12Y, N), g, x, y) - Dy(fld<T>(base, DU12X, N), g, x, y);
+  const T w1 = w0 - dw01;
+  const T dO01 = T(0.5) * dw01 * (T(2) * w0 - dw01);
+  const T dO12 = T(0.5) * dw12 * (T(2) * w1 - dw12);
+  fld<T>(base, T0 + 6, N)[c] = T(0.5) * (T(3) * dO01 - dO12);  // LHS^Omega
+  const T Om = T(0.5) * w0 * w0;
+  const T dxu = Dx(U, g, x, y), dyu = Dy(U, g, x, y);
+  const T dxv = Dx(V, g, x, y), dyv = Dy(V, g, x, y);
+  const T u = U[c], v = V[c], r = fld<T>(base, R0, N)[c];
+  const T sxx = T(2) * dxu, sxy = dyu + dxv, syy = T(2) * dyv;  // S_ij = d_j u_i + d_i u_j
+  const T nr = (T)g.nu * r;
+  const T *DR = fld<T>(base, DRHO, N);
+  fld<T>(base, T0 + 2, N)[c] = -(u * Dx(DR, g, x, y) + v * Dy(DR, g, x, y)) / T(3);
+  fld<T>(base, T0 + 4, N)[c] = -nr * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
+  fld<T>(base, T0 + 8, N)[c] = -Om * (dxu + dyv);
+  fld<T>(base, T0 + 9, N)[c] =
+      w0 * (Dx(fld<T>(base, FYR, N), g, x, y) - Dy(fld<T>(base, FXR, N), g, x, y));
+  fld<T>(base, WW, N)[c] = w0;
+  fld<T>(base, B1, N)[c] = Om * u;
+  fld<T>(base, B2, N)[c] = Om * v;
+  fld<T>(base, C1, N)[c] = nr * (u * sxx + v * sxy);
+  fld<T>(base, C2, N)[c] = nr * (u * sxy + v * syy);
+  fld<T>(base, G1, N)[c] = nr * sxx;
+  fld<T>(base, G2, N)[c] = nr * sxy;
+  fld<T>(base, G3, N)[c] = nr * syy;
 }
 
-// Pass 2 (radius 4): flux divergences RHS^{E,1}, RHS^{E,5}, RHS^{O,1}; H_i;
-// RHS^{O,4}; products w H for pass 3.
-__global__ void k_flux(Grid g, double *F, size_t N) {
+// Pass 2 (radius 4): RHS^{E,1}, RHS^{E,5}, RHS^{O,1}; H_i = d_j(nu rho S_ij)/rho;
+// RHS^{O,4} = H_x d_y w - H_y d_x w; products w H for pass 3.
+template <typename T>
+__global__ void k_flux(Grid g, double *base, size_t N) {
   CELL_INDEX;
-  const double r = F[R0 * N + c];
-  F[(T0 + 1) * N + c] = -(ddx(F + A1 * N, g, x, y) + ddy(F + A2 * N, g, x, y));
-  F[(T0 + 5) * N + c] = ddx(F + C1 * N, g, x, y) + ddy(F + C2 * N, g, x, y);
-  F[(T0 + 7) * N + c] = -(ddx(F + B1 * N, g, x, y) + ddy(F + B2 * N, g, x, y));
-  const double Hx = (ddx(F + G1 * N, g, x, y) + ddy(F + G2 * N, g, x, y)) / r;
-  const double Hy = (ddx(F + G2 * N, g, x, y) + ddy(F + G3 * N, g, x, y)) / r;
-  const double *W = F + WW * N;
-  F[(T0 + 10) * N + c] = Hx * ddy(W, g, x, y) - Hy * ddx(W, g, x, y);
-  const double w = W[c];
-  F[K1 * N + c] = w * Hy;
-  F[K2 * N + c] = w * Hx;
+  const T r = fld<T>(base, R0, N)[c];
+  fld<T>(base, T0 + 1, N)[c] =
+      -(Dx(fld<T>(base, A1, N), g, x, y) + Dy(fld<T>(base, A2, N), g, x, y));
+  fld<T>(base, T0 + 5, N)[c] = Dx(fld<T>(base, C1, N), g, x, y) + Dy(fld<T>(base, C2, N), g, x, y);
+  fld<T>(base, T0 + 7, N)[c] =
+      -(Dx(fld<T>(base, B1, N), g, x, y) + Dy(fld<T>(base, B2, N), g, x, y));
+  const T Hx = (Dx(fld<T>(base, G1, N), g, x, y) + Dy(fld<T>(base, G2, N), g, x, y)) / r;
+  const T Hy = (Dx(fld<T>(base, G2, N), g, x, y) + Dy(fld<T>(base, G3, N), g, x, y)) / r;
+  const T *W = fld<T>(base, WW, N);
+  fld<T>(base, T0 + 10, N)[c] = Hx * Dy(W, g, x, y) - Hy * Dx(W, g, x, y);
+  const T w = W[c];
+  fld<T>(base, K1, N)[c] = w * Hy;
+  fld<T>(base, K2, N)[c] = w * Hx;
 }
 
 // Pass 3 (radius 4): RHS^{O,5} = d_x (w H_y) - d_y (w H_x).
-__global__ void k_curl(Grid g, double *F, size_t N) {
+template <typename T>
+__global__ void k_curl(Grid g, double *base, size_t N) {
   CELL_INDEX;
-  F[(T0 + 11) * N + c] = ddx(F + K1 * N, g, x, y) - ddy(F + K2 * N, g, x, y);
+  fld<T>(base, T0 + 11, N)[c] =
+      Dx(fld<T>(base, K1, N), g, x, y) - Dy(fld<T>(base, K2, N), g, x, y);
 }
 
 // ---------------------------------------------------------------------------
-// Moments and whole-grid quantities
+// Block-deterministic reductions
 // ---------------------------------------------------------------------------
 
-__global__ void k_moments(Grid g, const double *snap, size_t N, double *rho, double *ux,
-                          double *uy) {
-  CELL_INDEX;
-  const double r = snap[c];
-  double u, v, Fx, Fy;
-  phys_velocity(g, x, y, r, snap[N + c], snap[2 * N + c], u, v, Fx, Fy);
-  if (rho) rho[c] = r;
-  ux[c] = u;
-  uy[c] = v;
-}
-
-__global__ void k_vorticity(Grid g, const double *ux, const double *uy, double *omega) {
-  CELL_INDEX;
-  omega[c] = ddx(uy, g, x, y) - ddy(ux, g, x, y);
-}
-
-// Block-deterministic sums: each block writes its partial for every
-// quantity; a single-block pass adds the partials in index order.
 template <int NQ>
 __device__ void block_sum_store(double (&v)[NQ], double *out /*[NQ]*/) {
   __shared__ double sh[NQ][32];
@@ -198,9 +217,44 @@ __device__ void block_sum_store(double (&v)[NQ], double *out /*[NQ]*/) {
   }
 }
 
+// Sums nb partial rows of width nq (fixed order per thread: 8 threads per
+// quantity take interleaved rows, then a fixed-order combination).
+__global__ void k_sum_partials(const double *partials, int nb, int nq, double *out) {
+  const int q = threadIdx.x >> 3, j = threadIdx.x & 7;
+  __shared__ double sh[32][8];
+  double a = 0.0;
+  if (q < nq)
+    for (int b = j; b < nb; b += 8) a += partials[(size_t)b * nq + q];
+  if (q < 32) sh[q][j] = a;
+  __syncthreads();
+  if (j == 0 && q < nq) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += sh[q][k];
+    out[q] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Moments and whole-grid quantities (FP64)
+// ---------------------------------------------------------------------------
+
+__global__ void k_moments(Grid g, const double *snap, size_t N, double *rho, double *ux,
+                          double *uy) {
+  CELL_INDEX;
+  const double r = snap[c], jx = snap[N + c], jy = snap[2 * N + c];
+  const double Fx = g.fxt[y] - g.alpha * jx, Fy = g.fyt[x] - g.alpha * jy;
+  if (rho) rho[c] = r;
+  ux[c] = (jx + 0.5 * Fx) / r;
+  uy[c] = (jy + 0.5 * Fy) / r;
+}
+
+__global__ void k_vorticity(Grid g, const double *ux, const double *uy, double *omega) {
+  CELL_INDEX;
+  omega[c] = Dx(uy, g, x, y) - Dy(ux, g, x, y);
+}
+
 __global__ void k_global(Grid g, const double *snap, const double *ux, const double *uy,
                          size_t N, double *partials) {
-  // grid-stride over cells, fixed order per block
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nthr = blockDim.x * blockDim.y;
@@ -209,8 +263,8 @@ __global__ void k_global(Grid g, const double *snap, const double *ux, const dou
     const double r = snap[c], jx = snap[N + c], jy = snap[2 * N + c];
     const double Fx = g.fxt[y] - g.alpha * jx, Fy = g.fyt[x] - g.alpha * jy;
     const double u = ux[c], v = uy[c];
-    const double dxu = ddx(ux, g, x, y), dyu = ddy(ux, g, x, y);
-    const double dxv = ddx(uy, g, x, y), dyv = ddy(uy, g, x, y);
+    const double dxu = Dx(ux, g, x, y), dyu = Dy(ux, g, x, y);
+    const double dxv = Dx(uy, g, x, y), dyv = Dy(uy, g, x, y);
     const double w = dxv - dyu;
     const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
     acc[0] += r;
@@ -224,63 +278,118 @@ __global__ void k_global(Grid g, const double *snap, const double *ux, const dou
   block_sum_store<7>(acc, partials + (size_t)blockIdx.x * 7);
 }
 
-__global__ void k_global_final(const double *partials, int nblocks, size_t N, double *out) {
+__global__ void k_global_scale(double *sums, size_t N) {
   const int q = threadIdx.x;
-  if (q >= 7) return;
-  double a = 0.0;
-  for (int b = 0; b < nblocks; ++b) a += partials[(size_t)b * 7 + q];
-  out[q] = q < 3 ? a : a / (double)N;
+  if (q >= 3 && q < 7) sums[q] /= (double)N;
 }
 
 // ---------------------------------------------------------------------------
-// Summed-area tables
+// Exact fixed-point summed-area tables
 // ---------------------------------------------------------------------------
 
-// Per-field sums (for the mean subtracted before the scan).
-__global__ void k_field_sums(const double *T, size_t N, double *partials) {
+// Largest magnitude of each term field: block partial maxima (order-free).
+template <typename T>
+__global__ void k_absmax(double *base, size_t N, double *partials) {
   const int f = blockIdx.y;
-  const double *A = T + (size_t)f * N;
-  double a[1] = {0.0};
+  const T *A = fld<T>(base, T0 + f, N);
+  T m = T(0);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (size_t)gridDim.x * blockDim.x)
-    a[0] += A[i];
-  block_sum_store<1>(a, partials + (size_t)f * gridDim.x + blockIdx.x);
+    m = fmax(m, fabs(A[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ T sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, sh[k]);
+    partials[(size_t)f * gridDim.x + blockIdx.x] = (double)m;
+  }
 }
 
-__global__ void k_field_means(const double *partials, int nblocks, size_t N, double *means,
-                              int nf) {
-  const int f = threadIdx.x;
-  if (f >= nf) return;
-  double a = 0.0;
-  for (int b = 0; b < nblocks; ++b) a += partials[(size_t)f * nblocks + b];
-  means[f] = a / (double)N;
+// Scale exponents, one warp per field: e_f with N * max|T_f| * 2^e_f < 2^62
+// (so every partial sum of the table fits in int64), capped so that 2^e_f is
+// a finite float.  scales[f] = 2^e_f, scales[12 + f] = 2^-e_f, and the
+// exponent itself as ((int *)(scales + 24))[f].
+__global__ void k_scales(const double *partials, int nb, size_t N, double *scales) {
+  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (f >= 12) return;
+  double m = 0.0;
+  for (int b = lane; b < nb; b += 32) m = fmax(m, partials[(size_t)f * nb + b]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    int e = 0;
+    if (m > 0.0) {
+      int ex, nbits = 0;
+      frexp(m, &ex);  // m < 2^ex
+      while (((size_t)1 << nbits) < N) ++nbits;
+      e = 62 - nbits - ex;
+      if (e > 120) e = 120;
+    }
+    scales[f] = ldexp(1.0, e);
+    scales[12 + f] = ldexp(1.0, -e);
+    reinterpret_cast<int *>(scales + 24)[f] = e;
+  }
 }
 
-// Inclusive scan along x of (T - mean), one CTA (256 threads) per (row, field).
-__global__ void __launch_bounds__(256) k_sat_rows(double *T, int nx, int ny,
-                                                  const double *means) {
+// round(v * 2^e) for a float v with |v| 2^e < 2^62, in integer arithmetic:
+// the float's 24-bit significand shifted by its exponent plus e (ties round
+// up).  Avoids the 64-bit float-to-integer conversion, which GB300 runs on
+// its slow FP64 path.
+__device__ __forceinline__ long long quantize(float v, int e) {
+  const unsigned bits = __float_as_uint(v);
+  const int ex = (int)((bits >> 23) & 0xffu);
+  long long mant = (long long)(bits & 0x7fffffu);
+  int shift;
+  if (ex == 0) {
+    shift = e - 149;  // subnormal: mant * 2^-149
+  } else {
+    mant |= 0x800000ll;
+    shift = ex - 150 + e;
+  }
+  long long q;
+  if (shift >= 0) {
+    q = mant << shift;
+  } else if (shift > -40) {
+    q = (mant + (1ll << (-shift - 1))) >> (-shift);
+  } else {
+    q = 0;
+  }
+  return (bits >> 31) ? -q : q;
+}
+__device__ __forceinline__ long long quantize(double v, int e) {
+  return __double2ll_rn(ldexp(v, e));
+}
+
+// Quantize and scan along x, one CTA (256 threads) per (row, field).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sat_rows(double *base, int nx, int ny,
+                                                  const double *scales) {
   const int y = blockIdx.x, f = blockIdx.y;
-  double *row = T + ((size_t)f * ny + y) * nx;
-  const double mean = means[f];
-  __shared__ double wsum[8];
-  __shared__ double carry_sh;
+  const size_t N = (size_t)nx * ny;
+  const T *row = fld<T>(base, T0 + f, N) + (size_t)y * nx;
+  long long *out = sat_base(base, N) + (size_t)f * N + (size_t)y * nx;
+  const int e = reinterpret_cast<const int *>(scales + 24)[f];
+  __shared__ long long wsum[8];
+  __shared__ long long carry_sh;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  double carry = 0.0;
-  for (int base = 0; base < nx; base += 256) {
-    const int x = base + tid;
-    double v = x < nx ? row[x] - mean : 0.0;
+  long long carry = 0;
+  for (int b0 = 0; b0 < nx; b0 += 256) {
+    const int x = b0 + tid;
+    long long v = x < nx ? quantize(row[x], e) : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const double n = __shfl_up_sync(0xffffffffu, v, o);
+      const long long n = __shfl_up_sync(0xffffffffu, v, o);
       if (lane >= o) v += n;
     }
     if (lane == 31) wsum[wid] = v;
     __syncthreads();
-    double off = carry;
+    long long off = carry;
     for (int k = 0; k < wid; ++k) off += wsum[k];
-    if (x < nx) row[x] = v + off;
+    if (x < nx) out[x] = v + off;
     if (tid == 255) {
-      double tot = carry;
+      long long tot = carry;
       for (int k = 0; k < 8; ++k) tot += wsum[k];
       carry_sh = tot;
     }
@@ -290,38 +399,28 @@ __global__ void __launch_bounds__(256) k_sat_rows(double *T, int nx, int ny,
   }
 }
 
-// Inclusive scan along y over a strip of 32 columns of one field: the 8
-// warps of the CTA each sum one chunk of rows, exchange the chunk totals
-// through shared memory, then rewrite their chunk as a running sum started
-// from the total of the chunks above.  Loads are coalesced across the strip.
-__global__ void __launch_bounds__(256) k_sat_cols(double *T, int nx, int ny) {
+// Scan along y over a strip of 32 columns: the 8 warps sum one chunk of rows
+// each, exchange chunk totals in shared memory, then rewrite their chunk.
+__global__ void __launch_bounds__(256) k_sat_cols(double *base, int nx, int ny) {
   const int f = blockIdx.y;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int w = threadIdx.y;
   const int chunk = (ny + 7) / 8;
   const int y0 = min(ny, w * chunk), y1 = min(ny, y0 + chunk);
-  double *col = T + (size_t)f * nx * ny + x;
-  __shared__ double tot[8][32];
-  double s = 0.0;
-  if (x < nx) {
-    int y = y0;
-    for (; y + 8 <= y1; y += 8) {
-      double v[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = col[(size_t)(y + k) * nx];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) s += v[k];
-    }
-    for (; y < y1; ++y) s += col[(size_t)y * nx];
-  }
+  const size_t N = (size_t)nx * ny;
+  long long *col = sat_base(base, N) + (size_t)f * N + x;
+  __shared__ long long tot[8][32];
+  long long s = 0;
+  if (x < nx)
+    for (int y = y0; y < y1; ++y) s += col[(size_t)y * nx];
   tot[w][threadIdx.x] = s;
   __syncthreads();
-  double acc = 0.0;
+  long long acc = 0;
   for (int k = 0; k < w; ++k) acc += tot[k][threadIdx.x];
   if (x < nx) {
     int y = y0;
     for (; y + 8 <= y1; y += 8) {
-      double v[8];
+      long long v[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) v[k] = col[(size_t)(y + k) * nx];
 #pragma unroll
@@ -337,124 +436,200 @@ __global__ void __launch_bounds__(256) k_sat_cols(double *T, int nx, int ny) {
   }
 }
 
-// Exclusive prefix P(x, y) = sum over x' < x, y' < y, from the inclusive
-// table S, for 0 <= x <= nx, 0 <= y <= ny.
-__device__ __forceinline__ double Pex(const double *S, int nx, int x, int y) {
-  return (x == 0 || y == 0) ? 0.0 : S[(size_t)(y - 1) * nx + (x - 1)];
+// Exclusive prefix P(x, y) = sum over x' < x, y' < y (0 <= x <= nx,
+// 0 <= y <= ny) from the inclusive table S; modular (unsigned) arithmetic:
+// the periodic extension may exceed int64 in between, the box sum does not.
+__device__ __forceinline__ unsigned long long Pex(const long long *S, int nx, int x, int y) {
+  return (x == 0 || y == 0) ? 0ull : (unsigned long long)S[(size_t)(y - 1) * nx + (x - 1)];
 }
-// Prefix over the periodic extension, 0 <= x < 2 nx, 0 <= y < 2 ny.
-__device__ __forceinline__ double Pext(const double *S, int nx, int ny, int x, int y) {
+__device__ __forceinline__ unsigned long long Pext(const long long *S, int nx, int ny, int x,
+                                                   int y) {
   const int qx = x >= nx, qy = y >= ny;
   const int xm = x - qx * nx, ym = y - qy * ny;
-  double v = Pex(S, nx, xm, ym);
+  unsigned long long v = Pex(S, nx, xm, ym);
   if (qx) v += Pex(S, nx, nx, ym);
   if (qy) v += Pex(S, nx, xm, ny);
   if (qx && qy) v += Pex(S, nx, nx, ny);
   return v;
 }
 
-// Balancing error of eqs. (12), (13) from the box LHS, the running sum of
-// the RHS terms and their largest magnitude.
-__device__ __forceinline__ double delta_of(double lhs, double sum, double mx) {
-  const double num = fabs(sum - lhs);
-  if (mx == 0.0) return num == 0.0 ? 0.0 : INFINITY;
+template <typename MT>
+__device__ __forceinline__ MT delta_of(MT lhs, MT sum, MT mx) {
+  const MT num = fabs(sum - lhs);
+  if (mx == MT(0)) return num == MT(0) ? MT(0) : MT(INFINITY);
   return num / mx;
 }
 
-constexpr int kQStats = 28;  // [dE, dE^2, dZ, dZ^2, (d_k, d_k^2) for the 12 fields]
+constexpr int kQStats = 14;  // per balance: [delta, delta^2, (d_k, d_k^2) for its 6 fields]
 
-// One thread per box: the 12 non-zero box averages (term 12, the 2D
-// vortex-stretching term, is identically 0), the two balancing errors, sums
-// of the deviations from the field means and of their squares for the
-// statistics, and optionally the per-box values.
-template <bool PER_BOX>
-__global__ void __launch_bounds__(256) k_query(const double *__restrict__ T, int nx, int ny,
-                                               const double *__restrict__ means,
-                                               const int *__restrict__ Ls, int nb,
+// Per (size, field) constants of the query, computed once: the field mean,
+// the factor from a quantized sum to a box mean, and the quantized sum a box
+// of the mean value would have (so box deviations are exact integers).
+struct QConst {
+  double mean_d, coef_d;
+  float mean_f, coef_f;
+  long long mq;
+  template <typename MT>
+  __device__ MT mean() const;
+  template <typename MT>
+  __device__ MT coef() const;
+};
+template <> __device__ double QConst::mean<double>() const { return mean_d; }
+template <> __device__ float QConst::mean<float>() const { return mean_f; }
+template <> __device__ double QConst::coef<double>() const { return coef_d; }
+template <> __device__ float QConst::coef<float>() const { return coef_f; }
+constexpr int kQConstDoubles = 32 * 12 * (int)(sizeof(QConst) / sizeof(double));
+
+__global__ void k_query_consts(const double *scales, const int *meta, int nL,
+                               const long long *S, size_t N, QConst *consts) {
+  const int t = threadIdx.x;
+  if (t >= nL * 12) return;
+  const int iL = t / 12, k = t % 12;
+  const double area = (double)meta[4 * iL] * (double)meta[4 * iL];
+  const long long total = S[(size_t)k * N + N - 1];
+  const double inv = scales[12 + k];
+  QConst q;
+  q.mean_d = (double)total * inv / (double)N;
+  q.coef_d = inv / area;
+  q.mean_f = (float)q.mean_d;
+  q.coef_f = (float)q.coef_d;
+  q.mq = __double2ll_rn((double)total * area / (double)N);
+  consts[t] = q;
+}
+
+// 64-bit integer to the query precision.  The float version splits the
+// integer into 32-bit halves: GB300 converts 64-bit integers on its slow
+// FP64 path, 32-bit ones at full rate.
+template <typename MT>
+__device__ __forceinline__ MT to_mt(long long v);
+template <>
+__device__ __forceinline__ double to_mt<double>(long long v) {
+  return (double)v;
+}
+template <>
+__device__ __forceinline__ float to_mt<float>(long long v) {
+  const int hi = (int)(v >> 32);
+  const unsigned lo = (unsigned)(v & 0xffffffffull);
+  return fmaf((float)hi, 4294967296.0f, (float)lo);
+}
+
+// Per size, meta[4*iL] = {L, n_boxes, origin offset (-1: all periodic
+// origins), per-box row offset}.  blockIdx.z selects the balance: 0 = energy
+// (fields 0..5: LHS^E, RHS^{E,1..5}), 1 = enstrophy (fields 6..11: LHS^O,
+// RHS^{O,1..5}; RHS^{O,6} is identically 0 in 2D and adds nothing).
+// One thread per (box, balance): exact integer box sums of its 6 term
+// fields, their deviations d_k from the field means, the box means, the
+// balancing error, and sums of d_k, d_k^2, delta and delta^2.
+template <typename MT, bool PER_BOX>
+__global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
+                                               const QConst *__restrict__ consts,
+                                               const int *__restrict__ meta,
                                                const int *__restrict__ origins,
                                                double *partials, double *per_box) {
-  const int iL = blockIdx.y;
-  const int L = Ls[iL];
+  const int iL = blockIdx.y, grp = blockIdx.z, k0 = 6 * grp;
+  const int L = meta[4 * iL], nb = meta[4 * iL + 1], ooff = meta[4 * iL + 2];
   const size_t N = (size_t)nx * ny;
-  const double invA = 1.0 / ((double)L * (double)L);
-  double mean[12], s1[12], s2[12];
+  const long long *S = sat_base(base, N) + (size_t)k0 * N;
+  const QConst *qc = consts + (size_t)iL * 12 + k0;
+  MT s1[6], s2[6];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    mean[k] = means[k];
-    s1[k] = 0.0;
-    s2[k] = 0.0;
+  for (int j = 0; j < 6; ++j) {
+    s1[j] = MT(0);
+    s2[j] = MT(0);
   }
-  double dE1 = 0.0, dE2 = 0.0, dZ1 = 0.0, dZ2 = 0.0;
+  MT d1 = 0, d2 = 0;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-    const int x0 = origins ? origins[2 * b] : b % nx;
-    const int y0 = origins ? origins[2 * b + 1] : b / nx;
-    double lhsE = 0.0, sumE = 0.0, maxE = 0.0, lhsZ = 0.0, sumZ = 0.0, maxZ = 0.0;
-    double *o = PER_BOX ? per_box + ((size_t)iL * nb + b) * 15 : nullptr;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const double *S = T + (size_t)k * N;
-      const double d = (Pext(S, nx, ny, x0 + L, y0 + L) - Pext(S, nx, ny, x0, y0 + L) -
-                        Pext(S, nx, ny, x0 + L, y0) + Pext(S, nx, ny, x0, y0)) * invA;
-      const double v = d + mean[k];
-      s1[k] += d;
-      s2[k] += d * d;
-      if (k == 0) {
-        lhsE = v;
-      } else if (k < 6) {
-        sumE += v;
-        maxE = fmax(maxE, fabs(v));
-      } else if (k == 6) {
-        lhsZ = v;
-      } else {
-        sumZ += v;
-        maxZ = fmax(maxZ, fabs(v));
-      }
-      if (PER_BOX) o[2 + k] = v;
+    int x0, y0;
+    if (ooff >= 0) {
+      x0 = origins[2 * (ooff + b)];
+      y0 = origins[2 * (ooff + b) + 1];
+    } else {
+      x0 = b % nx;
+      y0 = b / nx;
     }
-    const double dE = delta_of(lhsE, sumE, maxE), dZ = delta_of(lhsZ, sumZ, maxZ);
-    dE1 += dE;
-    dE2 += dE * dE;
-    dZ1 += dZ;
-    dZ2 += dZ * dZ;
+    MT lhs = 0, sum = 0, mx = 0;
+    double *o = PER_BOX ? per_box + ((size_t)meta[4 * iL + 3] + b) * 15 : nullptr;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const long long *Sk = S + (size_t)j * N;
+      const unsigned long long bs = Pext(Sk, nx, ny, x0 + L, y0 + L) -
+                                    Pext(Sk, nx, ny, x0, y0 + L) -
+                                    Pext(Sk, nx, ny, x0 + L, y0) + Pext(Sk, nx, ny, x0, y0);
+      const long long dq = (long long)(bs - (unsigned long long)qc[j].mq);
+      const MT d = to_mt<MT>(dq) * qc[j].coef<MT>();
+      const MT v = d + qc[j].mean<MT>();
+      s1[j] += d;
+      s2[j] += d * d;
+      if (j == 0) {
+        lhs = v;
+      } else {
+        sum += v;
+        mx = fmax(mx, fabs(v));
+      }
+      if (PER_BOX) o[2 + k0 + j] = (double)v;
+    }
+    const MT dl = delta_of(lhs, sum, mx);
+    d1 += dl;
+    d2 += dl * dl;
     if (PER_BOX) {
-      o[0] = dE;
-      o[1] = dZ;
-      o[14] = 0.0;
+      o[grp] = (double)dl;
+      if (grp == 1) o[14] = 0.0;
     }
   }
   double acc[kQStats];
-  acc[0] = dE1;
-  acc[1] = dE2;
-  acc[2] = dZ1;
-  acc[3] = dZ2;
+  acc[0] = d1;
+  acc[1] = d2;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    acc[4 + 2 * k] = s1[k];
-    acc[5 + 2 * k] = s2[k];
+  for (int j = 0; j < 6; ++j) {
+    acc[2 + 2 * j] = s1[j];
+    acc[3 + 2 * j] = s2[j];
   }
-  block_sum_store<kQStats>(acc, partials + ((size_t)iL * gridDim.x + blockIdx.x) * kQStats);
+  block_sum_store<kQStats>(
+      acc, partials + (((size_t)iL * 2 + grp) * gridDim.x + blockIdx.x) * kQStats);
 }
 
 // Mean and population standard deviation of the 15 quantities per size.
-__global__ void k_stats_final(const double *partials, int nblocks, const double *means,
-                              int nb, int nL, double *stats) {
-  const int iL = blockIdx.x, q = threadIdx.x;
-  if (q >= 15) return;
-  double mean = 0.0, sd = 0.0;
-  if (q < 14) {
-    const int i = q < 2 ? 2 * q : 4 + 2 * (q - 2);
-    double s1 = 0.0, s2 = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-      s1 += partials[((size_t)iL * nblocks + b) * kQStats + i];
-      s2 += partials[((size_t)iL * nblocks + b) * kQStats + i + 1];
-    }
-    const double m1 = s1 / nb;
-    const double shift = q >= 2 ? means[q - 2] : 0.0;
-    mean = shift + m1;
-    sd = sqrt(fmax(s2 / nb - m1 * m1, 0.0));
+// One CTA per size; 8 threads per (balance, slot) sum interleaved block
+// partials in a fixed order.
+__global__ void k_stats_final(const double *partials, int nblocks, const QConst *consts,
+                              const int *meta, double *stats) {
+  const int iL = blockIdx.x;
+  const int q = threadIdx.x >> 3, j = threadIdx.x & 7;  // q = grp * 14 + slot
+  __shared__ double sh[2 * kQStats][8];
+  double a = 0.0;
+  if (q < 2 * kQStats) {
+    const int grp = q / kQStats, slot = q % kQStats;
+    for (int b = j; b < nblocks; b += 8)
+      a += partials[(((size_t)iL * 2 + grp) * nblocks + b) * kQStats + slot];
+    sh[q][j] = a;
   }
-  stats[((size_t)iL * 15 + q) * 2] = mean;
-  stats[((size_t)iL * 15 + q) * 2 + 1] = sd;
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < 15) {
+    const int nb = meta[4 * iL + 1];
+    double mean = 0.0, sd = 0.0;
+    if (t < 14) {
+      int row;  // row of sh holding the (sum, sum of squares) pair
+      double shift = 0.0;
+      if (t < 2) {
+        row = t * kQStats;
+      } else {
+        const int k = t - 2, grp = k / 6;
+        row = grp * kQStats + 2 + 2 * (k % 6);
+        shift = consts[(size_t)iL * 12 + k].mean_d;
+      }
+      double s1 = 0.0, s2 = 0.0;
+      for (int m = 0; m < 8; ++m) {
+        s1 += sh[row][m];
+        s2 += sh[row + 1][m];
+      }
+      const double m1 = s1 / nb;
+      mean = shift + m1;
+      sd = sqrt(fmax(s2 / nb - m1 * m1, 0.0));
+    }
+    stats[((size_t)iL * 15 + t) * 2] = mean;
+    stats[((size_t)iL * 15 + t) * 2 + 1] = sd;
+  }
 }
 
 Grid grid_of(const Member &hm) {
@@ -463,6 +638,7 @@ Grid grid_of(const Member &hm) {
   g.ny = hm.ny;
   g.nu = hm.nu;
   g.alpha = hm.alpha;
+  g.rho_ref = hm.rho0;
   g.fxt = hm.fx_tab64;
   g.fyt = hm.fy_tab64;
   return g;
@@ -478,8 +654,8 @@ cudaError_t diag_moments(const Member &hm, const double *snap3, double *rho, dou
                          double *uy, double *omega, const DiagScratch &sc, cudaStream_t s) {
   const Grid g = grid_of(hm);
   const size_t N = (size_t)hm.nx * hm.ny;
-  double *U = ux ? ux : sc.f + (size_t)U0X * N;
-  double *V = uy ? uy : sc.f + (size_t)U0Y * N;
+  double *U = ux ? ux : sc.f + (size_t)kSnapSlots * N;
+  double *V = uy ? uy : sc.f + (size_t)(kSnapSlots + 1) * N;
   dim3 b(32, 8);
   k_moments<<<cells_grid(g, b), b, 0, s>>>(g, snap3, N, rho, U, V);
   if (omega) k_vorticity<<<cells_grid(g, b), b, 0, s>>>(g, U, V, omega);
@@ -490,66 +666,90 @@ cudaError_t diag_global(const Member &hm, const double *snap3, const DiagScratch
                         double *out7_dev, cudaStream_t s) {
   const Grid g = grid_of(hm);
   const size_t N = (size_t)hm.nx * hm.ny;
-  double *U = sc.f + (size_t)U0X * N, *V = sc.f + (size_t)U0Y * N;
+  double *U = sc.f + (size_t)kSnapSlots * N, *V = sc.f + (size_t)(kSnapSlots + 1) * N;
   dim3 b(32, 8);
   k_moments<<<cells_grid(g, b), b, 0, s>>>(g, snap3, N, nullptr, U, V);
   int nblocks = (int)((N + 255) / 256);
   if (nblocks > kMaxPartialBlocks) nblocks = kMaxPartialBlocks;
   k_global<<<nblocks, dim3(32, 8), 0, s>>>(g, snap3, U, V, N, sc.partials);
-  k_global_final<<<1, 32, 0, s>>>(sc.partials, nblocks, N, out7_dev);
+  k_sum_partials<<<1, 256, 0, s>>>(sc.partials, nblocks, 7, out7_dev);
+  k_global_scale<<<1, 32, 0, s>>>(out7_dev, N);
   return cudaGetLastError();
 }
 
-cudaError_t diag_terms(const Member &hm, const double *sn, const double *sn1,
+cudaError_t diag_terms(const Member &hm, int precision, const double *sn, const double *sn1,
                        const double *sn2, const DiagScratch &sc, cudaStream_t s) {
   const Grid g = grid_of(hm);
   const size_t N = (size_t)hm.nx * hm.ny;
   dim3 b(32, 8), gr = cells_grid(g, b);
-  k_prep<<<gr, b, 0, s>>>(g, sn, sn1, sn2, sc.f, N);
-  k_grad<<<gr, b, 0, s>>>(g, sc.f, N);
-  k_flux<<<gr, b, 0, s>>>(g, sc.f, N);
-  k_curl<<<gr, b, 0, s>>>(g, sc.f, N);
+  if (precision == 32) {
+    k_prep<float><<<gr, b, 0, s>>>(g, sn, sn1, sn2, sc.f, N);
+    k_grad<float><<<gr, b, 0, s>>>(g, sc.f, N);
+    k_flux<float><<<gr, b, 0, s>>>(g, sc.f, N);
+    k_curl<float><<<gr, b, 0, s>>>(g, sc.f, N);
+  } else {
+    k_prep<double><<<gr, b, 0, s>>>(g, sn, sn1, sn2, sc.f, N);
+    k_grad<double><<<gr, b, 0, s>>>(g, sc.f, N);
+    k_flux<double><<<gr, b, 0, s>>>(g, sc.f, N);
+    k_curl<double><<<gr, b, 0, s>>>(g, sc.f, N);
+  }
   return cudaGetLastError();
 }
 
-double *diag_term_fields(const DiagScratch &sc, size_t N) { return sc.f + (size_t)T0 * N; }
-
 size_t diag_partials_needed(int nL) {
-  return (size_t)12 * kMaxPartialBlocks + 16 + (size_t)nL * kMaxPartialBlocks * 30 +
-         (size_t)nL * 30;
+  return (size_t)12 * kMaxPartialBlocks + 32 + kQConstDoubles +
+         (size_t)nL * 2 * kMaxPartialBlocks * kQStats;
 }
 
-// SAT of the 12 term fields (in place) and the box queries for every L.
-// Ls_dev and origins_dev are device arrays; stats_dev receives [nL][15][2].
-cudaError_t diag_sat_and_query(const Member &hm, const int *Ls_dev, int nL,
-                               const int *origins_dev, int n_origins,
-                               const DiagScratch &sc, double *stats_dev,
-                               double *per_box_dev, cudaStream_t s) {
+// Fixed-point SAT of the 12 term fields and the box queries for every size.
+// meta_dev: [nL][4] {L, n_boxes, origin offset or -1, per-box row offset};
+// origins_dev: concatenated (x0, y0) pairs (may be NULL when every size uses
+// all periodic origins); stats_dev receives [nL][15][2].
+cudaError_t diag_sat_and_query(const Member &hm, int precision, const int *meta_dev, int nL,
+                               int max_boxes, const int *origins_dev, const DiagScratch &sc,
+                               double *stats_dev, double *per_box_dev, cudaStream_t s) {
   const int nx = hm.nx, ny = hm.ny;
   const size_t N = (size_t)nx * ny;
-  double *T = sc.f + (size_t)T0 * N;
-  double *part_means = sc.partials;                       // [12][kMaxPartialBlocks]
-  double *means = part_means + 12 * kMaxPartialBlocks;    // [12] (+4 pad)
-  double *part_q = means + 16;                            // [nL][blocks][30]
-  // about 16 elements per thread for the field sums
-  int nb_sum = (int)((N + 4095) / 4096);
-  if (nb_sum > kMaxPartialBlocks) nb_sum = kMaxPartialBlocks;
-  k_field_sums<<<dim3(nb_sum, 12), 256, 0, s>>>(T, N, part_means);
-  k_field_means<<<1, 32, 0, s>>>(part_means, nb_sum, N, means, 12);
-  k_sat_rows<<<dim3(ny, 12), 256, 0, s>>>(T, nx, ny, means);
-  k_sat_cols<<<dim3((nx + 31) / 32, 12), dim3(32, 8), 0, s>>>(T, nx, ny);
-  const int nbox = origins_dev ? n_origins : (int)N;
-  // about 4 boxes per thread, at most kMaxPartialBlocks CTAs per size
-  int qblocks = (nbox + 1023) / 1024;
+  double *part_max = sc.partials;                         // [12][blocks]
+  double *scales = part_max + 12 * kMaxPartialBlocks;     // [24] + 12 ints
+  QConst *consts = reinterpret_cast<QConst *>(scales + 32);  // [nL][12]
+  double *part_q = scales + 32 + kQConstDoubles;          // [nL][blocks][kQStats]
+  int nb_max = (int)((N + 4095) / 4096);
+  if (nb_max > kMaxPartialBlocks) nb_max = kMaxPartialBlocks;
+  if (precision == 32) {
+    k_absmax<float><<<dim3(nb_max, 12), 256, 0, s>>>(sc.f, N, part_max);
+    k_scales<<<1, 12 * 32, 0, s>>>(part_max, nb_max, N, scales);
+    k_sat_rows<float><<<dim3(ny, 12), 256, 0, s>>>(sc.f, nx, ny, scales);
+  } else {
+    k_absmax<double><<<dim3(nb_max, 12), 256, 0, s>>>(sc.f, N, part_max);
+    k_scales<<<1, 12 * 32, 0, s>>>(part_max, nb_max, N, scales);
+    k_sat_rows<double><<<dim3(ny, 12), 256, 0, s>>>(sc.f, nx, ny, scales);
+  }
+  k_sat_cols<<<dim3((nx + 31) / 32, 12), dim3(32, 8), 0, s>>>(sc.f, nx, ny);
+  k_query_consts<<<1, 32 * 12, 0, s>>>(scales, meta_dev, nL, sat_base(sc.f, N), N, consts);
+  // box lists: one box per thread; every periodic origin: about 4 per thread;
+  // at most kMaxPartialBlocks CTAs per size
+  const int per_cta = origins_dev ? 256 : 1024;
+  int qblocks = (max_boxes + per_cta - 1) / per_cta;
   if (qblocks > kMaxPartialBlocks) qblocks = kMaxPartialBlocks;
   if (qblocks < 1) qblocks = 1;
-  if (per_box_dev)
-    k_query<true><<<dim3(qblocks, nL), 256, 0, s>>>(T, nx, ny, means, Ls_dev, nbox,
-                                                    origins_dev, part_q, per_box_dev);
-  else
-    k_query<false><<<dim3(qblocks, nL), 256, 0, s>>>(T, nx, ny, means, Ls_dev, nbox,
-                                                     origins_dev, part_q, nullptr);
-  k_stats_final<<<nL, 32, 0, s>>>(part_q, qblocks, means, nbox, nL, stats_dev);
+  const dim3 qg(qblocks, nL, 2);
+  if (precision == 32) {
+    if (per_box_dev)
+      k_query<float, true><<<qg, 256, 0, s>>>(sc.f, nx, ny, consts, meta_dev, origins_dev,
+                                               part_q, per_box_dev);
+    else
+      k_query<float, false><<<qg, 256, 0, s>>>(sc.f, nx, ny, consts, meta_dev, origins_dev,
+                                                part_q, nullptr);
+  } else {
+    if (per_box_dev)
+      k_query<double, true><<<qg, 256, 0, s>>>(sc.f, nx, ny, consts, meta_dev, origins_dev,
+                                                part_q, per_box_dev);
+    else
+      k_query<double, false><<<qg, 256, 0, s>>>(sc.f, nx, ny, consts, meta_dev, origins_dev,
+                                                 part_q, nullptr);
+  }
+  k_stats_final<<<nL, 256, 0, s>>>(part_q, qblocks, consts, meta_dev, stats_dev);
   return cudaGetLastError();
 }
 

@@ -94,17 +94,20 @@ struct DiagScratch {
   double *partials; // reduction partials
   size_t npartials; // capacity in doubles
 };
-constexpr int kDiagFields = 40;
+constexpr int kDiagFields = 50;
 constexpr int kMaxPartialBlocks = 1024;
 
 cudaError_t diag_moments(const Member &hm, const double *snap3, double *rho, double *ux,
                          double *uy, double *omega, const DiagScratch &sc, cudaStream_t s);
 cudaError_t diag_global(const Member &hm, const double *snap3, const DiagScratch &sc,
                         double *out7_dev, cudaStream_t s);
-cudaError_t diag_terms(const Member &hm, const double *sn, const double *sn1,
+// precision: 32 (FP32 term arithmetic) or 64.
+cudaError_t diag_terms(const Member &hm, int precision, const double *sn, const double *sn1,
                        const double *sn2, const DiagScratch &sc, cudaStream_t s);
-cudaError_t diag_sat_and_query(const Member &hm, const int *Ls_dev, int nL,
-                               const int *origins_dev, int n_origins, const DiagScratch &sc,
+// meta_dev: [nL][4] {L, n_boxes, origin offset (-1: all periodic origins),
+// per-box row offset}; max_boxes: the largest n_boxes.
+cudaError_t diag_sat_and_query(const Member &hm, int precision, const int *meta_dev, int nL,
+                               int max_boxes, const int *origins_dev, const DiagScratch &sc,
                                double *stats_dev, double *per_box_dev, cudaStream_t s);
 size_t diag_partials_needed(int nL);
 

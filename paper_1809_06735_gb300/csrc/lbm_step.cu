@@ -274,6 +274,26 @@ __global__ void k_set_pop(const Member *__restrict__ members, int member, int cu
   }
 }
 
+// Error-free addition (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated FP32 sum of FP32 values, returned in FP64: the value of a
+// double-precision sum at FP32 arithmetic cost (GB300 runs FP64 at a small
+// fraction of its FP32 rate).
+__device__ __forceinline__ double csum(const float *v, const int *sign, int n) {
+  float s = sign[0] * v[0], c = 0.f;
+  for (int k = 1; k < n; ++k) {
+    float e;
+    two_sum(s, sign[k] * v[k], s, e);
+    c += e;
+  }
+  return (double)s + (double)c;
+}
+
 // (rho, j_x, j_y) of the pre-collision state, FP64, into d[3][ny*nx].
 template <typename T>
 __global__ void k_snapshot(const Member *__restrict__ members, int member, int cur, double *d) {
@@ -282,16 +302,35 @@ __global__ void k_snapshot(const Member *__restrict__ members, int member, int c
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= M.nx || y >= M.ny) return;
   const T *src = static_cast<const T *>(M.pop[cur]);
-  double r = 0.0, jx = 0.0, jy = 0.0;
+  T f[kQ];
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
-    const int xs = wrapi(x - cx_of(l), M.nx), ys = wrapi(y - cy_of(l), M.ny);
-    const double v = (double)src[(size_t)l * M.plane + (size_t)ys * M.pitch + xs];
-    r += v;
-    jx += cx_of(l) * v;
-    jy += cy_of(l) * v;
+    int xs = x - cx_of(l), ys = y - cy_of(l);  // one-cell shifts: a single wrap
+    xs = xs < 0 ? xs + M.nx : (xs >= M.nx ? xs - M.nx : xs);
+    ys = ys < 0 ? ys + M.ny : (ys >= M.ny ? ys - M.ny : ys);
+    f[l] = src[(size_t)l * M.plane + (size_t)ys * M.pitch + xs];
   }
-  if (sizeof(T) == 4) r += M.rho0;  // weights sum to 1; deviations carry no momentum
+  double r, jx, jy;
+  if constexpr (sizeof(T) == 4) {
+    // deviations: rho = rho0 + sum g (weights sum to 1), j = sum c g
+    const int one[kQ] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    const float ax[6] = {f[1], f[5], f[8], f[3], f[6], f[7]};
+    const float ay[6] = {f[2], f[5], f[6], f[4], f[7], f[8]};
+    const int sgn[6] = {1, 1, 1, -1, -1, -1};
+    r = M.rho0 + csum(f, one, kQ);
+    jx = csum(ax, sgn, 6);
+    jy = csum(ay, sgn, 6);
+  } else {
+    r = 0.0;
+    jx = 0.0;
+    jy = 0.0;
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      r += f[l];
+      jx += cx_of(l) * f[l];
+      jy += cy_of(l) * f[l];
+    }
+  }
   const size_t N = (size_t)M.nx * M.ny, c = (size_t)y * M.nx + x;
   d[c] = r;
   d[N + c] = jx;

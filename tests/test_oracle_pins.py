@@ -451,3 +451,22 @@ def test_global_budget_of_decaying_run(orc):
     g1 = orc.global_quantities(f1, tau)
     dEdt = (e2 - e0) / 2.0
     assert abs(dEdt - (-g1[6] + g1[5])) < 0.05 * abs(g1[6])
+
+
+def test_window_run_matches_full_run_inside_the_light_cone(orc):
+    """A window of a larger periodic grid, forced at its global coordinates,
+    reproduces the full run bit for bit on cells at least nsteps from its
+    edges (used to check sampled cells of grids too large for the oracle)."""
+    NX, NY, steps = 30, 26, 5
+    force = orc.Force(1, 3e-4, 3, 2e-3)
+    f0 = li.random_populations(NX, NY, seed=21)
+    full = orc.run(f0, steps, 0.58, force)
+    for (x0, y0, wx, wy) in [(3, 2, 16, 14), (25, 20, 12, 13), (0, 0, 11, 11)]:
+        xs = (x0 + np.arange(wx)) % NX
+        ys = (y0 + np.arange(wy)) % NY
+        win = f0[:, ys][:, :, xs]
+        got = orc.run_window(win, steps, 0.58, force, x0, y0, NX, NY)
+        inner = (slice(None), slice(steps, wy - steps), slice(steps, wx - steps))
+        want = full[:, ys][:, :, xs]
+        assert np.array_equal(got[inner], want[inner])
+        assert not np.array_equal(got, want)  # the edges are not valid
