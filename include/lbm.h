@@ -81,7 +81,13 @@ typedef struct lbm_config {
   int n_members;                 /* >= 1 */
   const lbm_member_cfg *members; /* host array of n_members (copied) */
   int precision;   /* 32: FP32 deviation populations; 64: plain FP64 */
-  int storage;     /* 0: default (double buffer); other values reserved */
+  int storage;     /* population storage: 1 = in place (AA pattern: one
+                      array, the even step swaps each cell's opposite
+                      populations, the odd step reads and writes the
+                      neighbours); 2 = double buffer (pull); 0 = chosen by
+                      the autotuner at create time together with the launch
+                      shape (FP32 ensembles above 1 M cells; otherwise
+                      double buffer).  Both move 72 B per FP32 update. */
   int diag_every;  /* > 0: lbm_step records the moment snapshots of the
                       time levels n = k*diag_every - 2, -1, 0 that the
                       eq. (17) time derivative needs; 0: only explicit
@@ -138,6 +144,13 @@ long long lbm_time(const lbm_handle *h);
  * replayed CUDA graph counts once).  Host-only. */
 long long lbm_launch_count(const lbm_handle *h);
 
+/* Launch configuration the handle uses (host-only; any pointer may be NULL):
+ * storage 1 (AA) or 2 (double buffer), warps per CTA and rows per warp of
+ * the batched FP32 kernel, persistent grid size (0: one CTA per tile), and
+ * the autotuned time of one step in ms (0 when not tuned). */
+int lbm_tuning(const lbm_handle *h, int *storage, int *warps, int *rows,
+               int *grid, float *step_ms);
+
 /* Records the moment snapshot (rho, j) of every member at the current time
  * into the 3-slot history used by the eq. (17) time derivative. */
 int lbm_record_snapshot(lbm_handle *h);
@@ -191,6 +204,24 @@ int lbm_subvolume_balance_batch(lbm_handle *h, const int *members,
                                 int n_members, const int *L, int nL,
                                 const int *origins, const int *counts,
                                 double *stats_out);
+
+/* Asynchronous form of lbm_subvolume_balance_batch: the diagnostic of the
+ * current time is queued on an internal stream after the work already queued
+ * on the handle's stream (its snapshots), and the call returns without
+ * waiting.  stats_dev (device, double[n_members][nL][15][2], NaN for skipped
+ * sizes) receives the statistics; it and the host arrays may be reused once
+ * lbm_diag_synchronize has returned (the host arrays right away).  Later
+ * calls that need the snapshot ring or the diagnostic scratch (the next
+ * snapshot record, moments, balances, adjoint, host transfers) are ordered
+ * after it on the device, so the stepping of the next diagnostic period runs
+ * concurrently with it. */
+int lbm_subvolume_balance_async(lbm_handle *h, const int *members,
+                                int n_members, const int *L, int nL,
+                                const int *origins, const int *counts,
+                                double *stats_dev);
+
+/* Blocks the host until the last asynchronous diagnostic has finished. */
+int lbm_diag_synchronize(lbm_handle *h);
 
 /* Public pre-collision populations f_l(x, n) of member `member` as
  * double[9][ny][nx] (full f, also for FP32 storage).  Host pointer if

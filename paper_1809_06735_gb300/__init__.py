@@ -71,11 +71,14 @@ def load_library(path: str = LIB_PATH):
         "lbm_step": ([P, I], I),
         "lbm_time": ([P], ctypes.c_longlong),
         "lbm_launch_count": ([P], ctypes.c_longlong),
+        "lbm_tuning": ([P, P, P, P, P, P], I),
         "lbm_record_snapshot": ([P], I),
         "lbm_moments": ([P, I, P, P, P, P], I),
         "lbm_global_balance": ([P, I, P], I),
         "lbm_subvolume_balance": ([P, I, P, I, P, P, P, P], I),
         "lbm_subvolume_balance_batch": ([P, P, I, P, I, P, P, P], I),
+        "lbm_subvolume_balance_async": ([P, P, I, P, I, P, P, P], I),
+        "lbm_diag_synchronize": ([P], I),
         "lbm_get_populations": ([P, I, P, I], I),
         "lbm_set_populations": ([P, I, P, I], I),
         "lbm_member_status": ([P, I, P], I),
@@ -130,7 +133,8 @@ class Lattice:
     (default: the current torch stream at construction)."""
 
     def __init__(self, members: Sequence[Member], precision: int = 32, diag_every: int = 0,
-                 graph_steps: int = 0, stream=None, device=None, diag_precision: int = 0):
+                 graph_steps: int = 0, stream=None, device=None, diag_precision: int = 0,
+                 storage: int = 0):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -140,7 +144,7 @@ class Lattice:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         arr = (_MemberCfg * len(self.members))(*[m.c() for m in self.members])
         self._arr = arr
-        self._cfg = _Config(len(self.members), arr, precision, 0, diag_every, graph_steps,
+        self._cfg = _Config(len(self.members), arr, precision, storage, diag_every, graph_steps,
                             diag_precision, ctypes.c_void_p(self.stream.cuda_stream))
         nbytes = ctypes.c_size_t()
         self._check(self.lib.lbm_workspace_size(ctypes.byref(self._cfg), ctypes.byref(nbytes)))
@@ -206,6 +210,16 @@ class Lattice:
     def launch_count(self) -> int:
         """Kernels issued by this handle so far (graph nodes counted)."""
         return int(self.lib.lbm_launch_count(self.h))
+
+    def tuning(self) -> dict:
+        """Launch configuration in use (storage 'aa' or 'double_buffer', CTA
+        shape, grid, autotuned ms per step)."""
+        st, w, r, g = (ctypes.c_int() for _ in range(4))
+        ms = ctypes.c_float()
+        self._check(self.lib.lbm_tuning(self.h, ctypes.byref(st), ctypes.byref(w), ctypes.byref(r),
+                                        ctypes.byref(g), ctypes.byref(ms)))
+        return {"storage": "aa" if st.value == 1 else "double_buffer", "warps_per_cta": w.value,
+                "rows_per_warp": r.value, "grid_ctas": g.value, "tuned_step_ms": ms.value}
 
     def record_snapshot(self):
         self._check(self.lib.lbm_record_snapshot(self.h))
@@ -299,6 +313,24 @@ class Lattice:
         self._check(self.lib.lbm_subvolume_balance_batch(
             self.h, _ptr(mem), len(mem), _ptr(Ls), len(Ls), _ptr(o), _ptr(counts), _ptr(stats)))
         return stats
+
+    def subvolume_balance_async(self, members, Ls, origins=None, out=None):
+        """Queue the diagnostic of the current time on the handle's diagnostic
+        stream and return at once; statistics land in the device tensor
+        ``out`` [n_members, nL, 15, 2] (allocated when None) once the work is
+        done (``diag_synchronize`` or any later ordered call)."""
+        mem = np.ascontiguousarray(members, dtype=np.int32)
+        Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+        if out is None:
+            out = self._torch.empty((len(mem), len(Ls), NQUANT, 2), dtype=self._torch.float64,
+                                    device=self.device)
+        o, counts = self._origin_lists(Ls, origins)
+        self._check(self.lib.lbm_subvolume_balance_async(
+            self.h, _ptr(mem), len(mem), _ptr(Ls), len(Ls), _ptr(o), _ptr(counts), _ptr(out)))
+        return out
+
+    def diag_synchronize(self):
+        self._check(self.lib.lbm_diag_synchronize(self.h))
 
     # -- adjoint ------------------------------------------------------------
     def adjoint_step(self, member: int, f_n, lam_in, lam_out, weight: float, box, L: int,

@@ -53,7 +53,7 @@ int check_config(const lbm_config *cfg, std::string &err) {
   if (!cfg) { err = "config is NULL"; return LBM_ERR_ARG; }
   if (cfg->n_members < 1 || !cfg->members) { err = "n_members must be >= 1 with a member array"; return LBM_ERR_ARG; }
   if (cfg->precision != 32 && cfg->precision != 64) { err = "precision must be 32 or 64"; return LBM_ERR_ARG; }
-  if (cfg->storage != 0) { err = "storage: only 0 (double buffer) is available"; return LBM_ERR_ARG; }
+  if (cfg->storage < 0 || cfg->storage > 2) { err = "storage must be 0 (tuned), 1 (AA) or 2 (double buffer)"; return LBM_ERR_ARG; }
   if (cfg->diag_precision != 0 && cfg->diag_precision != 32 && cfg->diag_precision != 64) { err = "diag_precision must be 0, 32 or 64"; return LBM_ERR_ARG; }
   if (cfg->diag_every < 0 || cfg->graph_steps < 0) { err = "diag_every and graph_steps must be >= 0"; return LBM_ERR_ARG; }
   for (int m = 0; m < cfg->n_members; ++m) {
@@ -101,7 +101,7 @@ Layout make_layout(const lbm_config *cfg) {
     const size_t N = (size_t)c.nx * c.ny;
     const size_t plane = (size_t)c.ny * pitch_of(c.nx, cfg->precision);
     L.pop0.push_back(take(es * 9 * plane));
-    L.pop1.push_back(take(es * 9 * plane));
+    L.pop1.push_back(cfg->storage == 1 ? L.pop0.back() : take(es * 9 * plane));  // AA: one array
     L.fx.push_back(take(es * c.ny));
     L.fy.push_back(take(es * c.nx));
     L.fx64.push_back(take(8 * c.ny));
@@ -113,7 +113,7 @@ Layout make_layout(const lbm_config *cfg) {
   L.scratch = take(8 * L.scratch_fields * L.Nmax);
   L.partials = take(8 * lbm::diag_partials_needed(kMaxL));
   L.stats = take(8 * (size_t)n * kMaxL * 30);
-  L.Ls = take(4 * 4 * (size_t)n * kMaxL);  // per-size meta rows {L, boxes, offsets}
+  L.Ls = take(4 * 8 * (size_t)n * kMaxL);  // per-size meta rows {L, boxes, offsets, out row}
   L.out7 = take(8 * 8);
   L.origin_cap = std::max<size_t>(4 * L.Nmax, (size_t)1 << 20);
   L.origins = take(8 * L.origin_cap);
@@ -137,13 +137,17 @@ struct lbm_handle {
   int diag_precision = 32;  // arithmetic of the term fields and box statistics
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t diag_stream = nullptr;  // asynchronous diagnostics
+  cudaEvent_t ev_ready = nullptr, ev_diag_done = nullptr;
+  bool diag_pending = false;
   int cur = 0;
   long long t = 0;
   long long ring_time[3] = {-1, -1, -1};
   lbm::DiagScratch sc{};
   lbm::LaunchCfg lc{8, 1, 0};
   int graph_k = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // by storage state
+  float tuned_ms = 0.f;  // autotuned time of one step, ms (0: not tuned)
   long long launches = 0;  // kernels issued (graph replays count their nodes)
   std::string err = "no error";
 };
@@ -257,7 +261,15 @@ double *snap_slot(lbm_handle *h, int m, int slot) {
   return h->hm[m].snap + (size_t)slot * 3 * N;
 }
 
+// Orders the main stream after any asynchronous diagnostic still running:
+// it reads the snapshot ring and uses the diagnostic scratch.
+int wait_diag(lbm_handle *h) {
+  if (h->diag_pending) CK(cudaStreamWaitEvent(h->stream, h->ev_diag_done, 0));
+  return LBM_OK;
+}
+
 int record(lbm_handle *h) {
+  if (int rc = wait_diag(h)) return rc;
   const int slot = (int)(h->t % 3);
   for (int m = 0; m < (int)h->mcfg.size(); ++m)
     CK(lbm::launch_snapshot(h->precision, h->d_members, m, h->mcfg[m].nx, h->mcfg[m].ny,
@@ -274,8 +286,12 @@ int check_member(lbm_handle *h, int member) {
   return LBM_OK;
 }
 
-// Autotune the batched launch: time each candidate shape on the live
-// buffers without flipping the buffer parity (the state is not changed).
+// Autotune of the batched launch, run at create time while the populations
+// are still undefined: each candidate (warps per CTA, rows per warp, grid
+// size, and -- when the storage is left to the tuner -- double buffer
+// versus in-place AA) is timed over 6 steps (both AA phases) on the live
+// buffers, and the fastest is kept.  The state is reset to its initial
+// phase afterwards.
 int autotune(lbm_handle *h) {
   if (h->precision != 32) return LBM_OK;
   size_t cells = 0;
@@ -285,11 +301,15 @@ int autotune(lbm_handle *h) {
   int dev = 0, nsm = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  struct Cand { lbm::LaunchCfg lc; float ms; };
+  struct Cand { lbm::LaunchCfg lc; int state; float ms; };
+  std::vector<int> states;
+  if (h->cfg.storage == 0) states = {0, 2};
+  else states = {h->cfg.storage == 1 ? 2 : 0};
   std::vector<Cand> cands;
-  for (int wy : {4, 8})
-    for (int rows : {1, 2, 4})
-      for (int per : {0, 4, 8}) cands.push_back({{wy, rows, per * nsm}, 0.f});
+  for (int st : states)
+    for (int wy : {4, 8})
+      for (int rows : {1, 2, 4})
+        for (int per : {0, 4, 8}) cands.push_back({{wy, rows, per * nsm}, st, 0.f});
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -298,9 +318,16 @@ int autotune(lbm_handle *h) {
     h->lc = cands[i].lc;
     int rc = build_tiles(h);
     if (rc) return rc;
-    for (int w = 0; w < 2; ++w) { rc = launch_one_step(h, h->stream, h->cur); if (rc) return rc; }
+    int st = cands[i].state;
+    for (int w = 0; w < 2; ++w) {
+      if ((rc = launch_one_step(h, h->stream, st))) return rc;
+      st ^= 1;
+    }
     CK(cudaEventRecord(e0, h->stream));
-    for (int r = 0; r < 5; ++r) { rc = launch_one_step(h, h->stream, h->cur); if (rc) return rc; }
+    for (int r = 0; r < 6; ++r) {
+      if ((rc = launch_one_step(h, h->stream, st))) return rc;
+      st ^= 1;
+    }
     CK(cudaEventRecord(e1, h->stream));
     CK(cudaEventSynchronize(e1));
     CK(cudaEventElapsedTime(&cands[i].ms, e0, e1));
@@ -309,6 +336,8 @@ int autotune(lbm_handle *h) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->lc = cands[best].lc;
+  h->cur = cands[best].state;
+  h->tuned_ms = cands[best].ms / 6.0f;
   return build_tiles(h);
 }
 
@@ -356,11 +385,17 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
 
   auto cleanup = [&](int code) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->diag_stream) cudaStreamDestroy(h->diag_stream);
+    if (h->ev_ready) cudaEventDestroy(h->ev_ready);
+    if (h->ev_diag_done) cudaEventDestroy(h->ev_diag_done);
     delete h;
     return code;
   };
-  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return cleanup(fail(nullptr, LBM_ERR_CUDA, "cannot create the capture stream"));
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->diag_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_diag_done, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(nullptr, LBM_ERR_CUDA, "cannot create the streams and events"));
 
   const size_t es = h->precision == 32 ? 4 : 8;
   std::vector<char> tab;
@@ -422,6 +457,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess)
     return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
+  h->cur = cfg->storage == 1 ? 2 : 0;
   rc = build_tiles(h);
   if (rc == LBM_OK) rc = autotune(h);
   if (rc != LBM_OK) {
@@ -434,8 +470,12 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
 
 int lbm_destroy(lbm_handle *h) {
   if (!h) return LBM_OK;
+  if (h->diag_stream) cudaStreamSynchronize(h->diag_stream);
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->diag_stream) cudaStreamDestroy(h->diag_stream);
+  if (h->ev_ready) cudaEventDestroy(h->ev_ready);
+  if (h->ev_diag_done) cudaEventDestroy(h->ev_diag_done);
   delete h;
   return LBM_OK;
 }
@@ -453,12 +493,20 @@ int lbm_init_fields(lbm_handle *h, int member, const double *rho, const double *
       return fail(h, LBM_ERR_ARG, "shared init fields need equal grids");
   const size_t N = (size_t)nx * ny;
   const double *r = rho, *u = ux, *v = uy;
+  if (int rc = wait_diag(h)) return rc;
   if (!on_device) {
     double *st = h->sc.f;  // staging: three scratch fields
     CK(cudaMemcpyAsync(st, rho, 8 * N, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(st + N, ux, 8 * N, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(st + 2 * N, uy, 8 * N, cudaMemcpyHostToDevice, h->stream));
     r = st; u = st + N; v = st + 2 * N;
+  }
+  if (h->cur >= 2) {
+    // AA storage restarts at its even phase; members not re-initialised here
+    // keep their data only when the phase already is even
+    if (h->cur == 3 && m1 - m0 != (int)h->mcfg.size())
+      return fail(h, LBM_ERR_ARG, "AA storage: initialise every member (or at an even step)");
+    h->cur = 2;
   }
   for (int m = m0; m < m1; ++m)
     CK(lbm::launch_init_fields(h->precision, h->d_members, m, nx, ny, r, u, v, h->cur, h->stream));
@@ -472,6 +520,17 @@ int lbm_init_fields(lbm_handle *h, int member, const double *rho, const double *
 long long lbm_time(const lbm_handle *h) { return h ? h->t : -1; }
 
 long long lbm_launch_count(const lbm_handle *h) { return h ? h->launches : -1; }
+
+int lbm_tuning(const lbm_handle *h, int *storage, int *warps, int *rows, int *grid,
+               float *step_ms) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (storage) *storage = h->cur >= 2 ? 1 : 2;
+  if (warps) *warps = h->lc.block_warps_y;
+  if (rows) *rows = h->lc.rows_per_warp;
+  if (grid) *grid = h->lc.grid_ctas;
+  if (step_ms) *step_ms = h->tuned_ms;
+  return LBM_OK;
+}
 
 int lbm_step(lbm_handle *h, int nsteps) {
   if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
@@ -508,6 +567,7 @@ int lbm_moments(lbm_handle *h, int member, double *rho, double *ux, double *uy,
                 double *omega) {
   int rc = check_member(h, member);
   if (rc) return rc;
+  if ((rc = wait_diag(h))) return rc;
   const lbm_member_cfg &c = h->mcfg[member];
   double *snap = h->sc.f;  // scratch fields 0..2
   CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, snap, h->stream));
@@ -520,6 +580,7 @@ int lbm_global_balance(lbm_handle *h, int member, double *out) {
   int rc = check_member(h, member);
   if (rc) return rc;
   if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+  if ((rc = wait_diag(h))) return rc;
   const lbm_member_cfg &c = h->mcfg[member];
   double *snap = h->sc.f;
   double *out_dev = reinterpret_cast<double *>(ws_at(h, h->lay.out7));
@@ -540,9 +601,9 @@ namespace {
 // the host with one synchronisation at the end.
 int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int nL,
                     const int *origins, const int *counts, double *stats_out,
-                    double *per_box_out) {
+                    double *per_box_out, double *stats_dev_out) {
   if (!L || nL < 1 || nL > kMaxL) return fail(h, LBM_ERR_ARG, "need 1..32 box sizes");
-  if (!stats_out) return fail(h, LBM_ERR_ARG, "stats_out is NULL");
+  if (!stats_out && !stats_dev_out) return fail(h, LBM_ERR_ARG, "stats output is NULL");
   if (nm < 1) return fail(h, LBM_ERR_ARG, "no member given");
   if (per_box_out && nm != 1) return fail(h, LBM_ERR_ARG, "per_box_out needs one member");
   if ((origins == nullptr) != (counts == nullptr))
@@ -576,7 +637,7 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
     return fail(h, LBM_ERR_HISTORY, "snapshots of time n-1 and n-2 are missing");
   // per member: the sizes that fit its grid, with their box counts and offsets
   std::vector<std::vector<int>> where(nm);
-  std::vector<int> meta((size_t)nm * kMaxL * 4, 0), maxb(nm, 0);
+  std::vector<int> meta((size_t)nm * kMaxL * 8, 0), maxb(nm, 0);
   for (int i = 0; i < nm; ++i) {
     const lbm_member_cfg &c = h->mcfg[members[i]];
     const int N = c.nx * c.ny;
@@ -584,11 +645,12 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
     for (int q = 0; q < nL; ++q) {
       const int nb = origins ? counts[q] : N;
       if (L[q] >= 1 && L[q] <= c.nx && L[q] <= c.ny) {
-        int *mrow = &meta[((size_t)i * kMaxL + k) * 4];
+        int *mrow = &meta[((size_t)i * kMaxL + k) * 8];
         mrow[0] = L[q];
         mrow[1] = nb;
         mrow[2] = origins ? ooff : -1;
         mrow[3] = row;
+        mrow[4] = i * nL + q;  // row of the statistics output
         maxb[i] = std::max(maxb[i], nb);
         where[i].push_back(q);
         ++k;
@@ -599,31 +661,44 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
       row += nb;
     }
   }
-  for (size_t k = 0; k < (size_t)nm * nL * 30; ++k) stats_out[k] = NAN;
+  // asynchronous: on the diagnostic stream, after the work queued so far on
+  // the main stream (the snapshots); synchronous: on the main stream, after
+  // any asynchronous diagnostic still running (shared scratch).
+  const bool async = stats_dev_out != nullptr;
+  cudaStream_t s = h->stream;
+  if (async) {
+    CK(cudaEventRecord(h->ev_ready, h->stream));
+    CK(cudaStreamWaitEvent(h->diag_stream, h->ev_ready, 0));
+    s = h->diag_stream;
+  } else if (h->diag_pending) {
+    CK(cudaStreamWaitEvent(h->stream, h->ev_diag_done, 0));
+  }
   int *meta_dev = reinterpret_cast<int *>(ws_at(h, h->lay.Ls));
   int *orig_dev = origins ? reinterpret_cast<int *>(ws_at(h, h->lay.origins)) : nullptr;
-  double *stats_dev = reinterpret_cast<double *>(ws_at(h, h->lay.stats));
-  CK(cudaMemcpyAsync(meta_dev, meta.data(), 4 * meta.size(), cudaMemcpyHostToDevice, h->stream));
+  double *stats_dev = async ? stats_dev_out : reinterpret_cast<double *>(ws_at(h, h->lay.stats));
+  CK(cudaMemsetAsync(stats_dev, 0xff, 8 * (size_t)nm * nL * 30, s));  // all-ones bits: NaN
+  CK(cudaMemcpyAsync(meta_dev, meta.data(), 4 * meta.size(), cudaMemcpyHostToDevice, s));
   if (origins)
-    CK(cudaMemcpyAsync(orig_dev, origins, 8 * total_boxes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(orig_dev, origins, 8 * total_boxes, cudaMemcpyHostToDevice, s));
   for (int i = 0; i < nm; ++i) {
     if (where[i].empty()) continue;
     const int m = members[i];
     CK(lbm::diag_terms(h->hm[m], h->diag_precision, snap_slot(h, m, (int)(t % 3)),
                        snap_slot(h, m, (int)((t - 1) % 3)), snap_slot(h, m, (int)((t - 2) % 3)),
-                       h->sc, h->stream));
-    CK(lbm::diag_sat_and_query(h->hm[m], h->diag_precision, meta_dev + (size_t)i * kMaxL * 4,
-                               (int)where[i].size(), maxb[i], orig_dev, h->sc,
-                               stats_dev + (size_t)i * kMaxL * 30, per_box_out, h->stream));
-    h->launches += 10;  // 4 term passes, max, scales, 2 scans, query, statistics
+                       h->sc, s));
+    CK(lbm::diag_sat_and_query(h->hm[m], h->diag_precision, meta_dev + (size_t)i * kMaxL * 8,
+                               (int)where[i].size(), maxb[i], orig_dev, h->sc, stats_dev,
+                               per_box_out, s));
+    h->launches += 11;  // 4 term passes, max, scales, 2 scans, constants, query, statistics
   }
-  std::vector<double> st((size_t)nm * kMaxL * 30);
-  CK(cudaMemcpyAsync(st.data(), stats_dev, 8 * st.size(), cudaMemcpyDeviceToHost, h->stream));
+  if (async) {
+    CK(cudaEventRecord(h->ev_diag_done, h->diag_stream));
+    h->diag_pending = true;
+    return LBM_OK;
+  }
+  CK(cudaMemcpyAsync(stats_out, stats_dev, 8 * (size_t)nm * nL * 30, cudaMemcpyDeviceToHost,
+                     h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  for (int i = 0; i < nm; ++i)
-    for (size_t k = 0; k < where[i].size(); ++k)
-      std::memcpy(stats_out + ((size_t)i * nL + where[i][k]) * 30,
-                  st.data() + ((size_t)i * kMaxL + k) * 30, 8 * 30);
   return LBM_OK;
 }
 
@@ -632,7 +707,9 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
 int lbm_subvolume_balance(lbm_handle *h, int member, const int *L, int nL, const int *origins,
                           const int *counts, double *stats_out, double *per_box_out) {
   if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
-  return balance_members(h, &member, 1, L, nL, origins, counts, stats_out, per_box_out);
+  if (!stats_out) return fail(h, LBM_ERR_ARG, "stats_out is NULL");
+  return balance_members(h, &member, 1, L, nL, origins, counts, stats_out, per_box_out,
+                         nullptr);
 }
 
 int lbm_subvolume_balance_batch(lbm_handle *h, const int *members, int n_members, const int *L,
@@ -640,7 +717,25 @@ int lbm_subvolume_balance_batch(lbm_handle *h, const int *members, int n_members
                                 double *stats_out) {
   if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
   if (!members) return fail(h, LBM_ERR_ARG, "members is NULL");
-  return balance_members(h, members, n_members, L, nL, origins, counts, stats_out, nullptr);
+  if (!stats_out) return fail(h, LBM_ERR_ARG, "stats_out is NULL");
+  return balance_members(h, members, n_members, L, nL, origins, counts, stats_out, nullptr,
+                         nullptr);
+}
+
+int lbm_subvolume_balance_async(lbm_handle *h, const int *members, int n_members, const int *L,
+                                int nL, const int *origins, const int *counts,
+                                double *stats_dev) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (!members) return fail(h, LBM_ERR_ARG, "members is NULL");
+  if (!stats_dev) return fail(h, LBM_ERR_ARG, "stats_dev is NULL");
+  return balance_members(h, members, n_members, L, nL, origins, counts, nullptr, nullptr,
+                         stats_dev);
+}
+
+int lbm_diag_synchronize(lbm_handle *h) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (h->diag_pending) CK(cudaEventSynchronize(h->ev_diag_done));
+  return LBM_OK;
 }
 
 extern "C" {
@@ -651,6 +746,7 @@ int lbm_get_populations(lbm_handle *h, int member, double *f, int on_device) {
   if (!f) return fail(h, LBM_ERR_ARG, "f is NULL");
   const lbm_member_cfg &c = h->mcfg[member];
   const size_t N = (size_t)c.nx * c.ny;
+  if ((rc = wait_diag(h))) return rc;
   double *dst = on_device ? f : h->sc.f;
   CK(lbm::launch_get_populations(h->precision, h->d_members, member, c.nx, c.ny, h->cur, dst, h->stream));
   h->launches += 1;
@@ -667,6 +763,7 @@ int lbm_set_populations(lbm_handle *h, int member, const double *f, int on_devic
   if (!f) return fail(h, LBM_ERR_ARG, "f is NULL");
   const lbm_member_cfg &c = h->mcfg[member];
   const size_t N = (size_t)c.nx * c.ny;
+  if ((rc = wait_diag(h))) return rc;
   const double *src = f;
   if (!on_device) {
     CK(cudaMemcpyAsync(h->sc.f, f, 8 * 9 * N, cudaMemcpyHostToDevice, h->stream));
@@ -704,6 +801,7 @@ int lbm_adjoint_step(lbm_handle *h, int member, const double *f_n, const double 
   if (obj_weight != 0.0 &&
       (L < 1 || L > c.nx || L > c.ny || bx < 0 || bx >= c.nx || by < 0 || by >= c.ny))
     return fail(h, LBM_ERR_ARG, "objective box outside the grid");
+  if ((rc = wait_diag(h))) return rc;
   CK(lbm::adjoint_step(h->hm[member], f_n, lambda_in, lambda_out, obj_weight, bx, by, L,
                        dJ_dtau, dJ_dF0, h->sc, h->stream));
   h->launches += lbm::adjoint_kernel_count(obj_weight);
@@ -718,6 +816,7 @@ int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx, i
   if (!acc) return fail(h, LBM_ERR_ARG, "acc is NULL");
   if (L < 1 || L > c.nx || L > c.ny || bx < 0 || bx >= c.nx || by < 0 || by >= c.ny)
     return fail(h, LBM_ERR_ARG, "objective box outside the grid");
+  if ((rc = wait_diag(h))) return rc;
   CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, h->sc.f,
                           h->stream));
   CK(lbm::objective_from_snapshot(h->hm[member], weight, bx, by, L, acc, h->sc, h->stream));

@@ -485,7 +485,7 @@ __global__ void k_query_consts(const double *scales, const int *meta, int nL,
   const int t = threadIdx.x;
   if (t >= nL * 12) return;
   const int iL = t / 12, k = t % 12;
-  const double area = (double)meta[4 * iL] * (double)meta[4 * iL];
+  const double area = (double)meta[8 * iL] * (double)meta[8 * iL];
   const long long total = S[(size_t)k * N + N - 1];
   const double inv = scales[12 + k];
   QConst q;
@@ -497,9 +497,9 @@ __global__ void k_query_consts(const double *scales, const int *meta, int nL,
   consts[t] = q;
 }
 
-// 64-bit integer to the query precision.  The float version splits the
-// integer into 32-bit halves: GB300 converts 64-bit integers on its slow
-// FP64 path, 32-bit ones at full rate.
+// 64-bit integer to the query precision.  The float version assembles the
+// IEEE bits with integer instructions (leading-zero count, shift, round half
+// up): GB300 issues integer-to-float conversions on its slow FP64 pipe.
 template <typename MT>
 __device__ __forceinline__ MT to_mt(long long v);
 template <>
@@ -508,13 +508,28 @@ __device__ __forceinline__ double to_mt<double>(long long v) {
 }
 template <>
 __device__ __forceinline__ float to_mt<float>(long long v) {
-  const int hi = (int)(v >> 32);
-  const unsigned lo = (unsigned)(v & 0xffffffffull);
-  return fmaf((float)hi, 4294967296.0f, (float)lo);
+  const unsigned long long sgn = (unsigned long long)v >> 63;
+  const unsigned long long a = sgn ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  if (a == 0ull) return 0.0f;
+  int e = 63 - __clzll((long long)a);  // index of the leading one
+  unsigned long long m;
+  if (e <= 23) {
+    m = a << (23 - e);
+  } else {
+    const int sh = e - 23;
+    m = (a + (1ull << (sh - 1))) >> sh;
+    if (m >> 24) {  // rounding carried into a new leading bit
+      m >>= 1;
+      ++e;
+    }
+  }
+  const unsigned bits = ((unsigned)sgn << 31) | ((unsigned)(e + 127) << 23) |
+                        ((unsigned)m & 0x7fffffu);
+  return __uint_as_float(bits);
 }
 
-// Per size, meta[4*iL] = {L, n_boxes, origin offset (-1: all periodic
-// origins), per-box row offset}.  blockIdx.z selects the balance: 0 = energy
+// Per size, meta[8*iL] = {L, n_boxes, origin offset (-1: all periodic
+// origins), per-box row offset, statistics output row, 3 unused}.  blockIdx.z selects the balance: 0 = energy
 // (fields 0..5: LHS^E, RHS^{E,1..5}), 1 = enstrophy (fields 6..11: LHS^O,
 // RHS^{O,1..5}; RHS^{O,6} is identically 0 in 2D and adds nothing).
 // One thread per (box, balance): exact integer box sums of its 6 term
@@ -527,7 +542,7 @@ __global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
                                                const int *__restrict__ origins,
                                                double *partials, double *per_box) {
   const int iL = blockIdx.y, grp = blockIdx.z, k0 = 6 * grp;
-  const int L = meta[4 * iL], nb = meta[4 * iL + 1], ooff = meta[4 * iL + 2];
+  const int L = meta[8 * iL], nb = meta[8 * iL + 1], ooff = meta[8 * iL + 2];
   const size_t N = (size_t)nx * ny;
   const long long *S = sat_base(base, N) + (size_t)k0 * N;
   const QConst *qc = consts + (size_t)iL * 12 + k0;
@@ -548,7 +563,7 @@ __global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
       y0 = b / nx;
     }
     MT lhs = 0, sum = 0, mx = 0;
-    double *o = PER_BOX ? per_box + ((size_t)meta[4 * iL + 3] + b) * 15 : nullptr;
+    double *o = PER_BOX ? per_box + ((size_t)meta[8 * iL + 3] + b) * 15 : nullptr;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const long long *Sk = S + (size_t)j * N;
@@ -606,7 +621,8 @@ __global__ void k_stats_final(const double *partials, int nblocks, const QConst 
   __syncthreads();
   const int t = threadIdx.x;
   if (t < 15) {
-    const int nb = meta[4 * iL + 1];
+    const int nb = meta[8 * iL + 1];
+    const size_t orow = (size_t)meta[8 * iL + 4];
     double mean = 0.0, sd = 0.0;
     if (t < 14) {
       int row;  // row of sh holding the (sum, sum of squares) pair
@@ -627,8 +643,8 @@ __global__ void k_stats_final(const double *partials, int nblocks, const QConst 
       mean = shift + m1;
       sd = sqrt(fmax(s2 / nb - m1 * m1, 0.0));
     }
-    stats[((size_t)iL * 15 + t) * 2] = mean;
-    stats[((size_t)iL * 15 + t) * 2 + 1] = sd;
+    stats[(orow * 15 + t) * 2] = mean;
+    stats[(orow * 15 + t) * 2 + 1] = sd;
   }
 }
 

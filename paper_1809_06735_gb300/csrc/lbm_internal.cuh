@@ -104,8 +104,9 @@ cudaError_t diag_global(const Member &hm, const double *snap3, const DiagScratch
 // precision: 32 (FP32 term arithmetic) or 64.
 cudaError_t diag_terms(const Member &hm, int precision, const double *sn, const double *sn1,
                        const double *sn2, const DiagScratch &sc, cudaStream_t s);
-// meta_dev: [nL][4] {L, n_boxes, origin offset (-1: all periodic origins),
-// per-box row offset}; max_boxes: the largest n_boxes.
+// meta_dev: [nL][8] {L, n_boxes, origin offset (-1: all periodic origins),
+// per-box row offset, statistics row, unused x3}; max_boxes: the largest
+// n_boxes.  stats_dev: rows of [15][2], written at the statistics rows.
 cudaError_t diag_sat_and_query(const Member &hm, int precision, const int *meta_dev, int nL,
                                int max_boxes, const int *origins_dev, const DiagScratch &sc,
                                double *stats_dev, double *per_box_dev, cudaStream_t s);

@@ -1,14 +1,28 @@
 // D2Q9 BGK stream-collide with exact-difference forcing (eq. (1), eq. (2),
 // Sec. 3 of Tauzin et al. 2018) and the kernels that move the state in and
-// out of the device storage convention (see lbm_internal.cuh).
+// out of the device storage (see lbm_internal.cuh).
 //
-// Hot kernel: k_step_f32_vec, one pass per time step over every member of
+// Storage states (an int carried by the handle and flipped by each step):
+//   0, 1  double buffer, pull layout: buffer `state` holds post-collision
+//         values at their origin cell; f_l(x, n) = pop[state][l][x - c_l];
+//         a step reads buffer `state` and writes the other one.
+//   2     in-place AA layout, even phase: f_l(x, n) = pop[0][l][x];
+//         the step reads slot l at x and writes f*_l(x) to slot opposite(l)
+//         at x (no neighbour access at all).
+//   3     in-place AA layout, odd phase: f_l(x, n) = pop[0][opposite(l)][x - c_l];
+//         the step reads there and writes f*_l(x) to slot l at x + c_l, which
+//         is the even-phase location of f_l(x + c_l, n + 1).
+// In the odd phase each location is read and then written by the same cell
+// (slot opposite(l) at x - c_l is slot m = opposite(l) at x + c_m), so the
+// in-place update has no race.  Both layouts move 72 B per FP32 lattice
+// update; AA needs one population array instead of two.
+//
+// Hot kernel: k_step_f32_vec, one launch per time step over every member of
 // the ensemble.  Each warp owns 128 consecutive cells of one row (4 per
-// lane); each of the 9 populations is fetched with one aligned 128-bit load
-// per lane from the source row y - c_y, and the +-1 shift of the x-moving
-// populations is done with a warp shuffle (one scalar load at each warp
-// edge), so DRAM sees 9 x 16 B of coalesced reads and 9 x 16 B of writes per
-// 4 cells: the algorithmic 72 B per lattice update.
+// lane); each of the 9 populations is one aligned 128-bit load per lane from
+// its source row, and the +-1 shift of the x-moving populations is a warp
+// shuffle with one scalar load at each warp edge (the AA odd phase does the
+// same for its shifted stores), so DRAM sees coalesced 16-byte accesses.
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -74,12 +88,29 @@ __device__ __forceinline__ void collide_f64(double f[kQ], double om, double Fex,
   }
 }
 
+// One-cell periodic shift.
+__device__ __forceinline__ int wrap1(int i, int n) {
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Storage index of the public population f_l(x, y) in a given state.
+__device__ __forceinline__ size_t pub_index(const Member &M, int state, int l, int x, int y) {
+  if (state == 2) return (size_t)l * M.plane + (size_t)y * M.pitch + x;
+  const int xs = wrap1(x - cx_of(l), M.nx), ys = wrap1(y - cy_of(l), M.ny);
+  const int slot = state == 3 ? opposite(l) : l;
+  return (size_t)slot * M.plane + (size_t)ys * M.pitch + xs;
+}
+__device__ __forceinline__ void *state_buffer(const Member &M, int state) {
+  return state < 2 ? M.pop[state] : M.pop[0];
+}
+
 // ---------------------------------------------------------------------------
 // Hot kernel: batched FP32 stream-collide, 4 cells per lane, nx % 4 == 0.
 // blockDim = (32, WY); a tile is 128 x (WY * ROWS) cells of one member.
+// MODE 0: double-buffer pull; 1: AA even phase; 2: AA odd phase.
 // ---------------------------------------------------------------------------
 
-template <int ROWS>
+template <int ROWS, int MODE>
 __global__ void __launch_bounds__(256) k_step_f32_vec(const Member *__restrict__ members,
                                                       const Tile *__restrict__ tiles,
                                                       int ntiles, int cur) {
@@ -89,18 +120,19 @@ __global__ void __launch_bounds__(256) k_step_f32_vec(const Member *__restrict__
     const Member &M = members[tl.member];
     const int nx = M.nx, ny = M.ny, pitch = M.pitch;
     const size_t plane = M.plane;
-    const float *__restrict__ src = static_cast<const float *>(M.pop[cur]);
-    float *__restrict__ dst = static_cast<float *>(M.pop[cur ^ 1]);
+    const float *src = static_cast<const float *>(MODE == 0 ? M.pop[cur] : M.pop[0]);
+    float *dst = static_cast<float *>(MODE == 0 ? M.pop[cur ^ 1] : M.pop[0]);
     const float *__restrict__ fxt = static_cast<const float *>(M.fx_tab);
     const float *__restrict__ fyt = static_cast<const float *>(M.fy_tab);
     const float rho0 = M.rho0_f, om = M.omega_f, alpha = M.alpha_f;
     const int x = tl.x0 + 4 * lane;
     const bool active = x < nx;
+    const bool last = active && (lane == 31 || x + 4 >= nx);  // last active lane of the row segment
     float4 fy4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) fy4 = *reinterpret_cast<const float4 *>(fyt + x);
     const float fy[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
-    const int xprev = (x == 0) ? nx - 1 : x - 1;   // source of lane 0's c_x=+1 cell
-    const int xnext = (x + 4 >= nx) ? 0 : x + 4;   // source of last cell's c_x=-1
+    const int xprev = (x == 0) ? nx - 1 : x - 1;  // cell left of the chunk
+    const int xnext = (x + 4 >= nx) ? 0 : x + 4;  // cell right of the chunk
 
 #pragma unroll 1
     for (int r = 0; r < ROWS; ++r) {
@@ -112,25 +144,37 @@ __global__ void __launch_bounds__(256) k_step_f32_vec(const Member *__restrict__
 #pragma unroll
       for (int l = 0; l < kQ; ++l) {
         const int cxl = cx_of(l), cyl = cy_of(l);
+        if (MODE == 1) {  // own cell, own slot
+          float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (active)
+            o = __ldg(reinterpret_cast<const float4 *>(src + (size_t)l * plane +
+                                                       (size_t)y * pitch + x));
+          v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
+          continue;
+        }
+        const int slot = MODE == 2 ? opposite(l) : l;
         const int ys = cyl == 0 ? y : (cyl > 0 ? ym : yp);  // pull from y - c_y
-        const float *row = src + (size_t)l * plane + (size_t)ys * pitch;
+        const float *row = src + (size_t)slot * plane + (size_t)ys * pitch;
+        // read-only (non-coherent) loads only when source and destination
+        // differ; the in-place phase reads what it later overwrites
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (active) o = __ldg(reinterpret_cast<const float4 *>(row + x));
+        if (active)
+          o = MODE == 0 ? __ldg(reinterpret_cast<const float4 *>(row + x))
+                        : *reinterpret_cast<const float4 *>(row + x);
         if (cxl == 0) {
           v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
         } else if (cxl > 0) {  // pull from x - 1
           float prev = __shfl_up_sync(0xffffffffu, o.w, 1);
-          if (active && (lane == 0 || x == 0)) prev = __ldg(row + xprev);
+          if (active && (lane == 0 || x == 0)) prev = MODE == 0 ? __ldg(row + xprev) : row[xprev];
           v[l][0] = prev; v[l][1] = o.x; v[l][2] = o.y; v[l][3] = o.z;
         } else {  // pull from x + 1
           float next = __shfl_down_sync(0xffffffffu, o.x, 1);
-          if (active && (lane == 31 || x + 4 >= nx)) next = __ldg(row + xnext);
+          if (last) next = MODE == 0 ? __ldg(row + xnext) : row[xnext];
           v[l][0] = o.y; v[l][1] = o.z; v[l][2] = o.w; v[l][3] = next;
         }
       }
       if (active) {
         const float fx = fxt[y];
-        float out[kQ][4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           float g[kQ];
@@ -138,60 +182,124 @@ __global__ void __launch_bounds__(256) k_step_f32_vec(const Member *__restrict__
           for (int l = 0; l < kQ; ++l) g[l] = v[l][c];
           collide_f32(g, rho0, om, fx, fy[c], alpha);
 #pragma unroll
-          for (int l = 0; l < kQ; ++l) out[l][c] = g[l];
+          for (int l = 0; l < kQ; ++l) v[l][c] = g[l];
         }
-        float *drow = dst + (size_t)y * pitch + x;
+      }
+      if (MODE == 0 || MODE == 1) {
+        if (active) {
 #pragma unroll
-        for (int l = 0; l < kQ; ++l)
-          __stcs(reinterpret_cast<float4 *>(drow + (size_t)l * plane),
-                 make_float4(out[l][0], out[l][1], out[l][2], out[l][3]));
+          for (int l = 0; l < kQ; ++l) {
+            const int slot = MODE == 1 ? opposite(l) : l;
+            __stcs(reinterpret_cast<float4 *>(dst + (size_t)slot * plane + (size_t)y * pitch + x),
+                   make_float4(v[l][0], v[l][1], v[l][2], v[l][3]));
+          }
+        }
+      } else {  // AA odd phase: f*_l(x) goes to slot l at x + c_l
+#pragma unroll
+        for (int l = 0; l < kQ; ++l) {
+          const int cxl = cx_of(l), cyl = cy_of(l);
+          const int yd = cyl == 0 ? y : (cyl > 0 ? yp : ym);
+          float *drow = dst + (size_t)l * plane + (size_t)yd * pitch;
+          if (cxl == 0) {
+            if (active)
+              __stcs(reinterpret_cast<float4 *>(drow + x),
+                     make_float4(v[l][0], v[l][1], v[l][2], v[l][3]));
+          } else if (cxl > 0) {
+            // chunk [x, x+3] receives the cells x-1 .. x+2
+            const float prev = __shfl_up_sync(0xffffffffu, v[l][3], 1);
+            if (active) {
+              if (lane != 0) {
+                __stcs(reinterpret_cast<float4 *>(drow + x),
+                       make_float4(prev, v[l][0], v[l][1], v[l][2]));
+              } else {
+                drow[x + 1] = v[l][0];
+                drow[x + 2] = v[l][1];
+                drow[x + 3] = v[l][2];
+              }
+              if (last) drow[xnext] = v[l][3];
+            }
+          } else {
+            // chunk [x, x+3] receives the cells x+1 .. x+4
+            const float next = __shfl_down_sync(0xffffffffu, v[l][0], 1);
+            if (active) {
+              if (!last) {
+                __stcs(reinterpret_cast<float4 *>(drow + x),
+                       make_float4(v[l][1], v[l][2], v[l][3], next));
+              } else {
+                drow[x] = v[l][1];
+                drow[x + 1] = v[l][2];
+                drow[x + 2] = v[l][3];
+              }
+              if (lane == 0) drow[xprev] = v[l][0];
+            }
+          }
+        }
       }
     }
   }
 }
 
+template <int ROWS>
+static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int ntiles, int state,
+                            int grid, dim3 block, cudaStream_t s) {
+  if (state < 2)
+    k_step_f32_vec<ROWS, 0><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+  else if (state == 2)
+    k_step_f32_vec<ROWS, 1><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+  else
+    k_step_f32_vec<ROWS, 2><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+}
+
 cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, int ntiles,
-                                int cur, const LaunchCfg &lc, cudaStream_t s) {
+                                int state, const LaunchCfg &lc, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   dim3 block(32, lc.block_warps_y);
   int grid = lc.grid_ctas > 0 ? (lc.grid_ctas < ntiles ? lc.grid_ctas : ntiles) : ntiles;
   switch (lc.rows_per_warp) {
-    case 1: k_step_f32_vec<1><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, cur); break;
-    case 2: k_step_f32_vec<2><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, cur); break;
-    case 4: k_step_f32_vec<4><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, cur); break;
-    case 8: k_step_f32_vec<8><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, cur); break;
+    case 1: launch_vec_rows<1>(d_members, d_tiles, ntiles, state, grid, block, s); break;
+    case 2: launch_vec_rows<2>(d_members, d_tiles, ntiles, state, grid, block, s); break;
+    case 4: launch_vec_rows<4>(d_members, d_tiles, ntiles, state, grid, block, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// General kernel: one cell per thread, any nx (FP32 deviation or FP64).
+// General kernel: one cell per thread, any nx (FP32 deviation or FP64), any
+// storage state.
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__global__ void k_step_scalar(const Member *__restrict__ members, int member, int cur) {
+__global__ void k_step_scalar(const Member *__restrict__ members, int member, int state) {
   const Member &M = members[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= M.nx || y >= M.ny) return;
-  const T *__restrict__ src = static_cast<const T *>(M.pop[cur]);
-  T *__restrict__ dst = static_cast<T *>(M.pop[cur ^ 1]);
+  const T *src = static_cast<const T *>(state_buffer(M, state));
+  T *dst = static_cast<T *>(state < 2 ? M.pop[state ^ 1] : M.pop[0]);
   const T fx = static_cast<const T *>(M.fx_tab)[y];
   const T fy = static_cast<const T *>(M.fy_tab)[x];
   T f[kQ];
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) {
-    const int xs = wrapi(x - cx_of(l), M.nx), ys = wrapi(y - cy_of(l), M.ny);
-    f[l] = src[(size_t)l * M.plane + (size_t)ys * M.pitch + xs];
-  }
+  for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
   if constexpr (sizeof(T) == 4) {
     collide_f32(f, M.rho0_f, M.omega_f, fx, fy, M.alpha_f);
   } else {
     collide_f64(f, M.omega, fx, fy, M.alpha);
   }
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) dst[(size_t)l * M.plane + (size_t)y * M.pitch + x] = f[l];
+  for (int l = 0; l < kQ; ++l) {
+    size_t o;
+    if (state < 2) {
+      o = (size_t)l * M.plane + (size_t)y * M.pitch + x;
+    } else if (state == 2) {
+      o = (size_t)opposite(l) * M.plane + (size_t)y * M.pitch + x;
+    } else {
+      const int xd = wrap1(x + cx_of(l), M.nx), yd = wrap1(y + cy_of(l), M.ny);
+      o = (size_t)l * M.plane + (size_t)yd * M.pitch + xd;
+    }
+    dst[o] = f[l];
+  }
 }
 
 static dim3 grid2d(int nx, int ny, dim3 b) {
@@ -199,35 +307,33 @@ static dim3 grid2d(int nx, int ny, dim3 b) {
 }
 
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member, int nx,
-                               int ny, int cur, cudaStream_t s) {
+                               int ny, int state, cudaStream_t s) {
   dim3 b(64, 4);
   if (precision == 32)
-    k_step_scalar<float><<<grid2d(nx, ny, b), b, 0, s>>>(d_members, member, cur);
+    k_step_scalar<float><<<grid2d(nx, ny, b), b, 0, s>>>(d_members, member, state);
   else
-    k_step_scalar<double><<<grid2d(nx, ny, b), b, 0, s>>>(d_members, member, cur);
+    k_step_scalar<double><<<grid2d(nx, ny, b), b, 0, s>>>(d_members, member, state);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // State conversion: init from (rho, u), public populations in and out,
-// moment snapshots and the divergence flag.
+// moment snapshots and the divergence flag.  All address the public
+// population f_l(x, n) through pub_index.
 // ---------------------------------------------------------------------------
 
-// Storage of population l at cell x holds the value that streams to x + c_l:
-// stored_l(x) = f_l(x + c_l, n).
 template <typename T>
 __global__ void k_init(const Member *__restrict__ members, int member, const double *rho,
-                       const double *ux, const double *uy, int cur) {
+                       const double *ux, const double *uy, int state) {
   const Member &M = members[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= M.nx || y >= M.ny) return;
-  T *dst = static_cast<T *>(M.pop[cur]);
+  T *dst = static_cast<T *>(state_buffer(M, state));
+  const size_t c = (size_t)y * M.nx + x;
+  const double r = rho[c], u = ux[c], v = uy[c];
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
-    const int xs = wrapi(x + cx_of(l), M.nx), ys = wrapi(y + cy_of(l), M.ny);
-    const size_t c = (size_t)ys * M.nx + xs;
-    const double r = rho[c], u = ux[c], v = uy[c];
     const double cu = cx_of(l) * u + cy_of(l) * v;
     const double poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * (u * u + v * v);
     double val;
@@ -235,42 +341,40 @@ __global__ void k_init(const Member *__restrict__ members, int member, const dou
       val = w_of(l) * ((r - M.rho0) + r * poly);  // deviation from t_l rho0
     else
       val = w_of(l) * r * (1.0 + poly);
-    dst[(size_t)l * M.plane + (size_t)y * M.pitch + x] = (T)val;
+    dst[pub_index(M, state, l, x, y)] = (T)val;
   }
 }
 
 template <typename T>
-__global__ void k_get_pop(const Member *__restrict__ members, int member, int cur, double *f) {
+__global__ void k_get_pop(const Member *__restrict__ members, int member, int state, double *f) {
   const Member &M = members[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= M.nx || y >= M.ny) return;
-  const T *src = static_cast<const T *>(M.pop[cur]);
+  const T *src = static_cast<const T *>(state_buffer(M, state));
   const size_t N = (size_t)M.nx * M.ny;
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
-    const int xs = wrapi(x - cx_of(l), M.nx), ys = wrapi(y - cy_of(l), M.ny);
-    double v = (double)src[(size_t)l * M.plane + (size_t)ys * M.pitch + xs];
+    double v = (double)src[pub_index(M, state, l, x, y)];
     if (sizeof(T) == 4) v += w_of(l) * M.rho0;
     f[(size_t)l * N + (size_t)y * M.nx + x] = v;
   }
 }
 
 template <typename T>
-__global__ void k_set_pop(const Member *__restrict__ members, int member, int cur,
+__global__ void k_set_pop(const Member *__restrict__ members, int member, int state,
                           const double *f) {
   const Member &M = members[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= M.nx || y >= M.ny) return;
-  T *dst = static_cast<T *>(M.pop[cur]);
+  T *dst = static_cast<T *>(state_buffer(M, state));
   const size_t N = (size_t)M.nx * M.ny;
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
-    const int xs = wrapi(x + cx_of(l), M.nx), ys = wrapi(y + cy_of(l), M.ny);
-    double v = f[(size_t)l * N + (size_t)ys * M.nx + xs];
+    double v = f[(size_t)l * N + (size_t)y * M.nx + x];
     if (sizeof(T) == 4) v -= w_of(l) * M.rho0;
-    dst[(size_t)l * M.plane + (size_t)y * M.pitch + x] = (T)v;
+    dst[pub_index(M, state, l, x, y)] = (T)v;
   }
 }
 
@@ -296,20 +400,16 @@ __device__ __forceinline__ double csum(const float *v, const int *sign, int n) {
 
 // (rho, j_x, j_y) of the pre-collision state, FP64, into d[3][ny*nx].
 template <typename T>
-__global__ void k_snapshot(const Member *__restrict__ members, int member, int cur, double *d) {
+__global__ void k_snapshot(const Member *__restrict__ members, int member, int state,
+                           double *d) {
   const Member &M = members[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= M.nx || y >= M.ny) return;
-  const T *src = static_cast<const T *>(M.pop[cur]);
+  const T *src = static_cast<const T *>(state_buffer(M, state));
   T f[kQ];
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) {
-    int xs = x - cx_of(l), ys = y - cy_of(l);  // one-cell shifts: a single wrap
-    xs = xs < 0 ? xs + M.nx : (xs >= M.nx ? xs - M.nx : xs);
-    ys = ys < 0 ? ys + M.ny : (ys >= M.ny ? ys - M.ny : ys);
-    f[l] = src[(size_t)l * M.plane + (size_t)ys * M.pitch + xs];
-  }
+  for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
   double r, jx, jy;
   if constexpr (sizeof(T) == 4) {
     // deviations: rho = rho0 + sum g (weights sum to 1), j = sum c g
@@ -338,18 +438,17 @@ __global__ void k_snapshot(const Member *__restrict__ members, int member, int c
 }
 
 template <typename T>
-__global__ void k_status(const Member *__restrict__ members, int member, int cur) {
+__global__ void k_status(const Member *__restrict__ members, int member, int state) {
   const Member &M = members[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= M.nx || y >= M.ny) return;
-  const T *src = static_cast<const T *>(M.pop[cur]);
+  const T *src = static_cast<const T *>(state_buffer(M, state));
   double r = 0.0;
   bool bad = false;
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
-    const int xs = wrapi(x - cx_of(l), M.nx), ys = wrapi(y - cy_of(l), M.ny);
-    const double v = (double)src[(size_t)l * M.plane + (size_t)ys * M.pitch + xs];
+    const double v = (double)src[pub_index(M, state, l, x, y)];
     bad |= !isfinite(v);
     r += v;
   }
@@ -369,32 +468,32 @@ __global__ void k_status(const Member *__restrict__ members, int member, int cur
 
 cudaError_t launch_init_fields(int precision, const Member *d_members, int member, int nx,
                                int ny, const double *rho, const double *ux,
-                               const double *uy, int cur, cudaStream_t s) {
-  LBM_DISPATCH(precision, k_init, d_members, member, rho, ux, uy, cur);
+                               const double *uy, int state, cudaStream_t s) {
+  LBM_DISPATCH(precision, k_init, d_members, member, rho, ux, uy, state);
   return cudaGetLastError();
 }
 
 cudaError_t launch_get_populations(int precision, const Member *d_members, int member,
-                                   int nx, int ny, int cur, double *f, cudaStream_t s) {
-  LBM_DISPATCH(precision, k_get_pop, d_members, member, cur, f);
+                                   int nx, int ny, int state, double *f, cudaStream_t s) {
+  LBM_DISPATCH(precision, k_get_pop, d_members, member, state, f);
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_populations(int precision, const Member *d_members, int member,
-                                   int nx, int ny, int cur, const double *f, cudaStream_t s) {
-  LBM_DISPATCH(precision, k_set_pop, d_members, member, cur, f);
+                                   int nx, int ny, int state, const double *f, cudaStream_t s) {
+  LBM_DISPATCH(precision, k_set_pop, d_members, member, state, f);
   return cudaGetLastError();
 }
 
 cudaError_t launch_snapshot(int precision, const Member *d_members, int member, int nx,
-                            int ny, int cur, double *dst, cudaStream_t s) {
-  LBM_DISPATCH(precision, k_snapshot, d_members, member, cur, dst);
+                            int ny, int state, double *dst, cudaStream_t s) {
+  LBM_DISPATCH(precision, k_snapshot, d_members, member, state, dst);
   return cudaGetLastError();
 }
 
 cudaError_t launch_status(int precision, const Member *d_members, int member, int nx,
-                          int ny, int cur, cudaStream_t s) {
-  LBM_DISPATCH(precision, k_status, d_members, member, cur);
+                          int ny, int state, cudaStream_t s) {
+  LBM_DISPATCH(precision, k_status, d_members, member, state);
   return cudaGetLastError();
 }
 

@@ -271,3 +271,32 @@ def test_balance_batch_equals_per_member(P):
     assert np.all(np.isnan(batch[0, 3:])) and np.all(np.isfinite(batch[0, :3, 2:, 0]))
     assert np.all(np.isnan(batch[1, 4:])) and np.all(np.isfinite(batch[1, :4, 2:, 0]))
     assert np.all(np.isfinite(batch[2, :, 2:, 0]))
+
+
+def test_async_balance_overlapped_with_stepping(P):
+    """The asynchronous diagnostic gives, bit for bit, the synchronous
+    statistics of the same time even while the next steps run on the main
+    stream; the next snapshot records wait for it."""
+    import torch
+    spec = [(64, 64, 0.55), (48, 40, 0.6), (128, 32, 0.52)]
+    lat = P.Lattice([P.Member(nx, ny, t) for nx, ny, t in spec], precision=32, diag_every=20,
+                    graph_steps=6)
+    for i, (nx, ny, _) in enumerate(spec):
+        lat.init_fields(i, 1.0 + li.smooth_fields(nx, ny, 70 + i, amp=0.01),
+                        li.smooth_fields(nx, ny, 80 + i, amp=0.03),
+                        li.smooth_fields(nx, ny, 90 + i, amp=0.03))
+    lat.step(20)
+    Ls = [2, 4, 16, 40]
+    origins = [li.table1_origins(32, L, seed=L, count=500) for L in (2, 4, 16)] + \
+        [np.zeros((1, 2), np.int32)]
+    ref = lat.subvolume_balance_batch([0, 1, 2], Ls, origins=origins)
+    out = lat.subvolume_balance_async([0, 1, 2], Ls, origins=origins)
+    lat.step(15)
+    lat.diag_synchronize()
+    got = out.cpu().numpy()
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    np.testing.assert_array_equal(got[~np.isnan(got)], ref[~np.isnan(ref)])
+    lat.step(5)  # records 38, 39, 40 after the asynchronous work
+    nxt = lat.subvolume_balance_batch([0, 1, 2], Ls, origins=origins)
+    assert np.all(np.isfinite(nxt[:, :3, 2:, 0]))
+    torch.cuda.synchronize()
