@@ -217,6 +217,29 @@ __device__ void block_sum_store(double (&v)[NQ], double *out /*[NQ]*/) {
   }
 }
 
+// The same block sum with the warp stage in the accumulation type MT: only
+// one value per warp and quantity is widened to FP64 (GB300 runs FP64
+// arithmetic and conversions at a small fraction of its FP32 rate).
+template <int NQ, typename MT>
+__device__ void block_sum_store_mt(MT (&v)[NQ], double *out /*[NQ]*/) {
+  __shared__ double sh[NQ][32];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    MT a = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[q][wid] = (double)a;
+  }
+  __syncthreads();
+  if (tid < NQ) {
+    double a = 0.0;
+    for (int k = 0; k < nw; ++k) a += sh[tid][k];
+    out[tid] = a;
+  }
+}
+
 // Sums nb partial rows of width nq (fixed order per thread: 8 threads per
 // quantity take interleaved rows, then a fixed-order combination).
 __global__ void k_sum_partials(const double *partials, int nb, int nq, double *out) {
@@ -591,7 +614,7 @@ __global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
       if (grp == 1) o[14] = 0.0;
     }
   }
-  double acc[kQStats];
+  MT acc[kQStats];
   acc[0] = d1;
   acc[1] = d2;
 #pragma unroll
@@ -599,7 +622,7 @@ __global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
     acc[2 + 2 * j] = s1[j];
     acc[3 + 2 * j] = s2[j];
   }
-  block_sum_store<kQStats>(
+  block_sum_store_mt<kQStats, MT>(
       acc, partials + (((size_t)iL * 2 + grp) * gridDim.x + blockIdx.x) * kQStats);
 }
 
@@ -743,9 +766,9 @@ cudaError_t diag_sat_and_query(const Member &hm, int precision, const int *meta_
   }
   k_sat_cols<<<dim3((nx + 31) / 32, 12), dim3(32, 8), 0, s>>>(sc.f, nx, ny);
   k_query_consts<<<1, 32 * 12, 0, s>>>(scales, meta_dev, nL, sat_base(sc.f, N), N, consts);
-  // box lists: one box per thread; every periodic origin: about 4 per thread;
+  // box lists: one box per thread; every periodic origin: about 16 per thread;
   // at most kMaxPartialBlocks CTAs per size
-  const int per_cta = origins_dev ? 256 : 1024;
+  const int per_cta = origins_dev ? 256 : 4096;
   int qblocks = (max_boxes + per_cta - 1) / per_cta;
   if (qblocks > kMaxPartialBlocks) qblocks = kMaxPartialBlocks;
   if (qblocks < 1) qblocks = 1;
