@@ -110,7 +110,10 @@ Layout make_layout(const lbm_config *cfg) {
     L.Nmax = std::max(L.Nmax, N);
   }
   L.scratch_fields = lbm::kDiagFields;
-  L.scratch = take(8 * L.scratch_fields * L.Nmax);
+  size_t pad = 0;  // the 12 prefix tables carry one extra row and column
+  for (int m = 0; m < n; ++m)
+    pad = std::max(pad, (size_t)cfg->members[m].nx + cfg->members[m].ny + 1);
+  L.scratch = take(8 * (L.scratch_fields * L.Nmax + 12 * pad));
   L.partials = take(8 * lbm::diag_partials_needed(kMaxL));
   L.stats = take(8 * (size_t)n * kMaxL * 30);
   L.Ls = take(4 * 8 * (size_t)n * kMaxL);  // per-size meta rows {L, boxes, offsets, out row}

@@ -23,8 +23,9 @@
 // final statistic is FP64 and block-deterministic.
 //
 // Scratch (doubles of N = nx*ny cells): slots 0..2 a temporary snapshot,
-// slots 3.. the term-stage fields (each slot holds N values of T), then 12
-// slots of int64 tables; reduction partials at sc.partials.
+// slots 3.. the term-stage fields (each slot holds N values of T), then the
+// 12 int64 tables of (nx+1)(ny+1) entries; reduction partials at
+// sc.partials.
 #include <cmath>
 #include <vector>
 
@@ -56,26 +57,48 @@ __host__ __device__ inline T *fld(double *base, int k, size_t N) {
 __host__ __device__ inline long long *sat_base(double *base, size_t N) {
   return reinterpret_cast<long long *>(base + (size_t)(kSnapSlots + NF) * N);
 }
+// Each table is the exclusive prefix P(x, y) = sum over x' < x, y' < y for
+// 0 <= x <= nx, 0 <= y <= ny, stored row-major with rows of nx + 1 (row 0
+// and column 0 are zero), so a corner is one load with no branch.
+__host__ __device__ inline size_t sat_stride(int nx, int ny) {
+  return (size_t)(nx + 1) * (size_t)(ny + 1);
+}
 
 __device__ __forceinline__ int wr(int i, int n) {
   if (n >= 4) return i < 0 ? i + n : (i >= n ? i - n : i);
   return wrapi(i, n);
 }
 
+// Wrapped neighbour offsets of one cell, computed once and shared by every
+// stencil of the cell: xo[d+4] = (x + d) mod nx, yo[d+4] = ((y + d) mod ny) nx.
+struct Nb {
+  int xo[9], yo[9];
+};
+__device__ __forceinline__ Nb make_nb(const Grid &g, int x, int y) {
+  Nb nb;
+#pragma unroll
+  for (int d = -4; d <= 4; ++d) {
+    nb.xo[d + 4] = wr(x + d, g.nx);
+    nb.yo[d + 4] = wr(y + d, g.ny) * g.nx;
+  }
+  return nb;
+}
+
 // Eq. (18) in x and y (dx = 1), periodic, in the paired form
 // 4/5 (A+1 - A-1) - 1/5 (A+2 - A-2) + 4/105 (A+3 - A-3) - 1/280 (A+4 - A-4).
 template <typename T>
-__device__ __forceinline__ T Dx(const T *A, const Grid &g, int x, int y) {
-  const T *r = A + (size_t)y * g.nx;
-  auto a = [&](int d) { return r[wr(x + d, g.nx)]; };
-  return T(0.8) * (a(1) - a(-1)) - T(0.2) * (a(2) - a(-2)) +
-         T(4.0 / 105.0) * (a(3) - a(-3)) - T(1.0 / 280.0) * (a(4) - a(-4));
+__device__ __forceinline__ T Dx(const T *A, const Nb &nb) {
+  const T *r = A + nb.yo[4];
+  return T(0.8) * (r[nb.xo[5]] - r[nb.xo[3]]) - T(0.2) * (r[nb.xo[6]] - r[nb.xo[2]]) +
+         T(4.0 / 105.0) * (r[nb.xo[7]] - r[nb.xo[1]]) -
+         T(1.0 / 280.0) * (r[nb.xo[8]] - r[nb.xo[0]]);
 }
 template <typename T>
-__device__ __forceinline__ T Dy(const T *A, const Grid &g, int x, int y) {
-  auto a = [&](int d) { return A[(size_t)wr(y + d, g.ny) * g.nx + x]; };
-  return T(0.8) * (a(1) - a(-1)) - T(0.2) * (a(2) - a(-2)) +
-         T(4.0 / 105.0) * (a(3) - a(-3)) - T(1.0 / 280.0) * (a(4) - a(-4));
+__device__ __forceinline__ T Dy(const T *A, const Nb &nb) {
+  const T *c = A + nb.xo[4];
+  return T(0.8) * (c[nb.yo[5]] - c[nb.yo[3]]) - T(0.2) * (c[nb.yo[6]] - c[nb.yo[2]]) +
+         T(4.0 / 105.0) * (c[nb.yo[7]] - c[nb.yo[1]]) -
+         T(1.0 / 280.0) * (c[nb.yo[8]] - c[nb.yo[0]]);
 }
 
 #define CELL_INDEX                                        \
@@ -135,26 +158,27 @@ __global__ void k_prep(Grid g, const double *s0, const double *s1, const double 
 template <typename T>
 __global__ void k_grad(Grid g, double *base, size_t N) {
   CELL_INDEX;
+  const Nb nb = make_nb(g, x, y);
   const T *U = fld<T>(base, U0X, N), *V = fld<T>(base, U0Y, N);
-  const T w0 = Dx(V, g, x, y) - Dy(U, g, x, y);
-  const T dw01 = Dx(fld<T>(base, DU01Y, N), g, x, y) - Dy(fld<T>(base, DU01X, N), g, x, y);
-  const T dw12 = Dx(fld<T>(base, DU12Y, N), g, x, y) - Dy(fld<T>(base, DU12X, N), g, x, y);
+  const T w0 = Dx(V, nb) - Dy(U, nb);
+  const T dw01 = Dx(fld<T>(base, DU01Y, N), nb) - Dy(fld<T>(base, DU01X, N), nb);
+  const T dw12 = Dx(fld<T>(base, DU12Y, N), nb) - Dy(fld<T>(base, DU12X, N), nb);
   const T w1 = w0 - dw01;
   const T dO01 = T(0.5) * dw01 * (T(2) * w0 - dw01);
   const T dO12 = T(0.5) * dw12 * (T(2) * w1 - dw12);
   fld<T>(base, T0 + 6, N)[c] = T(0.5) * (T(3) * dO01 - dO12);  // LHS^Omega
   const T Om = T(0.5) * w0 * w0;
-  const T dxu = Dx(U, g, x, y), dyu = Dy(U, g, x, y);
-  const T dxv = Dx(V, g, x, y), dyv = Dy(V, g, x, y);
+  const T dxu = Dx(U, nb), dyu = Dy(U, nb);
+  const T dxv = Dx(V, nb), dyv = Dy(V, nb);
   const T u = U[c], v = V[c], r = fld<T>(base, R0, N)[c];
   const T sxx = T(2) * dxu, sxy = dyu + dxv, syy = T(2) * dyv;  // S_ij = d_j u_i + d_i u_j
   const T nr = (T)g.nu * r;
   const T *DR = fld<T>(base, DRHO, N);
-  fld<T>(base, T0 + 2, N)[c] = -(u * Dx(DR, g, x, y) + v * Dy(DR, g, x, y)) / T(3);
+  fld<T>(base, T0 + 2, N)[c] = -(u * Dx(DR, nb) + v * Dy(DR, nb)) / T(3);
   fld<T>(base, T0 + 4, N)[c] = -nr * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
   fld<T>(base, T0 + 8, N)[c] = -Om * (dxu + dyv);
   fld<T>(base, T0 + 9, N)[c] =
-      w0 * (Dx(fld<T>(base, FYR, N), g, x, y) - Dy(fld<T>(base, FXR, N), g, x, y));
+      w0 * (Dx(fld<T>(base, FYR, N), nb) - Dy(fld<T>(base, FXR, N), nb));
   fld<T>(base, WW, N)[c] = w0;
   fld<T>(base, B1, N)[c] = Om * u;
   fld<T>(base, B2, N)[c] = Om * v;
@@ -170,16 +194,17 @@ __global__ void k_grad(Grid g, double *base, size_t N) {
 template <typename T>
 __global__ void k_flux(Grid g, double *base, size_t N) {
   CELL_INDEX;
+  const Nb nb = make_nb(g, x, y);
   const T r = fld<T>(base, R0, N)[c];
   fld<T>(base, T0 + 1, N)[c] =
-      -(Dx(fld<T>(base, A1, N), g, x, y) + Dy(fld<T>(base, A2, N), g, x, y));
-  fld<T>(base, T0 + 5, N)[c] = Dx(fld<T>(base, C1, N), g, x, y) + Dy(fld<T>(base, C2, N), g, x, y);
+      -(Dx(fld<T>(base, A1, N), nb) + Dy(fld<T>(base, A2, N), nb));
+  fld<T>(base, T0 + 5, N)[c] = Dx(fld<T>(base, C1, N), nb) + Dy(fld<T>(base, C2, N), nb);
   fld<T>(base, T0 + 7, N)[c] =
-      -(Dx(fld<T>(base, B1, N), g, x, y) + Dy(fld<T>(base, B2, N), g, x, y));
-  const T Hx = (Dx(fld<T>(base, G1, N), g, x, y) + Dy(fld<T>(base, G2, N), g, x, y)) / r;
-  const T Hy = (Dx(fld<T>(base, G2, N), g, x, y) + Dy(fld<T>(base, G3, N), g, x, y)) / r;
+      -(Dx(fld<T>(base, B1, N), nb) + Dy(fld<T>(base, B2, N), nb));
+  const T Hx = (Dx(fld<T>(base, G1, N), nb) + Dy(fld<T>(base, G2, N), nb)) / r;
+  const T Hy = (Dx(fld<T>(base, G2, N), nb) + Dy(fld<T>(base, G3, N), nb)) / r;
   const T *W = fld<T>(base, WW, N);
-  fld<T>(base, T0 + 10, N)[c] = Hx * Dy(W, g, x, y) - Hy * Dx(W, g, x, y);
+  fld<T>(base, T0 + 10, N)[c] = Hx * Dy(W, nb) - Hy * Dx(W, nb);
   const T w = W[c];
   fld<T>(base, K1, N)[c] = w * Hy;
   fld<T>(base, K2, N)[c] = w * Hx;
@@ -189,8 +214,9 @@ __global__ void k_flux(Grid g, double *base, size_t N) {
 template <typename T>
 __global__ void k_curl(Grid g, double *base, size_t N) {
   CELL_INDEX;
+  const Nb nb = make_nb(g, x, y);
   fld<T>(base, T0 + 11, N)[c] =
-      Dx(fld<T>(base, K1, N), g, x, y) - Dy(fld<T>(base, K2, N), g, x, y);
+      Dx(fld<T>(base, K1, N), nb) - Dy(fld<T>(base, K2, N), nb);
 }
 
 // ---------------------------------------------------------------------------
@@ -273,7 +299,8 @@ __global__ void k_moments(Grid g, const double *snap, size_t N, double *rho, dou
 
 __global__ void k_vorticity(Grid g, const double *ux, const double *uy, double *omega) {
   CELL_INDEX;
-  omega[c] = Dx(uy, g, x, y) - Dy(ux, g, x, y);
+  const Nb nb = make_nb(g, x, y);
+  omega[c] = Dx(uy, nb) - Dy(ux, nb);
 }
 
 __global__ void k_global(Grid g, const double *snap, const double *ux, const double *uy,
@@ -283,11 +310,12 @@ __global__ void k_global(Grid g, const double *snap, const double *ux, const dou
   const int nthr = blockDim.x * blockDim.y;
   for (size_t c = (size_t)blockIdx.x * nthr + tid; c < N; c += (size_t)gridDim.x * nthr) {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+    const Nb nb = make_nb(g, x, y);
     const double r = snap[c], jx = snap[N + c], jy = snap[2 * N + c];
     const double Fx = g.fxt[y] - g.alpha * jx, Fy = g.fyt[x] - g.alpha * jy;
     const double u = ux[c], v = uy[c];
-    const double dxu = Dx(ux, g, x, y), dyu = Dy(ux, g, x, y);
-    const double dxv = Dx(uy, g, x, y), dyv = Dy(uy, g, x, y);
+    const double dxu = Dx(ux, nb), dyu = Dy(ux, nb);
+    const double dxv = Dx(uy, nb), dyv = Dy(uy, nb);
     const double w = dxv - dyu;
     const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
     acc[0] += r;
@@ -392,11 +420,15 @@ __global__ void __launch_bounds__(256) k_sat_rows(double *base, int nx, int ny,
   const int y = blockIdx.x, f = blockIdx.y;
   const size_t N = (size_t)nx * ny;
   const T *row = fld<T>(base, T0 + f, N) + (size_t)y * nx;
-  long long *out = sat_base(base, N) + (size_t)f * N + (size_t)y * nx;
+  long long *tab = sat_base(base, N) + (size_t)f * sat_stride(nx, ny);
+  long long *out = tab + (size_t)(y + 1) * (nx + 1) + 1;  // row y+1, column 1..nx
   const int e = reinterpret_cast<const int *>(scales + 24)[f];
   __shared__ long long wsum[8];
   __shared__ long long carry_sh;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) out[-1] = 0;  // column 0
+  if (y == 0)
+    for (int i = tid; i <= nx; i += 256) tab[i] = 0;  // row 0
   long long carry = 0;
   for (int b0 = 0; b0 < nx; b0 += 256) {
     const int x = b0 + tid;
@@ -431,11 +463,12 @@ __global__ void __launch_bounds__(256) k_sat_cols(double *base, int nx, int ny) 
   const int chunk = (ny + 7) / 8;
   const int y0 = min(ny, w * chunk), y1 = min(ny, y0 + chunk);
   const size_t N = (size_t)nx * ny;
-  long long *col = sat_base(base, N) + (size_t)f * N + x;
+  const size_t rs = (size_t)nx + 1;  // padded row length
+  long long *col = sat_base(base, N) + (size_t)f * sat_stride(nx, ny) + rs + 1 + x;
   __shared__ long long tot[8][32];
   long long s = 0;
   if (x < nx)
-    for (int y = y0; y < y1; ++y) s += col[(size_t)y * nx];
+    for (int y = y0; y < y1; ++y) s += col[(size_t)y * rs];
   tot[w][threadIdx.x] = s;
   __syncthreads();
   long long acc = 0;
@@ -445,25 +478,25 @@ __global__ void __launch_bounds__(256) k_sat_cols(double *base, int nx, int ny) 
     for (; y + 8 <= y1; y += 8) {
       long long v[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = col[(size_t)(y + k) * nx];
+      for (int k = 0; k < 8; ++k) v[k] = col[(size_t)(y + k) * rs];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         acc += v[k];
-        col[(size_t)(y + k) * nx] = acc;
+        col[(size_t)(y + k) * rs] = acc;
       }
     }
     for (; y < y1; ++y) {
-      acc += col[(size_t)y * nx];
-      col[(size_t)y * nx] = acc;
+      acc += col[(size_t)y * rs];
+      col[(size_t)y * rs] = acc;
     }
   }
 }
 
-// Exclusive prefix P(x, y) = sum over x' < x, y' < y (0 <= x <= nx,
-// 0 <= y <= ny) from the inclusive table S; modular (unsigned) arithmetic:
-// the periodic extension may exceed int64 in between, the box sum does not.
+// Exclusive prefix P(x, y) (0 <= x <= nx, 0 <= y <= ny) from a padded table;
+// modular (unsigned) arithmetic: the periodic extension may exceed int64 in
+// between, the box sum does not.
 __device__ __forceinline__ unsigned long long Pex(const long long *S, int nx, int x, int y) {
-  return (x == 0 || y == 0) ? 0ull : (unsigned long long)S[(size_t)(y - 1) * nx + (x - 1)];
+  return (unsigned long long)S[(size_t)y * (nx + 1) + x];
 }
 __device__ __forceinline__ unsigned long long Pext(const long long *S, int nx, int ny, int x,
                                                    int y) {
@@ -504,12 +537,13 @@ template <> __device__ float QConst::coef<float>() const { return coef_f; }
 constexpr int kQConstDoubles = 32 * 12 * (int)(sizeof(QConst) / sizeof(double));
 
 __global__ void k_query_consts(const double *scales, const int *meta, int nL,
-                               const long long *S, size_t N, QConst *consts) {
+                               const long long *S, int nx, int ny, QConst *consts) {
+  const size_t N = (size_t)nx * ny;
   const int t = threadIdx.x;
   if (t >= nL * 12) return;
   const int iL = t / 12, k = t % 12;
   const double area = (double)meta[8 * iL] * (double)meta[8 * iL];
-  const long long total = S[(size_t)k * N + N - 1];
+  const long long total = S[(size_t)k * sat_stride(nx, ny) + (size_t)ny * (nx + 1) + nx];
   const double inv = scales[12 + k];
   QConst q;
   q.mean_d = (double)total * inv / (double)N;
@@ -567,7 +601,8 @@ __global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
   const int iL = blockIdx.y, grp = blockIdx.z, k0 = 6 * grp;
   const int L = meta[8 * iL], nb = meta[8 * iL + 1], ooff = meta[8 * iL + 2];
   const size_t N = (size_t)nx * ny;
-  const long long *S = sat_base(base, N) + (size_t)k0 * N;
+  const size_t sp = sat_stride(nx, ny), rs = (size_t)nx + 1;
+  const long long *S = sat_base(base, N) + (size_t)k0 * sp;
   const QConst *qc = consts + (size_t)iL * 12 + k0;
   MT s1[6], s2[6];
 #pragma unroll
@@ -585,14 +620,21 @@ __global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
       x0 = b % nx;
       y0 = b / nx;
     }
+    const bool inside = x0 + L <= nx && y0 + L <= ny;
     MT lhs = 0, sum = 0, mx = 0;
     double *o = PER_BOX ? per_box + ((size_t)meta[8 * iL + 3] + b) * 15 : nullptr;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      const long long *Sk = S + (size_t)j * N;
-      const unsigned long long bs = Pext(Sk, nx, ny, x0 + L, y0 + L) -
-                                    Pext(Sk, nx, ny, x0, y0 + L) -
-                                    Pext(Sk, nx, ny, x0 + L, y0) + Pext(Sk, nx, ny, x0, y0);
+      const long long *Sk = S + (size_t)j * sp;
+      unsigned long long bs;
+      if (inside) {  // no periodic wrap: four direct corner loads
+        const long long *lo = Sk + (size_t)y0 * rs + x0, *hi = lo + (size_t)L * rs;
+        bs = (unsigned long long)hi[L] - (unsigned long long)hi[0] -
+             (unsigned long long)lo[L] + (unsigned long long)lo[0];
+      } else {
+        bs = Pext(Sk, nx, ny, x0 + L, y0 + L) - Pext(Sk, nx, ny, x0, y0 + L) -
+             Pext(Sk, nx, ny, x0 + L, y0) + Pext(Sk, nx, ny, x0, y0);
+      }
       const long long dq = (long long)(bs - (unsigned long long)qc[j].mq);
       const MT d = to_mt<MT>(dq) * qc[j].coef<MT>();
       const MT v = d + qc[j].mean<MT>();
@@ -765,7 +807,7 @@ cudaError_t diag_sat_and_query(const Member &hm, int precision, const int *meta_
     k_sat_rows<double><<<dim3(ny, 12), 256, 0, s>>>(sc.f, nx, ny, scales);
   }
   k_sat_cols<<<dim3((nx + 31) / 32, 12), dim3(32, 8), 0, s>>>(sc.f, nx, ny);
-  k_query_consts<<<1, 32 * 12, 0, s>>>(scales, meta_dev, nL, sat_base(sc.f, N), N, consts);
+  k_query_consts<<<1, 32 * 12, 0, s>>>(scales, meta_dev, nL, sat_base(sc.f, N), nx, ny, consts);
   // box lists: one box per thread; every periodic origin: about 16 per thread;
   // at most kMaxPartialBlocks CTAs per size
   const int per_cta = origins_dev ? 256 : 4096;
