@@ -100,6 +100,10 @@ typedef struct lbm_config {
                       first; 0 = same as precision.  Snapshots, summed-area
                       tables (exact 64-bit fixed point) and all reductions
                       are exact or FP64 in both cases. */
+  int diag_batch;  /* members whose balance diagnostic shares one set of
+                      launches (each needs its own scratch slot of about
+                      400 B per cell); 0 = as many as fit an 8 GiB budget.
+                      Results do not depend on it. */
   void *cuda_stream; /* cudaStream_t of all work; NULL = default stream */
 } lbm_config;
 

@@ -48,7 +48,8 @@ class _Config(ctypes.Structure):
     _fields_ = [("n_members", ctypes.c_int), ("members", ctypes.POINTER(_MemberCfg)),
                 ("precision", ctypes.c_int), ("storage", ctypes.c_int),
                 ("diag_every", ctypes.c_int), ("graph_steps", ctypes.c_int),
-                ("diag_precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("diag_precision", ctypes.c_int), ("diag_batch", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -134,7 +135,7 @@ class Lattice:
 
     def __init__(self, members: Sequence[Member], precision: int = 32, diag_every: int = 0,
                  graph_steps: int = 0, stream=None, device=None, diag_precision: int = 0,
-                 storage: int = 0):
+                 storage: int = 0, diag_batch: int = 0):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -145,7 +146,7 @@ class Lattice:
         arr = (_MemberCfg * len(self.members))(*[m.c() for m in self.members])
         self._arr = arr
         self._cfg = _Config(len(self.members), arr, precision, storage, diag_every, graph_steps,
-                            diag_precision, ctypes.c_void_p(self.stream.cuda_stream))
+                            diag_precision, diag_batch, ctypes.c_void_p(self.stream.cuda_stream))
         nbytes = ctypes.c_size_t()
         self._check(self.lib.lbm_workspace_size(ctypes.byref(self._cfg), ctypes.byref(nbytes)))
         self.workspace_bytes = nbytes.value
@@ -351,11 +352,11 @@ class Lattice:
 
 
 def workspace_size(members: Sequence[Member], precision: int = 32, diag_every: int = 0,
-                   graph_steps: int = 0) -> int:
+                   graph_steps: int = 0, diag_batch: int = 0) -> int:
     """Host-only query of the device workspace bytes for a configuration."""
     lib = load_library()
     arr = (_MemberCfg * len(members))(*[m.c() for m in members])
-    cfg = _Config(len(members), arr, precision, 0, diag_every, graph_steps, 0, None)
+    cfg = _Config(len(members), arr, precision, 0, diag_every, graph_steps, 0, diag_batch, None)
     n = ctypes.c_size_t()
     rc = lib.lbm_workspace_size(ctypes.byref(cfg), ctypes.byref(n))
     if rc != LBM_OK:

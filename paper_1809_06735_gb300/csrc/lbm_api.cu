@@ -22,7 +22,8 @@ using lbm::Tile;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMaxL = 32;          // box sizes per balance call
+constexpr int kMaxL = lbm::kDiagMaxL;  // box sizes per balance call
+constexpr size_t kDiagBatchBytes = (size_t)8 << 30;  // default scratch budget of a batch
 constexpr int kTileW = 128;        // cells per warp row in the vector kernel
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -32,7 +33,9 @@ thread_local std::string g_last_error = "no error";
 struct Layout {
   size_t members, tiles, status;
   std::vector<size_t> pop0, pop1, fx, fy, fx64, fy64, snap;
-  size_t scratch, partials, stats, Ls, out7, origins;
+  size_t scratch, partials, jpart, jobs, stats, Ls, out7, origins;
+  int diag_slots;          // members per batched diagnostic launch
+  size_t slot_doubles, jpart_doubles;
   size_t total;
   size_t Nmax;
   size_t origin_cap;  // boxes the origin buffer holds
@@ -56,6 +59,7 @@ int check_config(const lbm_config *cfg, std::string &err) {
   if (cfg->storage < 0 || cfg->storage > 2) { err = "storage must be 0 (tuned), 1 (AA) or 2 (double buffer)"; return LBM_ERR_ARG; }
   if (cfg->diag_precision != 0 && cfg->diag_precision != 32 && cfg->diag_precision != 64) { err = "diag_precision must be 0, 32 or 64"; return LBM_ERR_ARG; }
   if (cfg->diag_every < 0 || cfg->graph_steps < 0) { err = "diag_every and graph_steps must be >= 0"; return LBM_ERR_ARG; }
+  if (cfg->diag_batch < 0) { err = "diag_batch must be >= 0"; return LBM_ERR_ARG; }
   for (int m = 0; m < cfg->n_members; ++m) {
     const lbm_member_cfg &c = cfg->members[m];
     char buf[160];
@@ -113,8 +117,18 @@ Layout make_layout(const lbm_config *cfg) {
   size_t pad = 0;  // the 12 prefix tables carry one extra row and column
   for (int m = 0; m < n; ++m)
     pad = std::max(pad, (size_t)cfg->members[m].nx + cfg->members[m].ny + 1);
-  L.scratch = take(8 * (L.scratch_fields * L.Nmax + 12 * pad));
-  L.partials = take(8 * lbm::diag_partials_needed(kMaxL));
+  // slot 0 doubles as general staging (three snapshots, adjoint fields)
+  L.slot_doubles = std::max(lbm::diag_slot_doubles(L.Nmax, pad),
+                            (size_t)L.scratch_fields * L.Nmax);
+  L.jpart_doubles = lbm::diag_job_partials(L.Nmax, pad);
+  const size_t per_slot = 8 * (L.slot_doubles + L.jpart_doubles);
+  size_t slots = cfg->diag_batch > 0 ? (size_t)cfg->diag_batch
+                                     : std::max<size_t>(1, kDiagBatchBytes / per_slot);
+  L.diag_slots = (int)std::min<size_t>(slots, (size_t)n);
+  L.scratch = take(8 * L.slot_doubles * L.diag_slots);
+  L.partials = take(8 * (size_t)lbm::kGeneralPartials);
+  L.jpart = take(8 * L.jpart_doubles * L.diag_slots);
+  L.jobs = take(sizeof(lbm::DiagJob) * n);
   L.stats = take(8 * (size_t)n * kMaxL * 30);
   L.Ls = take(4 * 8 * (size_t)n * kMaxL);  // per-size meta rows {L, boxes, offsets, out row}
   L.out7 = take(8 * 8);
@@ -384,7 +398,10 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
   h->sc.f = reinterpret_cast<double *>(ws_at(h, lay.scratch));
   h->sc.N = lay.Nmax;
   h->sc.partials = reinterpret_cast<double *>(ws_at(h, lay.partials));
-  h->sc.npartials = lbm::diag_partials_needed(kMaxL);
+  h->sc.slots = lay.diag_slots;
+  h->sc.slot_doubles = lay.slot_doubles;
+  h->sc.jpart = reinterpret_cast<double *>(ws_at(h, lay.jpart));
+  h->sc.jpart_doubles = lay.jpart_doubles;
 
   auto cleanup = [&](int code) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -683,16 +700,43 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
   CK(cudaMemcpyAsync(meta_dev, meta.data(), 4 * meta.size(), cudaMemcpyHostToDevice, s));
   if (origins)
     CK(cudaMemcpyAsync(orig_dev, origins, 8 * total_boxes, cudaMemcpyHostToDevice, s));
+  // one job per member with at least one fitting size; batches of up to
+  // sc.slots jobs, each batch one set of ten launches
+  std::vector<lbm::DiagJob> jobs;
   for (int i = 0; i < nm; ++i) {
     if (where[i].empty()) continue;
     const int m = members[i];
-    CK(lbm::diag_terms(h->hm[m], h->diag_precision, snap_slot(h, m, (int)(t % 3)),
-                       snap_slot(h, m, (int)((t - 1) % 3)), snap_slot(h, m, (int)((t - 2) % 3)),
-                       h->sc, s));
-    CK(lbm::diag_sat_and_query(h->hm[m], h->diag_precision, meta_dev + (size_t)i * kMaxL * 8,
-                               (int)where[i].size(), maxb[i], orig_dev, h->sc, stats_dev,
-                               per_box_out, s));
-    h->launches += 11;  // 4 term passes, max, scales, 2 scans, constants, query, statistics
+    const Member &hm = h->hm[m];
+    const size_t slot = jobs.size() % (size_t)h->sc.slots;
+    lbm::DiagJob J{};
+    J.nx = hm.nx;
+    J.ny = hm.ny;
+    J.nu = hm.nu;
+    J.alpha = hm.alpha;
+    J.rho_ref = hm.rho0;
+    J.fxt = hm.fx_tab64;
+    J.fyt = hm.fy_tab64;
+    J.s0 = snap_slot(h, m, (int)(t % 3));
+    J.s1 = snap_slot(h, m, (int)((t - 1) % 3));
+    J.s2 = snap_slot(h, m, (int)((t - 2) % 3));
+    J.base = h->sc.f + slot * h->sc.slot_doubles;
+    J.part = h->sc.jpart + slot * h->sc.jpart_doubles;
+    J.meta = meta_dev + (size_t)i * kMaxL * 8;
+    J.nL = (int)where[i].size();
+    J.max_boxes = maxb[i];
+    J.qblocks = lbm::diag_query_blocks(maxb[i], origins != nullptr);
+    jobs.push_back(J);
+  }
+  if (!jobs.empty()) {
+    auto *jobs_dev = reinterpret_cast<lbm::DiagJob *>(ws_at(h, h->lay.jobs));
+    CK(cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(lbm::DiagJob) * jobs.size(),
+                       cudaMemcpyHostToDevice, s));
+    for (size_t j0 = 0; j0 < jobs.size(); j0 += (size_t)h->sc.slots) {
+      const int G = (int)std::min(jobs.size() - j0, (size_t)h->sc.slots);
+      CK(lbm::diag_balance(jobs.data() + j0, jobs_dev + j0, G, h->diag_precision, orig_dev,
+                           stats_dev, per_box_out, s));
+      h->launches += 10;  // 4 term passes, scales, 2 scans, constants, query, statistics
+    }
   }
   if (async) {
     CK(cudaEventRecord(h->ev_diag_done, h->diag_stream));

@@ -22,10 +22,16 @@
 // MT = double or float, again by handle precision; every block partial and
 // final statistic is FP64 and block-deterministic.
 //
-// Scratch (doubles of N = nx*ny cells): slots 0..2 a temporary snapshot,
+// Batching.  The balance diagnostic of a group of members runs as ten
+// launches in all (four term passes, scale exponents, two scans, query
+// constants, box query, statistics), blockIdx.z (or the CTA index of the
+// per-job kernels) selecting the member; each member has its own field slot
+// and partials slot.
+//
+// Field slot (doubles of N = nx*ny cells): slots 0..2 a temporary snapshot,
 // slots 3.. the term-stage fields (each slot holds N values of T), then the
-// 12 int64 tables of (nx+1)(ny+1) entries; reduction partials at
-// sc.partials.
+// 12 int64 tables of (nx+1)(ny+1) entries.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -101,11 +107,125 @@ __device__ __forceinline__ T Dy(const T *A, const Nb &nb) {
          T(1.0 / 280.0) * (c[nb.yo[8]] - c[nb.yo[0]]);
 }
 
+constexpr int kQStats = 14;  // per balance: [delta, delta^2, (d_k, d_k^2) for its 6 fields]
+
+// Per (size, field) constants of the query, computed once: the field mean,
+// the factor from a quantized sum to a box mean, and the quantized sum a box
+// of the mean value would have (so box deviations are exact integers).
+struct QConst {
+  double mean_d, coef_d;
+  float mean_f, coef_f;
+  long long mq;
+  template <typename MT>
+  __device__ MT mean() const;
+  template <typename MT>
+  __device__ MT coef() const;
+};
+template <> __device__ double QConst::mean<double>() const { return mean_d; }
+template <> __device__ float QConst::mean<float>() const { return mean_f; }
+template <> __device__ double QConst::coef<double>() const { return coef_d; }
+template <> __device__ float QConst::coef<float>() const { return coef_f; }
+constexpr int kQConstDoubles = kDiagMaxL * 12 * (int)(sizeof(QConst) / sizeof(double));
+constexpr int kMaxQueryBlocks = 256;  // CTAs per (job, size, balance)
+
+// Per-job partials slot, in 8-byte words: [0, 32) scale factors and
+// exponents; the per-size query constants; the query CTA partials; then the
+// CTA maxima of the 12 term fields, [12][CTAs of the cell grid].
+constexpr size_t kPartScales = 0;
+constexpr size_t kPartConsts = 32;
+constexpr size_t kPartQuery = kPartConsts + kQConstDoubles;
+constexpr size_t kPartMax = kPartQuery + (size_t)kDiagMaxL * 2 * kMaxQueryBlocks * kQStats;
+
 #define CELL_INDEX                                        \
   const int x = blockIdx.x * blockDim.x + threadIdx.x;    \
   const int y = blockIdx.y * blockDim.y + threadIdx.y;    \
   if (x >= g.nx || y >= g.ny) return;                     \
   const size_t c = (size_t)y * g.nx + x;
+
+// Cell passes of the batched diagnostic: CTAs of 32 x 8 cells, blockIdx.z
+// the job.  A CTA wholly outside its job's grid returns at once; threads
+// past a ragged edge stay (valid = false) for the CTA-wide reductions.
+#define JOB_CELLS                                                            \
+  const DiagJob &J = jobs[blockIdx.z];                                       \
+  if ((int)(blockIdx.x * 32) >= J.nx || (int)(blockIdx.y * 8) >= J.ny) return; \
+  const Grid g = job_grid(J);                                                \
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y; \
+  const bool valid = x < g.nx && y < g.ny;                                   \
+  const size_t N = (size_t)g.nx * g.ny, c = (size_t)y * g.nx + x;            \
+  double *base = J.base;                                                     \
+  const int nbx = (g.nx + 31) / 32, nblk = nbx * ((g.ny + 7) / 8);           \
+  const int blk = blockIdx.y * nbx + blockIdx.x;
+
+__device__ __forceinline__ Grid job_grid(const DiagJob &J) {
+  Grid g;
+  g.nx = J.nx;
+  g.ny = J.ny;
+  g.nu = J.nu;
+  g.alpha = J.alpha;
+  g.rho_ref = J.rho_ref;
+  g.fxt = J.fxt;
+  g.fyt = J.fyt;
+  return g;
+}
+
+template <typename T>
+struct AbsBits;  // |v| as an unsigned integer that orders like |v|
+template <>
+struct AbsBits<float> {
+  using U = unsigned;
+  __device__ static U of(float v) {
+    const U b = __float_as_uint(v) & 0x7fffffffu;
+    return b > 0x7f800000u ? 0u : b;  // NaN counts as 0, as fmax does
+  }
+  __device__ static U warp_max(U b) { return __reduce_max_sync(0xffffffffu, b); }
+  __device__ static double value(U b) { return (double)__uint_as_float(b); }
+};
+template <>
+struct AbsBits<double> {
+  using U = unsigned long long;
+  __device__ static U of(double v) {
+    const U b = (U)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    return b > 0x7ff0000000000000ull ? 0ull : b;
+  }
+  __device__ static U warp_max(U b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const U n = __shfl_xor_sync(0xffffffffu, b, o);
+      b = n > b ? n : b;
+    }
+    return b;
+  }
+  __device__ static double value(U b) { return __longlong_as_double((long long)b); }
+};
+
+// Row f of the CTA maxima of term field f (bit patterns of |T_f|).
+template <typename T>
+__device__ __forceinline__ typename AbsBits<T>::U *max_part(const DiagJob &J) {
+  return reinterpret_cast<typename AbsBits<T>::U *>(J.part + kPartMax);
+}
+
+// Largest |v| over the CTA of K term fields (fields f[k]), stored at the
+// CTA's slot of each field's row of maxima.  Every thread of the CTA calls it.
+template <typename T, int K>
+__device__ __forceinline__ void block_absmax(const T (&v)[K], const int (&f)[K],
+                                             const DiagJob &J, int blk, int nblk) {
+  using AB = AbsBits<T>;
+  __shared__ typename AB::U sh[K][8];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const typename AB::U b = AB::warp_max(AB::of(v[k]));
+    if (threadIdx.x == 0) sh[k][threadIdx.y] = b;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (threadIdx.y == 0 && threadIdx.x == k) {
+      typename AB::U m = sh[k][0];
+      for (int i = 1; i < 8; ++i) m = sh[k][i] > m ? sh[k][i] : m;
+      max_part<T>(J)[(size_t)f[k] * nblk + blk] = m;
+    }
+  }
+}
 
 // Pass 0 (pointwise).  u = (j + F/2)/rho with F = F_ext - alpha j, i.e.
 // rho u = m = (1 - alpha/2) j + F_ext/2.  Differences between levels:
@@ -114,40 +234,50 @@ __device__ __forceinline__ T Dy(const T *A, const Nb &nb) {
 // E^0 - E^1 = [drho |u^0|^2 + rho^1 du . (2 u^0 - du)] / 2, and
 // LHS^E = (3 (E^0 - E^1) - (E^1 - E^2)) / 2 = eq. (17).
 template <typename T>
-__global__ void k_prep(Grid g, const double *s0, const double *s1, const double *s2,
-                       double *base, size_t N) {
-  CELL_INDEX;
-  const double r0d = s0[c], r1d = s1[c], r2d = s2[c];
-  const double jx0d = s0[N + c], jy0d = s0[2 * N + c];
-  const T dr01 = (T)(r0d - r1d), dr12 = (T)(r1d - r2d);
-  const T djx01 = (T)(jx0d - s1[N + c]), djy01 = (T)(jy0d - s1[2 * N + c]);
-  const T djx12 = (T)(s1[N + c] - s2[N + c]), djy12 = (T)(s1[2 * N + c] - s2[2 * N + c]);
-  const T r0 = (T)r0d, r1 = (T)r1d, r2 = (T)r2d;
-  const T jx0 = (T)jx0d, jy0 = (T)jy0d;
-  const T a = (T)g.alpha, ca = T(1) - T(0.5) * a;
-  const T Fx = (T)g.fxt[y] - a * jx0, Fy = (T)g.fyt[x] - a * jy0;
-  const T u0 = (jx0 + T(0.5) * Fx) / r0, v0 = (jy0 + T(0.5) * Fy) / r0;
-  const T du01 = (ca * djx01 - u0 * dr01) / r1, dv01 = (ca * djy01 - v0 * dr01) / r1;
-  const T u1 = u0 - du01, v1 = v0 - dv01;
-  const T du12 = (ca * djx12 - u1 * dr12) / r2, dv12 = (ca * djy12 - v1 * dr12) / r2;
-  const T q0 = u0 * u0 + v0 * v0, q1 = u1 * u1 + v1 * v1;
-  const T dE01 = T(0.5) * (dr01 * q0 + r1 * (du01 * (T(2) * u0 - du01) + dv01 * (T(2) * v0 - dv01)));
-  const T dE12 = T(0.5) * (dr12 * q1 + r2 * (du12 * (T(2) * u1 - du12) + dv12 * (T(2) * v1 - dv12)));
-  const T E0 = T(0.5) * r0 * q0;
-  fld<T>(base, U0X, N)[c] = u0;
-  fld<T>(base, U0Y, N)[c] = v0;
-  fld<T>(base, DU01X, N)[c] = du01;
-  fld<T>(base, DU01Y, N)[c] = dv01;
-  fld<T>(base, DU12X, N)[c] = du12;
-  fld<T>(base, DU12Y, N)[c] = dv12;
-  fld<T>(base, DRHO, N)[c] = (T)(r0d - g.rho_ref);
-  fld<T>(base, R0, N)[c] = r0;
-  fld<T>(base, FXR, N)[c] = Fx / r0;
-  fld<T>(base, FYR, N)[c] = Fy / r0;
-  fld<T>(base, A1, N)[c] = E0 * u0;
-  fld<T>(base, A2, N)[c] = E0 * v0;
-  fld<T>(base, T0 + 0, N)[c] = T(0.5) * (T(3) * dE01 - dE12);  // LHS^E
-  fld<T>(base, T0 + 3, N)[c] = u0 * Fx + v0 * Fy;                // RHS^{E,3} = u . F
+__global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) {
+  JOB_CELLS;
+  T lhs = 0, uf = 0;
+  if (valid) {
+    const double *s0 = J.s0, *s1 = J.s1, *s2 = J.s2;
+    const double r0d = s0[c], r1d = s1[c], r2d = s2[c];
+    const double jx0d = s0[N + c], jy0d = s0[2 * N + c];
+    const T dr01 = (T)(r0d - r1d), dr12 = (T)(r1d - r2d);
+    const T djx01 = (T)(jx0d - s1[N + c]), djy01 = (T)(jy0d - s1[2 * N + c]);
+    const T djx12 = (T)(s1[N + c] - s2[N + c]), djy12 = (T)(s1[2 * N + c] - s2[2 * N + c]);
+    const T r0 = (T)r0d, r1 = (T)r1d, r2 = (T)r2d;
+    const T jx0 = (T)jx0d, jy0 = (T)jy0d;
+    const T a = (T)g.alpha, ca = T(1) - T(0.5) * a;
+    const T Fx = (T)g.fxt[y] - a * jx0, Fy = (T)g.fyt[x] - a * jy0;
+    const T u0 = (jx0 + T(0.5) * Fx) / r0, v0 = (jy0 + T(0.5) * Fy) / r0;
+    const T du01 = (ca * djx01 - u0 * dr01) / r1, dv01 = (ca * djy01 - v0 * dr01) / r1;
+    const T u1 = u0 - du01, v1 = v0 - dv01;
+    const T du12 = (ca * djx12 - u1 * dr12) / r2, dv12 = (ca * djy12 - v1 * dr12) / r2;
+    const T q0 = u0 * u0 + v0 * v0, q1 = u1 * u1 + v1 * v1;
+    const T dE01 =
+        T(0.5) * (dr01 * q0 + r1 * (du01 * (T(2) * u0 - du01) + dv01 * (T(2) * v0 - dv01)));
+    const T dE12 =
+        T(0.5) * (dr12 * q1 + r2 * (du12 * (T(2) * u1 - du12) + dv12 * (T(2) * v1 - dv12)));
+    const T E0 = T(0.5) * r0 * q0;
+    lhs = T(0.5) * (T(3) * dE01 - dE12);  // LHS^E
+    uf = u0 * Fx + v0 * Fy;               // RHS^{E,3} = u . F
+    fld<T>(base, U0X, N)[c] = u0;
+    fld<T>(base, U0Y, N)[c] = v0;
+    fld<T>(base, DU01X, N)[c] = du01;
+    fld<T>(base, DU01Y, N)[c] = dv01;
+    fld<T>(base, DU12X, N)[c] = du12;
+    fld<T>(base, DU12Y, N)[c] = dv12;
+    fld<T>(base, DRHO, N)[c] = (T)(r0d - g.rho_ref);
+    fld<T>(base, R0, N)[c] = r0;
+    fld<T>(base, FXR, N)[c] = Fx / r0;
+    fld<T>(base, FYR, N)[c] = Fy / r0;
+    fld<T>(base, A1, N)[c] = E0 * u0;
+    fld<T>(base, A2, N)[c] = E0 * v0;
+    fld<T>(base, T0 + 0, N)[c] = lhs;
+    fld<T>(base, T0 + 3, N)[c] = uf;
+  }
+  const T mv[2] = {lhs, uf};
+  const int mf[2] = {0, 3};
+  block_absmax<T, 2>(mv, mf, J, blk, nblk);
 }
 
 // Pass 1 (radius 4): vorticity w = D_x u_y - D_y u_x and its level
@@ -156,67 +286,91 @@ __global__ void k_prep(Grid g, const double *s0, const double *s1, const double 
 // (grad p = grad(rho - rho_ref)/3), RHS^{E,4}, RHS^{O,2}, RHS^{O,3};
 // fluxes for pass 2.
 template <typename T>
-__global__ void k_grad(Grid g, double *base, size_t N) {
-  CELL_INDEX;
-  const Nb nb = make_nb(g, x, y);
-  const T *U = fld<T>(base, U0X, N), *V = fld<T>(base, U0Y, N);
-  const T w0 = Dx(V, nb) - Dy(U, nb);
-  const T dw01 = Dx(fld<T>(base, DU01Y, N), nb) - Dy(fld<T>(base, DU01X, N), nb);
-  const T dw12 = Dx(fld<T>(base, DU12Y, N), nb) - Dy(fld<T>(base, DU12X, N), nb);
-  const T w1 = w0 - dw01;
-  const T dO01 = T(0.5) * dw01 * (T(2) * w0 - dw01);
-  const T dO12 = T(0.5) * dw12 * (T(2) * w1 - dw12);
-  fld<T>(base, T0 + 6, N)[c] = T(0.5) * (T(3) * dO01 - dO12);  // LHS^Omega
-  const T Om = T(0.5) * w0 * w0;
-  const T dxu = Dx(U, nb), dyu = Dy(U, nb);
-  const T dxv = Dx(V, nb), dyv = Dy(V, nb);
-  const T u = U[c], v = V[c], r = fld<T>(base, R0, N)[c];
-  const T sxx = T(2) * dxu, sxy = dyu + dxv, syy = T(2) * dyv;  // S_ij = d_j u_i + d_i u_j
-  const T nr = (T)g.nu * r;
-  const T *DR = fld<T>(base, DRHO, N);
-  fld<T>(base, T0 + 2, N)[c] = -(u * Dx(DR, nb) + v * Dy(DR, nb)) / T(3);
-  fld<T>(base, T0 + 4, N)[c] = -nr * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
-  fld<T>(base, T0 + 8, N)[c] = -Om * (dxu + dyv);
-  fld<T>(base, T0 + 9, N)[c] =
-      w0 * (Dx(fld<T>(base, FYR, N), nb) - Dy(fld<T>(base, FXR, N), nb));
-  fld<T>(base, WW, N)[c] = w0;
-  fld<T>(base, B1, N)[c] = Om * u;
-  fld<T>(base, B2, N)[c] = Om * v;
-  fld<T>(base, C1, N)[c] = nr * (u * sxx + v * sxy);
-  fld<T>(base, C2, N)[c] = nr * (u * sxy + v * syy);
-  fld<T>(base, G1, N)[c] = nr * sxx;
-  fld<T>(base, G2, N)[c] = nr * sxy;
-  fld<T>(base, G3, N)[c] = nr * syy;
+__global__ void __launch_bounds__(256) k_grad(const DiagJob *__restrict__ jobs) {
+  JOB_CELLS;
+  T t2 = 0, t4 = 0, t6 = 0, t8 = 0, t9 = 0;
+  if (valid) {
+    const Nb nb = make_nb(g, x, y);
+    const T *U = fld<T>(base, U0X, N), *V = fld<T>(base, U0Y, N);
+    const T w0 = Dx(V, nb) - Dy(U, nb);
+    const T dw01 = Dx(fld<T>(base, DU01Y, N), nb) - Dy(fld<T>(base, DU01X, N), nb);
+    const T dw12 = Dx(fld<T>(base, DU12Y, N), nb) - Dy(fld<T>(base, DU12X, N), nb);
+    const T w1 = w0 - dw01;
+    const T dO01 = T(0.5) * dw01 * (T(2) * w0 - dw01);
+    const T dO12 = T(0.5) * dw12 * (T(2) * w1 - dw12);
+    t6 = T(0.5) * (T(3) * dO01 - dO12);  // LHS^Omega
+    const T Om = T(0.5) * w0 * w0;
+    const T dxu = Dx(U, nb), dyu = Dy(U, nb);
+    const T dxv = Dx(V, nb), dyv = Dy(V, nb);
+    const T u = U[c], v = V[c], r = fld<T>(base, R0, N)[c];
+    const T sxx = T(2) * dxu, sxy = dyu + dxv, syy = T(2) * dyv;  // S_ij = d_j u_i + d_i u_j
+    const T nr = (T)g.nu * r;
+    const T *DR = fld<T>(base, DRHO, N);
+    t2 = -(u * Dx(DR, nb) + v * Dy(DR, nb)) / T(3);
+    t4 = -nr * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
+    t8 = -Om * (dxu + dyv);
+    t9 = w0 * (Dx(fld<T>(base, FYR, N), nb) - Dy(fld<T>(base, FXR, N), nb));
+    fld<T>(base, T0 + 6, N)[c] = t6;
+    fld<T>(base, T0 + 2, N)[c] = t2;
+    fld<T>(base, T0 + 4, N)[c] = t4;
+    fld<T>(base, T0 + 8, N)[c] = t8;
+    fld<T>(base, T0 + 9, N)[c] = t9;
+    fld<T>(base, WW, N)[c] = w0;
+    fld<T>(base, B1, N)[c] = Om * u;
+    fld<T>(base, B2, N)[c] = Om * v;
+    fld<T>(base, C1, N)[c] = nr * (u * sxx + v * sxy);
+    fld<T>(base, C2, N)[c] = nr * (u * sxy + v * syy);
+    fld<T>(base, G1, N)[c] = nr * sxx;
+    fld<T>(base, G2, N)[c] = nr * sxy;
+    fld<T>(base, G3, N)[c] = nr * syy;
+  }
+  const T mv[5] = {t2, t4, t6, t8, t9};
+  const int mf[5] = {2, 4, 6, 8, 9};
+  block_absmax<T, 5>(mv, mf, J, blk, nblk);
 }
 
 // Pass 2 (radius 4): RHS^{E,1}, RHS^{E,5}, RHS^{O,1}; H_i = d_j(nu rho S_ij)/rho;
 // RHS^{O,4} = H_x d_y w - H_y d_x w; products w H for pass 3.
 template <typename T>
-__global__ void k_flux(Grid g, double *base, size_t N) {
-  CELL_INDEX;
-  const Nb nb = make_nb(g, x, y);
-  const T r = fld<T>(base, R0, N)[c];
-  fld<T>(base, T0 + 1, N)[c] =
-      -(Dx(fld<T>(base, A1, N), nb) + Dy(fld<T>(base, A2, N), nb));
-  fld<T>(base, T0 + 5, N)[c] = Dx(fld<T>(base, C1, N), nb) + Dy(fld<T>(base, C2, N), nb);
-  fld<T>(base, T0 + 7, N)[c] =
-      -(Dx(fld<T>(base, B1, N), nb) + Dy(fld<T>(base, B2, N), nb));
-  const T Hx = (Dx(fld<T>(base, G1, N), nb) + Dy(fld<T>(base, G2, N), nb)) / r;
-  const T Hy = (Dx(fld<T>(base, G2, N), nb) + Dy(fld<T>(base, G3, N), nb)) / r;
-  const T *W = fld<T>(base, WW, N);
-  fld<T>(base, T0 + 10, N)[c] = Hx * Dy(W, nb) - Hy * Dx(W, nb);
-  const T w = W[c];
-  fld<T>(base, K1, N)[c] = w * Hy;
-  fld<T>(base, K2, N)[c] = w * Hx;
+__global__ void __launch_bounds__(256) k_flux(const DiagJob *__restrict__ jobs) {
+  JOB_CELLS;
+  T t1 = 0, t5 = 0, t7 = 0, t10 = 0;
+  if (valid) {
+    const Nb nb = make_nb(g, x, y);
+    const T r = fld<T>(base, R0, N)[c];
+    t1 = -(Dx(fld<T>(base, A1, N), nb) + Dy(fld<T>(base, A2, N), nb));
+    t5 = Dx(fld<T>(base, C1, N), nb) + Dy(fld<T>(base, C2, N), nb);
+    t7 = -(Dx(fld<T>(base, B1, N), nb) + Dy(fld<T>(base, B2, N), nb));
+    const T Hx = (Dx(fld<T>(base, G1, N), nb) + Dy(fld<T>(base, G2, N), nb)) / r;
+    const T Hy = (Dx(fld<T>(base, G2, N), nb) + Dy(fld<T>(base, G3, N), nb)) / r;
+    const T *W = fld<T>(base, WW, N);
+    t10 = Hx * Dy(W, nb) - Hy * Dx(W, nb);
+    const T w = W[c];
+    fld<T>(base, T0 + 1, N)[c] = t1;
+    fld<T>(base, T0 + 5, N)[c] = t5;
+    fld<T>(base, T0 + 7, N)[c] = t7;
+    fld<T>(base, T0 + 10, N)[c] = t10;
+    fld<T>(base, K1, N)[c] = w * Hy;
+    fld<T>(base, K2, N)[c] = w * Hx;
+  }
+  const T mv[4] = {t1, t5, t7, t10};
+  const int mf[4] = {1, 5, 7, 10};
+  block_absmax<T, 4>(mv, mf, J, blk, nblk);
 }
 
 // Pass 3 (radius 4): RHS^{O,5} = d_x (w H_y) - d_y (w H_x).
 template <typename T>
-__global__ void k_curl(Grid g, double *base, size_t N) {
-  CELL_INDEX;
-  const Nb nb = make_nb(g, x, y);
-  fld<T>(base, T0 + 11, N)[c] =
-      Dx(fld<T>(base, K1, N), nb) - Dy(fld<T>(base, K2, N), nb);
+__global__ void __launch_bounds__(256) k_curl(const DiagJob *__restrict__ jobs) {
+  JOB_CELLS;
+  T t11 = 0;
+  if (valid) {
+    const Nb nb = make_nb(g, x, y);
+    t11 = Dx(fld<T>(base, K1, N), nb) - Dy(fld<T>(base, K2, N), nb);
+    fld<T>(base, T0 + 11, N)[c] = t11;
+  }
+  const T mv[1] = {t11};
+  const int mf[1] = {11};
+  block_absmax<T, 1>(mv, mf, J, blk, nblk);
 }
 
 // ---------------------------------------------------------------------------
@@ -338,46 +492,32 @@ __global__ void k_global_scale(double *sums, size_t N) {
 // Exact fixed-point summed-area tables
 // ---------------------------------------------------------------------------
 
-// Largest magnitude of each term field: block partial maxima (order-free).
+// Scale exponents, one CTA per job and one warp per field: e_f with
+// N * max|T_f| * 2^e_f < 2^62 (so every partial sum of the table fits in
+// int64), capped so that 2^e_f is a finite float.  scales[f] = 2^e_f,
+// scales[12 + f] = 2^-e_f, and the exponent itself as ((int *)(scales + 24))[f].
 template <typename T>
-__global__ void k_absmax(double *base, size_t N, double *partials) {
-  const int f = blockIdx.y;
-  const T *A = fld<T>(base, T0 + f, N);
-  T m = T(0);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (size_t)gridDim.x * blockDim.x)
-    m = fmax(m, fabs(A[i]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-  __shared__ T sh[32];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, sh[k]);
-    partials[(size_t)f * gridDim.x + blockIdx.x] = (double)m;
-  }
-}
-
-// Scale exponents, one warp per field: e_f with N * max|T_f| * 2^e_f < 2^62
-// (so every partial sum of the table fits in int64), capped so that 2^e_f is
-// a finite float.  scales[f] = 2^e_f, scales[12 + f] = 2^-e_f, and the
-// exponent itself as ((int *)(scales + 24))[f].
-__global__ void k_scales(const double *partials, int nb, size_t N, double *scales) {
+__global__ void k_scales(const DiagJob *__restrict__ jobs) {
+  const DiagJob &J = jobs[blockIdx.x];
   const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (f >= 12) return;
-  double m = 0.0;
-  for (int b = lane; b < nb; b += 32) m = fmax(m, partials[(size_t)f * nb + b]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  const size_t N = (size_t)J.nx * J.ny;
+  const int nblk = ((J.nx + 31) / 32) * ((J.ny + 7) / 8);
+  const typename AbsBits<T>::U *mb = max_part<T>(J) + (size_t)f * nblk;
+  typename AbsBits<T>::U b = 0;
+  for (int i = lane; i < nblk; i += 32) b = mb[i] > b ? mb[i] : b;
+  b = AbsBits<T>::warp_max(b);
   if (lane == 0) {
+    const double m = AbsBits<T>::value(b);
     int e = 0;
-    if (m > 0.0) {
+    if (m > 0.0 && m <= 1.7e308) {
       int ex, nbits = 0;
       frexp(m, &ex);  // m < 2^ex
       while (((size_t)1 << nbits) < N) ++nbits;
       e = 62 - nbits - ex;
       if (e > 120) e = 120;
     }
+    double *scales = J.part + kPartScales;
     scales[f] = ldexp(1.0, e);
     scales[12 + f] = ldexp(1.0, -e);
     reinterpret_cast<int *>(scales + 24)[f] = e;
@@ -413,16 +553,17 @@ __device__ __forceinline__ long long quantize(double v, int e) {
   return __double2ll_rn(ldexp(v, e));
 }
 
-// Quantize and scan along x, one CTA (256 threads) per (row, field).
+// Quantize and scan along x, one CTA (256 threads) per (row, field, job).
 template <typename T>
-__global__ void __launch_bounds__(256) k_sat_rows(double *base, int nx, int ny,
-                                                  const double *scales) {
-  const int y = blockIdx.x, f = blockIdx.y;
+__global__ void __launch_bounds__(256) k_sat_rows(const DiagJob *__restrict__ jobs) {
+  const DiagJob &J = jobs[blockIdx.z];
+  const int y = blockIdx.x, f = blockIdx.y, nx = J.nx, ny = J.ny;
+  if (y >= ny) return;
   const size_t N = (size_t)nx * ny;
-  const T *row = fld<T>(base, T0 + f, N) + (size_t)y * nx;
-  long long *tab = sat_base(base, N) + (size_t)f * sat_stride(nx, ny);
+  const T *row = fld<T>(J.base, T0 + f, N) + (size_t)y * nx;
+  long long *tab = sat_base(J.base, N) + (size_t)f * sat_stride(nx, ny);
   long long *out = tab + (size_t)(y + 1) * (nx + 1) + 1;  // row y+1, column 1..nx
-  const int e = reinterpret_cast<const int *>(scales + 24)[f];
+  const int e = reinterpret_cast<const int *>(J.part + kPartScales + 24)[f];
   __shared__ long long wsum[8];
   __shared__ long long carry_sh;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -456,7 +597,10 @@ __global__ void __launch_bounds__(256) k_sat_rows(double *base, int nx, int ny,
 
 // Scan along y over a strip of 32 columns: the 8 warps sum one chunk of rows
 // each, exchange chunk totals in shared memory, then rewrite their chunk.
-__global__ void __launch_bounds__(256) k_sat_cols(double *base, int nx, int ny) {
+__global__ void __launch_bounds__(256) k_sat_cols(const DiagJob *__restrict__ jobs) {
+  const DiagJob &J = jobs[blockIdx.z];
+  const int nx = J.nx, ny = J.ny;
+  if ((int)(blockIdx.x * 32) >= nx) return;
   const int f = blockIdx.y;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int w = threadIdx.y;
@@ -464,7 +608,7 @@ __global__ void __launch_bounds__(256) k_sat_cols(double *base, int nx, int ny) 
   const int y0 = min(ny, w * chunk), y1 = min(ny, y0 + chunk);
   const size_t N = (size_t)nx * ny;
   const size_t rs = (size_t)nx + 1;  // padded row length
-  long long *col = sat_base(base, N) + (size_t)f * sat_stride(nx, ny) + rs + 1 + x;
+  long long *col = sat_base(J.base, N) + (size_t)f * sat_stride(nx, ny) + rs + 1 + x;
   __shared__ long long tot[8][32];
   long long s = 0;
   if (x < nx)
@@ -516,42 +660,25 @@ __device__ __forceinline__ MT delta_of(MT lhs, MT sum, MT mx) {
   return num / mx;
 }
 
-constexpr int kQStats = 14;  // per balance: [delta, delta^2, (d_k, d_k^2) for its 6 fields]
-
-// Per (size, field) constants of the query, computed once: the field mean,
-// the factor from a quantized sum to a box mean, and the quantized sum a box
-// of the mean value would have (so box deviations are exact integers).
-struct QConst {
-  double mean_d, coef_d;
-  float mean_f, coef_f;
-  long long mq;
-  template <typename MT>
-  __device__ MT mean() const;
-  template <typename MT>
-  __device__ MT coef() const;
-};
-template <> __device__ double QConst::mean<double>() const { return mean_d; }
-template <> __device__ float QConst::mean<float>() const { return mean_f; }
-template <> __device__ double QConst::coef<double>() const { return coef_d; }
-template <> __device__ float QConst::coef<float>() const { return coef_f; }
-constexpr int kQConstDoubles = 32 * 12 * (int)(sizeof(QConst) / sizeof(double));
-
-__global__ void k_query_consts(const double *scales, const int *meta, int nL,
-                               const long long *S, int nx, int ny, QConst *consts) {
-  const size_t N = (size_t)nx * ny;
+// One CTA per job, one thread per (size, field).
+__global__ void k_query_consts(const DiagJob *__restrict__ jobs) {
+  const DiagJob &J = jobs[blockIdx.x];
   const int t = threadIdx.x;
-  if (t >= nL * 12) return;
+  if (t >= J.nL * 12) return;
+  const int nx = J.nx, ny = J.ny;
+  const size_t N = (size_t)nx * ny;
   const int iL = t / 12, k = t % 12;
-  const double area = (double)meta[8 * iL] * (double)meta[8 * iL];
-  const long long total = S[(size_t)k * sat_stride(nx, ny) + (size_t)ny * (nx + 1) + nx];
-  const double inv = scales[12 + k];
+  const double area = (double)J.meta[8 * iL] * (double)J.meta[8 * iL];
+  const long long total =
+      sat_base(J.base, N)[(size_t)k * sat_stride(nx, ny) + (size_t)ny * (nx + 1) + nx];
+  const double inv = J.part[kPartScales + 12 + k];
   QConst q;
   q.mean_d = (double)total * inv / (double)N;
   q.coef_d = inv / area;
   q.mean_f = (float)q.mean_d;
   q.coef_f = (float)q.coef_d;
   q.mq = __double2ll_rn((double)total * area / (double)N);
-  consts[t] = q;
+  reinterpret_cast<QConst *>(J.part + kPartConsts)[t] = q;
 }
 
 // 64-bit integer to the query precision.  The float version assembles the
@@ -585,25 +712,27 @@ __device__ __forceinline__ float to_mt<float>(long long v) {
   return __uint_as_float(bits);
 }
 
-// Per size, meta[8*iL] = {L, n_boxes, origin offset (-1: all periodic
-// origins), per-box row offset, statistics output row, 3 unused}.  blockIdx.z selects the balance: 0 = energy
-// (fields 0..5: LHS^E, RHS^{E,1..5}), 1 = enstrophy (fields 6..11: LHS^O,
-// RHS^{O,1..5}; RHS^{O,6} is identically 0 in 2D and adds nothing).
-// One thread per (box, balance): exact integer box sums of its 6 term
-// fields, their deviations d_k from the field means, the box means, the
-// balancing error, and sums of d_k, d_k^2, delta and delta^2.
+// Grid (query CTAs, sizes, 2 x jobs); blockIdx.z = 2 * job + balance, the
+// balance 0 = energy (fields 0..5: LHS^E, RHS^{E,1..5}), 1 = enstrophy
+// (fields 6..11: LHS^O, RHS^{O,1..5}; RHS^{O,6} is identically 0 in 2D and
+// adds nothing).  One thread per (box, balance): exact integer box sums of
+// its 6 term fields, their deviations d_k from the field means, the box
+// means, the balancing error, and sums of d_k, d_k^2, delta and delta^2.
 template <typename MT, bool PER_BOX>
-__global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
-                                               const QConst *__restrict__ consts,
-                                               const int *__restrict__ meta,
+__global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
                                                const int *__restrict__ origins,
-                                               double *partials, double *per_box) {
-  const int iL = blockIdx.y, grp = blockIdx.z, k0 = 6 * grp;
+                                               double *per_box) {
+  const DiagJob &J = jobs[blockIdx.z >> 1];
+  const int iL = blockIdx.y, grp = blockIdx.z & 1, k0 = 6 * grp;
+  if (iL >= J.nL || (int)blockIdx.x >= J.qblocks) return;
+  const int qb = J.qblocks;
+  const int nx = J.nx, ny = J.ny;
+  const int *meta = J.meta;
   const int L = meta[8 * iL], nb = meta[8 * iL + 1], ooff = meta[8 * iL + 2];
   const size_t N = (size_t)nx * ny;
   const size_t sp = sat_stride(nx, ny), rs = (size_t)nx + 1;
-  const long long *S = sat_base(base, N) + (size_t)k0 * sp;
-  const QConst *qc = consts + (size_t)iL * 12 + k0;
+  const long long *S = sat_base(J.base, N) + (size_t)k0 * sp;
+  const QConst *qc = reinterpret_cast<const QConst *>(J.part + kPartConsts) + (size_t)iL * 12 + k0;
   MT s1[6], s2[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
@@ -611,7 +740,7 @@ __global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
     s2[j] = MT(0);
   }
   MT d1 = 0, d2 = 0;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += qb * blockDim.x) {
     int x0, y0;
     if (ooff >= 0) {
       x0 = origins[2 * (ooff + b)];
@@ -665,15 +794,19 @@ __global__ void __launch_bounds__(256) k_query(double *base, int nx, int ny,
     acc[3 + 2 * j] = s2[j];
   }
   block_sum_store_mt<kQStats, MT>(
-      acc, partials + (((size_t)iL * 2 + grp) * gridDim.x + blockIdx.x) * kQStats);
+      acc, J.part + kPartQuery + (((size_t)iL * 2 + grp) * qb + blockIdx.x) * kQStats);
 }
 
 // Mean and population standard deviation of the 15 quantities per size.
-// One CTA per size; 8 threads per (balance, slot) sum interleaved block
+// Grid (sizes, jobs); 8 threads per (balance, slot) sum interleaved block
 // partials in a fixed order.
-__global__ void k_stats_final(const double *partials, int nblocks, const QConst *consts,
-                              const int *meta, double *stats) {
+__global__ void k_stats_final(const DiagJob *__restrict__ jobs, double *stats) {
+  const DiagJob &J = jobs[blockIdx.y];
   const int iL = blockIdx.x;
+  if (iL >= J.nL) return;
+  const int nblocks = J.qblocks;
+  const double *partials = J.part + kPartQuery;
+  const QConst *consts = reinterpret_cast<const QConst *>(J.part + kPartConsts);
   const int q = threadIdx.x >> 3, j = threadIdx.x & 7;  // q = grp * 14 + slot
   __shared__ double sh[2 * kQStats][8];
   double a = 0.0;
@@ -686,8 +819,8 @@ __global__ void k_stats_final(const double *partials, int nblocks, const QConst 
   __syncthreads();
   const int t = threadIdx.x;
   if (t < 15) {
-    const int nb = meta[8 * iL + 1];
-    const size_t orow = (size_t)meta[8 * iL + 4];
+    const int nb = J.meta[8 * iL + 1];
+    const size_t orow = (size_t)J.meta[8 * iL + 4];
     double mean = 0.0, sd = 0.0;
     if (t < 14) {
       int row;  // row of sh holding the (sum, sum of squares) pair
@@ -729,6 +862,35 @@ dim3 cells_grid(const Grid &g, dim3 b) {
   return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y);
 }
 
+template <typename T, typename MT>
+cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int G,
+                             const int *origins, double *stats, double *per_box,
+                             cudaStream_t s) {
+  int nx = 1, ny = 1, nL = 1, qblocks = 1;
+  for (int j = 0; j < G; ++j) {
+    nx = std::max(nx, jobs_host[j].nx);
+    ny = std::max(ny, jobs_host[j].ny);
+    nL = std::max(nL, jobs_host[j].nL);
+    qblocks = std::max(qblocks, jobs_host[j].qblocks);
+  }
+  const dim3 cb(32, 8), cg((nx + 31) / 32, (ny + 7) / 8, G);
+  k_prep<T><<<cg, cb, 0, s>>>(jobs);
+  k_grad<T><<<cg, cb, 0, s>>>(jobs);
+  k_flux<T><<<cg, cb, 0, s>>>(jobs);
+  k_curl<T><<<cg, cb, 0, s>>>(jobs);
+  k_scales<T><<<G, 12 * 32, 0, s>>>(jobs);
+  k_sat_rows<T><<<dim3(ny, 12, G), 256, 0, s>>>(jobs);
+  k_sat_cols<<<dim3((nx + 31) / 32, 12, G), dim3(32, 8), 0, s>>>(jobs);
+  k_query_consts<<<G, kDiagMaxL * 12, 0, s>>>(jobs);
+  const dim3 qg(qblocks, nL, 2 * G);
+  if (per_box)
+    k_query<MT, true><<<qg, 256, 0, s>>>(jobs, origins, per_box);
+  else
+    k_query<MT, false><<<qg, 256, 0, s>>>(jobs, origins, nullptr);
+  k_stats_final<<<dim3(nL, G), 256, 0, s>>>(jobs, stats);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t diag_moments(const Member &hm, const double *snap3, double *rho, double *ux,
@@ -758,80 +920,33 @@ cudaError_t diag_global(const Member &hm, const double *snap3, const DiagScratch
   return cudaGetLastError();
 }
 
-cudaError_t diag_terms(const Member &hm, int precision, const double *sn, const double *sn1,
-                       const double *sn2, const DiagScratch &sc, cudaStream_t s) {
-  const Grid g = grid_of(hm);
-  const size_t N = (size_t)hm.nx * hm.ny;
-  dim3 b(32, 8), gr = cells_grid(g, b);
-  if (precision == 32) {
-    k_prep<float><<<gr, b, 0, s>>>(g, sn, sn1, sn2, sc.f, N);
-    k_grad<float><<<gr, b, 0, s>>>(g, sc.f, N);
-    k_flux<float><<<gr, b, 0, s>>>(g, sc.f, N);
-    k_curl<float><<<gr, b, 0, s>>>(g, sc.f, N);
-  } else {
-    k_prep<double><<<gr, b, 0, s>>>(g, sn, sn1, sn2, sc.f, N);
-    k_grad<double><<<gr, b, 0, s>>>(g, sc.f, N);
-    k_flux<double><<<gr, b, 0, s>>>(g, sc.f, N);
-    k_curl<double><<<gr, b, 0, s>>>(g, sc.f, N);
-  }
-  return cudaGetLastError();
+// Box lists: one box per thread; every periodic origin: about 16 per
+// thread; at most kMaxQueryBlocks CTAs per (job, size, balance).
+int diag_query_blocks(int max_boxes, bool origin_list) {
+  const int per_cta = origin_list ? 256 : 4096;
+  return std::min(kMaxQueryBlocks, std::max(1, (max_boxes + per_cta - 1) / per_cta));
 }
 
-size_t diag_partials_needed(int nL) {
-  return (size_t)12 * kMaxPartialBlocks + 32 + kQConstDoubles +
-         (size_t)nL * 2 * kMaxPartialBlocks * kQStats;
+size_t diag_slot_doubles(size_t Nmax, size_t pad) {
+  // snapshot slots + term-stage fields + 12 padded tables
+  return (size_t)(kSnapSlots + NF) * Nmax + 12 * (Nmax + pad);
 }
 
-// Fixed-point SAT of the 12 term fields and the box queries for every size.
-// meta_dev: [nL][4] {L, n_boxes, origin offset or -1, per-box row offset};
-// origins_dev: concatenated (x0, y0) pairs (may be NULL when every size uses
-// all periodic origins); stats_dev receives [nL][15][2].
-cudaError_t diag_sat_and_query(const Member &hm, int precision, const int *meta_dev, int nL,
-                               int max_boxes, const int *origins_dev, const DiagScratch &sc,
-                               double *stats_dev, double *per_box_dev, cudaStream_t s) {
-  const int nx = hm.nx, ny = hm.ny;
-  const size_t N = (size_t)nx * ny;
-  double *part_max = sc.partials;                         // [12][blocks]
-  double *scales = part_max + 12 * kMaxPartialBlocks;     // [24] + 12 ints
-  QConst *consts = reinterpret_cast<QConst *>(scales + 32);  // [nL][12]
-  double *part_q = scales + 32 + kQConstDoubles;          // [nL][blocks][kQStats]
-  int nb_max = (int)((N + 4095) / 4096);
-  if (nb_max > kMaxPartialBlocks) nb_max = kMaxPartialBlocks;
-  if (precision == 32) {
-    k_absmax<float><<<dim3(nb_max, 12), 256, 0, s>>>(sc.f, N, part_max);
-    k_scales<<<1, 12 * 32, 0, s>>>(part_max, nb_max, N, scales);
-    k_sat_rows<float><<<dim3(ny, 12), 256, 0, s>>>(sc.f, nx, ny, scales);
-  } else {
-    k_absmax<double><<<dim3(nb_max, 12), 256, 0, s>>>(sc.f, N, part_max);
-    k_scales<<<1, 12 * 32, 0, s>>>(part_max, nb_max, N, scales);
-    k_sat_rows<double><<<dim3(ny, 12), 256, 0, s>>>(sc.f, nx, ny, scales);
-  }
-  k_sat_cols<<<dim3((nx + 31) / 32, 12), dim3(32, 8), 0, s>>>(sc.f, nx, ny);
-  k_query_consts<<<1, 32 * 12, 0, s>>>(scales, meta_dev, nL, sat_base(sc.f, N), nx, ny, consts);
-  // box lists: one box per thread; every periodic origin: about 16 per thread;
-  // at most kMaxPartialBlocks CTAs per size
-  const int per_cta = origins_dev ? 256 : 4096;
-  int qblocks = (max_boxes + per_cta - 1) / per_cta;
-  if (qblocks > kMaxPartialBlocks) qblocks = kMaxPartialBlocks;
-  if (qblocks < 1) qblocks = 1;
-  const dim3 qg(qblocks, nL, 2);
-  if (precision == 32) {
-    if (per_box_dev)
-      k_query<float, true><<<qg, 256, 0, s>>>(sc.f, nx, ny, consts, meta_dev, origins_dev,
-                                               part_q, per_box_dev);
-    else
-      k_query<float, false><<<qg, 256, 0, s>>>(sc.f, nx, ny, consts, meta_dev, origins_dev,
-                                                part_q, nullptr);
-  } else {
-    if (per_box_dev)
-      k_query<double, true><<<qg, 256, 0, s>>>(sc.f, nx, ny, consts, meta_dev, origins_dev,
-                                                part_q, per_box_dev);
-    else
-      k_query<double, false><<<qg, 256, 0, s>>>(sc.f, nx, ny, consts, meta_dev, origins_dev,
-                                                 part_q, nullptr);
-  }
-  k_stats_final<<<nL, 256, 0, s>>>(part_q, qblocks, consts, meta_dev, stats_dev);
-  return cudaGetLastError();
+size_t diag_job_partials(size_t Nmax, size_t pad) {
+  // CTAs of the 32 x 8 cell grid: ceil(nx/32) ceil(ny/8) <= N/256 + pad/8 + 1
+  const size_t ctas = Nmax / 256 + pad / 8 + 2;
+  return kPartMax + 12 * ctas;  // 8-byte words
+}
+
+cudaError_t diag_balance(const DiagJob *jobs_host, const DiagJob *jobs_dev, int G,
+                         int precision, const int *origins_dev, double *stats_dev,
+                         double *per_box_dev, cudaStream_t s) {
+  if (G < 1 || (per_box_dev && G != 1)) return cudaErrorInvalidValue;
+  if (precision == 32)
+    return balance_launches<float, float>(jobs_host, jobs_dev, G, origins_dev, stats_dev,
+                                          per_box_dev, s);
+  return balance_launches<double, double>(jobs_host, jobs_dev, G, origins_dev, stats_dev,
+                                          per_box_dev, s);
 }
 
 }  // namespace lbm

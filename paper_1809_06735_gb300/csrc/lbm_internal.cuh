@@ -89,28 +89,56 @@ cudaError_t launch_status(int precision, const Member *d_members, int member, in
 
 // Diagnostics (lbm_diag.cu).  scratch: device FP64 scratch of the handle.
 struct DiagScratch {
-  double *f;        // [nfields][N] field scratch
-  size_t N;         // cells of the largest member
-  double *partials; // reduction partials
-  size_t npartials; // capacity in doubles
+  double *f;          // slot 0: [nfields][N] field scratch (also general staging)
+  size_t N;           // cells of the largest member
+  double *partials;   // general reduction partials (kGeneralPartials doubles)
+  int slots;          // members one batched diagnostic launch covers
+  size_t slot_doubles;   // stride of the field slots (slot j at f + j * slot_doubles)
+  double *jpart;      // per-slot partials (slot j at jpart + j * jpart_doubles)
+  size_t jpart_doubles;
 };
 constexpr int kDiagFields = 50;
 constexpr int kMaxPartialBlocks = 1024;
+constexpr int kGeneralPartials = 8 * kMaxPartialBlocks;
+constexpr int kDiagMaxL = 32;  // box sizes per balance call
 
 cudaError_t diag_moments(const Member &hm, const double *snap3, double *rho, double *ux,
                          double *uy, double *omega, const DiagScratch &sc, cudaStream_t s);
 cudaError_t diag_global(const Member &hm, const double *snap3, const DiagScratch &sc,
                         double *out7_dev, cudaStream_t s);
-// precision: 32 (FP32 term arithmetic) or 64.
-cudaError_t diag_terms(const Member &hm, int precision, const double *sn, const double *sn1,
-                       const double *sn2, const DiagScratch &sc, cudaStream_t s);
-// meta_dev: [nL][8] {L, n_boxes, origin offset (-1: all periodic origins),
-// per-box row offset, statistics row, unused x3}; max_boxes: the largest
-// n_boxes.  stats_dev: rows of [15][2], written at the statistics rows.
-cudaError_t diag_sat_and_query(const Member &hm, int precision, const int *meta_dev, int nL,
-                               int max_boxes, const int *origins_dev, const DiagScratch &sc,
-                               double *stats_dev, double *per_box_dev, cudaStream_t s);
-size_t diag_partials_needed(int nL);
+
+// One member's share of a batched balance diagnostic.  Every stage runs as
+// one launch over all jobs of a batch; the device copy of the job table is
+// read by the kernels.
+struct DiagJob {
+  int nx, ny;
+  double nu, alpha, rho_ref;
+  const double *fxt, *fyt;     // F_ext,x(y), F_ext,y(x) (FP64 tables)
+  const double *s0, *s1, *s2;  // (rho, j_x, j_y) snapshots at n, n-1, n-2, [3][N]
+  double *base;                // field slot: term fields and summed-area tables
+  double *part;                // partials slot
+  const int *meta;             // [nL][8] {L, n_boxes, origin offset (-1: all
+                               // periodic origins), per-box row offset,
+                               // statistics row, unused x3}
+  int nL, max_boxes;
+  int qblocks;                 // query CTAs per (size, balance):
+                               // diag_query_blocks(max_boxes, origin list?)
+};
+// Query CTAs for a job: a fixed function of its own box count, so that the
+// statistics do not depend on which members share a batch.
+int diag_query_blocks(int max_boxes, bool origin_list);
+// Doubles of one field slot and of one partials slot for members of at most
+// Nmax cells and nx + ny + 1 <= pad.
+size_t diag_slot_doubles(size_t Nmax, size_t pad);
+size_t diag_job_partials(size_t Nmax, size_t pad);
+// The balance diagnostic of G jobs (precision 32: FP32 term arithmetic, 64:
+// FP64): term passes, summed-area tables, box queries and statistics, ten
+// launches in all.  origins_dev: concatenated (x0, y0) pairs shared by every
+// job (NULL when each size uses all periodic origins); stats_dev: rows of
+// [15][2] at the statistics rows; per_box_dev only with G == 1.
+cudaError_t diag_balance(const DiagJob *jobs_host, const DiagJob *jobs_dev, int G,
+                         int precision, const int *origins_dev, double *stats_dev,
+                         double *per_box_dev, cudaStream_t s);
 
 // Adjoint (lbm_adjoint.cu).
 cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_in,

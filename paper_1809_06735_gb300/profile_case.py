@@ -2,6 +2,7 @@
 
     python -m paper_1809_06735_gb300.profile_case step     # batched FP32 stream-collide
     python -m paper_1809_06735_gb300.profile_case diag     # one diagnostic event, 512^2
+    python -m paper_1809_06735_gb300.profile_case diag_batch  # batched event, 16 x 512^2
     python -m paper_1809_06735_gb300.profile_case fp64     # plain FP64 step, 512^2
     python -m paper_1809_06735_gb300.profile_case adjoint  # FP64 adjoint steps, 256^2
 
@@ -45,6 +46,22 @@ def case_diag(n=512, events=2):
     print("diag case done:", lat.launch_count, "launches")
 
 
+def case_diag_batch(members=16, n=512, events=2):
+    """One batched diagnostic event over 16 members (Table 1 random boxes),
+    as the ensemble benchmark runs it; about 2 GB of device memory."""
+    lat = Lattice([Member(n, n, 0.52)] * members, precision=32, diag_every=200)
+    for m in range(members):
+        lat.init_fields(m, *li.random_phase(n, seed=1000 + m, u_rms=0.02))
+    Ls = li.pow2_sizes(1, 8, n)
+    origins = [li.table1_origins(n, L, seed=7 + L) for L in Ls]
+    for _ in range(events):
+        lat.step(200)
+        stats = lat.subvolume_balance_batch(range(members), Ls, origins=origins)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(stats[:, :, 2:, 0]))
+    print("diag batch case done:", lat.launch_count, "launches")
+
+
 def case_fp64(n=512, steps=20):
     lat = Lattice([Member(n, n, 0.52)], precision=64)
     lat.init_fields(0, *li.random_phase(n, seed=1000, u_rms=0.02))
@@ -70,4 +87,5 @@ def case_adjoint(n=256, steps=6):
 
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "step"
-    {"step": case_step, "diag": case_diag, "fp64": case_fp64, "adjoint": case_adjoint}[which]()
+    {"step": case_step, "diag": case_diag, "diag_batch": case_diag_batch, "fp64": case_fp64,
+     "adjoint": case_adjoint}[which]()

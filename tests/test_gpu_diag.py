@@ -300,3 +300,34 @@ def test_async_balance_overlapped_with_stepping(P):
     nxt = lat.subvolume_balance_batch([0, 1, 2], Ls, origins=origins)
     assert np.all(np.isfinite(nxt[:, :3, 2:, 0]))
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_batched_diagnostic_independent_of_batch_size(P, prec):
+    """One member per diagnostic launch, two per launch (three batches, slots
+    reused) and all in one launch give bit-identical statistics, for uneven
+    grids with ragged 32 x 8 cell tiles, all periodic origins and origin
+    lists."""
+    spec = [(37, 23, 0.6), (64, 48, 0.55), (8, 8, 0.7), (130, 20, 0.52), (64, 48, 0.58)]
+    Ls = [2, 5, 8, 20, 40]
+    origins = [li.table1_origins(8, L, seed=L, count=300) if L <= 8 else
+               li.table1_origins(20, L, seed=L, count=40) for L in Ls]
+    origins[-1] = np.zeros((3, 2), np.int32)
+    res = []
+    for batch in (1, 2, 0):
+        lat = P.Lattice([P.Member(nx, ny, t) for nx, ny, t in spec], precision=prec,
+                        diag_every=12, diag_batch=batch)
+        for i, (nx, ny, _) in enumerate(spec):
+            lat.init_fields(i, 1.0 + li.smooth_fields(nx, ny, 10 + i, amp=0.01),
+                            li.smooth_fields(nx, ny, 20 + i, amp=0.03),
+                            li.smooth_fields(nx, ny, 30 + i, amp=0.03))
+        lat.step(12)
+        res.append((lat.subvolume_balance_batch(range(len(spec)), Ls),
+                    lat.subvolume_balance_batch(range(len(spec)), Ls, origins=origins)))
+    for a, b in res[1:]:
+        for x, y in ((res[0][0], a), (res[0][1], b)):
+            np.testing.assert_array_equal(np.isnan(x), np.isnan(y))
+            np.testing.assert_array_equal(x[~np.isnan(x)], y[~np.isnan(y)])
+    # sizes that fit: 8x8 only L <= 8; 130x20 and 37x23 L <= 20
+    assert np.all(np.isnan(res[0][0][2, 3:])) and np.all(np.isfinite(res[0][0][2, :3, 2:, 0]))
+    assert np.all(np.isfinite(res[0][0][1, :, 2:, 0]))
