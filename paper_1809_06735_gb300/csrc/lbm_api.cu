@@ -119,7 +119,7 @@ Layout make_layout(const lbm_config *cfg) {
     pad = std::max(pad, (size_t)cfg->members[m].nx + cfg->members[m].ny + 1);
   // slot 0 doubles as general staging (three snapshots, adjoint fields)
   L.slot_doubles = std::max(lbm::diag_slot_doubles(L.Nmax, pad),
-                            (size_t)L.scratch_fields * L.Nmax);
+                            ((size_t)L.scratch_fields * L.Nmax + 31) / 32 * 32);
   L.jpart_doubles = lbm::diag_job_partials(L.Nmax, pad);
   const size_t per_slot = 8 * (L.slot_doubles + L.jpart_doubles);
   size_t slots = cfg->diag_batch > 0 ? (size_t)cfg->diag_batch
@@ -288,11 +288,15 @@ int wait_diag(lbm_handle *h) {
 int record(lbm_handle *h) {
   if (int rc = wait_diag(h)) return rc;
   const int slot = (int)(h->t % 3);
-  for (int m = 0; m < (int)h->mcfg.size(); ++m)
-    CK(lbm::launch_snapshot(h->precision, h->d_members, m, h->mcfg[m].nx, h->mcfg[m].ny,
-                            h->cur, snap_slot(h, m, slot), h->stream));
+  int nx = 1, ny = 1;
+  for (const lbm_member_cfg &c : h->mcfg) {
+    nx = std::max(nx, c.nx);
+    ny = std::max(ny, c.ny);
+  }
+  CK(lbm::launch_snapshot_ring(h->precision, h->d_members, (int)h->mcfg.size(), nx, ny, h->cur,
+                               slot, h->stream));
   h->ring_time[slot] = h->t;
-  h->launches += (long long)h->mcfg.size();
+  h->launches += 1;
   return LBM_OK;
 }
 
@@ -637,16 +641,19 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
     if (total_boxes > h->lay.origin_cap)
       return fail(h, LBM_ERR_ARG, "too many boxes for the origin buffer");
   }
+  int nx_min = 0, ny_min = 0;  // every origin must lie in every listed grid
   for (int i = 0; i < nm; ++i) {
     int rc = check_member(h, members[i]);
     if (rc) return rc;
     const lbm_member_cfg &c = h->mcfg[members[i]];
-    if (origins)
-      for (size_t k = 0; k < total_boxes; ++k)
-        if (origins[2 * k] < 0 || origins[2 * k] >= c.nx || origins[2 * k + 1] < 0 ||
-            origins[2 * k + 1] >= c.ny)
-          return fail(h, LBM_ERR_ARG, "origin outside the grid");
+    nx_min = i ? std::min(nx_min, c.nx) : c.nx;
+    ny_min = i ? std::min(ny_min, c.ny) : c.ny;
   }
+  if (origins)
+    for (size_t k = 0; k < total_boxes; ++k)
+      if (origins[2 * k] < 0 || origins[2 * k] >= nx_min || origins[2 * k + 1] < 0 ||
+          origins[2 * k + 1] >= ny_min)
+        return fail(h, LBM_ERR_ARG, "origin outside the grid");
   // history n, n-1, n-2 (shared clock of all members)
   const long long t = h->t;
   if (h->ring_time[t % 3] != t) {
@@ -716,6 +723,11 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
     J.rho_ref = hm.rho0;
     J.fxt = hm.fx_tab64;
     J.fyt = hm.fy_tab64;
+    J.fxt_f = h->precision == 32 ? static_cast<const float *>(hm.fx_tab) : nullptr;
+    J.fyt_f = h->precision == 32 ? static_cast<const float *>(hm.fy_tab) : nullptr;
+    J.nu_f = (float)hm.nu;
+    J.alpha_f = (float)hm.alpha;
+    J.rho_ref_f = (float)hm.rho0;
     J.s0 = snap_slot(h, m, (int)(t % 3));
     J.s1 = snap_slot(h, m, (int)((t - 1) % 3));
     J.s2 = snap_slot(h, m, (int)((t - 2) % 3));
@@ -733,8 +745,8 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
                        cudaMemcpyHostToDevice, s));
     for (size_t j0 = 0; j0 < jobs.size(); j0 += (size_t)h->sc.slots) {
       const int G = (int)std::min(jobs.size() - j0, (size_t)h->sc.slots);
-      CK(lbm::diag_balance(jobs.data() + j0, jobs_dev + j0, G, h->diag_precision, orig_dev,
-                           stats_dev, per_box_out, s));
+      CK(lbm::diag_balance(jobs.data() + j0, jobs_dev + j0, G, h->diag_precision,
+                           h->precision == 32, orig_dev, stats_dev, per_box_out, s));
       h->launches += 10;  // 4 term passes, scales, 2 scans, constants, query, statistics
     }
   }

@@ -4,8 +4,9 @@
 // averages through summed-area tables (O(1) per box and size), the balancing
 // errors of eqs. (12), (13) and their statistics per box size.
 //
-// Precision.  Inputs are FP64 moment snapshots (rho, j_x, j_y), layout
-// [3][ny*nx].  The term fields are computed in T = double (FP64 handles, or
+// Precision.  Inputs are moment snapshots (rho, j_x, j_y): FP64 [3][ny*nx],
+// or for FP32 storage the compensated FP32 pairs (hi, lo) of rho - rho0,
+// j_x, j_y, [3][2][ny*nx], whose sums are the FP64 moments.  The term fields are computed in T = double (FP64 handles, or
 // on request) or T = float (FP32 handles): GB300 executes FP64 at a small
 // fraction of its FP32 rate, and the FP32 variant keeps its accuracy by
 // forming every cancelling quantity from FP64 differences first -- the time
@@ -32,6 +33,7 @@
 // slots 3.. the term-stage fields (each slot holds N values of T), then the
 // 12 int64 tables of (nx+1)(ny+1) entries.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <vector>
 
@@ -233,31 +235,133 @@ __device__ __forceinline__ void block_absmax(const T (&v)[K], const int (&f)[K],
 // u^0 - u^1 = (dm - u^0 drho) / rho^1  (exact identity).
 // E^0 - E^1 = [drho |u^0|^2 + rho^1 du . (2 u^0 - du)] / 2, and
 // LHS^E = (3 (E^0 - E^1) - (E^1 - E^2)) / 2 = eq. (17).
+// The three snapshot levels of one cell: their FP64 values where the
+// snapshots are FP64, and level differences formed without cancellation.
+template <typename T, bool PAIRS>
+struct Levels {
+  T dr01, dr12, djx01, djy01, djx12, djy12;  // level differences n-(n-1), (n-1)-(n-2)
+  T r0, r1, r2, jx0, jy0, drho;              // drho = rho^n - rho_ref
+};
+
+// FP64 snapshots [3][N]: differences in FP64, rounded once to T.
 template <typename T>
+__device__ __forceinline__ Levels<T, false> levels(const DiagJob &J, size_t N, size_t c) {
+  const double *s0 = J.s0, *s1 = J.s1, *s2 = J.s2;
+  const double r0d = s0[c], r1d = s1[c], r2d = s2[c];
+  const double jx0d = s0[N + c], jy0d = s0[2 * N + c];
+  const double jx1d = s1[N + c], jy1d = s1[2 * N + c];
+  Levels<T, false> v;
+  v.dr01 = (T)(r0d - r1d);
+  v.dr12 = (T)(r1d - r2d);
+  v.djx01 = (T)(jx0d - jx1d);
+  v.djy01 = (T)(jy0d - jy1d);
+  v.djx12 = (T)(jx1d - s2[N + c]);
+  v.djy12 = (T)(jy1d - s2[2 * N + c]);
+  v.r0 = (T)r0d;
+  v.r1 = (T)r1d;
+  v.r2 = (T)r2d;
+  v.jx0 = (T)jx0d;
+  v.jy0 = (T)jy0d;
+  v.drho = (T)(r0d - J.rho_ref);
+  return v;
+}
+
+// Compensated FP32 pairs [3][2][N] of (rho - rho0, j_x, j_y), rho0 = rho_ref:
+// T = float forms each difference as (hi - hi') + (lo - lo') (relative error
+// of the difference a few FP32 ulps, no FP64 instruction); T = double
+// evaluates hi + lo in FP64 first (the exact compensated sums) and proceeds
+// as from FP64 snapshots.
+template <typename T>
+__device__ __forceinline__ Levels<T, true> levels_pairs(const DiagJob &J, size_t N, size_t c) {
+  const float *p[3] = {reinterpret_cast<const float *>(J.s0),
+                       reinterpret_cast<const float *>(J.s1),
+                       reinterpret_cast<const float *>(J.s2)};
+  float hi[3][3], lo[3][3];  // [level][moment]
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      hi[k][q] = p[k][(size_t)(2 * q) * N + c];
+      lo[k][q] = p[k][(size_t)(2 * q + 1) * N + c];
+    }
+  Levels<T, true> v;
+  if constexpr (sizeof(T) == 4) {
+    auto dif = [&](int q, int a, int b) { return (hi[a][q] - hi[b][q]) + (lo[a][q] - lo[b][q]); };
+    v.dr01 = dif(0, 0, 1);
+    v.dr12 = dif(0, 1, 2);
+    v.djx01 = dif(1, 0, 1);
+    v.djy01 = dif(2, 0, 1);
+    v.djx12 = dif(1, 1, 2);
+    v.djy12 = dif(2, 1, 2);
+    const float rho0 = J.rho_ref_f;
+    v.drho = hi[0][0] + lo[0][0];
+    v.r0 = rho0 + v.drho;
+    v.r1 = rho0 + (hi[1][0] + lo[1][0]);
+    v.r2 = rho0 + (hi[2][0] + lo[2][0]);
+    v.jx0 = hi[0][1] + lo[0][1];
+    v.jy0 = hi[0][2] + lo[0][2];
+  } else {
+    double d[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) d[k][q] = (double)hi[k][q] + (double)lo[k][q];
+    const double r0d = J.rho_ref + d[0][0], r1d = J.rho_ref + d[1][0],
+                 r2d = J.rho_ref + d[2][0];
+    v.dr01 = r0d - r1d;
+    v.dr12 = r1d - r2d;
+    v.djx01 = d[0][1] - d[1][1];
+    v.djy01 = d[0][2] - d[1][2];
+    v.djx12 = d[1][1] - d[2][1];
+    v.djy12 = d[1][2] - d[2][2];
+    v.r0 = r0d;
+    v.r1 = r1d;
+    v.r2 = r2d;
+    v.jx0 = d[0][1];
+    v.jy0 = d[0][2];
+    v.drho = r0d - J.rho_ref;
+  }
+  return v;
+}
+
+// Pass 0 (pointwise).  u = (j + F/2)/rho with F = F_ext - alpha j, i.e.
+// rho u = m = (1 - alpha/2) j + F_ext/2.  Differences between levels:
+// m^0 - m^1 = (1 - alpha/2)(j^0 - j^1), and
+// u^0 - u^1 = (dm - u^0 drho) / rho^1  (exact identity).
+// E^0 - E^1 = [drho |u^0|^2 + rho^1 du . (2 u^0 - du)] / 2, and
+// LHS^E = (3 (E^0 - E^1) - (E^1 - E^2)) / 2 = eq. (17).
+template <typename T, bool PAIRS>
 __global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) {
   JOB_CELLS;
   T lhs = 0, uf = 0;
   if (valid) {
-    const double *s0 = J.s0, *s1 = J.s1, *s2 = J.s2;
-    const double r0d = s0[c], r1d = s1[c], r2d = s2[c];
-    const double jx0d = s0[N + c], jy0d = s0[2 * N + c];
-    const T dr01 = (T)(r0d - r1d), dr12 = (T)(r1d - r2d);
-    const T djx01 = (T)(jx0d - s1[N + c]), djy01 = (T)(jy0d - s1[2 * N + c]);
-    const T djx12 = (T)(s1[N + c] - s2[N + c]), djy12 = (T)(s1[2 * N + c] - s2[2 * N + c]);
-    const T r0 = (T)r0d, r1 = (T)r1d, r2 = (T)r2d;
-    const T jx0 = (T)jx0d, jy0 = (T)jy0d;
-    const T a = (T)g.alpha, ca = T(1) - T(0.5) * a;
-    const T Fx = (T)g.fxt[y] - a * jx0, Fy = (T)g.fyt[x] - a * jy0;
-    const T u0 = (jx0 + T(0.5) * Fx) / r0, v0 = (jy0 + T(0.5) * Fy) / r0;
-    const T du01 = (ca * djx01 - u0 * dr01) / r1, dv01 = (ca * djy01 - v0 * dr01) / r1;
+    Levels<T, PAIRS> L;
+    if constexpr (PAIRS)
+      L = levels_pairs<T>(J, N, c);
+    else
+      L = levels<T>(J, N, c);
+    T a, fex, fey;  // alpha, F_ext,x(y), F_ext,y(x)
+    if constexpr (PAIRS && sizeof(T) == 4) {
+      a = J.alpha_f;
+      fex = J.fxt_f[y];
+      fey = J.fyt_f[x];
+    } else {
+      a = (T)g.alpha;
+      fex = (T)g.fxt[y];
+      fey = (T)g.fyt[x];
+    }
+    const T ca = T(1) - T(0.5) * a;
+    const T Fx = fex - a * L.jx0, Fy = fey - a * L.jy0;
+    const T u0 = (L.jx0 + T(0.5) * Fx) / L.r0, v0 = (L.jy0 + T(0.5) * Fy) / L.r0;
+    const T du01 = (ca * L.djx01 - u0 * L.dr01) / L.r1, dv01 = (ca * L.djy01 - v0 * L.dr01) / L.r1;
     const T u1 = u0 - du01, v1 = v0 - dv01;
-    const T du12 = (ca * djx12 - u1 * dr12) / r2, dv12 = (ca * djy12 - v1 * dr12) / r2;
+    const T du12 = (ca * L.djx12 - u1 * L.dr12) / L.r2, dv12 = (ca * L.djy12 - v1 * L.dr12) / L.r2;
     const T q0 = u0 * u0 + v0 * v0, q1 = u1 * u1 + v1 * v1;
-    const T dE01 =
-        T(0.5) * (dr01 * q0 + r1 * (du01 * (T(2) * u0 - du01) + dv01 * (T(2) * v0 - dv01)));
-    const T dE12 =
-        T(0.5) * (dr12 * q1 + r2 * (du12 * (T(2) * u1 - du12) + dv12 * (T(2) * v1 - dv12)));
-    const T E0 = T(0.5) * r0 * q0;
+    const T dE01 = T(0.5) * (L.dr01 * q0 +
+                             L.r1 * (du01 * (T(2) * u0 - du01) + dv01 * (T(2) * v0 - dv01)));
+    const T dE12 = T(0.5) * (L.dr12 * q1 +
+                             L.r2 * (du12 * (T(2) * u1 - du12) + dv12 * (T(2) * v1 - dv12)));
+    const T E0 = T(0.5) * L.r0 * q0;
     lhs = T(0.5) * (T(3) * dE01 - dE12);  // LHS^E
     uf = u0 * Fx + v0 * Fy;               // RHS^{E,3} = u . F
     fld<T>(base, U0X, N)[c] = u0;
@@ -266,10 +370,10 @@ __global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) 
     fld<T>(base, DU01Y, N)[c] = dv01;
     fld<T>(base, DU12X, N)[c] = du12;
     fld<T>(base, DU12Y, N)[c] = dv12;
-    fld<T>(base, DRHO, N)[c] = (T)(r0d - g.rho_ref);
-    fld<T>(base, R0, N)[c] = r0;
-    fld<T>(base, FXR, N)[c] = Fx / r0;
-    fld<T>(base, FYR, N)[c] = Fy / r0;
+    fld<T>(base, DRHO, N)[c] = L.drho;
+    fld<T>(base, R0, N)[c] = L.r0;
+    fld<T>(base, FXR, N)[c] = Fx / L.r0;
+    fld<T>(base, FYR, N)[c] = Fy / L.r0;
     fld<T>(base, A1, N)[c] = E0 * u0;
     fld<T>(base, A2, N)[c] = E0 * v0;
     fld<T>(base, T0 + 0, N)[c] = lhs;
@@ -286,7 +390,7 @@ __global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) 
 // (grad p = grad(rho - rho_ref)/3), RHS^{E,4}, RHS^{O,2}, RHS^{O,3};
 // fluxes for pass 2.
 template <typename T>
-__global__ void __launch_bounds__(256) k_grad(const DiagJob *__restrict__ jobs) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_grad(const DiagJob *__restrict__ jobs) {
   JOB_CELLS;
   T t2 = 0, t4 = 0, t6 = 0, t8 = 0, t9 = 0;
   if (valid) {
@@ -304,7 +408,12 @@ __global__ void __launch_bounds__(256) k_grad(const DiagJob *__restrict__ jobs) 
     const T dxv = Dx(V, nb), dyv = Dy(V, nb);
     const T u = U[c], v = V[c], r = fld<T>(base, R0, N)[c];
     const T sxx = T(2) * dxu, sxy = dyu + dxv, syy = T(2) * dyv;  // S_ij = d_j u_i + d_i u_j
-    const T nr = (T)g.nu * r;
+    T nu;
+    if constexpr (sizeof(T) == 4)
+      nu = J.nu_f;
+    else
+      nu = g.nu;
+    const T nr = nu * r;
     const T *DR = fld<T>(base, DRHO, N);
     t2 = -(u * Dx(DR, nb) + v * Dy(DR, nb)) / T(3);
     t4 = -nr * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
@@ -553,9 +662,34 @@ __device__ __forceinline__ long long quantize(double v, int e) {
   return __double2ll_rn(ldexp(v, e));
 }
 
-// Quantize and scan along x, one CTA (256 threads) per (row, field, job).
+// Four consecutive values of a term row (x, x+1, x+2, x+3 < nx): one
+// 16-byte load per float quadruple (two per double) where the row allows.
+__device__ __forceinline__ void load4(const float *r, int x, bool vec, float (&v)[4]) {
+  if (vec) {
+    const float4 q = *reinterpret_cast<const float4 *>(r + x);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = r[x + k];
+  }
+}
+__device__ __forceinline__ void load4(const double *r, int x, bool vec, double (&v)[4]) {
+  if (vec) {
+    const double2 a = *reinterpret_cast<const double2 *>(r + x);
+    const double2 b = *reinterpret_cast<const double2 *>(r + x + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = r[x + k];
+  }
+}
+
+// Quantize and scan along x, one CTA (128 threads) per (row, field, job):
+// each thread scans 4 consecutive cells of a 512-cell segment, a warp scan
+// of the thread totals and a CTA combination of the 4 warp totals give the
+// segment, and a running carry chains the segments.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sat_rows(const DiagJob *__restrict__ jobs) {
+__global__ void __launch_bounds__(128) k_sat_rows(const DiagJob *__restrict__ jobs) {
   const DiagJob &J = jobs[blockIdx.z];
   const int y = blockIdx.x, f = blockIdx.y, nx = J.nx, ny = J.ny;
   if (y >= ny) return;
@@ -564,33 +698,45 @@ __global__ void __launch_bounds__(256) k_sat_rows(const DiagJob *__restrict__ jo
   long long *tab = sat_base(J.base, N) + (size_t)f * sat_stride(nx, ny);
   long long *out = tab + (size_t)(y + 1) * (nx + 1) + 1;  // row y+1, column 1..nx
   const int e = reinterpret_cast<const int *>(J.part + kPartScales + 24)[f];
-  __shared__ long long wsum[8];
-  __shared__ long long carry_sh;
+  const bool vec = nx % 4 == 0 && (reinterpret_cast<uintptr_t>(row) & 15) == 0;
+  __shared__ long long wsum[4];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) out[-1] = 0;  // column 0
   if (y == 0)
-    for (int i = tid; i <= nx; i += 256) tab[i] = 0;  // row 0
+    for (int i = tid; i <= nx; i += 128) tab[i] = 0;  // row 0
   long long carry = 0;
-  for (int b0 = 0; b0 < nx; b0 += 256) {
-    const int x = b0 + tid;
-    long long v = x < nx ? quantize(row[x], e) : 0;
+  for (int b0 = 0; b0 < nx; b0 += 512) {
+    const int x = b0 + 4 * tid;
+    long long v[4] = {0, 0, 0, 0};
+    if (x + 3 < nx) {
+      T a[4];
+      load4(row, x, vec, a);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = quantize(a[k], e);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (x + k < nx) v[k] = quantize(row[x + k], e);
+    }
+    v[1] += v[0];
+    v[2] += v[1];
+    v[3] += v[2];
+    long long t = v[3];  // inclusive scan of the thread totals over the warp
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const long long n = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += n;
+      const long long n = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += n;
     }
-    if (lane == 31) wsum[wid] = v;
+    if (lane == 31) wsum[wid] = t;
     __syncthreads();
-    long long off = carry;
-    for (int k = 0; k < wid; ++k) off += wsum[k];
-    if (x < nx) out[x] = v + off;
-    if (tid == 255) {
-      long long tot = carry;
-      for (int k = 0; k < 8; ++k) tot += wsum[k];
-      carry_sh = tot;
-    }
-    __syncthreads();
-    carry = carry_sh;
+    long long off = carry + (t - v[3]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < wid) off += wsum[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (x + k < nx) out[x + k] = v[k] + off;
+    carry += wsum[0] + wsum[1] + wsum[2] + wsum[3];
     __syncthreads();
   }
 }
@@ -863,7 +1009,7 @@ dim3 cells_grid(const Grid &g, dim3 b) {
 }
 
 template <typename T, typename MT>
-cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int G,
+cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int G, bool pairs,
                              const int *origins, double *stats, double *per_box,
                              cudaStream_t s) {
   int nx = 1, ny = 1, nL = 1, qblocks = 1;
@@ -874,12 +1020,15 @@ cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int 
     qblocks = std::max(qblocks, jobs_host[j].qblocks);
   }
   const dim3 cb(32, 8), cg((nx + 31) / 32, (ny + 7) / 8, G);
-  k_prep<T><<<cg, cb, 0, s>>>(jobs);
+  if (pairs)
+    k_prep<T, true><<<cg, cb, 0, s>>>(jobs);
+  else
+    k_prep<T, false><<<cg, cb, 0, s>>>(jobs);
   k_grad<T><<<cg, cb, 0, s>>>(jobs);
   k_flux<T><<<cg, cb, 0, s>>>(jobs);
   k_curl<T><<<cg, cb, 0, s>>>(jobs);
   k_scales<T><<<G, 12 * 32, 0, s>>>(jobs);
-  k_sat_rows<T><<<dim3(ny, 12, G), 256, 0, s>>>(jobs);
+  k_sat_rows<T><<<dim3(ny, 12, G), 128, 0, s>>>(jobs);
   k_sat_cols<<<dim3((nx + 31) / 32, 12, G), dim3(32, 8), 0, s>>>(jobs);
   k_query_consts<<<G, kDiagMaxL * 12, 0, s>>>(jobs);
   const dim3 qg(qblocks, nL, 2 * G);
@@ -928,8 +1077,10 @@ int diag_query_blocks(int max_boxes, bool origin_list) {
 }
 
 size_t diag_slot_doubles(size_t Nmax, size_t pad) {
-  // snapshot slots + term-stage fields + 12 padded tables
-  return (size_t)(kSnapSlots + NF) * Nmax + 12 * (Nmax + pad);
+  // snapshot slots + term-stage fields + 12 padded tables, in whole 256-byte
+  // units (so field rows keep the 16-byte alignment of vector loads)
+  const size_t d = (size_t)(kSnapSlots + NF) * Nmax + 12 * (Nmax + pad);
+  return (d + 31) / 32 * 32;
 }
 
 size_t diag_job_partials(size_t Nmax, size_t pad) {
@@ -939,14 +1090,14 @@ size_t diag_job_partials(size_t Nmax, size_t pad) {
 }
 
 cudaError_t diag_balance(const DiagJob *jobs_host, const DiagJob *jobs_dev, int G,
-                         int precision, const int *origins_dev, double *stats_dev,
-                         double *per_box_dev, cudaStream_t s) {
+                         int precision, bool pairs, const int *origins_dev,
+                         double *stats_dev, double *per_box_dev, cudaStream_t s) {
   if (G < 1 || (per_box_dev && G != 1)) return cudaErrorInvalidValue;
   if (precision == 32)
-    return balance_launches<float, float>(jobs_host, jobs_dev, G, origins_dev, stats_dev,
-                                          per_box_dev, s);
-  return balance_launches<double, double>(jobs_host, jobs_dev, G, origins_dev, stats_dev,
-                                          per_box_dev, s);
+    return balance_launches<float, float>(jobs_host, jobs_dev, G, pairs, origins_dev,
+                                          stats_dev, per_box_dev, s);
+  return balance_launches<double, double>(jobs_host, jobs_dev, G, pairs, origins_dev,
+                                          stats_dev, per_box_dev, s);
 }
 
 }  // namespace lbm

@@ -47,7 +47,9 @@ struct Member {
   void *fy_tab;          // F_ext,y as function of x: [nx]
   double *fx_tab64;      // the same tables in double (diagnostics, adjoint)
   double *fy_tab64;
-  double *snap;          // [3 slots][3 fields: rho, jx, jy][ny * nx]
+  double *snap;          // ring of 3 slots of (rho, jx, jy), 24 B per cell each:
+                         // FP64 [3][N], or FP32 storage (hi, lo) pairs
+                         // [3][2][N] of rho - rho0, jx, jy
   int *status;           // divergence flag
 };
 
@@ -82,6 +84,9 @@ cudaError_t launch_get_populations(int precision, const Member *d_members, int m
                                    int nx, int ny, int cur, double *f, cudaStream_t s);
 cudaError_t launch_set_populations(int precision, const Member *d_members, int member,
                                    int nx, int ny, int cur, const double *f, cudaStream_t s);
+// The ring snapshot of every member in one launch (layout at Member::snap).
+cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_members,
+                                 int nx_max, int ny_max, int state, int slot, cudaStream_t s);
 cudaError_t launch_snapshot(int precision, const Member *d_members, int member, int nx,
                             int ny, int cur, double *dst, cudaStream_t s);
 cudaError_t launch_status(int precision, const Member *d_members, int member, int nx,
@@ -114,7 +119,10 @@ struct DiagJob {
   int nx, ny;
   double nu, alpha, rho_ref;
   const double *fxt, *fyt;     // F_ext,x(y), F_ext,y(x) (FP64 tables)
-  const double *s0, *s1, *s2;  // (rho, j_x, j_y) snapshots at n, n-1, n-2, [3][N]
+  const float *fxt_f, *fyt_f;  // the same as FP32 tables (FP32 storage), else NULL
+  float nu_f, alpha_f, rho_ref_f;
+  const double *s0, *s1, *s2;  // ring snapshots at n, n-1, n-2 (Member::snap
+                               // layout; pairs = FP32 (hi, lo) form)
   double *base;                // field slot: term fields and summed-area tables
   double *part;                // partials slot
   const int *meta;             // [nL][8] {L, n_boxes, origin offset (-1: all
@@ -137,8 +145,8 @@ size_t diag_job_partials(size_t Nmax, size_t pad);
 // job (NULL when each size uses all periodic origins); stats_dev: rows of
 // [15][2] at the statistics rows; per_box_dev only with G == 1.
 cudaError_t diag_balance(const DiagJob *jobs_host, const DiagJob *jobs_dev, int G,
-                         int precision, const int *origins_dev, double *stats_dev,
-                         double *per_box_dev, cudaStream_t s);
+                         int precision, bool pairs, const int *origins_dev,
+                         double *stats_dev, double *per_box_dev, cudaStream_t s);
 
 // Adjoint (lbm_adjoint.cu).
 cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_in,

@@ -437,6 +437,65 @@ __global__ void k_snapshot(const Member *__restrict__ members, int member, int s
   d[2 * N + c] = jy;
 }
 
+// Compensated FP32 sum of FP32 values as the unevaluated pair (s, c): the
+// FP64 sum is (double)s + (double)c (the csum value) and differences of
+// nearby sums can be formed in FP32 as (s - s') + (c - c').
+__device__ __forceinline__ void csum_pair(const float *v, const int *sign, int n, float &s,
+                                          float &c) {
+  s = sign[0] * v[0];
+  c = 0.f;
+  for (int k = 1; k < n; ++k) {
+    float e;
+    two_sum(s, sign[k] * v[k], s, e);
+    c += e;
+  }
+}
+
+// The snapshot ring entry of every member at once (blockIdx.z = member):
+// (rho, j_x, j_y) of the pre-collision state into ring slot `slot` of
+// M.snap.  FP64 storage: [3][N] doubles.  FP32 deviation storage: [3][2][N]
+// floats, the compensated pairs (hi, lo) of rho - rho0, j_x, j_y.
+template <typename T>
+__global__ void k_snapshot_ring(const Member *__restrict__ members, int state, int slot) {
+  const Member &M = members[blockIdx.z];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= M.nx || y >= M.ny) return;
+  const T *src = static_cast<const T *>(state_buffer(M, state));
+  T f[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
+  const size_t N = (size_t)M.nx * M.ny, c = (size_t)y * M.nx + x;
+  if constexpr (sizeof(T) == 4) {
+    const int one[kQ] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    const float ax[6] = {f[1], f[5], f[8], f[3], f[6], f[7]};
+    const float ay[6] = {f[2], f[5], f[6], f[4], f[7], f[8]};
+    const int sgn[6] = {1, 1, 1, -1, -1, -1};
+    float hi[3], lo[3];
+    csum_pair(f, one, kQ, hi[0], lo[0]);
+    csum_pair(ax, sgn, 6, hi[1], lo[1]);
+    csum_pair(ay, sgn, 6, hi[2], lo[2]);
+    float *d = reinterpret_cast<float *>(M.snap) + (size_t)slot * 6 * N;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      d[(size_t)(2 * q) * N + c] = hi[q];
+      d[(size_t)(2 * q + 1) * N + c] = lo[q];
+    }
+  } else {
+    double r = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      r += f[l];
+      jx += cx_of(l) * f[l];
+      jy += cy_of(l) * f[l];
+    }
+    double *d = M.snap + (size_t)slot * 3 * N;
+    d[c] = r;
+    d[N + c] = jx;
+    d[2 * N + c] = jy;
+  }
+}
+
 template <typename T>
 __global__ void k_status(const Member *__restrict__ members, int member, int state) {
   const Member &M = members[member];
@@ -488,6 +547,18 @@ cudaError_t launch_set_populations(int precision, const Member *d_members, int m
 cudaError_t launch_snapshot(int precision, const Member *d_members, int member, int nx,
                             int ny, int state, double *dst, cudaStream_t s) {
   LBM_DISPATCH(precision, k_snapshot, d_members, member, state, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_members,
+                                 int nx_max, int ny_max, int state, int slot, cudaStream_t s) {
+  const dim3 b(64, 4);
+  dim3 g = grid2d(nx_max, ny_max, b);
+  g.z = n_members;
+  if (precision == 32)
+    k_snapshot_ring<float><<<g, b, 0, s>>>(d_members, state, slot);
+  else
+    k_snapshot_ring<double><<<g, b, 0, s>>>(d_members, state, slot);
   return cudaGetLastError();
 }
 

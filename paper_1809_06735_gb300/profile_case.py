@@ -1,6 +1,7 @@
 """Small, self-contained runs of each kernel family for Nsight Compute.
 
     python -m paper_1809_06735_gb300.profile_case step     # batched FP32 stream-collide
+    python -m paper_1809_06735_gb300.profile_case step_full  # the same, 64 x 512^2
     python -m paper_1809_06735_gb300.profile_case diag     # one diagnostic event, 512^2
     python -m paper_1809_06735_gb300.profile_case diag_batch  # batched event, 16 x 512^2
     python -m paper_1809_06735_gb300.profile_case fp64     # plain FP64 step, 512^2
@@ -8,7 +9,7 @@
 
 Sizes keep the working set above the L2 (so DRAM counters mean something)
 and below a few GB.  The step case creates its handle with the launch-shape
-autotuner on: 18 shapes x 7 launches = 126 launches of k_step_f32_vec come
+autotuner on: 2 storages x 18 shapes x 8 launches = 288 launches of k_step_f32_vec come
 before the first step of the run.
 """
 from __future__ import annotations
@@ -22,7 +23,7 @@ import lbm_inputs as li
 
 from . import Lattice, Member
 
-AUTOTUNE_LAUNCHES = 126
+AUTOTUNE_LAUNCHES = 288
 
 
 def case_step(members=16, n=512, steps=25):
@@ -32,6 +33,18 @@ def case_step(members=16, n=512, steps=25):
     lat.step(steps)
     torch.cuda.synchronize()
     print("step case done:", lat.launch_count, "launches")
+
+
+def case_step_full(members=64, n=512, steps=20):
+    """The ensemble benchmark's stream-collide workload (64 x 512^2, FP32,
+    autotuned storage and shape) for single-pass DRAM counters; the
+    autotuner's 288 launches come first."""
+    lat = Lattice([Member(n, n, 0.52)] * members, precision=32, graph_steps=0, diag_batch=1)
+    for m in range(members):
+        lat.init_fields(m, *li.random_phase(n, seed=1000 + m, u_rms=0.02))
+    lat.step(steps)
+    torch.cuda.synchronize()
+    print("step_full case done:", lat.launch_count, "launches", lat.tuning())
 
 
 def case_diag(n=512, events=2):
@@ -87,5 +100,5 @@ def case_adjoint(n=256, steps=6):
 
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "step"
-    {"step": case_step, "diag": case_diag, "diag_batch": case_diag_batch, "fp64": case_fp64,
+    {"step": case_step, "step_full": case_step_full, "diag": case_diag, "diag_batch": case_diag_batch, "fp64": case_fp64,
      "adjoint": case_adjoint}[which]()
