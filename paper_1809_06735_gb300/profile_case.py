@@ -35,10 +35,10 @@ def case_step(members=16, n=512, steps=25):
     print("step case done:", lat.launch_count, "launches")
 
 
-def case_step_full(members=64, n=512, steps=20):
+def case_step_full(members=64, n=512, steps=200):
     """The ensemble benchmark's stream-collide workload (64 x 512^2, FP32,
     autotuned storage and shape) for single-pass DRAM counters; the
-    autotuner's 288 launches come first."""
+    autotuner's 288 launches and the 64 initialisations come first."""
     lat = Lattice([Member(n, n, 0.52)] * members, precision=32, graph_steps=0, diag_batch=1)
     for m in range(members):
         lat.init_fields(m, *li.random_phase(n, seed=1000 + m, u_rms=0.02))
