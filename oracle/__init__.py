@@ -81,6 +81,12 @@ def _load():
             lib.orc_objective.argtypes = [I, I, D, I, D, I, D, P, I, I, I, I, I, P]
             lib.orc_objective.restype = I
             lib.orc_lattice.argtypes = [P, P, P]
+            lib.orc_box_mach.argtypes = [I, I, P, P, I, I, I]
+            lib.orc_box_mach.restype = D
+            lib.orc_bin.argtypes = [D, P, I]
+            lib.orc_bin.restype = I
+            lib.orc_distributions.argtypes = [I, I, P, P, P, P, I, P, I, P, I, P, I, P, P, P]
+            lib.orc_distributions.restype = I
             _lib = lib
     return _lib
 
@@ -288,6 +294,43 @@ def balance_stats(terms13, Ls, origins=None, per_box=False):
     if rc != 0:
         raise MemoryError("oracle stats failed")
     return (stats, pb) if per_box else stats
+
+
+def box_mach(ux, uy, x0, y0, L):
+    """Ma_V = sqrt(<|u|^2>_V) / c_s over the L x L box at (x0, y0), eq. (20)."""
+    ux, uy = _f64(ux), _f64(uy)
+    ny, nx = ux.shape
+    return _load().orc_box_mach(nx, ny, _p(ux), _p(uy), int(x0), int(y0), int(L))
+
+
+def hist_bin(v, edges):
+    """Bin of v: the number of edges <= v (-1 for NaN)."""
+    edges = _f64(edges)
+    return _load().orc_bin(float(v), _p(edges), len(edges))
+
+
+def distributions(terms13, ux, uy, Ls, delta_edges, mach_edges, origins=None):
+    """Histograms over the boxes of each size of delta^E, delta^Omega
+    ([nL, 2, len(delta_edges) + 1]) and of Ma_V ([nL, len(mach_edges) + 1]),
+    and the mean and population std of Ma_V ([nL, 2])."""
+    terms13, ux, uy = _f64(terms13), _f64(ux), _f64(uy)
+    _, ny, nx = terms13.shape
+    Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+    de, me = _f64(delta_edges), _f64(mach_edges)
+    nL = len(Ls)
+    if origins is not None:
+        origins = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1, 2)
+        nb, op = origins.shape[0], _p(origins)
+    else:
+        nb, op = nx * ny, None
+    hd = np.zeros((nL, 2, len(de) + 1), dtype=np.int64)
+    hm = np.zeros((nL, len(me) + 1), dtype=np.int64)
+    ms = np.empty((nL, 2))
+    rc = _load().orc_distributions(nx, ny, _p(terms13), _p(ux), _p(uy), _p(Ls), nL, op, nb,
+                                   _p(de), len(de), _p(me), len(me), _p(hd), _p(hm), _p(ms))
+    if rc != 0:
+        raise MemoryError("oracle distributions failed")
+    return hd, hm, ms
 
 
 def global_quantities(f, tau, force: Force = NO_FORCE):

@@ -30,7 +30,8 @@
  * Parity status: every function here is pinned by a CPU test (moment
  * identities, conservation, streaming permutation, Taylor-Green decay,
  * Kolmogorov laminar amplitude, stencil modified wavenumber, BDF2
- * exactness, symbolic continuum terms, brute-force box sums).
+ * exactness, symbolic continuum terms, brute-force box sums, closed-form
+ * box Mach numbers, brute-force histogram counts).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -510,6 +511,88 @@ int orc_balance_stats(int nx, int ny, const double *terms, const int *Ls,
       memcpy(per_box + (size_t)iL * nb * 15, vals, sizeof(double) * 15 * nb);
   }
   free(vals);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Distributions over boxes: sub-volume Mach number (eq. 20), PDFs (Sec. 4) */
+/* ------------------------------------------------------------------------ */
+
+/* Sub-volume Mach number of eq. (20), read as the RMS speed over the L x L
+ * box (lower-left origin (x0, y0), periodic) divided by the lattice speed of
+ * sound: Ma_V = sqrt(<u_x^2 + u_y^2>_V) / c_s, u the diagnostic velocity. */
+double orc_box_mach(int nx, int ny, const double *ux, const double *uy, int x0,
+                    int y0, int L) {
+  double s = 0.0;
+  for (int dy = 0; dy < L; ++dy)
+    for (int dx = 0; dx < L; ++dx) {
+      size_t c = (size_t)wrap(y0 + dy, ny) * nx + wrap(x0 + dx, nx);
+      s += ux[c] * ux[c] + uy[c] * uy[c];
+    }
+  return sqrt(s / ((double)L * (double)L)) / sqrt(CS2);
+}
+
+/* Histogram bin of v for ascending edges e[0..n-1]: the number of edges
+ * e_k <= v, so bin 0 holds v < e_0, bin k holds e_{k-1} <= v < e_k and bin n
+ * holds v >= e_{n-1} (+Inf included).  NaN belongs to no bin (-1). */
+int orc_bin(double v, const double *edges, int n) {
+  if (v != v) return -1;
+  int b = 0;
+  while (b < n && edges[b] <= v) ++b;
+  return b;
+}
+
+/* Distributions over the boxes of each size: the histograms behind the PDFs
+ * of the balancing errors shown in Sec. 4 and the mean and standard
+ * deviation of Ma_V (eq. 20) shown there against l.
+ *   hist_delta[(iL*2 + q)*(n_de + 1) + b]: boxes whose delta^E (q = 0) or
+ *     delta^Omega (q = 1) lies in bin b of delta_edges;
+ *   hist_mach[iL*(n_me + 1) + b]: the same for Ma_V and mach_edges;
+ *   mach_stats[iL*2 + 0 / 1]: mean and population standard deviation of Ma_V.
+ * Boxes as in orc_balance_stats; a size L > min(nx, ny) gives zero counts
+ * and NaN statistics. */
+int orc_distributions(int nx, int ny, const double *terms, const double *ux,
+                      const double *uy, const int *Ls, int nL,
+                      const int *origins, int n_origins,
+                      const double *delta_edges, int n_de,
+                      const double *mach_edges, int n_me,
+                      long long *hist_delta, long long *hist_mach,
+                      double *mach_stats) {
+  int nb = origins ? n_origins : nx * ny;
+  double *ma = (double *)malloc(sizeof(double) * (size_t)nb);
+  if (!ma) return -1;
+  for (int iL = 0; iL < nL; ++iL) {
+    int L = Ls[iL];
+    long long *hd = hist_delta + (size_t)iL * 2 * (n_de + 1);
+    long long *hm = hist_mach + (size_t)iL * (n_me + 1);
+    for (int b = 0; b < 2 * (n_de + 1); ++b) hd[b] = 0;
+    for (int b = 0; b <= n_me; ++b) hm[b] = 0;
+    if (L < 1 || L > nx || L > ny) {
+      mach_stats[2 * iL] = NAN;
+      mach_stats[2 * iL + 1] = NAN;
+      continue;
+    }
+    for (int b = 0; b < nb; ++b) {
+      int x0 = origins ? origins[2 * b] : b % nx;
+      int y0 = origins ? origins[2 * b + 1] : b / nx;
+      double v[15];
+      orc_box_values(nx, ny, terms, x0, y0, L, v);
+      for (int q = 0; q < 2; ++q) {
+        int k = orc_bin(v[q], delta_edges, n_de);
+        if (k >= 0) hd[q * (n_de + 1) + k] += 1;
+      }
+      ma[b] = orc_box_mach(nx, ny, ux, uy, x0, y0, L);
+      int k = orc_bin(ma[b], mach_edges, n_me);
+      if (k >= 0) hm[k] += 1;
+    }
+    double m = 0.0, var = 0.0;
+    for (int b = 0; b < nb; ++b) m += ma[b];
+    m /= nb;
+    for (int b = 0; b < nb; ++b) var += (ma[b] - m) * (ma[b] - m);
+    mach_stats[2 * iL] = m;
+    mach_stats[2 * iL + 1] = sqrt(var / nb);
+  }
+  free(ma);
   return 0;
 }
 

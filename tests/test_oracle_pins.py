@@ -470,3 +470,99 @@ def test_window_run_matches_full_run_inside_the_light_cone(orc):
         want = full[:, ys][:, :, xs]
         assert np.array_equal(got[inner], want[inner])
         assert not np.array_equal(got, want)  # the edges are not valid
+
+
+# --------------------------------------------------------------------------
+# Sub-volume Mach number (eq. 20) and distributions over boxes (Sec. 4)
+# --------------------------------------------------------------------------
+
+def test_box_mach_uniform_flow(orc):
+    """A uniform flow has Ma_V = |u| / c_s = |u| sqrt(3) in every box, every
+    size, wrapping boxes included (eq. 20)."""
+    ny, nx = 9, 13
+    U, V = 0.021, -0.037
+    ux, uy = np.full((ny, nx), U), np.full((ny, nx), V)
+    want = np.hypot(U, V) * np.sqrt(3.0)
+    for (x0, y0, L) in [(0, 0, 1), (12, 8, 5), (3, 2, 9), (7, 7, 4)]:
+        assert abs(orc.box_mach(ux, uy, x0, y0, L) - want) < 1e-15
+
+
+def test_box_mach_shear_rows_closed_form(orc):
+    """u = (U sin(2 pi y / N), 0): the box mean of sin^2 over rows y0..y0+L-1
+    is 1/2 - (1/2L) sum_j cos(a + j d), with the closed form of the sum
+    sin(L d / 2) / sin(d / 2) cos(a + (L - 1) d / 2), a = 4 pi y0 / N,
+    d = 4 pi / N (independent of the box's x extent)."""
+    N, U = 24, 0.05
+    y = np.arange(N)
+    ux = np.tile((U * np.sin(2 * np.pi * y / N))[:, None], (1, N))
+    uy = np.zeros((N, N))
+    d = 4 * np.pi / N
+    for (x0, y0, L) in [(0, 0, 5), (3, 20, 7), (11, 13, 10), (0, 5, 24)]:
+        a = y0 * d
+        s = np.sin(L * d / 2) / np.sin(d / 2) * np.cos(a + (L - 1) * d / 2)
+        mean_sq = U * U * (0.5 - s / (2 * L))
+        want = np.sqrt(mean_sq) * np.sqrt(3.0)
+        assert abs(orc.box_mach(ux, uy, x0, y0, L) - want) < 1e-14 * want + 1e-16
+
+
+def test_box_mach_taylor_green_whole_domain(orc):
+    """Taylor-Green velocity U (sin x cos y, -cos x sin y) on a full period:
+    <|u|^2> = U^2 / 2 exactly (discrete orthogonality), so the L = N box has
+    Ma = U sqrt(3/2) at every origin."""
+    N, U = 16, 0.03
+    k = 2 * np.pi / N
+    X, Y = np.meshgrid(np.arange(N), np.arange(N))
+    ux = U * np.sin(k * X) * np.cos(k * Y)
+    uy = -U * np.cos(k * X) * np.sin(k * Y)
+    for (x0, y0) in [(0, 0), (5, 11), (15, 15)]:
+        assert abs(orc.box_mach(ux, uy, x0, y0, N) - U * np.sqrt(1.5)) < 1e-15
+
+
+def test_histogram_bin_rule(orc):
+    """Bin of v = number of edges <= v: values equal to an edge go up, below
+    the first edge to bin 0, +Inf to the last bin, NaN to none."""
+    edges = [1e-6, 1e-4, 1e-2, 1.0]
+    cases = {0.0: 0, 5e-7: 0, 1e-6: 1, 5e-5: 1, 1e-4: 2, 0.5: 3, 1.0: 4, 7.0: 4,
+             float("inf"): 4, -1.0: 0}
+    for v, b in cases.items():
+        assert orc.hist_bin(v, edges) == b, v
+    assert orc.hist_bin(float("nan"), edges) == -1
+
+
+def test_distributions_count_every_box_once(orc):
+    """The histograms hold every box exactly once, in the bin a brute-force
+    count over the per-box balancing errors gives; Ma_V statistics equal the
+    mean and population std of brute-force box values; L > N gives zero
+    counts and NaN statistics."""
+    rng = np.random.default_rng(3)
+    ny, nx = 10, 12
+    terms = rng.normal(size=(13, ny, nx))
+    ux, uy = 0.05 * rng.normal(size=(ny, nx)), 0.05 * rng.normal(size=(ny, nx))
+    Ls = [1, 3, 10, 11]
+    de = np.geomspace(1e-3, 10.0, 9)
+    me = np.linspace(0.0, 0.3, 7)
+    origins = np.array([[0, 0], [11, 9], [5, 4], [2, 7], [5, 4]], dtype=np.int32)
+    for org in (None, origins):
+        hd, hm, ms = orc.distributions(terms, ux, uy, Ls, de, me, origins=org)
+        _, pb = orc.balance_stats(terms, Ls, origins=org, per_box=True)
+        boxes = [(b % nx, b // nx) for b in range(nx * ny)] if org is None else \
+            [tuple(o) for o in org]
+        for iL, L in enumerate(Ls):
+            if L > min(nx, ny):
+                assert hd[iL].sum() == 0 and hm[iL].sum() == 0 and np.all(np.isnan(ms[iL]))
+                continue
+            for q in range(2):
+                want = np.zeros(len(de) + 1, dtype=np.int64)
+                for b in range(len(boxes)):
+                    want[sum(1 for e in de if e <= pb[iL, b, q])] += 1
+                np.testing.assert_array_equal(hd[iL, q], want)
+            mach = [np.sqrt(np.mean([ux[(y0 + j) % ny, (x0 + i) % nx] ** 2 +
+                                     uy[(y0 + j) % ny, (x0 + i) % nx] ** 2
+                                     for j in range(L) for i in range(L)]) * 3.0)
+                    for (x0, y0) in boxes]
+            want = np.zeros(len(me) + 1, dtype=np.int64)
+            for m in mach:
+                want[sum(1 for e in me if e <= m)] += 1
+            np.testing.assert_array_equal(hm[iL], want)
+            assert abs(ms[iL, 0] - np.mean(mach)) < 1e-14
+            assert abs(ms[iL, 1] - np.std(mach)) < 1e-14
