@@ -209,6 +209,40 @@ int lbm_subvolume_balance_batch(lbm_handle *h, const int *members,
                                 const int *origins, const int *counts,
                                 double *stats_out);
 
+/* Largest number of histogram bin edges per quantity. */
+#define LBM_MAX_EDGES 256
+
+/* Distributions over the boxes of each size, for the members listed in the
+ * host array members[] (boxes, sizes and the synchronisation as
+ * lbm_subvolume_balance_batch): the histograms behind the paper's PDFs of
+ * the balancing errors (Sec. 4, at fixed l = L / N) and the sub-volume Mach
+ * number of eq. (20), read as Ma_V = sqrt(<u_x^2 + u_y^2>_V) / c_s with the
+ * diagnostic velocity u.
+ * delta_edges (host, n_delta_edges in 1..LBM_MAX_EDGES) and mach_edges
+ * (host, n_mach_edges): finite, strictly ascending bin edges e_0 < e_1 < ...;
+ * a value v goes to bin b = the number of edges <= v (bin 0: v < e_0; the
+ * last bin: v >= e_last, +Inf included; NaN in no bin).
+ * stats_out (host, may be NULL): the statistics of
+ * lbm_subvolume_balance_batch, double[n_members][nL][15][2].
+ * delta_hist_out (host): long long[n_members][nL][2][n_delta_edges + 1],
+ *   box counts of delta^E (index 0) and delta^Omega (1) per bin;
+ * mach_hist_out (host): long long[n_members][nL][n_mach_edges + 1];
+ * mach_stats_out (host): double[n_members][nL][2], mean and population
+ *   standard deviation of Ma_V over the boxes.
+ * Sizes that do not fit a member give zero counts and NaN statistics.
+ * Counts are exact integers (independent of launch order); the bin of a
+ * value is decided in the diagnostic precision (FP32 or FP64), so a value
+ * within rounding of an edge may fall on either side of it relative to an
+ * FP64 evaluation.  LBM_ERR_ARG for invalid edges or NULL outputs. */
+int lbm_subvolume_distributions(lbm_handle *h, const int *members,
+                                int n_members, const int *L, int nL,
+                                const int *origins, const int *counts,
+                                const double *delta_edges, int n_delta_edges,
+                                const double *mach_edges, int n_mach_edges,
+                                double *stats_out, long long *delta_hist_out,
+                                long long *mach_hist_out,
+                                double *mach_stats_out);
+
 /* Asynchronous form of lbm_subvolume_balance_batch: the diagnostic of the
  * current time is queued on an internal stream after the work already queued
  * on the handle's stream (its snapshots), and the call returns without

@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_subvolume_balance": ([P, I, P, I, P, P, P, P], I),
         "lbm_subvolume_balance_batch": ([P, P, I, P, I, P, P, P], I),
         "lbm_subvolume_balance_async": ([P, P, I, P, I, P, P, P], I),
+        "lbm_subvolume_distributions": ([P, P, I, P, I, P, P, P, I, P, I, P, P, P, P], I),
         "lbm_diag_synchronize": ([P], I),
         "lbm_get_populations": ([P, I, P, I], I),
         "lbm_set_populations": ([P, I, P, I], I),
@@ -314,6 +315,28 @@ class Lattice:
         self._check(self.lib.lbm_subvolume_balance_batch(
             self.h, _ptr(mem), len(mem), _ptr(Ls), len(Ls), _ptr(o), _ptr(counts), _ptr(stats)))
         return stats
+
+    def subvolume_distributions(self, members, Ls, delta_edges, mach_edges, origins=None):
+        """Distributions over the boxes of each size (one sync): a dict with
+        ``stats`` [n, nL, 15, 2] (as ``subvolume_balance_batch``),
+        ``delta_hist`` [n, nL, 2, len(delta_edges) + 1] box counts of
+        delta^E, delta^Omega per bin, ``mach_hist`` [n, nL, len(mach_edges) + 1]
+        and ``mach`` [n, nL, 2] (mean, std) of the sub-volume Mach number
+        Ma_V = sqrt(<|u|^2>_V) / c_s.  Bin b holds edges[b-1] <= v < edges[b]."""
+        mem = np.ascontiguousarray(members, dtype=np.int32)
+        Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+        de = np.ascontiguousarray(delta_edges, dtype=np.float64)
+        me = np.ascontiguousarray(mach_edges, dtype=np.float64)
+        n, nL = len(mem), len(Ls)
+        stats = np.empty((n, nL, NQUANT, 2))
+        dh = np.empty((n, nL, 2, len(de) + 1), dtype=np.int64)
+        mh = np.empty((n, nL, len(me) + 1), dtype=np.int64)
+        ma = np.empty((n, nL, 2))
+        o, counts = self._origin_lists(Ls, origins)
+        self._check(self.lib.lbm_subvolume_distributions(
+            self.h, _ptr(mem), n, _ptr(Ls), nL, _ptr(o), _ptr(counts), _ptr(de), len(de),
+            _ptr(me), len(me), _ptr(stats), _ptr(dh), _ptr(mh), _ptr(ma)))
+        return {"stats": stats, "delta_hist": dh, "mach_hist": mh, "mach": ma}
 
     def subvolume_balance_async(self, members, Ls, origins=None, out=None):
         """Queue the diagnostic of the current time on the handle's diagnostic

@@ -34,6 +34,7 @@ struct Layout {
   size_t members, tiles, status;
   std::vector<size_t> pop0, pop1, fx, fy, fx64, fy64, snap;
   size_t scratch, partials, jpart, jobs, stats, Ls, out7, origins;
+  size_t edges, hist, mach;  // distributions: bin edges, histograms, Ma_V statistics
   int diag_slots;          // members per batched diagnostic launch
   size_t slot_doubles, jpart_doubles;
   size_t total;
@@ -130,6 +131,9 @@ Layout make_layout(const lbm_config *cfg) {
   L.jpart = take(8 * L.jpart_doubles * L.diag_slots);
   L.jobs = take(sizeof(lbm::DiagJob) * n);
   L.stats = take(8 * (size_t)n * kMaxL * 30);
+  L.edges = take(8 * 2 * (size_t)lbm::kDiagMaxEdges);
+  L.hist = take(8 * (size_t)n * kMaxL * 3 * (lbm::kDiagMaxEdges + 1));
+  L.mach = take(8 * (size_t)n * kMaxL * 2);
   L.Ls = take(4 * 8 * (size_t)n * kMaxL);  // per-size meta rows {L, boxes, offsets, out row}
   L.out7 = take(8 * 8);
   L.origin_cap = std::max<size_t>(4 * L.Nmax, (size_t)1 << 20);
@@ -623,11 +627,35 @@ namespace {
 // Queues the diagnostic of each listed member (term fields, summed-area
 // tables, box queries, statistics) and copies every member's statistics to
 // the host with one synchronisation at the end.
+// Host side of a distributions request (lbm_subvolume_distributions).
+struct DistRequest {
+  const double *delta_edges, *mach_edges;
+  int n_delta, n_mach;
+  long long *delta_hist, *mach_hist;  // [nm][nL][2][n_delta + 1], [nm][nL][n_mach + 1]
+  double *mach_stats;                 // [nm][nL][2]
+};
+
+int check_edges(lbm_handle *h, const double *e, int n) {
+  if (!e || n < 1 || n > lbm::kDiagMaxEdges)
+    return fail(h, LBM_ERR_ARG, "need 1..256 bin edges");
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(e[i]) || (i > 0 && !(e[i] > e[i - 1])))
+      return fail(h, LBM_ERR_ARG, "bin edges must be finite and strictly ascending");
+  return LBM_OK;
+}
+
 int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int nL,
                     const int *origins, const int *counts, double *stats_out,
-                    double *per_box_out, double *stats_dev_out) {
+                    double *per_box_out, double *stats_dev_out,
+                    const DistRequest *dist = nullptr) {
   if (!L || nL < 1 || nL > kMaxL) return fail(h, LBM_ERR_ARG, "need 1..32 box sizes");
-  if (!stats_out && !stats_dev_out) return fail(h, LBM_ERR_ARG, "stats output is NULL");
+  if (!stats_out && !stats_dev_out && !dist) return fail(h, LBM_ERR_ARG, "stats output is NULL");
+  if (dist) {
+    if (int rc = check_edges(h, dist->delta_edges, dist->n_delta)) return rc;
+    if (int rc = check_edges(h, dist->mach_edges, dist->n_mach)) return rc;
+    if (!dist->delta_hist || !dist->mach_hist || !dist->mach_stats)
+      return fail(h, LBM_ERR_ARG, "distribution outputs are NULL");
+  }
   if (nm < 1) return fail(h, LBM_ERR_ARG, "no member given");
   if (per_box_out && nm != 1) return fail(h, LBM_ERR_ARG, "per_box_out needs one member");
   if ((origins == nullptr) != (counts == nullptr))
@@ -704,6 +732,22 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
   int *orig_dev = origins ? reinterpret_cast<int *>(ws_at(h, h->lay.origins)) : nullptr;
   double *stats_dev = async ? stats_dev_out : reinterpret_cast<double *>(ws_at(h, h->lay.stats));
   CK(cudaMemsetAsync(stats_dev, 0xff, 8 * (size_t)nm * nL * 30, s));  // all-ones bits: NaN
+  lbm::DiagDist dd{};
+  const size_t hrow = 3 * (size_t)(lbm::kDiagMaxEdges + 1);
+  if (dist) {
+    double *ed = reinterpret_cast<double *>(ws_at(h, h->lay.edges));
+    CK(cudaMemcpyAsync(ed, dist->delta_edges, 8 * dist->n_delta, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ed + lbm::kDiagMaxEdges, dist->mach_edges, 8 * dist->n_mach,
+                       cudaMemcpyHostToDevice, s));
+    dd.delta_edges = ed;
+    dd.mach_edges = ed + lbm::kDiagMaxEdges;
+    dd.n_delta = dist->n_delta;
+    dd.n_mach = dist->n_mach;
+    dd.hist = reinterpret_cast<unsigned long long *>(ws_at(h, h->lay.hist));
+    dd.mach = reinterpret_cast<double *>(ws_at(h, h->lay.mach));
+    CK(cudaMemsetAsync(dd.hist, 0, 8 * (size_t)nm * nL * hrow, s));
+    CK(cudaMemsetAsync(dd.mach, 0xff, 8 * (size_t)nm * nL * 2, s));
+  }
   CK(cudaMemcpyAsync(meta_dev, meta.data(), 4 * meta.size(), cudaMemcpyHostToDevice, s));
   if (origins)
     CK(cudaMemcpyAsync(orig_dev, origins, 8 * total_boxes, cudaMemcpyHostToDevice, s));
@@ -746,7 +790,8 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
     for (size_t j0 = 0; j0 < jobs.size(); j0 += (size_t)h->sc.slots) {
       const int G = (int)std::min(jobs.size() - j0, (size_t)h->sc.slots);
       CK(lbm::diag_balance(jobs.data() + j0, jobs_dev + j0, G, h->diag_precision,
-                           h->precision == 32, orig_dev, stats_dev, per_box_out, s));
+                           h->precision == 32, orig_dev, stats_dev, per_box_out,
+                           dist ? &dd : nullptr, s));
       h->launches += 10;  // 4 term passes, scales, 2 scans, constants, query, statistics
     }
   }
@@ -755,9 +800,30 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
     h->diag_pending = true;
     return LBM_OK;
   }
-  CK(cudaMemcpyAsync(stats_out, stats_dev, 8 * (size_t)nm * nL * 30, cudaMemcpyDeviceToHost,
-                     h->stream));
+  if (stats_out)
+    CK(cudaMemcpyAsync(stats_out, stats_dev, 8 * (size_t)nm * nL * 30, cudaMemcpyDeviceToHost,
+                       h->stream));
+  std::vector<unsigned long long> hist;
+  if (dist) {
+    hist.resize((size_t)nm * nL * hrow);
+    CK(cudaMemcpyAsync(hist.data(), dd.hist, 8 * hist.size(), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaMemcpyAsync(dist->mach_stats, dd.mach, 8 * (size_t)nm * nL * 2,
+                       cudaMemcpyDeviceToHost, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
+  if (dist) {  // rows [member][size][3][kDiagMaxEdges + 1] to the caller's layouts
+    const int bd = dist->n_delta + 1, bm = dist->n_mach + 1;
+    for (size_t r = 0; r < (size_t)nm * nL; ++r) {
+      const unsigned long long *src = hist.data() + r * hrow;
+      for (int q = 0; q < 2; ++q)
+        for (int b = 0; b < bd; ++b)
+          dist->delta_hist[(r * 2 + q) * bd + b] =
+              (long long)src[(size_t)q * (lbm::kDiagMaxEdges + 1) + b];
+      for (int b = 0; b < bm; ++b)
+        dist->mach_hist[r * bm + b] = (long long)src[2 * (size_t)(lbm::kDiagMaxEdges + 1) + b];
+    }
+  }
   return LBM_OK;
 }
 
@@ -789,6 +855,20 @@ int lbm_subvolume_balance_async(lbm_handle *h, const int *members, int n_members
   if (!stats_dev) return fail(h, LBM_ERR_ARG, "stats_dev is NULL");
   return balance_members(h, members, n_members, L, nL, origins, counts, nullptr, nullptr,
                          stats_dev);
+}
+
+int lbm_subvolume_distributions(lbm_handle *h, const int *members, int n_members, const int *L,
+                                int nL, const int *origins, const int *counts,
+                                const double *delta_edges, int n_delta_edges,
+                                const double *mach_edges, int n_mach_edges, double *stats_out,
+                                long long *delta_hist_out, long long *mach_hist_out,
+                                double *mach_stats_out) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (!members) return fail(h, LBM_ERR_ARG, "members is NULL");
+  DistRequest d{delta_edges, mach_edges, n_delta_edges, n_mach_edges,
+                delta_hist_out, mach_hist_out, mach_stats_out};
+  return balance_members(h, members, n_members, L, nL, origins, counts, stats_out, nullptr,
+                         nullptr, &d);
 }
 
 int lbm_diag_synchronize(lbm_handle *h) {

@@ -46,11 +46,13 @@ namespace {
 enum Field {
   U0X = 0, U0Y, DU01X, DU01Y, DU12X, DU12Y, DRHO, R0, FXR, FYR, A1, A2, WW, B1, B2, C1, C2,
   G1, G2, G3, K1, K2,
-  T0,  // T0..T11: term fields 0..11 (term 12, vortex stretching, is 0 in 2D)
-  NF = T0 + 12
+  T0,  // T0..T11: term fields 0..11 (term 12, vortex stretching, is 0 in 2D);
+       // T0 + 12: |u|^2 (the sub-volume Mach number of eq. (20))
+  NF = T0 + 13
 };
 constexpr int kSnapSlots = 3;
-static_assert(kSnapSlots + NF + 12 <= kDiagFields, "scratch too small");
+constexpr int kNT = 13;  // fields with a summed-area table: 12 terms, |u|^2
+static_assert(kSnapSlots + NF + kNT <= kDiagFields, "scratch too small");
 
 struct Grid {
   int nx, ny;
@@ -127,16 +129,19 @@ template <> __device__ double QConst::mean<double>() const { return mean_d; }
 template <> __device__ float QConst::mean<float>() const { return mean_f; }
 template <> __device__ double QConst::coef<double>() const { return coef_d; }
 template <> __device__ float QConst::coef<float>() const { return coef_f; }
-constexpr int kQConstDoubles = kDiagMaxL * 12 * (int)(sizeof(QConst) / sizeof(double));
+constexpr int kQConstDoubles = kDiagMaxL * kNT * (int)(sizeof(QConst) / sizeof(double));
 constexpr int kMaxQueryBlocks = 256;  // CTAs per (job, size, balance)
 
-// Per-job partials slot, in 8-byte words: [0, 32) scale factors and
-// exponents; the per-size query constants; the query CTA partials; then the
-// CTA maxima of the 12 term fields, [12][CTAs of the cell grid].
+// Per-job partials slot, in 8-byte words: [0, 40) scale factors 2^e,
+// 2^-e and the exponents e of the kNT tables; the per-size query constants
+// [size][kNT]; the query CTA partials [size][3 groups][CTA][kQStats]; then
+// the CTA maxima of the kNT fields, [kNT][CTAs of the cell grid].
 constexpr size_t kPartScales = 0;
-constexpr size_t kPartConsts = 32;
+constexpr size_t kPartConsts = 40;
 constexpr size_t kPartQuery = kPartConsts + kQConstDoubles;
-constexpr size_t kPartMax = kPartQuery + (size_t)kDiagMaxL * 2 * kMaxQueryBlocks * kQStats;
+constexpr size_t kPartMax = kPartQuery + (size_t)kDiagMaxL * 3 * kMaxQueryBlocks * kQStats;
+__host__ __device__ constexpr size_t inv_scale(int f) { return kPartScales + kNT + f; }
+__host__ __device__ constexpr size_t exps_at() { return kPartScales + 2 * kNT; }
 
 #define CELL_INDEX                                        \
   const int x = blockIdx.x * blockDim.x + threadIdx.x;    \
@@ -333,7 +338,7 @@ __device__ __forceinline__ Levels<T, true> levels_pairs(const DiagJob &J, size_t
 template <typename T, bool PAIRS>
 __global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) {
   JOB_CELLS;
-  T lhs = 0, uf = 0;
+  T lhs = 0, uf = 0, uu = 0;
   if (valid) {
     Levels<T, PAIRS> L;
     if constexpr (PAIRS)
@@ -364,6 +369,7 @@ __global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) 
     const T E0 = T(0.5) * L.r0 * q0;
     lhs = T(0.5) * (T(3) * dE01 - dE12);  // LHS^E
     uf = u0 * Fx + v0 * Fy;               // RHS^{E,3} = u . F
+    uu = q0;
     fld<T>(base, U0X, N)[c] = u0;
     fld<T>(base, U0Y, N)[c] = v0;
     fld<T>(base, DU01X, N)[c] = du01;
@@ -378,10 +384,11 @@ __global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) 
     fld<T>(base, A2, N)[c] = E0 * v0;
     fld<T>(base, T0 + 0, N)[c] = lhs;
     fld<T>(base, T0 + 3, N)[c] = uf;
+    fld<T>(base, T0 + 12, N)[c] = uu;
   }
-  const T mv[2] = {lhs, uf};
-  const int mf[2] = {0, 3};
-  block_absmax<T, 2>(mv, mf, J, blk, nblk);
+  const T mv[3] = {lhs, uf, uu};
+  const int mf[3] = {0, 3, 12};
+  block_absmax<T, 3>(mv, mf, J, blk, nblk);
 }
 
 // Pass 1 (radius 4): vorticity w = D_x u_y - D_y u_x and its level
@@ -604,12 +611,13 @@ __global__ void k_global_scale(double *sums, size_t N) {
 // Scale exponents, one CTA per job and one warp per field: e_f with
 // N * max|T_f| * 2^e_f < 2^62 (so every partial sum of the table fits in
 // int64), capped so that 2^e_f is a finite float.  scales[f] = 2^e_f,
-// scales[12 + f] = 2^-e_f, and the exponent itself as ((int *)(scales + 24))[f].
+// scales[kNT + f] = 2^-e_f, and the exponent itself at exps_at() as int.
+// nF: the number of fields with a table in this call (12, or 13 with |u|^2).
 template <typename T>
-__global__ void k_scales(const DiagJob *__restrict__ jobs) {
+__global__ void k_scales(const DiagJob *__restrict__ jobs, int nF) {
   const DiagJob &J = jobs[blockIdx.x];
   const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (f >= 12) return;
+  if (f >= nF) return;
   const size_t N = (size_t)J.nx * J.ny;
   const int nblk = ((J.nx + 31) / 32) * ((J.ny + 7) / 8);
   const typename AbsBits<T>::U *mb = max_part<T>(J) + (size_t)f * nblk;
@@ -626,10 +634,9 @@ __global__ void k_scales(const DiagJob *__restrict__ jobs) {
       e = 62 - nbits - ex;
       if (e > 120) e = 120;
     }
-    double *scales = J.part + kPartScales;
-    scales[f] = ldexp(1.0, e);
-    scales[12 + f] = ldexp(1.0, -e);
-    reinterpret_cast<int *>(scales + 24)[f] = e;
+    J.part[kPartScales + f] = ldexp(1.0, e);
+    J.part[inv_scale(f)] = ldexp(1.0, -e);
+    reinterpret_cast<int *>(J.part + exps_at())[f] = e;
   }
 }
 
@@ -697,7 +704,7 @@ __global__ void __launch_bounds__(128) k_sat_rows(const DiagJob *__restrict__ jo
   const T *row = fld<T>(J.base, T0 + f, N) + (size_t)y * nx;
   long long *tab = sat_base(J.base, N) + (size_t)f * sat_stride(nx, ny);
   long long *out = tab + (size_t)(y + 1) * (nx + 1) + 1;  // row y+1, column 1..nx
-  const int e = reinterpret_cast<const int *>(J.part + kPartScales + 24)[f];
+  const int e = reinterpret_cast<const int *>(J.part + exps_at())[f];
   const bool vec = nx % 4 == 0 && (reinterpret_cast<uintptr_t>(row) & 15) == 0;
   __shared__ long long wsum[4];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -806,18 +813,18 @@ __device__ __forceinline__ MT delta_of(MT lhs, MT sum, MT mx) {
   return num / mx;
 }
 
-// One CTA per job, one thread per (size, field).
-__global__ void k_query_consts(const DiagJob *__restrict__ jobs) {
+// One CTA per job, one thread per (size, field); constants at [size][kNT].
+__global__ void k_query_consts(const DiagJob *__restrict__ jobs, int nF) {
   const DiagJob &J = jobs[blockIdx.x];
   const int t = threadIdx.x;
-  if (t >= J.nL * 12) return;
+  const int iL = t / kNT, k = t % kNT;
+  if (iL >= J.nL || k >= nF) return;
   const int nx = J.nx, ny = J.ny;
   const size_t N = (size_t)nx * ny;
-  const int iL = t / 12, k = t % 12;
   const double area = (double)J.meta[8 * iL] * (double)J.meta[8 * iL];
   const long long total =
       sat_base(J.base, N)[(size_t)k * sat_stride(nx, ny) + (size_t)ny * (nx + 1) + nx];
-  const double inv = J.part[kPartScales + 12 + k];
+  const double inv = J.part[inv_scale(k)];
   QConst q;
   q.mean_d = (double)total * inv / (double)N;
   q.coef_d = inv / area;
@@ -858,18 +865,37 @@ __device__ __forceinline__ float to_mt<float>(long long v) {
   return __uint_as_float(bits);
 }
 
-// Grid (query CTAs, sizes, 2 x jobs); blockIdx.z = 2 * job + balance, the
-// balance 0 = energy (fields 0..5: LHS^E, RHS^{E,1..5}), 1 = enstrophy
-// (fields 6..11: LHS^O, RHS^{O,1..5}; RHS^{O,6} is identically 0 in 2D and
-// adds nothing).  One thread per (box, balance): exact integer box sums of
-// its 6 term fields, their deviations d_k from the field means, the box
-// means, the balancing error, and sums of d_k, d_k^2, delta and delta^2.
-template <typename MT, bool PER_BOX>
+// Bin of v among ne ascending edges: the number of edges <= v.
+template <typename MT>
+__device__ __forceinline__ int bin_of(MT v, const MT *edges, int ne) {
+  int lo = 0, hi = ne;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (edges[mid] <= v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Grid (query CTAs, sizes, NG x jobs), NG = 2, or 3 with the distributions
+// (EXT); blockIdx.z = NG * job + group.  Group 0 = energy balance (fields
+// 0..5: LHS^E, RHS^{E,1..5}), 1 = enstrophy (fields 6..11: LHS^O,
+// RHS^{O,1..5}; RHS^{O,6} is identically 0 in 2D and adds nothing), 2 =
+// sub-volume Mach number (field 12, |u|^2).  One thread per (box, group):
+// exact integer box sums of the group's fields, their deviations d_k from
+// the field means, the box means, the balancing error (or Ma_V), and sums of
+// d_k, d_k^2 and of the error's (or Ma_V's) deviation and its square; with
+// EXT also a CTA histogram in shared memory, added to the global one with
+// integer atomics (order-free, so deterministic).
+template <typename MT, bool PER_BOX, bool EXT>
 __global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
                                                const int *__restrict__ origins,
-                                               double *per_box) {
-  const DiagJob &J = jobs[blockIdx.z >> 1];
-  const int iL = blockIdx.y, grp = blockIdx.z & 1, k0 = 6 * grp;
+                                               double *per_box, DiagDist ext) {
+  constexpr int NG = EXT ? 3 : 2;
+  const DiagJob &J = jobs[blockIdx.z / NG];
+  const int iL = blockIdx.y, grp = blockIdx.z % NG, k0 = 6 * grp;
   if (iL >= J.nL || (int)blockIdx.x >= J.qblocks) return;
   const int qb = J.qblocks;
   const int nx = J.nx, ny = J.ny;
@@ -878,7 +904,23 @@ __global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
   const size_t N = (size_t)nx * ny;
   const size_t sp = sat_stride(nx, ny), rs = (size_t)nx + 1;
   const long long *S = sat_base(J.base, N) + (size_t)k0 * sp;
-  const QConst *qc = reinterpret_cast<const QConst *>(J.part + kPartConsts) + (size_t)iL * 12 + k0;
+  const QConst *qc =
+      reinterpret_cast<const QConst *>(J.part + kPartConsts) + (size_t)iL * kNT + k0;
+  const int nfield = grp == 2 ? 1 : 6;
+  __shared__ MT sedge[EXT ? kDiagMaxEdges : 1];
+  __shared__ unsigned shist[EXT ? kDiagMaxEdges + 1 : 1];
+  int ne = 0;
+  if constexpr (EXT) {
+    ne = grp == 2 ? ext.n_mach : ext.n_delta;
+    const double *e = grp == 2 ? ext.mach_edges : ext.delta_edges;
+    for (int i = threadIdx.x; i <= ne; i += blockDim.x) {
+      if (i < ne) sedge[i] = (MT)e[i];
+      shist[i] = 0u;
+    }
+    __syncthreads();
+  }
+  // group 2: deviations of Ma_V from the whole-grid value
+  const MT ma_ref = EXT ? sqrt(fmax(qc[0].mean<MT>(), MT(0))) * MT(1.7320508075688772) : MT(0);
   MT s1[6], s2[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
@@ -900,6 +942,7 @@ __global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
     double *o = PER_BOX ? per_box + ((size_t)meta[8 * iL + 3] + b) * 15 : nullptr;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
+      if (j >= nfield) break;
       const long long *Sk = S + (size_t)j * sp;
       unsigned long long bs;
       if (inside) {  // no periodic wrap: four direct corner loads
@@ -923,11 +966,22 @@ __global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
       }
       if (PER_BOX) o[2 + k0 + j] = (double)v;
     }
-    const MT dl = delta_of(lhs, sum, mx);
-    d1 += dl;
-    d2 += dl * dl;
+    MT val;  // delta of the group's balance, or Ma_V
+    if (EXT && grp == 2) {
+      val = sqrt(fmax(lhs, MT(0))) * MT(1.7320508075688772);
+      const MT dm = val - ma_ref;
+      d1 += dm;
+      d2 += dm * dm;
+    } else {
+      val = delta_of(lhs, sum, mx);
+      d1 += val;
+      d2 += val * val;
+    }
+    if constexpr (EXT) {
+      if (val == val) atomicAdd(&shist[bin_of(val, sedge, ne)], 1u);
+    }
     if (PER_BOX) {
-      o[grp] = (double)dl;
+      o[grp] = (double)val;
       if (grp == 1) o[14] = 0.0;
     }
   }
@@ -940,13 +994,21 @@ __global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
     acc[3 + 2 * j] = s2[j];
   }
   block_sum_store_mt<kQStats, MT>(
-      acc, J.part + kPartQuery + (((size_t)iL * 2 + grp) * qb + blockIdx.x) * kQStats);
+      acc, J.part + kPartQuery + (((size_t)iL * 3 + grp) * qb + blockIdx.x) * kQStats);
+  if constexpr (EXT) {
+    __syncthreads();
+    unsigned long long *h =
+        ext.hist + ((size_t)meta[8 * iL + 4] * 3 + grp) * (kDiagMaxEdges + 1);
+    for (int i = threadIdx.x; i <= ne; i += blockDim.x)
+      if (shist[i]) atomicAdd(&h[i], (unsigned long long)shist[i]);
+  }
 }
 
-// Mean and population standard deviation of the 15 quantities per size.
-// Grid (sizes, jobs); 8 threads per (balance, slot) sum interleaved block
-// partials in a fixed order.
-__global__ void k_stats_final(const DiagJob *__restrict__ jobs, double *stats) {
+// Mean and population standard deviation of the 15 quantities per size,
+// and with `mach` those of Ma_V.  Grid (sizes, jobs), 384 threads: 8 per
+// (group, slot) sum interleaved block partials in a fixed order.
+template <typename MT>
+__global__ void k_stats_final(const DiagJob *__restrict__ jobs, double *stats, double *mach) {
   const DiagJob &J = jobs[blockIdx.y];
   const int iL = blockIdx.x;
   if (iL >= J.nL) return;
@@ -954,19 +1016,20 @@ __global__ void k_stats_final(const DiagJob *__restrict__ jobs, double *stats) {
   const double *partials = J.part + kPartQuery;
   const QConst *consts = reinterpret_cast<const QConst *>(J.part + kPartConsts);
   const int q = threadIdx.x >> 3, j = threadIdx.x & 7;  // q = grp * 14 + slot
-  __shared__ double sh[2 * kQStats][8];
+  const int ngrp = mach ? 3 : 2;
+  __shared__ double sh[3 * kQStats][8];
   double a = 0.0;
-  if (q < 2 * kQStats) {
+  if (q < ngrp * kQStats) {
     const int grp = q / kQStats, slot = q % kQStats;
     for (int b = j; b < nblocks; b += 8)
-      a += partials[(((size_t)iL * 2 + grp) * nblocks + b) * kQStats + slot];
+      a += partials[(((size_t)iL * 3 + grp) * nblocks + b) * kQStats + slot];
     sh[q][j] = a;
   }
   __syncthreads();
   const int t = threadIdx.x;
+  const int nb = J.meta[8 * iL + 1];
+  const size_t orow = (size_t)J.meta[8 * iL + 4];
   if (t < 15) {
-    const int nb = J.meta[8 * iL + 1];
-    const size_t orow = (size_t)J.meta[8 * iL + 4];
     double mean = 0.0, sd = 0.0;
     if (t < 14) {
       int row;  // row of sh holding the (sum, sum of squares) pair
@@ -976,7 +1039,7 @@ __global__ void k_stats_final(const DiagJob *__restrict__ jobs, double *stats) {
       } else {
         const int k = t - 2, grp = k / 6;
         row = grp * kQStats + 2 + 2 * (k % 6);
-        shift = consts[(size_t)iL * 12 + k].mean_d;
+        shift = consts[(size_t)iL * kNT + k].mean_d;
       }
       double s1 = 0.0, s2 = 0.0;
       for (int m = 0; m < 8; ++m) {
@@ -989,6 +1052,19 @@ __global__ void k_stats_final(const DiagJob *__restrict__ jobs, double *stats) {
     }
     stats[(orow * 15 + t) * 2] = mean;
     stats[(orow * 15 + t) * 2 + 1] = sd;
+  } else if (t == 32 && mach) {
+    const int row = 2 * kQStats;
+    double s1 = 0.0, s2 = 0.0;
+    for (int m = 0; m < 8; ++m) {
+      s1 += sh[row][m];
+      s2 += sh[row + 1][m];
+    }
+    // the reference value the query subtracted, in the query precision
+    const QConst &c = consts[(size_t)iL * kNT + 12];
+    const double ref = (double)(sqrt(fmax(c.mean<MT>(), MT(0))) * MT(1.7320508075688772));
+    const double m1 = s1 / nb;
+    mach[orow * 2] = ref + m1;
+    mach[orow * 2 + 1] = sqrt(fmax(s2 / nb - m1 * m1, 0.0));
   }
 }
 
@@ -1011,7 +1087,7 @@ dim3 cells_grid(const Grid &g, dim3 b) {
 template <typename T, typename MT>
 cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int G, bool pairs,
                              const int *origins, double *stats, double *per_box,
-                             cudaStream_t s) {
+                             const DiagDist *dist, cudaStream_t s) {
   int nx = 1, ny = 1, nL = 1, qblocks = 1;
   for (int j = 0; j < G; ++j) {
     nx = std::max(nx, jobs_host[j].nx);
@@ -1019,6 +1095,7 @@ cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int 
     nL = std::max(nL, jobs_host[j].nL);
     qblocks = std::max(qblocks, jobs_host[j].qblocks);
   }
+  const int nF = dist ? kNT : 12;  // |u|^2 gets a table only for Ma_V
   const dim3 cb(32, 8), cg((nx + 31) / 32, (ny + 7) / 8, G);
   if (pairs)
     k_prep<T, true><<<cg, cb, 0, s>>>(jobs);
@@ -1027,16 +1104,22 @@ cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int 
   k_grad<T><<<cg, cb, 0, s>>>(jobs);
   k_flux<T><<<cg, cb, 0, s>>>(jobs);
   k_curl<T><<<cg, cb, 0, s>>>(jobs);
-  k_scales<T><<<G, 12 * 32, 0, s>>>(jobs);
-  k_sat_rows<T><<<dim3(ny, 12, G), 128, 0, s>>>(jobs);
-  k_sat_cols<<<dim3((nx + 31) / 32, 12, G), dim3(32, 8), 0, s>>>(jobs);
-  k_query_consts<<<G, kDiagMaxL * 12, 0, s>>>(jobs);
-  const dim3 qg(qblocks, nL, 2 * G);
-  if (per_box)
-    k_query<MT, true><<<qg, 256, 0, s>>>(jobs, origins, per_box);
-  else
-    k_query<MT, false><<<qg, 256, 0, s>>>(jobs, origins, nullptr);
-  k_stats_final<<<dim3(nL, G), 256, 0, s>>>(jobs, stats);
+  k_scales<T><<<G, kNT * 32, 0, s>>>(jobs, nF);
+  k_sat_rows<T><<<dim3(ny, nF, G), 128, 0, s>>>(jobs);
+  k_sat_cols<<<dim3((nx + 31) / 32, nF, G), dim3(32, 8), 0, s>>>(jobs);
+  k_query_consts<<<G, kDiagMaxL * kNT, 0, s>>>(jobs, nF);
+  const DiagDist none{};
+  if (dist) {
+    k_query<MT, false, true><<<dim3(qblocks, nL, 3 * G), 256, 0, s>>>(jobs, origins, nullptr,
+                                                                       *dist);
+  } else {
+    const dim3 qg(qblocks, nL, 2 * G);
+    if (per_box)
+      k_query<MT, true, false><<<qg, 256, 0, s>>>(jobs, origins, per_box, none);
+    else
+      k_query<MT, false, false><<<qg, 256, 0, s>>>(jobs, origins, nullptr, none);
+  }
+  k_stats_final<MT><<<dim3(nL, G), 384, 0, s>>>(jobs, stats, dist ? dist->mach : nullptr);
   return cudaGetLastError();
 }
 
@@ -1077,27 +1160,31 @@ int diag_query_blocks(int max_boxes, bool origin_list) {
 }
 
 size_t diag_slot_doubles(size_t Nmax, size_t pad) {
-  // snapshot slots + term-stage fields + 12 padded tables, in whole 256-byte
+  // snapshot slots + term-stage fields + kNT padded tables, in whole 256-byte
   // units (so field rows keep the 16-byte alignment of vector loads)
-  const size_t d = (size_t)(kSnapSlots + NF) * Nmax + 12 * (Nmax + pad);
+  const size_t d = (size_t)(kSnapSlots + NF) * Nmax + kNT * (Nmax + pad);
   return (d + 31) / 32 * 32;
 }
 
 size_t diag_job_partials(size_t Nmax, size_t pad) {
   // CTAs of the 32 x 8 cell grid: ceil(nx/32) ceil(ny/8) <= N/256 + pad/8 + 1
   const size_t ctas = Nmax / 256 + pad / 8 + 2;
-  return kPartMax + 12 * ctas;  // 8-byte words
+  return kPartMax + kNT * ctas;  // 8-byte words
 }
 
 cudaError_t diag_balance(const DiagJob *jobs_host, const DiagJob *jobs_dev, int G,
                          int precision, bool pairs, const int *origins_dev,
-                         double *stats_dev, double *per_box_dev, cudaStream_t s) {
-  if (G < 1 || (per_box_dev && G != 1)) return cudaErrorInvalidValue;
+                         double *stats_dev, double *per_box_dev, const DiagDist *dist,
+                         cudaStream_t s) {
+  if (G < 1 || (per_box_dev && G != 1) || (per_box_dev && dist)) return cudaErrorInvalidValue;
+  if (dist && (dist->n_delta < 1 || dist->n_delta > kDiagMaxEdges || dist->n_mach < 1 ||
+               dist->n_mach > kDiagMaxEdges))
+    return cudaErrorInvalidValue;
   if (precision == 32)
     return balance_launches<float, float>(jobs_host, jobs_dev, G, pairs, origins_dev,
-                                          stats_dev, per_box_dev, s);
+                                          stats_dev, per_box_dev, dist, s);
   return balance_launches<double, double>(jobs_host, jobs_dev, G, pairs, origins_dev,
-                                          stats_dev, per_box_dev, s);
+                                          stats_dev, per_box_dev, dist, s);
 }
 
 }  // namespace lbm

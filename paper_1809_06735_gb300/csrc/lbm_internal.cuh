@@ -102,10 +102,11 @@ struct DiagScratch {
   double *jpart;      // per-slot partials (slot j at jpart + j * jpart_doubles)
   size_t jpart_doubles;
 };
-constexpr int kDiagFields = 50;
+constexpr int kDiagFields = 52;
 constexpr int kMaxPartialBlocks = 1024;
 constexpr int kGeneralPartials = 8 * kMaxPartialBlocks;
 constexpr int kDiagMaxL = 32;  // box sizes per balance call
+constexpr int kDiagMaxEdges = 256;  // histogram bin edges per quantity
 
 cudaError_t diag_moments(const Member &hm, const double *snap3, double *rho, double *ux,
                          double *uy, double *omega, const DiagScratch &sc, cudaStream_t s);
@@ -144,9 +145,20 @@ size_t diag_job_partials(size_t Nmax, size_t pad);
 // launches in all.  origins_dev: concatenated (x0, y0) pairs shared by every
 // job (NULL when each size uses all periodic origins); stats_dev: rows of
 // [15][2] at the statistics rows; per_box_dev only with G == 1.
+// Distributions requested from a batched diagnostic: histograms of the
+// balancing errors and of the sub-volume Mach number Ma_V (eq. 20), and the
+// mean and standard deviation of Ma_V, per statistics row.
+struct DiagDist {
+  const double *delta_edges, *mach_edges;  // device, ascending, 1..kDiagMaxEdges
+  int n_delta, n_mach;
+  unsigned long long *hist;  // device [row][3: delta^E, delta^O, Ma_V][kDiagMaxEdges + 1],
+                             // zeroed by the caller; counts are added
+  double *mach;              // device [row][2]
+};
 cudaError_t diag_balance(const DiagJob *jobs_host, const DiagJob *jobs_dev, int G,
                          int precision, bool pairs, const int *origins_dev,
-                         double *stats_dev, double *per_box_dev, cudaStream_t s);
+                         double *stats_dev, double *per_box_dev, const DiagDist *dist,
+                         cudaStream_t s);
 
 // Adjoint (lbm_adjoint.cu).
 cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_in,
