@@ -237,7 +237,7 @@ def run_reference(args):
 def workload_config():
     wl = li.decaying_ensemble_workload()
     return {"workload": wl["name"], "members_per_gpu": wl["members"], "grid": [wl["n"], wl["n"]],
-            "tau": wl["tau"], "precision": "fp32 deviation populations, fp64 diagnostics",
+            "tau": wl["tau"], "precision": "fp32 deviation populations; diagnostic terms in fp32 from compensated snapshots, exact int64 box sums, fp64 statistics",
             "lbm_steps_per_step": PERIOD,
             "diagnostic": "per step, every member: balance terms + SAT + the paper's "
                           "Table 1 random boxes (56000 per member) at L=2..256",
