@@ -54,16 +54,19 @@ def _load():
             lib = ctypes.CDLL(build())
             D, I, P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
             lib.orc_feq.argtypes = [D, D, D, P]
-            lib.orc_force_ext.argtypes = [I, I, I, D, I, I, I, P, P]
+            lib.orc_force_ext.argtypes = [I, I, P, I, I, P, P]
+            lib.orc_force_field.argtypes = [I, I, P, P, P, P]
             lib.orc_collide_cell.argtypes = [P, D, D, D, D, P]
-            lib.orc_collide.argtypes = [I, I, D, I, D, I, D, P, P]
+            lib.orc_collide.argtypes = [I, I, D, P, P, P]
+            lib.orc_collide.restype = I
             lib.orc_stream.argtypes = [I, I, P, P]
-            lib.orc_run.argtypes = [I, I, D, I, D, I, D, P, I]
+            lib.orc_run.argtypes = [I, I, D, P, P, I]
             lib.orc_run.restype = I
-            lib.orc_run_window.argtypes = [I, I, D, I, D, I, D, P, I, I, I, I, I]
+            lib.orc_run_window.argtypes = [I, I, D, P, P, I, I, I, I, I]
             lib.orc_run_window.restype = I
             lib.orc_init.argtypes = [I, I, P, P, P, P]
-            lib.orc_moments.argtypes = [I, I, I, D, I, D, P, P, P, P, P, P]
+            lib.orc_moments.argtypes = [I, I, P, P, P, P, P, P, P]
+            lib.orc_moments.restype = I
             lib.orc_ddx.argtypes = [I, I, P, P]
             lib.orc_ddy.argtypes = [I, I, P, P]
             lib.orc_bdf2.argtypes = [ctypes.c_size_t, P, P, P, P]
@@ -74,11 +77,11 @@ def _load():
             lib.orc_box_values.argtypes = [I, I, P, I, I, I, P]
             lib.orc_balance_stats.argtypes = [I, I, P, P, I, P, I, P, P]
             lib.orc_balance_stats.restype = I
-            lib.orc_terms_from_populations.argtypes = [I, I, D, I, D, I, D, P, P, P, P]
+            lib.orc_terms_from_populations.argtypes = [I, I, D, P, P, P, P, P]
             lib.orc_terms_from_populations.restype = I
-            lib.orc_global.argtypes = [I, I, D, I, D, I, D, P, P]
+            lib.orc_global.argtypes = [I, I, D, P, P, P]
             lib.orc_global.restype = I
-            lib.orc_objective.argtypes = [I, I, D, I, D, I, D, P, I, I, I, I, I, P]
+            lib.orc_objective.argtypes = [I, I, D, P, P, I, I, I, I, I, P]
             lib.orc_objective.restype = I
             lib.orc_lattice.argtypes = [P, P, P]
             lib.orc_box_mach.argtypes = [I, I, P, P, I, I, I]
@@ -100,15 +103,25 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+class _ForceC(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("F0", ctypes.c_double), ("kf", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("phase", ctypes.c_double), ("FR0", ctypes.c_double)]
+
+
 class Force:
-    """Forcing of one member: Kolmogorov amplitude F0 at wavenumber kf (in
-    units of 2 pi / N) when kind == 1, plus drag alpha on the bare momentum."""
+    """Forcing of one member: kind 1 = Kolmogorov amplitude F0 at wavenumber
+    kf (in units of 2 pi / N); kind 2 = the paper's shell force of eqs. (14),
+    (15) (F^T_0 = F0, phase) plus the damping of eq. (16) (F^R_0 = FR0);
+    in every case drag alpha on the bare momentum."""
 
-    def __init__(self, kind: int = 0, F0: float = 0.0, kf: int = 0, alpha: float = 0.0):
+    def __init__(self, kind: int = 0, F0: float = 0.0, kf: int = 0, alpha: float = 0.0,
+                 phase: float = 0.0, FR0: float = 0.0):
         self.kind, self.F0, self.kf, self.alpha = int(kind), float(F0), int(kf), float(alpha)
+        self.phase, self.FR0 = float(phase), float(FR0)
+        self._c = _ForceC(self.kind, self.F0, self.kf, self.alpha, self.phase, self.FR0)
 
-    def args(self):
-        return (self.kind, self.F0, self.kf, self.alpha)
+    def ptr(self):
+        return ctypes.byref(self._c)
 
 
 NO_FORCE = Force()
@@ -129,10 +142,19 @@ def feq(rho: float, ux: float, uy: float) -> np.ndarray:
     return out
 
 
+def force_field(f, force: Force):
+    """External force (Fx, Fy) [ny, nx] of every cell for the state f, drag
+    excluded: the static force plus, for kind 2, the damping of eq. (16)."""
+    f = _f64(f)
+    _, ny, nx = f.shape
+    Fx, Fy = np.empty((ny, nx)), np.empty((ny, nx))
+    _load().orc_force_field(nx, ny, force.ptr(), _p(f), _p(Fx), _p(Fy))
+    return Fx, Fy
+
+
 def force_ext(nx, ny, force: Force, x, y):
     fx, fy = ctypes.c_double(), ctypes.c_double()
-    _load().orc_force_ext(nx, ny, force.kind, force.F0, force.kf, x, y,
-                          ctypes.byref(fx), ctypes.byref(fy))
+    _load().orc_force_ext(nx, ny, force.ptr(), x, y, ctypes.byref(fx), ctypes.byref(fy))
     return fx.value, fy.value
 
 
@@ -147,8 +169,8 @@ def collide(f, tau, force: Force = NO_FORCE):
     f = _f64(f)
     _, ny, nx = f.shape
     out = np.empty_like(f)
-    k, F0, kf, a = force.args()
-    _load().orc_collide(nx, ny, tau, k, F0, kf, a, _p(f), _p(out))
+    if _load().orc_collide(nx, ny, tau, force.ptr(), _p(f), _p(out)) != 0:
+        raise MemoryError("oracle collide failed")
     return out
 
 
@@ -172,8 +194,7 @@ def run(f, nsteps, tau, force: Force = NO_FORCE):
     """Return f after nsteps steps of eq. (1) (input not modified)."""
     f = _f64(f).copy()
     _, ny, nx = f.shape
-    k, F0, kf, a = force.args()
-    rc = _load().orc_run(nx, ny, tau, k, F0, kf, a, _p(f), int(nsteps))
+    rc = _load().orc_run(nx, ny, tau, force.ptr(), _p(f), int(nsteps))
     if rc != 0:
         raise MemoryError("oracle run failed")
     return f
@@ -185,8 +206,7 @@ def run_window(f_window, nsteps, tau, force: Force, x0, y0, NX, NY):
     from the window's edges are valid afterwards (light cone)."""
     f = _f64(f_window).copy()
     _, wy, wx = f.shape
-    k, F0, kf, a = force.args()
-    rc = _load().orc_run_window(wx, wy, tau, k, F0, kf, a, _p(f), int(nsteps), int(x0),
+    rc = _load().orc_run_window(wx, wy, tau, force.ptr(), _p(f), int(nsteps), int(x0),
                                 int(y0), int(NX), int(NY))
     if rc != 0:
         raise MemoryError("oracle window run failed")
@@ -198,8 +218,7 @@ def moments(f, force: Force = NO_FORCE):
     f = _f64(f)
     _, ny, nx = f.shape
     out = {k: np.empty((ny, nx)) for k in ("rho", "jx", "jy", "ux", "uy")}
-    k, F0, kf, a = force.args()
-    _load().orc_moments(nx, ny, k, F0, kf, a, _p(f), _p(out["rho"]), _p(out["jx"]),
+    _load().orc_moments(nx, ny, force.ptr(), _p(f), _p(out["rho"]), _p(out["jx"]),
                         _p(out["jy"]), _p(out["ux"]), _p(out["uy"]))
     return out
 
@@ -251,8 +270,7 @@ def terms_from_populations(f_n, f_n1, f_n2, tau, force: Force = NO_FORCE):
     f_n, f_n1, f_n2 = _f64(f_n), _f64(f_n1), _f64(f_n2)
     _, ny, nx = f_n.shape
     out = np.empty((NT, ny, nx))
-    k, F0, kf, a = force.args()
-    rc = _load().orc_terms_from_populations(nx, ny, tau, k, F0, kf, a, _p(f_n), _p(f_n1),
+    rc = _load().orc_terms_from_populations(nx, ny, tau, force.ptr(), _p(f_n), _p(f_n1),
                                             _p(f_n2), _p(out))
     if rc != 0:
         raise MemoryError("oracle terms failed")
@@ -338,8 +356,7 @@ def global_quantities(f, tau, force: Force = NO_FORCE):
     f = _f64(f)
     _, ny, nx = f.shape
     out = np.empty(7)
-    k, F0, kf, a = force.args()
-    rc = _load().orc_global(nx, ny, tau, k, F0, kf, a, _p(f), _p(out))
+    rc = _load().orc_global(nx, ny, tau, force.ptr(), _p(f), _p(out))
     if rc != 0:
         raise MemoryError("oracle global failed")
     return out
@@ -350,8 +367,7 @@ def objective(f0, tau, force: Force, n0, n1, bx, by, L):
     f0 = _f64(f0)
     _, ny, nx = f0.shape
     J = ctypes.c_double()
-    k, F0, kf, a = force.args()
-    rc = _load().orc_objective(nx, ny, tau, k, F0, kf, a, _p(f0), int(n0), int(n1),
+    rc = _load().orc_objective(nx, ny, tau, force.ptr(), _p(f0), int(n0), int(n1),
                                int(bx), int(by), int(L), ctypes.byref(J))
     if rc != 0:
         raise MemoryError("oracle objective failed")

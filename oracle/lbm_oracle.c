@@ -46,6 +46,22 @@ static const double TW[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
 static const double CS2 = 1.0 / 3.0;
 static const double PI = 3.14159265358979323846;
 
+/* Forcing of one member (Sec. 3 and the workloads):
+ *   kind 0: none;
+ *   kind 1: Kolmogorov F_ext = F0 (sin(2 pi kf y/ny), sin(2 pi kf x/nx));
+ *   kind 2: the paper's turbulence forcing, the shell force of eqs. (14),
+ *           (15) with amplitude F0 = F^T_0 and phase `phase`, plus the
+ *           large-scale damping of eq. (16) with amplitude FR0 = F^R_0;
+ * and in every case the linear drag -alpha j on the bare momentum. */
+typedef struct {
+  int kind;
+  double F0;
+  int kf;
+  double alpha;
+  double phase;
+  double FR0;
+} orc_force_t;
+
 static int wrap(int i, int n) {
   int r = i % n;
   return r < 0 ? r + n : r;
@@ -75,17 +91,106 @@ void orc_feq(double rho, double ux, double uy, double *feq) {
   }
 }
 
-/* External body force at cell (x, y): the Kolmogorov force
- * F0 (sin(2 pi kf y / ny), sin(2 pi kf x / nx)) when force_kind == 1,
- * zero otherwise. */
-void orc_force_ext(int nx, int ny, int force_kind, double F0, int kf, int x,
-                   int y, double *Fx, double *Fy) {
-  if (force_kind == 1) {
-    *Fx = F0 * sin(2.0 * PI * kf * (double)y / (double)ny);
-    *Fy = F0 * sin(2.0 * PI * kf * (double)x / (double)nx);
-  } else {
-    *Fx = 0.0;
-    *Fy = 0.0;
+/* Time-independent external body force at cell (x, y): the Kolmogorov
+ * force F0 (sin(2 pi kf y / ny), sin(2 pi kf x / nx)) for kind 1; for kind 2
+ * the shell force of eqs. (14), (15),
+ *   psi(x) = F^T_0 sum_k cos(2 pi (kx x / nx + ky y / ny) + phi),
+ *   F^T = (d_y psi, -d_x psi)  (exact derivatives of each cosine),
+ * the sum over one wavevector of each pair +-k with 5 <= |k| <= 7 (ky > 0,
+ * or ky = 0 and kx > 0; over both members of each pair the phase would only
+ * rescale the amplitude by 2 cos phi); zero otherwise. */
+void orc_force_ext(int nx, int ny, const orc_force_t *F, int x, int y,
+                   double *Fx, double *Fy) {
+  *Fx = 0.0;
+  *Fy = 0.0;
+  if (F->kind == 1) {
+    *Fx = F->F0 * sin(2.0 * PI * F->kf * (double)y / (double)ny);
+    *Fy = F->F0 * sin(2.0 * PI * F->kf * (double)x / (double)nx);
+  } else if (F->kind == 2) {
+    double fx = 0.0, fy = 0.0;
+    for (int ky = 0; ky <= 7; ++ky)
+      for (int kx = -7; kx <= 7; ++kx) {
+        int k2 = kx * kx + ky * ky;
+        if (k2 < 25 || k2 > 49) continue;
+        if (ky == 0 && kx <= 0) continue;
+        double th = 2.0 * PI * (kx * (double)x / nx + ky * (double)y / ny) + F->phase;
+        /* d_y cos(th) = -sin(th) 2 pi ky / ny; -d_x cos(th) = sin(th) 2 pi kx / nx */
+        fx -= sin(th) * 2.0 * PI * ky / ny;
+        fy += sin(th) * 2.0 * PI * kx / nx;
+      }
+    *Fx = F->F0 * fx;
+    *Fy = F->F0 * fy;
+  }
+}
+
+/* Large-scale damping of eq. (16) for the state f (kind 2):
+ *   F^R(x) = -F^R_0 sum_{1 <= |k| <= 2} u^(k) exp(2 pi i (kx x / nx + ky y / ny)),
+ *   u^(k) = (1 / (nx ny)) sum_x u(x) exp(-2 pi i (kx x / nx + ky y / ny)),
+ * over the 12 wavevectors of the shell, u = j / rho the bare velocity of f.
+ * With u^(k) = C_k - i S_k (C, S the cosine and sine sums over N) the
+ * real part of each term is C_k cos(th) + S_k sin(th). */
+static void damping_field(int nx, int ny, double FR0, const double *f,
+                          double *FRx, double *FRy) {
+  size_t N = (size_t)nx * ny;
+  double *u = (double *)malloc(sizeof(double) * 2 * N);
+  if (!u) return;
+  for (size_t c = 0; c < N; ++c) {
+    double r = 0.0, a = 0.0, b = 0.0;
+    for (int l = 0; l < Q; ++l) {
+      r += f[l * N + c];
+      a += CX[l] * f[l * N + c];
+      b += CY[l] * f[l * N + c];
+    }
+    u[c] = a / r;
+    u[N + c] = b / r;
+  }
+  for (size_t c = 0; c < N; ++c) FRx[c] = FRy[c] = 0.0;
+  for (int ky = -2; ky <= 2; ++ky)
+    for (int kx = -2; kx <= 2; ++kx) {
+      int k2 = kx * kx + ky * ky;
+      if (k2 < 1 || k2 > 4) continue;
+      double Cx = 0.0, Sx = 0.0, Cy = 0.0, Sy = 0.0;
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          size_t c = (size_t)y * nx + x;
+          double th = 2.0 * PI * (kx * (double)x / nx + ky * (double)y / ny);
+          Cx += u[c] * cos(th);
+          Sx += u[c] * sin(th);
+          Cy += u[N + c] * cos(th);
+          Sy += u[N + c] * sin(th);
+        }
+      Cx /= (double)N;
+      Sx /= (double)N;
+      Cy /= (double)N;
+      Sy /= (double)N;
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          size_t c = (size_t)y * nx + x;
+          double th = 2.0 * PI * (kx * (double)x / nx + ky * (double)y / ny);
+          FRx[c] -= FR0 * (Cx * cos(th) + Sx * sin(th));
+          FRy[c] -= FR0 * (Cy * cos(th) + Sy * sin(th));
+        }
+    }
+  free(u);
+}
+
+/* External force of every cell for the state f (drag excluded):
+ * orc_force_ext plus, for kind 2, the damping of eq. (16). */
+void orc_force_field(int nx, int ny, const orc_force_t *F, const double *f,
+                     double *Fx, double *Fy) {
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x)
+      orc_force_ext(nx, ny, F, x, y, &Fx[(size_t)y * nx + x], &Fy[(size_t)y * nx + x]);
+  if (F->kind == 2 && F->FR0 != 0.0) {
+    size_t N = (size_t)nx * ny;
+    double *d = (double *)malloc(sizeof(double) * 2 * N);
+    if (!d) return;
+    damping_field(nx, ny, F->FR0, f, d, d + N);
+    for (size_t c = 0; c < N; ++c) {
+      Fx[c] += d[c];
+      Fy[c] += d[N + c];
+    }
+    free(d);
   }
 }
 
@@ -122,18 +227,24 @@ void orc_collide_cell(const double *fin, double tau, double Fex, double Fey,
   }
 }
 
-/* Collision of the whole grid (no streaming): fout = fin + Omega(fin) + F. */
-void orc_collide(int nx, int ny, double tau, int force_kind, double F0, int kf,
-                 double alpha, const double *fin, double *fout) {
+/* Collision of the whole grid (no streaming): fout = fin + Omega(fin) + F,
+ * with the external force of the state fin (orc_force_field). */
+int orc_collide(int nx, int ny, double tau, const orc_force_t *F,
+                const double *fin, double *fout) {
   size_t plane = (size_t)nx * ny;
+  double *Fe = (double *)malloc(sizeof(double) * 2 * plane);
+  if (!Fe) return -1;
+  orc_force_field(nx, ny, F, fin, Fe, Fe + plane);
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
-      double a[Q], b[Q], Fex, Fey;
-      for (int l = 0; l < Q; ++l) a[l] = fin[l * plane + (size_t)y * nx + x];
-      orc_force_ext(nx, ny, force_kind, F0, kf, x, y, &Fex, &Fey);
-      orc_collide_cell(a, tau, Fex, Fey, alpha, b);
-      for (int l = 0; l < Q; ++l) fout[l * plane + (size_t)y * nx + x] = b[l];
+      size_t c = (size_t)y * nx + x;
+      double a[Q], b[Q];
+      for (int l = 0; l < Q; ++l) a[l] = fin[l * plane + c];
+      orc_collide_cell(a, tau, Fe[c], Fe[plane + c], F->alpha, b);
+      for (int l = 0; l < Q; ++l) fout[l * plane + c] = b[l];
     }
+  free(Fe);
+  return 0;
 }
 
 /* Streaming, the left-hand side of eq. (1): f_l(x + c_l, n + 1) = f*_l(x),
@@ -151,21 +262,22 @@ void orc_stream(int nx, int ny, const double *fin, double *fout) {
 
 /* One full time step of eq. (1): collide, then stream.  scratch holds one
  * population array (9 nx ny doubles).  f is updated in place. */
-void orc_step(int nx, int ny, double tau, int force_kind, double F0, int kf,
-              double alpha, double *f, double *scratch) {
-  orc_collide(nx, ny, tau, force_kind, F0, kf, alpha, f, scratch);
+int orc_step(int nx, int ny, double tau, const orc_force_t *F, double *f,
+             double *scratch) {
+  if (orc_collide(nx, ny, tau, F, f, scratch)) return -1;
   orc_stream(nx, ny, scratch, f);
+  return 0;
 }
 
 /* nsteps time steps; allocates its own scratch. */
-int orc_run(int nx, int ny, double tau, int force_kind, double F0, int kf,
-            double alpha, double *f, int nsteps) {
+int orc_run(int nx, int ny, double tau, const orc_force_t *F, double *f,
+            int nsteps) {
   double *s = (double *)malloc(sizeof(double) * Q * (size_t)nx * ny);
   if (!s) return -1;
-  for (int n = 0; n < nsteps; ++n)
-    orc_step(nx, ny, tau, force_kind, F0, kf, alpha, f, s);
+  int rc = 0;
+  for (int n = 0; n < nsteps && rc == 0; ++n) rc = orc_step(nx, ny, tau, F, f, s);
   free(s);
-  return 0;
+  return rc;
 }
 
 /* nsteps time steps on a wx x wy window cut out of a larger NX x NY periodic
@@ -174,10 +286,11 @@ int orc_run(int nx, int ny, double tau, int force_kind, double F0, int kf,
  * ((X0 + i) mod NX, (Y0 + j) mod NY) and the window treated as periodic.  A
  * step moves information by at most one cell, so after nsteps steps the
  * window cells at least nsteps cells away from its edges hold exactly the
- * values of the global run; the others are meaningless. */
-int orc_run_window(int wx, int wy, double tau, int force_kind, double F0, int kf,
-                   double alpha, double *f, int nsteps, int X0, int Y0, int NX,
-                   int NY) {
+ * values of the global run; the others are meaningless.  The damping of
+ * kind 2 depends on the whole grid, so kind 2 is refused (-2). */
+int orc_run_window(int wx, int wy, double tau, const orc_force_t *F, double *f,
+                   int nsteps, int X0, int Y0, int NX, int NY) {
+  if (F->kind == 2) return -2;
   size_t plane = (size_t)wx * wy;
   double *s = (double *)malloc(sizeof(double) * Q * plane);
   if (!s) return -1;
@@ -186,9 +299,8 @@ int orc_run_window(int wx, int wy, double tau, int force_kind, double F0, int kf
       for (int x = 0; x < wx; ++x) {
         double a[Q], b[Q], Fex, Fey;
         for (int l = 0; l < Q; ++l) a[l] = f[l * plane + (size_t)y * wx + x];
-        orc_force_ext(NX, NY, force_kind, F0, kf, wrap(X0 + x, NX), wrap(Y0 + y, NY), &Fex,
-                      &Fey);
-        orc_collide_cell(a, tau, Fex, Fey, alpha, b);
+        orc_force_ext(NX, NY, F, wrap(X0 + x, NX), wrap(Y0 + y, NY), &Fex, &Fey);
+        orc_collide_cell(a, tau, Fex, Fey, F->alpha, b);
         for (int l = 0; l < Q; ++l) s[l * plane + (size_t)y * wx + x] = b[l];
       }
     orc_stream(wx, wy, s, f);
@@ -210,24 +322,27 @@ void orc_init(int nx, int ny, const double *rho, const double *ux,
 
 /* Moments of the state f(., n): rho, bare momentum j, and the EDM velocity
  * u_phys = (j + F/2)/rho with F = F_ext - alpha j.  Any output may be NULL. */
-void orc_moments(int nx, int ny, int force_kind, double F0, int kf,
-                 double alpha, const double *f, double *rho, double *jx,
-                 double *jy, double *ux, double *uy) {
+int orc_moments(int nx, int ny, const orc_force_t *F, const double *f,
+                double *rho, double *jx, double *jy, double *ux, double *uy) {
   size_t plane = (size_t)nx * ny;
+  double *Fe = (double *)malloc(sizeof(double) * 2 * plane);
+  if (!Fe) return -1;
+  orc_force_field(nx, ny, F, f, Fe, Fe + plane);
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       size_t c = (size_t)y * nx + x;
-      double a[Q], r, px, py, Fex, Fey;
+      double a[Q], r, px, py;
       for (int l = 0; l < Q; ++l) a[l] = f[l * plane + c];
       cell_moments(a, &r, &px, &py);
-      orc_force_ext(nx, ny, force_kind, F0, kf, x, y, &Fex, &Fey);
-      double Fx = Fex - alpha * px, Fy = Fey - alpha * py;
+      double Fx = Fe[c] - F->alpha * px, Fy = Fe[plane + c] - F->alpha * py;
       if (rho) rho[c] = r;
       if (jx) jx[c] = px;
       if (jy) jy[c] = py;
       if (ux) ux[c] = (px + 0.5 * Fx) / r;
       if (uy) uy[c] = (py + 0.5 * Fy) / r;
     }
+  free(Fe);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -602,8 +717,7 @@ int orc_distributions(int nx, int ny, const double *terms, const double *ux,
 
 /* Term fields at time n from the pre-collision populations at n, n-1, n-2
  * (f_n, f_n1, f_n2), using u_phys and F = F_ext - alpha j at each level. */
-int orc_terms_from_populations(int nx, int ny, double tau, int force_kind,
-                               double F0, int kf, double alpha,
+int orc_terms_from_populations(int nx, int ny, double tau, const orc_force_t *F,
                                const double *f_n, const double *f_n1,
                                const double *f_n2, double *terms) {
   size_t N = (size_t)nx * ny;
@@ -616,17 +730,16 @@ int orc_terms_from_populations(int nx, int ny, double tau, int force_kind,
     rho[m] = buf + (3 * m + 0) * N;
     ux[m] = buf + (3 * m + 1) * N;
     uy[m] = buf + (3 * m + 2) * N;
-    orc_moments(nx, ny, force_kind, F0, kf, alpha, fs[m], rho[m], jx, jy,
-                ux[m], uy[m]);
+    if (orc_moments(nx, ny, F, fs[m], rho[m], jx, jy, ux[m], uy[m])) {
+      free(buf);
+      return -1;
+    }
     if (m == 0) {
-      for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x) {
-          size_t c = (size_t)y * nx + x;
-          double Fex, Fey;
-          orc_force_ext(nx, ny, force_kind, F0, kf, x, y, &Fex, &Fey);
-          Fx[c] = Fex - alpha * jx[c];
-          Fy[c] = Fey - alpha * jy[c];
-        }
+      orc_force_field(nx, ny, F, fs[0], Fx, Fy);
+      for (size_t c = 0; c < N; ++c) {
+        Fx[c] -= F->alpha * jx[c];
+        Fy[c] -= F->alpha * jy[c];
+      }
     }
   }
   int rc = orc_terms(nx, ny, tau, (const double *const *)rho,
@@ -641,15 +754,21 @@ int orc_terms_from_populations(int nx, int ny, double tau, int force_kind,
  *   out[3] = <E> = mean rho |u|^2 / 2,  out[4] = <Omega> = mean w^2 / 2,
  *   out[5] = <u . F>,  out[6] = <eps> = mean nu rho S_ij d_j u_i
  * with u = u_phys and the eq. (18) derivatives. */
-int orc_global(int nx, int ny, double tau, int force_kind, double F0, int kf,
-               double alpha, const double *f, double *out) {
+int orc_global(int nx, int ny, double tau, const orc_force_t *F,
+               const double *f, double *out) {
   size_t N = (size_t)nx * ny;
   double *b = (double *)malloc(sizeof(double) * N * 11);
   if (!b) return -1;
   double *rho = b, *jx = b + N, *jy = b + 2 * N, *u = b + 3 * N,
          *v = b + 4 * N, *dxu = b + 5 * N, *dyu = b + 6 * N, *dxv = b + 7 * N,
          *dyv = b + 8 * N;
-  orc_moments(nx, ny, force_kind, F0, kf, alpha, f, rho, jx, jy, u, v);
+  double *Fe = (double *)malloc(sizeof(double) * N * 2);
+  if (!Fe || orc_moments(nx, ny, F, f, rho, jx, jy, u, v)) {
+    free(b);
+    free(Fe);
+    return -1;
+  }
+  orc_force_field(nx, ny, F, f, Fe, Fe + N);
   orc_ddx(nx, ny, u, dxu);
   orc_ddy(nx, ny, u, dyu);
   orc_ddx(nx, ny, v, dxv);
@@ -659,9 +778,7 @@ int orc_global(int nx, int ny, double tau, int force_kind, double F0, int kf,
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       size_t c = (size_t)y * nx + x;
-      double Fex, Fey;
-      orc_force_ext(nx, ny, force_kind, F0, kf, x, y, &Fex, &Fey);
-      double Fx = Fex - alpha * jx[c], Fy = Fey - alpha * jy[c];
+      double Fx = Fe[c] - F->alpha * jx[c], Fy = Fe[N + c] - F->alpha * jy[c];
       double w = dxv[c] - dyu[c];
       double sxx = 2 * dxu[c], sxy = dyu[c] + dxv[c], syy = 2 * dyv[c];
       s[0] += rho[c];
@@ -678,6 +795,7 @@ int orc_global(int nx, int ny, double tau, int force_kind, double F0, int kf,
   out[2] = s[2];
   for (int k = 3; k < 7; ++k) out[k] = s[k] / (double)N;
   free(b);
+  free(Fe);
   return 0;
 }
 
@@ -685,9 +803,9 @@ int orc_global(int nx, int ny, double tau, int force_kind, double F0, int kf,
  * n in [n0, n1] of the L x L box average (origin (bx, by)) of RHS^{E,4}(n),
  * the local dissipation term of eq. (8), evaluated on the state f(., n).
  * Runs the forward model from f0 (copied, not modified) for n1 steps. */
-int orc_objective(int nx, int ny, double tau, int force_kind, double F0,
-                  int kf, double alpha, const double *f0, int n0, int n1,
-                  int bx, int by, int L, double *J) {
+int orc_objective(int nx, int ny, double tau, const orc_force_t *F,
+                  const double *f0, int n0, int n1, int bx, int by, int L,
+                  double *J) {
   size_t N = (size_t)nx * ny;
   double *f = (double *)malloc(sizeof(double) * Q * N);
   double *s = (double *)malloc(sizeof(double) * Q * N);
@@ -705,7 +823,7 @@ int orc_objective(int nx, int ny, double tau, int force_kind, double F0,
   double nu = CS2 * (tau - 0.5), acc = 0.0;
   for (int n = 0; n <= n1; ++n) {
     if (n >= n0) {
-      orc_moments(nx, ny, force_kind, F0, kf, alpha, f, rho, jx, jy, u, v);
+      orc_moments(nx, ny, F, f, rho, jx, jy, u, v);
       orc_ddx(nx, ny, u, dxu);
       orc_ddy(nx, ny, u, dyu);
       orc_ddx(nx, ny, v, dxv);
@@ -717,7 +835,7 @@ int orc_objective(int nx, int ny, double tau, int force_kind, double F0,
       }
       acc += orc_box_mean(nx, ny, eps, bx, by, L);
     }
-    if (n < n1) orc_step(nx, ny, tau, force_kind, F0, kf, alpha, f, s);
+    if (n < n1) orc_step(nx, ny, tau, F, f, s);
   }
   *J = acc / (double)(n1 - n0 + 1);
   free(f);

@@ -566,3 +566,80 @@ def test_distributions_count_every_box_once(orc):
             np.testing.assert_array_equal(hm[iL], want)
             assert abs(ms[iL, 0] - np.mean(mach)) < 1e-14
             assert abs(ms[iL, 1] - np.std(mach)) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# The paper's turbulence forcing: shell force (eqs. 14, 15), damping (eq. 16)
+# --------------------------------------------------------------------------
+
+def _half_shell(kmin2, kmax2):
+    return [(kx, ky) for ky in range(0, 8) for kx in range(-7, 8)
+            if kmin2 <= kx * kx + ky * ky <= kmax2 and (ky > 0 or kx > 0)]
+
+
+def test_shell_force_is_spectral_curl_of_streamfunction(orc):
+    """F^T = (d_y psi, -d_x psi) of the eq. (14) streamfunction: the oracle's
+    analytic field equals the FFT derivative of psi sampled on the grid
+    (non-square grid, non-zero phase), is divergence-free, and has Fourier
+    support only on the shell 5 <= |k| <= 7."""
+    nx, ny, F0, phi = 48, 40, 8e-4, 0.7
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    psi = np.zeros((ny, nx))
+    for kx, ky in _half_shell(25, 49):
+        psi += F0 * np.cos(2 * np.pi * (kx * X / nx + ky * Y / ny) + phi)
+    KX = 2 * np.pi * np.fft.fftfreq(nx, 1.0 / nx)[None, :] / nx
+    KY = 2 * np.pi * np.fft.fftfreq(ny, 1.0 / ny)[:, None] / ny
+    ph = np.fft.fft2(psi)
+    fx_want = np.real(np.fft.ifft2(1j * KY * ph))
+    fy_want = np.real(np.fft.ifft2(-1j * KX * ph))
+    f = orc.init(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    Fx, Fy = orc.force_field(f, orc.Force(2, F0, 0, 0.0, phase=phi, FR0=0.0))
+    scale = np.max(np.abs(fx_want))
+    assert np.max(np.abs(Fx - fx_want)) < 1e-13 * scale
+    assert np.max(np.abs(Fy - fy_want)) < 1e-13 * scale
+    div = np.real(np.fft.ifft2(1j * KX * np.fft.fft2(Fx) + 1j * KY * np.fft.fft2(Fy)))
+    assert np.max(np.abs(div)) < 1e-13 * scale
+    kk = np.hypot(np.fft.fftfreq(nx, 1.0 / nx)[None, :], np.fft.fftfreq(ny, 1.0 / ny)[:, None])
+    spec = np.abs(np.fft.fft2(Fx)) + np.abs(np.fft.fft2(Fy))
+    assert np.max(spec[(kk < 5 - 1e-9) | (kk > 7 + 1e-9)]) < 1e-12 * np.max(spec)
+    assert abs(Fx.mean()) < 1e-17 and abs(Fy.mean()) < 1e-17
+
+
+def test_damping_removes_exactly_the_large_scale_modes(orc):
+    """Eq. (16) on f = f_eq(1, u) (so j / rho = u exactly): the damping is
+    -F^R_0 times the part of u on the modes 1 <= |k| <= 2 -- here the
+    prescribed (1,0), (1,1), (0,2) components -- and ignores (2,1), (3,0)
+    and the mean flow."""
+    nx, ny, FR0 = 32, 24, 1e-5
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    ax, ay = 2 * np.pi * X / nx, 2 * np.pi * Y / ny
+    inside_x = 0.01 * np.cos(ax) + 0.004 * np.sin(ax + ay)
+    inside_y = -0.006 * np.cos(2 * ay + 0.3)
+    outside_x = 0.003 * np.sin(2 * ax + ay) + 0.002 + 0.005 * np.cos(3 * ax)
+    outside_y = 0.004 * np.cos(2 * ax + ay) - 0.001
+    f = orc.init(np.ones((ny, nx)), inside_x + outside_x, inside_y + outside_y)
+    Fx, Fy = orc.force_field(f, orc.Force(2, 0.0, 0, 0.0, phase=0.0, FR0=FR0))
+    assert np.max(np.abs(Fx + FR0 * inside_x)) < 1e-18
+    assert np.max(np.abs(Fy + FR0 * inside_y)) < 1e-18
+
+
+def test_paper_forcing_step_conserves_mass_and_adds_the_total_force(orc):
+    """One step with the paper's forcing and drag: mass is conserved and the
+    momentum gained equals sum_x (F^T + F^R - alpha j) (EDM adds exactly F
+    per cell); both forcing fields have zero mean, so the gain is the drag."""
+    n = 24
+    rho = 1.0 + li.smooth_fields(n, n, 3, amp=0.01)
+    ux, uy = li.smooth_fields(n, n, 4, amp=0.03), li.smooth_fields(n, n, 5, amp=0.03)
+    f = orc.init(rho, ux, uy)
+    force = orc.Force(2, 8e-4, 0, 2e-3, phase=0.4, FR0=1e-3)
+    g = orc.run(f, 1, 0.6, force)
+    cx, cy, _ = orc.lattice()
+    jx0 = np.einsum("l,lyx->yx", cx, f)
+    jy0 = np.einsum("l,lyx->yx", cy, f)
+    Fx, Fy = orc.force_field(f, force)
+    assert abs(g.sum() - f.sum()) < 1e-12
+    gain_x = np.einsum("l,lyx->", cx, g) - jx0.sum()
+    gain_y = np.einsum("l,lyx->", cy, g) - jy0.sum()
+    assert abs(gain_x - (Fx - 2e-3 * jx0).sum()) < 1e-13
+    assert abs(gain_y - (Fy - 2e-3 * jy0).sum()) < 1e-13
+    assert abs(gain_x + 2e-3 * jx0.sum()) < 1e-13
