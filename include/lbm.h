@@ -71,10 +71,22 @@ typedef struct lbm_member_cfg {
   double tau;       /* BGK relaxation time of eq. (1); nu = (tau - 1/2)/3,
                        eq. (5).  Must be > 0.5 */
   double rho0;      /* reference density of the FP32 deviation storage */
-  int force_kind;   /* 0: no external force; 1: Kolmogorov force */
+  int force_kind;   /* 0: no external force; 1: Kolmogorov force
+                       F0 (sin(2 pi kf y/ny), sin(2 pi kf x/nx));
+                       2: the paper's turbulence forcing (Sec. 3): the
+                       shell force of eqs. (14), (15) -- streamfunction
+                       F0 sum_k cos(2 pi (kx x/nx + ky y/ny) + phase) over
+                       one of each pair +-k with 5 <= |k| <= 7, force
+                       (d_y psi, -d_x psi) -- plus the large-scale damping
+                       of eq. (16): -FR0 times the projection of the bare
+                       velocity j/rho of the state being collided on the
+                       modes 1 <= |k| <= 2 (one extra read of the
+                       populations per step; no adjoint) */
   int kf;           /* Kolmogorov wavenumber, in units of 2 pi / n */
-  double F0;        /* Kolmogorov amplitude */
+  double F0;        /* Kolmogorov amplitude, or F^T_0 of eq. (14) */
   double alpha;     /* linear drag coefficient on the bare momentum */
+  double phase;     /* phi of eq. (14) (force_kind 2) */
+  double FR0;       /* F^R_0 of eq. (16) (force_kind 2) */
 } lbm_member_cfg;
 
 typedef struct lbm_config {

@@ -41,7 +41,8 @@ class LBMError(RuntimeError):
 class _MemberCfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("force_kind", ctypes.c_int), ("kf", ctypes.c_int),
-                ("F0", ctypes.c_double), ("alpha", ctypes.c_double)]
+                ("F0", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("phase", ctypes.c_double), ("FR0", ctypes.c_double)]
 
 
 class _Config(ctypes.Structure):
@@ -100,8 +101,10 @@ def load_library(path: str = LIB_PATH):
 class Member:
     """One ensemble member: an nx x ny doubly periodic grid with relaxation
     time tau (eq. (1), nu = (tau - 1/2)/3 by eq. (5)), reference density rho0,
-    optional Kolmogorov force F0 (sin(2 pi kf y/ny), sin(2 pi kf x/nx)) and
-    linear drag alpha on the bare momentum."""
+    an optional force -- kind 1: Kolmogorov F0 (sin(2 pi kf y/ny),
+    sin(2 pi kf x/nx)); kind 2: the paper's shell force of eqs. (14), (15)
+    (amplitude F0, phase) with the large-scale damping of eq. (16) (FR0) --
+    and linear drag alpha on the bare momentum."""
     nx: int
     ny: int
     tau: float
@@ -110,10 +113,12 @@ class Member:
     kf: int = 0
     F0: float = 0.0
     alpha: float = 0.0
+    phase: float = 0.0
+    FR0: float = 0.0
 
     def c(self) -> _MemberCfg:
         return _MemberCfg(self.nx, self.ny, self.tau, self.rho0, self.force_kind, self.kf,
-                          self.F0, self.alpha)
+                          self.F0, self.alpha, self.phase, self.FR0)
 
 
 def _ptr(t) -> Optional[int]:

@@ -33,6 +33,7 @@ thread_local std::string g_last_error = "no error";
 struct Layout {
   size_t members, tiles, status;
   std::vector<size_t> pop0, pop1, fx, fy, fx64, fy64, snap;
+  std::vector<size_t> ft, ft64, trig, trig64, damp, damp_f, damp_ring, proj;  // force kind 2
   size_t scratch, partials, jpart, jobs, stats, Ls, out7, origins;
   size_t edges, hist, mach;  // distributions: bin edges, histograms, Ma_V statistics
   int diag_slots;          // members per batched diagnostic launch
@@ -47,6 +48,67 @@ int pitch_of(int nx, int precision) {
   // rows start on 16-byte boundaries: 4 floats or 2 doubles
   const int q = precision == 32 ? 4 : 2;
   return (nx + q - 1) / q * q;
+}
+
+// Tables of force kind 2.  ft: the shell force of eqs. (14), (15) in FP64,
+// [2][ny * nx]: psi = F0 sum_k cos(2 pi (kx x/nx + ky y/ny) + phase) over one
+// of each pair +-k with 5 <= |k| <= 7 (ky > 0, or ky = 0 and kx > 0), force
+// (d_y psi, -d_x psi) = F0 sum_k sin(theta_k) (-2 pi ky/ny, 2 pi kx/nx),
+// with sin(theta) = sin(a_x + phase) cos(b_y) + cos(a_x + phase) sin(b_y)
+// from per-axis tables.  ftp: the same with rows of `pitch` (zero padded).
+// trig: cos, sin of 2 pi x/nx and of 4 pi x/nx ([4][nx]), then of y ([4][ny]).
+void shell_force_tables(const lbm_member_cfg &c, int pitch, std::vector<double> *ft,
+                        std::vector<double> *ftp, std::vector<double> *trig) {
+  const double pi = 3.14159265358979323846;
+  const int nx = c.nx, ny = c.ny;
+  const size_t N = (size_t)nx * ny;
+  ft->assign(2 * N, 0.0);
+  std::vector<double> sa(nx), ca(nx), sb(ny), cb(ny);
+  for (int ky = 0; ky <= 7; ++ky)
+    for (int kx = -7; kx <= 7; ++kx) {
+      const int k2 = kx * kx + ky * ky;
+      if (k2 < 25 || k2 > 49 || (ky == 0 && kx <= 0)) continue;
+      for (int x = 0; x < nx; ++x) {
+        const double a = 2.0 * pi * kx * (double)x / nx + c.phase;
+        sa[x] = std::sin(a);
+        ca[x] = std::cos(a);
+      }
+      for (int y = 0; y < ny; ++y) {
+        const double b = 2.0 * pi * ky * (double)y / ny;
+        sb[y] = std::sin(b);
+        cb[y] = std::cos(b);
+      }
+      const double gx = -2.0 * pi * ky / ny, gy = 2.0 * pi * kx / nx;
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          const double st = sa[x] * cb[y] + ca[x] * sb[y];
+          (*ft)[(size_t)y * nx + x] += gx * st;
+          (*ft)[N + (size_t)y * nx + x] += gy * st;
+        }
+    }
+  for (double &v : *ft) v *= c.F0;
+  const size_t plane = (size_t)ny * pitch;
+  ftp->assign(2 * plane, 0.0);
+  for (int k = 0; k < 2; ++k)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x)
+        (*ftp)[k * plane + (size_t)y * pitch + x] = (*ft)[k * N + (size_t)y * nx + x];
+  trig->assign(4 * ((size_t)nx + ny), 0.0);
+  for (int x = 0; x < nx; ++x) {
+    const double a = 2.0 * pi * x / nx;
+    (*trig)[x] = std::cos(a);
+    (*trig)[nx + x] = std::sin(a);
+    (*trig)[2 * nx + x] = std::cos(2.0 * a);
+    (*trig)[3 * nx + x] = std::sin(2.0 * a);
+  }
+  double *ty = trig->data() + 4 * (size_t)nx;
+  for (int y = 0; y < ny; ++y) {
+    const double b = 2.0 * pi * y / ny;
+    ty[y] = std::cos(b);
+    ty[ny + y] = std::sin(b);
+    ty[2 * ny + y] = std::cos(2.0 * b);
+    ty[3 * ny + y] = std::sin(2.0 * b);
+  }
 }
 
 bool vector_eligible(const lbm_member_cfg &m, int precision) {
@@ -74,11 +136,12 @@ int check_config(const lbm_config *cfg, std::string &err) {
     if (!(c.rho0 > 0) || !std::isfinite(c.rho0)) {
       snprintf(buf, sizeof buf, "member %d: rho0 must be > 0", m); err = buf; return LBM_ERR_ARG;
     }
-    if (c.force_kind != 0 && c.force_kind != 1) {
-      snprintf(buf, sizeof buf, "member %d: force_kind must be 0 or 1", m); err = buf; return LBM_ERR_ARG;
+    if (c.force_kind < 0 || c.force_kind > 2) {
+      snprintf(buf, sizeof buf, "member %d: force_kind must be 0, 1 or 2", m); err = buf; return LBM_ERR_ARG;
     }
-    if (!std::isfinite(c.F0) || !std::isfinite(c.alpha)) {
-      snprintf(buf, sizeof buf, "member %d: F0/alpha not finite", m); err = buf; return LBM_ERR_ARG;
+    if (!std::isfinite(c.F0) || !std::isfinite(c.alpha) ||
+        (c.force_kind == 2 && (!std::isfinite(c.phase) || !std::isfinite(c.FR0)))) {
+      snprintf(buf, sizeof buf, "member %d: force parameters not finite", m); err = buf; return LBM_ERR_ARG;
     }
   }
   return LBM_OK;
@@ -112,6 +175,17 @@ Layout make_layout(const lbm_config *cfg) {
     L.fx64.push_back(take(8 * c.ny));
     L.fy64.push_back(take(8 * c.nx));
     L.snap.push_back(take(8 * 9 * N));
+    const bool k2 = c.force_kind == 2;  // shell force tables, damping state
+    const size_t nt = 4 * ((size_t)c.nx + c.ny);
+    const size_t pctas = (size_t)((c.nx + 63) / 64) * ((c.ny + 3) / 4);
+    L.ft.push_back(take(k2 ? es * 2 * plane : 0));
+    L.ft64.push_back(take(k2 ? 8 * 2 * N : 0));
+    L.trig.push_back(take(k2 ? es * nt : 0));
+    L.trig64.push_back(take(k2 ? 8 * nt : 0));
+    L.damp.push_back(take(k2 ? 8 * lbm::kDamp : 0));
+    L.damp_f.push_back(take(k2 ? 4 * lbm::kDamp : 0));
+    L.damp_ring.push_back(take(k2 ? 8 * 3 * lbm::kDamp : 0));
+    L.proj.push_back(take(k2 ? 8 * lbm::kDamp * pctas : 0));
     L.Nmax = std::max(L.Nmax, N);
   }
   L.scratch_fields = lbm::kDiagFields;
@@ -161,11 +235,12 @@ struct lbm_handle {
   cudaStream_t diag_stream = nullptr;  // asynchronous diagnostics
   cudaEvent_t ev_ready = nullptr, ev_diag_done = nullptr;
   bool diag_pending = false;
+  bool has_kind2 = false;  // some member uses the paper's forcing (kind 2)
   int cur = 0;
   long long t = 0;
   long long ring_time[3] = {-1, -1, -1};
   lbm::DiagScratch sc{};
-  lbm::LaunchCfg lc{8, 1, 0};
+  lbm::LaunchCfg lc{8, 1, 0, 0};
   int graph_k = 0;
   cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // by storage state
   float tuned_ms = 0.f;  // autotuned time of one step, ms (0: not tuned)
@@ -211,8 +286,31 @@ int build_tiles(lbm_handle *h) {
   return LBM_OK;
 }
 
-// One time step of every member on stream s.
+// Largest grid of the handle (batched per-member launches).
+void max_grid(const lbm_handle *h, int *nx, int *ny) {
+  *nx = 1;
+  *ny = 1;
+  for (const lbm_member_cfg &c : h->mcfg) {
+    *nx = std::max(*nx, c.nx);
+    *ny = std::max(*ny, c.ny);
+  }
+}
+
+// Damping coefficients of eq. (16) of every kind-2 member for the state in
+// storage `cur`: slot < 0 for the step about to run, else a ring slot.
+int project(lbm_handle *h, cudaStream_t s, int cur, int slot) {
+  int nx, ny;
+  max_grid(h, &nx, &ny);
+  CK(lbm::launch_projection(h->precision, h->d_members, (int)h->mcfg.size(), nx, ny, cur, slot,
+                            s));
+  return LBM_OK;
+}
+
+// One time step of every member on stream s (kind-2 members first get the
+// damping of the state being collided).
 int launch_one_step(lbm_handle *h, cudaStream_t s, int cur) {
+  if (h->has_kind2)
+    if (int rc = project(h, s, cur, -1)) return rc;
   if (h->ntiles > 0) CK(lbm::launch_step_f32_vec(h->d_members, h->d_tiles, h->ntiles, cur, h->lc, s));
   for (int m : h->scalar_members)
     CK(lbm::launch_step_scalar(h->precision, h->d_members, m, h->mcfg[m].nx, h->mcfg[m].ny, cur, s));
@@ -220,7 +318,7 @@ int launch_one_step(lbm_handle *h, cudaStream_t s, int cur) {
 }
 
 long long kernels_per_step(const lbm_handle *h) {
-  return (h->ntiles > 0 ? 1 : 0) + (long long)h->scalar_members.size();
+  return (h->ntiles > 0 ? 1 : 0) + (long long)h->scalar_members.size() + (h->has_kind2 ? 2 : 0);
 }
 
 void drop_graphs(lbm_handle *h) {
@@ -299,8 +397,12 @@ int record(lbm_handle *h) {
   }
   CK(lbm::launch_snapshot_ring(h->precision, h->d_members, (int)h->mcfg.size(), nx, ny, h->cur,
                                slot, h->stream));
-  h->ring_time[slot] = h->t;
   h->launches += 1;
+  if (h->has_kind2) {  // the damping of this state, for the diagnostic
+    if (int rc = project(h, h->stream, h->cur, slot)) return rc;
+    h->launches += 2;
+  }
+  h->ring_time[slot] = h->t;
   return LBM_OK;
 }
 
@@ -334,7 +436,8 @@ int autotune(lbm_handle *h) {
   for (int st : states)
     for (int wy : {4, 8})
       for (int rows : {1, 2, 4})
-        for (int per : {0, 4, 8}) cands.push_back({{wy, rows, per * nsm}, st, 0.f});
+        for (int per : {0, 4, 8})
+          cands.push_back({{wy, rows, per * nsm, h->lc.paper_force}, st, 0.f});
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -453,6 +556,18 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
     M.fy_tab64 = reinterpret_cast<double *>(ws_at(h, lay.fy64[m]));
     M.snap = reinterpret_cast<double *>(ws_at(h, lay.snap[m]));
     M.status = reinterpret_cast<int *>(ws_at(h, lay.status)) + m;
+    if (c.force_kind == 2) {
+      M.FR0 = c.FR0;
+      M.ft_tab = ws_at(h, lay.ft[m]);
+      M.ft_tab64 = reinterpret_cast<double *>(ws_at(h, lay.ft64[m]));
+      M.trig = ws_at(h, lay.trig[m]);
+      M.trig64 = reinterpret_cast<double *>(ws_at(h, lay.trig64[m]));
+      M.damp = reinterpret_cast<double *>(ws_at(h, lay.damp[m]));
+      M.damp_f = reinterpret_cast<float *>(ws_at(h, lay.damp_f[m]));
+      M.damp_ring = reinterpret_cast<double *>(ws_at(h, lay.damp_ring[m]));
+      M.proj_part = reinterpret_cast<double *>(ws_at(h, lay.proj[m]));
+      h->has_kind2 = true;
+    }
     h->hm.push_back(M);
     // Kolmogorov tables: F_ext,x(y) = F0 sin(2 pi kf y / ny), F_ext,y(x) likewise.
     std::vector<double> fx(c.ny, 0.0), fy(c.nx, 0.0);
@@ -475,6 +590,20 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
     if (e == cudaSuccess) e = cudaMemcpyAsync(M.fy_tab64, fy.data(), 8 * fy.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(M.pop[0], 0, es * 9 * M.plane, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(M.pop[1], 0, es * 9 * M.plane, s);
+    if (e == cudaSuccess && c.force_kind == 2) {
+      std::vector<double> ft, ftp, trig;
+      shell_force_tables(c, M.pitch, &ft, &ftp, &trig);
+      e = put(M.ft_tab, ftp);
+      if (e == cudaSuccess) e = put(M.trig, trig);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(M.ft_tab64, ft.data(), 8 * ft.size(), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(M.trig64, trig.data(), 8 * trig.size(), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(M.damp, 0, 8 * lbm::kDamp, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(M.damp_f, 0, 4 * lbm::kDamp, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(M.damp_ring, 0, 8 * 3 * lbm::kDamp, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables are temporaries
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // fx/fy are temporaries
     if (e != cudaSuccess)
       return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
@@ -486,6 +615,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
   if (e != cudaSuccess)
     return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
   h->cur = cfg->storage == 1 ? 2 : 0;
+  h->lc.paper_force = h->has_kind2 ? 1 : 0;
   rc = build_tiles(h);
   if (rc == LBM_OK) rc = autotune(h);
   if (rc != LBM_OK) {
@@ -598,6 +728,10 @@ int lbm_moments(lbm_handle *h, int member, double *rho, double *ux, double *uy,
   if ((rc = wait_diag(h))) return rc;
   const lbm_member_cfg &c = h->mcfg[member];
   double *snap = h->sc.f;  // scratch fields 0..2
+  if (c.force_kind == 2) {  // damping of the current state into Member::damp
+    if ((rc = project(h, h->stream, h->cur, -1))) return rc;
+    h->launches += 2;
+  }
   CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, snap, h->stream));
   CK(lbm::diag_moments(h->hm[member], snap, rho, ux, uy, omega, h->sc, h->stream));
   h->launches += omega ? 3 : 2;
@@ -612,6 +746,10 @@ int lbm_global_balance(lbm_handle *h, int member, double *out) {
   const lbm_member_cfg &c = h->mcfg[member];
   double *snap = h->sc.f;
   double *out_dev = reinterpret_cast<double *>(ws_at(h, h->lay.out7));
+  if (c.force_kind == 2) {  // damping of the current state into Member::damp
+    if ((rc = project(h, h->stream, h->cur, -1))) return rc;
+    h->launches += 2;
+  }
   CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, snap, h->stream));
   CK(lbm::diag_global(h->hm[member], snap, h->sc, out_dev, h->stream));
   h->launches += 4;
@@ -781,6 +919,13 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
     J.nL = (int)where[i].size();
     J.max_boxes = maxb[i];
     J.qblocks = lbm::diag_query_blocks(maxb[i], origins != nullptr);
+    J.force_kind = hm.force_kind;
+    if (hm.force_kind == 2) {  // damping coefficients recorded with each snapshot
+      J.ft64 = hm.ft_tab64;
+      J.trig64 = hm.trig64;
+      for (int k = 0; k < 3; ++k)
+        J.dc[k] = hm.damp_ring + (size_t)((t - k) % 3) * lbm::kDamp;
+    }
     jobs.push_back(J);
   }
   if (!jobs.empty()) {
@@ -934,6 +1079,9 @@ int lbm_adjoint_step(lbm_handle *h, int member, const double *f_n, const double 
   int rc = check_member(h, member);
   if (rc) return rc;
   const lbm_member_cfg &c = h->mcfg[member];
+  if (c.force_kind == 2)
+    return fail(h, LBM_ERR_ARG, "the adjoint supports force kinds 0 and 1 (the damping of "
+                                "kind 2 couples every cell)");
   if (!f_n || !lambda_out) return fail(h, LBM_ERR_ARG, "f_n and lambda_out must not be NULL");
   if (lambda_in == lambda_out) return fail(h, LBM_ERR_ARG, "lambda_out may not alias lambda_in");
   if (!std::isfinite(obj_weight)) return fail(h, LBM_ERR_ARG, "obj_weight not finite");
@@ -952,6 +1100,8 @@ int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx, i
   int rc = check_member(h, member);
   if (rc) return rc;
   const lbm_member_cfg &c = h->mcfg[member];
+  if (c.force_kind == 2)
+    return fail(h, LBM_ERR_ARG, "the objective supports force kinds 0 and 1");
   if (!acc) return fail(h, LBM_ERR_ARG, "acc is NULL");
   if (L < 1 || L > c.nx || L > c.ny || bx < 0 || bx >= c.nx || by < 0 || by >= c.ny)
     return fail(h, LBM_ERR_ARG, "objective box outside the grid");

@@ -58,7 +58,24 @@ struct Grid {
   int nx, ny;
   double nu, alpha, rho_ref;
   const double *fxt, *fyt;  // F_ext,x(y), F_ext,y(x)
+  // force kind 2: shell force [2][N], trig tables, damping coefficients
+  const double *ft64, *trig64, *damp;
 };
+
+// External force (drag excluded) at cell (x, y): the separable tables, or
+// for force kind 2 the shell force plus the damping of eq. (16).
+__device__ __forceinline__ void ext_force(const Grid &g, int x, int y, double &fx, double &fy) {
+  if (g.ft64) {
+    double rx, ry;
+    damping_at<double, double>(g.damp, g.trig64, g.nx, g.ny, x, y, rx, ry);
+    const size_t c = (size_t)y * g.nx + x, N = (size_t)g.nx * g.ny;
+    fx = g.ft64[c] + rx;
+    fy = g.ft64[N + c] + ry;
+  } else {
+    fx = g.fxt[y];
+    fy = g.fyt[x];
+  }
+}
 
 template <typename T>
 __host__ __device__ inline T *fld(double *base, int k, size_t N) {
@@ -172,6 +189,9 @@ __device__ __forceinline__ Grid job_grid(const DiagJob &J) {
   g.rho_ref = J.rho_ref;
   g.fxt = J.fxt;
   g.fyt = J.fyt;
+  g.ft64 = nullptr;  // kind 2 is handled per level in k_prep
+  g.trig64 = nullptr;
+  g.damp = nullptr;
   return g;
 }
 
@@ -345,8 +365,22 @@ __global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) 
       L = levels_pairs<T>(J, N, c);
     else
       L = levels<T>(J, N, c);
-    T a, fex, fey;  // alpha, F_ext,x(y), F_ext,y(x)
-    if constexpr (PAIRS && sizeof(T) == 4) {
+    // alpha, the external force at level n, and its changes between levels
+    // (non-zero only for the time-dependent damping of force kind 2)
+    T a, fex, fey, dfx01 = 0, dfy01 = 0, dfx12 = 0, dfy12 = 0;
+    if (J.force_kind == 2) {
+      a = (T)g.alpha;
+      double r[3][2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        damping_at<double, double>(J.dc[k], J.trig64, g.nx, g.ny, x, y, r[k][0], r[k][1]);
+      fex = (T)(J.ft64[c] + r[0][0]);
+      fey = (T)(J.ft64[N + c] + r[0][1]);
+      dfx01 = (T)(r[0][0] - r[1][0]);
+      dfy01 = (T)(r[0][1] - r[1][1]);
+      dfx12 = (T)(r[1][0] - r[2][0]);
+      dfy12 = (T)(r[1][1] - r[2][1]);
+    } else if constexpr (PAIRS && sizeof(T) == 4) {
       a = J.alpha_f;
       fex = J.fxt_f[y];
       fey = J.fyt_f[x];
@@ -358,9 +392,12 @@ __global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) 
     const T ca = T(1) - T(0.5) * a;
     const T Fx = fex - a * L.jx0, Fy = fey - a * L.jy0;
     const T u0 = (L.jx0 + T(0.5) * Fx) / L.r0, v0 = (L.jy0 + T(0.5) * Fy) / L.r0;
-    const T du01 = (ca * L.djx01 - u0 * L.dr01) / L.r1, dv01 = (ca * L.djy01 - v0 * L.dr01) / L.r1;
+    // m^n - m^{n-1} = (1 - alpha/2)(j^n - j^{n-1}) + (F_ext^n - F_ext^{n-1})/2
+    const T du01 = (ca * L.djx01 + T(0.5) * dfx01 - u0 * L.dr01) / L.r1;
+    const T dv01 = (ca * L.djy01 + T(0.5) * dfy01 - v0 * L.dr01) / L.r1;
     const T u1 = u0 - du01, v1 = v0 - dv01;
-    const T du12 = (ca * L.djx12 - u1 * L.dr12) / L.r2, dv12 = (ca * L.djy12 - v1 * L.dr12) / L.r2;
+    const T du12 = (ca * L.djx12 + T(0.5) * dfx12 - u1 * L.dr12) / L.r2;
+    const T dv12 = (ca * L.djy12 + T(0.5) * dfy12 - v1 * L.dr12) / L.r2;
     const T q0 = u0 * u0 + v0 * v0, q1 = u1 * u1 + v1 * v1;
     const T dE01 = T(0.5) * (L.dr01 * q0 +
                              L.r1 * (du01 * (T(2) * u0 - du01) + dv01 * (T(2) * v0 - dv01)));
@@ -561,7 +598,9 @@ __global__ void k_moments(Grid g, const double *snap, size_t N, double *rho, dou
                           double *uy) {
   CELL_INDEX;
   const double r = snap[c], jx = snap[N + c], jy = snap[2 * N + c];
-  const double Fx = g.fxt[y] - g.alpha * jx, Fy = g.fyt[x] - g.alpha * jy;
+  double fex, fey;
+  ext_force(g, x, y, fex, fey);
+  const double Fx = fex - g.alpha * jx, Fy = fey - g.alpha * jy;
   if (rho) rho[c] = r;
   ux[c] = (jx + 0.5 * Fx) / r;
   uy[c] = (jy + 0.5 * Fy) / r;
@@ -582,7 +621,9 @@ __global__ void k_global(Grid g, const double *snap, const double *ux, const dou
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
     const Nb nb = make_nb(g, x, y);
     const double r = snap[c], jx = snap[N + c], jy = snap[2 * N + c];
-    const double Fx = g.fxt[y] - g.alpha * jx, Fy = g.fyt[x] - g.alpha * jy;
+    double fex, fey;
+    ext_force(g, x, y, fex, fey);
+    const double Fx = fex - g.alpha * jx, Fy = fey - g.alpha * jy;
     const double u = ux[c], v = uy[c];
     const double dxu = Dx(ux, nb), dyu = Dy(ux, nb);
     const double dxv = Dx(uy, nb), dyv = Dy(uy, nb);
@@ -1077,6 +1118,10 @@ Grid grid_of(const Member &hm) {
   g.rho_ref = hm.rho0;
   g.fxt = hm.fx_tab64;
   g.fyt = hm.fy_tab64;
+  const bool k2 = hm.force_kind == 2;  // damping of the current state (Member::damp)
+  g.ft64 = k2 ? hm.ft_tab64 : nullptr;
+  g.trig64 = k2 ? hm.trig64 : nullptr;
+  g.damp = k2 ? hm.damp : nullptr;
   return g;
 }
 

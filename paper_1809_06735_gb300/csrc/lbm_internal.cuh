@@ -51,7 +51,49 @@ struct Member {
                          // FP64 [3][N], or FP32 storage (hi, lo) pairs
                          // [3][2][N] of rho - rho0, jx, jy
   int *status;           // divergence flag
+  // force kind 2 (shell force of eqs. (14), (15), damping of eq. (16))
+  double FR0;
+  void *ft_tab;          // shell force F^T: [2][ny][pitch] (float or double)
+  double *ft_tab64;      // the same in FP64, [2][ny * nx]
+  void *trig;            // cos, sin of 2 pi x/nx and 4 pi x/nx ([4][nx]), then
+                         // of 2 pi y/ny and 4 pi y/ny ([4][ny]) (float or double)
+  double *trig64;        // the same in FP64
+  double *damp;          // damping coefficients of the state being stepped
+  float *damp_f;         // (kDamp values, layout at damping_at) and float copies
+  double *damp_ring;     // the coefficients of each snapshot ring slot [3][kDamp]
+  double *proj_part;     // projection CTA partials [CTAs][kDamp]
 };
+
+// Damping coefficients of eq. (16): for component c (0: x, 1: y) and the
+// representatives m of the 6 pairs +-k, 1 <= |k| <= 2, in the order (1,0),
+// (0,1), (1,1), (1,-1), (2,0), (0,2): A = -2 F^R_0 C, B = -2 F^R_0 S at
+// [c * 12 + 2 m] and [c * 12 + 2 m + 1], with C, S the means over the grid
+// of u_c cos(theta_m), u_c sin(theta_m).  The pair sums double the terms.
+constexpr int kDamp = 24;
+
+// F^R(x, y) from the coefficients D and the trig tables (layout at
+// Member::trig): sum_m A_m cos(theta_m) + B_m sin(theta_m), with the (1,1)
+// and (1,-1) terms regrouped by the angle-sum identities.
+template <typename T, typename C>
+__host__ __device__ inline void damping_at(const C *D, const T *trig, int nx, int ny, int x,
+                                           int y, T &fx, T &fy) {
+  const T cx = trig[x], sx = trig[nx + x], c2x = trig[2 * nx + x], s2x = trig[3 * nx + x];
+  const T *ty = trig + 4 * nx;
+  const T cy = ty[y], sy = ty[ny + y], c2y = ty[2 * ny + y], s2y = ty[3 * ny + y];
+  T out[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const C *d = D + 12 * k;
+    const T A0 = (T)d[0], B0 = (T)d[1], A1 = (T)d[2], B1 = (T)d[3], A2 = (T)d[4], B2 = (T)d[5];
+    const T A3 = (T)d[6], B3 = (T)d[7], A4 = (T)d[8], B4 = (T)d[9], A5 = (T)d[10], B5 = (T)d[11];
+    const T P = A0 + (A2 + A3) * cy + (B2 - B3) * sy;
+    const T Q = B0 + (B2 + B3) * cy - (A2 - A3) * sy;
+    const T R = A1 * cy + B1 * sy + A5 * c2y + B5 * s2y;
+    out[k] = P * cx + Q * sx + A4 * c2x + B4 * s2x + R;
+  }
+  fx = out[0];
+  fy = out[1];
+}
 
 // Tile of the batched stream-collide: member, first x, first y.
 struct Tile {
@@ -71,6 +113,7 @@ struct LaunchCfg {
   int block_warps_y;  // warps per CTA (rows per CTA pass)
   int rows_per_warp;  // rows each warp processes per tile
   int grid_ctas;      // 0: one CTA per tile; else persistent grid size
+  int paper_force;    // 1: some member has force kind 2 (kernel variant)
 };
 
 cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, int ntiles,
@@ -84,6 +127,13 @@ cudaError_t launch_get_populations(int precision, const Member *d_members, int m
                                    int nx, int ny, int cur, double *f, cudaStream_t s);
 cudaError_t launch_set_populations(int precision, const Member *d_members, int member,
                                    int nx, int ny, int cur, const double *f, cudaStream_t s);
+// Damping of eq. (16): the projection of the bare velocity of the current
+// state (storage `state`) of every kind-2 member on the 6 mode pairs, then
+// the coefficients (kDamp doubles): slot < 0 into Member::damp / damp_f
+// (the step about to run), slot 0..2 into that ring slot of damp_ring.
+// Two launches; members of other kinds are skipped.
+cudaError_t launch_projection(int precision, const Member *d_members, int n_members,
+                              int nx_max, int ny_max, int state, int slot, cudaStream_t s);
 // The ring snapshot of every member in one launch (layout at Member::snap).
 cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_members,
                                  int nx_max, int ny_max, int state, int slot, cudaStream_t s);
@@ -130,6 +180,9 @@ struct DiagJob {
                                // periodic origins), per-box row offset,
                                // statistics row, unused x3}
   int nL, max_boxes;
+  int force_kind;              // 2: external force = ft64 + damping from dc[level]
+  const double *ft64, *trig64; // force kind 2: shell force [2][N], trig tables
+  const double *dc[3];         // force kind 2: damping coefficients at n, n-1, n-2
   int qblocks;                 // query CTAs per (size, balance):
                                // diag_query_blocks(max_boxes, origin list?)
 };

@@ -110,7 +110,44 @@ __device__ __forceinline__ void *state_buffer(const Member &M, int state) {
 // MODE 0: double-buffer pull; 1: AA even phase; 2: AA odd phase.
 // ---------------------------------------------------------------------------
 
-template <int ROWS, int MODE>
+// External force of 4 consecutive cells (x .. x+3, x % 4 == 0) of row y for
+// force kind 2: the shell force table plus the damping of eq. (16) from the
+// member's coefficients of this step.
+__device__ __forceinline__ void paper_force4(const Member &M, int x, int y, float (&fx)[4],
+                                             float (&fy)[4]) {
+  const float *ft = static_cast<const float *>(M.ft_tab) + (size_t)y * M.pitch + x;
+  const float4 tx = __ldg(reinterpret_cast<const float4 *>(ft));
+  const float4 ty = __ldg(reinterpret_cast<const float4 *>(ft + M.plane));
+  const float *tr = static_cast<const float *>(M.trig);
+  const int nx = M.nx, ny = M.ny;
+  const float4 cx = __ldg(reinterpret_cast<const float4 *>(tr + x));
+  const float4 sx = __ldg(reinterpret_cast<const float4 *>(tr + nx + x));
+  const float4 c2x = __ldg(reinterpret_cast<const float4 *>(tr + 2 * nx + x));
+  const float4 s2x = __ldg(reinterpret_cast<const float4 *>(tr + 3 * nx + x));
+  const float *tyt = tr + 4 * nx;
+  const float cy = tyt[y], sy = tyt[ny + y], c2y = tyt[2 * ny + y], s2y = tyt[3 * ny + y];
+  const float bx[4] = {tx.x, tx.y, tx.z, tx.w}, by[4] = {ty.x, ty.y, ty.z, ty.w};
+  const float cxa[4] = {cx.x, cx.y, cx.z, cx.w}, sxa[4] = {sx.x, sx.y, sx.z, sx.w};
+  const float c2xa[4] = {c2x.x, c2x.y, c2x.z, c2x.w}, s2xa[4] = {s2x.x, s2x.y, s2x.z, s2x.w};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float *d = M.damp_f + 12 * k;
+    const float P = d[0] + (d[4] + d[6]) * cy + (d[5] - d[7]) * sy;
+    const float Q = d[1] + (d[5] + d[7]) * cy - (d[4] - d[6]) * sy;
+    const float R = d[2] * cy + d[3] * sy + d[10] * c2y + d[11] * s2y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float v = (k ? by[i] : bx[i]) + P * cxa[i] + Q * sxa[i] + d[8] * c2xa[i] +
+                      d[9] * s2xa[i] + R;
+      if (k)
+        fy[i] = v;
+      else
+        fx[i] = v;
+    }
+  }
+}
+
+template <int ROWS, int MODE, bool PF>
 __global__ void __launch_bounds__(256) k_step_f32_vec(const Member *__restrict__ members,
                                                       const Tile *__restrict__ tiles,
                                                       int ntiles, int cur) {
@@ -174,13 +211,23 @@ __global__ void __launch_bounds__(256) k_step_f32_vec(const Member *__restrict__
         }
       }
       if (active) {
-        const float fx = fxt[y];
+        float fxc[4], fyc[4];
+        if (PF && M.force_kind == 2) {
+          paper_force4(M, x, y, fxc, fyc);
+        } else {
+          const float fx = fxt[y];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            fxc[c] = fx;
+            fyc[c] = fy[c];
+          }
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           float g[kQ];
 #pragma unroll
           for (int l = 0; l < kQ; ++l) g[l] = v[l][c];
-          collide_f32(g, rho0, om, fx, fy[c], alpha);
+          collide_f32(g, rho0, om, fxc[c], fyc[c], alpha);
 #pragma unroll
           for (int l = 0; l < kQ; ++l) v[l][c] = g[l];
         }
@@ -239,15 +286,24 @@ __global__ void __launch_bounds__(256) k_step_f32_vec(const Member *__restrict__
   }
 }
 
-template <int ROWS>
+template <int ROWS, bool PF>
 static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int ntiles, int state,
                             int grid, dim3 block, cudaStream_t s) {
   if (state < 2)
-    k_step_f32_vec<ROWS, 0><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+    k_step_f32_vec<ROWS, 0, PF><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
   else if (state == 2)
-    k_step_f32_vec<ROWS, 1><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+    k_step_f32_vec<ROWS, 1, PF><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
   else
-    k_step_f32_vec<ROWS, 2><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+    k_step_f32_vec<ROWS, 2, PF><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+}
+
+template <int ROWS>
+static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int ntiles, int state,
+                            int grid, dim3 block, bool pf, cudaStream_t s) {
+  if (pf)
+    launch_vec_rows<ROWS, true>(d_members, d_tiles, ntiles, state, grid, block, s);
+  else
+    launch_vec_rows<ROWS, false>(d_members, d_tiles, ntiles, state, grid, block, s);
 }
 
 cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, int ntiles,
@@ -256,9 +312,9 @@ cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, in
   dim3 block(32, lc.block_warps_y);
   int grid = lc.grid_ctas > 0 ? (lc.grid_ctas < ntiles ? lc.grid_ctas : ntiles) : ntiles;
   switch (lc.rows_per_warp) {
-    case 1: launch_vec_rows<1>(d_members, d_tiles, ntiles, state, grid, block, s); break;
-    case 2: launch_vec_rows<2>(d_members, d_tiles, ntiles, state, grid, block, s); break;
-    case 4: launch_vec_rows<4>(d_members, d_tiles, ntiles, state, grid, block, s); break;
+    case 1: launch_vec_rows<1>(d_members, d_tiles, ntiles, state, grid, block, lc.paper_force != 0, s); break;
+    case 2: launch_vec_rows<2>(d_members, d_tiles, ntiles, state, grid, block, lc.paper_force != 0, s); break;
+    case 4: launch_vec_rows<4>(d_members, d_tiles, ntiles, state, grid, block, lc.paper_force != 0, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -277,8 +333,18 @@ __global__ void k_step_scalar(const Member *__restrict__ members, int member, in
   if (x >= M.nx || y >= M.ny) return;
   const T *src = static_cast<const T *>(state_buffer(M, state));
   T *dst = static_cast<T *>(state < 2 ? M.pop[state ^ 1] : M.pop[0]);
-  const T fx = static_cast<const T *>(M.fx_tab)[y];
-  const T fy = static_cast<const T *>(M.fy_tab)[x];
+  T fx = static_cast<const T *>(M.fx_tab)[y];
+  T fy = static_cast<const T *>(M.fy_tab)[x];
+  if (M.force_kind == 2) {  // shell force table + damping of eq. (16)
+    const T *ft = static_cast<const T *>(M.ft_tab) + (size_t)y * M.pitch + x;
+    T rx, ry;
+    if constexpr (sizeof(T) == 4)
+      damping_at<T, float>(M.damp_f, static_cast<const T *>(M.trig), M.nx, M.ny, x, y, rx, ry);
+    else
+      damping_at<T, double>(M.damp, static_cast<const T *>(M.trig), M.nx, M.ny, x, y, rx, ry);
+    fx = ft[0] + rx;
+    fy = ft[M.plane] + ry;
+  }
   T f[kQ];
 #pragma unroll
   for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
@@ -496,6 +562,90 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
   }
 }
 
+// Projection for the damping of eq. (16): each CTA (64 x 4 cells of member
+// blockIdx.z) sums u_c cos(theta_m) and u_c sin(theta_m) over its cells, u =
+// j / rho the bare velocity of the state in storage `state`, in the order of
+// kDamp, and stores the sums (FP64) at its slot of Member::proj_part.
+template <typename T>
+__global__ void __launch_bounds__(256) k_project(const Member *__restrict__ members, int state) {
+  const Member &M = members[blockIdx.z];
+  if (M.force_kind != 2) return;
+  if ((int)(blockIdx.x * 64) >= M.nx || (int)(blockIdx.y * 4) >= M.ny) return;
+  const int x = blockIdx.x * 64 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y;
+  T acc[kDamp];
+#pragma unroll
+  for (int q = 0; q < kDamp; ++q) acc[q] = T(0);
+  if (x < M.nx && y < M.ny) {
+    const T *src = static_cast<const T *>(state_buffer(M, state));
+    T f[kQ];
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
+    T r = sizeof(T) == 4 ? (T)M.rho0_f : T(0), jx = T(0), jy = T(0);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      r += f[l];
+      jx += (T)cx_of(l) * f[l];
+      jy += (T)cy_of(l) * f[l];
+    }
+    const T u[2] = {jx / r, jy / r};
+    const T *tr = static_cast<const T *>(M.trig);
+    const int nx = M.nx, ny = M.ny;
+    const T cx = tr[x], sx = tr[nx + x], c2x = tr[2 * nx + x], s2x = tr[3 * nx + x];
+    const T cy = tr[4 * nx + y], sy = tr[4 * nx + ny + y];
+    const T c2y = tr[4 * nx + 2 * ny + y], s2y = tr[4 * nx + 3 * ny + y];
+    const T cm[6] = {cx, cy, cx * cy - sx * sy, cx * cy + sx * sy, c2x, c2y};
+    const T sm[6] = {sx, sy, sx * cy + cx * sy, sx * cy - cx * sy, s2x, s2y};
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        acc[12 * k + 2 * m] = u[k] * cm[m];
+        acc[12 * k + 2 * m + 1] = u[k] * sm[m];
+      }
+  }
+  __shared__ double sh[kDamp][8];
+  const int tid = threadIdx.y * 64 + threadIdx.x, lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < kDamp; ++q) {
+    T a = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[q][wid] = (double)a;
+  }
+  __syncthreads();
+  if (tid < kDamp) {
+    double a = 0.0;
+    for (int w = 0; w < 8; ++w) a += sh[tid][w];
+    const int blk = blockIdx.y * ((M.nx + 63) / 64) + blockIdx.x;
+    M.proj_part[(size_t)blk * kDamp + tid] = a;
+  }
+}
+
+// Coefficients from the CTA sums, one CTA per member: 8 threads per value
+// sum interleaved CTA partials, then a fixed-order combination.
+__global__ void k_project_final(const Member *__restrict__ members, int slot) {
+  const Member &M = members[blockIdx.x];
+  if (M.force_kind != 2) return;
+  const int nblk = ((M.nx + 63) / 64) * ((M.ny + 3) / 4);
+  const int q = threadIdx.x >> 3, j = threadIdx.x & 7;
+  __shared__ double sh[kDamp][8];
+  double a = 0.0;
+  for (int b = j; b < nblk; b += 8) a += M.proj_part[(size_t)b * kDamp + q];
+  sh[q][j] = a;
+  __syncthreads();
+  if (j == 0) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += sh[q][k];
+    const double coef = -2.0 * M.FR0 * s / ((double)M.nx * (double)M.ny);
+    if (slot < 0) {
+      M.damp[q] = coef;
+      M.damp_f[q] = (float)coef;
+    } else {
+      M.damp_ring[slot * kDamp + q] = coef;
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_status(const Member *__restrict__ members, int member, int state) {
   const Member &M = members[member];
@@ -559,6 +709,19 @@ cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_m
     k_snapshot_ring<float><<<g, b, 0, s>>>(d_members, state, slot);
   else
     k_snapshot_ring<double><<<g, b, 0, s>>>(d_members, state, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_projection(int precision, const Member *d_members, int n_members,
+                              int nx_max, int ny_max, int state, int slot, cudaStream_t s) {
+  const dim3 b(64, 4);
+  dim3 g = grid2d(nx_max, ny_max, b);
+  g.z = n_members;
+  if (precision == 32)
+    k_project<float><<<g, b, 0, s>>>(d_members, state);
+  else
+    k_project<double><<<g, b, 0, s>>>(d_members, state);
+  k_project_final<<<n_members, kDamp * 8, 0, s>>>(d_members, slot);
   return cudaGetLastError();
 }
 
