@@ -33,7 +33,7 @@ thread_local std::string g_last_error = "no error";
 struct Layout {
   size_t members, tiles, status;
   std::vector<size_t> pop0, pop1, fx, fy, fx64, fy64, snap;
-  std::vector<size_t> ft, ft64, trig, trig64, damp, damp_f, damp_ring, proj;  // force kind 2
+  std::vector<size_t> ft, ft64, trig, trig64, damp, damp_f, damp_ring, proj, drows;  // kind 2
   size_t scratch, partials, jpart, jobs, stats, Ls, out7, origins;
   size_t edges, hist, mach;  // distributions: bin edges, histograms, Ma_V statistics
   int diag_slots;          // members per batched diagnostic launch
@@ -186,6 +186,7 @@ Layout make_layout(const lbm_config *cfg) {
     L.damp_f.push_back(take(k2 ? 4 * lbm::kDamp : 0));
     L.damp_ring.push_back(take(k2 ? 8 * 3 * lbm::kDamp : 0));
     L.proj.push_back(take(k2 ? 8 * lbm::kDamp * pctas : 0));
+    L.drows.push_back(take(k2 && cfg->precision == 32 ? 4 * 6 * (size_t)c.ny : 0));
     L.Nmax = std::max(L.Nmax, N);
   }
   L.scratch_fields = lbm::kDiagFields;
@@ -566,6 +567,8 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
       M.damp_f = reinterpret_cast<float *>(ws_at(h, lay.damp_f[m]));
       M.damp_ring = reinterpret_cast<double *>(ws_at(h, lay.damp_ring[m]));
       M.proj_part = reinterpret_cast<double *>(ws_at(h, lay.proj[m]));
+      M.damp_rows = h->precision == 32 ? reinterpret_cast<float *>(ws_at(h, lay.drows[m]))
+                                       : nullptr;
       h->has_kind2 = true;
     }
     h->hm.push_back(M);

@@ -62,6 +62,7 @@ struct Member {
   float *damp_f;         // (kDamp values, layout at damping_at) and float copies
   double *damp_ring;     // the coefficients of each snapshot ring slot [3][kDamp]
   double *proj_part;     // projection CTA partials [CTAs][kDamp]
+  float *damp_rows;      // FP32 storage: per-row damping factors [ny][6]
 };
 
 // Damping coefficients of eq. (16): for component c (0: x, 1: y) and the

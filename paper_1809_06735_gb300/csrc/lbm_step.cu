@@ -119,26 +119,23 @@ __device__ __forceinline__ void paper_force4(const Member &M, int x, int y, floa
   const float4 tx = __ldg(reinterpret_cast<const float4 *>(ft));
   const float4 ty = __ldg(reinterpret_cast<const float4 *>(ft + M.plane));
   const float *tr = static_cast<const float *>(M.trig);
-  const int nx = M.nx, ny = M.ny;
+  const int nx = M.nx;
   const float4 cx = __ldg(reinterpret_cast<const float4 *>(tr + x));
   const float4 sx = __ldg(reinterpret_cast<const float4 *>(tr + nx + x));
   const float4 c2x = __ldg(reinterpret_cast<const float4 *>(tr + 2 * nx + x));
   const float4 s2x = __ldg(reinterpret_cast<const float4 *>(tr + 3 * nx + x));
-  const float *tyt = tr + 4 * nx;
-  const float cy = tyt[y], sy = tyt[ny + y], c2y = tyt[2 * ny + y], s2y = tyt[3 * ny + y];
+  const float *row = M.damp_rows + 6 * (size_t)y;  // (P, Q, R) of x, then of y
   const float bx[4] = {tx.x, tx.y, tx.z, tx.w}, by[4] = {ty.x, ty.y, ty.z, ty.w};
   const float cxa[4] = {cx.x, cx.y, cx.z, cx.w}, sxa[4] = {sx.x, sx.y, sx.z, sx.w};
   const float c2xa[4] = {c2x.x, c2x.y, c2x.z, c2x.w}, s2xa[4] = {s2x.x, s2x.y, s2x.z, s2x.w};
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const float *d = M.damp_f + 12 * k;
-    const float P = d[0] + (d[4] + d[6]) * cy + (d[5] - d[7]) * sy;
-    const float Q = d[1] + (d[5] + d[7]) * cy - (d[4] - d[6]) * sy;
-    const float R = d[2] * cy + d[3] * sy + d[10] * c2y + d[11] * s2y;
+    const float P = row[3 * k], Q = row[3 * k + 1], R = row[3 * k + 2];
+    const float A4 = M.damp_f[12 * k + 8], B4 = M.damp_f[12 * k + 9];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const float v = (k ? by[i] : bx[i]) + P * cxa[i] + Q * sxa[i] + d[8] * c2xa[i] +
-                      d[9] * s2xa[i] + R;
+      const float v = (k ? by[i] : bx[i]) + P * cxa[i] + Q * sxa[i] + A4 * c2xa[i] +
+                      B4 * s2xa[i] + R;
       if (k)
         fy[i] = v;
       else
@@ -603,45 +600,69 @@ __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ memb
         acc[12 * k + 2 * m + 1] = u[k] * sm[m];
       }
   }
-  __shared__ double sh[kDamp][8];
+  // CTA sums in T (256 cells), widened to FP64 once per CTA and value: a
+  // per-warp widening would put 24 conversions per warp on GB300's slow
+  // FP64 pipe
+  __shared__ T sh[kDamp][8];
   const int tid = threadIdx.y * 64 + threadIdx.x, lane = tid & 31, wid = tid >> 5;
 #pragma unroll
   for (int q = 0; q < kDamp; ++q) {
     T a = acc[q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    if (lane == 0) sh[q][wid] = (double)a;
+    if (lane == 0) sh[q][wid] = a;
   }
   __syncthreads();
   if (tid < kDamp) {
-    double a = 0.0;
-    for (int w = 0; w < 8; ++w) a += sh[tid][w];
+    T a = sh[tid][0];
+    for (int w = 1; w < 8; ++w) a += sh[tid][w];
     const int blk = blockIdx.y * ((M.nx + 63) / 64) + blockIdx.x;
-    M.proj_part[(size_t)blk * kDamp + tid] = a;
+    M.proj_part[(size_t)blk * kDamp + tid] = (double)a;
   }
 }
 
-// Coefficients from the CTA sums, one CTA per member: 8 threads per value
-// sum interleaved CTA partials, then a fixed-order combination.
-__global__ void k_project_final(const Member *__restrict__ members, int slot) {
+// Coefficients from the CTA sums, one CTA (kDamp x 32 threads) per member:
+// 32 threads per value sum interleaved CTA partials, then a fixed-order
+// combination.  For the step about to run (slot < 0) also the per-row
+// factors of the FP32 kernel: with the damping written as
+// P(y) cos(a_x) + Q(y) sin(a_x) + A4 cos(2 a_x) + B4 sin(2 a_x) + R(y)
+// (see damping_at), Member::damp_rows[y] = (P, Q, R) of x, then of y.
+__global__ void __launch_bounds__(kDamp * 32) k_project_final(const Member *__restrict__ members,
+                                                                int slot) {
   const Member &M = members[blockIdx.x];
   if (M.force_kind != 2) return;
   const int nblk = ((M.nx + 63) / 64) * ((M.ny + 3) / 4);
-  const int q = threadIdx.x >> 3, j = threadIdx.x & 7;
-  __shared__ double sh[kDamp][8];
+  const int q = threadIdx.x >> 5, j = threadIdx.x & 31;
+  __shared__ double sh[kDamp][33];
+  __shared__ double coef[kDamp];
   double a = 0.0;
-  for (int b = j; b < nblk; b += 8) a += M.proj_part[(size_t)b * kDamp + q];
+  for (int b = j; b < nblk; b += 32) a += M.proj_part[(size_t)b * kDamp + q];
   sh[q][j] = a;
   __syncthreads();
   if (j == 0) {
     double s = 0.0;
-    for (int k = 0; k < 8; ++k) s += sh[q][k];
-    const double coef = -2.0 * M.FR0 * s / ((double)M.nx * (double)M.ny);
+    for (int k = 0; k < 32; ++k) s += sh[q][k];
+    const double c = -2.0 * M.FR0 * s / ((double)M.nx * (double)M.ny);
+    coef[q] = c;
     if (slot < 0) {
-      M.damp[q] = coef;
-      M.damp_f[q] = (float)coef;
+      M.damp[q] = c;
+      M.damp_f[q] = (float)c;
     } else {
-      M.damp_ring[slot * kDamp + q] = coef;
+      M.damp_ring[slot * kDamp + q] = c;
+    }
+  }
+  if (slot >= 0 || M.damp_rows == nullptr) return;
+  __syncthreads();
+  const double *ty = M.trig64 + 4 * (size_t)M.nx;
+  for (int y = threadIdx.x; y < M.ny; y += blockDim.x) {
+    const double cy = ty[y], sy = ty[M.ny + y], c2y = ty[2 * M.ny + y], s2y = ty[3 * M.ny + y];
+    float *row = M.damp_rows + 6 * (size_t)y;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double *d = coef + 12 * k;
+      row[3 * k] = (float)(d[0] + (d[4] + d[6]) * cy + (d[5] - d[7]) * sy);
+      row[3 * k + 1] = (float)(d[1] + (d[5] + d[7]) * cy - (d[4] - d[6]) * sy);
+      row[3 * k + 2] = (float)(d[2] * cy + d[3] * sy + d[10] * c2y + d[11] * s2y);
     }
   }
 }
@@ -721,7 +742,7 @@ cudaError_t launch_projection(int precision, const Member *d_members, int n_memb
     k_project<float><<<g, b, 0, s>>>(d_members, state);
   else
     k_project<double><<<g, b, 0, s>>>(d_members, state);
-  k_project_final<<<n_members, kDamp * 8, 0, s>>>(d_members, slot);
+  k_project_final<<<n_members, kDamp * 32, 0, s>>>(d_members, slot);
   return cudaGetLastError();
 }
 

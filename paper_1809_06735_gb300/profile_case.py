@@ -4,6 +4,7 @@
     python -m paper_1809_06735_gb300.profile_case step_full  # the same, 64 x 512^2
     python -m paper_1809_06735_gb300.profile_case diag     # one diagnostic event, 512^2
     python -m paper_1809_06735_gb300.profile_case diag_batch  # batched event, 16 x 512^2
+    python -m paper_1809_06735_gb300.profile_case paper_forcing  # force kind 2, 64 x 256^2
     python -m paper_1809_06735_gb300.profile_case fp64     # plain FP64 step, 512^2
     python -m paper_1809_06735_gb300.profile_case adjoint  # FP64 adjoint steps, 256^2
 
@@ -45,6 +46,18 @@ def case_step_full(members=64, n=512, steps=200):
     lat.step(steps)
     torch.cuda.synchronize()
     print("step_full case done:", lat.launch_count, "launches", lat.tuning())
+
+
+def case_paper_forcing(members=64, n=256, steps=30):
+    """The paper's forcing (force kind 2) on 64 FP32 members of 256^2: the
+    damping projection and the stream-collide with the shell-force table."""
+    lat = Lattice([Member(n, n, 0.52, 1.0, 2, 0, 8e-4, 0.0, 0.0, 1e-5)] * members,
+                  precision=32, graph_steps=0)
+    for m in range(members):
+        lat.init_fields(m, *li.random_phase(n, seed=3000 + m, u_rms=0.02))
+    lat.step(steps)
+    torch.cuda.synchronize()
+    print("paper forcing case done:", lat.launch_count, "launches", lat.tuning())
 
 
 def case_diag(n=512, events=2):
@@ -100,5 +113,6 @@ def case_adjoint(n=256, steps=6):
 
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "step"
-    {"step": case_step, "step_full": case_step_full, "diag": case_diag, "diag_batch": case_diag_batch, "fp64": case_fp64,
+    {"step": case_step, "step_full": case_step_full, "paper_forcing": case_paper_forcing,
+     "diag": case_diag, "diag_batch": case_diag_batch, "fp64": case_fp64,
      "adjoint": case_adjoint}[which]()
