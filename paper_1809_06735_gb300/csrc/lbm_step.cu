@@ -559,35 +559,47 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
   }
 }
 
-// Projection for the damping of eq. (16): each CTA (64 x 4 cells of member
-// blockIdx.z) sums u_c cos(theta_m) and u_c sin(theta_m) over its cells, u =
-// j / rho the bare velocity of the state in storage `state`, in the order of
-// kDamp, and stores the sums (FP64) at its slot of Member::proj_part.
+// Projection for the damping of eq. (16): each CTA (64 x 16 cells of member
+// blockIdx.z; every thread 4 rows, 4 apart) sums u_c cos(theta_m) and
+// u_c sin(theta_m) over its cells, u = j / rho the bare velocity of the
+// state in storage `state`, in the order of kDamp, and stores the sums
+// (FP64) at its slot of Member::proj_part.
+constexpr int kProjRows = 4;
 template <typename T>
 __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ members, int state) {
   const Member &M = members[blockIdx.z];
   if (M.force_kind != 2) return;
-  if ((int)(blockIdx.x * 64) >= M.nx || (int)(blockIdx.y * 4) >= M.ny) return;
-  const int x = blockIdx.x * 64 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y;
+  if ((int)(blockIdx.x * 64) >= M.nx || (int)(blockIdx.y * 4 * kProjRows) >= M.ny) return;
+  const int nx = M.nx, ny = M.ny;
+  const int x = blockIdx.x * 64 + threadIdx.x;
   T acc[kDamp];
 #pragma unroll
   for (int q = 0; q < kDamp; ++q) acc[q] = T(0);
-  if (x < M.nx && y < M.ny) {
-    const T *src = static_cast<const T *>(state_buffer(M, state));
+  const T *src = static_cast<const T *>(state_buffer(M, state));
+  const T *tr = static_cast<const T *>(M.trig);
+  T cx = 0, sx = 0, c2x = 0, s2x = 0;
+  if (x < nx) {
+    cx = tr[x];
+    sx = tr[nx + x];
+    c2x = tr[2 * nx + x];
+    s2x = tr[3 * nx + x];
+  }
+#pragma unroll
+  for (int r = 0; r < kProjRows; ++r) {
+    const int y = blockIdx.y * 4 * kProjRows + r * 4 + threadIdx.y;
+    if (x >= nx || y >= ny) continue;
     T f[kQ];
 #pragma unroll
     for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
-    T r = sizeof(T) == 4 ? (T)M.rho0_f : T(0), jx = T(0), jy = T(0);
+    T rho = sizeof(T) == 4 ? (T)M.rho0_f : T(0), jx = T(0), jy = T(0);
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
-      r += f[l];
+      rho += f[l];
       jx += (T)cx_of(l) * f[l];
       jy += (T)cy_of(l) * f[l];
     }
-    const T u[2] = {jx / r, jy / r};
-    const T *tr = static_cast<const T *>(M.trig);
-    const int nx = M.nx, ny = M.ny;
-    const T cx = tr[x], sx = tr[nx + x], c2x = tr[2 * nx + x], s2x = tr[3 * nx + x];
+    const T ir = T(1) / rho;
+    const T u[2] = {jx * ir, jy * ir};
     const T cy = tr[4 * nx + y], sy = tr[4 * nx + ny + y];
     const T c2y = tr[4 * nx + 2 * ny + y], s2y = tr[4 * nx + 3 * ny + y];
     const T cm[6] = {cx, cy, cx * cy - sx * sy, cx * cy + sx * sy, c2x, c2y};
@@ -596,13 +608,12 @@ __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ memb
     for (int k = 0; k < 2; ++k)
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
-        acc[12 * k + 2 * m] = u[k] * cm[m];
-        acc[12 * k + 2 * m + 1] = u[k] * sm[m];
+        acc[12 * k + 2 * m] += u[k] * cm[m];
+        acc[12 * k + 2 * m + 1] += u[k] * sm[m];
       }
   }
-  // CTA sums in T (256 cells), widened to FP64 once per CTA and value: a
-  // per-warp widening would put 24 conversions per warp on GB300's slow
-  // FP64 pipe
+  // CTA sums in T, widened to FP64 once per CTA and value: a per-warp
+  // widening would put 24 conversions per warp on GB300's slow FP64 pipe
   __shared__ T sh[kDamp][8];
   const int tid = threadIdx.y * 64 + threadIdx.x, lane = tid & 31, wid = tid >> 5;
 #pragma unroll
@@ -616,7 +627,7 @@ __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ memb
   if (tid < kDamp) {
     T a = sh[tid][0];
     for (int w = 1; w < 8; ++w) a += sh[tid][w];
-    const int blk = blockIdx.y * ((M.nx + 63) / 64) + blockIdx.x;
+    const int blk = blockIdx.y * ((nx + 63) / 64) + blockIdx.x;
     M.proj_part[(size_t)blk * kDamp + tid] = (double)a;
   }
 }
@@ -631,18 +642,21 @@ __global__ void __launch_bounds__(kDamp * 32) k_project_final(const Member *__re
                                                                 int slot) {
   const Member &M = members[blockIdx.x];
   if (M.force_kind != 2) return;
-  const int nblk = ((M.nx + 63) / 64) * ((M.ny + 3) / 4);
-  const int q = threadIdx.x >> 5, j = threadIdx.x & 31;
-  __shared__ double sh[kDamp][33];
+  const int nblk = ((M.nx + 63) / 64) * ((M.ny + 4 * kProjRows - 1) / (4 * kProjRows));
+  const int q = threadIdx.x >> 5, j = threadIdx.x & 31;  // one warp per value
   __shared__ double coef[kDamp];
-  double a = 0.0;
-  for (int b = j; b < nblk; b += 32) a += M.proj_part[(size_t)b * kDamp + q];
-  sh[q][j] = a;
-  __syncthreads();
+  double a0 = 0.0, a1 = 0.0;  // two independent chains, fixed order
+  int b = j;
+  for (; b + 32 < nblk; b += 64) {
+    a0 += M.proj_part[(size_t)b * kDamp + q];
+    a1 += M.proj_part[(size_t)(b + 32) * kDamp + q];
+  }
+  if (b < nblk) a0 += M.proj_part[(size_t)b * kDamp + q];
+  double a = a0 + a1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
   if (j == 0) {
-    double s = 0.0;
-    for (int k = 0; k < 32; ++k) s += sh[q][k];
-    const double c = -2.0 * M.FR0 * s / ((double)M.nx * (double)M.ny);
+    const double c = -2.0 * M.FR0 * a / ((double)M.nx * (double)M.ny);
     coef[q] = c;
     if (slot < 0) {
       M.damp[q] = c;
@@ -736,7 +750,7 @@ cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_m
 cudaError_t launch_projection(int precision, const Member *d_members, int n_members,
                               int nx_max, int ny_max, int state, int slot, cudaStream_t s) {
   const dim3 b(64, 4);
-  dim3 g = grid2d(nx_max, ny_max, b);
+  dim3 g = grid2d(nx_max, ny_max, dim3(64, 4 * kProjRows));
   g.z = n_members;
   if (precision == 32)
     k_project<float><<<g, b, 0, s>>>(d_members, state);
