@@ -33,7 +33,7 @@ thread_local std::string g_last_error = "no error";
 struct Layout {
   size_t members, tiles, status;
   std::vector<size_t> pop0, pop1, fx, fy, fx64, fy64, snap;
-  std::vector<size_t> ft, ft64, trig, trig64, damp, damp_f, damp_ring, proj, drows;  // kind 2
+  std::vector<size_t> ft, ft64, trig, trig64, damp, damp_f, damp_ring, proj, drows, pcount;
   size_t scratch, partials, jpart, jobs, stats, Ls, out7, origins;
   size_t edges, hist, mach;  // distributions: bin edges, histograms, Ma_V statistics
   int diag_slots;          // members per batched diagnostic launch
@@ -187,6 +187,7 @@ Layout make_layout(const lbm_config *cfg) {
     L.damp_ring.push_back(take(k2 ? 8 * 3 * lbm::kDamp : 0));
     L.proj.push_back(take(k2 ? 8 * lbm::kDamp * pctas : 0));
     L.drows.push_back(take(k2 && cfg->precision == 32 ? 4 * 6 * (size_t)c.ny : 0));
+    L.pcount.push_back(take(k2 ? sizeof(unsigned) : 0));
     L.Nmax = std::max(L.Nmax, N);
   }
   L.scratch_fields = lbm::kDiagFields;
@@ -319,7 +320,7 @@ int launch_one_step(lbm_handle *h, cudaStream_t s, int cur) {
 }
 
 long long kernels_per_step(const lbm_handle *h) {
-  return (h->ntiles > 0 ? 1 : 0) + (long long)h->scalar_members.size() + (h->has_kind2 ? 2 : 0);
+  return (h->ntiles > 0 ? 1 : 0) + (long long)h->scalar_members.size() + (h->has_kind2 ? 1 : 0);
 }
 
 void drop_graphs(lbm_handle *h) {
@@ -401,7 +402,7 @@ int record(lbm_handle *h) {
   h->launches += 1;
   if (h->has_kind2) {  // the damping of this state, for the diagnostic
     if (int rc = project(h, h->stream, h->cur, slot)) return rc;
-    h->launches += 2;
+    h->launches += 1;
   }
   h->ring_time[slot] = h->t;
   return LBM_OK;
@@ -569,6 +570,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
       M.proj_part = reinterpret_cast<double *>(ws_at(h, lay.proj[m]));
       M.damp_rows = h->precision == 32 ? reinterpret_cast<float *>(ws_at(h, lay.drows[m]))
                                        : nullptr;
+      M.proj_count = reinterpret_cast<unsigned *>(ws_at(h, lay.pcount[m]));
       h->has_kind2 = true;
     }
     h->hm.push_back(M);
@@ -605,6 +607,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
       if (e == cudaSuccess) e = cudaMemsetAsync(M.damp, 0, 8 * lbm::kDamp, s);
       if (e == cudaSuccess) e = cudaMemsetAsync(M.damp_f, 0, 4 * lbm::kDamp, s);
       if (e == cudaSuccess) e = cudaMemsetAsync(M.damp_ring, 0, 8 * 3 * lbm::kDamp, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(M.proj_count, 0, sizeof(unsigned), s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables are temporaries
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // fx/fy are temporaries
@@ -733,7 +736,7 @@ int lbm_moments(lbm_handle *h, int member, double *rho, double *ux, double *uy,
   double *snap = h->sc.f;  // scratch fields 0..2
   if (c.force_kind == 2) {  // damping of the current state into Member::damp
     if ((rc = project(h, h->stream, h->cur, -1))) return rc;
-    h->launches += 2;
+    h->launches += 1;
   }
   CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, snap, h->stream));
   CK(lbm::diag_moments(h->hm[member], snap, rho, ux, uy, omega, h->sc, h->stream));
@@ -751,7 +754,7 @@ int lbm_global_balance(lbm_handle *h, int member, double *out) {
   double *out_dev = reinterpret_cast<double *>(ws_at(h, h->lay.out7));
   if (c.force_kind == 2) {  // damping of the current state into Member::damp
     if ((rc = project(h, h->stream, h->cur, -1))) return rc;
-    h->launches += 2;
+    h->launches += 1;
   }
   CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, snap, h->stream));
   CK(lbm::diag_global(h->hm[member], snap, h->sc, out_dev, h->stream));

@@ -63,6 +63,7 @@ struct Member {
   double *damp_ring;     // the coefficients of each snapshot ring slot [3][kDamp]
   double *proj_part;     // projection CTA partials [CTAs][kDamp]
   float *damp_rows;      // FP32 storage: per-row damping factors [ny][6]
+  unsigned *proj_count;  // CTAs of the projection done (zero between launches)
 };
 
 // Damping coefficients of eq. (16): for component c (0: x, 1: y) and the
@@ -132,7 +133,7 @@ cudaError_t launch_set_populations(int precision, const Member *d_members, int m
 // state (storage `state`) of every kind-2 member on the 6 mode pairs, then
 // the coefficients (kDamp doubles): slot < 0 into Member::damp / damp_f
 // (the step about to run), slot 0..2 into that ring slot of damp_ring.
-// Two launches; members of other kinds are skipped.
+// One launch; members of other kinds are skipped.
 cudaError_t launch_projection(int precision, const Member *d_members, int n_members,
                               int nx_max, int ny_max, int state, int slot, cudaStream_t s);
 // The ring snapshot of every member in one launch (layout at Member::snap).

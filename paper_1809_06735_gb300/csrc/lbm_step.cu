@@ -563,10 +563,16 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
 // blockIdx.z; every thread 4 rows, 4 apart) sums u_c cos(theta_m) and
 // u_c sin(theta_m) over its cells, u = j / rho the bare velocity of the
 // state in storage `state`, in the order of kDamp, and stores the sums
-// (FP64) at its slot of Member::proj_part.
+// (FP64) at its slot of Member::proj_part.  The member's last CTA to finish
+// (a counter in Member::proj_count) reduces the slots in a fixed order into
+// the coefficients: slot < 0 into Member::damp / damp_f and, for FP32
+// storage, the per-row factors P(y) cos(a_x) + Q(y) sin(a_x) + R(y) of
+// damping_at in Member::damp_rows[y] = (P, Q, R) of x, then of y; slot
+// 0..2 into that ring slot of Member::damp_ring.
 constexpr int kProjRows = 4;
 template <typename T>
-__global__ void __launch_bounds__(256) k_project(const Member *__restrict__ members, int state) {
+__global__ void __launch_bounds__(256) k_project(const Member *__restrict__ members, int state,
+                                                 int slot) {
   const Member &M = members[blockIdx.z];
   if (M.force_kind != 2) return;
   if ((int)(blockIdx.x * 64) >= M.nx || (int)(blockIdx.y * 4 * kProjRows) >= M.ny) return;
@@ -624,52 +630,50 @@ __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ memb
     if (lane == 0) sh[q][wid] = a;
   }
   __syncthreads();
+  const int nblk = ((nx + 63) / 64) * ((ny + 4 * kProjRows - 1) / (4 * kProjRows));
   if (tid < kDamp) {
     T a = sh[tid][0];
     for (int w = 1; w < 8; ++w) a += sh[tid][w];
     const int blk = blockIdx.y * ((nx + 63) / 64) + blockIdx.x;
     M.proj_part[(size_t)blk * kDamp + tid] = (double)a;
+    __threadfence();
   }
-}
-
-// Coefficients from the CTA sums, one CTA (kDamp x 32 threads) per member:
-// 32 threads per value sum interleaved CTA partials, then a fixed-order
-// combination.  For the step about to run (slot < 0) also the per-row
-// factors of the FP32 kernel: with the damping written as
-// P(y) cos(a_x) + Q(y) sin(a_x) + A4 cos(2 a_x) + B4 sin(2 a_x) + R(y)
-// (see damping_at), Member::damp_rows[y] = (P, Q, R) of x, then of y.
-__global__ void __launch_bounds__(kDamp * 32) k_project_final(const Member *__restrict__ members,
-                                                                int slot) {
-  const Member &M = members[blockIdx.x];
-  if (M.force_kind != 2) return;
-  const int nblk = ((M.nx + 63) / 64) * ((M.ny + 4 * kProjRows - 1) / (4 * kProjRows));
-  const int q = threadIdx.x >> 5, j = threadIdx.x & 31;  // one warp per value
+  __shared__ int is_last;
+  __syncthreads();
+  if (tid == 0) is_last = atomicAdd(M.proj_count, 1u) == (unsigned)(nblk - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // last CTA: one warp per value, two fixed-order chains and a shuffle tree
   __shared__ double coef[kDamp];
-  double a0 = 0.0, a1 = 0.0;  // two independent chains, fixed order
-  int b = j;
-  for (; b + 32 < nblk; b += 64) {
-    a0 += M.proj_part[(size_t)b * kDamp + q];
-    a1 += M.proj_part[(size_t)(b + 32) * kDamp + q];
-  }
-  if (b < nblk) a0 += M.proj_part[(size_t)b * kDamp + q];
-  double a = a0 + a1;
+  for (int q = wid; q < kDamp; q += 8) {
+    double a0 = 0.0, a1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nblk; b += 64) {
+      a0 += __ldcg(M.proj_part + (size_t)b * kDamp + q);
+      a1 += __ldcg(M.proj_part + (size_t)(b + 32) * kDamp + q);
+    }
+    if (b < nblk) a0 += __ldcg(M.proj_part + (size_t)b * kDamp + q);
+    double a = a0 + a1;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-  if (j == 0) {
-    const double c = -2.0 * M.FR0 * a / ((double)M.nx * (double)M.ny);
-    coef[q] = c;
-    if (slot < 0) {
-      M.damp[q] = c;
-      M.damp_f[q] = (float)c;
-    } else {
-      M.damp_ring[slot * kDamp + q] = c;
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) {
+      const double c = -2.0 * M.FR0 * a / ((double)nx * (double)ny);
+      coef[q] = c;
+      if (slot < 0) {
+        M.damp[q] = c;
+        M.damp_f[q] = (float)c;
+      } else {
+        M.damp_ring[slot * kDamp + q] = c;
+      }
     }
   }
+  if (tid == 0) *M.proj_count = 0u;  // ready for the next launch
   if (slot >= 0 || M.damp_rows == nullptr) return;
   __syncthreads();
-  const double *ty = M.trig64 + 4 * (size_t)M.nx;
-  for (int y = threadIdx.x; y < M.ny; y += blockDim.x) {
-    const double cy = ty[y], sy = ty[M.ny + y], c2y = ty[2 * M.ny + y], s2y = ty[3 * M.ny + y];
+  const double *tyd = M.trig64 + 4 * (size_t)nx;
+  for (int y = tid; y < ny; y += 256) {
+    const double cy = tyd[y], sy = tyd[ny + y], c2y = tyd[2 * ny + y], s2y = tyd[3 * ny + y];
     float *row = M.damp_rows + 6 * (size_t)y;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -753,10 +757,9 @@ cudaError_t launch_projection(int precision, const Member *d_members, int n_memb
   dim3 g = grid2d(nx_max, ny_max, dim3(64, 4 * kProjRows));
   g.z = n_members;
   if (precision == 32)
-    k_project<float><<<g, b, 0, s>>>(d_members, state);
+    k_project<float><<<g, b, 0, s>>>(d_members, state, slot);
   else
-    k_project<double><<<g, b, 0, s>>>(d_members, state);
-  k_project_final<<<n_members, kDamp * 32, 0, s>>>(d_members, slot);
+    k_project<double><<<g, b, 0, s>>>(d_members, state, slot);
   return cudaGetLastError();
 }
 
