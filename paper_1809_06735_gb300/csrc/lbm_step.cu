@@ -145,7 +145,7 @@ __device__ __forceinline__ void paper_force4(const Member &M, int x, int y, floa
 }
 
 template <int ROWS, int MODE, bool PF>
-__global__ void __launch_bounds__(256) k_step_f32_vec(const Member *__restrict__ members,
+__global__ void __launch_bounds__(256, PF ? 3 : 1) k_step_f32_vec(const Member *__restrict__ members,
                                                       const Tile *__restrict__ tiles,
                                                       int ntiles, int cur) {
   const int lane = threadIdx.x;
@@ -559,8 +559,8 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
   }
 }
 
-// Projection for the damping of eq. (16): each CTA (64 x 16 cells of member
-// blockIdx.z; every thread 4 rows, 4 apart) sums u_c cos(theta_m) and
+// Projection for the damping of eq. (16): each CTA (64 x 64 cells of member
+// blockIdx.z; every thread 16 rows, 4 apart) sums u_c cos(theta_m) and
 // u_c sin(theta_m) over its cells, u = j / rho the bare velocity of the
 // state in storage `state`, in the order of kDamp, and stores the sums
 // (FP64) at its slot of Member::proj_part.  The member's last CTA to finish
@@ -569,7 +569,7 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
 // storage, the per-row factors P(y) cos(a_x) + Q(y) sin(a_x) + R(y) of
 // damping_at in Member::damp_rows[y] = (P, Q, R) of x, then of y; slot
 // 0..2 into that ring slot of Member::damp_ring.
-constexpr int kProjRows = 4;
+constexpr int kProjRows = 16;
 template <typename T>
 __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ members, int state,
                                                  int slot) {
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ memb
     c2x = tr[2 * nx + x];
     s2x = tr[3 * nx + x];
   }
-#pragma unroll
+#pragma unroll 4
   for (int r = 0; r < kProjRows; ++r) {
     const int y = blockIdx.y * 4 * kProjRows + r * 4 + threadIdx.y;
     if (x >= nx || y >= ny) continue;
