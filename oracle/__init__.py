@@ -70,7 +70,10 @@ def _load():
             lib.orc_ddx.argtypes = [I, I, P, P]
             lib.orc_ddy.argtypes = [I, I, P, P]
             lib.orc_bdf2.argtypes = [ctypes.c_size_t, P, P, P, P]
-            lib.orc_terms.argtypes = [I, I, D, P, P, P, P, P, P]
+            lib.orc_terms.argtypes = [I, I, D, P, P, P, P, P, P, P]
+            lib.orc_tau_eff.argtypes = [P, D, P]
+            lib.orc_tau_eff.restype = D
+            lib.orc_nu_field.argtypes = [I, I, D, P, P, P]
             lib.orc_terms.restype = I
             lib.orc_box_mean.argtypes = [I, I, P, I, I, I]
             lib.orc_box_mean.restype = D
@@ -105,20 +108,24 @@ def _f64(a) -> np.ndarray:
 
 class _ForceC(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("F0", ctypes.c_double), ("kf", ctypes.c_int),
-                ("alpha", ctypes.c_double), ("phase", ctypes.c_double), ("FR0", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("phase", ctypes.c_double), ("FR0", ctypes.c_double),
+                ("collision", ctypes.c_int), ("Cs", ctypes.c_double)]
 
 
 class Force:
-    """Forcing of one member: kind 1 = Kolmogorov amplitude F0 at wavenumber
-    kf (in units of 2 pi / N); kind 2 = the paper's shell force of eqs. (14),
-    (15) (F^T_0 = F0, phase) plus the damping of eq. (16) (F^R_0 = FR0);
-    in every case drag alpha on the bare momentum."""
+    """Model of one member.  Forcing: kind 1 = Kolmogorov amplitude F0 at
+    wavenumber kf (in units of 2 pi / N); kind 2 = the paper's shell force of
+    eqs. (14), (15) (F^T_0 = F0, phase) plus the damping of eq. (16)
+    (F^R_0 = FR0); in every case drag alpha on the bare momentum.  Collision:
+    0 BGK, 1 Smagorinsky (constant Cs), 2 the turbulent viscosity of eq. (7)."""
 
     def __init__(self, kind: int = 0, F0: float = 0.0, kf: int = 0, alpha: float = 0.0,
-                 phase: float = 0.0, FR0: float = 0.0):
+                 phase: float = 0.0, FR0: float = 0.0, collision: int = 0, Cs: float = 0.0):
         self.kind, self.F0, self.kf, self.alpha = int(kind), float(F0), int(kf), float(alpha)
         self.phase, self.FR0 = float(phase), float(FR0)
-        self._c = _ForceC(self.kind, self.F0, self.kf, self.alpha, self.phase, self.FR0)
+        self.collision, self.Cs = int(collision), float(Cs)
+        self._c = _ForceC(self.kind, self.F0, self.kf, self.alpha, self.phase, self.FR0,
+                          self.collision, self.Cs)
 
     def ptr(self):
         return ctypes.byref(self._c)
@@ -139,6 +146,21 @@ def lattice():
 def feq(rho: float, ux: float, uy: float) -> np.ndarray:
     out = np.zeros(9)
     _load().orc_feq(rho, ux, uy, _p(out))
+    return out
+
+
+def tau_eff(f9, tau0, model: Force):
+    """Local relaxation time of one cell's populations for the collision model."""
+    f9 = _f64(f9)
+    return _load().orc_tau_eff(_p(f9), float(tau0), model.ptr())
+
+
+def nu_field(f, tau0, model: Force):
+    """Local viscosity (tau_eff - 1/2)/3 of every cell of the state f."""
+    f = _f64(f)
+    _, ny, nx = f.shape
+    out = np.empty((ny, nx))
+    _load().orc_nu_field(nx, ny, float(tau0), model.ptr(), _p(f), _p(out))
     return out
 
 
@@ -246,8 +268,9 @@ def bdf2(An, An1, An2):
     return out
 
 
-def terms(tau, rho3, ux3, uy3, Fx, Fy):
-    """13 term fields from (rho, u) at levels n, n-1, n-2 and F at n."""
+def terms(tau, rho3, ux3, uy3, Fx, Fy, nu=None):
+    """13 term fields from (rho, u) at levels n, n-1, n-2 and F at n; the
+    viscosity is (tau - 1/2)/3, or the per-cell field ``nu`` [ny, nx]."""
     rho3 = [_f64(a) for a in rho3]
     ux3 = [_f64(a) for a in ux3]
     uy3 = [_f64(a) for a in uy3]
@@ -258,9 +281,10 @@ def terms(tau, rho3, ux3, uy3, Fx, Fy):
     u = arr(*[a.ctypes.data for a in ux3])
     v = arr(*[a.ctypes.data for a in uy3])
     out = np.empty((NT, ny, nx))
+    nu = None if nu is None else _f64(nu)
     rc = _load().orc_terms(nx, ny, tau, ctypes.cast(r, ctypes.c_void_p),
                            ctypes.cast(u, ctypes.c_void_p), ctypes.cast(v, ctypes.c_void_p),
-                           _p(Fx), _p(Fy), _p(out))
+                           _p(Fx), _p(Fy), None if nu is None else _p(nu), _p(out))
     if rc != 0:
         raise MemoryError("oracle terms failed")
     return out

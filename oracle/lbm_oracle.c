@@ -46,13 +46,16 @@ static const double TW[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
 static const double CS2 = 1.0 / 3.0;
 static const double PI = 3.14159265358979323846;
 
-/* Forcing of one member (Sec. 3 and the workloads):
+/* Model of one member.  Forcing (Sec. 3 and the workloads):
  *   kind 0: none;
  *   kind 1: Kolmogorov F_ext = F0 (sin(2 pi kf y/ny), sin(2 pi kf x/nx));
  *   kind 2: the paper's turbulence forcing, the shell force of eqs. (14),
  *           (15) with amplitude F0 = F^T_0 and phase `phase`, plus the
  *           large-scale damping of eq. (16) with amplitude FR0 = F^R_0;
- * and in every case the linear drag -alpha j on the bare momentum. */
+ * and in every case the linear drag -alpha j on the bare momentum.
+ * Collision (Sec. 1): 0 BGK with tau; 1 Smagorinsky eddy viscosity
+ * nu_t = C |S| (the paper's form, C = Cs, dx = 1); 2 the turbulent
+ * viscosity of eq. (7); each gives a local tau_eff (orc_tau_eff). */
 typedef struct {
   int kind;
   double F0;
@@ -60,7 +63,9 @@ typedef struct {
   double alpha;
   double phase;
   double FR0;
-} orc_force_t;
+  int collision;
+  double Cs;
+} orc_model_t;
 
 static int wrap(int i, int n) {
   int r = i % n;
@@ -99,7 +104,7 @@ void orc_feq(double rho, double ux, double uy, double *feq) {
  * the sum over one wavevector of each pair +-k with 5 <= |k| <= 7 (ky > 0,
  * or ky = 0 and kx > 0; over both members of each pair the phase would only
  * rescale the amplitude by 2 cos phi); zero otherwise. */
-void orc_force_ext(int nx, int ny, const orc_force_t *F, int x, int y,
+void orc_force_ext(int nx, int ny, const orc_model_t *F, int x, int y,
                    double *Fx, double *Fy) {
   *Fx = 0.0;
   *Fy = 0.0;
@@ -176,7 +181,7 @@ static void damping_field(int nx, int ny, double FR0, const double *f,
 
 /* External force of every cell for the state f (drag excluded):
  * orc_force_ext plus, for kind 2, the damping of eq. (16). */
-void orc_force_field(int nx, int ny, const orc_force_t *F, const double *f,
+void orc_force_field(int nx, int ny, const orc_model_t *F, const double *f,
                      double *Fx, double *Fy) {
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x)
@@ -227,9 +232,57 @@ void orc_collide_cell(const double *fin, double tau, double Fex, double Fey,
   }
 }
 
+/* Local relaxation time of one cell (populations fc) for the member's
+ * collision model.  The strain rate comes from the non-equilibrium second
+ * moment of the pre-collision populations, Pi^neq = sum_l c c (f - f_eq),
+ * f_eq = eq. (2) at u = j / rho, through the Chapman-Enskog relation
+ * Pi^neq = -2 rho cs^2 tau S (S_ij = (d_i u_j + d_j u_i) / 2, dt = 1):
+ *   Smagorinsky: tau = tau0 + nu_t / cs^2, nu_t = C sqrt(S:S), with S taken
+ *     at tau itself: tau (tau - tau0) = C sqrt(Pi:Pi) / (2 rho cs^4), the
+ *     positive root tau = (tau0 + sqrt(tau0^2 + 2 C |Pi| / (rho cs^4))) / 2;
+ *   eq. (7): nu_t = -(cs^2 / 3) tau0^2 Tr(S^3) / Tr(S^2) with S taken at tau0
+ *     (the formula assumes tau_eff ~ tau0), i.e. tau = tau0 + tau0 Tr(Pi^3)
+ *     / (2 rho Tr(Pi^2)) (tau0 where Pi = 0). */
+double orc_tau_eff(const double *fc, double tau0, const orc_model_t *P) {
+  if (P->collision == 0) return tau0;
+  double rho, jx, jy, feq[Q];
+  cell_moments(fc, &rho, &jx, &jy);
+  orc_feq(rho, jx / rho, jy / rho, feq);
+  double pxx = 0.0, pxy = 0.0, pyy = 0.0;
+  for (int l = 0; l < Q; ++l) {
+    double d = fc[l] - feq[l];
+    pxx += CX[l] * CX[l] * d;
+    pxy += CX[l] * CY[l] * d;
+    pyy += CY[l] * CY[l] * d;
+  }
+  double tr2 = pxx * pxx + 2.0 * pxy * pxy + pyy * pyy; /* Tr(Pi^2) = Pi:Pi */
+  if (P->collision == 1) {
+    double cs4 = CS2 * CS2;
+    return 0.5 * (tau0 + sqrt(tau0 * tau0 + 2.0 * P->Cs * sqrt(tr2) / (rho * cs4)));
+  }
+  if (tr2 == 0.0) return tau0;
+  /* Tr(Pi^3) of the symmetric 2 x 2 tensor, by matrix products */
+  double a2xx = pxx * pxx + pxy * pxy, a2xy = pxx * pxy + pxy * pyy,
+         a2yy = pxy * pxy + pyy * pyy;
+  double tr3 = a2xx * pxx + 2.0 * a2xy * pxy + a2yy * pyy;
+  return tau0 + tau0 * tr3 / (2.0 * rho * tr2);
+}
+
+/* Local viscosity of every cell of the state f, eq. (5) with the local
+ * relaxation time: nu = cs^2 (tau_eff - 1/2). */
+void orc_nu_field(int nx, int ny, double tau, const orc_model_t *P, const double *f,
+                  double *nu) {
+  size_t plane = (size_t)nx * ny;
+  for (size_t c = 0; c < plane; ++c) {
+    double a[Q];
+    for (int l = 0; l < Q; ++l) a[l] = f[l * plane + c];
+    nu[c] = CS2 * (orc_tau_eff(a, tau, P) - 0.5);
+  }
+}
+
 /* Collision of the whole grid (no streaming): fout = fin + Omega(fin) + F,
  * with the external force of the state fin (orc_force_field). */
-int orc_collide(int nx, int ny, double tau, const orc_force_t *F,
+int orc_collide(int nx, int ny, double tau, const orc_model_t *F,
                 const double *fin, double *fout) {
   size_t plane = (size_t)nx * ny;
   double *Fe = (double *)malloc(sizeof(double) * 2 * plane);
@@ -240,7 +293,7 @@ int orc_collide(int nx, int ny, double tau, const orc_force_t *F,
       size_t c = (size_t)y * nx + x;
       double a[Q], b[Q];
       for (int l = 0; l < Q; ++l) a[l] = fin[l * plane + c];
-      orc_collide_cell(a, tau, Fe[c], Fe[plane + c], F->alpha, b);
+      orc_collide_cell(a, orc_tau_eff(a, tau, F), Fe[c], Fe[plane + c], F->alpha, b);
       for (int l = 0; l < Q; ++l) fout[l * plane + c] = b[l];
     }
   free(Fe);
@@ -262,7 +315,7 @@ void orc_stream(int nx, int ny, const double *fin, double *fout) {
 
 /* One full time step of eq. (1): collide, then stream.  scratch holds one
  * population array (9 nx ny doubles).  f is updated in place. */
-int orc_step(int nx, int ny, double tau, const orc_force_t *F, double *f,
+int orc_step(int nx, int ny, double tau, const orc_model_t *F, double *f,
              double *scratch) {
   if (orc_collide(nx, ny, tau, F, f, scratch)) return -1;
   orc_stream(nx, ny, scratch, f);
@@ -270,7 +323,7 @@ int orc_step(int nx, int ny, double tau, const orc_force_t *F, double *f,
 }
 
 /* nsteps time steps; allocates its own scratch. */
-int orc_run(int nx, int ny, double tau, const orc_force_t *F, double *f,
+int orc_run(int nx, int ny, double tau, const orc_model_t *F, double *f,
             int nsteps) {
   double *s = (double *)malloc(sizeof(double) * Q * (size_t)nx * ny);
   if (!s) return -1;
@@ -288,7 +341,7 @@ int orc_run(int nx, int ny, double tau, const orc_force_t *F, double *f,
  * window cells at least nsteps cells away from its edges hold exactly the
  * values of the global run; the others are meaningless.  The damping of
  * kind 2 depends on the whole grid, so kind 2 is refused (-2). */
-int orc_run_window(int wx, int wy, double tau, const orc_force_t *F, double *f,
+int orc_run_window(int wx, int wy, double tau, const orc_model_t *F, double *f,
                    int nsteps, int X0, int Y0, int NX, int NY) {
   if (F->kind == 2) return -2;
   size_t plane = (size_t)wx * wy;
@@ -300,7 +353,7 @@ int orc_run_window(int wx, int wy, double tau, const orc_force_t *F, double *f,
         double a[Q], b[Q], Fex, Fey;
         for (int l = 0; l < Q; ++l) a[l] = f[l * plane + (size_t)y * wx + x];
         orc_force_ext(NX, NY, F, wrap(X0 + x, NX), wrap(Y0 + y, NY), &Fex, &Fey);
-        orc_collide_cell(a, tau, Fex, Fey, F->alpha, b);
+        orc_collide_cell(a, orc_tau_eff(a, tau, F), Fex, Fey, F->alpha, b);
         for (int l = 0; l < Q; ++l) s[l * plane + (size_t)y * wx + x] = b[l];
       }
     orc_stream(wx, wy, s, f);
@@ -322,7 +375,7 @@ void orc_init(int nx, int ny, const double *rho, const double *ux,
 
 /* Moments of the state f(., n): rho, bare momentum j, and the EDM velocity
  * u_phys = (j + F/2)/rho with F = F_ext - alpha j.  Any output may be NULL. */
-int orc_moments(int nx, int ny, const orc_force_t *F, const double *f,
+int orc_moments(int nx, int ny, const orc_model_t *F, const double *f,
                 double *rho, double *jx, double *jy, double *ux, double *uy) {
   size_t plane = (size_t)nx * ny;
   double *Fe = (double *)malloc(sizeof(double) * 2 * plane);
@@ -401,9 +454,11 @@ void orc_bdf2(size_t n, const double *An, const double *An1, const double *An2,
  * The compressibility term of enstrophy follows eq. (11): -(w^2/2) div u. */
 int orc_terms(int nx, int ny, double tau, const double *const *rho,
               const double *const *ux, const double *const *uy,
-              const double *Fx, const double *Fy, double *terms) {
+              const double *Fx, const double *Fy, const double *nu_field,
+              double *terms) {
   size_t N = (size_t)nx * ny;
-  const double nu = CS2 * (tau - 0.5);
+  const double nu0 = CS2 * (tau - 0.5);
+#define NU(i) (nu_field ? nu_field[i] : nu0)
   /* scratch fields */
   enum {
     DXUX, DYUX, DXUY, DYUY, W0, W1, W2, E0, E1, E2, OM0, OM1, OM2,
@@ -471,13 +526,13 @@ int orc_terms(int nx, int ny, double tau, const double *const *rho,
                  + F_(SXY)[i] * F_(DYUX)[i] /* i=x, j=y: S_xy d_y u_x */
                  + F_(SXY)[i] * F_(DXUY)[i] /* i=y, j=x: S_yx d_x u_y */
                  + F_(SYY)[i] * F_(DYUY)[i];
-    T_(4)[i] = -nu * r[i] * sdu;
+    T_(4)[i] = -NU(i) * r[i] * sdu;
   }
 
   /* RHS^{E,5} = d_j (nu rho u_i S_ij) */
   for (size_t i = 0; i < N; ++i) {
-    F_(TMPA)[i] = nu * r[i] * (u[i] * F_(SXX)[i] + v[i] * F_(SXY)[i]); /* j=x */
-    F_(TMPB)[i] = nu * r[i] * (u[i] * F_(SXY)[i] + v[i] * F_(SYY)[i]); /* j=y */
+    F_(TMPA)[i] = NU(i) * r[i] * (u[i] * F_(SXX)[i] + v[i] * F_(SXY)[i]); /* j=x */
+    F_(TMPB)[i] = NU(i) * r[i] * (u[i] * F_(SXY)[i] + v[i] * F_(SYY)[i]); /* j=y */
   }
   orc_ddx(nx, ny, F_(TMPA), F_(TMPC));
   orc_ddy(nx, ny, F_(TMPB), F_(TMPD));
@@ -485,15 +540,15 @@ int orc_terms(int nx, int ny, double tau, const double *const *rho,
 
   /* H_i = (1/rho) d_j (nu rho S_ij) */
   for (size_t i = 0; i < N; ++i) {
-    F_(TMPA)[i] = nu * r[i] * F_(SXX)[i];
-    F_(TMPB)[i] = nu * r[i] * F_(SXY)[i];
+    F_(TMPA)[i] = NU(i) * r[i] * F_(SXX)[i];
+    F_(TMPB)[i] = NU(i) * r[i] * F_(SXY)[i];
   }
   orc_ddx(nx, ny, F_(TMPA), F_(TMPC));
   orc_ddy(nx, ny, F_(TMPB), F_(TMPD));
   for (size_t i = 0; i < N; ++i) F_(HX)[i] = (F_(TMPC)[i] + F_(TMPD)[i]) / r[i];
   for (size_t i = 0; i < N; ++i) {
-    F_(TMPA)[i] = nu * r[i] * F_(SXY)[i];
-    F_(TMPB)[i] = nu * r[i] * F_(SYY)[i];
+    F_(TMPA)[i] = NU(i) * r[i] * F_(SXY)[i];
+    F_(TMPB)[i] = NU(i) * r[i] * F_(SYY)[i];
   }
   orc_ddx(nx, ny, F_(TMPA), F_(TMPC));
   orc_ddy(nx, ny, F_(TMPB), F_(TMPD));
@@ -541,6 +596,7 @@ int orc_terms(int nx, int ny, double tau, const double *const *rho,
 
 #undef F_
 #undef T_
+#undef NU
   free(s);
   return 0;
 }
@@ -716,8 +772,10 @@ int orc_distributions(int nx, int ny, const double *terms, const double *ux,
 /* ------------------------------------------------------------------------ */
 
 /* Term fields at time n from the pre-collision populations at n, n-1, n-2
- * (f_n, f_n1, f_n2), using u_phys and F = F_ext - alpha j at each level. */
-int orc_terms_from_populations(int nx, int ny, double tau, const orc_force_t *F,
+ * (f_n, f_n1, f_n2), using u_phys and F = F_ext - alpha j at each level and,
+ * for a variable-viscosity collision, the local viscosity of the state at
+ * time n. */
+int orc_terms_from_populations(int nx, int ny, double tau, const orc_model_t *F,
                                const double *f_n, const double *f_n1,
                                const double *f_n2, double *terms) {
   size_t N = (size_t)nx * ny;
@@ -742,9 +800,19 @@ int orc_terms_from_populations(int nx, int ny, double tau, const orc_force_t *F,
       }
     }
   }
+  double *nu = NULL;
+  if (F->collision != 0) {
+    nu = (double *)malloc(sizeof(double) * N);
+    if (!nu) {
+      free(buf);
+      return -1;
+    }
+    orc_nu_field(nx, ny, tau, F, f_n, nu);
+  }
   int rc = orc_terms(nx, ny, tau, (const double *const *)rho,
                      (const double *const *)ux, (const double *const *)uy, Fx,
-                     Fy, terms);
+                     Fy, nu, terms);
+  free(nu);
   free(buf);
   return rc;
 }
@@ -754,7 +822,7 @@ int orc_terms_from_populations(int nx, int ny, double tau, const orc_force_t *F,
  *   out[3] = <E> = mean rho |u|^2 / 2,  out[4] = <Omega> = mean w^2 / 2,
  *   out[5] = <u . F>,  out[6] = <eps> = mean nu rho S_ij d_j u_i
  * with u = u_phys and the eq. (18) derivatives. */
-int orc_global(int nx, int ny, double tau, const orc_force_t *F,
+int orc_global(int nx, int ny, double tau, const orc_model_t *F,
                const double *f, double *out) {
   size_t N = (size_t)nx * ny;
   double *b = (double *)malloc(sizeof(double) * N * 11);
@@ -773,7 +841,8 @@ int orc_global(int nx, int ny, double tau, const orc_force_t *F,
   orc_ddy(nx, ny, u, dyu);
   orc_ddx(nx, ny, v, dxv);
   orc_ddy(nx, ny, v, dyv);
-  double nu = CS2 * (tau - 0.5);
+  double *nu = b + 9 * N; /* local viscosity of the state */
+  orc_nu_field(nx, ny, tau, F, f, nu);
   double s[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
@@ -787,7 +856,7 @@ int orc_global(int nx, int ny, double tau, const orc_force_t *F,
       s[3] += 0.5 * rho[c] * (u[c] * u[c] + v[c] * v[c]);
       s[4] += 0.5 * w * w;
       s[5] += u[c] * Fx + v[c] * Fy;
-      s[6] += nu * rho[c] *
+      s[6] += nu[c] * rho[c] *
               (sxx * dxu[c] + sxy * dyu[c] + sxy * dxv[c] + syy * dyv[c]);
     }
   out[0] = s[0];
@@ -803,7 +872,7 @@ int orc_global(int nx, int ny, double tau, const orc_force_t *F,
  * n in [n0, n1] of the L x L box average (origin (bx, by)) of RHS^{E,4}(n),
  * the local dissipation term of eq. (8), evaluated on the state f(., n).
  * Runs the forward model from f0 (copied, not modified) for n1 steps. */
-int orc_objective(int nx, int ny, double tau, const orc_force_t *F,
+int orc_objective(int nx, int ny, double tau, const orc_model_t *F,
                   const double *f0, int n0, int n1, int bx, int by, int L,
                   double *J) {
   size_t N = (size_t)nx * ny;

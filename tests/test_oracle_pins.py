@@ -643,3 +643,98 @@ def test_paper_forcing_step_conserves_mass_and_adds_the_total_force(orc):
     assert abs(gain_x - (Fx - 2e-3 * jx0).sum()) < 1e-13
     assert abs(gain_y - (Fy - 2e-3 * jy0).sum()) < 1e-13
     assert abs(gain_x + 2e-3 * jx0.sum()) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Variable-viscosity collisions (Sec. 1: Smagorinsky, eq. 7)
+# --------------------------------------------------------------------------
+
+def _pi_neq(orc, f9):
+    cx, cy, _ = orc.lattice()
+    rho = f9.sum()
+    u = np.array([(cx * f9).sum(), (cy * f9).sum()]) / rho
+    d = f9 - orc.feq(rho, u[0], u[1])
+    C = np.stack([cx, cy], 1).astype(float)
+    return rho, np.einsum("la,lb,l->ab", C, C, d)
+
+
+def test_collision_models_keep_tau0_at_equilibrium(orc):
+    """No non-equilibrium stress, no eddy viscosity: tau_eff = tau0."""
+    f9 = orc.feq(1.02, 0.03, -0.05)
+    for coll in (1, 2):
+        m = orc.Force(0, collision=coll, Cs=0.1)
+        assert orc.tau_eff(f9, 0.53, m) == 0.53
+
+
+def test_smagorinsky_tau_solves_its_implicit_definition(orc):
+    """nu_t = C sqrt(S:S) with S = -Pi^neq / (2 rho cs^2 tau_eff) evaluated at
+    the returned tau_eff itself (numpy tensor algebra on the populations)."""
+    rng = np.random.default_rng(7)
+    for k in range(5):
+        f9 = orc.feq(1.0 + 0.02 * rng.normal(), 0.05 * rng.normal(), 0.05 * rng.normal())
+        f9 = f9 * (1.0 + 0.02 * rng.normal(size=9))
+        tau0, C = 0.51 + 0.1 * k, 0.02 + 0.05 * k
+        tau = orc.tau_eff(f9, tau0, orc.Force(0, collision=1, Cs=C))
+        rho, Pi = _pi_neq(orc, f9)
+        S = -Pi / (2.0 * rho / 3.0 * tau)
+        assert tau > tau0
+        assert abs((tau - tau0) / 3.0 - C * np.sqrt(np.sum(S * S))) < 1e-14
+
+
+def test_eq7_viscosity_from_strain_traces(orc):
+    """Eq. (7): nu_t = -(cs^2/3) tau0^2 Tr(S^3) / Tr(S^2), S from Pi^neq at
+    tau0; traces by numpy matrix powers.  A traceless 2D strain has
+    Tr(S^3) = 0 (eigenvalues +-s), so a pure shear keeps tau0."""
+    rng = np.random.default_rng(8)
+    for k in range(5):
+        f9 = orc.feq(1.0 + 0.02 * rng.normal(), 0.05 * rng.normal(), 0.05 * rng.normal())
+        f9 = f9 * (1.0 + 0.03 * rng.normal(size=9))
+        tau0 = 0.52 + 0.05 * k
+        tau = orc.tau_eff(f9, tau0, orc.Force(0, collision=2))
+        rho, Pi = _pi_neq(orc, f9)
+        S = -Pi / (2.0 * rho / 3.0 * tau0)
+        nu_t = -(1.0 / 9.0) * tau0 ** 2 * np.trace(S @ S @ S) / np.trace(S @ S)
+        assert abs((tau - tau0) / 3.0 - nu_t) < 1e-15 + 1e-12 * abs(nu_t)
+    # pure shear: Pi^neq with only the xy component (add c_x c_y-odd mode)
+    f9 = orc.feq(1.0, 0.0, 0.0)
+    f9[[5, 7]] += 1e-4
+    f9[[6, 8]] -= 1e-4
+    assert orc.tau_eff(f9, 0.55, orc.Force(0, collision=2)) == pytest.approx(0.55, abs=1e-15)
+
+
+def test_chapman_enskog_strain_from_nonequilibrium_stress(orc):
+    """The relation the models use, Pi^neq = -2 rho cs^2 tau S: on a decaying
+    BGK shear wave u_x = U sin(2 pi y / N) the measured Pi^neq_xy matches
+    -rho cs^2 tau d_y u_x to about 1% (Chapman-Enskog, O(k^2) corrections)."""
+    N, U, tau = 64, 0.01, 0.8
+    y = np.arange(N)
+    ux = np.tile((U * np.sin(2 * np.pi * y / N))[:, None], (1, 4))
+    f = orc.run(orc.init(np.ones((N, 4)), ux, np.zeros((N, 4))), 200, tau)
+    m = orc.moments(f)
+    for yy in (5, 16, 40):
+        _, Pi = _pi_neq(orc, f[:, yy, 0])
+        k = 2 * np.pi / N
+        amp = m["jx"][:, 0].max()  # current wave amplitude (rho ~ 1)
+        dudy = amp * k * np.cos(k * yy)
+        want = -(1.0 / 3.0) * tau * dudy
+        assert abs(Pi[0, 1] - want) < 0.01 * abs(amp * k / 3.0 * tau)
+
+
+def test_terms_take_a_local_viscosity(orc):
+    """A constant viscosity field reproduces the tau form; RHS^{E,4} is
+    pointwise proportional to the local viscosity."""
+    n = 16
+    rng = np.random.default_rng(4)
+    rho3 = [1.0 + 0.01 * li.smooth_fields(n, n, 20 + k) for k in range(3)]
+    ux3 = [li.smooth_fields(n, n, 30 + k) for k in range(3)]
+    uy3 = [li.smooth_fields(n, n, 40 + k) for k in range(3)]
+    Fx, Fy = np.zeros((n, n)), np.zeros((n, n))
+    tau = 0.6
+    T0 = orc.terms(tau, rho3, ux3, uy3, Fx, Fy)
+    Tc = orc.terms(tau, rho3, ux3, uy3, Fx, Fy, nu=np.full((n, n), (tau - 0.5) / 3.0))
+    np.testing.assert_array_equal(T0, Tc)
+    nu = 0.01 + 0.02 * rng.random((n, n))
+    Tv = orc.terms(tau, rho3, ux3, uy3, Fx, Fy, nu=nu)
+    T1 = orc.terms(tau, rho3, ux3, uy3, Fx, Fy, nu=np.ones((n, n)))
+    np.testing.assert_allclose(Tv[4], nu * T1[4], rtol=1e-14, atol=1e-30)
+    np.testing.assert_array_equal(Tv[[0, 1, 2, 3, 6, 7, 8, 9]], T0[[0, 1, 2, 3, 6, 7, 8, 9]])
