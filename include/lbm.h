@@ -87,6 +87,15 @@ typedef struct lbm_member_cfg {
   double alpha;     /* linear drag coefficient on the bare momentum */
   double phase;     /* phi of eq. (14) (force_kind 2) */
   double FR0;       /* F^R_0 of eq. (16) (force_kind 2) */
+  int collision;    /* 0: BGK with tau (eq. 1); variable viscosity (Sec. 1)
+                       with a local relaxation time from the non-equilibrium
+                       stress Pi^neq = -2 rho cs^2 tau S of the pre-collision
+                       populations: 1: Smagorinsky nu_t = Cs sqrt(S:S)
+                       (S at the local tau itself; closed-form root);
+                       2: the turbulent viscosity of eq. (7) (S at tau).
+                       The diagnostic then uses the local viscosity of each
+                       cell at time n; no adjoint */
+  double Cs;        /* Smagorinsky constant (collision 1; dx = 1) */
 } lbm_member_cfg;
 
 typedef struct lbm_config {
@@ -329,7 +338,8 @@ int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx,
  * nx, ny: grid, 1 <= nx * ny <= LBM_STATIC_MAX_CELLS (larger grids return
  *      LBM_ERR_ARG with a message; use lbm_global_balance for them).
  * m:   host pointer to the member parameters (tau, force_kind, kf, F0,
- *      alpha are used; rho0 is not).
+ *      alpha are used; rho0 is not); force kinds 0 and 1 with the BGK
+ *      collision only (others return LBM_ERR_ARG).
  * out: host pointer to LBM_NGLOBAL doubles; the call synchronises
  *      cuda_stream (NULL = legacy default stream) before returning.
  * Calls no cudaMalloc or cudaFree.  The first call on a device looks up the

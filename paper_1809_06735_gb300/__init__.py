@@ -42,7 +42,8 @@ class _MemberCfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("force_kind", ctypes.c_int), ("kf", ctypes.c_int),
                 ("F0", ctypes.c_double), ("alpha", ctypes.c_double),
-                ("phase", ctypes.c_double), ("FR0", ctypes.c_double)]
+                ("phase", ctypes.c_double), ("FR0", ctypes.c_double),
+                ("collision", ctypes.c_int), ("Cs", ctypes.c_double)]
 
 
 class _Config(ctypes.Structure):
@@ -104,7 +105,8 @@ class Member:
     an optional force -- kind 1: Kolmogorov F0 (sin(2 pi kf y/ny),
     sin(2 pi kf x/nx)); kind 2: the paper's shell force of eqs. (14), (15)
     (amplitude F0, phase) with the large-scale damping of eq. (16) (FR0) --
-    and linear drag alpha on the bare momentum."""
+    linear drag alpha on the bare momentum, and the collision: 0 BGK, 1
+    Smagorinsky (constant Cs), 2 the turbulent viscosity of eq. (7)."""
     nx: int
     ny: int
     tau: float
@@ -115,10 +117,12 @@ class Member:
     alpha: float = 0.0
     phase: float = 0.0
     FR0: float = 0.0
+    collision: int = 0
+    Cs: float = 0.0
 
     def c(self) -> _MemberCfg:
         return _MemberCfg(self.nx, self.ny, self.tau, self.rho0, self.force_kind, self.kf,
-                          self.F0, self.alpha, self.phase, self.FR0)
+                          self.F0, self.alpha, self.phase, self.FR0, self.collision, self.Cs)
 
 
 def _ptr(t) -> Optional[int]:

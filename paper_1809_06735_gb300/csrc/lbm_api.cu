@@ -34,6 +34,7 @@ struct Layout {
   size_t members, tiles, status;
   std::vector<size_t> pop0, pop1, fx, fy, fx64, fy64, snap;
   std::vector<size_t> ft, ft64, trig, trig64, damp, damp_f, damp_ring, proj, drows, pcount;
+  std::vector<size_t> nu_ring;  // variable viscosity: local viscosity per snapshot slot
   size_t scratch, partials, jpart, jobs, stats, Ls, out7, origins;
   size_t edges, hist, mach;  // distributions: bin edges, histograms, Ma_V statistics
   int diag_slots;          // members per batched diagnostic launch
@@ -139,6 +140,10 @@ int check_config(const lbm_config *cfg, std::string &err) {
     if (c.force_kind < 0 || c.force_kind > 2) {
       snprintf(buf, sizeof buf, "member %d: force_kind must be 0, 1 or 2", m); err = buf; return LBM_ERR_ARG;
     }
+    if (c.collision < 0 || c.collision > 2 || !std::isfinite(c.Cs) || c.Cs < 0.0) {
+      snprintf(buf, sizeof buf, "member %d: collision must be 0, 1 or 2 with Cs >= 0", m);
+      err = buf; return LBM_ERR_ARG;
+    }
     if (!std::isfinite(c.F0) || !std::isfinite(c.alpha) ||
         (c.force_kind == 2 && (!std::isfinite(c.phase) || !std::isfinite(c.FR0)))) {
       snprintf(buf, sizeof buf, "member %d: force parameters not finite", m); err = buf; return LBM_ERR_ARG;
@@ -188,6 +193,7 @@ Layout make_layout(const lbm_config *cfg) {
     L.proj.push_back(take(k2 ? 8 * lbm::kDamp * pctas : 0));
     L.drows.push_back(take(k2 && cfg->precision == 32 ? 4 * 6 * (size_t)c.ny : 0));
     L.pcount.push_back(take(k2 ? sizeof(unsigned) : 0));
+    L.nu_ring.push_back(take(c.collision != 0 ? es * 3 * N : 0));
     L.Nmax = std::max(L.Nmax, N);
   }
   L.scratch_fields = lbm::kDiagFields;
@@ -238,6 +244,7 @@ struct lbm_handle {
   cudaEvent_t ev_ready = nullptr, ev_diag_done = nullptr;
   bool diag_pending = false;
   bool has_kind2 = false;  // some member uses the paper's forcing (kind 2)
+  bool has_vv = false;     // some member has a variable-viscosity collision
   int cur = 0;
   long long t = 0;
   long long ring_time[3] = {-1, -1, -1};
@@ -558,6 +565,14 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
     M.fy_tab64 = reinterpret_cast<double *>(ws_at(h, lay.fy64[m]));
     M.snap = reinterpret_cast<double *>(ws_at(h, lay.snap[m]));
     M.status = reinterpret_cast<int *>(ws_at(h, lay.status)) + m;
+    M.collision = c.collision;
+    M.Cs = c.Cs;
+    M.Cs_f = (float)c.Cs;
+    M.tau_f = (float)c.tau;
+    if (c.collision != 0) {
+      M.nu_ring = ws_at(h, lay.nu_ring[m]);
+      h->has_vv = true;
+    }
     if (c.force_kind == 2) {
       M.FR0 = c.FR0;
       M.ft_tab = ws_at(h, lay.ft[m]);
@@ -621,7 +636,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
   if (e != cudaSuccess)
     return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
   h->cur = cfg->storage == 1 ? 2 : 0;
-  h->lc.paper_force = h->has_kind2 ? 1 : 0;
+  h->lc.paper_force = h->has_kind2 || h->has_vv ? 1 : 0;
   rc = build_tiles(h);
   if (rc == LBM_OK) rc = autotune(h);
   if (rc != LBM_OK) {
@@ -926,6 +941,13 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
     J.max_boxes = maxb[i];
     J.qblocks = lbm::diag_query_blocks(maxb[i], origins != nullptr);
     J.force_kind = hm.force_kind;
+    if (hm.collision != 0) {  // local viscosity recorded with the snapshot at n
+      const size_t N = (size_t)hm.nx * hm.ny;
+      if (h->precision == 32)
+        J.nu_cell_f = static_cast<const float *>(hm.nu_ring) + (size_t)(t % 3) * N;
+      else
+        J.nu_cell_d = static_cast<const double *>(hm.nu_ring) + (size_t)(t % 3) * N;
+    }
     if (hm.force_kind == 2) {  // damping coefficients recorded with each snapshot
       J.ft64 = hm.ft_tab64;
       J.trig64 = hm.trig64;
@@ -1088,6 +1110,8 @@ int lbm_adjoint_step(lbm_handle *h, int member, const double *f_n, const double 
   if (c.force_kind == 2)
     return fail(h, LBM_ERR_ARG, "the adjoint supports force kinds 0 and 1 (the damping of "
                                 "kind 2 couples every cell)");
+  if (c.collision != 0)
+    return fail(h, LBM_ERR_ARG, "the adjoint supports the BGK collision only");
   if (!f_n || !lambda_out) return fail(h, LBM_ERR_ARG, "f_n and lambda_out must not be NULL");
   if (lambda_in == lambda_out) return fail(h, LBM_ERR_ARG, "lambda_out may not alias lambda_in");
   if (!std::isfinite(obj_weight)) return fail(h, LBM_ERR_ARG, "obj_weight not finite");
@@ -1106,8 +1130,8 @@ int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx, i
   int rc = check_member(h, member);
   if (rc) return rc;
   const lbm_member_cfg &c = h->mcfg[member];
-  if (c.force_kind == 2)
-    return fail(h, LBM_ERR_ARG, "the objective supports force kinds 0 and 1");
+  if (c.force_kind == 2 || c.collision != 0)
+    return fail(h, LBM_ERR_ARG, "the objective supports force kinds 0 and 1 with BGK");
   if (!acc) return fail(h, LBM_ERR_ARG, "acc is NULL");
   if (L < 1 || L > c.nx || L > c.ny || bx < 0 || bx >= c.nx || by < 0 || by >= c.ny)
     return fail(h, LBM_ERR_ARG, "objective box outside the grid");

@@ -60,6 +60,7 @@ struct Grid {
   const double *fxt, *fyt;  // F_ext,x(y), F_ext,y(x)
   // force kind 2: shell force [2][N], trig tables, damping coefficients
   const double *ft64, *trig64, *damp;
+  const double *nu_field;  // local viscosity per cell (variable viscosity), else NULL
 };
 
 // External force (drag excluded) at cell (x, y): the separable tables, or
@@ -192,6 +193,7 @@ __device__ __forceinline__ Grid job_grid(const DiagJob &J) {
   g.ft64 = nullptr;  // kind 2 is handled per level in k_prep
   g.trig64 = nullptr;
   g.damp = nullptr;
+  g.nu_field = nullptr;  // the job's own per-cell viscosity (k_grad)
   return g;
 }
 
@@ -452,8 +454,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_grad(const Diag
     const T dxv = Dx(V, nb), dyv = Dy(V, nb);
     const T u = U[c], v = V[c], r = fld<T>(base, R0, N)[c];
     const T sxx = T(2) * dxu, sxy = dyu + dxv, syy = T(2) * dyv;  // S_ij = d_j u_i + d_i u_j
-    T nu;
-    if constexpr (sizeof(T) == 4)
+    T nu;  // the local viscosity at time n (variable-viscosity collisions)
+    if (J.nu_cell_d)
+      nu = (T)J.nu_cell_d[c];
+    else if (J.nu_cell_f)
+      nu = (T)J.nu_cell_f[c];
+    else if constexpr (sizeof(T) == 4)
       nu = J.nu_f;
     else
       nu = g.nu;
@@ -635,7 +641,8 @@ __global__ void k_global(Grid g, const double *snap, const double *ux, const dou
     acc[3] += 0.5 * r * (u * u + v * v);
     acc[4] += 0.5 * w * w;
     acc[5] += u * Fx + v * Fy;
-    acc[6] += g.nu * r * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
+    const double nu = g.nu_field ? g.nu_field[c] : g.nu;
+    acc[6] += nu * r * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
   }
   block_sum_store<7>(acc, partials + (size_t)blockIdx.x * 7);
 }
@@ -1122,6 +1129,7 @@ Grid grid_of(const Member &hm) {
   g.ft64 = k2 ? hm.ft_tab64 : nullptr;
   g.trig64 = k2 ? hm.trig64 : nullptr;
   g.damp = k2 ? hm.damp : nullptr;
+  g.nu_field = nullptr;
   return g;
 }
 
@@ -1184,9 +1192,12 @@ cudaError_t diag_moments(const Member &hm, const double *snap3, double *rho, dou
 
 cudaError_t diag_global(const Member &hm, const double *snap3, const DiagScratch &sc,
                         double *out7_dev, cudaStream_t s) {
-  const Grid g = grid_of(hm);
+  Grid g = grid_of(hm);
   const size_t N = (size_t)hm.nx * hm.ny;
-  double *U = sc.f + (size_t)kSnapSlots * N, *V = sc.f + (size_t)(kSnapSlots + 1) * N;
+  // snap3 holds (rho, j_x, j_y) and, with a variable-viscosity collision,
+  // the local viscosity as a fourth field
+  if (hm.collision != 0) g.nu_field = snap3 + 3 * N;
+  double *U = sc.f + (size_t)(kSnapSlots + 1) * N, *V = sc.f + (size_t)(kSnapSlots + 2) * N;
   dim3 b(32, 8);
   k_moments<<<cells_grid(g, b), b, 0, s>>>(g, snap3, N, nullptr, U, V);
   int nblocks = (int)((N + 255) / 256);

@@ -64,7 +64,32 @@ struct Member {
   double *proj_part;     // projection CTA partials [CTAs][kDamp]
   float *damp_rows;      // FP32 storage: per-row damping factors [ny][6]
   unsigned *proj_count;  // CTAs of the projection done (zero between launches)
+  // variable-viscosity collision (1: Smagorinsky, 2: eq. (7)); 0: BGK
+  int collision;
+  float Cs_f, tau_f;     // float copies of Cs and tau
+  double Cs;
+  void *nu_ring;         // local viscosity at each snapshot slot [3][N]
+                         // (storage precision), collision != 0
 };
+
+// Local relaxation time of a cell from its non-equilibrium stress
+// Pi^neq = sum c c (f - f_eq), f_eq of eq. (2) at u = j / rho, through the
+// Chapman-Enskog relation Pi^neq = -2 rho cs^2 tau S:
+//   1: Smagorinsky nu_t = Cs sqrt(S:S) with S at the local tau itself, the
+//      positive root tau = (tau0 + sqrt(tau0^2 + 18 Cs |Pi| / rho)) / 2;
+//   2: eq. (7), nu_t = -(cs^2 / 3) tau0^2 Tr(S^3) / Tr(S^2) with S at tau0,
+//      tau = tau0 + tau0 Tr(Pi^3) / (2 rho Tr(Pi^2)).
+// pxx, pxy, pyy: the components of Pi^neq; rho the density.
+template <typename T>
+__host__ __device__ inline T tau_from_stress(T pxx, T pxy, T pyy, T rho, T tau0, int coll,
+                                             T Cs) {
+  const T tr2 = pxx * pxx + T(2) * pxy * pxy + pyy * pyy;
+  if (coll == 1) return T(0.5) * (tau0 + sqrt(tau0 * tau0 + T(18) * Cs * sqrt(tr2) / rho));
+  if (tr2 == T(0)) return tau0;
+  const T a2xx = pxx * pxx + pxy * pxy, a2xy = pxy * (pxx + pyy), a2yy = pxy * pxy + pyy * pyy;
+  const T tr3 = a2xx * pxx + T(2) * a2xy * pxy + a2yy * pyy;
+  return tau0 + tau0 * tr3 / (T(2) * rho * tr2);
+}
 
 // Damping coefficients of eq. (16): for component c (0: x, 1: y) and the
 // representatives m of the 6 pairs +-k, 1 <= |k| <= 2, in the order (1,0),
@@ -115,7 +140,8 @@ struct LaunchCfg {
   int block_warps_y;  // warps per CTA (rows per CTA pass)
   int rows_per_warp;  // rows each warp processes per tile
   int grid_ctas;      // 0: one CTA per tile; else persistent grid size
-  int paper_force;    // 1: some member has force kind 2 (kernel variant)
+  int paper_force;    // 1: some member has force kind 2 or a variable-viscosity
+                      // collision (the extended kernel variant)
 };
 
 cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, int ntiles,
@@ -185,6 +211,8 @@ struct DiagJob {
   int force_kind;              // 2: external force = ft64 + damping from dc[level]
   const double *ft64, *trig64; // force kind 2: shell force [2][N], trig tables
   const double *dc[3];         // force kind 2: damping coefficients at n, n-1, n-2
+  const float *nu_cell_f;      // variable viscosity: local viscosity at n (FP32
+  const double *nu_cell_d;     // or FP64 storage), else both NULL
   int qblocks;                 // query CTAs per (size, balance):
                                // diag_query_blocks(max_boxes, origin list?)
 };

@@ -180,7 +180,7 @@ extern "C" int lbm_global_balance_static(const double *f, int nx, int ny,
   if ((long long)nx * ny > (long long)LBM_STATIC_MAX_CELLS)
     return fail_static(LBM_ERR_ARG,
                        "grid larger than LBM_STATIC_MAX_CELLS cells: use lbm_global_balance");
-  if (!(m->tau > 0.5) || (m->force_kind != 0 && m->force_kind != 1) || !std::isfinite(m->F0) ||
+  if (!(m->tau > 0.5) || (m->force_kind != 0 && m->force_kind != 1) || m->collision != 0 || !std::isfinite(m->F0) ||
       !std::isfinite(m->alpha))
     return fail_static(LBM_ERR_ARG, "invalid member parameters");
   double *scratch = nullptr;

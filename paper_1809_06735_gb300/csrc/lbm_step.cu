@@ -36,14 +36,66 @@ namespace lbm {
 // EDM term F_l = f_eq_l(rho, u + du) - f_eq_l(rho, u) written as
 // t_l rho [3 c.du + 4.5 c.du (2 c.u + c.du) - 1.5 du.(2u + du)], du = F/rho,
 // F = F_ext - alpha j.  Post-collision g_l - omega (g_l - g_eq_l) + F_l.
+// Local relaxation time of the variable-viscosity collisions in deviation
+// form: Pi^neq = sum c c g - drho cs^2 I - rho u u (moments as collide_f32
+// forms them, so the snapshot's viscosity is the one the step used).
+__device__ __forceinline__ float local_tau_f32(const float g[kQ], float drho, float rho, float ux,
+                                               float uy, float tau0, int coll, float Cs) {
+  const float d4 = (g[5] + g[6]) + (g[7] + g[8]);
+  const float pxx = (g[1] + g[3]) + d4 - drho * (1.0f / 3.0f) - rho * ux * ux;
+  const float pyy = (g[2] + g[4]) + d4 - drho * (1.0f / 3.0f) - rho * uy * uy;
+  const float pxy = (g[5] - g[6]) + (g[7] - g[8]) - rho * ux * uy;
+  return tau_from_stress<float>(pxx, pxy, pyy, rho, tau0, coll, Cs);
+}
+__device__ __forceinline__ void moments_f32(const float g[kQ], float rho0, float &drho,
+                                            float &rho, float &jx, float &jy, float &ir,
+                                            float &ux, float &uy) {
+  drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+  jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+  rho = rho0 + drho;
+  ir = 1.0f / rho;
+  ux = jx * ir;
+  uy = jy * ir;
+}
+// FP64: Pi^neq = sum c c f - rho cs^2 I - rho u u.
+__device__ __forceinline__ double local_tau_f64(const double f[kQ], double rho, double ux,
+                                                double uy, double tau0, int coll, double Cs) {
+  double sxx = 0.0, sxy = 0.0, syy = 0.0;
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) {
+    sxx += cx_of(l) * cx_of(l) * f[l];
+    sxy += cx_of(l) * cy_of(l) * f[l];
+    syy += cy_of(l) * cy_of(l) * f[l];
+  }
+  return tau_from_stress<double>(sxx - rho / 3.0 - rho * ux * ux, sxy - rho * ux * uy,
+                                 syy - rho / 3.0 - rho * uy * uy, rho, tau0, coll, Cs);
+}
+__device__ __forceinline__ void moments_f64(const double f[kQ], double &rho, double &ux,
+                                            double &uy) {
+  double r = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) {
+    r += f[l];
+    jx += cx_of(l) * f[l];
+    jy += cy_of(l) * f[l];
+  }
+  rho = r;
+  const double ir = 1.0 / r;
+  ux = jx * ir;
+  uy = jy * ir;
+}
+
+// With VV (variable viscosity, collision != 0) omega = 1 / local_tau_f32.
+template <bool VV = false>
 __device__ __forceinline__ void collide_f32(float g[kQ], float rho0, float om, float Fex,
-                                            float Fey, float alpha) {
-  const float drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-  const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-  const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-  const float rho = rho0 + drho;
-  const float ir = 1.0f / rho;
-  const float ux = jx * ir, uy = jy * ir;
+                                            float Fey, float alpha, int coll = 0,
+                                            float tau0 = 0.f, float Cs = 0.f) {
+  float drho, rho, jx, jy, ir, ux, uy;
+  moments_f32(g, rho0, drho, rho, jx, jy, ir, ux, uy);
+  if constexpr (VV) {
+    if (coll != 0) om = 1.0f / local_tau_f32(g, drho, rho, ux, uy, tau0, coll, Cs);
+  }
   const float Fx = Fex - alpha * jx, Fy = Fey - alpha * jy;
   const float dux = Fx * ir, duy = Fy * ir;
   const float usq = ux * ux + uy * uy;
@@ -61,9 +113,11 @@ __device__ __forceinline__ void collide_f32(float g[kQ], float rho0, float om, f
   }
 }
 
-// FP64 plain form on the full populations f_l.
+// FP64 plain form on the full populations f_l; coll != 0: omega from the
+// local relaxation time (Pi^neq = sum c c f - rho cs^2 I - rho u u).
 __device__ __forceinline__ void collide_f64(double f[kQ], double om, double Fex, double Fey,
-                                            double alpha) {
+                                            double alpha, int coll = 0, double tau0 = 0.0,
+                                            double Cs = 0.0) {
   double rho = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
@@ -73,6 +127,7 @@ __device__ __forceinline__ void collide_f64(double f[kQ], double om, double Fex,
   }
   const double ir = 1.0 / rho;
   const double ux = jx * ir, uy = jy * ir;
+  if (coll != 0) om = 1.0 / local_tau_f64(f, rho, ux, uy, tau0, coll, Cs);
   const double Fx = Fex - alpha * jx, Fy = Fey - alpha * jy;
   const double dux = Fx * ir, duy = Fy * ir;
   const double usq = ux * ux + uy * uy;
@@ -224,7 +279,10 @@ __global__ void __launch_bounds__(256, PF ? 3 : 1) k_step_f32_vec(const Member *
           float g[kQ];
 #pragma unroll
           for (int l = 0; l < kQ; ++l) g[l] = v[l][c];
-          collide_f32(g, rho0, om, fxc[c], fyc[c], alpha);
+          if constexpr (PF)
+            collide_f32<true>(g, rho0, om, fxc[c], fyc[c], alpha, M.collision, M.tau_f, M.Cs_f);
+          else
+            collide_f32(g, rho0, om, fxc[c], fyc[c], alpha);
 #pragma unroll
           for (int l = 0; l < kQ; ++l) v[l][c] = g[l];
         }
@@ -346,9 +404,9 @@ __global__ void k_step_scalar(const Member *__restrict__ members, int member, in
 #pragma unroll
   for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
   if constexpr (sizeof(T) == 4) {
-    collide_f32(f, M.rho0_f, M.omega_f, fx, fy, M.alpha_f);
+    collide_f32<true>(f, M.rho0_f, M.omega_f, fx, fy, M.alpha_f, M.collision, M.tau_f, M.Cs_f);
   } else {
-    collide_f64(f, M.omega, fx, fy, M.alpha);
+    collide_f64(f, M.omega, fx, fy, M.alpha, M.collision, M.tau, M.Cs);
   }
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
@@ -461,7 +519,8 @@ __device__ __forceinline__ double csum(const float *v, const int *sign, int n) {
   return (double)s + (double)c;
 }
 
-// (rho, j_x, j_y) of the pre-collision state, FP64, into d[3][ny*nx].
+// (rho, j_x, j_y) of the pre-collision state, FP64, into d[3][ny*nx]; with a
+// variable-viscosity collision also the local viscosity as d[3][ny*nx].
 template <typename T>
 __global__ void k_snapshot(const Member *__restrict__ members, int member, int state,
                            double *d) {
@@ -498,6 +557,19 @@ __global__ void k_snapshot(const Member *__restrict__ members, int member, int s
   d[c] = r;
   d[N + c] = jx;
   d[2 * N + c] = jy;
+  if (M.collision != 0) {  // local viscosity as a fourth field
+    double t;
+    if constexpr (sizeof(T) == 4) {
+      float drho, rho, jxf, jyf, ir, ux, uy;
+      moments_f32(f, M.rho0_f, drho, rho, jxf, jyf, ir, ux, uy);
+      t = (double)local_tau_f32(f, drho, rho, ux, uy, M.tau_f, M.collision, M.Cs_f);
+    } else {
+      double rho, ux, uy;
+      moments_f64(f, rho, ux, uy);
+      t = local_tau_f64(f, rho, ux, uy, M.tau, M.collision, M.Cs);
+    }
+    d[3 * N + c] = (t - 0.5) / 3.0;
+  }
 }
 
 // Compensated FP32 sum of FP32 values as the unevaluated pair (s, c): the
@@ -544,6 +616,12 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
       d[(size_t)(2 * q) * N + c] = hi[q];
       d[(size_t)(2 * q + 1) * N + c] = lo[q];
     }
+    if (M.collision != 0) {  // the local viscosity the step from this state uses
+      float drho, rho, jx, jy, ir, ux, uy;
+      moments_f32(f, M.rho0_f, drho, rho, jx, jy, ir, ux, uy);
+      const float t = local_tau_f32(f, drho, rho, ux, uy, M.tau_f, M.collision, M.Cs_f);
+      static_cast<float *>(M.nu_ring)[(size_t)slot * N + c] = (t - 0.5f) * (1.0f / 3.0f);
+    }
   } else {
     double r = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
@@ -556,6 +634,12 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
     d[c] = r;
     d[N + c] = jx;
     d[2 * N + c] = jy;
+    if (M.collision != 0) {
+      double rho, ux, uy;
+      moments_f64(f, rho, ux, uy);
+      const double t = local_tau_f64(f, rho, ux, uy, M.tau, M.collision, M.Cs);
+      static_cast<double *>(M.nu_ring)[(size_t)slot * N + c] = (t - 0.5) / 3.0;
+    }
   }
 }
 

@@ -59,6 +59,12 @@ def test_workspace_size_validates(P):
         P.workspace_size(ok, 16)
     with pytest.raises(P.LBMError):
         P.workspace_size([P.Member(8, 8, 0.6, force_kind=3)], 32)
+    with pytest.raises(P.LBMError):
+        P.workspace_size([P.Member(8, 8, 0.6, collision=3)], 32)
+    with pytest.raises(P.LBMError):
+        P.workspace_size([P.Member(8, 8, 0.6, collision=1, Cs=-0.1)], 32)
+    with pytest.raises(P.LBMError):
+        P.workspace_size([P.Member(8, 8, 0.6, force_kind=2, FR0=float("nan"))], 32)
 
 
 def test_workspace_scales_with_grid(P):
