@@ -74,6 +74,11 @@ def _load():
             lib.orc_tau_eff.argtypes = [P, D, P]
             lib.orc_tau_eff.restype = D
             lib.orc_nu_field.argtypes = [I, I, D, P, P, P]
+            lib.orc_feq_entropic.argtypes = [D, D, D, P]
+            lib.orc_elbm_alpha.argtypes = [P, P]
+            lib.orc_elbm_alpha.restype = D
+            lib.orc_elbm_cell.argtypes = [P, D, D, D, D, P]
+            lib.orc_elbm_cell.restype = D
             lib.orc_terms.restype = I
             lib.orc_box_mean.argtypes = [I, I, P, I, I, I]
             lib.orc_box_mean.restype = D
@@ -117,7 +122,8 @@ class Force:
     wavenumber kf (in units of 2 pi / N); kind 2 = the paper's shell force of
     eqs. (14), (15) (F^T_0 = F0, phase) plus the damping of eq. (16)
     (F^R_0 = FR0); in every case drag alpha on the bare momentum.  Collision:
-    0 BGK, 1 Smagorinsky (constant Cs), 2 the turbulent viscosity of eq. (7)."""
+    0 BGK, 1 Smagorinsky (constant Cs), 2 the turbulent viscosity of eq. (7),
+    3 the entropic LBM."""
 
     def __init__(self, kind: int = 0, F0: float = 0.0, kf: int = 0, alpha: float = 0.0,
                  phase: float = 0.0, FR0: float = 0.0, collision: int = 0, Cs: float = 0.0):
@@ -147,6 +153,28 @@ def feq(rho: float, ux: float, uy: float) -> np.ndarray:
     out = np.zeros(9)
     _load().orc_feq(rho, ux, uy, _p(out))
     return out
+
+
+def feq_entropic(rho, ux, uy):
+    """The D2Q9 entropic equilibrium (minimiser of H = sum f ln(f/t))."""
+    out = np.zeros(9)
+    _load().orc_feq_entropic(float(rho), float(ux), float(uy), _p(out))
+    return out
+
+
+def elbm_alpha(f9, delta9):
+    """Non-trivial root alpha of H(f + alpha Delta) = H(f)."""
+    f9, delta9 = _f64(f9), _f64(delta9)
+    return _load().orc_elbm_alpha(_p(f9), _p(delta9))
+
+
+def elbm_cell(f9, tau0, Fex=0.0, Fey=0.0, alpha_drag=0.0):
+    """(post-collision populations, alpha) of one ELBM collision."""
+    f9 = _f64(f9)
+    out = np.zeros(9)
+    a = _load().orc_elbm_cell(_p(f9), float(tau0), float(Fex), float(Fey), float(alpha_drag),
+                              _p(out))
+    return out, a
 
 
 def tau_eff(f9, tau0, model: Force):

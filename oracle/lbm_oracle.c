@@ -55,7 +55,8 @@ static const double PI = 3.14159265358979323846;
  * and in every case the linear drag -alpha j on the bare momentum.
  * Collision (Sec. 1): 0 BGK with tau; 1 Smagorinsky eddy viscosity
  * nu_t = C |S| (the paper's form, C = Cs, dx = 1); 2 the turbulent
- * viscosity of eq. (7); each gives a local tau_eff (orc_tau_eff). */
+ * viscosity of eq. (7); each gives a local tau_eff (orc_tau_eff); 3 the
+ * entropic LBM (ELBM, orc_elbm_cell). */
 typedef struct {
   int kind;
   double F0;
@@ -232,6 +233,98 @@ void orc_collide_cell(const double *fin, double tau, double Fex, double Fey,
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Entropic LBM (Sec. 1)                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* The equilibrium of the entropic LBM: the minimiser of the H-function
+ * H(f) = sum_l f_l ln(f_l / t_l) (Sec. 1) under fixed rho and j, which for
+ * D2Q9 has the closed product form
+ *   f_eq_l = t_l rho prod_{a = x, y} (2 - s_a) ((2 u_a + s_a) / (1 - u_a))^{c_la},
+ *   s_a = sqrt(1 + 3 u_a^2). */
+void orc_feq_entropic(double rho, double ux, double uy, double *feq) {
+  double sx = sqrt(1.0 + 3.0 * ux * ux), sy = sqrt(1.0 + 3.0 * uy * uy);
+  double bx = (2.0 * ux + sx) / (1.0 - ux), by = (2.0 * uy + sy) / (1.0 - uy);
+  for (int l = 0; l < Q; ++l)
+    feq[l] = TW[l] * rho * (2.0 - sx) * (2.0 - sy) * pow(bx, CX[l]) * pow(by, CY[l]);
+}
+
+/* phi(z) = (1 + z) ln(1 + z) - z, z > -1: a series for small |z| (where the
+ * two terms cancel), else directly. */
+static double phi_entropy(double z) {
+  if (fabs(z) < 0.1) {
+    double s = 0.0, p = z * z; /* sum_{k >= 2} (-1)^k z^k / (k (k - 1)) */
+    for (int k = 2; k < 24; ++k) {
+      s += ((k & 1) ? -p : p) / (double)(k * (k - 1));
+      p *= z;
+    }
+    return s;
+  }
+  return (1.0 + z) * log1p(z) - z;
+}
+
+/* Entropy condition of ELBM for populations f and Delta = f_eq - f:
+ *   g(a) = H(f + a Delta) - H(f)
+ *        = sum_l f_l phi(a y_l) - a sum_l Delta_l ln(1 + y_l),  y = Delta / f,
+ * an identity that uses sum_l Delta_l = 0 (mass) and keeps every term of the
+ * difference of order Delta^2 (no cancellation of O(1) entropies). */
+static double entropy_gap(const double *f, const double *d, double a) {
+  double s1 = 0.0, s2 = 0.0;
+  for (int l = 0; l < Q; ++l) {
+    double y = d[l] / f[l];
+    s1 += f[l] * phi_entropy(a * y);
+    s2 += d[l] * log1p(y);
+  }
+  return s1 - a * s2;
+}
+
+/* The non-trivial root alpha > 1 of the entropy condition (g(0) = 0,
+ * g(1) = H(f_eq) - H(f) <= 0, g convex): bisection on [1, a_max) where
+ * a_max keeps every f_l + a Delta_l positive; alpha = 2 (the BGK value)
+ * when the state is at equilibrium to rounding, when a population is not
+ * positive, or when no root lies below min(a_max, 64). */
+double orc_elbm_alpha(const double *f, const double *d) {
+  double ymax = 0.0, amax = 64.0;
+  for (int l = 0; l < Q; ++l) {
+    if (!(f[l] > 0.0)) return 2.0;
+    double y = d[l] / f[l];
+    if (fabs(y) > ymax) ymax = fabs(y);
+    if (y < 0.0 && -1.0 / y < amax) amax = -1.0 / y;
+  }
+  if (ymax < 1e-12) return 2.0;
+  double lo = 1.0, hi = amax * (1.0 - 1e-12);
+  if (entropy_gap(f, d, hi) < 0.0) return 2.0;
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (entropy_gap(f, d, mid) < 0.0)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* ELBM collision of one cell: f' = f + alpha beta (f_eq - f) + F_l with
+ * beta = 1 / (2 tau0) (the effective relaxation time is tau_eff = 2 tau0 /
+ * alpha, Sec. 1), f_eq the entropic equilibrium at u = j / rho, and the EDM
+ * term F_l = f_eq(rho, u + F / rho) - f_eq(rho, u) with the same
+ * equilibrium.  Returns alpha. */
+double orc_elbm_cell(const double *fin, double tau0, double Fex, double Fey,
+                     double alpha_drag, double *fout) {
+  double rho, jx, jy;
+  cell_moments(fin, &rho, &jx, &jy);
+  double ux = jx / rho, uy = jy / rho;
+  double Fx = Fex - alpha_drag * jx, Fy = Fey - alpha_drag * jy;
+  double feq[Q], fsh[Q], d[Q];
+  orc_feq_entropic(rho, ux, uy, feq);
+  orc_feq_entropic(rho, ux + Fx / rho, uy + Fy / rho, fsh);
+  for (int l = 0; l < Q; ++l) d[l] = feq[l] - fin[l];
+  double a = orc_elbm_alpha(fin, d);
+  double beta = 1.0 / (2.0 * tau0);
+  for (int l = 0; l < Q; ++l) fout[l] = fin[l] + a * beta * d[l] + (fsh[l] - feq[l]);
+  return a;
+}
+
 /* Local relaxation time of one cell (populations fc) for the member's
  * collision model.  The strain rate comes from the non-equilibrium second
  * moment of the pre-collision populations, Pi^neq = sum_l c c (f - f_eq),
@@ -245,6 +338,13 @@ void orc_collide_cell(const double *fin, double tau, double Fex, double Fey,
  *     / (2 rho Tr(Pi^2)) (tau0 where Pi = 0). */
 double orc_tau_eff(const double *fc, double tau0, const orc_model_t *P) {
   if (P->collision == 0) return tau0;
+  if (P->collision == 3) { /* ELBM: tau_eff = 2 tau0 / alpha */
+    double rho, jx, jy, feq[Q], d[Q];
+    cell_moments(fc, &rho, &jx, &jy);
+    orc_feq_entropic(rho, jx / rho, jy / rho, feq);
+    for (int l = 0; l < Q; ++l) d[l] = feq[l] - fc[l];
+    return 2.0 * tau0 / orc_elbm_alpha(fc, d);
+  }
   double rho, jx, jy, feq[Q];
   cell_moments(fc, &rho, &jx, &jy);
   orc_feq(rho, jx / rho, jy / rho, feq);
@@ -293,7 +393,10 @@ int orc_collide(int nx, int ny, double tau, const orc_model_t *F,
       size_t c = (size_t)y * nx + x;
       double a[Q], b[Q];
       for (int l = 0; l < Q; ++l) a[l] = fin[l * plane + c];
-      orc_collide_cell(a, orc_tau_eff(a, tau, F), Fe[c], Fe[plane + c], F->alpha, b);
+      if (F->collision == 3)
+        orc_elbm_cell(a, tau, Fe[c], Fe[plane + c], F->alpha, b);
+      else
+        orc_collide_cell(a, orc_tau_eff(a, tau, F), Fe[c], Fe[plane + c], F->alpha, b);
       for (int l = 0; l < Q; ++l) fout[l * plane + c] = b[l];
     }
   free(Fe);
@@ -353,7 +456,10 @@ int orc_run_window(int wx, int wy, double tau, const orc_model_t *F, double *f,
         double a[Q], b[Q], Fex, Fey;
         for (int l = 0; l < Q; ++l) a[l] = f[l * plane + (size_t)y * wx + x];
         orc_force_ext(NX, NY, F, wrap(X0 + x, NX), wrap(Y0 + y, NY), &Fex, &Fey);
-        orc_collide_cell(a, orc_tau_eff(a, tau, F), Fex, Fey, F->alpha, b);
+        if (F->collision == 3)
+          orc_elbm_cell(a, tau, Fex, Fey, F->alpha, b);
+        else
+          orc_collide_cell(a, orc_tau_eff(a, tau, F), Fex, Fey, F->alpha, b);
         for (int l = 0; l < Q; ++l) s[l * plane + (size_t)y * wx + x] = b[l];
       }
     orc_stream(wx, wy, s, f);

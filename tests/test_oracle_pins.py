@@ -738,3 +738,66 @@ def test_terms_take_a_local_viscosity(orc):
     T1 = orc.terms(tau, rho3, ux3, uy3, Fx, Fy, nu=np.ones((n, n)))
     np.testing.assert_allclose(Tv[4], nu * T1[4], rtol=1e-14, atol=1e-30)
     np.testing.assert_array_equal(Tv[[0, 1, 2, 3, 6, 7, 8, 9]], T0[[0, 1, 2, 3, 6, 7, 8, 9]])
+
+
+# --------------------------------------------------------------------------
+# Entropic LBM (Sec. 1)
+# --------------------------------------------------------------------------
+
+def _H(f):
+    _, _, t = __import__("oracle").lattice()
+    return float(np.sum(f * np.log(f / t)))
+
+
+def test_entropic_equilibrium_is_the_constrained_minimum_of_H(orc):
+    """The closed form conserves rho and j exactly and equals a numerical
+    minimisation of H = sum f ln(f/t) under those constraints (scipy)."""
+    from scipy.optimize import minimize
+    cx, cy, t = orc.lattice()
+    for rho, ux, uy in [(1.0, 0.0, 0.0), (1.03, 0.05, -0.02), (0.97, -0.12, 0.08)]:
+        feq = orc.feq_entropic(rho, ux, uy)
+        assert abs(feq.sum() - rho) < 1e-15
+        assert abs((cx * feq).sum() - rho * ux) < 1e-15
+        assert abs((cy * feq).sum() - rho * uy) < 1e-15
+        cons = [{"type": "eq", "fun": lambda f: f.sum() - rho},
+                {"type": "eq", "fun": lambda f: (cx * f).sum() - rho * ux},
+                {"type": "eq", "fun": lambda f: (cy * f).sum() - rho * uy}]
+        x0 = t * rho * (1.0 + 0.1 * np.sin(np.arange(9)))
+        res = minimize(lambda f: np.sum(f * np.log(f / t)), x0, constraints=cons,
+                       bounds=[(1e-9, None)] * 9, method="SLSQP",
+                       options={"ftol": 1e-15, "maxiter": 500})
+        assert np.max(np.abs(res.x - feq)) < 1e-6
+
+
+def test_elbm_alpha_satisfies_the_entropy_condition(orc):
+    """H(f + alpha Delta) = H(f) by direct evaluation of H, alpha in (1,
+    a_max); alpha -> 2 (BGK) as the state approaches equilibrium."""
+    rng = np.random.default_rng(11)
+    for k in range(6):
+        feq = orc.feq_entropic(1.0 + 0.02 * rng.normal(), 0.05 * rng.normal(), 0.05 * rng.normal())
+        f = feq * (1.0 + 0.05 * rng.normal(size=9))
+        cx, cy, _ = orc.lattice()
+        rho, jx, jy = f.sum(), (cx * f).sum(), (cy * f).sum()
+        d = orc.feq_entropic(rho, jx / rho, jy / rho) - f
+        a = orc.elbm_alpha(f, d)
+        assert a > 1.0 and np.all(f + a * d > 0)
+        assert abs(_H(f + a * d) - _H(f)) < 1e-13
+    feq = orc.feq_entropic(1.0, 0.03, 0.01)
+    for eps in (1e-3, 1e-5):
+        f = feq * (1.0 + eps * np.cos(np.arange(9)))
+        rho, jx, jy = f.sum(), (cx * f).sum(), (cy * f).sum()
+        d = orc.feq_entropic(rho, jx / rho, jy / rho) - f
+        assert abs(orc.elbm_alpha(f, d) - 2.0) < 50 * eps
+
+
+def test_elbm_cell_conserves_mass_and_adds_the_force(orc):
+    rng = np.random.default_rng(12)
+    cx, cy, _ = orc.lattice()
+    f = orc.feq_entropic(1.01, 0.04, -0.03) * (1.0 + 0.03 * rng.normal(size=9))
+    Fex, Fey, drag = 2e-4, -1e-4, 1e-3
+    out, a = orc.elbm_cell(f, 0.52, Fex, Fey, drag)
+    jx, jy = (cx * f).sum(), (cy * f).sum()
+    assert abs(out.sum() - f.sum()) < 1e-15
+    assert abs((cx * out).sum() - jx - (Fex - drag * jx)) < 1e-15
+    assert abs((cy * out).sum() - jy - (Fey - drag * jy)) < 1e-15
+    assert 1.0 < a < 64.0
