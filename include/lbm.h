@@ -92,7 +92,12 @@ typedef struct lbm_member_cfg {
                        stress Pi^neq = -2 rho cs^2 tau S of the pre-collision
                        populations: 1: Smagorinsky nu_t = Cs sqrt(S:S)
                        (S at the local tau itself; closed-form root);
-                       2: the turbulent viscosity of eq. (7) (S at tau).
+                       2: the turbulent viscosity of eq. (7) (S at tau);
+                       3: the entropic LBM (equilibrium minimising
+                       H = sum f ln(f/t), relaxation f + alpha (f_eq - f) /
+                       (2 tau) with alpha the root of the entropy condition
+                       H(f + alpha (f_eq - f)) = H(f), tau_eff = 2 tau /
+                       alpha; runs in the general kernel).
                        The diagnostic then uses the local viscosity of each
                        cell at time n; no adjoint */
   double Cs;        /* Smagorinsky constant (collision 1; dx = 1) */

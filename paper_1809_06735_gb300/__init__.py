@@ -106,7 +106,8 @@ class Member:
     sin(2 pi kf x/nx)); kind 2: the paper's shell force of eqs. (14), (15)
     (amplitude F0, phase) with the large-scale damping of eq. (16) (FR0) --
     linear drag alpha on the bare momentum, and the collision: 0 BGK, 1
-    Smagorinsky (constant Cs), 2 the turbulent viscosity of eq. (7)."""
+    Smagorinsky (constant Cs), 2 the turbulent viscosity of eq. (7), 3 the
+    entropic LBM."""
     nx: int
     ny: int
     tau: float

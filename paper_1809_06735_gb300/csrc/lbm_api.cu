@@ -112,8 +112,10 @@ void shell_force_tables(const lbm_member_cfg &c, int pitch, std::vector<double> 
   }
 }
 
+// The vectorised FP32 kernel serves nx % 4 == 0 with every collision but
+// the entropic one (its per-cell root finding runs in the general kernel).
 bool vector_eligible(const lbm_member_cfg &m, int precision) {
-  return precision == 32 && m.nx % 4 == 0;
+  return precision == 32 && m.nx % 4 == 0 && m.collision != 3;
 }
 
 int check_config(const lbm_config *cfg, std::string &err) {
@@ -140,8 +142,8 @@ int check_config(const lbm_config *cfg, std::string &err) {
     if (c.force_kind < 0 || c.force_kind > 2) {
       snprintf(buf, sizeof buf, "member %d: force_kind must be 0, 1 or 2", m); err = buf; return LBM_ERR_ARG;
     }
-    if (c.collision < 0 || c.collision > 2 || !std::isfinite(c.Cs) || c.Cs < 0.0) {
-      snprintf(buf, sizeof buf, "member %d: collision must be 0, 1 or 2 with Cs >= 0", m);
+    if (c.collision < 0 || c.collision > 3 || !std::isfinite(c.Cs) || c.Cs < 0.0) {
+      snprintf(buf, sizeof buf, "member %d: collision must be 0..3 with Cs >= 0", m);
       err = buf; return LBM_ERR_ARG;
     }
     if (!std::isfinite(c.F0) || !std::isfinite(c.alpha) ||

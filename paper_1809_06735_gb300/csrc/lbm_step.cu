@@ -86,6 +86,158 @@ __device__ __forceinline__ void moments_f64(const double f[kQ], double &rho, dou
   uy = jy * ir;
 }
 
+// ---------------------------------------------------------------------------
+// Entropic LBM (collision 3): the equilibrium minimising H = sum f ln(f/t),
+// the non-trivial root alpha of H(f + alpha Delta) = H(f), Delta = f_eq - f,
+// f' = f + alpha Delta / (2 tau0) + F_l (EDM on the same equilibrium).
+// ---------------------------------------------------------------------------
+
+// phi(z) = (1 + z) ln(1 + z) - z: series where the terms cancel.
+template <typename T>
+__device__ __forceinline__ T phi_entropy(T z) {
+  const T lim = sizeof(T) == 4 ? T(0.1) : T(0.1);
+  if (fabs(z) < lim) {
+    const int K = sizeof(T) == 4 ? 10 : 24;
+    T s = T(0), p = z * z;
+#pragma unroll
+    for (int k = 2; k < K; ++k) {
+      s += ((k & 1) ? -p : p) / T(k * (k - 1));
+      p *= z;
+    }
+    return s;
+  }
+  return (T(1) + z) * log1p(z) - z;
+}
+
+// g(a) = sum f phi(a y) - a S2, y = Delta / f, S2 = sum Delta ln(1 + y).
+template <typename T>
+__device__ __forceinline__ T entropy_gap(const T f[kQ], const T y[kQ], T S2, T a) {
+  T s = T(0);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) s += f[l] * phi_entropy<T>(a * y[l]);
+  return s - a * S2;
+}
+
+// The root alpha > 1 (alpha = 2 at equilibrium, for non-positive populations
+// or without a root below min(a_max, 64)).  FP64: bisection to 1e-15 (the
+// oracle's procedure); FP32: safeguarded Newton from 2, g'(a) = sum Delta
+// ln(1 + a y) - S2, to 1e-6.
+template <typename T>
+__device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
+  T y[kQ], ymax = T(0), amax = T(64), S2 = T(0);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) {
+    if (!(f[l] > T(0))) return T(2);
+    y[l] = d[l] / f[l];
+    ymax = fmax(ymax, fabs(y[l]));
+    if (y[l] < T(0)) amax = fmin(amax, -T(1) / y[l]);
+    S2 += d[l] * log1p(y[l]);
+  }
+  if (ymax < (sizeof(T) == 4 ? T(1e-7) : T(1e-12))) return T(2);
+  T lo = T(1), hi = amax * (sizeof(T) == 4 ? T(1 - 1e-6) : T(1 - 1e-12));
+  if (entropy_gap<T>(f, y, S2, hi) < T(0)) return T(2);
+  if constexpr (sizeof(T) == 8) {
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+      const T mid = T(0.5) * (lo + hi);
+      if (entropy_gap<T>(f, y, S2, mid) < T(0))
+        lo = mid;
+      else
+        hi = mid;
+    }
+    return T(0.5) * (lo + hi);
+  } else {
+    T a = fmin(T(2), T(0.5) * (lo + hi));
+    for (int it = 0; it < 30; ++it) {
+      const T g = entropy_gap<T>(f, y, S2, a);
+      if (g < T(0))
+        lo = a;
+      else
+        hi = a;
+      T dg = -S2;
+#pragma unroll
+      for (int l = 0; l < kQ; ++l) dg += d[l] * log1p(a * y[l]);
+      T an = a - g / dg;
+      if (!(an > lo && an < hi)) an = T(0.5) * (lo + hi);  // leave the bracket: bisect
+      const bool done = fabs(an - a) < T(1e-6) * a;
+      a = an;
+      if (done) break;
+    }
+    return a;
+  }
+}
+
+// ln of the entropic equilibrium's velocity factor, per population:
+// ln P_l(u) = sum_a [ln(2 - s_a) + c_la ln((2 u_a + s_a) / (1 - u_a))],
+// s_a = sqrt(1 + 3 u_a^2), each logarithm as log1p of a cancellation-free
+// argument (s - 1 = 3 u^2 / (1 + s)).
+template <typename T>
+__device__ __forceinline__ void entropic_logp(T ux, T uy, T lp[kQ]) {
+  const T sx = sqrt(T(1) + T(3) * ux * ux), sy = sqrt(T(1) + T(3) * uy * uy);
+  const T qx = T(3) * ux * ux / (T(1) + sx), qy = T(3) * uy * uy / (T(1) + sy);
+  const T a0x = log1p(-qx), a0y = log1p(-qy);
+  const T a1x = log1p((T(3) * ux + qx) / (T(1) - ux));
+  const T a1y = log1p((T(3) * uy + qy) / (T(1) - uy));
+#pragma unroll
+  for (int l = 0; l < kQ; ++l)
+    lp[l] = a0x + a0y + (T)cx_of(l) * a1x + (T)cy_of(l) * a1y;
+}
+
+// One ELBM collision in storage form (FP32: deviations g = f - t rho0, FP64:
+// f); returns alpha.
+template <typename T>
+__device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
+  T rho, jx, jy, drho;
+  if constexpr (sizeof(T) == 4) {
+    float ir, ux, uy;
+    moments_f32(v, rho0, drho, rho, jx, jy, ir, ux, uy);
+  } else {
+    rho = T(0);
+    jx = T(0);
+    jy = T(0);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      rho += v[l];
+      jx += cx_of(l) * v[l];
+      jy += cy_of(l) * v[l];
+    }
+    drho = T(0);
+  }
+  const T ux = jx / rho, uy = jy / rho;
+  const T Fx = Fex - alpha_drag * jx, Fy = Fey - alpha_drag * jy;
+  T lp[kQ], lps[kQ];
+  entropic_logp<T>(ux, uy, lp);
+  entropic_logp<T>(ux + Fx / rho, uy + Fy / rho, lps);
+  T f[kQ], d[kQ], Fl[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) {
+    const T t = (T)w_of(l);
+    const T em = expm1(lp[l]);  // P_l - 1
+    if constexpr (sizeof(T) == 4) {
+      f[l] = t * rho0 + v[l];
+      d[l] = t * (drho * (T(1) + em) + rho0 * em) - v[l];  // f_eq - f, deviation form
+    } else {
+      f[l] = v[l];
+      d[l] = t * rho * (T(1) + em) - v[l];
+    }
+    Fl[l] = t * rho * (T(1) + em) * expm1(lps[l] - lp[l]);
+  }
+  const T a = elbm_alpha<T>(f, d);
+  const T ab = a / (T(2) * tau0);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) v[l] = v[l] + ab * d[l] + Fl[l];
+  return a;
+}
+
+// Relaxation time 2 tau0 / alpha of the ELBM state v (storage form).
+template <typename T>
+__device__ T elbm_tau(const T v[kQ], T rho0, T tau0) {
+  T w[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) w[l] = v[l];
+  const T a = collide_elbm<T>(w, rho0, tau0, T(0), T(0), T(0));
+  return T(2) * tau0 / a;
+}
+
 // With VV (variable viscosity, collision != 0) omega = 1 / local_tau_f32.
 template <bool VV = false>
 __device__ __forceinline__ void collide_f32(float g[kQ], float rho0, float om, float Fex,
@@ -403,7 +555,12 @@ __global__ void k_step_scalar(const Member *__restrict__ members, int member, in
   T f[kQ];
 #pragma unroll
   for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
-  if constexpr (sizeof(T) == 4) {
+  if (M.collision == 3) {
+    if constexpr (sizeof(T) == 4)
+      collide_elbm<float>(f, M.rho0_f, M.tau_f, fx, fy, M.alpha_f);
+    else
+      collide_elbm<double>(f, 0.0, M.tau, fx, fy, M.alpha);
+  } else if constexpr (sizeof(T) == 4) {
     collide_f32<true>(f, M.rho0_f, M.omega_f, fx, fy, M.alpha_f, M.collision, M.tau_f, M.Cs_f);
   } else {
     collide_f64(f, M.omega, fx, fy, M.alpha, M.collision, M.tau, M.Cs);
@@ -559,7 +716,12 @@ __global__ void k_snapshot(const Member *__restrict__ members, int member, int s
   d[2 * N + c] = jy;
   if (M.collision != 0) {  // local viscosity as a fourth field
     double t;
-    if constexpr (sizeof(T) == 4) {
+    if (M.collision == 3) {
+      if constexpr (sizeof(T) == 4)
+        t = (double)elbm_tau<float>(f, M.rho0_f, M.tau_f);
+      else
+        t = elbm_tau<double>(f, 0.0, M.tau);
+    } else if constexpr (sizeof(T) == 4) {
       float drho, rho, jxf, jyf, ir, ux, uy;
       moments_f32(f, M.rho0_f, drho, rho, jxf, jyf, ir, ux, uy);
       t = (double)local_tau_f32(f, drho, rho, ux, uy, M.tau_f, M.collision, M.Cs_f);
@@ -617,9 +779,14 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
       d[(size_t)(2 * q + 1) * N + c] = lo[q];
     }
     if (M.collision != 0) {  // the local viscosity the step from this state uses
-      float drho, rho, jx, jy, ir, ux, uy;
-      moments_f32(f, M.rho0_f, drho, rho, jx, jy, ir, ux, uy);
-      const float t = local_tau_f32(f, drho, rho, ux, uy, M.tau_f, M.collision, M.Cs_f);
+      float t;
+      if (M.collision == 3) {
+        t = elbm_tau<float>(f, M.rho0_f, M.tau_f);
+      } else {
+        float drho, rho, jx, jy, ir, ux, uy;
+        moments_f32(f, M.rho0_f, drho, rho, jx, jy, ir, ux, uy);
+        t = local_tau_f32(f, drho, rho, ux, uy, M.tau_f, M.collision, M.Cs_f);
+      }
       static_cast<float *>(M.nu_ring)[(size_t)slot * N + c] = (t - 0.5f) * (1.0f / 3.0f);
     }
   } else {
@@ -635,9 +802,14 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
     d[N + c] = jx;
     d[2 * N + c] = jy;
     if (M.collision != 0) {
-      double rho, ux, uy;
-      moments_f64(f, rho, ux, uy);
-      const double t = local_tau_f64(f, rho, ux, uy, M.tau, M.collision, M.Cs);
+      double t;
+      if (M.collision == 3) {
+        t = elbm_tau<double>(f, 0.0, M.tau);
+      } else {
+        double rho, ux, uy;
+        moments_f64(f, rho, ux, uy);
+        t = local_tau_f64(f, rho, ux, uy, M.tau, M.collision, M.Cs);
+      }
       static_cast<double *>(M.nu_ring)[(size_t)slot * N + c] = (t - 0.5) / 3.0;
     }
   }

@@ -60,7 +60,7 @@ def test_workspace_size_validates(P):
     with pytest.raises(P.LBMError):
         P.workspace_size([P.Member(8, 8, 0.6, force_kind=3)], 32)
     with pytest.raises(P.LBMError):
-        P.workspace_size([P.Member(8, 8, 0.6, collision=3)], 32)
+        P.workspace_size([P.Member(8, 8, 0.6, collision=4)], 32)
     with pytest.raises(P.LBMError):
         P.workspace_size([P.Member(8, 8, 0.6, collision=1, Cs=-0.1)], 32)
     with pytest.raises(P.LBMError):

@@ -1,6 +1,7 @@
 """GPU parity of the variable-viscosity collisions (Sec. 1: the Smagorinsky
 eddy viscosity and the turbulent viscosity of eq. (7), each a local
-relaxation time from the non-equilibrium stress) against the FP64 oracle,
+relaxation time from the non-equilibrium stress, and the entropic LBM with
+its per-cell entropy-condition root) against the FP64 oracle,
 through the C ABI: trajectories (FP64 within 1e-12, FP32 within 2e-6 on
 every population) in mixed ensembles on both kernels and both storages, the
 whole-grid budget with the local viscosity, and the balance terms whose
@@ -40,7 +41,8 @@ def _fields(nx, ny, seed, amp=0.05):
 # kernels, every force kind
 SPEC = [(64, 48, 0.51, 0, 0.0, 0, 0.0, 1), (37, 23, 0.53, 1, 2e-4, 2, 1e-3, 1),
         (48, 40, 0.52, 2, 2e-5, 0, 0.0, 2), (32, 32, 0.55, 1, 2e-4, 2, 0.0, 2),
-        (40, 40, 0.56, 0, 0.0, 0, 0.0, 0)]
+        (40, 40, 0.56, 0, 0.0, 0, 0.0, 0), (48, 40, 0.505, 0, 0.0, 0, 0.0, 3),
+        (37, 23, 0.51, 1, 2e-4, 2, 1e-3, 3)]
 
 
 def _member(P, spec):
@@ -81,12 +83,12 @@ def test_collision_models_change_the_flow(P, orc):
     nx, ny, tau = 48, 40, 0.51
     f = orc.init(*_fields(nx, ny, 3))
     bgk = orc.run(f, 20, tau)
-    for coll, cs in ((1, CS), (2, 0.0)):
+    for coll, cs in ((1, CS), (2, 0.0), (3, 0.0)):
         other = orc.run(f, 20, tau, orc.Force(0, collision=coll, Cs=cs))
         assert rel_err(other, bgk) > 50 * FP32_TOL, coll
 
 
-@pytest.mark.parametrize("coll", [1, 2])
+@pytest.mark.parametrize("coll", [1, 2, 3])
 def test_collision_budget_and_balance_terms(P, orc, coll):
     nx, ny, tau = 64, 48, 0.52
     model = orc.Force(1, 2e-4, 2, 1e-3, collision=coll, Cs=CS if coll == 1 else 0.0)
@@ -116,12 +118,14 @@ def test_collision_budget_and_balance_terms(P, orc, coll):
     assert np.max(np.abs(T_bgk[4] - T[4])) > 1e4 * TERM_TOL * scale[4]
 
 
-def test_fp32_collision_diagnostic(P, orc):
-    """FP32 storage and diagnostic with the Smagorinsky model: box terms within
-    the FP32 bar of the oracle on the exported states."""
+@pytest.mark.parametrize("coll", [1, 3])
+def test_fp32_collision_diagnostic(P, orc, coll):
+    """FP32 storage and diagnostic with the Smagorinsky model and ELBM: box
+    terms within the FP32 bar of the oracle on the exported states."""
     nx, ny, tau = 64, 64, 0.51
-    model = orc.Force(0, collision=1, Cs=CS)
-    lat = P.Lattice([P.Member(nx, ny, tau, 1.0, 0, 0, 0.0, 0.0, 0.0, 0.0, 1, CS)],
+    cs = CS if coll == 1 else 0.0
+    model = orc.Force(0, collision=coll, Cs=cs)
+    lat = P.Lattice([P.Member(nx, ny, tau, 1.0, 0, 0, 0.0, 0.0, 0.0, 0.0, coll, cs)],
                     precision=32, diag_every=16)
     lat.init_fields(0, *_fields(nx, ny, 21))
     lat.step(14)
