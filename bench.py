@@ -263,6 +263,36 @@ def paper_forcing_leg(P, stream, dev, peak):
             "storage": tune["storage"]}
 
 
+def collision_models_leg(P, stream, dev, peak):
+    """The variable-viscosity collisions (Sec. 1) on 16 FP32 members of
+    512^2 (tau0 = 0.51): Smagorinsky (Cs = 0.1) and eq. (7) on the extended
+    vectorised kernel, the entropic LBM (its per-cell root finding) on the
+    general kernel.  Every step moves 72 algorithmic bytes per update."""
+    import torch
+    n, M, steps = 512, 16, 40
+    fields = li.random_phase(n, seed=4000, u_rms=0.02)
+    out = {"members": M, "grid": [n, n], "tau0": 0.51}
+    for name, coll, cs in (("smagorinsky", 1, 0.1), ("eq7", 2, 0.0), ("elbm", 3, 0.0)):
+        lat = P.Lattice([P.Member(n, n, 0.51, collision=coll, Cs=cs)] * M, precision=32,
+                        graph_steps=20, stream=stream, device=dev)
+        for m in range(M):
+            lat.init_fields(m, *fields)
+        lat.step(20)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        lat.step(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        secs = a.elapsed_time(b) / 1e3
+        lu = M * n * n * steps
+        gbs = BYTES_PER_LU_F32 * lu / secs / 1e9
+        out[name] = {"glups": lu / secs / 1e9, "achieved_gbs": gbs, "frac": gbs / peak,
+                     "kernel": "k_step_scalar<float>" if coll == 3 else "k_step_f32_vec (extended)"}
+        del lat
+    return out
+
+
 def workload_config():
     wl = li.decaying_ensemble_workload()
     return {"workload": wl["name"], "members_per_gpu": wl["members"], "grid": [wl["n"], wl["n"]],
@@ -389,6 +419,7 @@ def run_ours(args):
     fp64_glups = n * n / fp64_s / 1e9
     del lat64
     paper_forcing = paper_forcing_leg(P, stream, dev, measured_peaks()[0])
+    collisions = collision_models_leg(P, stream, dev, measured_peaks()[0])
 
     # end to end through the C ABI with host buffers: every step uploads the
     # initial fields of all members from pinned host memory, runs the period
@@ -438,6 +469,7 @@ def run_ours(args):
             "fp64_plain_single_instance": {"glups": fp64_glups, "grid": [n, n],
                                            "ratio_batched_fp32_over_fp64": step_glups / fp64_glups},
             "paper_forcing_ensemble": paper_forcing,
+            "collision_models": collisions,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -5,6 +5,7 @@
     python -m paper_1809_06735_gb300.profile_case diag     # one diagnostic event, 512^2
     python -m paper_1809_06735_gb300.profile_case diag_batch  # batched event, 16 x 512^2
     python -m paper_1809_06735_gb300.profile_case paper_forcing  # force kind 2, 64 x 256^2
+    python -m paper_1809_06735_gb300.profile_case collisions  # Smagorinsky, eq. (7), ELBM
     python -m paper_1809_06735_gb300.profile_case fp64     # plain FP64 step, 512^2
     python -m paper_1809_06735_gb300.profile_case adjoint  # FP64 adjoint steps, 256^2
 
@@ -58,6 +59,21 @@ def case_paper_forcing(members=64, n=256, steps=30):
     lat.step(steps)
     torch.cuda.synchronize()
     print("paper forcing case done:", lat.launch_count, "launches", lat.tuning())
+
+
+def case_collisions(members=16, n=512, steps=12):
+    """The variable-viscosity collisions on 16 FP32 members of 512^2: one
+    handle each for Smagorinsky, eq. (7) and the entropic LBM."""
+    fields = li.random_phase(n, seed=4000, u_rms=0.02)
+    for coll, cs in ((1, 0.1), (2, 0.0), (3, 0.0)):
+        lat = Lattice([Member(n, n, 0.51, collision=coll, Cs=cs)] * members, precision=32,
+                      graph_steps=0)
+        for m in range(members):
+            lat.init_fields(m, *fields)
+        lat.step(steps)
+        torch.cuda.synchronize()
+        print("collision", coll, "done:", lat.launch_count, "launches", lat.tuning())
+        del lat
 
 
 def case_diag(n=512, events=2):
@@ -114,5 +130,6 @@ def case_adjoint(n=256, steps=6):
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "step"
     {"step": case_step, "step_full": case_step_full, "paper_forcing": case_paper_forcing,
+     "collisions": case_collisions,
      "diag": case_diag, "diag_batch": case_diag_batch, "fp64": case_fp64,
      "adjoint": case_adjoint}[which]()
