@@ -101,7 +101,7 @@ __device__ __forceinline__ T phi_entropy(T z) {
     T s = T(0), p = z * z;
 #pragma unroll
     for (int k = 2; k < K; ++k) {
-      s += ((k & 1) ? -p : p) / T(k * (k - 1));
+      s += ((k & 1) ? -p : p) * T(1.0 / (k * (k - 1)));
       p *= z;
     }
     return s;
@@ -109,19 +109,26 @@ __device__ __forceinline__ T phi_entropy(T z) {
   return (T(1) + z) * log1p(z) - z;
 }
 
-// g(a) = sum f phi(a y) - a S2, y = Delta / f, S2 = sum Delta ln(1 + y).
+// g(a) = sum f phi(a y) - a S2, y = Delta / f, S2 = sum Delta ln(1 + y);
+// *scale (if given) receives the magnitude of the terms, the size of g's
+// rounding noise.
 template <typename T>
-__device__ __forceinline__ T entropy_gap(const T f[kQ], const T y[kQ], T S2, T a) {
+__device__ __forceinline__ T entropy_gap(const T f[kQ], const T y[kQ], T S2, T a,
+                                         T *scale = nullptr) {
   T s = T(0);
 #pragma unroll
   for (int l = 0; l < kQ; ++l) s += f[l] * phi_entropy<T>(a * y[l]);
+  if (scale) *scale = s + a * fabs(S2);
   return s - a * S2;
 }
 
 // The root alpha > 1 (alpha = 2 at equilibrium, for non-positive populations
 // or without a root below min(a_max, 64)).  FP64: bisection to 1e-15 (the
-// oracle's procedure); FP32: safeguarded Newton from 2, g'(a) = sum Delta
-// ln(1 + a y) - S2, to 1e-6.
+// oracle's procedure); FP32: Newton from 2, g'(a) = sum Delta ln(1 + a y) -
+// S2, kept inside a bisection bracket, until |g| is at the level of its
+// rounding (1e-6 of the terms; then one last Newton step if it stays in the
+// bracket) or the step is below 1e-6 -- about 2-3 iterations, so the lanes
+// of a warp finish together.
 template <typename T>
 __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
   T y[kQ], ymax = T(0), amax = T(64), S2 = T(0);
@@ -148,7 +155,9 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
   } else {
     T a = fmin(T(2), T(0.5) * (lo + hi));
     for (int it = 0; it < 30; ++it) {
-      const T g = entropy_gap<T>(f, y, S2, a);
+      T scale;
+      const T g = entropy_gap<T>(f, y, S2, a, &scale);
+      const bool conv = fabs(g) <= T(1e-6) * scale;
       if (g < T(0))
         lo = a;
       else
@@ -157,7 +166,9 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
 #pragma unroll
       for (int l = 0; l < kQ; ++l) dg += d[l] * log1p(a * y[l]);
       T an = a - g / dg;
-      if (!(an > lo && an < hi)) an = T(0.5) * (lo + hi);  // leave the bracket: bisect
+      const bool inside = an > lo && an < hi;
+      if (conv) return inside ? an : a;
+      if (!inside) an = T(0.5) * (lo + hi);  // left the bracket: bisect
       const bool done = fabs(an - a) < T(1e-6) * a;
       a = an;
       if (done) break;
