@@ -1,4 +1,5 @@
-"""Python access to the FP64 CPU oracle (``lbm_oracle.c``).
+"""Python access to the FP64 CPU oracle (``lbm_oracle.c``, and
+``lbm_oracle3d.c`` for the three-dimensional D3Q19 extension).
 
 TEST INFRASTRUCTURE ONLY: the oracle is a plain, slow restatement of the
 D2Q9 LBGK method (eqs. (1), (2) with exact-difference forcing) and of the
@@ -23,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
+_SRC3 = os.path.join(_HERE, "lbm_oracle3d.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -39,10 +41,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (plain -O2, no fast-math)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or (
-            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+            os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3))):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+                               "-ffp-contract=off", "-o", tmp, _SRC, _SRC3, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -92,6 +94,21 @@ def _load():
             lib.orc_objective.argtypes = [I, I, D, P, P, I, I, I, I, I, P]
             lib.orc_objective.restype = I
             lib.orc_lattice.argtypes = [P, P, P]
+            lib.orc3_lattice.argtypes = [P, P, P, P]
+            lib.orc3_feq.argtypes = [D, D, D, D, P]
+            lib.orc3_run.argtypes = [I, I, I, D, I, D, I, D, P, I]
+            lib.orc3_run.restype = I
+            lib.orc3_init.argtypes = [I, I, I, P, P, P, P, P]
+            lib.orc3_moments.argtypes = [I, I, I, I, D, I, D, P, P, P, P, P, P, P, P]
+            lib.orc3_d.argtypes = [I, I, I, I, P, P]
+            lib.orc3_terms.argtypes = [I, I, I, D, P, P, P, P, P, P, P, P]
+            lib.orc3_terms.restype = I
+            lib.orc3_terms_from_populations.argtypes = [I, I, I, D, I, D, I, D, P, P, P, P]
+            lib.orc3_terms_from_populations.restype = I
+            lib.orc3_box_mean.argtypes = [I, I, I, P, I, I, I, I]
+            lib.orc3_box_mean.restype = D
+            lib.orc3_balance_stats.argtypes = [I, I, I, P, P, I, P, I, P, P]
+            lib.orc3_balance_stats.restype = I
             lib.orc_box_mach.argtypes = [I, I, P, P, I, I, I]
             lib.orc_box_mach.restype = D
             lib.orc_bin.argtypes = [D, P, I]
@@ -424,3 +441,110 @@ def objective(f0, tau, force: Force, n0, n1, bx, by, L):
     if rc != 0:
         raise MemoryError("oracle objective failed")
     return J.value
+
+
+# --------------------------------------------------------------------------
+# Three dimensions (D3Q19; lbm_oracle3d.c).  Populations f[19, nz, ny, nx],
+# fields A[nz, ny, nx]; force = (kind, F0, kf, alpha) with kind 1 the cyclic
+# Kolmogorov force F0 (sin(2 pi kf y/ny), sin(2 pi kf z/nz), sin(2 pi kf x/nx)).
+# --------------------------------------------------------------------------
+
+def lattice3():
+    cx, cy, cz = (np.zeros(19, np.int32) for _ in range(3))
+    t = np.zeros(19)
+    _load().orc3_lattice(_p(cx), _p(cy), _p(cz), _p(t))
+    return cx, cy, cz, t
+
+
+def feq3(rho, ux, uy, uz):
+    out = np.zeros(19)
+    _load().orc3_feq(float(rho), float(ux), float(uy), float(uz), _p(out))
+    return out
+
+
+def init3(rho, ux, uy, uz):
+    rho, ux, uy, uz = (_f64(a) for a in (rho, ux, uy, uz))
+    nz, ny, nx = rho.shape
+    f = np.empty((19, nz, ny, nx))
+    _load().orc3_init(nx, ny, nz, _p(rho), _p(ux), _p(uy), _p(uz), _p(f))
+    return f
+
+
+def run3(f, nsteps, tau, kind=0, F0=0.0, kf=0, alpha=0.0):
+    f = _f64(f).copy()
+    _, nz, ny, nx = f.shape
+    if _load().orc3_run(nx, ny, nz, float(tau), int(kind), float(F0), int(kf), float(alpha),
+                        _p(f), int(nsteps)) != 0:
+        raise MemoryError("oracle 3D run failed")
+    return f
+
+
+def moments3(f, kind=0, F0=0.0, kf=0, alpha=0.0):
+    """dict rho, ux, uy, uz (u = (j + F/2)/rho), Fx, Fy, Fz (F = F_ext - alpha j)."""
+    f = _f64(f)
+    _, nz, ny, nx = f.shape
+    out = {k: np.empty((nz, ny, nx)) for k in ("rho", "ux", "uy", "uz", "Fx", "Fy", "Fz")}
+    _load().orc3_moments(nx, ny, nz, int(kind), float(F0), int(kf), float(alpha), _p(f),
+                         *(_p(out[k]) for k in ("rho", "ux", "uy", "uz", "Fx", "Fy", "Fz")))
+    return out
+
+
+def d3(A, axis):
+    """Eq. (18) along axis 0 = x, 1 = y, 2 = z of A[nz, ny, nx]."""
+    A = _f64(A)
+    nz, ny, nx = A.shape
+    out = np.empty_like(A)
+    _load().orc3_d(nx, ny, nz, int(axis), _p(A), _p(out))
+    return out
+
+
+def terms3(tau, rho3, ux3, uy3, uz3, Fx, Fy, Fz):
+    """13 term fields [13, nz, ny, nx] from (rho, u) at n, n-1, n-2 and F at n."""
+    levels = [[_f64(a) for a in L] for L in (rho3, ux3, uy3, uz3)]
+    Fx, Fy, Fz = _f64(Fx), _f64(Fy), _f64(Fz)
+    nz, ny, nx = Fx.shape
+    arr = ctypes.c_void_p * 3
+    ptrs = [arr(*[a.ctypes.data for a in L]) for L in levels]
+    out = np.empty((NT, nz, ny, nx))
+    rc = _load().orc3_terms(nx, ny, nz, float(tau), *(ctypes.cast(p, ctypes.c_void_p) for p in ptrs),
+                            _p(Fx), _p(Fy), _p(Fz), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle 3D terms failed")
+    return out
+
+
+def terms3_from_populations(f_n, f_n1, f_n2, tau, kind=0, F0=0.0, kf=0, alpha=0.0):
+    f_n, f_n1, f_n2 = _f64(f_n), _f64(f_n1), _f64(f_n2)
+    _, nz, ny, nx = f_n.shape
+    out = np.empty((NT, nz, ny, nx))
+    rc = _load().orc3_terms_from_populations(nx, ny, nz, float(tau), int(kind), float(F0), int(kf),
+                                             float(alpha), _p(f_n), _p(f_n1), _p(f_n2), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle 3D terms failed")
+    return out
+
+
+def box_mean3(A, x0, y0, z0, L):
+    A = _f64(A)
+    nz, ny, nx = A.shape
+    return _load().orc3_box_mean(nx, ny, nz, _p(A), int(x0), int(y0), int(z0), int(L))
+
+
+def balance_stats3(T, Ls, origins=None, per_box=False):
+    """stats [nL, 15, 2] (and per-box [nL, boxes, 15]) of L^3 boxes; origins
+    None (every periodic origin) or [n, 3] (x0, y0, z0) triples."""
+    T = _f64(T)
+    _, nz, ny, nx = T.shape
+    Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+    if origins is not None:
+        origins = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1, 3)
+        nb, op = origins.shape[0], _p(origins)
+    else:
+        nb, op = nx * ny * nz, None
+    stats = np.empty((len(Ls), NQ, 2))
+    pb = np.empty((len(Ls), nb, NQ)) if per_box else None
+    rc = _load().orc3_balance_stats(nx, ny, nz, _p(T), _p(Ls), len(Ls), op, nb, _p(stats),
+                                    _p(pb) if per_box else None)
+    if rc != 0:
+        raise MemoryError("oracle 3D stats failed")
+    return (stats, pb) if per_box else stats

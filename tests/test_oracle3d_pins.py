@@ -1,0 +1,179 @@
+"""Pins of the three-dimensional (D3Q19) oracle against facts fixed by the
+lattice, by the mathematics and by an independent symbolic evaluation of
+the general index forms of eqs. (8)-(11), whose vortex-stretching term
+RHS^{Omega,6} does not vanish in three dimensions."""
+import numpy as np
+import pytest
+
+import lbm_inputs as li
+
+
+def _smooth3(n, seed, amp):
+    rng = np.random.default_rng(seed)
+    x = 2 * np.pi * np.arange(n) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    out = np.zeros((n, n, n))
+    for _ in range(4):
+        k = rng.integers(-2, 3, size=3)
+        out += rng.normal() * np.cos(k[0] * X + k[1] * Y + k[2] * Z + rng.uniform(0, 2 * np.pi))
+    return amp * out / np.max(np.abs(out))
+
+
+def test_d3q19_isotropy(orc):
+    """sum t = 1, sum t c = 0, sum t c c = cs^2 I, fourth moments cs^4
+    (delta delta + 2 perms), opposite pairs."""
+    cx, cy, cz, t = orc.lattice3()
+    C = np.stack([cx, cy, cz], 1).astype(float)
+    cs2 = 1.0 / 3.0
+    assert abs(t.sum() - 1) < 1e-15
+    assert np.max(np.abs(np.einsum("l,la->a", t, C))) < 1e-15
+    np.testing.assert_allclose(np.einsum("l,la,lb->ab", t, C, C), cs2 * np.eye(3), atol=1e-15)
+    M4 = np.einsum("l,la,lb,lc,ld->abcd", t, C, C, C, C)
+    d = np.eye(3)
+    want = cs2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                       + np.einsum("ad,bc->abcd", d, d))
+    np.testing.assert_allclose(M4, want, atol=1e-15)
+    for l in range(19):
+        assert sum(1 for m in range(19) if (C[m] == -C[l]).all()) == 1
+
+
+def test_d3q19_step_conserves_mass_and_adds_the_force(orc):
+    n = 6
+    rho, ux, uy, uz = 1 + _smooth3(n, 1, 0.01), _smooth3(n, 2, 0.03), _smooth3(n, 3, 0.03), \
+        _smooth3(n, 4, 0.03)
+    f = orc.init3(rho, ux, uy, uz)
+    F0, kf, a = 3e-4, 1, 2e-3
+    g = orc.run3(f, 1, 0.57, 1, F0, kf, a)
+    cx, cy, cz, _ = orc.lattice3()
+    m0 = orc.moments3(f, 1, F0, kf, a)
+    assert abs(g.sum() - f.sum()) < 1e-12
+    for C, Fk in ((cx, "Fx"), (cy, "Fy"), (cz, "Fz")):
+        gain = np.einsum("l,lzyx->", C, g) - np.einsum("l,lzyx->", C, f)
+        assert abs(gain - m0[Fk].sum()) < 1e-13
+
+
+def test_d3q19_shear_wave_decay_rate(orc):
+    """u_x = U sin(2 pi z / N) decays as exp(-nu k^2 t), nu = (tau - 1/2)/3,
+    to the lattice's O(k^2) corrections (within 1%)."""
+    N, U, tau, steps = 32, 1e-4, 0.8, 300
+    z = np.arange(N)
+    shape = (N, 2, 2)
+    ux = np.broadcast_to((U * np.sin(2 * np.pi * z / N))[:, None, None], shape).copy()
+    f = orc.init3(np.ones(shape), ux, np.zeros(shape), np.zeros(shape))
+    g = orc.run3(f, steps, tau)
+    amp = orc.moments3(g)["ux"][:, 0, 0]
+    fit = np.sum(amp * np.sin(2 * np.pi * z / N)) / np.sum(np.sin(2 * np.pi * z / N) ** 2)
+    nu, k = (tau - 0.5) / 3.0, 2 * np.pi / N
+    assert abs(fit / U / np.exp(-nu * k * k * steps) - 1.0) < 0.01
+
+
+def test_d3_stencil_is_eq18_on_each_axis(orc):
+    """Along every axis the derivative of sin(k x) has the modified
+    wavenumber of eq. (18): (8/5) sin(k) - (2/5) sin(2k) + (8/105) sin(3k)
+    - (1/140) sin(4k)."""
+    n = 16
+    k = 2 * np.pi * 3 / n
+    kt = 1.6 * np.sin(k) - 0.4 * np.sin(2 * k) + 8 / 105 * np.sin(3 * k) - np.sin(4 * k) / 140
+    i = np.arange(n)
+    for axis in range(3):
+        shape = [1, 1, 1]
+        shape[2 - axis] = n
+        A = np.broadcast_to(np.sin(k * i).reshape(shape), (n, n, n)).copy()
+        want = np.broadcast_to((kt * np.cos(k * i)).reshape(shape), (n, n, n))
+        np.testing.assert_allclose(orc.d3(A, axis), want, atol=1e-14)
+
+
+def _symbolic_terms3(n, tau, t_n, wt):
+    sp = pytest.importorskip("sympy")
+    x, y, z, t = sp.symbols("x y z t", real=True)
+    k = 2 * sp.pi / n
+    R = sp.Rational
+    rho = 1 + R(2, 100) * sp.cos(k * x + k * z + R(1, 3)) * sp.cos(wt * t)
+    ux = R(2, 100) * sp.sin(k * y - R(1, 2) + wt * t) + R(1, 100) * sp.cos(k * z + k * y)
+    uy = R(15, 1000) * sp.cos(k * x + R(7, 10)) * sp.cos(wt * t) - R(5, 1000) * sp.sin(k * z)
+    uz = R(1, 100) * sp.sin(k * x + k * y + wt * t) + R(4, 1000) * sp.cos(k * y - k * z)
+    Fx = R(3, 10000) * sp.sin(k * y)
+    Fy = R(2, 10000) * sp.sin(k * z) * sp.cos(k * x)
+    Fz = -R(1, 10000) * sp.cos(k * x - k * y)
+    u, F, X = [ux, uy, uz], [Fx, Fy, Fz], [x, y, z]
+    nu = R(1, 3) * (sp.nsimplify(tau) - R(1, 2))
+    p = rho / 3
+    d = lambda e, j: sp.diff(e, X[j])  # noqa: E731
+    eps = sp.LeviCivita
+    R3 = range(3)
+    om = [sum(eps(i, j, kk) * d(u[kk], j) for j in R3 for kk in R3) for i in R3]
+    E = rho * sum(ui * ui for ui in u) / 2
+    Om = sum(o * o for o in om) / 2
+    S = [[d(u[i], j) + d(u[j], i) for j in R3] for i in R3]
+    H = [sum(d(nu * rho * S[i][j], j) for j in R3) / rho for i in R3]
+    T = [
+        sp.diff(E, t),
+        -sum(d(E * u[j], j) for j in R3),
+        -sum(u[i] * d(p, i) for i in R3),
+        sum(u[i] * F[i] for i in R3),
+        -sum(nu * rho * S[i][j] * d(u[i], j) for i in R3 for j in R3),
+        sum(d(nu * rho * u[i] * S[i][j], j) for i in R3 for j in R3),
+        sp.diff(Om, t),
+        -sum(d(Om * u[j], j) for j in R3),
+        -Om * sum(d(u[j], j) for j in R3),
+        sum(om[i] * eps(i, j, kk) * d(F[kk] / rho, j) for i in R3 for j in R3 for kk in R3),
+        sum(H[i] * eps(i, j, kk) * d(om[kk], j) for i in R3 for j in R3 for kk in R3),
+        sum(d(eps(i, j, kk) * om[i] * H[kk], j) for i in R3 for j in R3 for kk in R3),
+        sum(om[i] * om[j] * d(u[i], j) for i in R3 for j in R3),
+    ]
+    xs = np.arange(n, dtype=float)
+    ZZ, YY, XX = np.meshgrid(xs, xs, xs, indexing="ij")
+
+    def ev(e, tt):
+        fn = sp.lambdify((x, y, z, t), e, "numpy")
+        return np.broadcast_to(np.asarray(fn(XX, YY, ZZ, tt), dtype=float), XX.shape).copy()
+
+    fields = {name: [ev(e, t_n - m) for m in range(3)]
+              for name, e in (("rho", rho), ("ux", ux), ("uy", uy), ("uz", uz))}
+    return [ev(e, t_n) for e in T], fields, [ev(e, t_n) for e in F]
+
+
+def test_terms3_match_symbolic_continuum(orc):
+    """Every discrete 3D term (eq. 18 stencils, eq. 17 in time) matches the
+    exact continuum term of the general index forms on a smooth 3D field to
+    the schemes' truncation error, vortex stretching included."""
+    n, tau, wt, t_n = 48, 0.58, 2e-3, 10.0
+    exact, fl, F = _symbolic_terms3(n, tau, t_n, wt)
+    got = orc.terms3(tau, fl["rho"], fl["ux"], fl["uy"], fl["uz"], *F)
+    for q in range(13):
+        scale = max(np.max(np.abs(exact[q])), 1e-300)
+        tol = 1e-5 if q in (0, 6) else 5e-7
+        err = np.max(np.abs(got[q] - exact[q])) / scale
+        assert err < tol, (orc.TERM_NAMES[q], err)
+    assert np.max(np.abs(exact[12])) > 0.1 * np.max(np.abs(exact[8]))  # stretching is there
+
+
+def test_terms3_divergence_terms_vanish_on_whole_domain(orc):
+    n = 12
+    rho3 = [1 + _smooth3(n, 10 + m, 0.01) for m in range(3)]
+    u3 = [[_smooth3(n, 20 + 3 * m + c, 0.03) for m in range(3)] for c in range(3)]
+    F = [_smooth3(n, 40 + c, 1e-4) for c in range(3)]
+    T = orc.terms3(0.55, rho3, u3[0], u3[1], u3[2], *F)
+    for q in (1, 5, 7, 11):
+        assert abs(T[q].mean()) < 1e-14 * np.max(np.abs(T[q])), orc.TERM_NAMES[q]
+    assert np.max(np.abs(T[12])) > 0
+
+
+def test_box_mean3_brute_force(orc):
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((5, 4, 6))
+    nz, ny, nx = A.shape
+    for L in (1, 2, 4):
+        for (x0, y0, z0) in [(0, 0, 0), (5, 3, 4), (2, 1, 3), (4, 0, 1)]:
+            ref = np.roll(np.roll(np.roll(A, -z0, 0), -y0, 1), -x0, 2)[:L, :L, :L].mean()
+            assert abs(orc.box_mean3(A, x0, y0, z0, L) - ref) < 1e-14
+
+
+def test_balance_stats3_all_origins_mean_is_global(orc):
+    n = 6
+    T = np.stack([_smooth3(n, 50 + q, 1.0) + 0.1 * q for q in range(13)])
+    st, pb = orc.balance_stats3(T, [1, 2, 6, 7], per_box=True)
+    for iL in range(3):
+        np.testing.assert_allclose(st[iL, 2:, 0], T.reshape(13, -1).mean(axis=1), atol=5e-14)
+    assert np.all(np.isnan(st[3]))
+    assert np.all(np.abs(st[2, 2:, 1]) < 1e-14)
