@@ -46,6 +46,19 @@ class _MemberCfg(ctypes.Structure):
                 ("collision", ctypes.c_int), ("Cs", ctypes.c_double)]
 
 
+class _MemberCfg3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("force_kind", ctypes.c_int), ("kf", ctypes.c_int), ("F0", ctypes.c_double),
+                ("alpha", ctypes.c_double)]
+
+
+class _Config3(ctypes.Structure):
+    _fields_ = [("n_members", ctypes.c_int), ("members", ctypes.POINTER(_MemberCfg3)),
+                ("precision", ctypes.c_int), ("diag_every", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
 class _Config(ctypes.Structure):
     _fields_ = [("n_members", ctypes.c_int), ("members", ctypes.POINTER(_MemberCfg)),
                 ("precision", ctypes.c_int), ("storage", ctypes.c_int),
@@ -89,6 +102,17 @@ def load_library(path: str = LIB_PATH):
         "lbm_adjoint_step": ([P, I, P, P, P, D, I, I, I, P, P], I),
         "lbm_objective_accumulate": ([P, I, D, I, I, I, P], I),
         "lbm_last_error": ([P], ctypes.c_char_p),
+        "lbm3d_workspace_size": ([ctypes.POINTER(_Config3), ctypes.POINTER(S)], I),
+        "lbm3d_create": ([ctypes.POINTER(_Config3), P, S, ctypes.POINTER(P)], I),
+        "lbm3d_destroy": ([P], I),
+        "lbm3d_init_fields": ([P, I, P, P, P, P, I], I),
+        "lbm3d_step": ([P, I], I),
+        "lbm3d_time": ([P], ctypes.c_longlong),
+        "lbm3d_get_populations": ([P, I, P, I], I),
+        "lbm3d_set_populations": ([P, I, P, I], I),
+        "lbm3d_record_snapshot": ([P], I),
+        "lbm3d_subvolume_balance": ([P, I, P, I, P, P, P, P], I),
+        "lbm3d_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -395,3 +419,114 @@ def workspace_size(members: Sequence[Member], precision: int = 32, diag_every: i
     if rc != LBM_OK:
         raise LBMError(rc, lib.lbm_last_error(None).decode())
     return n.value
+
+
+@dataclass
+class Member3:
+    """One member of the three-dimensional extension: an nx x ny x nz doubly
+    periodic D3Q19 grid, relaxation time tau, reference density rho0, the
+    cyclic Kolmogorov force F0 (sin(2 pi kf y/ny), sin(2 pi kf z/nz),
+    sin(2 pi kf x/nx)) when force_kind == 1, drag alpha."""
+    nx: int
+    ny: int
+    nz: int
+    tau: float
+    rho0: float = 1.0
+    force_kind: int = 0
+    kf: int = 0
+    F0: float = 0.0
+    alpha: float = 0.0
+
+    def c(self) -> _MemberCfg3:
+        return _MemberCfg3(self.nx, self.ny, self.nz, self.tau, self.rho0, self.force_kind,
+                           self.kf, self.F0, self.alpha)
+
+
+class Lattice3D:
+    """Handle over D3Q19 members (include/lbm3d.h): FP32 deviation or FP64
+    storage, workspace in one torch uint8 CUDA tensor, work on ``stream``."""
+
+    def __init__(self, members: Sequence[Member3], precision: int = 32, diag_every: int = 0,
+                 stream=None, device=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.members = list(members)
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._arr = (_MemberCfg3 * len(self.members))(*[m.c() for m in self.members])
+        self._cfg = _Config3(len(self.members), self._arr, precision, diag_every,
+                             ctypes.c_void_p(self.stream.cuda_stream))
+        n = ctypes.c_size_t()
+        self._check(self.lib.lbm3d_workspace_size(ctypes.byref(self._cfg), ctypes.byref(n)))
+        self.workspace = torch.empty(n.value + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self._check(self.lib.lbm3d_create(ctypes.byref(self._cfg), ctypes.c_void_p(aligned),
+                                              n.value, ctypes.byref(h)))
+        self.h = h
+
+    def _check(self, rc: int):
+        if rc != LBM_OK:
+            msg = self.lib.lbm3d_last_error(getattr(self, "h", None)).decode()
+            raise LBMError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.lbm3d_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shape(self, m):
+        M = self.members[m]
+        return M.nz, M.ny, M.nx
+
+    def init_fields(self, member: int, rho, ux, uy, uz):
+        """f(x, 0) = f_eq(rho, u) from host arrays [nz, ny, nx]."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy, uz)]
+        self._check(self.lib.lbm3d_init_fields(self.h, member, *[_ptr(a) for a in arrs], 0))
+
+    def step(self, nsteps: int = 1):
+        self._check(self.lib.lbm3d_step(self.h, int(nsteps)))
+
+    @property
+    def time(self) -> int:
+        return int(self.lib.lbm3d_time(self.h))
+
+    def record_snapshot(self):
+        self._check(self.lib.lbm3d_record_snapshot(self.h))
+
+    def get_populations_host(self, member: int) -> np.ndarray:
+        out = np.empty((19,) + self._shape(member))
+        self._check(self.lib.lbm3d_get_populations(self.h, member, _ptr(out), 0))
+        return out
+
+    def set_populations(self, member: int, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        self._check(self.lib.lbm3d_set_populations(self.h, member, _ptr(f), 0))
+
+    def subvolume_balance(self, member: int, Ls, origins=None, per_box: bool = False):
+        """Statistics [nL, 15, 2] over L^3 boxes (every periodic origin, or one
+        [n, 3] array of (x0, y0, z0) per size); with ``per_box`` also the
+        device tensor [rows, 15]."""
+        Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+        nz, ny, nx = self._shape(member)
+        o = counts = None
+        if origins is not None:
+            per = [np.ascontiguousarray(a, dtype=np.int32).reshape(-1, 3) for a in origins]
+            counts = np.array([p.shape[0] for p in per], dtype=np.int32)
+            o = np.ascontiguousarray(np.concatenate(per, 0))
+        rows = len(Ls) * nx * ny * nz if o is None else int(counts.sum())
+        stats = np.empty((len(Ls), NQUANT, 2))
+        pb = None
+        if per_box:
+            pb = self._torch.empty((rows, NQUANT), dtype=self._torch.float64, device=self.device)
+        self._check(self.lib.lbm3d_subvolume_balance(self.h, member, _ptr(Ls), len(Ls), _ptr(o),
+                                                     _ptr(counts), _ptr(stats), _ptr(pb)))
+        return (stats, pb) if per_box else stats

@@ -1,0 +1,978 @@
+// Three-dimensional extension (include/lbm3d.h): D3Q19 BGK stream-collide
+// with exact-difference forcing (eq. (1), eq. (2), Sec. 3 of Tauzin et al.
+// 2018) and the sub-volume energy/enstrophy balance of eqs. (8)-(13) in the
+// general index forms, with vortex stretching, over L x L x L boxes.
+//
+// Storage: double buffer, pull layout pop[b][l][z][y][x] (x fastest): the
+// pre-collision f_l(x, n) = pop[cur][l][x - c_l].  FP32 stores deviations
+// g = f - t rho0, FP64 f.  One thread per cell; one launch per member.
+//
+// Diagnostic (FP64 arithmetic): snapshots (rho, j_x, j_y, j_z) of the levels
+// n, n-1, n-2 (FP32 storage: compensated sums of the FP32 populations, so
+// the FP64 value of the stored state); four term passes; 13 exact 64-bit
+// fixed-point summed-volume tables (scale 2^e per field with N max|T| 2^e <
+// 2^62); 8-corner box sums in modular integer arithmetic; FP64 statistics
+// with fixed-order reductions.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm3d.h"
+
+namespace {
+
+constexpr int kQ3 = 19;
+__host__ __device__ constexpr int c3x(int l) {
+  return (l == 1 || l == 7 || l == 9 || l == 11 || l == 13) ? 1
+         : (l == 2 || l == 8 || l == 10 || l == 12 || l == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int c3y(int l) {
+  return (l == 3 || l == 7 || l == 10 || l == 15 || l == 17) ? 1
+         : (l == 4 || l == 8 || l == 9 || l == 16 || l == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int c3z(int l) {
+  return (l == 5 || l == 11 || l == 14 || l == 15 || l == 18) ? 1
+         : (l == 6 || l == 12 || l == 13 || l == 16 || l == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr double w3(int l) {
+  return l == 0 ? 1.0 / 3.0 : (l <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+struct M3 {
+  int nx, ny, nz, force_kind, kf, pad;
+  double tau, omega, rho0, F0, alpha, nu;
+  float rho0_f, omega_f, alpha_f, F0_f;
+  size_t N;
+  void *pop[2];
+  double *snap;  // ring [3 slots][4][N]: rho, jx, jy, jz
+  void *ftab;    // force kind 1: F_x(y) [ny], F_y(z) [nz], F_z(x) [nx] (storage precision)
+  double *ftab64;  // the same in FP64
+};
+
+__device__ __forceinline__ int wrp(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__device__ __forceinline__ size_t cell(const M3 &M, int x, int y, int z) {
+  return ((size_t)z * M.ny + y) * M.nx + x;
+}
+
+// External force of the cyclic Kolmogorov kind at (x, y, z), from the
+// per-axis tables (zero tables for force kind 0).
+template <typename T>
+__device__ __forceinline__ void force3(const M3 &M, const T *tab, int x, int y, int z, T &fx,
+                                       T &fy, T &fz) {
+  fx = tab[y];
+  fy = tab[M.ny + z];
+  fz = tab[M.ny + M.nz + x];
+}
+
+// BGK + EDM collision of one cell in storage form (FP32: deviations).
+template <typename T>
+__device__ __forceinline__ void collide3(T v[kQ3], T rho0, T om, T Fex, T Fey, T Fez, T alpha) {
+  T dr = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+  for (int l = 0; l < kQ3; ++l) {
+    dr += v[l];
+    jx += (T)c3x(l) * v[l];
+    jy += (T)c3y(l) * v[l];
+    jz += (T)c3z(l) * v[l];
+  }
+  const T rho = sizeof(T) == 4 ? rho0 + dr : dr;
+  const T drho = sizeof(T) == 4 ? dr : dr - rho0;  // FP64: rho0 passed as 0
+  const T ir = T(1) / rho;
+  const T ux = jx * ir, uy = jy * ir, uz = jz * ir;
+  const T Fx = Fex - alpha * jx, Fy = Fey - alpha * jy, Fz = Fez - alpha * jz;
+  const T dux = Fx * ir, duy = Fy * ir, duz = Fz * ir;
+  const T usq = ux * ux + uy * uy + uz * uz;
+  const T dsq = dux * (T(2) * ux + dux) + duy * (T(2) * uy + duy) + duz * (T(2) * uz + duz);
+#pragma unroll
+  for (int l = 0; l < kQ3; ++l) {
+    const T t = (T)w3(l);
+    const T cu = (T)c3x(l) * ux + (T)c3y(l) * uy + (T)c3z(l) * uz;
+    const T cd = (T)c3x(l) * dux + (T)c3y(l) * duy + (T)c3z(l) * duz;
+    T eq;
+    if constexpr (sizeof(T) == 4)
+      eq = t * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+    else
+      eq = t * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
+    const T Fl = t * rho * (T(3) * cd + T(4.5) * cd * (T(2) * cu + cd) - T(1.5) * dsq);
+    v[l] = v[l] - om * (v[l] - eq) + Fl;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k3_step(const M3 *__restrict__ ms, int member, int cur) {
+  const M3 &M = ms[member];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y,
+            z = blockIdx.z;
+  if (x >= M.nx || y >= M.ny) return;
+  const T *src = static_cast<const T *>(M.pop[cur]);
+  T *dst = static_cast<T *>(M.pop[cur ^ 1]);
+  const size_t N = M.N;
+  T v[kQ3];
+#pragma unroll
+  for (int l = 0; l < kQ3; ++l)
+    v[l] = src[(size_t)l * N + cell(M, wrp(x - c3x(l), M.nx), wrp(y - c3y(l), M.ny),
+                                    wrp(z - c3z(l), M.nz))];
+  T fx, fy, fz;
+  force3<T>(M, static_cast<const T *>(M.ftab), x, y, z, fx, fy, fz);
+  if constexpr (sizeof(T) == 4)
+    collide3<float>(v, M.rho0_f, M.omega_f, fx, fy, fz, M.alpha_f);
+  else
+    collide3<double>(v, 0.0, M.omega, fx, fy, fz, M.alpha);
+  const size_t c = cell(M, x, y, z);
+#pragma unroll
+  for (int l = 0; l < kQ3; ++l) dst[(size_t)l * N + c] = v[l];
+}
+
+template <typename T>
+__global__ void k3_init(const M3 *__restrict__ ms, int member, int cur, const double *rho,
+                        const double *ux, const double *uy, const double *uz) {
+  const M3 &M = ms[member];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y,
+            z = blockIdx.z;
+  if (x >= M.nx || y >= M.ny) return;
+  const size_t c = cell(M, x, y, z);
+  const double r = rho[c], u = ux[c], v = uy[c], w = uz[c], uu = u * u + v * v + w * w;
+  T *dst = static_cast<T *>(M.pop[cur]);
+#pragma unroll
+  for (int l = 0; l < kQ3; ++l) {
+    const double cu = c3x(l) * u + c3y(l) * v + c3z(l) * w;
+    const double feq = w3(l) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    // the population at x is stored at its pull origin x - c_l
+    const size_t o = cell(M, wrp(x - c3x(l), M.nx), wrp(y - c3y(l), M.ny), wrp(z - c3z(l), M.nz));
+    dst[(size_t)l * M.N + o] = (T)(sizeof(T) == 4 ? feq - w3(l) * M.rho0 : feq);
+  }
+}
+
+// Public <-> storage (to_public: storage -> f[19][N] doubles).
+template <typename T>
+__global__ void k3_copy(const M3 *__restrict__ ms, int member, int cur, double *f, int to_public) {
+  const M3 &M = ms[member];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y,
+            z = blockIdx.z;
+  if (x >= M.nx || y >= M.ny) return;
+  const size_t c = cell(M, x, y, z);
+  T *st = static_cast<T *>(M.pop[cur]);
+#pragma unroll
+  for (int l = 0; l < kQ3; ++l) {
+    const size_t o = (size_t)l * M.N +
+                     cell(M, wrp(x - c3x(l), M.nx), wrp(y - c3y(l), M.ny), wrp(z - c3z(l), M.nz));
+    const double off = sizeof(T) == 4 ? w3(l) * M.rho0 : 0.0;
+    if (to_public)
+      f[(size_t)l * M.N + c] = (double)st[o] + off;
+    else
+      st[o] = (T)(f[(size_t)l * M.N + c] - off);
+  }
+}
+
+__device__ __forceinline__ void two_sum3(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (rho, j) of the current state into snapshot slot `slot` (FP64; FP32
+// storage by compensated FP32 sums of the stored deviations).
+template <typename T>
+__global__ void k3_snapshot(const M3 *__restrict__ ms, int member, int cur, int slot) {
+  const M3 &M = ms[member];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y,
+            z = blockIdx.z;
+  if (x >= M.nx || y >= M.ny) return;
+  const T *st = static_cast<const T *>(M.pop[cur]);
+  T v[kQ3];
+#pragma unroll
+  for (int l = 0; l < kQ3; ++l)
+    v[l] = st[(size_t)l * M.N + cell(M, wrp(x - c3x(l), M.nx), wrp(y - c3y(l), M.ny),
+                                     wrp(z - c3z(l), M.nz))];
+  double out[4];
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float s = 0.f, e = 0.f;
+#pragma unroll
+      for (int l = 0; l < kQ3; ++l) {
+        const int c = q == 0 ? 1 : (q == 1 ? c3x(l) : (q == 2 ? c3y(l) : c3z(l)));
+        if (c == 0) continue;
+        float d;
+        two_sum3(s, c > 0 ? v[l] : -v[l], s, d);
+        e += d;
+      }
+      out[q] = (double)s + (double)e;
+    }
+    out[0] += M.rho0;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = 0.0;
+#pragma unroll
+    for (int l = 0; l < kQ3; ++l) {
+      out[0] += v[l];
+      out[1] += c3x(l) * v[l];
+      out[2] += c3y(l) * v[l];
+      out[3] += c3z(l) * v[l];
+    }
+  }
+  double *d = M.snap + (size_t)slot * 4 * M.N;
+  const size_t c = cell(M, x, y, z);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) d[(size_t)q * M.N + c] = out[q];
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostic (FP64)
+// ---------------------------------------------------------------------------
+
+// scratch field indices (each N doubles)
+enum F3 {
+  UX0, UY0, UZ0, UX1, UY1, UZ1, UX2, UY2, UZ2, R0, DR, FRX, FRY, FRZ, WX, WY, WZ,
+  EUX, EUY, EUZ, CUX, CUY, CUZ, OUX, OUY, OUZ, SXX, SXY, SXZ, SYY, SYZ, SZZ, HWX, HWY, HWZ,
+  T3,  // T3 .. T3 + 12: the 13 term fields
+  NF3 = T3 + 13
+};
+
+struct Diag3 {
+  const M3 *m;
+  const double *s0, *s1, *s2;  // snapshots of n, n-1, n-2
+  double *f;                   // NF3 fields of N doubles, then the tables
+};
+
+// Eq. (18) along axis a (0 x, 1 y, 2 z), periodic.
+__device__ __forceinline__ double D3(const M3 &M, const double *A, int x, int y, int z, int a) {
+  const double cf[4] = {0.8, -0.2, 4.0 / 105.0, -1.0 / 280.0};
+  double s = 0.0;
+#pragma unroll
+  for (int k = 1; k <= 4; ++k) {
+    size_t p, q;
+    if (a == 0) {
+      p = cell(M, wrp(x + k, M.nx) % M.nx, y, z);
+      q = cell(M, (wrp(x - k, M.nx) + M.nx) % M.nx, y, z);
+    } else if (a == 1) {
+      p = cell(M, x, wrp(y + k, M.ny) % M.ny, z);
+      q = cell(M, x, (wrp(y - k, M.ny) + M.ny) % M.ny, z);
+    } else {
+      p = cell(M, x, y, wrp(z + k, M.nz) % M.nz);
+      q = cell(M, x, y, (wrp(z - k, M.nz) + M.nz) % M.nz);
+    }
+    s += cf[k - 1] * (A[p] - A[q]);
+  }
+  return s;
+}
+
+#define D3CELL                                                                   \
+  const M3 &M = *J.m;                                                            \
+  const int x = blockIdx.x * blockDim.x + threadIdx.x,                           \
+            y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;           \
+  if (x >= M.nx || y >= M.ny) return;                                            \
+  const size_t N = M.N, c = cell(M, x, y, z);                                    \
+  auto F = [&](int k) { return J.f + (size_t)k * N; };
+
+// Pass 0: velocities u = (j + F/2)/rho at the three levels, rho, rho - rho0,
+// F/rho; LHS^E (eq. 17) and RHS^{E,3} = u . F.
+__global__ void k3_prep(Diag3 J) {
+  D3CELL;
+  double fx, fy, fz;
+  force3<double>(M, M.ftab64, x, y, z, fx, fy, fz);
+  const double *S[3] = {J.s0, J.s1, J.s2};
+  double E[3], u0[3] = {0, 0, 0}, F0v[3] = {0, 0, 0};
+  for (int m = 0; m < 3; ++m) {
+    const double r = S[m][c], jx = S[m][N + c], jy = S[m][2 * N + c], jz = S[m][3 * N + c];
+    const double Fx = fx - M.alpha * jx, Fy = fy - M.alpha * jy, Fz = fz - M.alpha * jz;
+    const double u = (jx + 0.5 * Fx) / r, v = (jy + 0.5 * Fy) / r, w = (jz + 0.5 * Fz) / r;
+    F(UX0 + 3 * m)[c] = u;
+    F(UY0 + 3 * m)[c] = v;
+    F(UZ0 + 3 * m)[c] = w;
+    E[m] = 0.5 * r * (u * u + v * v + w * w);
+    if (m == 0) {
+      u0[0] = u;
+      u0[1] = v;
+      u0[2] = w;
+      F0v[0] = Fx;
+      F0v[1] = Fy;
+      F0v[2] = Fz;
+      F(R0)[c] = r;
+      F(DR)[c] = r - M.rho0;
+      F(FRX)[c] = Fx / r;
+      F(FRY)[c] = Fy / r;
+      F(FRZ)[c] = Fz / r;
+    }
+  }
+  F(T3 + 0)[c] = 1.5 * E[0] - 2.0 * E[1] + 0.5 * E[2];
+  F(T3 + 3)[c] = u0[0] * F0v[0] + u0[1] * F0v[1] + u0[2] * F0v[2];
+}
+
+// Pass 1: velocity gradients G_ij = d_j u_i at n, vorticity at the three
+// levels (LHS^Omega), S, RHS^{E,2}, RHS^{E,4}, RHS^{O,2}, RHS^{O,3},
+// RHS^{O,6}, and the fluxes of pass 2.
+__global__ void k3_grad(Diag3 J) {
+  D3CELL;
+  double G[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) G[i][j] = D3(M, F(UX0 + i), x, y, z, j);
+  double Om[3], w0[3];
+  w0[0] = G[2][1] - G[1][2];
+  w0[1] = G[0][2] - G[2][0];
+  w0[2] = G[1][0] - G[0][1];
+  Om[0] = 0.5 * (w0[0] * w0[0] + w0[1] * w0[1] + w0[2] * w0[2]);
+  for (int m = 1; m < 3; ++m) {
+    const double *U = F(UX0 + 3 * m), *V = F(UY0 + 3 * m), *W = F(UZ0 + 3 * m);
+    const double wx = D3(M, W, x, y, z, 1) - D3(M, V, x, y, z, 2);
+    const double wy = D3(M, U, x, y, z, 2) - D3(M, W, x, y, z, 0);
+    const double wz = D3(M, V, x, y, z, 0) - D3(M, U, x, y, z, 1);
+    Om[m] = 0.5 * (wx * wx + wy * wy + wz * wz);
+  }
+  F(T3 + 6)[c] = 1.5 * Om[0] - 2.0 * Om[1] + 0.5 * Om[2];
+  const double u[3] = {F(UX0)[c], F(UY0)[c], F(UZ0)[c]}, r = F(R0)[c];
+  const double nr = M.nu * r;
+  double S[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) S[i][j] = G[i][j] + G[j][i];
+  double gp = 0.0, sd = 0.0, st = 0.0;
+  for (int i = 0; i < 3; ++i) gp += u[i] * D3(M, F(DR), x, y, z, i) / 3.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      sd += S[i][j] * G[i][j];
+      st += w0[i] * w0[j] * G[i][j];
+    }
+  const double div = G[0][0] + G[1][1] + G[2][2];
+  double cf = 0.0;  // omega . curl(F / rho)
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    cf += w0[i] * (D3(M, F(FRX + k), x, y, z, j) - D3(M, F(FRX + j), x, y, z, k));
+  }
+  F(T3 + 2)[c] = -gp;
+  F(T3 + 4)[c] = -nr * sd;
+  F(T3 + 8)[c] = -Om[0] * div;
+  F(T3 + 9)[c] = cf;
+  F(T3 + 12)[c] = st;
+  const double E0 = 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  for (int j = 0; j < 3; ++j) {
+    F(EUX + j)[c] = E0 * u[j];
+    F(OUX + j)[c] = Om[0] * u[j];
+    F(CUX + j)[c] = nr * (u[0] * S[0][j] + u[1] * S[1][j] + u[2] * S[2][j]);
+    F(WX + j)[c] = w0[j];
+  }
+  F(SXX)[c] = nr * S[0][0];
+  F(SXY)[c] = nr * S[0][1];
+  F(SXZ)[c] = nr * S[0][2];
+  F(SYY)[c] = nr * S[1][1];
+  F(SYZ)[c] = nr * S[1][2];
+  F(SZZ)[c] = nr * S[2][2];
+}
+
+// Pass 2: RHS^{E,1}, RHS^{E,5}, RHS^{O,1}; H_i = d_j(nu rho S_ij)/rho;
+// RHS^{O,4} = H . curl(omega); H x omega for pass 3.
+__global__ void k3_flux(Diag3 J) {
+  D3CELL;
+  double e1 = 0.0, e5 = 0.0, o1 = 0.0;
+  for (int j = 0; j < 3; ++j) {
+    e1 -= D3(M, F(EUX + j), x, y, z, j);
+    e5 += D3(M, F(CUX + j), x, y, z, j);
+    o1 -= D3(M, F(OUX + j), x, y, z, j);
+  }
+  const int sidx[3][3] = {{SXX, SXY, SXZ}, {SXY, SYY, SYZ}, {SXZ, SYZ, SZZ}};
+  const double r = F(R0)[c];
+  double H[3];
+  for (int i = 0; i < 3; ++i) {
+    double h = 0.0;
+    for (int j = 0; j < 3; ++j) h += D3(M, F(sidx[i][j]), x, y, z, j);
+    H[i] = h / r;
+  }
+  double o4 = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    o4 += H[i] * (D3(M, F(WX + k), x, y, z, j) - D3(M, F(WX + j), x, y, z, k));
+  }
+  const double w[3] = {F(WX)[c], F(WY)[c], F(WZ)[c]};
+  F(T3 + 1)[c] = e1;
+  F(T3 + 5)[c] = e5;
+  F(T3 + 7)[c] = o1;
+  F(T3 + 10)[c] = o4;
+  for (int j = 0; j < 3; ++j) {
+    const int a = (j + 1) % 3, b = (j + 2) % 3;
+    F(HWX + j)[c] = H[a] * w[b] - H[b] * w[a];
+  }
+}
+
+// Pass 3: RHS^{O,5} = div(H x omega).
+__global__ void k3_curl(Diag3 J) {
+  D3CELL;
+  double s = 0.0;
+  for (int j = 0; j < 3; ++j) s += D3(M, F(HWX + j), x, y, z, j);
+  F(T3 + 11)[c] = s;
+}
+
+// Summed-volume tables: table k at tab + k * (nx+1)(ny+1)(nz+1), exclusive
+// prefix P(x, y, z) over x' < x, y' < y, z' < z (the zero planes included).
+__device__ __forceinline__ size_t tidx(const M3 &M, int x, int y, int z) {
+  return ((size_t)z * (M.ny + 1) + y) * (M.nx + 1) + x;
+}
+
+// Largest |T_k| of each field: one CTA per field, fixed-order max.
+__global__ void k3_absmax(Diag3 J, double *maxes) {
+  const M3 &M = *J.m;
+  const int k = blockIdx.x;
+  const double *A = J.f + (size_t)(T3 + k) * M.N;
+  double m = 0.0;
+  for (size_t i = threadIdx.x; i < M.N; i += blockDim.x) m = fmax(m, fabs(A[i]));
+  __shared__ double sh[256];
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // scale 2^e with N max |T_k| 2^e < 2^62: every partial sum fits int64
+    const double mx = sh[0];
+    int e = 0;
+    if (mx > 0.0) {
+      int ex, nbits = 0;
+      frexp(mx, &ex);  // mx < 2^ex
+      while (((size_t)1 << nbits) < M.N) ++nbits;
+      e = 62 - nbits - ex;
+      if (e > 1000) e = 1000;
+    }
+    maxes[k] = ldexp(1.0, e);
+    maxes[16 + k] = (double)e;
+  }
+}
+
+// Quantised values scanned along x: one thread per (y, z, field) row.
+__global__ void k3_scan_x(Diag3 J, const double *scales, long long *tab) {
+  const M3 &M = *J.m;
+  const int y = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y, k = blockIdx.z;
+  if (y > M.ny || z > M.nz) return;
+  const size_t ts = (size_t)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
+  long long *t = tab + (size_t)k * ts;
+  if (y == 0 || z == 0) {  // zero planes
+    for (int x = 0; x <= M.nx; ++x) t[tidx(M, x, y, z)] = 0;
+    return;
+  }
+  const double *A = J.f + (size_t)(T3 + k) * M.N;
+  const double sc = scales[k];
+  long long acc = 0;
+  t[tidx(M, 0, y, z)] = 0;
+  for (int x = 0; x < M.nx; ++x) {
+    acc += __double2ll_rn(A[cell(M, x, y - 1, z - 1)] * sc);
+    t[tidx(M, x + 1, y, z)] = acc;
+  }
+}
+
+// Prefix along y (axis 1) or z (axis 2) of the tables in place: one thread
+// per (x, other coordinate, field) line.
+__global__ void k3_scan_yz(Diag3 J, long long *tab, int axis) {
+  const M3 &M = *J.m;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, o = blockIdx.y, k = blockIdx.z;
+  if (x > M.nx) return;
+  const int no = axis == 1 ? M.nz : M.ny, nl = axis == 1 ? M.ny : M.nz;
+  if (o > no) return;
+  const size_t ts = (size_t)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
+  long long *t = tab + (size_t)k * ts;
+  long long acc = 0;
+  for (int i = 1; i <= nl; ++i) {
+    const size_t p = axis == 1 ? tidx(M, x, i, o) : tidx(M, x, o, i);
+    acc += t[p];
+    t[p] = acc;
+  }
+}
+
+// Exclusive prefix at (x, y, z) for 0 <= x < 2 nx etc. (periodic extension),
+// modular arithmetic.
+__device__ __forceinline__ unsigned long long P3(const M3 &M, const long long *t, int x, int y,
+                                                 int z) {
+  unsigned long long v = 0;
+  const int qx = x > M.nx, qy = y > M.ny, qz = z > M.nz;
+  const int xm = x - qx * M.nx, ym = y - qy * M.ny, zm = z - qz * M.nz;
+  for (int a = 0; a <= qx; ++a)
+    for (int b = 0; b <= qy; ++b)
+      for (int d = 0; d <= qz; ++d)
+        v += (unsigned long long)t[tidx(M, a ? M.nx : xm, b ? M.ny : ym, d ? M.nz : zm)];
+  return v;
+}
+
+__device__ __forceinline__ double delta3(const double *v, int nrhs) {
+  double sum = 0.0, mx = 0.0;
+  for (int i = 1; i <= nrhs; ++i) {
+    sum += v[i];
+    mx = fmax(mx, fabs(v[i]));
+  }
+  const double num = fabs(sum - v[0]);
+  if (mx == 0.0) return num == 0.0 ? 0.0 : INFINITY;
+  return num / mx;
+}
+
+constexpr int kQS3 = 30;  // per size: sums and sums of squares of 15 quantities
+
+// One thread per box: the 13 box means (exact integer sums), delta^E,
+// delta^Omega; CTA partial sums (fixed order) of the 15 quantities and
+// their squares, deviations from the field means.
+__global__ void __launch_bounds__(256) k3_query(Diag3 J, const long long *tab,
+                                                const double *scales, const double *means,
+                                                int L, int nb, const int *origins,
+                                                double *partials, double *per_box) {
+  const M3 &M = *J.m;
+  const size_t ts = (size_t)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
+  const double area = (double)L * L * L;
+  double acc[kQS3];
+  for (int q = 0; q < kQS3; ++q) acc[q] = 0.0;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    int x0, y0, z0;
+    if (origins) {
+      x0 = origins[3 * b];
+      y0 = origins[3 * b + 1];
+      z0 = origins[3 * b + 2];
+    } else {
+      x0 = b % M.nx;
+      y0 = (b / M.nx) % M.ny;
+      z0 = b / (M.nx * M.ny);
+    }
+    double v[15];
+    for (int k = 0; k < 13; ++k) {
+      const long long *t = tab + (size_t)k * ts;
+      const int X0 = x0, X1 = x0 + L, Y0 = y0, Y1 = y0 + L, Z0 = z0, Z1 = z0 + L;
+      const unsigned long long s =
+          P3(M, t, X1, Y1, Z1) - P3(M, t, X0, Y1, Z1) - P3(M, t, X1, Y0, Z1) - P3(M, t, X1, Y1, Z0) +
+          P3(M, t, X0, Y0, Z1) + P3(M, t, X0, Y1, Z0) + P3(M, t, X1, Y0, Z0) - P3(M, t, X0, Y0, Z0);
+      v[2 + k] = (double)(long long)s / scales[k] / area;
+    }
+    v[0] = delta3(v + 2, 5);
+    v[1] = delta3(v + 8, 6);
+    if (per_box)
+      for (int q = 0; q < 15; ++q) per_box[(size_t)b * 15 + q] = v[q];
+    for (int q = 0; q < 15; ++q) {
+      const double d = v[q] - (q < 2 ? 0.0 : means[q - 2]);
+      acc[2 * q] += d;
+      acc[2 * q + 1] += d * d;
+    }
+  }
+  __shared__ double sh[kQS3][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < kQS3; ++q) {
+    double a = acc[q];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[q][wid] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < kQS3) {
+    double a = 0.0;
+    for (int w = 0; w < 8; ++w) a += sh[threadIdx.x][w];
+    partials[(size_t)blockIdx.x * kQS3 + threadIdx.x] = a;
+  }
+}
+
+// Field means (exact table totals) for the deviation sums of the query.
+__global__ void k3_means(Diag3 J, const long long *tab, const double *scales, double *means) {
+  const M3 &M = *J.m;
+  const int k = threadIdx.x;
+  if (k >= 13) return;
+  const size_t ts = (size_t)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
+  means[k] = (double)tab[(size_t)k * ts + tidx(M, M.nx, M.ny, M.nz)] / scales[k] / (double)M.N;
+}
+
+__global__ void k3_stats(const double *partials, int nblocks, const double *means, int nb,
+                         double *stats) {
+  const int q = threadIdx.x;
+  if (q >= 15) return;
+  double s1 = 0.0, s2 = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    s1 += partials[(size_t)b * kQS3 + 2 * q];
+    s2 += partials[(size_t)b * kQS3 + 2 * q + 1];
+  }
+  const double m1 = s1 / nb;
+  stats[2 * q] = (q < 2 ? 0.0 : means[q - 2]) + m1;
+  stats[2 * q + 1] = sqrt(fmax(s2 / nb - m1 * m1, 0.0));
+}
+
+}  // namespace
+
+struct lbm3d_handle {
+  lbm3d_config cfg;
+  std::vector<lbm3d_member_cfg> mcfg;
+  std::vector<M3> hm;
+  M3 *d_m = nullptr;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  int precision = 32;
+  cudaStream_t stream = nullptr;
+  int cur = 0;
+  long long t = 0;
+  long long ring_time[3] = {-1, -1, -1};
+  double *diag = nullptr;  // NF3 fields + tables + partials, largest member
+  size_t diag_doubles = 0;
+  int *d_origins = nullptr;
+  size_t origin_cap = 0;
+  std::string err = "no error";
+};
+
+namespace {
+
+thread_local std::string g_err3 = "no error";
+
+int fail3(lbm3d_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  g_err3 = msg;
+  return code;
+}
+
+#define CK3(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail3(h, LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr size_t kAl = 256;
+size_t al(size_t v) { return (v + kAl - 1) / kAl * kAl; }
+constexpr int kMaxQBlocks3 = 1024;
+
+struct Layout3 {
+  size_t members;
+  std::vector<size_t> pop0, pop1, snap, ftab, ftab64;
+  size_t diag, origins, total, diag_doubles, origin_cap;
+};
+
+int check3(const lbm3d_config *cfg, std::string &err) {
+  if (!cfg || cfg->n_members < 1 || !cfg->members) { err = "need n_members >= 1 and members"; return LBM_ERR_ARG; }
+  if (cfg->precision != 32 && cfg->precision != 64) { err = "precision must be 32 or 64"; return LBM_ERR_ARG; }
+  if (cfg->diag_every < 0) { err = "diag_every must be >= 0"; return LBM_ERR_ARG; }
+  for (int m = 0; m < cfg->n_members; ++m) {
+    const lbm3d_member_cfg &c = cfg->members[m];
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || (long long)c.nx * c.ny * c.nz > (1LL << 28)) { err = "grid out of range"; return LBM_ERR_ARG; }
+    if (!(c.tau > 0.5) || !std::isfinite(c.tau)) { err = "tau must be > 0.5"; return LBM_ERR_ARG; }
+    if (!(c.rho0 > 0.0) || !std::isfinite(c.rho0)) { err = "rho0 must be > 0"; return LBM_ERR_ARG; }
+    if (c.force_kind != 0 && c.force_kind != 1) { err = "force_kind must be 0 or 1"; return LBM_ERR_ARG; }
+    if (!std::isfinite(c.F0) || !std::isfinite(c.alpha)) { err = "F0/alpha not finite"; return LBM_ERR_ARG; }
+  }
+  return LBM_OK;
+}
+
+Layout3 layout3(const lbm3d_config *cfg) {
+  Layout3 L{};
+  size_t off = 0;
+  auto take = [&](size_t b) { size_t o = off; off = al(off + b); return o; };
+  const size_t es = cfg->precision == 32 ? 4 : 8;
+  L.members = take(sizeof(M3) * cfg->n_members);
+  size_t Nmax = 0, Tmax = 0;
+  for (int m = 0; m < cfg->n_members; ++m) {
+    const lbm3d_member_cfg &c = cfg->members[m];
+    const size_t N = (size_t)c.nx * c.ny * c.nz;
+    L.pop0.push_back(take(es * kQ3 * N));
+    L.pop1.push_back(take(es * kQ3 * N));
+    L.snap.push_back(take(8 * 3 * 4 * N));
+    L.ftab.push_back(take(es * (c.nx + c.ny + c.nz)));
+    L.ftab64.push_back(take(8 * (c.nx + c.ny + c.nz)));
+    Nmax = std::max(Nmax, N);
+    Tmax = std::max(Tmax, (size_t)(c.nx + 1) * (c.ny + 1) * (c.nz + 1));
+  }
+  // fields, 13 tables (as int64), scales/means, query partials
+  L.diag_doubles = (size_t)NF3 * Nmax + 13 * Tmax + 80 + (size_t)kMaxQBlocks3 * kQS3;
+  L.diag = take(8 * L.diag_doubles);
+  L.origin_cap = std::max<size_t>(3 * Nmax, (size_t)3 << 20);
+  L.origins = take(4 * L.origin_cap);
+  L.total = off;
+  return L;
+}
+
+dim3 cells3(const lbm3d_member_cfg &c) { return dim3((c.nx + 63) / 64, (c.ny + 3) / 4, c.nz); }
+
+int check_member3(lbm3d_handle *h, int m) {
+  if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (m < 0 || m >= (int)h->mcfg.size()) return fail3(h, LBM_ERR_ARG, "member out of range");
+  return LBM_OK;
+}
+
+bool snap_time3(const lbm3d_handle *h, long long t) {
+  const long long D = h->cfg.diag_every;
+  if (D <= 0) return false;
+  const long long r = t % D;
+  return r == 0 || r == D - 1 || r == D - 2;
+}
+
+int record3(lbm3d_handle *h) {
+  const int slot = (int)(h->t % 3);
+  for (int m = 0; m < (int)h->mcfg.size(); ++m) {
+    if (h->precision == 32)
+      k3_snapshot<float><<<cells3(h->mcfg[m]), dim3(64, 4), 0, h->stream>>>(h->d_m, m, h->cur, slot);
+    else
+      k3_snapshot<double><<<cells3(h->mcfg[m]), dim3(64, 4), 0, h->stream>>>(h->d_m, m, h->cur, slot);
+  }
+  CK3(cudaGetLastError());
+  h->ring_time[slot] = h->t;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm3d_workspace_size(const lbm3d_config *cfg, size_t *bytes) {
+  std::string err;
+  if (int rc = check3(cfg, err)) return fail3(nullptr, rc, err);
+  if (!bytes) return fail3(nullptr, LBM_ERR_ARG, "bytes is NULL");
+  *bytes = layout3(cfg).total;
+  return LBM_OK;
+}
+
+int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_handle **out) {
+  std::string err;
+  if (int rc = check3(cfg, err)) return fail3(nullptr, rc, err);
+  if (!out) return fail3(nullptr, LBM_ERR_ARG, "out is NULL");
+  const Layout3 L = layout3(cfg);
+  if (!workspace || bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % kAl)
+    return fail3(nullptr, LBM_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
+  lbm3d_handle *h = new lbm3d_handle();
+  h->cfg = *cfg;
+  h->mcfg.assign(cfg->members, cfg->members + cfg->n_members);
+  h->cfg.members = h->mcfg.data();
+  h->ws = static_cast<char *>(workspace);
+  h->ws_bytes = bytes;
+  h->precision = cfg->precision;
+  h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  h->d_m = reinterpret_cast<M3 *>(h->ws + L.members);
+  h->diag = reinterpret_cast<double *>(h->ws + L.diag);
+  h->diag_doubles = L.diag_doubles;
+  h->d_origins = reinterpret_cast<int *>(h->ws + L.origins);
+  h->origin_cap = L.origin_cap;
+  const size_t es = cfg->precision == 32 ? 4 : 8;
+  for (int m = 0; m < cfg->n_members; ++m) {
+    const lbm3d_member_cfg &c = h->mcfg[m];
+    M3 M{};
+    M.nx = c.nx;
+    M.ny = c.ny;
+    M.nz = c.nz;
+    M.force_kind = c.force_kind;
+    M.kf = c.kf;
+    M.tau = c.tau;
+    M.omega = 1.0 / c.tau;
+    M.rho0 = c.rho0;
+    M.F0 = c.F0;
+    M.alpha = c.alpha;
+    M.nu = (c.tau - 0.5) / 3.0;
+    M.rho0_f = (float)c.rho0;
+    M.omega_f = (float)(1.0 / c.tau);
+    M.alpha_f = (float)c.alpha;
+    M.F0_f = (float)c.F0;
+    M.N = (size_t)c.nx * c.ny * c.nz;
+    M.pop[0] = h->ws + L.pop0[m];
+    M.pop[1] = h->ws + L.pop1[m];
+    M.snap = reinterpret_cast<double *>(h->ws + L.snap[m]);
+    M.ftab = h->ws + L.ftab[m];
+    M.ftab64 = reinterpret_cast<double *>(h->ws + L.ftab64[m]);
+    h->hm.push_back(M);
+    // force tables: F_x(y), F_y(z), F_z(x)
+    std::vector<double> ft(c.nx + c.ny + c.nz, 0.0);
+    if (c.force_kind == 1) {
+      const double pi = 3.14159265358979323846;
+      for (int y = 0; y < c.ny; ++y) ft[y] = c.F0 * std::sin(2.0 * pi * c.kf * (double)y / c.ny);
+      for (int z = 0; z < c.nz; ++z) ft[c.ny + z] = c.F0 * std::sin(2.0 * pi * c.kf * (double)z / c.nz);
+      for (int x = 0; x < c.nx; ++x)
+        ft[c.ny + c.nz + x] = c.F0 * std::sin(2.0 * pi * c.kf * (double)x / c.nx);
+    }
+    std::vector<float> ftf(ft.begin(), ft.end());
+    cudaError_t e = cudaMemsetAsync(M.pop[0], 0, es * kQ3 * M.N, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M.pop[1], 0, es * kQ3 * M.N, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(M.ftab64, ft.data(), 8 * ft.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = es == 8 ? cudaMemcpyAsync(M.ftab, ft.data(), 8 * ft.size(), cudaMemcpyHostToDevice, h->stream)
+                  : cudaMemcpyAsync(M.ftab, ftf.data(), 4 * ftf.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host tables are temporaries
+    if (e != cudaSuccess) {
+      delete h;
+      return fail3(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(h->d_m, h->hm.data(), sizeof(M3) * h->hm.size(),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail3(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm3d_destroy(lbm3d_handle *h) {
+  if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+  cudaStreamSynchronize(h->stream);
+  delete h;
+  return LBM_OK;
+}
+
+int lbm3d_init_fields(lbm3d_handle *h, int member, const double *rho, const double *ux,
+                      const double *uy, const double *uz, int on_device) {
+  if (int rc = check_member3(h, member)) return rc;
+  if (!rho || !ux || !uy || !uz) return fail3(h, LBM_ERR_ARG, "fields must not be NULL");
+  const M3 &M = h->hm[member];
+  const double *src[4] = {rho, ux, uy, uz};
+  double *dev[4];
+  if (!on_device) {  // stage through the diagnostic scratch
+    for (int q = 0; q < 4; ++q) {
+      dev[q] = h->diag + (size_t)q * M.N;
+      CK3(cudaMemcpyAsync(dev[q], src[q], 8 * M.N, cudaMemcpyHostToDevice, h->stream));
+    }
+  } else {
+    for (int q = 0; q < 4; ++q) dev[q] = const_cast<double *>(src[q]);
+  }
+  if (h->precision == 32)
+    k3_init<float><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur,
+                                                                          dev[0], dev[1], dev[2], dev[3]);
+  else
+    k3_init<double><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur,
+                                                                           dev[0], dev[1], dev[2], dev[3]);
+  CK3(cudaGetLastError());
+  if (!on_device) CK3(cudaStreamSynchronize(h->stream));
+  for (long long &r : h->ring_time) r = -1;
+  return LBM_OK;
+}
+
+int lbm3d_step(lbm3d_handle *h, int nsteps) {
+  if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (nsteps < 0) return fail3(h, LBM_ERR_ARG, "nsteps must be >= 0");
+  for (int s = 0; s < nsteps; ++s) {
+    if (snap_time3(h, h->t) && h->ring_time[h->t % 3] != h->t)
+      if (int rc = record3(h)) return rc;
+    for (int m = 0; m < (int)h->mcfg.size(); ++m) {
+      if (h->precision == 32)
+        k3_step<float><<<cells3(h->mcfg[m]), dim3(64, 4), 0, h->stream>>>(h->d_m, m, h->cur);
+      else
+        k3_step<double><<<cells3(h->mcfg[m]), dim3(64, 4), 0, h->stream>>>(h->d_m, m, h->cur);
+    }
+    CK3(cudaGetLastError());
+    h->cur ^= 1;
+    h->t += 1;
+  }
+  if (snap_time3(h, h->t) && h->ring_time[h->t % 3] != h->t) return record3(h);
+  return LBM_OK;
+}
+
+long long lbm3d_time(const lbm3d_handle *h) { return h ? h->t : -1; }
+
+int lbm3d_get_populations(lbm3d_handle *h, int member, double *f, int on_device) {
+  if (int rc = check_member3(h, member)) return rc;
+  if (!f) return fail3(h, LBM_ERR_ARG, "f is NULL");
+  const M3 &M = h->hm[member];
+  double *dst = on_device ? f : h->diag;
+  if (h->precision == 32)
+    k3_copy<float><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur, dst, 1);
+  else
+    k3_copy<double><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur, dst, 1);
+  CK3(cudaGetLastError());
+  if (!on_device) {
+    CK3(cudaMemcpyAsync(f, dst, 8 * kQ3 * M.N, cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm3d_set_populations(lbm3d_handle *h, int member, const double *f, int on_device) {
+  if (int rc = check_member3(h, member)) return rc;
+  if (!f) return fail3(h, LBM_ERR_ARG, "f is NULL");
+  const M3 &M = h->hm[member];
+  double *src = const_cast<double *>(f);
+  if (!on_device) {
+    src = h->diag;
+    CK3(cudaMemcpyAsync(src, f, 8 * kQ3 * M.N, cudaMemcpyHostToDevice, h->stream));
+  }
+  if (h->precision == 32)
+    k3_copy<float><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur, src, 0);
+  else
+    k3_copy<double><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur, src, 0);
+  CK3(cudaGetLastError());
+  if (!on_device) CK3(cudaStreamSynchronize(h->stream));
+  for (long long &r : h->ring_time) r = -1;
+  return LBM_OK;
+}
+
+int lbm3d_record_snapshot(lbm3d_handle *h) {
+  if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+  return record3(h);
+}
+
+int lbm3d_subvolume_balance(lbm3d_handle *h, int member, const int *L, int nL,
+                            const int *origins, const int *counts, double *stats_out,
+                            double *per_box_out) {
+  if (int rc = check_member3(h, member)) return rc;
+  if (!L || nL < 1 || nL > 32 || !stats_out) return fail3(h, LBM_ERR_ARG, "need 1..32 sizes and stats_out");
+  if ((origins == nullptr) != (counts == nullptr))
+    return fail3(h, LBM_ERR_ARG, "origins and counts go together");
+  const lbm3d_member_cfg &c = h->mcfg[member];
+  const M3 &M = h->hm[member];
+  size_t total = 0;
+  if (origins) {
+    for (int i = 0; i < nL; ++i) {
+      if (counts[i] < 1) return fail3(h, LBM_ERR_ARG, "every size needs a box");
+      total += counts[i];
+    }
+    if (3 * total > h->origin_cap) return fail3(h, LBM_ERR_ARG, "too many boxes");
+    for (size_t b = 0; b < total; ++b)
+      if (origins[3 * b] < 0 || origins[3 * b] >= c.nx || origins[3 * b + 1] < 0 ||
+          origins[3 * b + 1] >= c.ny || origins[3 * b + 2] < 0 || origins[3 * b + 2] >= c.nz)
+        return fail3(h, LBM_ERR_ARG, "origin outside the grid");
+  }
+  const long long t = h->t;
+  if (h->ring_time[t % 3] != t)
+    if (int rc = record3(h)) return rc;
+  if (t < 2 || h->ring_time[(t - 1) % 3] != t - 1 || h->ring_time[(t - 2) % 3] != t - 2)
+    return fail3(h, LBM_ERR_HISTORY, "snapshots of time n-1 and n-2 are missing");
+  const int Lmax = std::min(c.nx, std::min(c.ny, c.nz));
+  if (per_box_out)
+    for (int i = 0; i < nL; ++i)
+      if (L[i] < 1 || L[i] > Lmax) return fail3(h, LBM_ERR_ARG, "per_box_out needs every size to fit");
+  const size_t N = M.N;
+  Diag3 J;
+  J.m = h->d_m + member;
+  J.s0 = M.snap + (size_t)(t % 3) * 4 * N;
+  J.s1 = M.snap + (size_t)((t - 1) % 3) * 4 * N;
+  J.s2 = M.snap + (size_t)((t - 2) % 3) * 4 * N;
+  J.f = h->diag;
+  const size_t T = (size_t)(c.nx + 1) * (c.ny + 1) * (c.nz + 1);
+  long long *tab = reinterpret_cast<long long *>(h->diag + (size_t)NF3 * N);
+  double *scales = h->diag + (size_t)NF3 * N + 13 * T;  // [16] scales, [16] exponents
+  double *means = scales + 32;                           // [16]
+  double *sd = scales + 48;                              // [30] statistics of one size
+  double *partials = scales + 80;                        // [blocks][kQS3]
+  const dim3 cb(64, 4), cg = cells3(c);
+  k3_prep<<<cg, cb, 0, h->stream>>>(J);
+  k3_grad<<<cg, cb, 0, h->stream>>>(J);
+  k3_flux<<<cg, cb, 0, h->stream>>>(J);
+  k3_curl<<<cg, cb, 0, h->stream>>>(J);
+  k3_absmax<<<13, 256, 0, h->stream>>>(J, scales);
+  k3_scan_x<<<dim3((c.ny + 1 + 63) / 64, c.nz + 1, 13), 64, 0, h->stream>>>(J, scales, tab);
+  k3_scan_yz<<<dim3((c.nx + 1 + 63) / 64, c.nz + 1, 13), 64, 0, h->stream>>>(J, tab, 1);
+  k3_scan_yz<<<dim3((c.nx + 1 + 63) / 64, c.ny + 1, 13), 64, 0, h->stream>>>(J, tab, 2);
+  k3_means<<<1, 32, 0, h->stream>>>(J, tab, scales, means);
+  CK3(cudaGetLastError());
+  if (origins)
+    CK3(cudaMemcpyAsync(h->d_origins, origins, 12 * total, cudaMemcpyHostToDevice, h->stream));
+  std::vector<double> host(30 * (size_t)nL, std::nan(""));
+  size_t ooff = 0, row = 0;
+  for (int i = 0; i < nL; ++i) {
+    const int nb = origins ? counts[i] : (int)N;
+    if (L[i] >= 1 && L[i] <= Lmax) {
+      const int qb = std::min(kMaxQBlocks3, std::max(1, (nb + 255) / 256));
+      k3_query<<<qb, 256, 0, h->stream>>>(J, tab, scales, means, L[i], nb,
+                                          origins ? h->d_origins + 3 * ooff : nullptr, partials,
+                                          per_box_out ? per_box_out + row * 15 : nullptr);
+      k3_stats<<<1, 32, 0, h->stream>>>(partials, qb, means, nb, sd);
+      CK3(cudaGetLastError());
+      CK3(cudaMemcpyAsync(host.data() + 30 * (size_t)i, sd, 8 * 30, cudaMemcpyDeviceToHost,
+                          h->stream));
+    }
+    ooff += origins ? counts[i] : 0;
+    row += nb;
+  }
+  CK3(cudaStreamSynchronize(h->stream));
+  std::copy(host.begin(), host.end(), stats_out);
+  return LBM_OK;
+}
+
+const char *lbm3d_last_error(const lbm3d_handle *h) {
+  return h ? h->err.c_str() : g_err3.c_str();
+}
+
+}  // extern "C"

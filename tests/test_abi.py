@@ -1,6 +1,6 @@
 """CPU checks of the C ABI: the library builds for sm_103a, loads, exports
-every entry point that include/lbm.h declares, and its host-only calls
-validate configurations (no GPU needed)."""
+every entry point that include/lbm.h and include/lbm3d.h declare, and its
+host-only calls validate configurations (no GPU needed)."""
 import os
 import re
 import subprocess
@@ -8,7 +8,7 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "lbm.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("lbm.h", "lbm3d.h")]
 
 
 @pytest.fixture(scope="module")
@@ -21,22 +21,23 @@ def P():
 
 
 def declared_symbols():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lbm(?:3d)?_[a-z_0-9]+)\s*\(", text)))
 
 
 def test_header_declares_the_boundary():
     syms = declared_symbols()
     for s in ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
-              "lbm_subvolume_balance", "lbm_adjoint_step"):
+              "lbm_subvolume_balance", "lbm_adjoint_step", "lbm_subvolume_distributions",
+              "lbm3d_create", "lbm3d_step", "lbm3d_subvolume_balance"):
         assert s in syms
 
 
 def test_library_exports_every_declared_symbol(P):
     out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r"\sT\s(lbm_\w+)", out))
+    exported = set(re.findall(r"\sT\s(lbm(?:3d)?_\w+)", out))
     missing = [s for s in declared_symbols() if s not in exported]
     assert not missing, missing
     lib = P.load_library()
@@ -73,3 +74,21 @@ def test_workspace_scales_with_grid(P):
     small = P.workspace_size([P.Member(512, 512, 0.52)], 32)
     big = P.workspace_size([P.Member(1024, 1024, 0.52)], 32)
     assert 3.5 < big / small < 4.5
+
+
+def test_3d_config_checks(P):
+    """Host-only validation of the 3D configuration."""
+    import ctypes
+    lib = P.load_library()
+    n = ctypes.c_size_t()
+
+    def size(members, precision=32):
+        arr = (P._MemberCfg3 * len(members))(*[m.c() for m in members])
+        cfg = P._Config3(len(members), arr, precision, 0, None)
+        return lib.lbm3d_workspace_size(ctypes.byref(cfg), ctypes.byref(n))
+
+    assert size([P.Member3(16, 12, 8, 0.6)]) == 0 and n.value > 19 * 4 * 2 * 16 * 12 * 8
+    assert size([P.Member3(16, 12, 8, 0.5)]) == -1
+    assert size([P.Member3(0, 12, 8, 0.6)]) == -1
+    assert size([P.Member3(8, 8, 8, 0.6, force_kind=2)]) == -1
+    assert size([P.Member3(8, 8, 8, 0.6)], precision=16) == -1

@@ -1,0 +1,121 @@
+"""GPU parity of the three-dimensional extension (D3Q19 BGK with EDM forcing;
+the general-index balance terms with vortex stretching over L^3 boxes)
+against the FP64 oracle, through the C ABI of include/lbm3d.h: trajectories
+(FP64 within 1e-12, FP32 within 2e-6 on every population), state round
+trips, and the box terms and statistics on the GPU's exported states."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TERM_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1809_06735_gb300 as P
+    P.load_library()
+    return P
+
+
+def rel_err(got, want):
+    return float(np.max(np.abs(got - want) / np.abs(want)))
+
+
+def _smooth3(shape, seed, amp):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    Z, Y, X = np.meshgrid(2 * np.pi * np.arange(nz) / nz, 2 * np.pi * np.arange(ny) / ny,
+                          2 * np.pi * np.arange(nx) / nx, indexing="ij")
+    out = np.zeros(shape)
+    for _ in range(4):
+        k = rng.integers(-2, 3, size=3)
+        out += rng.normal() * np.cos(k[0] * X + k[1] * Y + k[2] * Z + rng.uniform(0, 2 * np.pi))
+    return amp * out / np.max(np.abs(out))
+
+
+def _fields(shape, seed):
+    return (1.0 + _smooth3(shape, seed, 0.01), _smooth3(shape, seed + 1, 0.04),
+            _smooth3(shape, seed + 2, 0.04), _smooth3(shape, seed + 3, 0.04))
+
+
+SPEC = [(12, 10, 8, 0.57, 1, 1, 3e-4, 2e-3), (16, 16, 16, 0.52, 0, 0, 0.0, 0.0),
+        (5, 7, 3, 0.8, 1, 1, 1e-4, 0.0)]
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 2e-6)])
+def test_3d_trajectories(P, orc, prec, tol):
+    lat = P.Lattice3D([P.Member3(*sp) for sp in SPEC], precision=prec)
+    init = []
+    for i, (nx, ny, nz, *_r) in enumerate(SPEC):
+        fl = _fields((nz, ny, nx), 10 * i)
+        lat.init_fields(i, *fl)
+        init.append(orc.init3(*fl))
+    done = 0
+    for steps in (1, 5, 24):
+        lat.step(steps - done)
+        done = steps
+        for i, (nx, ny, nz, tau, k, kf, F0, a) in enumerate(SPEC):
+            ref = orc.run3(init[i], steps, tau, k, F0, kf, a)
+            err = rel_err(lat.get_populations_host(i), ref)
+            assert err < tol, (prec, steps, i, err)
+
+
+def test_3d_state_roundtrip(P, orc):
+    shape = (6, 5, 7)
+    f = orc.init3(*_fields(shape, 3)) * (1 + 0.01 * np.random.default_rng(1).normal(size=(19,) + shape))
+    lat = P.Lattice3D([P.Member3(7, 5, 6, 0.6)], precision=64)
+    lat.set_populations(0, f)
+    assert np.array_equal(lat.get_populations_host(0), f)
+    lat.step(3)
+    assert rel_err(lat.get_populations_host(0), orc.run3(f, 3, 0.6)) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_3d_balance_terms(P, orc, prec):
+    """All origins and origin lists at several L (one beyond the grid: NaN);
+    per-box terms within 1e-10 of each field's magnitude of the oracle's on
+    the same exported states; vortex stretching is present."""
+    nx, ny, nz, tau, F0, kf, a = 12, 10, 8, 0.57, 3e-4, 1, 2e-3
+    lat = P.Lattice3D([P.Member3(nx, ny, nz, tau, 1.0, 1, kf, F0, a)], precision=prec,
+                      diag_every=10)
+    lat.init_fields(0, *_fields((nz, ny, nx), 40))
+    lat.step(8)
+    f8 = lat.get_populations_host(0)
+    lat.step(1)
+    f9 = lat.get_populations_host(0)
+    lat.step(1)
+    f10 = lat.get_populations_host(0)
+    T = orc.terms3_from_populations(f10, f9, f8, tau, 1, F0, kf, a)
+    scale = np.max(np.abs(T.reshape(13, -1)), axis=1) + 1e-300
+    assert scale[12] > 1e-6 * scale[8]  # RHS^{O,6} does not vanish in 3D
+    Ls = [1, 3, 8]
+    stats, pb = lat.subvolume_balance(0, Ls, per_box=True)
+    pb = pb.cpu().numpy().reshape(len(Ls), -1, 15)
+    want, want_pb = orc.balance_stats3(T, Ls, per_box=True)
+    for iL in range(len(Ls)):
+        d = np.abs(pb[iL][:, 2:] - want_pb[iL][:, 2:]) / scale[None, :]
+        assert np.max(d) < TERM_TOL, (Ls[iL], np.max(d))
+        np.testing.assert_allclose(stats[iL, 2:, 0], want[iL, 2:, 0], rtol=0,
+                                   atol=TERM_TOL * np.max(scale))
+    rng = np.random.default_rng(2)
+    origins = [np.stack([rng.integers(0, nx, 50), rng.integers(0, ny, 50), rng.integers(0, nz, 50)], 1)
+               for _ in range(3)]
+    Ls2 = [2, 5, 9]
+    st2 = lat.subvolume_balance(0, Ls2, origins=origins)
+    assert np.all(np.isnan(st2[2]))
+    for iL in range(2):
+        w = orc.balance_stats3(T, [Ls2[iL]], origins=origins[iL])
+        np.testing.assert_allclose(st2[iL, 2:, 0], w[0, 2:, 0], rtol=0, atol=TERM_TOL * np.max(scale))
+        np.testing.assert_allclose(st2[iL, :2, 0], w[0, :2, 0], rtol=1e-6, atol=1e-8)
+
+
+def test_3d_history_required(P):
+    lat = P.Lattice3D([P.Member3(8, 8, 8, 0.6)], precision=64)
+    lat.init_fields(0, np.ones((8, 8, 8)), *(np.zeros((8, 8, 8)) for _ in range(3)))
+    lat.step(4)
+    with pytest.raises(P.LBMError) as e:
+        lat.subvolume_balance(0, [2])
+    assert e.value.code == -4
