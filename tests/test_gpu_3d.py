@@ -47,7 +47,8 @@ SPEC = [(12, 10, 8, 0.57, 1, 1, 3e-4, 2e-3), (16, 16, 16, 0.52, 0, 0, 0.0, 0.0),
 
 @pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 2e-6)])
 def test_3d_trajectories(P, orc, prec, tol):
-    lat = P.Lattice3D([P.Member3(*sp) for sp in SPEC], precision=prec)
+    lat = P.Lattice3D([P.Member3(nx, ny, nz, tau, 1.0, k, kf, F0, a)
+                       for (nx, ny, nz, tau, k, kf, F0, a) in SPEC], precision=prec)
     init = []
     for i, (nx, ny, nz, *_r) in enumerate(SPEC):
         fl = _fields((nz, ny, nx), 10 * i)
