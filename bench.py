@@ -293,6 +293,51 @@ def collision_models_leg(P, stream, dev, peak):
     return out
 
 
+def three_d_leg(P, stream, dev, peak):
+    """The three-dimensional extension: 2 FP32 D3Q19 members of 128^3 (152
+    algorithmic bytes per update: 19 populations read and written), and one
+    FP64 balance event (all 64^3 periodic origins, L = 2..64) on a 64^3
+    member."""
+    import torch
+    n, M, steps = 128, 2, 40
+    g = np.random.default_rng(5)
+    x = 2 * np.pi * np.arange(n) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    ux = 0.02 * np.sin(X + 0.3) * np.cos(Y) * np.cos(Z)
+    uy = -0.02 * np.cos(X + 0.3) * np.sin(Y) * np.cos(Z) + 0.005 * g.normal() * np.sin(Z)
+    uz = 0.005 * np.sin(X - Y)
+    rho = np.ones((n, n, n))
+    lat = P.Lattice3D([P.Member3(n, n, n, 0.52)] * M, precision=32, stream=stream, device=dev)
+    for m in range(M):
+        lat.init_fields(m, rho, ux, uy, uz)
+    lat.step(10)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    lat.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    secs = a.elapsed_time(b) / 1e3
+    lu = M * n ** 3 * steps
+    gbs = 152.0 * lu / secs / 1e9
+    del lat
+    nd = 64
+    sl = (slice(None, None, 2),) * 3
+    dl = P.Lattice3D([P.Member3(nd, nd, nd, 0.52)], precision=64, diag_every=20, stream=stream,
+                     device=dev)
+    dl.init_fields(0, rho[sl], ux[sl], uy[sl], uz[sl])
+    dl.step(20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = dl.subvolume_balance(0, [2, 4, 8, 16, 32, 64])
+    diag_s = time.perf_counter() - t0
+    assert np.all(np.isfinite(st[:, 2:, 0]))
+    del dl
+    return {"members": M, "grid": [n, n, n], "precision": "fp32", "glups": lu / secs / 1e9,
+            "bytes_per_lu": 152, "achieved_gbs": gbs, "frac": gbs / peak,
+            "diagnostic_event_ms_fp64_64cubed_all_origins": 1e3 * diag_s}
+
+
 def workload_config():
     wl = li.decaying_ensemble_workload()
     return {"workload": wl["name"], "members_per_gpu": wl["members"], "grid": [wl["n"], wl["n"]],
@@ -420,6 +465,7 @@ def run_ours(args):
     del lat64
     paper_forcing = paper_forcing_leg(P, stream, dev, measured_peaks()[0])
     collisions = collision_models_leg(P, stream, dev, measured_peaks()[0])
+    three_d = three_d_leg(P, stream, dev, measured_peaks()[0])
 
     # end to end through the C ABI with host buffers: every step uploads the
     # initial fields of all members from pinned host memory, runs the period
@@ -470,6 +516,7 @@ def run_ours(args):
                                            "ratio_batched_fp32_over_fp64": step_glups / fp64_glups},
             "paper_forcing_ensemble": paper_forcing,
             "collision_models": collisions,
+            "three_d": three_d,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -6,6 +6,7 @@
     python -m paper_1809_06735_gb300.profile_case diag_batch  # batched event, 16 x 512^2
     python -m paper_1809_06735_gb300.profile_case paper_forcing  # force kind 2, 64 x 256^2
     python -m paper_1809_06735_gb300.profile_case collisions  # Smagorinsky, eq. (7), ELBM
+    python -m paper_1809_06735_gb300.profile_case 3d       # D3Q19, 2 x 128^3; 3D balance
     python -m paper_1809_06735_gb300.profile_case fp64     # plain FP64 step, 512^2
     python -m paper_1809_06735_gb300.profile_case adjoint  # FP64 adjoint steps, 256^2
 
@@ -76,6 +77,29 @@ def case_collisions(members=16, n=512, steps=12):
         del lat
 
 
+def case_3d(members=2, n=128, steps=12):
+    """The D3Q19 stream-collide on 2 FP32 members of 128^3, then one FP64
+    balance event on a 48^3 member."""
+    from . import Lattice3D, Member3
+    x = 2 * np.pi * np.arange(n) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    ux, uy = 0.02 * np.sin(X) * np.cos(Y) * np.cos(Z), -0.02 * np.cos(X) * np.sin(Y) * np.cos(Z)
+    uz, rho = 0.005 * np.sin(X - Y), np.ones((n, n, n))
+    lat = Lattice3D([Member3(n, n, n, 0.52)] * members, precision=32)
+    for m in range(members):
+        lat.init_fields(m, rho, ux, uy, uz)
+    lat.step(steps)
+    torch.cuda.synchronize()
+    nd = 48
+    dl = Lattice3D([Member3(nd, nd, nd, 0.52)], precision=64, diag_every=6)
+    dl.init_fields(0, *(a[:nd, :nd, :nd] for a in (rho, ux, uy, uz)))
+    dl.step(6)
+    st = dl.subvolume_balance(0, [2, 8, 32])
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(st[:, 2:, 0]))
+    print("3d case done")
+
+
 def case_diag(n=512, events=2):
     lat = Lattice([Member(n, n, 0.52)], precision=32, diag_every=200)
     lat.init_fields(0, *li.random_phase(n, seed=1000, u_rms=0.02))
@@ -130,6 +154,6 @@ def case_adjoint(n=256, steps=6):
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "step"
     {"step": case_step, "step_full": case_step_full, "paper_forcing": case_paper_forcing,
-     "collisions": case_collisions,
+     "collisions": case_collisions, "3d": case_3d,
      "diag": case_diag, "diag_batch": case_diag_batch, "fp64": case_fp64,
      "adjoint": case_adjoint}[which]()
