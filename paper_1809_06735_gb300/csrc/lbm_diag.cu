@@ -85,9 +85,11 @@ __host__ __device__ inline T *fld(double *base, int k, size_t N) {
 __host__ __device__ inline long long *sat_base(double *base, size_t N) {
   return reinterpret_cast<long long *>(base + (size_t)(kSnapSlots + NF) * N);
 }
-// Each table is the exclusive prefix P(x, y) = sum over x' < x, y' < y for
-// 0 <= x <= nx, 0 <= y <= ny, stored row-major with rows of nx + 1 (row 0
-// and column 0 are zero), so a corner is one load with no branch.
+// The tables are the exclusive prefixes P_f(x, y) = sum over x' < x, y' < y
+// of field f for 0 <= x <= nx, 0 <= y <= ny (row 0 and column 0 are zero),
+// interleaved by field: record (x, y) holds the nF fields' values at
+// ((y (nx + 1) + x) nF + f), so the corner of a box is one or two sectors
+// for a whole balance instead of one sector per field.
 __host__ __device__ inline size_t sat_stride(int nx, int ny) {
   return (size_t)(nx + 1) * (size_t)(ny + 1);
 }
@@ -533,6 +535,268 @@ __global__ void __launch_bounds__(256) k_curl(const DiagJob *__restrict__ jobs) 
 }
 
 // ---------------------------------------------------------------------------
+// FP32 term passes 1-3 with four consecutive cells per thread (nx % 4 == 0):
+// the x-taps of a row come from three aligned float4 loads (x - 4, x, x + 4,
+// wrapped; nx % 4 == 0 keeps the wrapped quadruples aligned) and the y-taps
+// from one float4 per row, about a sixth of the load instructions of the
+// one-cell kernels above.  Same formulas per cell.  CTA (bx, by) covers
+// 128 x 8 cells, i.e. the cells of the one-cell CTAs 4 bx .. 4 bx + 3 in
+// row by: it stores its maxima in slot 4 bx and zero in the other three.
+// ---------------------------------------------------------------------------
+
+#define JOB_CELLS4                                                           \
+  const DiagJob &J = jobs[blockIdx.z];                                       \
+  if ((int)(blockIdx.x * 128) >= J.nx || (int)(blockIdx.y * 8) >= J.ny) return; \
+  const int nx = J.nx, ny = J.ny;                                            \
+  const int x = blockIdx.x * 128 + 4 * threadIdx.x, y = blockIdx.y * 8 + threadIdx.y; \
+  const bool valid = x < nx && y < ny;                                       \
+  const size_t N = (size_t)nx * ny, c = (size_t)y * nx + x;                  \
+  double *base = J.base;                                                     \
+  const int nbx = (nx + 31) / 32, nblk = nbx * ((ny + 7) / 8);               \
+  const int blk = blockIdx.y * nbx + 4 * blockIdx.x;
+
+// Wrapped offsets of a thread's quadruple: the quadruples left and right of
+// it, and the row offsets y + d for d = -4..4.
+struct Nb4 {
+  int xl, xr, yo[9];
+};
+__device__ __forceinline__ Nb4 make_nb4(int nx, int ny, int x, int y) {
+  Nb4 nb;
+  nb.xl = x >= 4 ? x - 4 : x - 4 + nx;
+  nb.xr = x + 4 < nx ? x + 4 : x + 4 - nx;
+#pragma unroll
+  for (int d = -4; d <= 4; ++d) nb.yo[d + 4] = wr(y + d, ny) * nx;
+  return nb;
+}
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4 *>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+// Eq. (18) along x for the four cells (paired form as Dx), and their values.
+__device__ __forceinline__ void dx4(const float *A, const Nb4 &nb, int x, float (&d)[4],
+                                    float (&ctr)[4]) {
+  float a[12];
+  const float *r = A + nb.yo[4];
+  float t[4];
+  ld4(r + nb.xl, t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[i] = t[i];
+  ld4(r + x, t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[4 + i] = ctr[i] = t[i];
+  ld4(r + nb.xr, t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[8 + i] = t[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = 4 + i;
+    d[i] = 0.8f * (a[k + 1] - a[k - 1]) - 0.2f * (a[k + 2] - a[k - 2]) +
+           float(4.0 / 105.0) * (a[k + 3] - a[k - 3]) -
+           float(1.0 / 280.0) * (a[k + 4] - a[k - 4]);
+  }
+}
+// Eq. (18) along y for the four cells.
+__device__ __forceinline__ void dy4(const float *A, const Nb4 &nb, int x, float (&d)[4]) {
+  float m[9][4];
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    if (k != 4) ld4(A + nb.yo[k] + x, m[k]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    d[i] = 0.8f * (m[5][i] - m[3][i]) - 0.2f * (m[6][i] - m[2][i]) +
+           float(4.0 / 105.0) * (m[7][i] - m[1][i]) - float(1.0 / 280.0) * (m[8][i] - m[0][i]);
+}
+
+// The CTA maxima of K fields from per-thread maxima (NaN-ignoring, as the
+// one-cell kernels), stored in slot blk and zero in slots blk + 1..3.
+template <int K>
+__device__ __forceinline__ void block_absmax4(const float (&v)[K], const int (&f)[K],
+                                              const DiagJob &J, int blk, int nblk, int nbx) {
+  block_absmax<float, K>(v, f, J, blk, nblk);
+  if (threadIdx.y == 0 && threadIdx.x < 3 * K) {
+    const int k = threadIdx.x / 3, o = 1 + threadIdx.x % 3;
+    if ((blk % nbx) + o < nbx) max_part<float>(J)[(size_t)f[k] * nblk + blk + o] = 0u;
+  }
+}
+__device__ __forceinline__ float absmax4(const float (&t)[4]) {
+  return fmaxf(fmaxf(fabsf(t[0]), fabsf(t[1])), fmaxf(fabsf(t[2]), fabsf(t[3])));
+}
+
+__global__ void __launch_bounds__(256, 2) k_grad4(const DiagJob *__restrict__ jobs) {
+  JOB_CELLS4;
+  float m2 = 0, m4 = 0, m6 = 0, m8 = 0, m9 = 0;
+  if (valid) {
+    const Nb4 nb = make_nb4(nx, ny, x, y);
+    const float *U = fld<float>(base, U0X, N), *V = fld<float>(base, U0Y, N);
+    float dxu[4], dyu[4], dxv[4], dyv[4], u[4], v[4], w0[4], a[4], b[4], t[4];
+    dx4(U, nb, x, dxu, u);
+    dy4(U, nb, x, dyu);
+    dx4(V, nb, x, dxv, v);
+    dy4(V, nb, x, dyv);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w0[i] = dxv[i] - dyu[i];
+    st4(fld<float>(base, WW, N) + c, w0);
+    // LHS^Omega from the vorticity differences between levels
+    dx4(fld<float>(base, DU01Y, N), nb, x, a, t);
+    dy4(fld<float>(base, DU01X, N), nb, x, b);
+    float dw01[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dw01[i] = a[i] - b[i];
+    dx4(fld<float>(base, DU12Y, N), nb, x, a, t);
+    dy4(fld<float>(base, DU12X, N), nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float dw12 = a[i] - b[i], w1 = w0[i] - dw01[i];
+      const float dO01 = 0.5f * dw01[i] * (2.f * w0[i] - dw01[i]);
+      const float dO12 = 0.5f * dw12 * (2.f * w1 - dw12);
+      t[i] = 0.5f * (3.f * dO01 - dO12);
+    }
+    st4(fld<float>(base, T0 + 6, N) + c, t);
+    m6 = absmax4(t);
+    // RHS^{E,2} = -u . grad p
+    const float *DR = fld<float>(base, DRHO, N);
+    dx4(DR, nb, x, a, t);
+    dy4(DR, nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = -(u[i] * a[i] + v[i] * b[i]) / 3.f;
+    st4(fld<float>(base, T0 + 2, N) + c, t);
+    m2 = absmax4(t);
+    // RHS^{O,3} = w curl(F/rho)
+    dx4(fld<float>(base, FYR, N), nb, x, a, t);
+    dy4(fld<float>(base, FXR, N), nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = w0[i] * (a[i] - b[i]);
+    st4(fld<float>(base, T0 + 9, N) + c, t);
+    m9 = absmax4(t);
+    float r[4], nr[4];
+    ld4(fld<float>(base, R0, N) + c, r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float nu = J.nu_cell_d ? (float)J.nu_cell_d[c + i]
+                                   : (J.nu_cell_f ? J.nu_cell_f[c + i] : J.nu_f);
+      nr[i] = nu * r[i];
+    }
+    float sxx[4], sxy[4], syy[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      sxx[i] = 2.f * dxu[i];
+      sxy[i] = dyu[i] + dxv[i];
+      syy[i] = 2.f * dyv[i];
+      t[i] = -nr[i] * (sxx[i] * dxu[i] + sxy[i] * dyu[i] + sxy[i] * dxv[i] + syy[i] * dyv[i]);
+    }
+    st4(fld<float>(base, T0 + 4, N) + c, t);
+    m4 = absmax4(t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float Om = 0.5f * w0[i] * w0[i];
+      t[i] = -Om * (dxu[i] + dyv[i]);
+      a[i] = Om * u[i];
+      b[i] = Om * v[i];
+    }
+    st4(fld<float>(base, T0 + 8, N) + c, t);
+    m8 = absmax4(t);
+    st4(fld<float>(base, B1, N) + c, a);
+    st4(fld<float>(base, B2, N) + c, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[i] = nr[i] * (u[i] * sxx[i] + v[i] * sxy[i]);
+      b[i] = nr[i] * (u[i] * sxy[i] + v[i] * syy[i]);
+    }
+    st4(fld<float>(base, C1, N) + c, a);
+    st4(fld<float>(base, C2, N) + c, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[i] = nr[i] * sxx[i];
+      b[i] = nr[i] * sxy[i];
+      t[i] = nr[i] * syy[i];
+    }
+    st4(fld<float>(base, G1, N) + c, a);
+    st4(fld<float>(base, G2, N) + c, b);
+    st4(fld<float>(base, G3, N) + c, t);
+  }
+  const float mv[5] = {m2, m4, m6, m8, m9};
+  const int mf[5] = {2, 4, 6, 8, 9};
+  block_absmax4<5>(mv, mf, J, blk, nblk, nbx);
+}
+
+__global__ void __launch_bounds__(256) k_flux4(const DiagJob *__restrict__ jobs) {
+  JOB_CELLS4;
+  float m1 = 0, m5 = 0, m7 = 0, m10 = 0;
+  if (valid) {
+    const Nb4 nb = make_nb4(nx, ny, x, y);
+    float a[4], b[4], ctr[4], t[4];
+    float r[4];
+    ld4(fld<float>(base, R0, N) + c, r);
+    dx4(fld<float>(base, A1, N), nb, x, a, ctr);
+    dy4(fld<float>(base, A2, N), nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = -(a[i] + b[i]);
+    st4(fld<float>(base, T0 + 1, N) + c, t);
+    m1 = absmax4(t);
+    dx4(fld<float>(base, C1, N), nb, x, a, ctr);
+    dy4(fld<float>(base, C2, N), nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = a[i] + b[i];
+    st4(fld<float>(base, T0 + 5, N) + c, t);
+    m5 = absmax4(t);
+    dx4(fld<float>(base, B1, N), nb, x, a, ctr);
+    dy4(fld<float>(base, B2, N), nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = -(a[i] + b[i]);
+    st4(fld<float>(base, T0 + 7, N) + c, t);
+    m7 = absmax4(t);
+    float Hx[4], Hy[4];
+    const float *G2p = fld<float>(base, G2, N);
+    dx4(fld<float>(base, G1, N), nb, x, a, ctr);
+    dy4(G2p, nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Hx[i] = (a[i] + b[i]) / r[i];
+    dx4(G2p, nb, x, a, ctr);
+    dy4(fld<float>(base, G3, N), nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Hy[i] = (a[i] + b[i]) / r[i];
+    const float *W = fld<float>(base, WW, N);
+    float w[4];
+    dx4(W, nb, x, a, w);
+    dy4(W, nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = Hx[i] * b[i] - Hy[i] * a[i];
+    st4(fld<float>(base, T0 + 10, N) + c, t);
+    m10 = absmax4(t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = w[i] * Hy[i];
+    st4(fld<float>(base, K1, N) + c, t);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = w[i] * Hx[i];
+    st4(fld<float>(base, K2, N) + c, t);
+  }
+  const float mv[4] = {m1, m5, m7, m10};
+  const int mf[4] = {1, 5, 7, 10};
+  block_absmax4<4>(mv, mf, J, blk, nblk, nbx);
+}
+
+__global__ void __launch_bounds__(256) k_curl4(const DiagJob *__restrict__ jobs) {
+  JOB_CELLS4;
+  float m11 = 0;
+  if (valid) {
+    const Nb4 nb = make_nb4(nx, ny, x, y);
+    float a[4], b[4], ctr[4], t[4];
+    dx4(fld<float>(base, K1, N), nb, x, a, ctr);
+    dy4(fld<float>(base, K2, N), nb, x, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = a[i] - b[i];
+    st4(fld<float>(base, T0 + 11, N) + c, t);
+    m11 = absmax4(t);
+  }
+  const float mv[1] = {m11};
+  const int mf[1] = {11};
+  block_absmax4<1>(mv, mf, J, blk, nblk, nbx);
+}
+
+// ---------------------------------------------------------------------------
 // Block-deterministic reductions
 // ---------------------------------------------------------------------------
 
@@ -717,122 +981,151 @@ __device__ __forceinline__ long long quantize(double v, int e) {
   return __double2ll_rn(ldexp(v, e));
 }
 
-// Four consecutive values of a term row (x, x+1, x+2, x+3 < nx): one
-// 16-byte load per float quadruple (two per double) where the row allows.
-__device__ __forceinline__ void load4(const float *r, int x, bool vec, float (&v)[4]) {
-  if (vec) {
+// Summed-area tables by strips of kStrip = 128 columns, 4 consecutive cells
+// per lane (each term field read twice, each table record written once):
+//   k_strip_sums  per (field, row), the quantised sums of the row's strips
+//                 and their exclusive prefix: the part of the row left of
+//                 each strip;
+//   k_sat_tile    a CTA per strip with one warp per field walks down the
+//                 rows: left part + warp scan of the strip's 128 cells +
+//                 running column sum (registers) is the table row, staged in
+//                 shared memory and written as whole interleaved records.
+// The left parts, int64 [field][strip][row], live in the term stage's
+// intermediate fields (U0X on), dead by then: nF * ny * ceil(nx/128) <= 13 N.
+constexpr int kStrip = 128;
+
+__device__ __forceinline__ long long *strip_base(double *base, size_t N) {
+  return reinterpret_cast<long long *>(fld<double>(base, U0X, N));
+}
+
+// Cells x..x+3 of a term row (zero past nx): one 16-byte load per float
+// quadruple (two per double) where the row allows.
+__device__ __forceinline__ void load4(const float *r, int x, int nx, bool vec, float (&v)[4]) {
+  if (vec && x + 3 < nx) {
     const float4 q = *reinterpret_cast<const float4 *>(r + x);
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = r[x + k];
+    for (int k = 0; k < 4; ++k) v[k] = x + k < nx ? r[x + k] : 0.f;
   }
 }
-__device__ __forceinline__ void load4(const double *r, int x, bool vec, double (&v)[4]) {
-  if (vec) {
+__device__ __forceinline__ void load4(const double *r, int x, int nx, bool vec, double (&v)[4]) {
+  if (vec && x + 3 < nx) {
     const double2 a = *reinterpret_cast<const double2 *>(r + x);
     const double2 b = *reinterpret_cast<const double2 *>(r + x + 2);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = r[x + k];
+    for (int k = 0; k < 4; ++k) v[k] = x + k < nx ? r[x + k] : 0.0;
   }
 }
 
-// Quantize and scan along x, one CTA (128 threads) per (row, field, job):
-// each thread scans 4 consecutive cells of a 512-cell segment, a warp scan
-// of the thread totals and a CTA combination of the 4 warp totals give the
-// segment, and a running carry chains the segments.
 template <typename T>
-__global__ void __launch_bounds__(128) k_sat_rows(const DiagJob *__restrict__ jobs) {
-  const DiagJob &J = jobs[blockIdx.z];
-  const int y = blockIdx.x, f = blockIdx.y, nx = J.nx, ny = J.ny;
-  if (y >= ny) return;
-  const size_t N = (size_t)nx * ny;
-  const T *row = fld<T>(J.base, T0 + f, N) + (size_t)y * nx;
-  long long *tab = sat_base(J.base, N) + (size_t)f * sat_stride(nx, ny);
-  long long *out = tab + (size_t)(y + 1) * (nx + 1) + 1;  // row y+1, column 1..nx
-  const int e = reinterpret_cast<const int *>(J.part + exps_at())[f];
-  const bool vec = nx % 4 == 0 && (reinterpret_cast<uintptr_t>(row) & 15) == 0;
-  __shared__ long long wsum[4];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) out[-1] = 0;  // column 0
-  if (y == 0)
-    for (int i = tid; i <= nx; i += 128) tab[i] = 0;  // row 0
-  long long carry = 0;
-  for (int b0 = 0; b0 < nx; b0 += 512) {
-    const int x = b0 + 4 * tid;
-    long long v[4] = {0, 0, 0, 0};
-    if (x + 3 < nx) {
-      T a[4];
-      load4(row, x, vec, a);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) v[k] = quantize(a[k], e);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (x + k < nx) v[k] = quantize(row[x + k], e);
-    }
-    v[1] += v[0];
-    v[2] += v[1];
-    v[3] += v[2];
-    long long t = v[3];  // inclusive scan of the thread totals over the warp
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long n = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += n;
-    }
-    if (lane == 31) wsum[wid] = t;
-    __syncthreads();
-    long long off = carry + (t - v[3]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      if (k < wid) off += wsum[k];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (x + k < nx) out[x + k] = v[k] + off;
-    carry += wsum[0] + wsum[1] + wsum[2] + wsum[3];
-    __syncthreads();
-  }
+__device__ __forceinline__ bool vec_rows(const T *A, int nx) {
+  return nx % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
 }
 
-// Scan along y over a strip of 32 columns: the 8 warps sum one chunk of rows
-// each, exchange chunk totals in shared memory, then rewrite their chunk.
-__global__ void __launch_bounds__(256) k_sat_cols(const DiagJob *__restrict__ jobs) {
+// One warp per (row, field), 4 strips in flight; grid (ceil(ny/8), nF, G).
+template <typename T>
+__global__ void __launch_bounds__(256) k_strip_sums(const DiagJob *__restrict__ jobs) {
+  constexpr int U = 4;
   const DiagJob &J = jobs[blockIdx.z];
-  const int nx = J.nx, ny = J.ny;
-  if ((int)(blockIdx.x * 32) >= nx) return;
-  const int f = blockIdx.y;
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int w = threadIdx.y;
-  const int chunk = (ny + 7) / 8;
-  const int y0 = min(ny, w * chunk), y1 = min(ny, y0 + chunk);
+  const int nx = J.nx, ny = J.ny, f = blockIdx.y, ns = (nx + kStrip - 1) / kStrip;
+  const int lane = threadIdx.x & 31, y = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (y >= ny) return;  // whole warps
   const size_t N = (size_t)nx * ny;
-  const size_t rs = (size_t)nx + 1;  // padded row length
-  long long *col = sat_base(J.base, N) + (size_t)f * sat_stride(nx, ny) + rs + 1 + x;
-  __shared__ long long tot[8][32];
-  long long s = 0;
-  if (x < nx)
-    for (int y = y0; y < y1; ++y) s += col[(size_t)y * rs];
-  tot[w][threadIdx.x] = s;
-  __syncthreads();
-  long long acc = 0;
-  for (int k = 0; k < w; ++k) acc += tot[k][threadIdx.x];
-  if (x < nx) {
-    int y = y0;
-    for (; y + 8 <= y1; y += 8) {
-      long long v[8];
+  const T *A = fld<T>(J.base, T0 + f, N);
+  const bool vec = vec_rows(A, nx);
+  A += (size_t)y * nx;
+  const int e = reinterpret_cast<const int *>(J.part + exps_at())[f];
+  long long *out = strip_base(J.base, N) + (size_t)f * ns * ny + y;
+  long long acc = 0;  // lane 0: the row's sum left of the current strip
+  for (int s0 = 0; s0 < ns; s0 += U) {
+    T a[U][4];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = col[(size_t)(y + k) * rs];
+    for (int u = 0; u < U; ++u)
+      if (s0 + u < ns) load4(A, (s0 + u) * kStrip + 4 * lane, nx, vec, a[u]);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        acc += v[k];
-        col[(size_t)(y + k) * rs] = acc;
+    for (int u = 0; u < U; ++u) {
+      if (s0 + u >= ns) break;
+      long long v = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v += quantize(a[u][k], e);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        out[(size_t)(s0 + u) * ny] = acc;
+        acc += v;
       }
     }
-    for (; y < y1; ++y) {
-      acc += col[(size_t)y * rs];
-      col[(size_t)y * rs] = acc;
+  }
+}
+
+__device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// A CTA of NF warps (warp f = field f) per (strip, job); grid (ns, 1, G).
+// Lane l holds columns x0 + 4l .. x0 + 4l + 3.  Each row is staged in one of
+// two shared tiles [field][129] (column c at (c % 4) 32 + c / 4: conflict-free
+// writes) and copied out as the consecutive words of its records, so one
+// barrier per row suffices.
+template <typename T, int NF>
+__global__ void __launch_bounds__(NF * 32) k_sat_tile(const DiagJob *__restrict__ jobs) {
+  constexpr int R = sizeof(T) == 4 ? 8 : 4;  // rows of loads in flight per warp
+  constexpr int NT = NF * 32, TS = kStrip + 1;
+  __shared__ long long tile[2][NF][TS];
+  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31, s = blockIdx.x;
+  const DiagJob &J = jobs[blockIdx.z];
+  const int nx = J.nx, ny = J.ny, ns = (nx + kStrip - 1) / kStrip;
+  if (s >= ns) return;  // whole CTA
+  const int x0 = s * kStrip, x = x0 + 4 * lane;
+  const int nw = (nx - x0 < kStrip ? nx - x0 : kStrip) * NF;  // record words per row
+  const size_t N = (size_t)nx * ny, rs = (size_t)nx + 1;
+  const T *A = fld<T>(J.base, T0 + f, N);
+  const bool vec = vec_rows(A, nx);
+  const long long *left = strip_base(J.base, N) + ((size_t)f * ns + s) * ny;
+  long long *tab = sat_base(J.base, N);
+  const int e = reinterpret_cast<const int *>(J.part + exps_at())[f];
+  for (int w = threadIdx.x; w < nw; w += NT) tab[(size_t)(x0 + 1) * NF + w] = 0;  // row 0
+  if (s == 0 && threadIdx.x < NF) tab[threadIdx.x] = 0;
+  long long col[4] = {0, 0, 0, 0}, lf = 0;
+  for (int y0 = 0; y0 < ny; y0 += R) {
+    if ((y0 & 31) == 0) lf = y0 + lane < ny ? left[y0 + lane] : 0;  // 32 rows' left parts
+    T a[R][4];
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (y0 + k < ny) load4(A + (size_t)(y0 + k) * nx, x, nx, vec, a[k]);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int y = y0 + k;
+      const long long l = __shfl_sync(0xffffffffu, lf, (y0 & 31) + k);
+      if (y >= ny) break;  // the same for the whole CTA
+      long long v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = quantize(a[k][j], e);
+      v[1] += v[0];
+      v[2] += v[1];
+      v[3] += v[2];
+      const long long off = l + warp_incl_scan(v[3], lane) - v[3];
+      long long *t = tile[y & 1][f];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        col[j] += off + v[j];
+        t[j * 32 + lane] = col[j];
+      }
+      __syncthreads();
+      long long *out = tab + ((size_t)(y + 1) * rs + x0 + 1) * NF;
+      for (int w = threadIdx.x; w < nw; w += NT) {
+        const int c = w / NF, g = w - c * NF;
+        out[w] = tile[y & 1][g][(c & 3) * 32 + (c >> 2)];
+      }
+      if (s == 0 && threadIdx.x < NF) tab[(size_t)(y + 1) * rs * NF + threadIdx.x] = 0;
     }
   }
 }
@@ -840,17 +1133,18 @@ __global__ void __launch_bounds__(256) k_sat_cols(const DiagJob *__restrict__ jo
 // Exclusive prefix P(x, y) (0 <= x <= nx, 0 <= y <= ny) from a padded table;
 // modular (unsigned) arithmetic: the periodic extension may exceed int64 in
 // between, the box sum does not.
-__device__ __forceinline__ unsigned long long Pex(const long long *S, int nx, int x, int y) {
-  return (unsigned long long)S[(size_t)y * (nx + 1) + x];
+__device__ __forceinline__ unsigned long long Pex(const long long *S, int nx, int nF, int x,
+                                                  int y) {
+  return (unsigned long long)S[((size_t)y * (nx + 1) + x) * nF];
 }
-__device__ __forceinline__ unsigned long long Pext(const long long *S, int nx, int ny, int x,
-                                                   int y) {
+__device__ __forceinline__ unsigned long long Pext(const long long *S, int nx, int ny, int nF,
+                                                   int x, int y) {
   const int qx = x >= nx, qy = y >= ny;
   const int xm = x - qx * nx, ym = y - qy * ny;
-  unsigned long long v = Pex(S, nx, xm, ym);
-  if (qx) v += Pex(S, nx, nx, ym);
-  if (qy) v += Pex(S, nx, xm, ny);
-  if (qx && qy) v += Pex(S, nx, nx, ny);
+  unsigned long long v = Pex(S, nx, nF, xm, ym);
+  if (qx) v += Pex(S, nx, nF, nx, ym);
+  if (qy) v += Pex(S, nx, nF, xm, ny);
+  if (qx && qy) v += Pex(S, nx, nF, nx, ny);
   return v;
 }
 
@@ -870,8 +1164,7 @@ __global__ void k_query_consts(const DiagJob *__restrict__ jobs, int nF) {
   const int nx = J.nx, ny = J.ny;
   const size_t N = (size_t)nx * ny;
   const double area = (double)J.meta[8 * iL] * (double)J.meta[8 * iL];
-  const long long total =
-      sat_base(J.base, N)[(size_t)k * sat_stride(nx, ny) + (size_t)ny * (nx + 1) + nx];
+  const long long total = sat_base(J.base, N)[(sat_stride(nx, ny) - 1) * nF + k];
   const double inv = J.part[inv_scale(k)];
   QConst q;
   q.mean_d = (double)total * inv / (double)N;
@@ -927,43 +1220,74 @@ __device__ __forceinline__ int bin_of(MT v, const MT *edges, int ne) {
   return lo;
 }
 
-// Grid (query CTAs, sizes, NG x jobs), NG = 2, or 3 with the distributions
-// (EXT); blockIdx.z = NG * job + group.  Group 0 = energy balance (fields
-// 0..5: LHS^E, RHS^{E,1..5}), 1 = enstrophy (fields 6..11: LHS^O,
-// RHS^{O,1..5}; RHS^{O,6} is identically 0 in 2D and adds nothing), 2 =
-// sub-volume Mach number (field 12, |u|^2).  One thread per (box, group):
+// Block sum of the two balances' accumulators of a CTA whose even threads
+// hold energy (group 0) and odd threads enstrophy (group 1) values: warp
+// stage in MT over lanes of one parity, then a fixed-order sum over warps.
+template <int NQ, typename MT>
+__device__ void block_sum_store_pairs(MT (&v)[NQ], double *out0, double *out1) {
+  __shared__ double sh[2][NQ][32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    MT a = v[q];
+#pragma unroll
+    for (int o = 16; o > 1; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane < 2) sh[lane][q][wid] = (double)a;
+  }
+  __syncthreads();
+  if (tid < 2 * NQ) {
+    const int g = tid / NQ, q = tid % NQ;
+    double a = 0.0;
+    for (int k = 0; k < nw; ++k) a += sh[g][q][k];
+    (g ? out1 : out0)[q] = a;
+  }
+}
+
+// Grid (query CTAs, sizes, NZ x jobs), NZ = 1, or 2 with the distributions
+// (EXT), blockIdx.z = NZ * job + part.  Part 0: thread pairs per box, the
+// even thread the energy balance (fields 0..5: LHS^E, RHS^{E,1..5}), the odd
+// one the enstrophy balance (fields 6..11: LHS^O, RHS^{O,1..5}; RHS^{O,6}
+// is identically 0 in 2D and adds nothing), so the two read the halves of
+// the same interleaved corner records; part 1 (EXT): one thread per box for
+// the sub-volume Mach number (field 12, |u|^2).  Each thread walks its boxes
+// (CTA c takes passes c, c + qb, ...) with the next origin prefetched:
 // exact integer box sums of the group's fields, their deviations d_k from
 // the field means, the box means, the balancing error (or Ma_V), and sums of
 // d_k, d_k^2 and of the error's (or Ma_V's) deviation and its square; with
 // EXT also a CTA histogram in shared memory, added to the global one with
 // integer atomics (order-free, so deterministic).
 template <typename MT, bool PER_BOX, bool EXT>
-__global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
+__global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs, int nF,
                                                const int *__restrict__ origins,
                                                double *per_box, DiagDist ext) {
-  constexpr int NG = EXT ? 3 : 2;
-  const DiagJob &J = jobs[blockIdx.z / NG];
-  const int iL = blockIdx.y, grp = blockIdx.z % NG, k0 = 6 * grp;
+  constexpr int NZ = EXT ? 2 : 1;
+  const DiagJob &J = jobs[blockIdx.z / NZ];
+  const bool mpart = EXT && blockIdx.z % NZ == 1;
+  const int iL = blockIdx.y;
   if (iL >= J.nL || (int)blockIdx.x >= J.qblocks) return;
+  const int grp = mpart ? 2 : (int)(threadIdx.x & 1), k0 = 6 * grp;
+  const int slot = mpart ? (int)threadIdx.x : (int)(threadIdx.x >> 1);
+  const int per_pass = mpart ? 256 : 128;
   const int qb = J.qblocks;
   const int nx = J.nx, ny = J.ny;
   const int *meta = J.meta;
   const int L = meta[8 * iL], nb = meta[8 * iL + 1], ooff = meta[8 * iL + 2];
   const size_t N = (size_t)nx * ny;
-  const size_t sp = sat_stride(nx, ny), rs = (size_t)nx + 1;
-  const long long *S = sat_base(J.base, N) + (size_t)k0 * sp;
+  const size_t rs = (size_t)nx + 1;
+  const long long *S = sat_base(J.base, N) + k0;
   const QConst *qc =
       reinterpret_cast<const QConst *>(J.part + kPartConsts) + (size_t)iL * kNT + k0;
   const int nfield = grp == 2 ? 1 : 6;
   __shared__ MT sedge[EXT ? kDiagMaxEdges : 1];
-  __shared__ unsigned shist[EXT ? kDiagMaxEdges + 1 : 1];
+  __shared__ unsigned shist[2][EXT ? kDiagMaxEdges + 1 : 1];
   int ne = 0;
   if constexpr (EXT) {
-    ne = grp == 2 ? ext.n_mach : ext.n_delta;
-    const double *e = grp == 2 ? ext.mach_edges : ext.delta_edges;
+    ne = mpart ? ext.n_mach : ext.n_delta;
+    const double *e = mpart ? ext.mach_edges : ext.delta_edges;
     for (int i = threadIdx.x; i <= ne; i += blockDim.x) {
       if (i < ne) sedge[i] = (MT)e[i];
-      shist[i] = 0u;
+      shist[0][i] = 0u;
+      shist[1][i] = 0u;
     }
     __syncthreads();
   }
@@ -976,30 +1300,38 @@ __global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
     s2[j] = MT(0);
   }
   MT d1 = 0, d2 = 0;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += qb * blockDim.x) {
-    int x0, y0;
+  const int stride = qb * per_pass;
+  int b = blockIdx.x * per_pass + slot;
+  auto origin = [&](int i, int &x, int &y) {
     if (ooff >= 0) {
-      x0 = origins[2 * (ooff + b)];
-      y0 = origins[2 * (ooff + b) + 1];
+      x = origins[2 * (ooff + i)];
+      y = origins[2 * (ooff + i) + 1];
     } else {
-      x0 = b % nx;
-      y0 = b / nx;
+      x = i % nx;
+      y = i / nx;
     }
+  };
+  int x0 = 0, y0 = 0;
+  if (b < nb) origin(b, x0, y0);
+  for (; b < nb; b += stride) {
+    int xn = 0, yn = 0;  // the next box's origin, loaded ahead
+    if (b + stride < nb) origin(b + stride, xn, yn);
     const bool inside = x0 + L <= nx && y0 + L <= ny;
     MT lhs = 0, sum = 0, mx = 0;
     double *o = PER_BOX ? per_box + ((size_t)meta[8 * iL + 3] + b) * 15 : nullptr;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       if (j >= nfield) break;
-      const long long *Sk = S + (size_t)j * sp;
+      const long long *Sk = S + j;
       unsigned long long bs;
       if (inside) {  // no periodic wrap: four direct corner loads
-        const long long *lo = Sk + (size_t)y0 * rs + x0, *hi = lo + (size_t)L * rs;
-        bs = (unsigned long long)hi[L] - (unsigned long long)hi[0] -
-             (unsigned long long)lo[L] + (unsigned long long)lo[0];
+        const long long *lo = Sk + ((size_t)y0 * rs + x0) * nF, *hi = lo + (size_t)L * rs * nF;
+        const size_t dx = (size_t)L * nF;
+        bs = (unsigned long long)hi[dx] - (unsigned long long)hi[0] -
+             (unsigned long long)lo[dx] + (unsigned long long)lo[0];
       } else {
-        bs = Pext(Sk, nx, ny, x0 + L, y0 + L) - Pext(Sk, nx, ny, x0, y0 + L) -
-             Pext(Sk, nx, ny, x0 + L, y0) + Pext(Sk, nx, ny, x0, y0);
+        bs = Pext(Sk, nx, ny, nF, x0 + L, y0 + L) - Pext(Sk, nx, ny, nF, x0, y0 + L) -
+             Pext(Sk, nx, ny, nF, x0 + L, y0) + Pext(Sk, nx, ny, nF, x0, y0);
       }
       const long long dq = (long long)(bs - (unsigned long long)qc[j].mq);
       const MT d = to_mt<MT>(dq) * qc[j].coef<MT>();
@@ -1026,12 +1358,14 @@ __global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
       d2 += val * val;
     }
     if constexpr (EXT) {
-      if (val == val) atomicAdd(&shist[bin_of(val, sedge, ne)], 1u);
+      if (val == val) atomicAdd(&shist[mpart ? 0 : grp][bin_of(val, sedge, ne)], 1u);
     }
     if (PER_BOX) {
       o[grp] = (double)val;
       if (grp == 1) o[14] = 0.0;
     }
+    x0 = xn;
+    y0 = yn;
   }
   MT acc[kQStats];
   acc[0] = d1;
@@ -1041,14 +1375,21 @@ __global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
     acc[2 + 2 * j] = s1[j];
     acc[3 + 2 * j] = s2[j];
   }
-  block_sum_store_mt<kQStats, MT>(
-      acc, J.part + kPartQuery + (((size_t)iL * 3 + grp) * qb + blockIdx.x) * kQStats);
+  double *pq = J.part + kPartQuery;
+  if (mpart)
+    block_sum_store_mt<kQStats, MT>(acc, pq + (((size_t)iL * 3 + 2) * qb + blockIdx.x) * kQStats);
+  else
+    block_sum_store_pairs<kQStats, MT>(acc, pq + (((size_t)iL * 3 + 0) * qb + blockIdx.x) * kQStats,
+                                       pq + (((size_t)iL * 3 + 1) * qb + blockIdx.x) * kQStats);
   if constexpr (EXT) {
     __syncthreads();
-    unsigned long long *h =
-        ext.hist + ((size_t)meta[8 * iL + 4] * 3 + grp) * (kDiagMaxEdges + 1);
-    for (int i = threadIdx.x; i <= ne; i += blockDim.x)
-      if (shist[i]) atomicAdd(&h[i], (unsigned long long)shist[i]);
+    const int ng = mpart ? 1 : 2;
+    for (int g = 0; g < ng; ++g) {
+      unsigned long long *h =
+          ext.hist + ((size_t)meta[8 * iL + 4] * 3 + (mpart ? 2 : g)) * (kDiagMaxEdges + 1);
+      for (int i = threadIdx.x; i <= ne; i += blockDim.x)
+        if (shist[g][i]) atomicAdd(&h[i], (unsigned long long)shist[g][i]);
+    }
   }
 }
 
@@ -1154,23 +1495,37 @@ cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int 
     k_prep<T, true><<<cg, cb, 0, s>>>(jobs);
   else
     k_prep<T, false><<<cg, cb, 0, s>>>(jobs);
-  k_grad<T><<<cg, cb, 0, s>>>(jobs);
-  k_flux<T><<<cg, cb, 0, s>>>(jobs);
-  k_curl<T><<<cg, cb, 0, s>>>(jobs);
+  bool quad = sizeof(T) == 4;  // four cells per thread where every job allows
+  for (int j = 0; j < G && quad; ++j)
+    quad = jobs_host[j].nx % 4 == 0 && (reinterpret_cast<uintptr_t>(jobs_host[j].base) & 15) == 0;
+  if (quad) {
+    const dim3 cg4((nx + 127) / 128, (ny + 7) / 8, G);
+    k_grad4<<<cg4, cb, 0, s>>>(jobs);
+    k_flux4<<<cg4, cb, 0, s>>>(jobs);
+    k_curl4<<<cg4, cb, 0, s>>>(jobs);
+  } else {
+    k_grad<T><<<cg, cb, 0, s>>>(jobs);
+    k_flux<T><<<cg, cb, 0, s>>>(jobs);
+    k_curl<T><<<cg, cb, 0, s>>>(jobs);
+  }
   k_scales<T><<<G, kNT * 32, 0, s>>>(jobs, nF);
-  k_sat_rows<T><<<dim3(ny, nF, G), 128, 0, s>>>(jobs);
-  k_sat_cols<<<dim3((nx + 31) / 32, nF, G), dim3(32, 8), 0, s>>>(jobs);
+  const int ns = (nx + kStrip - 1) / kStrip;
+  k_strip_sums<T><<<dim3((ny + 7) / 8, nF, G), 256, 0, s>>>(jobs);
+  if (nF == kNT)
+    k_sat_tile<T, kNT><<<dim3(ns, 1, G), kNT * 32, 0, s>>>(jobs);
+  else
+    k_sat_tile<T, 12><<<dim3(ns, 1, G), 12 * 32, 0, s>>>(jobs);
   k_query_consts<<<G, kDiagMaxL * kNT, 0, s>>>(jobs, nF);
   const DiagDist none{};
   if (dist) {
-    k_query<MT, false, true><<<dim3(qblocks, nL, 3 * G), 256, 0, s>>>(jobs, origins, nullptr,
+    k_query<MT, false, true><<<dim3(qblocks, nL, 2 * G), 256, 0, s>>>(jobs, nF, origins, nullptr,
                                                                        *dist);
   } else {
-    const dim3 qg(qblocks, nL, 2 * G);
+    const dim3 qg(qblocks, nL, G);
     if (per_box)
-      k_query<MT, true, false><<<qg, 256, 0, s>>>(jobs, origins, per_box, none);
+      k_query<MT, true, false><<<qg, 256, 0, s>>>(jobs, nF, origins, per_box, none);
     else
-      k_query<MT, false, false><<<qg, 256, 0, s>>>(jobs, origins, nullptr, none);
+      k_query<MT, false, false><<<qg, 256, 0, s>>>(jobs, nF, origins, nullptr, none);
   }
   k_stats_final<MT><<<dim3(nL, G), 384, 0, s>>>(jobs, stats, dist ? dist->mach : nullptr);
   return cudaGetLastError();
@@ -1208,10 +1563,10 @@ cudaError_t diag_global(const Member &hm, const double *snap3, const DiagScratch
   return cudaGetLastError();
 }
 
-// Box lists: one box per thread; every periodic origin: about 16 per
-// thread; at most kMaxQueryBlocks CTAs per (job, size, balance).
+// Box lists: about 8 boxes per thread pair; every periodic origin: about 32
+// per thread pair; at most kMaxQueryBlocks CTAs per (job, size, part).
 int diag_query_blocks(int max_boxes, bool origin_list) {
-  const int per_cta = origin_list ? 256 : 4096;
+  const int per_cta = origin_list ? 1024 : 4096;
   return std::min(kMaxQueryBlocks, std::max(1, (max_boxes + per_cta - 1) / per_cta));
 }
 
