@@ -569,7 +569,7 @@ __device__ __forceinline__ Nb4 make_nb4(int nx, int ny, int x, int y) {
   return nb;
 }
 __device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
-  const float4 q = *reinterpret_cast<const float4 *>(p);
+  const float4 q = __ldg(reinterpret_cast<const float4 *>(p));  // read-only in the pass
   v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 __device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
