@@ -146,6 +146,8 @@ struct LaunchCfg {
 
 cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, int ntiles,
                                 int cur, const LaunchCfg &lc, cudaStream_t s);
+cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tiles, int ntiles,
+                                     int state, const LaunchCfg &lc, int slot, cudaStream_t s);
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member,
                                int nx, int ny, int cur, cudaStream_t s);
 cudaError_t launch_init_fields(int precision, const Member *d_members, int member, int nx,

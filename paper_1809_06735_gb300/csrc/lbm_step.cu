@@ -322,6 +322,27 @@ __device__ __forceinline__ void *state_buffer(const Member &M, int state) {
   return state < 2 ? M.pop[state] : M.pop[0];
 }
 
+// Error-free addition (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated FP32 sum of FP32 values as the unevaluated pair (s, c): the
+// FP64 sum is (double)s + (double)c (the csum value) and differences of
+// nearby sums can be formed in FP32 as (s - s') + (c - c').
+__device__ __forceinline__ void csum_pair(const float *v, const int *sign, int n, float &s,
+                                          float &c) {
+  s = sign[0] * v[0];
+  c = 0.f;
+  for (int k = 1; k < n; ++k) {
+    float e;
+    two_sum(s, sign[k] * v[k], s, e);
+    c += e;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Hot kernel: batched FP32 stream-collide, 4 cells per lane, nx % 4 == 0.
 // blockDim = (32, WY); a tile is 128 x (WY * ROWS) cells of one member.
@@ -362,10 +383,12 @@ __device__ __forceinline__ void paper_force4(const Member &M, int x, int y, floa
   }
 }
 
-template <int ROWS, int MODE, bool PF>
-__global__ void __launch_bounds__(256, PF ? 3 : 1) k_step_f32_vec(const Member *__restrict__ members,
+// SNAP: the step also records the snapshot-ring entry of the state it
+// reads (slot snap_slot), the same compensated pairs as k_snapshot_ring.
+template <int ROWS, int MODE, bool PF, bool SNAP = false>
+__global__ void __launch_bounds__(256, PF ? 3 : (SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
                                                       const Tile *__restrict__ tiles,
-                                                      int ntiles, int cur) {
+                                                      int ntiles, int cur, int snap_slot) {
   const int lane = threadIdx.x;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tl = tiles[t];
@@ -423,6 +446,34 @@ __global__ void __launch_bounds__(256, PF ? 3 : 1) k_step_f32_vec(const Member *
           float next = __shfl_down_sync(0xffffffffu, o.x, 1);
           if (last) next = MODE == 0 ? __ldg(row + xnext) : row[xnext];
           v[l][0] = o.y; v[l][1] = o.z; v[l][2] = o.w; v[l][3] = next;
+        }
+      }
+      if constexpr (SNAP) {
+        if (active) {  // (rho - rho0, j_x, j_y) of f(., n) as compensated pairs
+          float hs[3][4], ls[3][4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int one[kQ] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+            const int sgn[6] = {1, 1, 1, -1, -1, -1};
+            float f[kQ];
+#pragma unroll
+            for (int l = 0; l < kQ; ++l) f[l] = v[l][c];
+            const float ax[6] = {f[1], f[5], f[8], f[3], f[6], f[7]};
+            const float ay[6] = {f[2], f[5], f[6], f[4], f[7], f[8]};
+            csum_pair(f, one, kQ, hs[0][c], ls[0][c]);
+            csum_pair(ax, sgn, 6, hs[1][c], ls[1][c]);
+            csum_pair(ay, sgn, 6, hs[2][c], ls[2][c]);
+          }
+          const size_t N = (size_t)nx * ny;
+          float *d = reinterpret_cast<float *>(M.snap) + (size_t)snap_slot * 6 * N +
+                     (size_t)y * nx + x;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            __stcs(reinterpret_cast<float4 *>(d + (size_t)(2 * q) * N),
+                   make_float4(hs[q][0], hs[q][1], hs[q][2], hs[q][3]));
+            __stcs(reinterpret_cast<float4 *>(d + (size_t)(2 * q + 1) * N),
+                   make_float4(ls[q][0], ls[q][1], ls[q][2], ls[q][3]));
+          }
         }
       }
       if (active) {
@@ -504,15 +555,15 @@ __global__ void __launch_bounds__(256, PF ? 3 : 1) k_step_f32_vec(const Member *
   }
 }
 
-template <int ROWS, bool PF>
+template <int ROWS, bool PF, bool SNAP = false>
 static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int ntiles, int state,
-                            int grid, dim3 block, cudaStream_t s) {
+                            int grid, dim3 block, cudaStream_t s, int slot = -1) {
   if (state < 2)
-    k_step_f32_vec<ROWS, 0, PF><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+    k_step_f32_vec<ROWS, 0, PF, SNAP><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state, slot);
   else if (state == 2)
-    k_step_f32_vec<ROWS, 1, PF><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+    k_step_f32_vec<ROWS, 1, PF, SNAP><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state, slot);
   else
-    k_step_f32_vec<ROWS, 2, PF><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state);
+    k_step_f32_vec<ROWS, 2, PF, SNAP><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state, slot);
 }
 
 template <int ROWS>
@@ -533,6 +584,22 @@ cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, in
     case 1: launch_vec_rows<1>(d_members, d_tiles, ntiles, state, grid, block, lc.paper_force != 0, s); break;
     case 2: launch_vec_rows<2>(d_members, d_tiles, ntiles, state, grid, block, lc.paper_force != 0, s); break;
     case 4: launch_vec_rows<4>(d_members, d_tiles, ntiles, state, grid, block, lc.paper_force != 0, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// One step with the snapshot of the state it reads recorded into ring slot
+// `slot` (members without the paper forcing or a variable viscosity only).
+cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tiles, int ntiles,
+                                     int state, const LaunchCfg &lc, int slot, cudaStream_t s) {
+  if (ntiles <= 0 || lc.paper_force != 0 || slot < 0 || slot > 2) return cudaErrorInvalidValue;
+  dim3 block(32, lc.block_warps_y);
+  int grid = lc.grid_ctas > 0 ? (lc.grid_ctas < ntiles ? lc.grid_ctas : ntiles) : ntiles;
+  switch (lc.rows_per_warp) {
+    case 1: launch_vec_rows<1, false, true>(d_members, d_tiles, ntiles, state, grid, block, s, slot); break;
+    case 2: launch_vec_rows<2, false, true>(d_members, d_tiles, ntiles, state, grid, block, s, slot); break;
+    case 4: launch_vec_rows<4, false, true>(d_members, d_tiles, ntiles, state, grid, block, s, slot); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -667,13 +734,6 @@ __global__ void k_set_pop(const Member *__restrict__ members, int member, int st
   }
 }
 
-// Error-free addition (Knuth's TwoSum): s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
 // Compensated FP32 sum of FP32 values, returned in FP64: the value of a
 // double-precision sum at FP32 arithmetic cost (GB300 runs FP64 at a small
 // fraction of its FP32 rate).
@@ -742,20 +802,6 @@ __global__ void k_snapshot(const Member *__restrict__ members, int member, int s
       t = local_tau_f64(f, rho, ux, uy, M.tau, M.collision, M.Cs);
     }
     d[3 * N + c] = (t - 0.5) / 3.0;
-  }
-}
-
-// Compensated FP32 sum of FP32 values as the unevaluated pair (s, c): the
-// FP64 sum is (double)s + (double)c (the csum value) and differences of
-// nearby sums can be formed in FP32 as (s - s') + (c - c').
-__device__ __forceinline__ void csum_pair(const float *v, const int *sign, int n, float &s,
-                                          float &c) {
-  s = sign[0] * v[0];
-  c = 0.f;
-  for (int k = 1; k < n; ++k) {
-    float e;
-    two_sum(s, sign[k] * v[k], s, e);
-    c += e;
   }
 }
 
