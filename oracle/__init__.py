@@ -94,16 +94,17 @@ def _load():
             lib.orc_objective.argtypes = [I, I, D, P, P, I, I, I, I, I, P]
             lib.orc_objective.restype = I
             lib.orc_lattice.argtypes = [P, P, P]
-            lib.orc3_lattice.argtypes = [P, P, P, P]
-            lib.orc3_feq.argtypes = [D, D, D, D, P]
-            lib.orc3_run.argtypes = [I, I, I, D, I, D, I, D, P, I]
+            lib.orc3_lattice.argtypes = [I, P, P, P, P]
+            lib.orc3_lattice.restype = I
+            lib.orc3_feq.argtypes = [I, D, D, D, D, P]
+            lib.orc3_run.argtypes = [I, I, I, I, D, I, D, I, D, P, I]
             lib.orc3_run.restype = I
-            lib.orc3_init.argtypes = [I, I, I, P, P, P, P, P]
-            lib.orc3_moments.argtypes = [I, I, I, I, D, I, D, P, P, P, P, P, P, P, P]
+            lib.orc3_init.argtypes = [I, I, I, I, P, P, P, P, P]
+            lib.orc3_moments.argtypes = [I, I, I, I, I, D, I, D, P, P, P, P, P, P, P, P]
             lib.orc3_d.argtypes = [I, I, I, I, P, P]
             lib.orc3_terms.argtypes = [I, I, I, D, P, P, P, P, P, P, P, P]
             lib.orc3_terms.restype = I
-            lib.orc3_terms_from_populations.argtypes = [I, I, I, D, I, D, I, D, P, P, P, P]
+            lib.orc3_terms_from_populations.argtypes = [I, I, I, I, D, I, D, I, D, P, P, P, P]
             lib.orc3_terms_from_populations.restype = I
             lib.orc3_box_mean.argtypes = [I, I, I, P, I, I, I, I]
             lib.orc3_box_mean.restype = D
@@ -444,37 +445,47 @@ def objective(f0, tau, force: Force, n0, n1, bx, by, L):
 
 
 # --------------------------------------------------------------------------
-# Three dimensions (D3Q19; lbm_oracle3d.c).  Populations f[19, nz, ny, nx],
-# fields A[nz, ny, nx]; force = (kind, F0, kf, alpha) with kind 1 the cyclic
+# Three dimensions (D3Q19 and D3Q27; lbm_oracle3d.c).  Populations f[q, nz,
+# ny, nx] (q = 19 or 27, read from the array's first axis), fields
+# A[nz, ny, nx]; force = (kind, F0, kf, alpha) with kind 1 the cyclic
 # Kolmogorov force F0 (sin(2 pi kf y/ny), sin(2 pi kf z/nz), sin(2 pi kf x/nx)).
 # --------------------------------------------------------------------------
 
-def lattice3():
-    cx, cy, cz = (np.zeros(19, np.int32) for _ in range(3))
-    t = np.zeros(19)
-    _load().orc3_lattice(_p(cx), _p(cy), _p(cz), _p(t))
+def _q3(q):
+    if q not in (19, 27):
+        raise ValueError("3D lattice must be D3Q19 or D3Q27")
+    return q
+
+
+def lattice3(q=19):
+    q = _q3(q)
+    cx, cy, cz = (np.zeros(q, np.int32) for _ in range(3))
+    t = np.zeros(q)
+    _load().orc3_lattice(q, _p(cx), _p(cy), _p(cz), _p(t))
     return cx, cy, cz, t
 
 
-def feq3(rho, ux, uy, uz):
-    out = np.zeros(19)
-    _load().orc3_feq(float(rho), float(ux), float(uy), float(uz), _p(out))
+def feq3(rho, ux, uy, uz, q=19):
+    q = _q3(q)
+    out = np.zeros(q)
+    _load().orc3_feq(q, float(rho), float(ux), float(uy), float(uz), _p(out))
     return out
 
 
-def init3(rho, ux, uy, uz):
+def init3(rho, ux, uy, uz, q=19):
+    q = _q3(q)
     rho, ux, uy, uz = (_f64(a) for a in (rho, ux, uy, uz))
     nz, ny, nx = rho.shape
-    f = np.empty((19, nz, ny, nx))
-    _load().orc3_init(nx, ny, nz, _p(rho), _p(ux), _p(uy), _p(uz), _p(f))
+    f = np.empty((q, nz, ny, nx))
+    _load().orc3_init(q, nx, ny, nz, _p(rho), _p(ux), _p(uy), _p(uz), _p(f))
     return f
 
 
 def run3(f, nsteps, tau, kind=0, F0=0.0, kf=0, alpha=0.0):
     f = _f64(f).copy()
-    _, nz, ny, nx = f.shape
-    if _load().orc3_run(nx, ny, nz, float(tau), int(kind), float(F0), int(kf), float(alpha),
-                        _p(f), int(nsteps)) != 0:
+    q, nz, ny, nx = f.shape
+    if _load().orc3_run(_q3(q), nx, ny, nz, float(tau), int(kind), float(F0), int(kf),
+                        float(alpha), _p(f), int(nsteps)) != 0:
         raise MemoryError("oracle 3D run failed")
     return f
 
@@ -482,9 +493,9 @@ def run3(f, nsteps, tau, kind=0, F0=0.0, kf=0, alpha=0.0):
 def moments3(f, kind=0, F0=0.0, kf=0, alpha=0.0):
     """dict rho, ux, uy, uz (u = (j + F/2)/rho), Fx, Fy, Fz (F = F_ext - alpha j)."""
     f = _f64(f)
-    _, nz, ny, nx = f.shape
+    q, nz, ny, nx = f.shape
     out = {k: np.empty((nz, ny, nx)) for k in ("rho", "ux", "uy", "uz", "Fx", "Fy", "Fz")}
-    _load().orc3_moments(nx, ny, nz, int(kind), float(F0), int(kf), float(alpha), _p(f),
+    _load().orc3_moments(_q3(q), nx, ny, nz, int(kind), float(F0), int(kf), float(alpha), _p(f),
                          *(_p(out[k]) for k in ("rho", "ux", "uy", "uz", "Fx", "Fy", "Fz")))
     return out
 
@@ -515,10 +526,12 @@ def terms3(tau, rho3, ux3, uy3, uz3, Fx, Fy, Fz):
 
 def terms3_from_populations(f_n, f_n1, f_n2, tau, kind=0, F0=0.0, kf=0, alpha=0.0):
     f_n, f_n1, f_n2 = _f64(f_n), _f64(f_n1), _f64(f_n2)
-    _, nz, ny, nx = f_n.shape
+    q, nz, ny, nx = f_n.shape
+    assert f_n1.shape == f_n.shape and f_n2.shape == f_n.shape
     out = np.empty((NT, nz, ny, nx))
-    rc = _load().orc3_terms_from_populations(nx, ny, nz, float(tau), int(kind), float(F0), int(kf),
-                                             float(alpha), _p(f_n), _p(f_n1), _p(f_n2), _p(out))
+    rc = _load().orc3_terms_from_populations(_q3(q), nx, ny, nz, float(tau), int(kind), float(F0),
+                                             int(kf), float(alpha), _p(f_n), _p(f_n1), _p(f_n2),
+                                             _p(out))
     if rc != 0:
         raise MemoryError("oracle 3D terms failed")
     return out

@@ -1,7 +1,7 @@
 /*
  * Oracle for the three-dimensional extension of the method of Tauzin,
  * Biferale, Sbragaglia, Gupta, Toschi, Bartel, Ehrhardt (Comput. & Fluids
- * 172, 2018): the D3Q19 lattice BGK of eq. (1) with the eq. (2) equilibrium
+ * 172, 2018): the D3Q19 and D3Q27 lattice BGK of eq. (1) with the eq. (2) equilibrium
  * and exact-difference forcing, and the sub-volume energy and enstrophy
  * balance of eqs. (8)-(13) in their general index forms, where the vortex
  * stretching term RHS^{Omega,6} = omega_i omega_j d_j u_i no longer vanishes
@@ -16,6 +16,11 @@
  *     c_7..18 = (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1),
  *     (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1);
  *     weights 1/3, 1/18, 1/36; c_s^2 = 1/3.
+ *   - D3Q27 order: the D3Q19 order, then the corners c_19..26 = (1,1,1),
+ *     (-1,-1,-1), (1,1,-1), (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1),
+ *     (1,-1,-1); weights 8/27, 2/27, 1/54, 1/216 by |c|^2 = 0..3.  The
+ *     lattice is the first argument (q = 19 or 27) of every function that
+ *     touches populations.
  *   - Arrays: f[((l nz + z) ny + y) nx + x], fields A[(z ny + y) nx + x].
  *   - Force kind 1: F_ext = F0 (sin(2 pi kf y/ny), sin(2 pi kf z/nz),
  *     sin(2 pi kf x/nx)), plus drag -alpha j; EDM as in two dimensions.
@@ -26,35 +31,51 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define Q3 19
-static const int C3X[Q3] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-static const int C3Y[Q3] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-static const int C3Z[Q3] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+/* Velocity sets.  D3Q27 = rest, 6 axis, 12 edge and 8 corner velocities;
+ * D3Q19 is its first 19 entries (no corners).  Weights by |c|^2:
+ *   D3Q19: 1/3, 1/18, 1/36;  D3Q27: 8/27, 2/27, 1/54, 1/216;
+ * both with c_s^2 = 1/3 and the same eq. (2) equilibrium. */
+#define QMAX 27
+static const int C3X[QMAX] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0,
+                              1, -1, 1, -1, 1, -1, -1, 1};
+static const int C3Y[QMAX] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1,
+                              1, -1, 1, -1, -1, 1, 1, -1};
+static const int C3Z[QMAX] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1,
+                              1, -1, -1, 1, 1, -1, 1, -1};
 static const double CS2_3 = 1.0 / 3.0;
 static const double PI3 = 3.14159265358979323846;
 
-static double w3(int l) { return l == 0 ? 1.0 / 3.0 : (l <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+static double w3(int q, int l) {
+  const int c2 = C3X[l] * C3X[l] + C3Y[l] * C3Y[l] + C3Z[l] * C3Z[l];
+  if (q == 27) return c2 == 0 ? 8.0 / 27.0 : (c2 == 1 ? 2.0 / 27.0 : (c2 == 2 ? 1.0 / 54.0 : 1.0 / 216.0));
+  return c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+static int valid_q(int q) { return q == 19 || q == 27; }
 
 static int wrap3(int i, int n) {
   int r = i % n;
   return r < 0 ? r + n : r;
 }
 
-void orc3_lattice(int *cx, int *cy, int *cz, double *t) {
-  for (int l = 0; l < Q3; ++l) {
+/* The lattice of q = 19 or 27 velocities; returns -1 for another q. */
+int orc3_lattice(int q, int *cx, int *cy, int *cz, double *t) {
+  if (!valid_q(q)) return -1;
+  for (int l = 0; l < q; ++l) {
     cx[l] = C3X[l];
     cy[l] = C3Y[l];
     cz[l] = C3Z[l];
-    t[l] = w3(l);
+    t[l] = w3(q, l);
   }
+  return 0;
 }
 
-/* Eq. (2) on D3Q19. */
-void orc3_feq(double rho, double ux, double uy, double uz, double *feq) {
+/* Eq. (2) on D3Qq. */
+void orc3_feq(int q, double rho, double ux, double uy, double uz, double *feq) {
   double uu = ux * ux + uy * uy + uz * uz;
-  for (int l = 0; l < Q3; ++l) {
+  for (int l = 0; l < q; ++l) {
     double cu = C3X[l] * ux + C3Y[l] * uy + C3Z[l] * uz;
-    feq[l] = w3(l) * rho * (1.0 + cu / CS2_3 + cu * cu / (2.0 * CS2_3 * CS2_3) - uu / (2.0 * CS2_3));
+    feq[l] = w3(q, l) * rho * (1.0 + cu / CS2_3 + cu * cu / (2.0 * CS2_3 * CS2_3) - uu / (2.0 * CS2_3));
   }
 }
 
@@ -69,9 +90,9 @@ void orc3_force_ext(int nx, int ny, int nz, int kind, double F0, int kf, int x, 
   }
 }
 
-static void moments3(const double *fc, double *rho, double *jx, double *jy, double *jz) {
+static void moments3(int q, const double *fc, double *rho, double *jx, double *jy, double *jz) {
   double r = 0, a = 0, b = 0, c = 0;
-  for (int l = 0; l < Q3; ++l) {
+  for (int l = 0; l < q; ++l) {
     r += fc[l];
     a += C3X[l] * fc[l];
     b += C3Y[l] * fc[l];
@@ -84,62 +105,64 @@ static void moments3(const double *fc, double *rho, double *jx, double *jy, doub
 }
 
 /* BGK collision of one cell with the EDM term, F = F_ext - alpha j. */
-void orc3_collide_cell(const double *fin, double tau, double Fex, double Fey, double Fez,
+void orc3_collide_cell(int q, const double *fin, double tau, double Fex, double Fey, double Fez,
                        double alpha, double *fout) {
   double rho, jx, jy, jz;
-  moments3(fin, &rho, &jx, &jy, &jz);
+  moments3(q, fin, &rho, &jx, &jy, &jz);
   double ux = jx / rho, uy = jy / rho, uz = jz / rho;
   double Fx = Fex - alpha * jx, Fy = Fey - alpha * jy, Fz = Fez - alpha * jz;
-  double feq[Q3], fsh[Q3];
-  orc3_feq(rho, ux, uy, uz, feq);
-  orc3_feq(rho, ux + Fx / rho, uy + Fy / rho, uz + Fz / rho, fsh);
-  for (int l = 0; l < Q3; ++l) fout[l] = fin[l] - (fin[l] - feq[l]) / tau + (fsh[l] - feq[l]);
+  double feq[QMAX], fsh[QMAX];
+  orc3_feq(q, rho, ux, uy, uz, feq);
+  orc3_feq(q, rho, ux + Fx / rho, uy + Fy / rho, uz + Fz / rho, fsh);
+  for (int l = 0; l < q; ++l) fout[l] = fin[l] - (fin[l] - feq[l]) / tau + (fsh[l] - feq[l]);
 }
 
 /* One step of eq. (1): collide, then stream f_l(x + c_l) = f*_l(x). */
-int orc3_step(int nx, int ny, int nz, double tau, int kind, double F0, int kf, double alpha,
-              double *f, double *s) {
+int orc3_step(int q, int nx, int ny, int nz, double tau, int kind, double F0, int kf,
+              double alpha, double *f, double *s) {
+  if (!valid_q(q)) return -1;
   size_t N = (size_t)nx * ny * nz;
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         size_t c = ((size_t)z * ny + y) * nx + x;
-        double a[Q3], b[Q3], Fx, Fy, Fz;
-        for (int l = 0; l < Q3; ++l) a[l] = f[l * N + c];
+        double a[QMAX], b[QMAX], Fx, Fy, Fz;
+        for (int l = 0; l < q; ++l) a[l] = f[l * N + c];
         orc3_force_ext(nx, ny, nz, kind, F0, kf, x, y, z, &Fx, &Fy, &Fz);
-        orc3_collide_cell(a, tau, Fx, Fy, Fz, alpha, b);
-        for (int l = 0; l < Q3; ++l) {
+        orc3_collide_cell(q, a, tau, Fx, Fy, Fz, alpha, b);
+        for (int l = 0; l < q; ++l) {
           size_t d = ((size_t)wrap3(z + C3Z[l], nz) * ny + wrap3(y + C3Y[l], ny)) * nx +
                      wrap3(x + C3X[l], nx);
           s[l * N + d] = b[l];
         }
       }
-  memcpy(f, s, sizeof(double) * Q3 * N);
+  memcpy(f, s, sizeof(double) * q * N);
   return 0;
 }
 
-int orc3_run(int nx, int ny, int nz, double tau, int kind, double F0, int kf, double alpha,
-             double *f, int nsteps) {
-  double *s = (double *)malloc(sizeof(double) * Q3 * (size_t)nx * ny * nz);
+int orc3_run(int q, int nx, int ny, int nz, double tau, int kind, double F0, int kf,
+             double alpha, double *f, int nsteps) {
+  if (!valid_q(q)) return -1;
+  double *s = (double *)malloc(sizeof(double) * q * (size_t)nx * ny * nz);
   if (!s) return -1;
-  for (int n = 0; n < nsteps; ++n) orc3_step(nx, ny, nz, tau, kind, F0, kf, alpha, f, s);
+  for (int n = 0; n < nsteps; ++n) orc3_step(q, nx, ny, nz, tau, kind, F0, kf, alpha, f, s);
   free(s);
   return 0;
 }
 
-void orc3_init(int nx, int ny, int nz, const double *rho, const double *ux, const double *uy,
-               const double *uz, double *f) {
+void orc3_init(int q, int nx, int ny, int nz, const double *rho, const double *ux,
+               const double *uy, const double *uz, double *f) {
   size_t N = (size_t)nx * ny * nz;
   for (size_t c = 0; c < N; ++c) {
-    double e[Q3];
-    orc3_feq(rho[c], ux[c], uy[c], uz[c], e);
-    for (int l = 0; l < Q3; ++l) f[l * N + c] = e[l];
+    double e[QMAX];
+    orc3_feq(q, rho[c], ux[c], uy[c], uz[c], e);
+    for (int l = 0; l < q; ++l) f[l * N + c] = e[l];
   }
 }
 
 /* rho, bare momentum j and u = (j + F/2)/rho (F = F_ext - alpha j); any
  * output may be NULL. */
-void orc3_moments(int nx, int ny, int nz, int kind, double F0, int kf, double alpha,
+void orc3_moments(int q, int nx, int ny, int nz, int kind, double F0, int kf, double alpha,
                   const double *f, double *rho, double *ux, double *uy, double *uz,
                   double *Fx_out, double *Fy_out, double *Fz_out) {
   size_t N = (size_t)nx * ny * nz;
@@ -147,9 +170,9 @@ void orc3_moments(int nx, int ny, int nz, int kind, double F0, int kf, double al
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         size_t c = ((size_t)z * ny + y) * nx + x;
-        double a[Q3], r, jx, jy, jz, Fex, Fey, Fez;
-        for (int l = 0; l < Q3; ++l) a[l] = f[l * N + c];
-        moments3(a, &r, &jx, &jy, &jz);
+        double a[QMAX], r, jx, jy, jz, Fex, Fey, Fez;
+        for (int l = 0; l < q; ++l) a[l] = f[l * N + c];
+        moments3(q, a, &r, &jx, &jy, &jz);
         orc3_force_ext(nx, ny, nz, kind, F0, kf, x, y, z, &Fex, &Fey, &Fez);
         double Fx = Fex - alpha * jx, Fy = Fey - alpha * jy, Fz = Fez - alpha * jz;
         if (rho) rho[c] = r;
@@ -335,9 +358,10 @@ int orc3_terms(int nx, int ny, int nz, double tau, const double *const *rho,
   return 0;
 }
 
-int orc3_terms_from_populations(int nx, int ny, int nz, double tau, int kind, double F0, int kf,
-                                double alpha, const double *f_n, const double *f_n1,
+int orc3_terms_from_populations(int q, int nx, int ny, int nz, double tau, int kind, double F0,
+                                int kf, double alpha, const double *f_n, const double *f_n1,
                                 const double *f_n2, double *terms) {
+  if (!valid_q(q)) return -1;
   size_t N = (size_t)nx * ny * nz;
   double *b = (double *)malloc(sizeof(double) * N * 15);
   if (!b) return -1;
@@ -348,7 +372,7 @@ int orc3_terms_from_populations(int nx, int ny, int nz, double tau, int kind, do
     ux[m] = b + (4 * m + 1) * N;
     uy[m] = b + (4 * m + 2) * N;
     uz[m] = b + (4 * m + 3) * N;
-    orc3_moments(nx, ny, nz, kind, F0, kf, alpha, fs[m], rho[m], ux[m], uy[m], uz[m],
+    orc3_moments(q, nx, ny, nz, kind, F0, kf, alpha, fs[m], rho[m], ux[m], uy[m], uz[m],
                  m == 0 ? b + 12 * N : NULL, m == 0 ? b + 13 * N : NULL,
                  m == 0 ? b + 14 * N : NULL);
   }

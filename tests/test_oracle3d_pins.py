@@ -1,4 +1,4 @@
-"""Pins of the three-dimensional (D3Q19) oracle against facts fixed by the
+"""Pins of the three-dimensional (D3Q19, D3Q27) oracle against facts fixed by the
 lattice, by the mathematics and by an independent symbolic evaluation of
 the general index forms of eqs. (8)-(11), whose vortex-stretching term
 RHS^{Omega,6} does not vanish in three dimensions."""
@@ -19,10 +19,12 @@ def _smooth3(n, seed, amp):
     return amp * out / np.max(np.abs(out))
 
 
-def test_d3q19_isotropy(orc):
+@pytest.mark.parametrize("q", [19, 27])
+def test_d3q_isotropy(orc, q):
     """sum t = 1, sum t c = 0, sum t c c = cs^2 I, fourth moments cs^4
-    (delta delta + 2 perms), opposite pairs."""
-    cx, cy, cz, t = orc.lattice3()
+    (delta delta + 2 perms), opposite pairs, no repeated velocity."""
+    cx, cy, cz, t = orc.lattice3(q)
+    assert len(t) == q and len({(a, b, c) for a, b, c in zip(cx, cy, cz)}) == q
     C = np.stack([cx, cy, cz], 1).astype(float)
     cs2 = 1.0 / 3.0
     assert abs(t.sum() - 1) < 1e-15
@@ -33,18 +35,37 @@ def test_d3q19_isotropy(orc):
     want = cs2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
                        + np.einsum("ad,bc->abcd", d, d))
     np.testing.assert_allclose(M4, want, atol=1e-15)
-    for l in range(19):
-        assert sum(1 for m in range(19) if (C[m] == -C[l]).all()) == 1
+    for l in range(q):
+        assert sum(1 for m in range(q) if (C[m] == -C[l]).all()) == 1
 
 
-def test_d3q19_step_conserves_mass_and_adds_the_force(orc):
+def test_d3q27_is_the_tensor_product_lattice(orc):
+    """D3Q27 = D1Q3 x D1Q3 x D1Q3: every velocity of {-1, 0, 1}^3 once, with
+    weight w(c_x) w(c_y) w(c_z), w(0) = 2/3, w(+-1) = 1/6; its first 19
+    velocities are the D3Q19 set in the same order."""
+    cx, cy, cz, t = orc.lattice3(27)
+    w1 = {0: 2.0 / 3.0, 1: 1.0 / 6.0, -1: 1.0 / 6.0}
+    assert {(a, b, c) for a, b, c in zip(cx, cy, cz)} == {
+        (a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)}
+    for a, b, c, tl in zip(cx, cy, cz, t):
+        assert abs(tl - w1[a] * w1[b] * w1[c]) < 1e-16
+    c19 = orc.lattice3(19)
+    for k in range(3):
+        assert np.array_equal(c19[k], (cx, cy, cz)[k][:19])
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_d3q_step_conserves_mass_and_adds_the_force(orc, q):
     n = 6
     rho, ux, uy, uz = 1 + _smooth3(n, 1, 0.01), _smooth3(n, 2, 0.03), _smooth3(n, 3, 0.03), \
         _smooth3(n, 4, 0.03)
-    f = orc.init3(rho, ux, uy, uz)
+    f = orc.init3(rho, ux, uy, uz, q=q)
     F0, kf, a = 3e-4, 1, 2e-3
     g = orc.run3(f, 1, 0.57, 1, F0, kf, a)
-    cx, cy, cz, _ = orc.lattice3()
+    cx, cy, cz, _ = orc.lattice3(q)
+    m = orc.moments3(f)
+    np.testing.assert_allclose(m["rho"], rho, rtol=1e-14)  # f_eq carries (rho, rho u)
+    np.testing.assert_allclose(m["ux"], ux, atol=1e-15)
     m0 = orc.moments3(f, 1, F0, kf, a)
     assert abs(g.sum() - f.sum()) < 1e-12
     for C, Fk in ((cx, "Fx"), (cy, "Fy"), (cz, "Fz")):
@@ -52,14 +73,15 @@ def test_d3q19_step_conserves_mass_and_adds_the_force(orc):
         assert abs(gain - m0[Fk].sum()) < 1e-13
 
 
-def test_d3q19_shear_wave_decay_rate(orc):
+@pytest.mark.parametrize("q", [19, 27])
+def test_d3q_shear_wave_decay_rate(orc, q):
     """u_x = U sin(2 pi z / N) decays as exp(-nu k^2 t), nu = (tau - 1/2)/3,
     to the lattice's O(k^2) corrections (within 1%)."""
     N, U, tau, steps = 32, 1e-4, 0.8, 300
     z = np.arange(N)
     shape = (N, 2, 2)
     ux = np.broadcast_to((U * np.sin(2 * np.pi * z / N))[:, None, None], shape).copy()
-    f = orc.init3(np.ones(shape), ux, np.zeros(shape), np.zeros(shape))
+    f = orc.init3(np.ones(shape), ux, np.zeros(shape), np.zeros(shape), q=q)
     g = orc.run3(f, steps, tau)
     amp = orc.moments3(g)["ux"][:, 0, 0]
     fit = np.sum(amp * np.sin(2 * np.pi * z / N)) / np.sum(np.sin(2 * np.pi * z / N) ** 2)
