@@ -1,6 +1,6 @@
 /*
  * Three-dimensional extension of the GB300 library (liblbm.so): the D3Q19
- * lattice BGK of eq. (1) with the eq. (2) equilibrium and exact-difference
+ * and D3Q27 lattice BGK of eq. (1) with the eq. (2) equilibrium and exact-difference
  * forcing (Sec. 3) of Tauzin et al. (2018), and the sub-volume energy and
  * enstrophy balance of eqs. (8)-(13) in their general index forms, where
  * the vortex-stretching term RHS^{Omega,6} = omega_i omega_j d_j u_i does
@@ -10,9 +10,13 @@
  *
  * Lattice order: c_0 = 0; c_1..6 = +x, -x, +y, -y, +z, -z; c_7..18 =
  * (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1),
- * (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1); weights 1/3, 1/18,
- * 1/36.  Public populations: double[19][nz][ny][nx] (x fastest), the
- * pre-collision f_l(x, n) of eq. (1); fields double[nz][ny][nx].
+ * (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1): D3Q19, weights 1/3,
+ * 1/18, 1/36.  D3Q27 adds the corners c_19..26 = (1,1,1), (-1,-1,-1),
+ * (1,1,-1), (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1), (1,-1,-1), weights
+ * 8/27, 2/27, 1/54, 1/216 by |c|^2 = 0..3; both with c_s^2 = 1/3 and the
+ * eq. (2) equilibrium.  Public populations: double[q][nz][ny][nx] (x
+ * fastest, q = 19 or 27), the pre-collision f_l(x, n) of eq. (1); fields
+ * double[nz][ny][nx].
  */
 #ifndef LBM3D_H
 #define LBM3D_H
@@ -43,6 +47,8 @@ typedef struct lbm3d_config {
   int diag_every;   /* > 0: lbm3d_step records the snapshots of the times
                        k diag_every - 2, -1, 0 that eq. (17) needs */
   void *cuda_stream; /* cudaStream_t of all work; NULL = default stream */
+  int lattice;      /* velocity set of every member: 19 (D3Q19; also 0) or 27
+                       (D3Q27); anything else is LBM_ERR_ARG */
 } lbm3d_config;
 
 typedef struct lbm3d_handle lbm3d_handle;
@@ -65,7 +71,7 @@ int lbm3d_init_fields(lbm3d_handle *h, int member, const double *rho, const doub
 int lbm3d_step(lbm3d_handle *h, int nsteps);
 long long lbm3d_time(const lbm3d_handle *h);
 
-/* Public populations double[19][nz][ny][nx] of one member, host or device
+/* Public populations double[q][nz][ny][nx] of one member, host or device
  * (index for index the oracle's f(., n)); set accepts the same layout. */
 int lbm3d_get_populations(lbm3d_handle *h, int member, double *f, int on_device);
 int lbm3d_set_populations(lbm3d_handle *h, int member, const double *f, int on_device);

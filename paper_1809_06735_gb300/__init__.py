@@ -56,7 +56,7 @@ class _MemberCfg3(ctypes.Structure):
 class _Config3(ctypes.Structure):
     _fields_ = [("n_members", ctypes.c_int), ("members", ctypes.POINTER(_MemberCfg3)),
                 ("precision", ctypes.c_int), ("diag_every", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("lattice", ctypes.c_int)]
 
 
 class _Config(ctypes.Structure):
@@ -443,11 +443,12 @@ class Member3:
 
 
 class Lattice3D:
-    """Handle over D3Q19 members (include/lbm3d.h): FP32 deviation or FP64
-    storage, workspace in one torch uint8 CUDA tensor, work on ``stream``."""
+    """Handle over D3Q19 or D3Q27 members (``lattice`` 19 or 27;
+    include/lbm3d.h): FP32 deviation or FP64 storage, workspace in one torch
+    uint8 CUDA tensor, work on ``stream``."""
 
     def __init__(self, members: Sequence[Member3], precision: int = 32, diag_every: int = 0,
-                 stream=None, device=None):
+                 stream=None, device=None, lattice: int = 19):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -455,8 +456,9 @@ class Lattice3D:
         self.device = torch.device(device if device is not None else "cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._arr = (_MemberCfg3 * len(self.members))(*[m.c() for m in self.members])
+        self.q = 27 if lattice == 27 else 19
         self._cfg = _Config3(len(self.members), self._arr, precision, diag_every,
-                             ctypes.c_void_p(self.stream.cuda_stream))
+                             ctypes.c_void_p(self.stream.cuda_stream), int(lattice))
         n = ctypes.c_size_t()
         self._check(self.lib.lbm3d_workspace_size(ctypes.byref(self._cfg), ctypes.byref(n)))
         self.workspace = torch.empty(n.value + 256, dtype=torch.uint8, device=self.device)
@@ -503,7 +505,7 @@ class Lattice3D:
         self._check(self.lib.lbm3d_record_snapshot(self.h))
 
     def get_populations_host(self, member: int) -> np.ndarray:
-        out = np.empty((19,) + self._shape(member))
+        out = np.empty((self.q,) + self._shape(member))
         self._check(self.lib.lbm3d_get_populations(self.h, member, _ptr(out), 0))
         return out
 

@@ -1,4 +1,4 @@
-// Three-dimensional extension (include/lbm3d.h): D3Q19 BGK stream-collide
+// Three-dimensional extension (include/lbm3d.h): D3Q19 and D3Q27 BGK stream-collide
 // with exact-difference forcing (eq. (1), eq. (2), Sec. 3 of Tauzin et al.
 // 2018) and the sub-volume energy/enstrophy balance of eqs. (8)-(13) in the
 // general index forms, with vortex stretching, over L x L x L boxes.
@@ -24,25 +24,37 @@
 
 namespace {
 
-constexpr int kQ3 = 19;
+// Velocity sets: D3Q27 = rest, 6 axis, 12 edge, 8 corner velocities in the
+// order of include/lbm3d.h; D3Q19 is its first 19 entries.  Weights by
+// |c|^2: D3Q19 1/3, 1/18, 1/36; D3Q27 8/27, 2/27, 1/54, 1/216.
+constexpr int kQmax = 27;
 __host__ __device__ constexpr int c3x(int l) {
-  return (l == 1 || l == 7 || l == 9 || l == 11 || l == 13) ? 1
-         : (l == 2 || l == 8 || l == 10 || l == 12 || l == 14) ? -1 : 0;
+  return (l == 1 || l == 7 || l == 9 || l == 11 || l == 13 || l == 19 || l == 21 || l == 23 ||
+          l == 26) ? 1
+         : (l == 2 || l == 8 || l == 10 || l == 12 || l == 14 || l == 20 || l == 22 || l == 24 ||
+            l == 25) ? -1 : 0;
 }
 __host__ __device__ constexpr int c3y(int l) {
-  return (l == 3 || l == 7 || l == 10 || l == 15 || l == 17) ? 1
-         : (l == 4 || l == 8 || l == 9 || l == 16 || l == 18) ? -1 : 0;
+  return (l == 3 || l == 7 || l == 10 || l == 15 || l == 17 || l == 19 || l == 21 || l == 24 ||
+          l == 25) ? 1
+         : (l == 4 || l == 8 || l == 9 || l == 16 || l == 18 || l == 20 || l == 22 || l == 23 ||
+            l == 26) ? -1 : 0;
 }
 __host__ __device__ constexpr int c3z(int l) {
-  return (l == 5 || l == 11 || l == 14 || l == 15 || l == 18) ? 1
-         : (l == 6 || l == 12 || l == 13 || l == 16 || l == 17) ? -1 : 0;
+  return (l == 5 || l == 11 || l == 14 || l == 15 || l == 18 || l == 19 || l == 22 || l == 23 ||
+          l == 25) ? 1
+         : (l == 6 || l == 12 || l == 13 || l == 16 || l == 17 || l == 20 || l == 21 || l == 24 ||
+            l == 26) ? -1 : 0;
 }
+template <int Q>
 __host__ __device__ constexpr double w3(int l) {
-  return l == 0 ? 1.0 / 3.0 : (l <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+  return Q == 27 ? (l == 0 ? 8.0 / 27.0 : (l <= 6 ? 2.0 / 27.0 : (l <= 18 ? 1.0 / 54.0 : 1.0 / 216.0)))
+                 : (l == 0 ? 1.0 / 3.0 : (l <= 6 ? 1.0 / 18.0 : 1.0 / 36.0));
 }
 
 struct M3 {
-  int nx, ny, nz, force_kind, kf, pad;
+  int nx, ny, nz, force_kind, kf, q;  // q: 19 or 27 velocities
+  long long item0, items;  // the member's work items of the four-cell kernel (0: not in it)
   double tau, omega, rho0, F0, alpha, nu;
   float rho0_f, omega_f, alpha_f, F0_f;
   size_t N;
@@ -69,11 +81,11 @@ __device__ __forceinline__ void force3(const M3 &M, const T *tab, int x, int y, 
 }
 
 // BGK + EDM collision of one cell in storage form (FP32: deviations).
-template <typename T>
-__device__ __forceinline__ void collide3(T v[kQ3], T rho0, T om, T Fex, T Fey, T Fez, T alpha) {
+template <typename T, int Q>
+__device__ __forceinline__ void collide3(T v[Q], T rho0, T om, T Fex, T Fey, T Fez, T alpha) {
   T dr = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
-  for (int l = 0; l < kQ3; ++l) {
+  for (int l = 0; l < Q; ++l) {
     dr += v[l];
     jx += (T)c3x(l) * v[l];
     jy += (T)c3y(l) * v[l];
@@ -88,8 +100,8 @@ __device__ __forceinline__ void collide3(T v[kQ3], T rho0, T om, T Fex, T Fey, T
   const T usq = ux * ux + uy * uy + uz * uz;
   const T dsq = dux * (T(2) * ux + dux) + duy * (T(2) * uy + duy) + duz * (T(2) * uz + duz);
 #pragma unroll
-  for (int l = 0; l < kQ3; ++l) {
-    const T t = (T)w3(l);
+  for (int l = 0; l < Q; ++l) {
+    const T t = (T)w3<Q>(l);
     const T cu = (T)c3x(l) * ux + (T)c3y(l) * uy + (T)c3z(l) * uz;
     const T cd = (T)c3x(l) * dux + (T)c3y(l) * duy + (T)c3z(l) * duz;
     T eq;
@@ -102,7 +114,7 @@ __device__ __forceinline__ void collide3(T v[kQ3], T rho0, T om, T Fex, T Fey, T
   }
 }
 
-template <typename T>
+template <typename T, int Q>
 __global__ void __launch_bounds__(256) k3_step(const M3 *__restrict__ ms, int member, int cur) {
   const M3 &M = ms[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y,
@@ -111,23 +123,92 @@ __global__ void __launch_bounds__(256) k3_step(const M3 *__restrict__ ms, int me
   const T *src = static_cast<const T *>(M.pop[cur]);
   T *dst = static_cast<T *>(M.pop[cur ^ 1]);
   const size_t N = M.N;
-  T v[kQ3];
+  T v[Q];
 #pragma unroll
-  for (int l = 0; l < kQ3; ++l)
+  for (int l = 0; l < Q; ++l)
     v[l] = src[(size_t)l * N + cell(M, wrp(x - c3x(l), M.nx), wrp(y - c3y(l), M.ny),
                                     wrp(z - c3z(l), M.nz))];
   T fx, fy, fz;
   force3<T>(M, static_cast<const T *>(M.ftab), x, y, z, fx, fy, fz);
   if constexpr (sizeof(T) == 4)
-    collide3<float>(v, M.rho0_f, M.omega_f, fx, fy, fz, M.alpha_f);
+    collide3<float, Q>(v, M.rho0_f, M.omega_f, fx, fy, fz, M.alpha_f);
   else
-    collide3<double>(v, 0.0, M.omega, fx, fy, fz, M.alpha);
+    collide3<double, Q>(v, 0.0, M.omega, fx, fy, fz, M.alpha);
   const size_t c = cell(M, x, y, z);
 #pragma unroll
-  for (int l = 0; l < kQ3; ++l) dst[(size_t)l * N + c] = v[l];
+  for (int l = 0; l < Q; ++l) dst[(size_t)l * N + c] = v[l];
 }
 
-template <typename T>
+// FP32 stream-collide with 4 consecutive cells per lane (nx % 4 == 0), all
+// such members in one persistent launch: a work item is 4 rows (y0 .. y0+3)
+// of a 128-cell x segment of one z plane of one member, a warp per row; the
+// items of every member are numbered consecutively (M3::item0, M3::items).
+// Each population is one aligned 16-byte load per lane from its source row
+// (y - c_y, z - c_z); the -+1 x-shift is a warp shuffle with one scalar
+// load at the segment's edges (the periodic wrap included), as in 2D.
+template <int Q>
+__global__ void __launch_bounds__(128) k3_step_vec(const M3 *__restrict__ ms, int n_members,
+                                                   long long n_items, int cur) {
+  const int lane = threadIdx.x;
+  int m = 0;
+  for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
+    while (it >= ms[m].item0 + ms[m].items) ++m;  // items ascend with the member
+    const M3 &M = ms[m];
+    const int nx = M.nx, ny = M.ny, nz = M.nz;
+    const long long li = it - M.item0;
+    const int gx = (nx + 127) / 128, gy = (ny + 3) / 4;
+    const int xs = (int)(li % gx), yg = (int)((li / gx) % gy), z = (int)(li / ((long long)gx * gy));
+    const int x = xs * 128 + 4 * lane, y = yg * 4 + threadIdx.y;
+    if (y >= ny) continue;  // whole warps
+    const bool active = x < nx;
+    const bool last = active && (lane == 31 || x + 4 >= nx);
+    const int xprev = x == 0 ? nx - 1 : x - 1, xnext = x + 4 >= nx ? 0 : x + 4;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z + 1 == nz ? 0 : z + 1;
+    const size_t N = M.N, rowy[3] = {(size_t)yp * nx, (size_t)y * nx, (size_t)ym * nx};
+    const size_t slab[3] = {(size_t)zp * ny * nx, (size_t)z * ny * nx, (size_t)zm * ny * nx};
+    const float *src = static_cast<const float *>(M.pop[cur]);
+    float *dst = static_cast<float *>(M.pop[cur ^ 1]);
+    float v[Q][4];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      // pull from (y - c_y, z - c_z): entry 1 + c of the (+1, 0, -1) neighbours
+      const float *row = src + (size_t)l * N + slab[1 + c3z(l)] + rowy[1 + c3y(l)];
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (active) o = __ldg(reinterpret_cast<const float4 *>(row + x));
+      if (c3x(l) == 0) {
+        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
+      } else if (c3x(l) > 0) {  // from x - 1
+        float prev = __shfl_up_sync(0xffffffffu, o.w, 1);
+        if (active && (lane == 0 || x == 0)) prev = __ldg(row + xprev);
+        v[l][0] = prev; v[l][1] = o.x; v[l][2] = o.y; v[l][3] = o.z;
+      } else {  // from x + 1
+        float next = __shfl_down_sync(0xffffffffu, o.x, 1);
+        if (last) next = __ldg(row + xnext);
+        v[l][0] = o.y; v[l][1] = o.z; v[l][2] = o.w; v[l][3] = next;
+      }
+    }
+    if (!active) continue;
+    const float *tab = static_cast<const float *>(M.ftab);
+    const float fx = tab[y], fy = tab[ny + z];
+    const size_t c = slab[1] + rowy[1] + x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float g[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) g[l] = v[l][i];
+      collide3<float, Q>(g, M.rho0_f, M.omega_f, fx, fy, tab[ny + nz + x + i], M.alpha_f);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) v[l][i] = g[l];
+    }
+#pragma unroll
+    for (int l = 0; l < Q; ++l)
+      __stcs(reinterpret_cast<float4 *>(dst + (size_t)l * N + c),
+             make_float4(v[l][0], v[l][1], v[l][2], v[l][3]));
+  }
+}
+
+template <typename T, int Q>
 __global__ void k3_init(const M3 *__restrict__ ms, int member, int cur, const double *rho,
                         const double *ux, const double *uy, const double *uz) {
   const M3 &M = ms[member];
@@ -138,17 +219,17 @@ __global__ void k3_init(const M3 *__restrict__ ms, int member, int cur, const do
   const double r = rho[c], u = ux[c], v = uy[c], w = uz[c], uu = u * u + v * v + w * w;
   T *dst = static_cast<T *>(M.pop[cur]);
 #pragma unroll
-  for (int l = 0; l < kQ3; ++l) {
+  for (int l = 0; l < Q; ++l) {
     const double cu = c3x(l) * u + c3y(l) * v + c3z(l) * w;
-    const double feq = w3(l) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    const double feq = w3<Q>(l) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
     // the population at x is stored at its pull origin x - c_l
     const size_t o = cell(M, wrp(x - c3x(l), M.nx), wrp(y - c3y(l), M.ny), wrp(z - c3z(l), M.nz));
-    dst[(size_t)l * M.N + o] = (T)(sizeof(T) == 4 ? feq - w3(l) * M.rho0 : feq);
+    dst[(size_t)l * M.N + o] = (T)(sizeof(T) == 4 ? feq - w3<Q>(l) * M.rho0 : feq);
   }
 }
 
 // Public <-> storage (to_public: storage -> f[19][N] doubles).
-template <typename T>
+template <typename T, int Q>
 __global__ void k3_copy(const M3 *__restrict__ ms, int member, int cur, double *f, int to_public) {
   const M3 &M = ms[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y,
@@ -157,10 +238,10 @@ __global__ void k3_copy(const M3 *__restrict__ ms, int member, int cur, double *
   const size_t c = cell(M, x, y, z);
   T *st = static_cast<T *>(M.pop[cur]);
 #pragma unroll
-  for (int l = 0; l < kQ3; ++l) {
+  for (int l = 0; l < Q; ++l) {
     const size_t o = (size_t)l * M.N +
                      cell(M, wrp(x - c3x(l), M.nx), wrp(y - c3y(l), M.ny), wrp(z - c3z(l), M.nz));
-    const double off = sizeof(T) == 4 ? w3(l) * M.rho0 : 0.0;
+    const double off = sizeof(T) == 4 ? w3<Q>(l) * M.rho0 : 0.0;
     if (to_public)
       f[(size_t)l * M.N + c] = (double)st[o] + off;
     else
@@ -176,16 +257,16 @@ __device__ __forceinline__ void two_sum3(float a, float b, float &s, float &e) {
 
 // (rho, j) of the current state into snapshot slot `slot` (FP64; FP32
 // storage by compensated FP32 sums of the stored deviations).
-template <typename T>
+template <typename T, int Q>
 __global__ void k3_snapshot(const M3 *__restrict__ ms, int member, int cur, int slot) {
   const M3 &M = ms[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y,
             z = blockIdx.z;
   if (x >= M.nx || y >= M.ny) return;
   const T *st = static_cast<const T *>(M.pop[cur]);
-  T v[kQ3];
+  T v[Q];
 #pragma unroll
-  for (int l = 0; l < kQ3; ++l)
+  for (int l = 0; l < Q; ++l)
     v[l] = st[(size_t)l * M.N + cell(M, wrp(x - c3x(l), M.nx), wrp(y - c3y(l), M.ny),
                                      wrp(z - c3z(l), M.nz))];
   double out[4];
@@ -194,7 +275,7 @@ __global__ void k3_snapshot(const M3 *__restrict__ ms, int member, int cur, int 
     for (int q = 0; q < 4; ++q) {
       float s = 0.f, e = 0.f;
 #pragma unroll
-      for (int l = 0; l < kQ3; ++l) {
+      for (int l = 0; l < Q; ++l) {
         const int c = q == 0 ? 1 : (q == 1 ? c3x(l) : (q == 2 ? c3y(l) : c3z(l)));
         if (c == 0) continue;
         float d;
@@ -208,7 +289,7 @@ __global__ void k3_snapshot(const M3 *__restrict__ ms, int member, int cur, int 
 #pragma unroll
     for (int q = 0; q < 4; ++q) out[q] = 0.0;
 #pragma unroll
-    for (int l = 0; l < kQ3; ++l) {
+    for (int l = 0; l < Q; ++l) {
       out[0] += v[l];
       out[1] += c3x(l) * v[l];
       out[2] += c3y(l) * v[l];
@@ -596,6 +677,9 @@ struct lbm3d_handle {
   char *ws = nullptr;
   size_t ws_bytes = 0;
   int precision = 32;
+  int q = 19;  // lattice velocities
+  long long vec_items = 0;  // work items of the four-cell FP32 kernel
+  int vec_grid = 0;         // its persistent grid
   cudaStream_t stream = nullptr;
   int cur = 0;
   long long t = 0;
@@ -634,10 +718,25 @@ struct Layout3 {
   size_t diag, origins, total, diag_doubles, origin_cap;
 };
 
+int lattice_q(const lbm3d_config *cfg) { return cfg->lattice == 27 ? 27 : 19; }
+
+// Launches kernel template K<T, Q> for the handle's precision and lattice.
+#define DISPATCH3(h, K, grid, block, ...)                                                   \
+  do {                                                                                   \
+    if ((h)->precision == 32) {                                                          \
+      if ((h)->q == 27) K<float, 27><<<grid, block, 0, (h)->stream>>>(__VA_ARGS__);      \
+      else K<float, 19><<<grid, block, 0, (h)->stream>>>(__VA_ARGS__);                   \
+    } else {                                                                             \
+      if ((h)->q == 27) K<double, 27><<<grid, block, 0, (h)->stream>>>(__VA_ARGS__);     \
+      else K<double, 19><<<grid, block, 0, (h)->stream>>>(__VA_ARGS__);                  \
+    }                                                                                    \
+  } while (0)
+
 int check3(const lbm3d_config *cfg, std::string &err) {
   if (!cfg || cfg->n_members < 1 || !cfg->members) { err = "need n_members >= 1 and members"; return LBM_ERR_ARG; }
   if (cfg->precision != 32 && cfg->precision != 64) { err = "precision must be 32 or 64"; return LBM_ERR_ARG; }
   if (cfg->diag_every < 0) { err = "diag_every must be >= 0"; return LBM_ERR_ARG; }
+  if (cfg->lattice != 0 && cfg->lattice != 19 && cfg->lattice != 27) { err = "lattice must be 19 or 27 (0: 19)"; return LBM_ERR_ARG; }
   for (int m = 0; m < cfg->n_members; ++m) {
     const lbm3d_member_cfg &c = cfg->members[m];
     if (c.nx < 1 || c.ny < 1 || c.nz < 1 || (long long)c.nx * c.ny * c.nz > (1LL << 28)) { err = "grid out of range"; return LBM_ERR_ARG; }
@@ -654,13 +753,14 @@ Layout3 layout3(const lbm3d_config *cfg) {
   size_t off = 0;
   auto take = [&](size_t b) { size_t o = off; off = al(off + b); return o; };
   const size_t es = cfg->precision == 32 ? 4 : 8;
+  const size_t Q = lattice_q(cfg);
   L.members = take(sizeof(M3) * cfg->n_members);
   size_t Nmax = 0, Tmax = 0;
   for (int m = 0; m < cfg->n_members; ++m) {
     const lbm3d_member_cfg &c = cfg->members[m];
     const size_t N = (size_t)c.nx * c.ny * c.nz;
-    L.pop0.push_back(take(es * kQ3 * N));
-    L.pop1.push_back(take(es * kQ3 * N));
+    L.pop0.push_back(take(es * Q * N));
+    L.pop1.push_back(take(es * Q * N));
     L.snap.push_back(take(8 * 3 * 4 * N));
     L.ftab.push_back(take(es * (c.nx + c.ny + c.nz)));
     L.ftab64.push_back(take(8 * (c.nx + c.ny + c.nz)));
@@ -693,12 +793,8 @@ bool snap_time3(const lbm3d_handle *h, long long t) {
 
 int record3(lbm3d_handle *h) {
   const int slot = (int)(h->t % 3);
-  for (int m = 0; m < (int)h->mcfg.size(); ++m) {
-    if (h->precision == 32)
-      k3_snapshot<float><<<cells3(h->mcfg[m]), dim3(64, 4), 0, h->stream>>>(h->d_m, m, h->cur, slot);
-    else
-      k3_snapshot<double><<<cells3(h->mcfg[m]), dim3(64, 4), 0, h->stream>>>(h->d_m, m, h->cur, slot);
-  }
+  for (int m = 0; m < (int)h->mcfg.size(); ++m)
+    DISPATCH3(h, k3_snapshot, cells3(h->mcfg[m]), dim3(64, 4), h->d_m, m, h->cur, slot);
   CK3(cudaGetLastError());
   h->ring_time[slot] = h->t;
   return LBM_OK;
@@ -730,6 +826,7 @@ int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_h
   h->ws = static_cast<char *>(workspace);
   h->ws_bytes = bytes;
   h->precision = cfg->precision;
+  h->q = lattice_q(cfg);
   h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   h->d_m = reinterpret_cast<M3 *>(h->ws + L.members);
   h->diag = reinterpret_cast<double *>(h->ws + L.diag);
@@ -737,9 +834,11 @@ int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_h
   h->d_origins = reinterpret_cast<int *>(h->ws + L.origins);
   h->origin_cap = L.origin_cap;
   const size_t es = cfg->precision == 32 ? 4 : 8;
+  const size_t Q = h->q;
   for (int m = 0; m < cfg->n_members; ++m) {
     const lbm3d_member_cfg &c = h->mcfg[m];
     M3 M{};
+    M.q = h->q;
     M.nx = c.nx;
     M.ny = c.ny;
     M.nz = c.nz;
@@ -756,6 +855,10 @@ int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_h
     M.alpha_f = (float)c.alpha;
     M.F0_f = (float)c.F0;
     M.N = (size_t)c.nx * c.ny * c.nz;
+    M.item0 = h->vec_items;
+    M.items = cfg->precision == 32 && c.nx % 4 == 0
+                  ? (long long)((c.nx + 127) / 128) * ((c.ny + 3) / 4) * c.nz : 0;
+    h->vec_items += M.items;
     M.pop[0] = h->ws + L.pop0[m];
     M.pop[1] = h->ws + L.pop1[m];
     M.snap = reinterpret_cast<double *>(h->ws + L.snap[m]);
@@ -772,8 +875,8 @@ int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_h
         ft[c.ny + c.nz + x] = c.F0 * std::sin(2.0 * pi * c.kf * (double)x / c.nx);
     }
     std::vector<float> ftf(ft.begin(), ft.end());
-    cudaError_t e = cudaMemsetAsync(M.pop[0], 0, es * kQ3 * M.N, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(M.pop[1], 0, es * kQ3 * M.N, h->stream);
+    cudaError_t e = cudaMemsetAsync(M.pop[0], 0, es * Q * M.N, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M.pop[1], 0, es * Q * M.N, h->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(M.ftab64, ft.data(), 8 * ft.size(), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
@@ -784,6 +887,20 @@ int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_h
       delete h;
       return fail3(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
     }
+  }
+  if (h->vec_items > 0) {  // persistent grid: resident CTAs per SM x SMs
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = h->q == 27 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_step_vec<27>, 128, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_step_vec<19>, 128, 0);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail3(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+    }
+    const long long g = (long long)std::max(1, sms) * std::max(1, per_sm);
+    h->vec_grid = (int)std::min<long long>(g, h->vec_items);
   }
   cudaError_t e = cudaMemcpyAsync(h->d_m, h->hm.data(), sizeof(M3) * h->hm.size(),
                                   cudaMemcpyHostToDevice, h->stream);
@@ -818,12 +935,8 @@ int lbm3d_init_fields(lbm3d_handle *h, int member, const double *rho, const doub
   } else {
     for (int q = 0; q < 4; ++q) dev[q] = const_cast<double *>(src[q]);
   }
-  if (h->precision == 32)
-    k3_init<float><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur,
-                                                                          dev[0], dev[1], dev[2], dev[3]);
-  else
-    k3_init<double><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur,
-                                                                           dev[0], dev[1], dev[2], dev[3]);
+  DISPATCH3(h, k3_init, cells3(h->mcfg[member]), dim3(64, 4), h->d_m, member, h->cur, dev[0],
+            dev[1], dev[2], dev[3]);
   CK3(cudaGetLastError());
   if (!on_device) CK3(cudaStreamSynchronize(h->stream));
   for (long long &r : h->ring_time) r = -1;
@@ -836,12 +949,16 @@ int lbm3d_step(lbm3d_handle *h, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
     if (snap_time3(h, h->t) && h->ring_time[h->t % 3] != h->t)
       if (int rc = record3(h)) return rc;
-    for (int m = 0; m < (int)h->mcfg.size(); ++m) {
-      if (h->precision == 32)
-        k3_step<float><<<cells3(h->mcfg[m]), dim3(64, 4), 0, h->stream>>>(h->d_m, m, h->cur);
+    if (h->vec_items > 0) {  // every FP32 member with nx % 4 == 0, one launch
+      const int n = (int)h->mcfg.size();
+      if (h->q == 27)
+        k3_step_vec<27><<<h->vec_grid, dim3(32, 4), 0, h->stream>>>(h->d_m, n, h->vec_items, h->cur);
       else
-        k3_step<double><<<cells3(h->mcfg[m]), dim3(64, 4), 0, h->stream>>>(h->d_m, m, h->cur);
+        k3_step_vec<19><<<h->vec_grid, dim3(32, 4), 0, h->stream>>>(h->d_m, n, h->vec_items, h->cur);
     }
+    for (int m = 0; m < (int)h->mcfg.size(); ++m)
+      if (h->hm[m].items == 0)
+        DISPATCH3(h, k3_step, cells3(h->mcfg[m]), dim3(64, 4), h->d_m, m, h->cur);
     CK3(cudaGetLastError());
     h->cur ^= 1;
     h->t += 1;
@@ -857,13 +974,10 @@ int lbm3d_get_populations(lbm3d_handle *h, int member, double *f, int on_device)
   if (!f) return fail3(h, LBM_ERR_ARG, "f is NULL");
   const M3 &M = h->hm[member];
   double *dst = on_device ? f : h->diag;
-  if (h->precision == 32)
-    k3_copy<float><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur, dst, 1);
-  else
-    k3_copy<double><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur, dst, 1);
+  DISPATCH3(h, k3_copy, cells3(h->mcfg[member]), dim3(64, 4), h->d_m, member, h->cur, dst, 1);
   CK3(cudaGetLastError());
   if (!on_device) {
-    CK3(cudaMemcpyAsync(f, dst, 8 * kQ3 * M.N, cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaMemcpyAsync(f, dst, 8 * (size_t)h->q * M.N, cudaMemcpyDeviceToHost, h->stream));
     CK3(cudaStreamSynchronize(h->stream));
   }
   return LBM_OK;
@@ -876,12 +990,9 @@ int lbm3d_set_populations(lbm3d_handle *h, int member, const double *f, int on_d
   double *src = const_cast<double *>(f);
   if (!on_device) {
     src = h->diag;
-    CK3(cudaMemcpyAsync(src, f, 8 * kQ3 * M.N, cudaMemcpyHostToDevice, h->stream));
+    CK3(cudaMemcpyAsync(src, f, 8 * (size_t)h->q * M.N, cudaMemcpyHostToDevice, h->stream));
   }
-  if (h->precision == 32)
-    k3_copy<float><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur, src, 0);
-  else
-    k3_copy<double><<<cells3(h->mcfg[member]), dim3(64, 4), 0, h->stream>>>(h->d_m, member, h->cur, src, 0);
+  DISPATCH3(h, k3_copy, cells3(h->mcfg[member]), dim3(64, 4), h->d_m, member, h->cur, src, 0);
   CK3(cudaGetLastError());
   if (!on_device) CK3(cudaStreamSynchronize(h->stream));
   for (long long &r : h->ring_time) r = -1;

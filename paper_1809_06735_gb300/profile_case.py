@@ -78,18 +78,20 @@ def case_collisions(members=16, n=512, steps=12):
 
 
 def case_3d(members=2, n=128, steps=12):
-    """The D3Q19 stream-collide on 2 FP32 members of 128^3, then one FP64
-    balance event on a 48^3 member."""
+    """The D3Q19 and D3Q27 stream-collide on 2 FP32 members of 128^3 each,
+    then one FP64 balance event on a 48^3 member."""
     from . import Lattice3D, Member3
     x = 2 * np.pi * np.arange(n) / n
     Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
     ux, uy = 0.02 * np.sin(X) * np.cos(Y) * np.cos(Z), -0.02 * np.cos(X) * np.sin(Y) * np.cos(Z)
     uz, rho = 0.005 * np.sin(X - Y), np.ones((n, n, n))
-    lat = Lattice3D([Member3(n, n, n, 0.52)] * members, precision=32)
-    for m in range(members):
-        lat.init_fields(m, rho, ux, uy, uz)
-    lat.step(steps)
-    torch.cuda.synchronize()
+    for q in (19, 27):
+        lat = Lattice3D([Member3(n, n, n, 0.52)] * members, precision=32, lattice=q)
+        for m in range(members):
+            lat.init_fields(m, rho, ux, uy, uz)
+        lat.step(steps)
+        torch.cuda.synchronize()
+        del lat
     nd = 48
     dl = Lattice3D([Member3(nd, nd, nd, 0.52)], precision=64, diag_every=6)
     dl.init_fields(0, *(a[:nd, :nd, :nd] for a in (rho, ux, uy, uz)))

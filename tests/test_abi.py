@@ -82,12 +82,17 @@ def test_3d_config_checks(P):
     lib = P.load_library()
     n = ctypes.c_size_t()
 
-    def size(members, precision=32):
+    def size(members, precision=32, lattice=0):
         arr = (P._MemberCfg3 * len(members))(*[m.c() for m in members])
-        cfg = P._Config3(len(members), arr, precision, 0, None)
+        cfg = P._Config3(len(members), arr, precision, 0, None, lattice)
         return lib.lbm3d_workspace_size(ctypes.byref(cfg), ctypes.byref(n))
 
     assert size([P.Member3(16, 12, 8, 0.6)]) == 0 and n.value > 19 * 4 * 2 * 16 * 12 * 8
+    q19 = n.value
+    assert size([P.Member3(16, 12, 8, 0.6)], lattice=19) == 0 and n.value == q19
+    assert size([P.Member3(16, 12, 8, 0.6)], lattice=27) == 0
+    assert n.value - q19 >= 8 * 4 * 2 * 16 * 12 * 8  # two buffers of 8 more populations
+    assert size([P.Member3(16, 12, 8, 0.6)], lattice=15) == -1
     assert size([P.Member3(16, 12, 8, 0.5)]) == -1
     assert size([P.Member3(0, 12, 8, 0.6)]) == -1
     assert size([P.Member3(8, 8, 8, 0.6, force_kind=2)]) == -1

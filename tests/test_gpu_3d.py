@@ -1,4 +1,4 @@
-"""GPU parity of the three-dimensional extension (D3Q19 BGK with EDM forcing;
+"""GPU parity of the three-dimensional extension (D3Q19 and D3Q27 BGK with EDM forcing;
 the general-index balance terms with vortex stretching over L^3 boxes)
 against the FP64 oracle, through the C ABI of include/lbm3d.h: trajectories
 (FP64 within 1e-12, FP32 within 2e-6 on every population), state round
@@ -45,15 +45,16 @@ SPEC = [(12, 10, 8, 0.57, 1, 1, 3e-4, 2e-3), (16, 16, 16, 0.52, 0, 0, 0.0, 0.0),
         (5, 7, 3, 0.8, 1, 1, 1e-4, 0.0)]
 
 
+@pytest.mark.parametrize("q", [19, 27])
 @pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 2e-6)])
-def test_3d_trajectories(P, orc, prec, tol):
+def test_3d_trajectories(P, orc, prec, tol, q):
     lat = P.Lattice3D([P.Member3(nx, ny, nz, tau, 1.0, k, kf, F0, a)
-                       for (nx, ny, nz, tau, k, kf, F0, a) in SPEC], precision=prec)
+                       for (nx, ny, nz, tau, k, kf, F0, a) in SPEC], precision=prec, lattice=q)
     init = []
     for i, (nx, ny, nz, *_r) in enumerate(SPEC):
         fl = _fields((nz, ny, nx), 10 * i)
         lat.init_fields(i, *fl)
-        init.append(orc.init3(*fl))
+        init.append(orc.init3(*fl, q=q))
     done = 0
     for steps in (1, 5, 24):
         lat.step(steps - done)
@@ -64,24 +65,26 @@ def test_3d_trajectories(P, orc, prec, tol):
             assert err < tol, (prec, steps, i, err)
 
 
-def test_3d_state_roundtrip(P, orc):
+@pytest.mark.parametrize("q", [19, 27])
+def test_3d_state_roundtrip(P, orc, q):
     shape = (6, 5, 7)
-    f = orc.init3(*_fields(shape, 3)) * (1 + 0.01 * np.random.default_rng(1).normal(size=(19,) + shape))
-    lat = P.Lattice3D([P.Member3(7, 5, 6, 0.6)], precision=64)
+    f = orc.init3(*_fields(shape, 3), q=q) * (
+        1 + 0.01 * np.random.default_rng(1).normal(size=(q,) + shape))
+    lat = P.Lattice3D([P.Member3(7, 5, 6, 0.6)], precision=64, lattice=q)
     lat.set_populations(0, f)
     assert np.array_equal(lat.get_populations_host(0), f)
     lat.step(3)
     assert rel_err(lat.get_populations_host(0), orc.run3(f, 3, 0.6)) < 1e-12
 
 
-@pytest.mark.parametrize("prec", [64, 32])
-def test_3d_balance_terms(P, orc, prec):
+@pytest.mark.parametrize("prec,q", [(64, 19), (32, 19), (64, 27), (32, 27)])
+def test_3d_balance_terms(P, orc, prec, q):
     """All origins and origin lists at several L (one beyond the grid: NaN);
     per-box terms within 1e-10 of each field's magnitude of the oracle's on
     the same exported states; vortex stretching is present."""
     nx, ny, nz, tau, F0, kf, a = 12, 10, 8, 0.57, 3e-4, 1, 2e-3
     lat = P.Lattice3D([P.Member3(nx, ny, nz, tau, 1.0, 1, kf, F0, a)], precision=prec,
-                      diag_every=10)
+                      diag_every=10, lattice=q)
     lat.init_fields(0, *_fields((nz, ny, nx), 40))
     lat.step(8)
     f8 = lat.get_populations_host(0)
