@@ -246,6 +246,7 @@ struct lbm_handle {
   cudaEvent_t ev_ready = nullptr, ev_diag_done = nullptr;
   bool diag_pending = false;
   bool has_kind2 = false;  // some member uses the paper's forcing (kind 2)
+  bool proj_quad = true;   // every kind-2 member allows the four-cell projection
   bool has_vv = false;     // some member has a variable-viscosity collision
   int cur = 0;
   long long t = 0;
@@ -313,7 +314,7 @@ int project(lbm_handle *h, cudaStream_t s, int cur, int slot) {
   int nx, ny;
   max_grid(h, &nx, &ny);
   CK(lbm::launch_projection(h->precision, h->d_members, (int)h->mcfg.size(), nx, ny, cur, slot,
-                            s));
+                            h->proj_quad, s));
   return LBM_OK;
 }
 
@@ -589,6 +590,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
                                        : nullptr;
       M.proj_count = reinterpret_cast<unsigned *>(ws_at(h, lay.pcount[m]));
       h->has_kind2 = true;
+      if (h->precision != 32 || c.nx % 4 != 0) h->proj_quad = false;
     }
     h->hm.push_back(M);
     // Kolmogorov tables: F_ext,x(y) = F0 sin(2 pi kf y / ny), F_ext,y(x) likewise.

@@ -163,7 +163,8 @@ cudaError_t launch_set_populations(int precision, const Member *d_members, int m
 // (the step about to run), slot 0..2 into that ring slot of damp_ring.
 // One launch; members of other kinds are skipped.
 cudaError_t launch_projection(int precision, const Member *d_members, int n_members,
-                              int nx_max, int ny_max, int state, int slot, cudaStream_t s);
+                              int nx_max, int ny_max, int state, int slot, bool quad,
+                              cudaStream_t s);
 // The ring snapshot of every member in one launch (layout at Member::snap).
 cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_members,
                                  int nx_max, int ny_max, int state, int slot, cudaStream_t s);

@@ -872,6 +872,60 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
   }
 }
 
+// The member's last projection CTA to finish (a counter in
+// Member::proj_count; the caller wrote its partials and fenced) reduces the
+// nblk CTA partials in a fixed order into the damping coefficients and, for
+// the running step of FP32 storage, the per-row factors.  Every thread of
+// the CTA calls it (256 threads: tid, lane, wid of the CTA).
+__device__ void project_finalize(const Member &M, int nblk, int slot, int tid, int lane, int wid) {
+  const int nx = M.nx, ny = M.ny;
+  __shared__ int is_last;
+  __syncthreads();
+  if (tid == 0) is_last = atomicAdd(M.proj_count, 1u) == (unsigned)(nblk - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // last CTA: one warp per value, two fixed-order chains and a shuffle tree
+  __shared__ double coef[kDamp];
+  for (int q = wid; q < kDamp; q += 8) {
+    double a0 = 0.0, a1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nblk; b += 64) {
+      a0 += __ldcg(M.proj_part + (size_t)b * kDamp + q);
+      a1 += __ldcg(M.proj_part + (size_t)(b + 32) * kDamp + q);
+    }
+    if (b < nblk) a0 += __ldcg(M.proj_part + (size_t)b * kDamp + q);
+    double a = a0 + a1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) {
+      const double c = -2.0 * M.FR0 * a / ((double)nx * (double)ny);
+      coef[q] = c;
+      if (slot < 0) {
+        M.damp[q] = c;
+        M.damp_f[q] = (float)c;
+      } else {
+        M.damp_ring[slot * kDamp + q] = c;
+      }
+    }
+  }
+  if (tid == 0) *M.proj_count = 0u;  // ready for the next launch
+  if (slot >= 0 || M.damp_rows == nullptr) return;
+  __syncthreads();
+  const double *tyd = M.trig64 + 4 * (size_t)nx;
+  for (int y = tid; y < ny; y += 256) {
+    const double cy = tyd[y], sy = tyd[ny + y], c2y = tyd[2 * ny + y], s2y = tyd[3 * ny + y];
+    float *row = M.damp_rows + 6 * (size_t)y;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double *d = coef + 12 * k;
+      row[3 * k] = (float)(d[0] + (d[4] + d[6]) * cy + (d[5] - d[7]) * sy);
+      row[3 * k + 1] = (float)(d[1] + (d[5] + d[7]) * cy - (d[4] - d[6]) * sy);
+      row[3 * k + 2] = (float)(d[2] * cy + d[3] * sy + d[10] * c2y + d[11] * s2y);
+    }
+  }
+}
+
 // Projection for the damping of eq. (16): each CTA (64 x 64 cells of member
 // blockIdx.z; every thread 16 rows, 4 apart) sums u_c cos(theta_m) and
 // u_c sin(theta_m) over its cells, u = j / rho the bare velocity of the
@@ -951,51 +1005,120 @@ __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ memb
     M.proj_part[(size_t)blk * kDamp + tid] = (double)a;
     __threadfence();
   }
-  __shared__ int is_last;
-  __syncthreads();
-  if (tid == 0) is_last = atomicAdd(M.proj_count, 1u) == (unsigned)(nblk - 1);
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  // last CTA: one warp per value, two fixed-order chains and a shuffle tree
-  __shared__ double coef[kDamp];
-  for (int q = wid; q < kDamp; q += 8) {
-    double a0 = 0.0, a1 = 0.0;
-    int b = lane;
-    for (; b + 32 < nblk; b += 64) {
-      a0 += __ldcg(M.proj_part + (size_t)b * kDamp + q);
-      a1 += __ldcg(M.proj_part + (size_t)(b + 32) * kDamp + q);
-    }
-    if (b < nblk) a0 += __ldcg(M.proj_part + (size_t)b * kDamp + q);
-    double a = a0 + a1;
+  project_finalize(M, nblk, slot, tid, lane, wid);
+}
+
+// FP32 projection with 4 consecutive cells per lane (every kind-2 member
+// with nx % 4 == 0): CTA (32, 8), a warp per 128-cell row segment, each
+// thread kProj4Rows rows 8 apart, so a CTA covers 128 x 8 kProj4Rows cells.
+// The populations of the state are pulled as in k_step_f32_vec (MODE 0:
+// double buffer `state`, 1: AA even, 2: AA odd): one float4 per population
+// and lane, the x-shift by shuffles.  Same sums per cell as k_project.
+constexpr int kProj4Rows = 8;
+template <int MODE>
+__global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ members, int state,
+                                                  int slot) {
+  const Member &M = members[blockIdx.z];
+  if (M.force_kind != 2) return;
+  if ((int)(blockIdx.x * 128) >= M.nx || (int)(blockIdx.y * 8 * kProj4Rows) >= M.ny) return;
+  const int nx = M.nx, ny = M.ny, pitch = M.pitch, lane = threadIdx.x;
+  const size_t plane = M.plane;
+  const int x = blockIdx.x * 128 + 4 * lane;
+  const bool active = x < nx;
+  const bool last = active && (lane == 31 || x + 4 >= nx);
+  const int xprev = x == 0 ? nx - 1 : x - 1, xnext = x + 4 >= nx ? 0 : x + 4;
+  const float *src = static_cast<const float *>(MODE == 0 ? M.pop[state] : M.pop[0]);
+  const float *tr = static_cast<const float *>(M.trig);
+  float cx[4] = {0, 0, 0, 0}, sx[4] = {0, 0, 0, 0}, c2x[4] = {0, 0, 0, 0}, s2x[4] = {0, 0, 0, 0};
+  if (active) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    if (lane == 0) {
-      const double c = -2.0 * M.FR0 * a / ((double)nx * (double)ny);
-      coef[q] = c;
-      if (slot < 0) {
-        M.damp[q] = c;
-        M.damp_f[q] = (float)c;
-      } else {
-        M.damp_ring[slot * kDamp + q] = c;
+    for (int i = 0; i < 4; ++i) {
+      cx[i] = tr[x + i];
+      sx[i] = tr[nx + x + i];
+      c2x[i] = tr[2 * nx + x + i];
+      s2x[i] = tr[3 * nx + x + i];
+    }
+  }
+  float acc[kDamp];
+#pragma unroll
+  for (int q = 0; q < kDamp; ++q) acc[q] = 0.f;
+#pragma unroll 1
+  for (int r = 0; r < kProj4Rows; ++r) {
+    const int y = blockIdx.y * 8 * kProj4Rows + r * 8 + threadIdx.y;
+    if (y >= ny) break;  // whole warps
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
+    float v[kQ][4];
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const int cxl = cx_of(l), cyl = cy_of(l);
+      if (MODE == 1) {  // own cell, own slot
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (active)
+          o = __ldg(reinterpret_cast<const float4 *>(src + (size_t)l * plane + (size_t)y * pitch + x));
+        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
+        continue;
+      }
+      const int sl = MODE == 2 ? opposite(l) : l;
+      const int ys = cyl == 0 ? y : (cyl > 0 ? ym : yp);  // from y - c_y
+      const float *row = src + (size_t)sl * plane + (size_t)ys * pitch;
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (active) o = __ldg(reinterpret_cast<const float4 *>(row + x));
+      if (cxl == 0) {
+        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
+      } else if (cxl > 0) {  // from x - 1
+        float prev = __shfl_up_sync(0xffffffffu, o.w, 1);
+        if (active && (lane == 0 || x == 0)) prev = __ldg(row + xprev);
+        v[l][0] = prev; v[l][1] = o.x; v[l][2] = o.y; v[l][3] = o.z;
+      } else {  // from x + 1
+        float next = __shfl_down_sync(0xffffffffu, o.x, 1);
+        if (last) next = __ldg(row + xnext);
+        v[l][0] = o.y; v[l][1] = o.z; v[l][2] = o.w; v[l][3] = next;
       }
     }
-  }
-  if (tid == 0) *M.proj_count = 0u;  // ready for the next launch
-  if (slot >= 0 || M.damp_rows == nullptr) return;
-  __syncthreads();
-  const double *tyd = M.trig64 + 4 * (size_t)nx;
-  for (int y = tid; y < ny; y += 256) {
-    const double cy = tyd[y], sy = tyd[ny + y], c2y = tyd[2 * ny + y], s2y = tyd[3 * ny + y];
-    float *row = M.damp_rows + 6 * (size_t)y;
+    if (!active) continue;
+    const float cy = tr[4 * nx + y], sy = tr[4 * nx + ny + y];
+    const float c2y = tr[4 * nx + 2 * ny + y], s2y = tr[4 * nx + 3 * ny + y];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const double *d = coef + 12 * k;
-      row[3 * k] = (float)(d[0] + (d[4] + d[6]) * cy + (d[5] - d[7]) * sy);
-      row[3 * k + 1] = (float)(d[1] + (d[5] + d[7]) * cy - (d[4] - d[6]) * sy);
-      row[3 * k + 2] = (float)(d[2] * cy + d[3] * sy + d[10] * c2y + d[11] * s2y);
+    for (int i = 0; i < 4; ++i) {
+      float rho = M.rho0_f, jx = 0.f, jy = 0.f;
+#pragma unroll
+      for (int l = 0; l < kQ; ++l) {
+        rho += v[l][i];
+        jx += (float)cx_of(l) * v[l][i];
+        jy += (float)cy_of(l) * v[l][i];
+      }
+      const float ir = 1.0f / rho;
+      const float u[2] = {jx * ir, jy * ir};
+      const float cm[6] = {cx[i], cy, cx[i] * cy - sx[i] * sy, cx[i] * cy + sx[i] * sy, c2x[i], c2y};
+      const float sm[6] = {sx[i], sy, sx[i] * cy + cx[i] * sy, sx[i] * cy - cx[i] * sy, s2x[i], s2y};
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          acc[12 * k + 2 * m] += u[k] * cm[m];
+          acc[12 * k + 2 * m + 1] += u[k] * sm[m];
+        }
     }
   }
+  __shared__ float sh[kDamp][8];
+  const int tid = threadIdx.y * 32 + threadIdx.x, wid = threadIdx.y;
+#pragma unroll
+  for (int q = 0; q < kDamp; ++q) {
+    float a = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[q][wid] = a;
+  }
+  __syncthreads();
+  const int gx = (nx + 127) / 128;
+  const int nblk = gx * ((ny + 8 * kProj4Rows - 1) / (8 * kProj4Rows));
+  if (tid < kDamp) {
+    float a = sh[tid][0];
+    for (int w = 1; w < 8; ++w) a += sh[tid][w];
+    M.proj_part[(size_t)(blockIdx.y * gx + blockIdx.x) * kDamp + tid] = (double)a;
+    __threadfence();
+  }
+  project_finalize(M, nblk, slot, tid, lane, wid);
 }
 
 template <typename T>
@@ -1065,7 +1188,19 @@ cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_m
 }
 
 cudaError_t launch_projection(int precision, const Member *d_members, int n_members,
-                              int nx_max, int ny_max, int state, int slot, cudaStream_t s) {
+                              int nx_max, int ny_max, int state, int slot, bool quad,
+                              cudaStream_t s) {
+  if (quad && precision == 32) {  // four cells per lane
+    dim3 g((nx_max + 127) / 128, (ny_max + 8 * kProj4Rows - 1) / (8 * kProj4Rows), n_members);
+    const dim3 b4(32, 8);
+    if (state < 2)
+      k_project4<0><<<g, b4, 0, s>>>(d_members, state, slot);
+    else if (state == 2)
+      k_project4<1><<<g, b4, 0, s>>>(d_members, state, slot);
+    else
+      k_project4<2><<<g, b4, 0, s>>>(d_members, state, slot);
+    return cudaGetLastError();
+  }
   const dim3 b(64, 4);
   dim3 g = grid2d(nx_max, ny_max, dim3(64, 4 * kProjRows));
   g.z = n_members;
