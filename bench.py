@@ -376,17 +376,17 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     lat = P.Lattice([P.Member(n, n, tau)] * M, precision=32, diag_every=PERIOD,
                     graph_steps=PURE_STEPS - 1, stream=stream, device=dev)
-    # pinned host initial fields (also the e2e inputs)
-    host = torch.empty((M, 3, n, n), dtype=torch.float64, pin_memory=True)
+    # pinned host initial fields [rho, ux, uy][member][y][x] (also the e2e inputs)
+    host = torch.empty((3, M, n, n), dtype=torch.float64, pin_memory=True)
     for m in range(M):
         r, u, v = li.random_phase(n, seed=member_seed(wl["seed0"], rank, M, m), u_rms=wl["u_rms"])
-        host[m, 0].copy_(torch.from_numpy(r))
-        host[m, 1].copy_(torch.from_numpy(u))
-        host[m, 2].copy_(torch.from_numpy(v))
+        host[0, m].copy_(torch.from_numpy(r))
+        host[1, m].copy_(torch.from_numpy(u))
+        host[2, m].copy_(torch.from_numpy(v))
     hnp = host.numpy()
     dev_fields = host.to(dev)
     for m in range(M):
-        lat.init_fields(m, dev_fields[m, 0], dev_fields[m, 1], dev_fields[m, 2])
+        lat.init_fields(m, dev_fields[0, m], dev_fields[1, m], dev_fields[2, m])
     torch.cuda.synchronize()
     Ls = wl["Ls"]
     all_members = list(range(M))
@@ -460,7 +460,7 @@ def run_ours(args):
     # plain single-instance FP64 step on one 512^2 member
     lat64 = P.Lattice([P.Member(n, n, tau)], precision=64, graph_steps=20, stream=stream,
                       device=dev)
-    lat64.init_fields(0, dev_fields[0, 0], dev_fields[0, 1], dev_fields[0, 2])
+    lat64.init_fields(0, dev_fields[0, 0], dev_fields[1, 0], dev_fields[2, 0])
     lat64.step(40)
     a, b = ev(), ev()
     torch.cuda.synchronize()
@@ -479,13 +479,17 @@ def run_ours(args):
     # initial fields of all members from pinned host memory, runs the period
     # and reads the statistics back.
     e2e_steps = max(1, min(args.steps, 3))
+
+    def e2e_step():
+        lat.init_fields_batch(all_members, hnp[0], hnp[1], hnp[2])
+        lat.step(PERIOD)
+        return lat.subvolume_balance_batch(all_members, Ls, origins=boxes)
+
+    e2e_step()  # warm-up: the step graph of the storage parity after a restart
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(e2e_steps):
-        for m in range(M):
-            lat.init_fields(m, hnp[m, 0], hnp[m, 1], hnp[m, 2])
-        lat.step(PERIOD)
-        lat.subvolume_balance_batch(all_members, Ls, origins=boxes)
+        e2e_step()
     torch.cuda.synchronize()
     te = time.perf_counter() - te
     e2e = {"value": ws * lu_per_gpu_step * e2e_steps / te / 1e9, "unit": "GLUPS",

@@ -161,6 +161,17 @@ int lbm_destroy(lbm_handle *h);
 int lbm_init_fields(lbm_handle *h, int member, const double *rho,
                     const double *ux, const double *uy, int on_device);
 
+/* lbm_init_fields for n members at once (the indices in `members`, host
+ * array, each listed once, all with the same grid), each from its own
+ * fields: rho, ux, uy are double[n][ny][nx] (member members[i] takes block
+ * i).  Host pointers (on_device == 0) are copied through the workspace's
+ * diagnostic scratch in chunks of whole members, one copy per field and
+ * chunk, with a single synchronisation at the end; device pointers are read
+ * in place.  With AA storage at an odd step every member must be listed.
+ * Resets the step counter and snapshot history like lbm_init_fields. */
+int lbm_init_fields_batch(lbm_handle *h, const int *members, int n, const double *rho,
+                          const double *ux, const double *uy, int on_device);
+
 /* Advances every member by nsteps time steps of eq. (1): per cell, pull the
  * populations from the neighbours x - c_l, take rho and j, form F, collide
  * with the BGK operator and the EDM term, store.  When diag_every > 0 the

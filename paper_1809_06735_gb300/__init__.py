@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_create": ([ctypes.POINTER(_Config), P, S, ctypes.POINTER(P)], I),
         "lbm_destroy": ([P], I),
         "lbm_init_fields": ([P, I, P, P, P, I], I),
+        "lbm_init_fields_batch": ([P, P, I, P, P, P, I], I),
         "lbm_step": ([P, I], I),
         "lbm_time": ([P], ctypes.c_longlong),
         "lbm_launch_count": ([P], ctypes.c_longlong),
@@ -234,6 +235,23 @@ class Lattice:
             r, u, v = (self._dev(a) for a in (rho, ux, uy))
             self._check(self.lib.lbm_init_fields(self.h, member, _ptr(r), _ptr(u), _ptr(v), 1))
             self._keep = (r, u, v)
+
+    def init_fields_batch(self, members, rho, ux, uy):
+        """init_fields for several members (equal grids) from stacked fields
+        [n, ny, nx]: numpy arrays go through one host copy per field and a
+        single synchronisation, tensors are read on the device."""
+        mem = np.ascontiguousarray(members, dtype=np.int32)
+        if isinstance(rho, np.ndarray):
+            r, u, v = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
+            on_dev = 0
+        else:
+            r, u, v = (self._dev(a) for a in (rho, ux, uy))
+            on_dev = 1
+            self._keep = (r, u, v)
+        for a in (r, u, v):
+            assert a.shape[0] == len(mem), "one field block per listed member"
+        self._check(self.lib.lbm_init_fields_batch(self.h, _ptr(mem), len(mem), _ptr(r), _ptr(u),
+                                                   _ptr(v), on_dev))
 
     def step(self, nsteps: int = 1):
         self._check(self.lib.lbm_step(self.h, int(nsteps)))

@@ -692,8 +692,54 @@ int lbm_init_fields(lbm_handle *h, int member, const double *rho, const double *
     h->cur = 2;
   }
   for (int m = m0; m < m1; ++m)
-    CK(lbm::launch_init_fields(h->precision, h->d_members, m, nx, ny, r, u, v, h->cur, h->stream));
+    CK(lbm::launch_init_fields(h->precision, h->d_members, &m, 1, nx, ny, r, u, v, h->cur,
+                               h->stream));
   h->launches += m1 - m0;
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));
+  h->t = 0;
+  h->ring_time[0] = h->ring_time[1] = h->ring_time[2] = -1;
+  return LBM_OK;
+}
+
+int lbm_init_fields_batch(lbm_handle *h, const int *members, int n, const double *rho,
+                          const double *ux, const double *uy, int on_device) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (!members || n < 1 || n > (int)h->mcfg.size())
+    return fail(h, LBM_ERR_ARG, "need 1..n_members member indices");
+  if (!rho || !ux || !uy) return fail(h, LBM_ERR_ARG, "rho/ux/uy must not be NULL");
+  std::vector<char> seen(h->mcfg.size(), 0);
+  for (int i = 0; i < n; ++i) {
+    const int m = members[i];
+    if (m < 0 || m >= (int)h->mcfg.size()) return fail(h, LBM_ERR_ARG, "member index out of range");
+    if (seen[m]) return fail(h, LBM_ERR_ARG, "member listed twice");
+    seen[m] = 1;
+    if (h->mcfg[m].nx != h->mcfg[members[0]].nx || h->mcfg[m].ny != h->mcfg[members[0]].ny)
+      return fail(h, LBM_ERR_ARG, "batched init fields need equal grids");
+  }
+  if (h->cur == 3 && n != (int)h->mcfg.size())
+    return fail(h, LBM_ERR_ARG, "AA storage: initialise every member (or at an even step)");
+  const int nx = h->mcfg[members[0]].nx, ny = h->mcfg[members[0]].ny;
+  const size_t N = (size_t)nx * ny;
+  if (int rc = wait_diag(h)) return rc;
+  if (h->cur >= 2) h->cur = 2;  // AA storage restarts at its even phase
+  // host fields go through the diagnostic scratch (every slot) in chunks of
+  // whole members: one copy per field and chunk, one synchronisation at the end
+  const size_t cap = on_device ? (size_t)n : (size_t)h->sc.slots * h->sc.slot_doubles / (3 * N);
+  if (cap < 1) return fail(h, LBM_ERR_WORKSPACE, "staging scratch smaller than one member");
+  for (int i0 = 0; i0 < n; i0 += (int)std::min<size_t>(cap, (size_t)(n - i0))) {
+    const int k = (int)std::min<size_t>(cap, (size_t)(n - i0));
+    const double *r = rho + (size_t)i0 * N, *u = ux + (size_t)i0 * N, *v = uy + (size_t)i0 * N;
+    if (!on_device) {
+      double *st = h->sc.f;
+      CK(cudaMemcpyAsync(st, r, 8 * N * k, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(st + N * k, u, 8 * N * k, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(st + 2 * N * k, v, 8 * N * k, cudaMemcpyHostToDevice, h->stream));
+      r = st; u = st + N * k; v = st + 2 * N * k;
+    }
+    CK(lbm::launch_init_fields(h->precision, h->d_members, members + i0, k, nx, ny, r, u, v,
+                               h->cur, h->stream));
+    h->launches += (k + lbm::InitList::kMax - 1) / lbm::InitList::kMax;
+  }
   if (!on_device) CK(cudaStreamSynchronize(h->stream));
   h->t = 0;
   h->ring_time[0] = h->ring_time[1] = h->ring_time[2] = -1;

@@ -150,9 +150,17 @@ cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tile
                                      int state, const LaunchCfg &lc, int slot, cudaStream_t s);
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member,
                                int nx, int ny, int cur, cudaStream_t s);
-cudaError_t launch_init_fields(int precision, const Member *d_members, int member, int nx,
-                               int ny, const double *rho, const double *ux,
-                               const double *uy, int cur, cudaStream_t s);
+// Member indices of one batched launch (kernel parameter).
+struct InitList {
+  static constexpr int kMax = 256;
+  int n;
+  int m[kMax];
+};
+// Equilibrium initialisation of the n members members[0..n) (host array,
+// equal grids nx x ny), member members[i] from rho/ux/uy + i nx ny.
+cudaError_t launch_init_fields(int precision, const Member *d_members, const int *members, int n,
+                               int nx, int ny, const double *rho, const double *ux,
+                               const double *uy, int state, cudaStream_t s);
 cudaError_t launch_get_populations(int precision, const Member *d_members, int member,
                                    int nx, int ny, int cur, double *f, cudaStream_t s);
 cudaError_t launch_set_populations(int precision, const Member *d_members, int member,

@@ -678,26 +678,38 @@ cudaError_t launch_step_scalar(int precision, const Member *d_members, int membe
 // population f_l(x, n) through pub_index.
 // ---------------------------------------------------------------------------
 
+// f(x, 0) = f_eq(rho(x), u(x)) (eq. 2) for the members of `list`
+// (blockIdx.z = entry), each from its own fields at rho + entry * N etc.
+// FP32 storage: the deviation t_l (rho - rho0 + rho poly) in FP32 arithmetic
+// from rho - rho0 formed in FP64 (GB300 runs FP64 arithmetic and
+// conversions on a slow pipe); FP64 storage: FP64 throughout.
 template <typename T>
-__global__ void k_init(const Member *__restrict__ members, int member, const double *rho,
+__global__ void k_init(const Member *__restrict__ members, InitList list, const double *rho,
                        const double *ux, const double *uy, int state) {
-  const Member &M = members[member];
+  const Member &M = members[list.m[blockIdx.z]];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= M.nx || y >= M.ny) return;
   T *dst = static_cast<T *>(state_buffer(M, state));
-  const size_t c = (size_t)y * M.nx + x;
-  const double r = rho[c], u = ux[c], v = uy[c];
+  const size_t N = (size_t)M.nx * M.ny;
+  const size_t c = (size_t)blockIdx.z * N + (size_t)y * M.nx + x;
+  if constexpr (sizeof(T) == 4) {
+    const float dr = (float)(rho[c] - M.rho0), r = (float)rho[c];
+    const float u = (float)ux[c], v = (float)uy[c], uu = u * u + v * v;
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) {
-    const double cu = cx_of(l) * u + cy_of(l) * v;
-    const double poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * (u * u + v * v);
-    double val;
-    if (sizeof(T) == 4)
-      val = w_of(l) * ((r - M.rho0) + r * poly);  // deviation from t_l rho0
-    else
-      val = w_of(l) * r * (1.0 + poly);
-    dst[pub_index(M, state, l, x, y)] = (T)val;
+    for (int l = 0; l < kQ; ++l) {
+      const float cu = (float)cx_of(l) * u + (float)cy_of(l) * v;
+      const float poly = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
+      dst[pub_index(M, state, l, x, y)] = (float)w_of(l) * (dr + r * poly);
+    }
+  } else {
+    const double r = rho[c], u = ux[c], v = uy[c];
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const double cu = cx_of(l) * u + cy_of(l) * v;
+      const double poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * (u * u + v * v);
+      dst[pub_index(M, state, l, x, y)] = (T)(w_of(l) * r * (1.0 + poly));
+    }
   }
 }
 
@@ -1150,10 +1162,23 @@ __global__ void k_status(const Member *__restrict__ members, int member, int sta
       kern<double><<<g, b, 0, s>>>(__VA_ARGS__);                        \
   } while (0)
 
-cudaError_t launch_init_fields(int precision, const Member *d_members, int member, int nx,
-                               int ny, const double *rho, const double *ux,
+cudaError_t launch_init_fields(int precision, const Member *d_members, const int *members, int n,
+                               int nx, int ny, const double *rho, const double *ux,
                                const double *uy, int state, cudaStream_t s) {
-  LBM_DISPATCH(precision, k_init, d_members, member, rho, ux, uy, state);
+  const size_t N = (size_t)nx * ny;
+  for (int i0 = 0; i0 < n; i0 += InitList::kMax) {
+    InitList list;
+    list.n = n - i0 < InitList::kMax ? n - i0 : InitList::kMax;
+    for (int i = 0; i < list.n; ++i) list.m[i] = members[i0 + i];
+    const dim3 b(64, 4);
+    dim3 g = grid2d(nx, ny, b);
+    g.z = list.n;
+    const size_t o = (size_t)i0 * N;
+    if (precision == 32)
+      k_init<float><<<g, b, 0, s>>>(d_members, list, rho + o, ux + o, uy + o, state);
+    else
+      k_init<double><<<g, b, 0, s>>>(d_members, list, rho + o, ux + o, uy + o, state);
+  }
   return cudaGetLastError();
 }
 
