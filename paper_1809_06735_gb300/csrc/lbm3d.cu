@@ -27,7 +27,6 @@ namespace {
 // Velocity sets: D3Q27 = rest, 6 axis, 12 edge, 8 corner velocities in the
 // order of include/lbm3d.h; D3Q19 is its first 19 entries.  Weights by
 // |c|^2: D3Q19 1/3, 1/18, 1/36; D3Q27 8/27, 2/27, 1/54, 1/216.
-constexpr int kQmax = 27;
 __host__ __device__ constexpr int c3x(int l) {
   return (l == 1 || l == 7 || l == 9 || l == 11 || l == 13 || l == 19 || l == 21 || l == 23 ||
           l == 26) ? 1
