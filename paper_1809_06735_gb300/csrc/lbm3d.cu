@@ -491,33 +491,52 @@ __device__ __forceinline__ size_t tidx(const M3 &M, int x, int y, int z) {
 }
 
 // Largest |T_k| of each field: one CTA per field, fixed-order max.
-__global__ void k3_absmax(Diag3 J, double *maxes) {
+// Largest |T_k| per term field: grid (CTAs, 13), each CTA a strided share
+// of the cells, combined with an integer atomicMax on the bit pattern
+// (non-negative doubles order like their bits; NaN counts as 0).  maxbits
+// [13] must be zero on entry.
+__global__ void __launch_bounds__(256) k3_absmax(Diag3 J, unsigned long long *maxbits) {
   const M3 &M = *J.m;
-  const int k = blockIdx.x;
+  const int k = blockIdx.y;
   const double *A = J.f + (size_t)(T3 + k) * M.N;
-  double m = 0.0;
-  for (size_t i = threadIdx.x; i < M.N; i += blockDim.x) m = fmax(m, fabs(A[i]));
-  __shared__ double sh[256];
-  sh[threadIdx.x] = m;
+  unsigned long long m = 0ull;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M.N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(A[i]) & 0x7fffffffffffffffull;
+    if (b <= 0x7ff0000000000000ull && b > m) m = b;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long n = __shfl_xor_sync(0xffffffffu, m, o);
+    m = n > m ? n : m;
+  }
+  __shared__ unsigned long long sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
-    // scale 2^e with N max |T_k| 2^e < 2^62: every partial sum fits int64
-    const double mx = sh[0];
-    int e = 0;
-    if (mx > 0.0) {
-      int ex, nbits = 0;
-      frexp(mx, &ex);  // mx < 2^ex
-      while (((size_t)1 << nbits) < M.N) ++nbits;
-      e = 62 - nbits - ex;
-      if (e > 1000) e = 1000;
-    }
-    maxes[k] = ldexp(1.0, e);
-    maxes[16 + k] = (double)e;
+    for (int w = 1; w < 8; ++w) m = sh[w] > m ? sh[w] : m;
+    atomicMax(maxbits + k, m);
   }
+}
+
+// Scales 2^e with N max |T_k| 2^e < 2^62 (every partial sum fits int64):
+// maxes[k] = 2^e, maxes[16 + k] = e, maxes[80 + k] = 2^-e (one thread per field).
+__global__ void k3_scales(Diag3 J, const unsigned long long *maxbits, double *maxes) {
+  const M3 &M = *J.m;
+  const int k = threadIdx.x;
+  if (k >= 13) return;
+  const double mx = __longlong_as_double((long long)maxbits[k]);
+  int e = 0;
+  if (mx > 0.0) {
+    int ex, nbits = 0;
+    frexp(mx, &ex);  // mx < 2^ex
+    while (((size_t)1 << nbits) < M.N) ++nbits;
+    e = 62 - nbits - ex;
+    if (e > 1000) e = 1000;
+  }
+  maxes[k] = ldexp(1.0, e);
+  maxes[16 + k] = (double)e;
+  maxes[80 + k] = ldexp(1.0, -e);
 }
 
 // Quantised values scanned along x: one thread per (y, z, field) row.
@@ -595,7 +614,7 @@ __global__ void __launch_bounds__(256) k3_query(Diag3 J, const long long *tab,
                                                 double *partials, double *per_box) {
   const M3 &M = *J.m;
   const size_t ts = (size_t)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
-  const double area = (double)L * L * L;
+  const double inv_area = 1.0 / ((double)L * L * L);
   double acc[kQS3];
   for (int q = 0; q < kQS3; ++q) acc[q] = 0.0;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
@@ -616,7 +635,7 @@ __global__ void __launch_bounds__(256) k3_query(Diag3 J, const long long *tab,
       const unsigned long long s =
           P3(M, t, X1, Y1, Z1) - P3(M, t, X0, Y1, Z1) - P3(M, t, X1, Y0, Z1) - P3(M, t, X1, Y1, Z0) +
           P3(M, t, X0, Y0, Z1) + P3(M, t, X0, Y1, Z0) + P3(M, t, X1, Y0, Z0) - P3(M, t, X0, Y0, Z0);
-      v[2 + k] = (double)(long long)s / scales[k] / area;
+      v[2 + k] = (double)(long long)s * (scales[80 + k] * inv_area);  // 2^-e / L^3
     }
     v[0] = delta3(v + 2, 5);
     v[1] = delta3(v + 8, 6);
@@ -652,18 +671,28 @@ __global__ void k3_means(Diag3 J, const long long *tab, const double *scales, do
   means[k] = (double)tab[(size_t)k * ts + tidx(M, M.nx, M.ny, M.nz)] / scales[k] / (double)M.N;
 }
 
+// Mean and population standard deviation of the 15 quantities of one size
+// from the query's CTA partials: a warp per quantity (15 x 32 threads), each
+// lane a fixed-order chain over the CTAs, then a shuffle tree.
 __global__ void k3_stats(const double *partials, int nblocks, const double *means, int nb,
                          double *stats) {
-  const int q = threadIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= 15) return;
   double s1 = 0.0, s2 = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
+  for (int b = lane; b < nblocks; b += 32) {
     s1 += partials[(size_t)b * kQS3 + 2 * q];
     s2 += partials[(size_t)b * kQS3 + 2 * q + 1];
   }
-  const double m1 = s1 / nb;
-  stats[2 * q] = (q < 2 ? 0.0 : means[q - 2]) + m1;
-  stats[2 * q + 1] = sqrt(fmax(s2 / nb - m1 * m1, 0.0));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    const double m1 = s1 / nb;
+    stats[2 * q] = (q < 2 ? 0.0 : means[q - 2]) + m1;
+    stats[2 * q + 1] = sqrt(fmax(s2 / nb - m1 * m1, 0.0));
+  }
 }
 
 }  // namespace
@@ -767,7 +796,7 @@ Layout3 layout3(const lbm3d_config *cfg) {
     Tmax = std::max(Tmax, (size_t)(c.nx + 1) * (c.ny + 1) * (c.nz + 1));
   }
   // fields, 13 tables (as int64), scales/means, query partials
-  L.diag_doubles = (size_t)NF3 * Nmax + 13 * Tmax + 80 + (size_t)kMaxQBlocks3 * kQS3;
+  L.diag_doubles = (size_t)NF3 * Nmax + 13 * Tmax + 112 + (size_t)kMaxQBlocks3 * kQS3;
   L.diag = take(8 * L.diag_doubles);
   L.origin_cap = std::max<size_t>(3 * Nmax, (size_t)3 << 20);
   L.origins = take(4 * L.origin_cap);
@@ -1045,13 +1074,17 @@ int lbm3d_subvolume_balance(lbm3d_handle *h, int member, const int *L, int nL,
   double *scales = h->diag + (size_t)NF3 * N + 13 * T;  // [16] scales, [16] exponents
   double *means = scales + 32;                           // [16]
   double *sd = scales + 48;                              // [30] statistics of one size
-  double *partials = scales + 80;                        // [blocks][kQS3]
+  // scales + 80: [16] inverse scales 2^-e; scales + 96: [16] maxima bit patterns
+  double *partials = scales + 112;                       // [blocks][kQS3]
   const dim3 cb(64, 4), cg = cells3(c);
   k3_prep<<<cg, cb, 0, h->stream>>>(J);
   k3_grad<<<cg, cb, 0, h->stream>>>(J);
   k3_flux<<<cg, cb, 0, h->stream>>>(J);
   k3_curl<<<cg, cb, 0, h->stream>>>(J);
-  k3_absmax<<<13, 256, 0, h->stream>>>(J, scales);
+  unsigned long long *maxbits = reinterpret_cast<unsigned long long *>(scales + 96);
+  CK3(cudaMemsetAsync(maxbits, 0, 16 * sizeof(unsigned long long), h->stream));
+  k3_absmax<<<dim3((unsigned)std::min<size_t>(256, (N + 2047) / 2048), 13), 256, 0, h->stream>>>(J, maxbits);
+  k3_scales<<<1, 32, 0, h->stream>>>(J, maxbits, scales);
   k3_scan_x<<<dim3((c.ny + 1 + 63) / 64, c.nz + 1, 13), 64, 0, h->stream>>>(J, scales, tab);
   k3_scan_yz<<<dim3((c.nx + 1 + 63) / 64, c.nz + 1, 13), 64, 0, h->stream>>>(J, tab, 1);
   k3_scan_yz<<<dim3((c.nx + 1 + 63) / 64, c.ny + 1, 13), 64, 0, h->stream>>>(J, tab, 2);
@@ -1068,7 +1101,7 @@ int lbm3d_subvolume_balance(lbm3d_handle *h, int member, const int *L, int nL,
       k3_query<<<qb, 256, 0, h->stream>>>(J, tab, scales, means, L[i], nb,
                                           origins ? h->d_origins + 3 * ooff : nullptr, partials,
                                           per_box_out ? per_box_out + row * 15 : nullptr);
-      k3_stats<<<1, 32, 0, h->stream>>>(partials, qb, means, nb, sd);
+      k3_stats<<<1, 15 * 32, 0, h->stream>>>(partials, qb, means, nb, sd);
       CK3(cudaGetLastError());
       CK3(cudaMemcpyAsync(host.data() + 30 * (size_t)i, sd, 8 * 30, cudaMemcpyDeviceToHost,
                           h->stream));
