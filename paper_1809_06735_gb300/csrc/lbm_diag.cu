@@ -952,30 +952,23 @@ __global__ void k_scales(const DiagJob *__restrict__ jobs, int nF) {
   }
 }
 
-// round(v * 2^e) for a float v with |v| 2^e < 2^62, in integer arithmetic:
-// the float's 24-bit significand shifted by its exponent plus e (ties round
-// up).  Avoids the 64-bit float-to-integer conversion, which GB300 runs on
-// its slow FP64 path.
+// round(v * 2^e) for a float v with |v| 2^e < 2^62 (ties to even), without
+// float-to-integer conversions (GB300 runs them at a fraction of the ALU
+// rate): w = v 2^e is exact in FP32; below 2^23 adding 2^23 rounds w to an
+// integer that the sum's significand bits hold; from 2^23 on w already is an
+// integer, its significand shifted by the exponent.  NaN or Inf gives 0.
 __device__ __forceinline__ long long quantize(float v, int e) {
-  const unsigned bits = __float_as_uint(v);
-  const int ex = (int)((bits >> 23) & 0xffu);
-  long long mant = (long long)(bits & 0x7fffffu);
-  int shift;
-  if (ex == 0) {
-    shift = e - 149;  // subnormal: mant * 2^-149
-  } else {
-    mant |= 0x800000ll;
-    shift = ex - 150 + e;
-  }
+  const float w = v * __int_as_float((e + 127) << 23);  // 2^e, -126 <= e <= 120
+  const float aw = fabsf(w);
   long long q;
-  if (shift >= 0) {
-    q = mant << shift;
-  } else if (shift > -40) {
-    q = (mant + (1ll << (-shift - 1))) >> (-shift);
+  if (aw < 8388608.0f) {
+    q = __float_as_int(aw + 8388608.0f) - 0x4B000000;
   } else {
-    q = 0;
+    const unsigned bits = __float_as_uint(aw);
+    const int sh = (int)(bits >> 23) - 150;  // 0 .. 38 for |w| < 2^62
+    q = sh < 40 ? (long long)((bits & 0x7fffffu) | 0x800000u) << sh : 0ll;
   }
-  return (bits >> 31) ? -q : q;
+  return w < 0.0f ? -q : q;
 }
 __device__ __forceinline__ long long quantize(double v, int e) {
   return __double2ll_rn(ldexp(v, e));
