@@ -49,6 +49,9 @@ typedef struct lbm3d_config {
   void *cuda_stream; /* cudaStream_t of all work; NULL = default stream */
   int lattice;      /* velocity set of every member: 19 (D3Q19; also 0) or 27
                        (D3Q27); anything else is LBM_ERR_ARG */
+  int diag_precision; /* arithmetic of the balance terms: 64 (also 0) FP64;
+                         32 FP32 (level differences formed in FP64 from the
+                         FP64 snapshots, rounded once) */
 } lbm3d_config;
 
 typedef struct lbm3d_handle lbm3d_handle;

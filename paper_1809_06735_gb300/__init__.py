@@ -56,7 +56,8 @@ class _MemberCfg3(ctypes.Structure):
 class _Config3(ctypes.Structure):
     _fields_ = [("n_members", ctypes.c_int), ("members", ctypes.POINTER(_MemberCfg3)),
                 ("precision", ctypes.c_int), ("diag_every", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p), ("lattice", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("lattice", ctypes.c_int),
+                ("diag_precision", ctypes.c_int)]
 
 
 class _Config(ctypes.Structure):
@@ -462,11 +463,12 @@ class Member3:
 
 class Lattice3D:
     """Handle over D3Q19 or D3Q27 members (``lattice`` 19 or 27;
-    include/lbm3d.h): FP32 deviation or FP64 storage, workspace in one torch
-    uint8 CUDA tensor, work on ``stream``."""
+    include/lbm3d.h): FP32 deviation or FP64 storage, balance terms in FP64
+    (``diag_precision`` 0 or 64) or FP32 (32), workspace in one torch uint8
+    CUDA tensor, work on ``stream``."""
 
     def __init__(self, members: Sequence[Member3], precision: int = 32, diag_every: int = 0,
-                 stream=None, device=None, lattice: int = 19):
+                 stream=None, device=None, lattice: int = 19, diag_precision: int = 0):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -476,7 +478,8 @@ class Lattice3D:
         self._arr = (_MemberCfg3 * len(self.members))(*[m.c() for m in self.members])
         self.q = 27 if lattice == 27 else 19
         self._cfg = _Config3(len(self.members), self._arr, precision, diag_every,
-                             ctypes.c_void_p(self.stream.cuda_stream), int(lattice))
+                             ctypes.c_void_p(self.stream.cuda_stream), int(lattice),
+                             int(diag_precision))
         n = ctypes.c_size_t()
         self._check(self.lib.lbm3d_workspace_size(ctypes.byref(self._cfg), ctypes.byref(n)))
         self.workspace = torch.empty(n.value + 256, dtype=torch.uint8, device=self.device)

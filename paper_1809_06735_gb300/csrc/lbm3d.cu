@@ -307,7 +307,7 @@ __global__ void k3_snapshot(const M3 *__restrict__ ms, int member, int cur, int 
 
 // scratch field indices (each N doubles)
 enum F3 {
-  UX0, UY0, UZ0, UX1, UY1, UZ1, UX2, UY2, UZ2, R0, DR, FRX, FRY, FRZ, WX, WY, WZ,
+  UX0, UY0, UZ0, DU01X, DU01Y, DU01Z, DU12X, DU12Y, DU12Z, R0, DR, FRX, FRY, FRZ, WX, WY, WZ,
   EUX, EUY, EUZ, CUX, CUY, CUZ, OUX, OUY, OUZ, SXX, SXY, SXZ, SYY, SYZ, SZZ, HWX, HWY, HWZ,
   T3,  // T3 .. T3 + 12: the 13 term fields
   NF3 = T3 + 13
@@ -319,118 +319,163 @@ struct Diag3 {
   double *f;                   // NF3 fields of N doubles, then the tables
 };
 
-// Eq. (18) along axis a (0 x, 1 y, 2 z), periodic.
-__device__ __forceinline__ double D3(const M3 &M, const double *A, int x, int y, int z, int a) {
-  const double cf[4] = {0.8, -0.2, 4.0 / 105.0, -1.0 / 280.0};
-  double s = 0.0;
+// Periodic index for i in [-4, n + 4): one compare for n >= 4, a modulo for
+// the tiny grids.
+__device__ __forceinline__ int wrap4(int i, int n) {
+  if (n >= 4) return i < 0 ? i + n : (i >= n ? i - n : i);
+  return ((i % n) + n) % n;
+}
+
+// Eq. (18) along axis a (0 x, 1 y, 2 z), periodic, in the arithmetic type T.
+template <typename T>
+__device__ __forceinline__ T D3(const M3 &M, const T *A, int x, int y, int z, int a) {
+  const T cf[4] = {T(0.8), T(-0.2), T(4.0 / 105.0), T(-1.0 / 280.0)};
+  T s = T(0);
 #pragma unroll
   for (int k = 1; k <= 4; ++k) {
     size_t p, q;
     if (a == 0) {
-      p = cell(M, wrp(x + k, M.nx) % M.nx, y, z);
-      q = cell(M, (wrp(x - k, M.nx) + M.nx) % M.nx, y, z);
+      p = cell(M, wrap4(x + k, M.nx), y, z);
+      q = cell(M, wrap4(x - k, M.nx), y, z);
     } else if (a == 1) {
-      p = cell(M, x, wrp(y + k, M.ny) % M.ny, z);
-      q = cell(M, x, (wrp(y - k, M.ny) + M.ny) % M.ny, z);
+      p = cell(M, x, wrap4(y + k, M.ny), z);
+      q = cell(M, x, wrap4(y - k, M.ny), z);
     } else {
-      p = cell(M, x, y, wrp(z + k, M.nz) % M.nz);
-      q = cell(M, x, y, (wrp(z - k, M.nz) + M.nz) % M.nz);
+      p = cell(M, x, y, wrap4(z + k, M.nz));
+      q = cell(M, x, y, wrap4(z - k, M.nz));
     }
     s += cf[k - 1] * (A[p] - A[q]);
   }
   return s;
 }
 
+// One thread per cell; scratch field k holds N values of T in its N-double
+// slot.
 #define D3CELL                                                                   \
   const M3 &M = *J.m;                                                            \
   const int x = blockIdx.x * blockDim.x + threadIdx.x,                           \
             y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;           \
   if (x >= M.nx || y >= M.ny) return;                                            \
   const size_t N = M.N, c = cell(M, x, y, z);                                    \
-  auto F = [&](int k) { return J.f + (size_t)k * N; };
+  auto F = [&](int k) { return reinterpret_cast<T *>(J.f + (size_t)k * N); };
 
-// Pass 0: velocities u = (j + F/2)/rho at the three levels, rho, rho - rho0,
-// F/rho; LHS^E (eq. 17) and RHS^{E,3} = u . F.
+// Pass 0.  Bare momentum j and u = (j + F/2)/rho with F = F_ext - alpha j,
+// i.e. rho u = m = (1 - alpha/2) j + F_ext/2.  The level differences of rho
+// and j are formed in FP64 from the FP64 snapshots and rounded once to T;
+// u^n - u^{n-1} = ((1 - alpha/2)(j^n - j^{n-1}) - u^n (rho^n - rho^{n-1}))
+// / rho^{n-1} (exact identity), and E^n - E^{n-1} = [drho |u^n|^2 +
+// rho^{n-1} du . (2 u^n - du)] / 2, so LHS^E = (3 dE01 - dE12)/2 (eq. 17)
+// carries no cancellation of the level values themselves.  Stores u^n, the
+// two velocity differences, rho, rho - rho0, F/rho; LHS^E and
+// RHS^{E,3} = u . F.
+template <typename T>
 __global__ void k3_prep(Diag3 J) {
   D3CELL;
-  double fx, fy, fz;
-  force3<double>(M, M.ftab64, x, y, z, fx, fy, fz);
-  const double *S[3] = {J.s0, J.s1, J.s2};
-  double E[3], u0[3] = {0, 0, 0}, F0v[3] = {0, 0, 0};
-  for (int m = 0; m < 3; ++m) {
-    const double r = S[m][c], jx = S[m][N + c], jy = S[m][2 * N + c], jz = S[m][3 * N + c];
-    const double Fx = fx - M.alpha * jx, Fy = fy - M.alpha * jy, Fz = fz - M.alpha * jz;
-    const double u = (jx + 0.5 * Fx) / r, v = (jy + 0.5 * Fy) / r, w = (jz + 0.5 * Fz) / r;
-    F(UX0 + 3 * m)[c] = u;
-    F(UY0 + 3 * m)[c] = v;
-    F(UZ0 + 3 * m)[c] = w;
-    E[m] = 0.5 * r * (u * u + v * v + w * w);
-    if (m == 0) {
-      u0[0] = u;
-      u0[1] = v;
-      u0[2] = w;
-      F0v[0] = Fx;
-      F0v[1] = Fy;
-      F0v[2] = Fz;
-      F(R0)[c] = r;
-      F(DR)[c] = r - M.rho0;
-      F(FRX)[c] = Fx / r;
-      F(FRY)[c] = Fy / r;
-      F(FRZ)[c] = Fz / r;
-    }
+  double fxd, fyd, fzd;
+  force3<double>(M, M.ftab64, x, y, z, fxd, fyd, fzd);
+  const double *S0 = J.s0, *S1 = J.s1, *S2 = J.s2;
+  const double r0d = S0[c], r1d = S1[c], r2d = S2[c];
+  T j0[3], dj01[3], dj12[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const size_t o = (size_t)(i + 1) * N + c;
+    j0[i] = (T)S0[o];
+    dj01[i] = (T)(S0[o] - S1[o]);
+    dj12[i] = (T)(S1[o] - S2[o]);
   }
-  F(T3 + 0)[c] = 1.5 * E[0] - 2.0 * E[1] + 0.5 * E[2];
-  F(T3 + 3)[c] = u0[0] * F0v[0] + u0[1] * F0v[1] + u0[2] * F0v[2];
+  const T r0 = (T)r0d, r1 = (T)r1d, r2 = (T)r2d;
+  const T dr01 = (T)(r0d - r1d), dr12 = (T)(r1d - r2d);
+  const T a = (T)M.alpha, ca = T(1) - T(0.5) * a;
+  const T fe[3] = {(T)fxd, (T)fyd, (T)fzd};
+  T u0[3], du01[3], du12[3], Fv[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Fv[i] = fe[i] - a * j0[i];
+    u0[i] = (j0[i] + T(0.5) * Fv[i]) / r0;
+  }
+  T q0 = T(0), q1 = T(0), p01 = T(0), p12 = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    du01[i] = (ca * dj01[i] - u0[i] * dr01) / r1;
+    const T u1 = u0[i] - du01[i];
+    du12[i] = (ca * dj12[i] - u1 * dr12) / r2;
+    q0 += u0[i] * u0[i];
+    q1 += u1 * u1;
+    p01 += du01[i] * (T(2) * u0[i] - du01[i]);
+    p12 += du12[i] * (T(2) * u1 - du12[i]);
+  }
+  const T dE01 = T(0.5) * (dr01 * q0 + r1 * p01);
+  const T dE12 = T(0.5) * (dr12 * q1 + r2 * p12);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    F(UX0 + i)[c] = u0[i];
+    F(DU01X + i)[c] = du01[i];
+    F(DU12X + i)[c] = du12[i];
+    F(FRX + i)[c] = Fv[i] / r0;
+  }
+  F(R0)[c] = r0;
+  F(DR)[c] = (T)(r0d - M.rho0);
+  F(T3 + 0)[c] = T(0.5) * (T(3) * dE01 - dE12);
+  F(T3 + 3)[c] = u0[0] * Fv[0] + u0[1] * Fv[1] + u0[2] * Fv[2];
 }
 
-// Pass 1: velocity gradients G_ij = d_j u_i at n, vorticity at the three
-// levels (LHS^Omega), S, RHS^{E,2}, RHS^{E,4}, RHS^{O,2}, RHS^{O,3},
-// RHS^{O,6}, and the fluxes of pass 2.
+// Pass 1: velocity gradients G_ij = d_j u_i at n, the vorticity w^n and its
+// level differences dw = curl(du) (LHS^Omega = (3 dO01 - dO12)/2 with
+// O^n - O^{n-1} = dw01 . (2 w^n - dw01)/2), S, RHS^{E,2}, RHS^{E,4},
+// RHS^{O,2}, RHS^{O,3}, RHS^{O,6}, and the fluxes of pass 2.
+template <typename T>
 __global__ void k3_grad(Diag3 J) {
   D3CELL;
-  double G[3][3];
+  T G[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) G[i][j] = D3(M, F(UX0 + i), x, y, z, j);
-  double Om[3], w0[3];
+    for (int j = 0; j < 3; ++j) G[i][j] = D3<T>(M, F(UX0 + i), x, y, z, j);
+  T w0[3];
   w0[0] = G[2][1] - G[1][2];
   w0[1] = G[0][2] - G[2][0];
   w0[2] = G[1][0] - G[0][1];
-  Om[0] = 0.5 * (w0[0] * w0[0] + w0[1] * w0[1] + w0[2] * w0[2]);
-  for (int m = 1; m < 3; ++m) {
-    const double *U = F(UX0 + 3 * m), *V = F(UY0 + 3 * m), *W = F(UZ0 + 3 * m);
-    const double wx = D3(M, W, x, y, z, 1) - D3(M, V, x, y, z, 2);
-    const double wy = D3(M, U, x, y, z, 2) - D3(M, W, x, y, z, 0);
-    const double wz = D3(M, V, x, y, z, 0) - D3(M, U, x, y, z, 1);
-    Om[m] = 0.5 * (wx * wx + wy * wy + wz * wz);
+  T dO[2];
+  T w1[3];
+  for (int m = 0; m < 2; ++m) {
+    const T *U = F((m ? DU12X : DU01X)), *V = F((m ? DU12Y : DU01Y)), *W = F((m ? DU12Z : DU01Z));
+    const T dw[3] = {D3<T>(M, W, x, y, z, 1) - D3<T>(M, V, x, y, z, 2),
+                     D3<T>(M, U, x, y, z, 2) - D3<T>(M, W, x, y, z, 0),
+                     D3<T>(M, V, x, y, z, 0) - D3<T>(M, U, x, y, z, 1)};
+    const T *wl = m ? w1 : w0;  // the later level of the pair
+    T p = T(0);
+    for (int i = 0; i < 3; ++i) p += dw[i] * (T(2) * wl[i] - dw[i]);
+    dO[m] = T(0.5) * p;
+    if (m == 0)
+      for (int i = 0; i < 3; ++i) w1[i] = w0[i] - dw[i];
   }
-  F(T3 + 6)[c] = 1.5 * Om[0] - 2.0 * Om[1] + 0.5 * Om[2];
-  const double u[3] = {F(UX0)[c], F(UY0)[c], F(UZ0)[c]}, r = F(R0)[c];
-  const double nr = M.nu * r;
-  double S[3][3];
+  F(T3 + 6)[c] = T(0.5) * (T(3) * dO[0] - dO[1]);
+  const T Om0 = T(0.5) * (w0[0] * w0[0] + w0[1] * w0[1] + w0[2] * w0[2]);
+  const T u[3] = {F(UX0)[c], F(UY0)[c], F(UZ0)[c]}, r = F(R0)[c];
+  const T nr = (T)M.nu * r;
+  T S[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) S[i][j] = G[i][j] + G[j][i];
-  double gp = 0.0, sd = 0.0, st = 0.0;
-  for (int i = 0; i < 3; ++i) gp += u[i] * D3(M, F(DR), x, y, z, i) / 3.0;
+  T gp = T(0), sd = T(0), st = T(0);
+  for (int i = 0; i < 3; ++i) gp += u[i] * D3<T>(M, F(DR), x, y, z, i) / T(3);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       sd += S[i][j] * G[i][j];
       st += w0[i] * w0[j] * G[i][j];
     }
-  const double div = G[0][0] + G[1][1] + G[2][2];
-  double cf = 0.0;  // omega . curl(F / rho)
+  const T div = G[0][0] + G[1][1] + G[2][2];
+  T cf = T(0);  // omega . curl(F / rho)
   for (int i = 0; i < 3; ++i) {
     const int j = (i + 1) % 3, k = (i + 2) % 3;
-    cf += w0[i] * (D3(M, F(FRX + k), x, y, z, j) - D3(M, F(FRX + j), x, y, z, k));
+    cf += w0[i] * (D3<T>(M, F(FRX + k), x, y, z, j) - D3<T>(M, F(FRX + j), x, y, z, k));
   }
   F(T3 + 2)[c] = -gp;
   F(T3 + 4)[c] = -nr * sd;
-  F(T3 + 8)[c] = -Om[0] * div;
+  F(T3 + 8)[c] = -Om0 * div;
   F(T3 + 9)[c] = cf;
   F(T3 + 12)[c] = st;
-  const double E0 = 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const T E0 = T(0.5) * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   for (int j = 0; j < 3; ++j) {
     F(EUX + j)[c] = E0 * u[j];
-    F(OUX + j)[c] = Om[0] * u[j];
+    F(OUX + j)[c] = Om0 * u[j];
     F(CUX + j)[c] = nr * (u[0] * S[0][j] + u[1] * S[1][j] + u[2] * S[2][j]);
     F(WX + j)[c] = w0[j];
   }
@@ -444,28 +489,29 @@ __global__ void k3_grad(Diag3 J) {
 
 // Pass 2: RHS^{E,1}, RHS^{E,5}, RHS^{O,1}; H_i = d_j(nu rho S_ij)/rho;
 // RHS^{O,4} = H . curl(omega); H x omega for pass 3.
+template <typename T>
 __global__ void k3_flux(Diag3 J) {
   D3CELL;
-  double e1 = 0.0, e5 = 0.0, o1 = 0.0;
+  T e1 = T(0), e5 = T(0), o1 = T(0);
   for (int j = 0; j < 3; ++j) {
-    e1 -= D3(M, F(EUX + j), x, y, z, j);
-    e5 += D3(M, F(CUX + j), x, y, z, j);
-    o1 -= D3(M, F(OUX + j), x, y, z, j);
+    e1 -= D3<T>(M, F(EUX + j), x, y, z, j);
+    e5 += D3<T>(M, F(CUX + j), x, y, z, j);
+    o1 -= D3<T>(M, F(OUX + j), x, y, z, j);
   }
   const int sidx[3][3] = {{SXX, SXY, SXZ}, {SXY, SYY, SYZ}, {SXZ, SYZ, SZZ}};
-  const double r = F(R0)[c];
-  double H[3];
+  const T r = F(R0)[c];
+  T H[3];
   for (int i = 0; i < 3; ++i) {
-    double h = 0.0;
-    for (int j = 0; j < 3; ++j) h += D3(M, F(sidx[i][j]), x, y, z, j);
+    T h = T(0);
+    for (int j = 0; j < 3; ++j) h += D3<T>(M, F(sidx[i][j]), x, y, z, j);
     H[i] = h / r;
   }
-  double o4 = 0.0;
+  T o4 = T(0);
   for (int i = 0; i < 3; ++i) {
     const int j = (i + 1) % 3, k = (i + 2) % 3;
-    o4 += H[i] * (D3(M, F(WX + k), x, y, z, j) - D3(M, F(WX + j), x, y, z, k));
+    o4 += H[i] * (D3<T>(M, F(WX + k), x, y, z, j) - D3<T>(M, F(WX + j), x, y, z, k));
   }
-  const double w[3] = {F(WX)[c], F(WY)[c], F(WZ)[c]};
+  const T w[3] = {F(WX)[c], F(WY)[c], F(WZ)[c]};
   F(T3 + 1)[c] = e1;
   F(T3 + 5)[c] = e5;
   F(T3 + 7)[c] = o1;
@@ -477,10 +523,11 @@ __global__ void k3_flux(Diag3 J) {
 }
 
 // Pass 3: RHS^{O,5} = div(H x omega).
+template <typename T>
 __global__ void k3_curl(Diag3 J) {
   D3CELL;
-  double s = 0.0;
-  for (int j = 0; j < 3; ++j) s += D3(M, F(HWX + j), x, y, z, j);
+  T s = T(0);
+  for (int j = 0; j < 3; ++j) s += D3<T>(M, F(HWX + j), x, y, z, j);
   F(T3 + 11)[c] = s;
 }
 
@@ -490,20 +537,29 @@ __device__ __forceinline__ size_t tidx(const M3 &M, int x, int y, int z) {
   return ((size_t)z * (M.ny + 1) + y) * (M.nx + 1) + x;
 }
 
-// Largest |T_k| of each field: one CTA per field, fixed-order max.
 // Largest |T_k| per term field: grid (CTAs, 13), each CTA a strided share
 // of the cells, combined with an integer atomicMax on the bit pattern
 // (non-negative doubles order like their bits; NaN counts as 0).  maxbits
 // [13] must be zero on entry.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  return b <= 0x7ff0000000000000ull ? b : 0ull;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float v) {  // as the double's bits
+  const float a = fabsf(v);
+  return a == a ? (unsigned long long)__double_as_longlong((double)a) : 0ull;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) k3_absmax(Diag3 J, unsigned long long *maxbits) {
   const M3 &M = *J.m;
   const int k = blockIdx.y;
-  const double *A = J.f + (size_t)(T3 + k) * M.N;
+  const T *A = reinterpret_cast<const T *>(J.f + (size_t)(T3 + k) * M.N);
   unsigned long long m = 0ull;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M.N;
        i += (size_t)gridDim.x * blockDim.x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(A[i]) & 0x7fffffffffffffffull;
-    if (b <= 0x7ff0000000000000ull && b > m) m = b;
+    const unsigned long long b = abs_bits(A[i]);
+    if (b > m) m = b;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -540,6 +596,7 @@ __global__ void k3_scales(Diag3 J, const unsigned long long *maxbits, double *ma
 }
 
 // Quantised values scanned along x: one thread per (y, z, field) row.
+template <typename T>
 __global__ void k3_scan_x(Diag3 J, const double *scales, long long *tab) {
   const M3 &M = *J.m;
   const int y = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y, k = blockIdx.z;
@@ -550,12 +607,12 @@ __global__ void k3_scan_x(Diag3 J, const double *scales, long long *tab) {
     for (int x = 0; x <= M.nx; ++x) t[tidx(M, x, y, z)] = 0;
     return;
   }
-  const double *A = J.f + (size_t)(T3 + k) * M.N;
+  const T *A = reinterpret_cast<const T *>(J.f + (size_t)(T3 + k) * M.N);
   const double sc = scales[k];
   long long acc = 0;
   t[tidx(M, 0, y, z)] = 0;
   for (int x = 0; x < M.nx; ++x) {
-    acc += __double2ll_rn(A[cell(M, x, y - 1, z - 1)] * sc);
+    acc += __double2ll_rn((double)A[cell(M, x, y - 1, z - 1)] * sc);
     t[tidx(M, x + 1, y, z)] = acc;
   }
 }
@@ -706,6 +763,7 @@ struct lbm3d_handle {
   size_t ws_bytes = 0;
   int precision = 32;
   int q = 19;  // lattice velocities
+  int diag_prec = 64;  // arithmetic of the balance terms
   long long vec_items = 0;  // work items of the four-cell FP32 kernel
   int vec_grid = 0;         // its persistent grid
   cudaStream_t stream = nullptr;
@@ -765,6 +823,7 @@ int check3(const lbm3d_config *cfg, std::string &err) {
   if (cfg->precision != 32 && cfg->precision != 64) { err = "precision must be 32 or 64"; return LBM_ERR_ARG; }
   if (cfg->diag_every < 0) { err = "diag_every must be >= 0"; return LBM_ERR_ARG; }
   if (cfg->lattice != 0 && cfg->lattice != 19 && cfg->lattice != 27) { err = "lattice must be 19 or 27 (0: 19)"; return LBM_ERR_ARG; }
+  if (cfg->diag_precision != 0 && cfg->diag_precision != 32 && cfg->diag_precision != 64) { err = "diag_precision must be 0, 32 or 64"; return LBM_ERR_ARG; }
   for (int m = 0; m < cfg->n_members; ++m) {
     const lbm3d_member_cfg &c = cfg->members[m];
     if (c.nx < 1 || c.ny < 1 || c.nz < 1 || (long long)c.nx * c.ny * c.nz > (1LL << 28)) { err = "grid out of range"; return LBM_ERR_ARG; }
@@ -855,6 +914,7 @@ int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_h
   h->ws_bytes = bytes;
   h->precision = cfg->precision;
   h->q = lattice_q(cfg);
+  h->diag_prec = cfg->diag_precision == 32 ? 32 : 64;
   h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   h->d_m = reinterpret_cast<M3 *>(h->ws + L.members);
   h->diag = reinterpret_cast<double *>(h->ws + L.diag);
@@ -1077,15 +1137,27 @@ int lbm3d_subvolume_balance(lbm3d_handle *h, int member, const int *L, int nL,
   // scales + 80: [16] inverse scales 2^-e; scales + 96: [16] maxima bit patterns
   double *partials = scales + 112;                       // [blocks][kQS3]
   const dim3 cb(64, 4), cg = cells3(c);
-  k3_prep<<<cg, cb, 0, h->stream>>>(J);
-  k3_grad<<<cg, cb, 0, h->stream>>>(J);
-  k3_flux<<<cg, cb, 0, h->stream>>>(J);
-  k3_curl<<<cg, cb, 0, h->stream>>>(J);
   unsigned long long *maxbits = reinterpret_cast<unsigned long long *>(scales + 96);
   CK3(cudaMemsetAsync(maxbits, 0, 16 * sizeof(unsigned long long), h->stream));
-  k3_absmax<<<dim3((unsigned)std::min<size_t>(256, (N + 2047) / 2048), 13), 256, 0, h->stream>>>(J, maxbits);
-  k3_scales<<<1, 32, 0, h->stream>>>(J, maxbits, scales);
-  k3_scan_x<<<dim3((c.ny + 1 + 63) / 64, c.nz + 1, 13), 64, 0, h->stream>>>(J, scales, tab);
+  const dim3 ag((unsigned)std::min<size_t>(256, (N + 2047) / 2048), 13);
+  const dim3 sg((c.ny + 1 + 63) / 64, c.nz + 1, 13);
+  if (h->diag_prec == 32) {  // term arithmetic in FP32
+    k3_prep<float><<<cg, cb, 0, h->stream>>>(J);
+    k3_grad<float><<<cg, cb, 0, h->stream>>>(J);
+    k3_flux<float><<<cg, cb, 0, h->stream>>>(J);
+    k3_curl<float><<<cg, cb, 0, h->stream>>>(J);
+    k3_absmax<float><<<ag, 256, 0, h->stream>>>(J, maxbits);
+    k3_scales<<<1, 32, 0, h->stream>>>(J, maxbits, scales);
+    k3_scan_x<float><<<sg, 64, 0, h->stream>>>(J, scales, tab);
+  } else {
+    k3_prep<double><<<cg, cb, 0, h->stream>>>(J);
+    k3_grad<double><<<cg, cb, 0, h->stream>>>(J);
+    k3_flux<double><<<cg, cb, 0, h->stream>>>(J);
+    k3_curl<double><<<cg, cb, 0, h->stream>>>(J);
+    k3_absmax<double><<<ag, 256, 0, h->stream>>>(J, maxbits);
+    k3_scales<<<1, 32, 0, h->stream>>>(J, maxbits, scales);
+    k3_scan_x<double><<<sg, 64, 0, h->stream>>>(J, scales, tab);
+  }
   k3_scan_yz<<<dim3((c.nx + 1 + 63) / 64, c.nz + 1, 13), 64, 0, h->stream>>>(J, tab, 1);
   k3_scan_yz<<<dim3((c.nx + 1 + 63) / 64, c.ny + 1, 13), 64, 0, h->stream>>>(J, tab, 2);
   k3_means<<<1, 32, 0, h->stream>>>(J, tab, scales, means);

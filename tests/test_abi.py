@@ -93,6 +93,10 @@ def test_3d_config_checks(P):
     assert size([P.Member3(16, 12, 8, 0.6)], lattice=27) == 0
     assert n.value - q19 >= 8 * 4 * 2 * 16 * 12 * 8  # two buffers of 8 more populations
     assert size([P.Member3(16, 12, 8, 0.6)], lattice=15) == -1
+    arr = (P._MemberCfg3 * 1)(P.Member3(16, 12, 8, 0.6).c())
+    for dp, rc in ((0, 0), (32, 0), (64, 0), (16, -1)):
+        cfg = P._Config3(1, arr, 32, 0, None, 19, dp)
+        assert lib.lbm3d_workspace_size(ctypes.byref(cfg), ctypes.byref(n)) == rc, dp
     assert size([P.Member3(16, 12, 8, 0.5)]) == -1
     assert size([P.Member3(0, 12, 8, 0.6)]) == -1
     assert size([P.Member3(8, 8, 8, 0.6, force_kind=2)]) == -1

@@ -116,6 +116,52 @@ def test_3d_balance_terms(P, orc, prec, q):
         np.testing.assert_allclose(st2[iL, :2, 0], w[0, :2, 0], rtol=1e-6, atol=1e-8)
 
 
+# FP32 balance arithmetic: the level differences are formed in FP64 from the
+# FP64 snapshots and rounded once; the remaining error is the FP32 rounding
+# amplified by the nested eq. (18) differences (three for RHS^{O,4} and
+# RHS^{O,5}), as in two dimensions: bar 1e-4 of each field's magnitude.
+FP32_TERM_TOL = 1e-4
+
+
+@pytest.mark.parametrize("prec,q", [(32, 19), (32, 27), (64, 19)])
+def test_3d_balance_terms_fp32_arithmetic(P, orc, prec, q):
+    """diag_precision 32: per-box terms within 1e-4 of each field's
+    magnitude of the oracle's on the same exported states (all origins and
+    an origin list), balancing-error statistics within 1e-3 relative; vortex
+    stretching present."""
+    nx, ny, nz, tau, F0, kf, a = 16, 12, 10, 0.57, 3e-4, 1, 2e-3
+    lat = P.Lattice3D([P.Member3(nx, ny, nz, tau, 1.0, 1, kf, F0, a)], precision=prec,
+                      diag_every=10, lattice=q, diag_precision=32)
+    lat.init_fields(0, *_fields((nz, ny, nx), 60))
+    lat.step(8)
+    f8 = lat.get_populations_host(0)
+    lat.step(1)
+    f9 = lat.get_populations_host(0)
+    lat.step(1)
+    f10 = lat.get_populations_host(0)
+    T = orc.terms3_from_populations(f10, f9, f8, tau, 1, F0, kf, a)
+    scale = np.max(np.abs(T.reshape(13, -1)), axis=1) + 1e-300
+    assert scale[12] > 1e-6 * scale[8]
+    Ls = [1, 3, 8]
+    stats, pb = lat.subvolume_balance(0, Ls, per_box=True)
+    pb = pb.cpu().numpy().reshape(len(Ls), -1, 15)
+    want, want_pb = orc.balance_stats3(T, Ls, per_box=True)
+    for iL in range(len(Ls)):
+        d = np.abs(pb[iL][:, 2:] - want_pb[iL][:, 2:]) / scale[None, :]
+        assert np.max(d) < FP32_TERM_TOL, (Ls[iL], np.max(d))
+        np.testing.assert_allclose(stats[iL, 2:, 0], want[iL, 2:, 0], rtol=0,
+                                   atol=FP32_TERM_TOL * np.max(scale))
+    rng = np.random.default_rng(3)
+    origins = [np.stack([rng.integers(0, nx, 60), rng.integers(0, ny, 60),
+                         rng.integers(0, nz, 60)], 1) for _ in range(2)]
+    st2 = lat.subvolume_balance(0, [4, 9], origins=origins)
+    for iL, L in enumerate([4, 9]):
+        w = orc.balance_stats3(T, [L], origins=origins[iL])
+        np.testing.assert_allclose(st2[iL, 2:, 0], w[0, 2:, 0], rtol=0,
+                                   atol=FP32_TERM_TOL * np.max(scale))
+        np.testing.assert_allclose(st2[iL, :2, 0], w[0, :2, 0], rtol=1e-3)
+
+
 def test_3d_history_required(P):
     lat = P.Lattice3D([P.Member3(8, 8, 8, 0.6)], precision=64)
     lat.init_fields(0, np.ones((8, 8, 8)), *(np.zeros((8, 8, 8)) for _ in range(3)))
