@@ -649,31 +649,77 @@ __device__ __forceinline__ unsigned long long P3(const M3 &M, const long long *t
   return v;
 }
 
-__device__ __forceinline__ double delta3(const double *v, int nrhs) {
-  double sum = 0.0, mx = 0.0;
-  for (int i = 1; i <= nrhs; ++i) {
+template <int NRHS, typename MT>
+__device__ __forceinline__ MT delta3(const MT *v) {
+  MT sum = MT(0), mx = MT(0);
+#pragma unroll
+  for (int i = 1; i <= NRHS; ++i) {
     sum += v[i];
     mx = fmax(mx, fabs(v[i]));
   }
-  const double num = fabs(sum - v[0]);
-  if (mx == 0.0) return num == 0.0 ? 0.0 : INFINITY;
+  const MT num = fabs(sum - v[0]);
+  if (mx == MT(0)) return num == MT(0) ? MT(0) : MT(INFINITY);
   return num / mx;
+}
+
+// 64-bit integer to the query precision; the float version assembles the
+// IEEE bits with integer instructions (round to nearest, ties away), since
+// GB300 runs integer-to-float conversions on its slow FP64 pipe.
+template <typename MT>
+__device__ __forceinline__ MT i64_to(long long v);
+template <>
+__device__ __forceinline__ double i64_to<double>(long long v) {
+  return (double)v;
+}
+template <>
+__device__ __forceinline__ float i64_to<float>(long long v) {
+  const unsigned long long sg = (unsigned long long)v >> 63;
+  const unsigned long long a = sg ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  if (a == 0ull) return 0.0f;
+  int e = 63 - __clzll((long long)a);
+  unsigned long long m;
+  if (e <= 23) {
+    m = a << (23 - e);
+  } else {
+    const int sh = e - 23;
+    m = (a + (1ull << (sh - 1))) >> sh;
+    if (m >> 24) {
+      m >>= 1;
+      ++e;
+    }
+  }
+  return __uint_as_float(((unsigned)sg << 31) | ((unsigned)(e + 127) << 23) |
+                         ((unsigned)m & 0x7fffffu));
 }
 
 constexpr int kQS3 = 30;  // per size: sums and sums of squares of 15 quantities
 
-// One thread per box: the 13 box means (exact integer sums), delta^E,
-// delta^Omega; CTA partial sums (fixed order) of the 15 quantities and
-// their squares, deviations from the field means.
+// One thread per box: the 13 box sums exactly in integers, their deviations
+// from the field means formed in integers too (the mean box sum L^3 total/N,
+// rounded) and only then converted to the query precision MT; box means,
+// delta^E, delta^Omega; CTA partial sums (fixed order) of the 15 quantities'
+// deviations and squares, MT within each warp and FP64 across warps.
+template <typename MT>
 __global__ void __launch_bounds__(256) k3_query(Diag3 J, const long long *tab,
                                                 const double *scales, const double *means,
                                                 int L, int nb, const int *origins,
                                                 double *partials, double *per_box) {
   const M3 &M = *J.m;
   const size_t ts = (size_t)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
-  const double inv_area = 1.0 / ((double)L * L * L);
-  double acc[kQS3];
-  for (int q = 0; q < kQS3; ++q) acc[q] = 0.0;
+  __shared__ long long smq[13];
+  __shared__ MT scoef[13], smean[13];
+  if (threadIdx.x < 13) {
+    const int k = threadIdx.x;
+    const double vol = (double)L * L * L;
+    const long long total = tab[(size_t)k * ts + tidx(M, M.nx, M.ny, M.nz)];
+    smq[k] = __double2ll_rn((double)total * (vol / (double)M.N));
+    scoef[k] = (MT)(scales[80 + k] / vol);  // 2^-e / L^3
+    smean[k] = (MT)means[k];
+  }
+  __syncthreads();
+  MT acc[kQS3];
+#pragma unroll
+  for (int q = 0; q < kQS3; ++q) acc[q] = MT(0);
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
     int x0, y0, z0;
     if (origins) {
@@ -685,31 +731,35 @@ __global__ void __launch_bounds__(256) k3_query(Diag3 J, const long long *tab,
       y0 = (b / M.nx) % M.ny;
       z0 = b / (M.nx * M.ny);
     }
-    double v[15];
+    MT v[15], d[15];
+#pragma unroll 1
     for (int k = 0; k < 13; ++k) {
       const long long *t = tab + (size_t)k * ts;
       const int X0 = x0, X1 = x0 + L, Y0 = y0, Y1 = y0 + L, Z0 = z0, Z1 = z0 + L;
       const unsigned long long s =
           P3(M, t, X1, Y1, Z1) - P3(M, t, X0, Y1, Z1) - P3(M, t, X1, Y0, Z1) - P3(M, t, X1, Y1, Z0) +
           P3(M, t, X0, Y0, Z1) + P3(M, t, X0, Y1, Z0) + P3(M, t, X1, Y0, Z0) - P3(M, t, X0, Y0, Z0);
-      v[2 + k] = (double)(long long)s * (scales[80 + k] * inv_area);  // 2^-e / L^3
+      d[2 + k] = i64_to<MT>((long long)(s - (unsigned long long)smq[k])) * scoef[k];
+      v[2 + k] = d[2 + k] + smean[k];
     }
-    v[0] = delta3(v + 2, 5);
-    v[1] = delta3(v + 8, 6);
+    v[0] = d[0] = delta3<5>(v + 2);
+    v[1] = d[1] = delta3<6>(v + 8);
     if (per_box)
-      for (int q = 0; q < 15; ++q) per_box[(size_t)b * 15 + q] = v[q];
+#pragma unroll
+      for (int q = 0; q < 15; ++q) per_box[(size_t)b * 15 + q] = (double)v[q];
+#pragma unroll
     for (int q = 0; q < 15; ++q) {
-      const double d = v[q] - (q < 2 ? 0.0 : means[q - 2]);
-      acc[2 * q] += d;
-      acc[2 * q + 1] += d * d;
+      acc[2 * q] += d[q];
+      acc[2 * q + 1] += d[q] * d[q];
     }
   }
   __shared__ double sh[kQS3][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
   for (int q = 0; q < kQS3; ++q) {
-    double a = acc[q];
+    MT a = acc[q];
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    if (lane == 0) sh[q][wid] = a;
+    if (lane == 0) sh[q][wid] = (double)a;
   }
   __syncthreads();
   if (threadIdx.x < kQS3) {
@@ -1170,9 +1220,14 @@ int lbm3d_subvolume_balance(lbm3d_handle *h, int member, const int *L, int nL,
     const int nb = origins ? counts[i] : (int)N;
     if (L[i] >= 1 && L[i] <= Lmax) {
       const int qb = std::min(kMaxQBlocks3, std::max(1, (nb + 255) / 256));
-      k3_query<<<qb, 256, 0, h->stream>>>(J, tab, scales, means, L[i], nb,
-                                          origins ? h->d_origins + 3 * ooff : nullptr, partials,
-                                          per_box_out ? per_box_out + row * 15 : nullptr);
+      const int *og = origins ? h->d_origins + 3 * ooff : nullptr;
+      double *pbo = per_box_out ? per_box_out + row * 15 : nullptr;
+      if (h->diag_prec == 32)
+        k3_query<float><<<qb, 256, 0, h->stream>>>(J, tab, scales, means, L[i], nb, og, partials,
+                                                   pbo);
+      else
+        k3_query<double><<<qb, 256, 0, h->stream>>>(J, tab, scales, means, L[i], nb, og,
+                                                    partials, pbo);
       k3_stats<<<1, 15 * 32, 0, h->stream>>>(partials, qb, means, nb, sd);
       CK3(cudaGetLastError());
       CK3(cudaMemcpyAsync(host.data() + 30 * (size_t)i, sd, 8 * 30, cudaMemcpyDeviceToHost,
