@@ -483,33 +483,60 @@ def run_ours(args):
     collisions = collision_models_leg(P, stream, dev, measured_peaks()[0])
     three_d = three_d_leg(P, stream, dev, measured_peaks()[0])
 
-    # end to end through the C ABI with host buffers: every step uploads the
-    # initial fields of all members from pinned host memory, runs the period
-    # and reads the statistics back.
+    # end to end through the public API with host buffers: every step uploads
+    # the initial fields of all members from pinned host memory, runs the
+    # period and reads its statistics back to the host.  Pipelined as a
+    # production caller would: step k's upload (copy stream) and step k-1's
+    # statistics read overlap step k's stream-collide; the diagnostic runs
+    # on the library's diagnostic stream.
     e2e_steps = max(1, min(args.steps, 5))
+    dev_in = torch.empty((3, M, n, n), dtype=torch.float64, device=dev)
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied, consumed = torch.cuda.Event(), torch.cuda.Event()
+    host_stats = torch.empty((e2e_steps + 1, M, len(Ls), 15, 2), dtype=torch.float64,
+                             pin_memory=True)
+    e2e_buf = [torch.empty((M, len(Ls), 15, 2), dtype=torch.float64, device=dev)
+               for _ in range(2)]
 
-    def e2e_step():
-        lat.init_fields_batch(all_members, hnp[0], hnp[1], hnp[2])
-        lat.step(PERIOD)
-        return lat.subvolume_balance_batch(all_members, Ls, origins=boxes)
+    def e2e_run(nsteps, record):
+        for k in range(nsteps):
+            copy_stream.wait_event(consumed)  # the previous step's init has read dev_in
+            with torch.cuda.stream(copy_stream):
+                dev_in.copy_(host, non_blocking=True)
+            copied.record(copy_stream)
+            stream.wait_event(copied)
+            lat.init_fields_batch(all_members, dev_in[0], dev_in[1], dev_in[2])
+            consumed.record(stream)
+            lat.step(PERIOD)
+            if k > 0:  # step k-1's statistics to the host while step k runs
+                lat.diag_synchronize()
+                with torch.cuda.stream(copy_stream):
+                    record[k - 1].copy_(e2e_buf[(k - 1) % 2], non_blocking=True)
+            if k > 1:  # the read of step k-2's statistics has left e2e_buf[k % 2]
+                copy_stream.synchronize()
+            lat.subvolume_balance_async(all_members, Ls, origins=boxes, out=e2e_buf[k % 2])
+        lat.diag_synchronize()
+        with torch.cuda.stream(copy_stream):
+            record[nsteps - 1].copy_(e2e_buf[(nsteps - 1) % 2], non_blocking=True)
+        copy_stream.synchronize()
 
-    e2e_step()  # warm-up: the step graph of the storage parity after a restart
+    e2e_run(1, host_stats)  # warm-up: the step graph of the storage parity after a restart
     torch.cuda.synchronize()
-    times = []
-    for _ in range(e2e_steps):  # each step ends with the statistics on the host
-        te = time.perf_counter()
-        e2e_step()
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - te)
-    te = float(np.median(times))
+    te = time.perf_counter()
+    e2e_run(e2e_steps, host_stats)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te
+    assert np.all(np.isfinite(host_stats[:e2e_steps, :, :, 2:, 0].numpy()))
     if ws > 1:
         te = max_over_ranks(te)
-    e2e = {"value": ws * lu_per_gpu_step / te / 1e9, "unit": "GLUPS",
+    e2e = {"value": ws * lu_per_gpu_step * e2e_steps / te / 1e9, "unit": "GLUPS",
            "h2d_bytes_per_step": int(M * 3 * n * n * 8),
            "d2h_bytes_per_step": int(M * len(Ls) * 30 * 8),
-           "note": "init from pinned host fields + 200 steps + balance stats to host, "
-                   "per step, wall clock, median of %d steps (%.1f-%.1f ms)"
-                   % (e2e_steps, 1e3 * min(times), 1e3 * max(times))}
+           "note": "per step: pinned host fields of all members uploaded (copy stream) and "
+                   "initialised through lbm_init_fields_batch, 200 steps, Table 1 statistics "
+                   "to pinned host memory; step k's upload and step k-1's statistics "
+                   "overlap step k; wall clock over %d steps including pipeline fill and "
+                   "drain" % e2e_steps}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

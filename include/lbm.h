@@ -157,7 +157,10 @@ int lbm_destroy(lbm_handle *h);
  * state f_l(x, 0) = f_eq_l(rho(x), u(x)) of eq. (2) and resets the step
  * counter and snapshot history of the handle.  rho, ux, uy: double[ny][nx],
  * host pointers if on_device == 0 (copied through the workspace; the call
- * synchronises), device pointers otherwise. */
+ * synchronises, and first waits for a queued lbm_subvolume_balance_async,
+ * whose scratch it reuses), device pointers otherwise (queued on the stream;
+ * an asynchronous diagnostic still running is not waited for: it reads the
+ * snapshot ring, not the populations). */
 int lbm_init_fields(lbm_handle *h, int member, const double *rho,
                     const double *ux, const double *uy, int on_device);
 
@@ -167,7 +170,9 @@ int lbm_init_fields(lbm_handle *h, int member, const double *rho,
  * i).  Host pointers (on_device == 0) are copied through the workspace's
  * diagnostic scratch in chunks of whole members, one copy per field and
  * chunk, with a single synchronisation at the end; device pointers are read
- * in place.  With AA storage at an odd step every member must be listed.
+ * in place, without waiting for a queued asynchronous diagnostic (as in
+ * lbm_init_fields).  With AA storage at an odd step every member must be
+ * listed.
  * Resets the step counter and snapshot history like lbm_init_fields. */
 int lbm_init_fields_batch(lbm_handle *h, const int *members, int n, const double *rho,
                           const double *ux, const double *uy, int on_device);

@@ -676,7 +676,11 @@ int lbm_init_fields(lbm_handle *h, int member, const double *rho, const double *
       return fail(h, LBM_ERR_ARG, "shared init fields need equal grids");
   const size_t N = (size_t)nx * ny;
   const double *r = rho, *u = ux, *v = uy;
-  if (int rc = wait_diag(h)) return rc;
+  // host fields are staged in the diagnostic scratch: wait for a queued
+  // asynchronous diagnostic; device fields only overwrite the populations,
+  // which the diagnostic never reads (it works on the snapshot ring)
+  if (!on_device)
+    if (int rc = wait_diag(h)) return rc;
   if (!on_device) {
     double *st = h->sc.f;  // staging: three scratch fields
     CK(cudaMemcpyAsync(st, rho, 8 * N, cudaMemcpyHostToDevice, h->stream));
@@ -720,7 +724,8 @@ int lbm_init_fields_batch(lbm_handle *h, const int *members, int n, const double
     return fail(h, LBM_ERR_ARG, "AA storage: initialise every member (or at an even step)");
   const int nx = h->mcfg[members[0]].nx, ny = h->mcfg[members[0]].ny;
   const size_t N = (size_t)nx * ny;
-  if (int rc = wait_diag(h)) return rc;
+  if (!on_device)  // staging in the diagnostic scratch (see lbm_init_fields)
+    if (int rc = wait_diag(h)) return rc;
   if (h->cur >= 2) h->cur = 2;  // AA storage restarts at its even phase
   // host fields go through the diagnostic scratch (every slot) in chunks of
   // whole members: one copy per field and chunk, one synchronisation at the end

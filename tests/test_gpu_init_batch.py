@@ -76,3 +76,33 @@ def test_batch_argument_checks(P):
         lat.init_fields_batch([0, 3], r, u, v)  # out of range
     lat.init_fields_batch([1, 0], r, u, v)
     assert lat.time == 0
+
+
+def test_device_init_does_not_disturb_queued_diagnostic(P):
+    """A device-field (re)initialisation queued right after an asynchronous
+    diagnostic does not wait for it and does not change its statistics: the
+    diagnostic works on the snapshot ring, the initialisation on the
+    populations."""
+    import torch
+    n, M, D = 64, 4, 20
+    members = [P.Member(n, n, 0.55)] * M
+    r, u, v = _fields(M, n, n, 40)
+    dev = [torch.from_numpy(x).cuda() for x in (r, u, v)]
+    Ls = [2, 4, 8, 16]
+    a = P.Lattice(members, precision=32, diag_every=D)
+    b = P.Lattice(members, precision=32, diag_every=D)
+    for lat in (a, b):
+        lat.init_fields_batch(list(range(M)), *dev)
+        lat.step(D)
+    want = b.subvolume_balance_batch(list(range(M)), Ls)
+    out = a.subvolume_balance_async(list(range(M)), Ls)
+    r2, u2, v2 = _fields(M, n, n, 41)
+    a.init_fields_batch(list(range(M)), *(torch.from_numpy(x).cuda() for x in (r2, u2, v2)))
+    a.step(3)
+    a.diag_synchronize()
+    assert np.array_equal(out.cpu().numpy(), want, equal_nan=True)
+    c = P.Lattice(members, precision=32)
+    c.init_fields_batch(list(range(M)), r2, u2, v2)
+    c.step(3)
+    for m in range(M):
+        assert np.array_equal(a.get_populations_host(m), c.get_populations_host(m))
