@@ -353,6 +353,53 @@ __device__ __forceinline__ Levels<T, true> levels_pairs(const DiagJob &J, size_t
   return v;
 }
 
+// The 15 pointwise fields of pass 0 of one cell, in the order of kPrepField.
+template <typename T>
+struct PrepOut {
+  T v[15];
+};
+__device__ constexpr int kPrepField[15] = {U0X, U0Y, DU01X, DU01Y, DU12X, DU12Y, DRHO, R0, FXR,
+                                           FYR, A1, A2, T0 + 0, T0 + 3, T0 + 12};
+
+// Pass 0 arithmetic of one cell from its levels, alpha, the external force
+// at level n and the force's changes between levels (see k_prep).
+template <typename T, bool PAIRS>
+__device__ __forceinline__ PrepOut<T> prep_point(const Levels<T, PAIRS> &L, T a, T fex, T fey,
+                                                 T dfx01, T dfy01, T dfx12, T dfy12) {
+  const T ca = T(1) - T(0.5) * a;
+  const T Fx = fex - a * L.jx0, Fy = fey - a * L.jy0;
+  const T u0 = (L.jx0 + T(0.5) * Fx) / L.r0, v0 = (L.jy0 + T(0.5) * Fy) / L.r0;
+  // m^n - m^{n-1} = (1 - alpha/2)(j^n - j^{n-1}) + (F_ext^n - F_ext^{n-1})/2
+  const T du01 = (ca * L.djx01 + T(0.5) * dfx01 - u0 * L.dr01) / L.r1;
+  const T dv01 = (ca * L.djy01 + T(0.5) * dfy01 - v0 * L.dr01) / L.r1;
+  const T u1 = u0 - du01, v1 = v0 - dv01;
+  const T du12 = (ca * L.djx12 + T(0.5) * dfx12 - u1 * L.dr12) / L.r2;
+  const T dv12 = (ca * L.djy12 + T(0.5) * dfy12 - v1 * L.dr12) / L.r2;
+  const T q0 = u0 * u0 + v0 * v0, q1 = u1 * u1 + v1 * v1;
+  const T dE01 = T(0.5) * (L.dr01 * q0 +
+                           L.r1 * (du01 * (T(2) * u0 - du01) + dv01 * (T(2) * v0 - dv01)));
+  const T dE12 = T(0.5) * (L.dr12 * q1 +
+                           L.r2 * (du12 * (T(2) * u1 - du12) + dv12 * (T(2) * v1 - dv12)));
+  const T E0 = T(0.5) * L.r0 * q0;
+  PrepOut<T> o;
+  o.v[0] = u0;
+  o.v[1] = v0;
+  o.v[2] = du01;
+  o.v[3] = dv01;
+  o.v[4] = du12;
+  o.v[5] = dv12;
+  o.v[6] = L.drho;
+  o.v[7] = L.r0;
+  o.v[8] = Fx / L.r0;
+  o.v[9] = Fy / L.r0;
+  o.v[10] = E0 * u0;
+  o.v[11] = E0 * v0;
+  o.v[12] = T(0.5) * (T(3) * dE01 - dE12);  // LHS^E
+  o.v[13] = u0 * Fx + v0 * Fy;               // RHS^{E,3} = u . F
+  o.v[14] = q0;                              // |u|^2
+  return o;
+}
+
 // Pass 0 (pointwise).  u = (j + F/2)/rho with F = F_ext - alpha j, i.e.
 // rho u = m = (1 - alpha/2) j + F_ext/2.  Differences between levels:
 // m^0 - m^1 = (1 - alpha/2)(j^0 - j^1), and
@@ -393,43 +440,82 @@ __global__ void __launch_bounds__(256) k_prep(const DiagJob *__restrict__ jobs) 
       fex = (T)g.fxt[y];
       fey = (T)g.fyt[x];
     }
-    const T ca = T(1) - T(0.5) * a;
-    const T Fx = fex - a * L.jx0, Fy = fey - a * L.jy0;
-    const T u0 = (L.jx0 + T(0.5) * Fx) / L.r0, v0 = (L.jy0 + T(0.5) * Fy) / L.r0;
-    // m^n - m^{n-1} = (1 - alpha/2)(j^n - j^{n-1}) + (F_ext^n - F_ext^{n-1})/2
-    const T du01 = (ca * L.djx01 + T(0.5) * dfx01 - u0 * L.dr01) / L.r1;
-    const T dv01 = (ca * L.djy01 + T(0.5) * dfy01 - v0 * L.dr01) / L.r1;
-    const T u1 = u0 - du01, v1 = v0 - dv01;
-    const T du12 = (ca * L.djx12 + T(0.5) * dfx12 - u1 * L.dr12) / L.r2;
-    const T dv12 = (ca * L.djy12 + T(0.5) * dfy12 - v1 * L.dr12) / L.r2;
-    const T q0 = u0 * u0 + v0 * v0, q1 = u1 * u1 + v1 * v1;
-    const T dE01 = T(0.5) * (L.dr01 * q0 +
-                             L.r1 * (du01 * (T(2) * u0 - du01) + dv01 * (T(2) * v0 - dv01)));
-    const T dE12 = T(0.5) * (L.dr12 * q1 +
-                             L.r2 * (du12 * (T(2) * u1 - du12) + dv12 * (T(2) * v1 - dv12)));
-    const T E0 = T(0.5) * L.r0 * q0;
-    lhs = T(0.5) * (T(3) * dE01 - dE12);  // LHS^E
-    uf = u0 * Fx + v0 * Fy;               // RHS^{E,3} = u . F
-    uu = q0;
-    fld<T>(base, U0X, N)[c] = u0;
-    fld<T>(base, U0Y, N)[c] = v0;
-    fld<T>(base, DU01X, N)[c] = du01;
-    fld<T>(base, DU01Y, N)[c] = dv01;
-    fld<T>(base, DU12X, N)[c] = du12;
-    fld<T>(base, DU12Y, N)[c] = dv12;
-    fld<T>(base, DRHO, N)[c] = L.drho;
-    fld<T>(base, R0, N)[c] = L.r0;
-    fld<T>(base, FXR, N)[c] = Fx / L.r0;
-    fld<T>(base, FYR, N)[c] = Fy / L.r0;
-    fld<T>(base, A1, N)[c] = E0 * u0;
-    fld<T>(base, A2, N)[c] = E0 * v0;
-    fld<T>(base, T0 + 0, N)[c] = lhs;
-    fld<T>(base, T0 + 3, N)[c] = uf;
-    fld<T>(base, T0 + 12, N)[c] = uu;
+    const PrepOut<T> o = prep_point<T, PAIRS>(L, a, fex, fey, dfx01, dfy01, dfx12, dfy12);
+    lhs = o.v[12];
+    uf = o.v[13];
+    uu = o.v[14];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) fld<T>(base, kPrepField[k], N)[c] = o.v[k];
   }
   const T mv[3] = {lhs, uf, uu};
   const int mf[3] = {0, 3, 12};
   block_absmax<T, 3>(mv, mf, J, blk, nblk);
+}
+
+// Pass 0 for FP32 pair snapshots and force kinds 0/1 with two consecutive
+// cells per thread (nx % 4 == 0): 18 eight-byte loads of the level pairs and
+// 15 eight-byte stores per thread, the same per-cell arithmetic as k_prep.
+// CTA (32, 8) covers 64 x 8 cells, the cells of the one-cell CTAs 2 bx and
+// 2 bx + 1: maxima in slot 2 bx, zero in 2 bx + 1.
+__global__ void __launch_bounds__(256) k_prep2(const DiagJob *__restrict__ jobs) {
+  const DiagJob &J = jobs[blockIdx.z];
+  if ((int)(blockIdx.x * 64) >= J.nx || (int)(blockIdx.y * 8) >= J.ny) return;
+  const int nx = J.nx, ny = J.ny;
+  const int x = blockIdx.x * 64 + 2 * threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  const bool valid = x < nx && y < ny;
+  const size_t N = (size_t)nx * ny, c = (size_t)y * nx + x;
+  double *base = J.base;
+  const int nbx = (nx + 31) / 32, nblk = nbx * ((ny + 7) / 8);
+  const int blk = blockIdx.y * nbx + 2 * blockIdx.x;
+  float m0 = 0.f, m3 = 0.f, m12 = 0.f;
+  if (valid) {
+    const float *p[3] = {reinterpret_cast<const float *>(J.s0),
+                         reinterpret_cast<const float *>(J.s1),
+                         reinterpret_cast<const float *>(J.s2)};
+    float2 hi[3][3], lo[3][3];  // [level][moment], two cells
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        hi[k][q] = __ldg(reinterpret_cast<const float2 *>(p[k] + (size_t)(2 * q) * N + c));
+        lo[k][q] = __ldg(reinterpret_cast<const float2 *>(p[k] + (size_t)(2 * q + 1) * N + c));
+      }
+    const float fex = J.fxt_f[y], fey2[2] = {J.fyt_f[x], J.fyt_f[x + 1]};
+    const float rho0 = J.rho_ref_f, a = J.alpha_f;
+    PrepOut<float> o[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      auto h = [&](int k, int q) { return i ? hi[k][q].y : hi[k][q].x; };
+      auto l = [&](int k, int q) { return i ? lo[k][q].y : lo[k][q].x; };
+      auto dif = [&](int q, int a1, int b1) { return (h(a1, q) - h(b1, q)) + (l(a1, q) - l(b1, q)); };
+      Levels<float, true> L;  // as levels_pairs<float>
+      L.dr01 = dif(0, 0, 1);
+      L.dr12 = dif(0, 1, 2);
+      L.djx01 = dif(1, 0, 1);
+      L.djy01 = dif(2, 0, 1);
+      L.djx12 = dif(1, 1, 2);
+      L.djy12 = dif(2, 1, 2);
+      L.drho = h(0, 0) + l(0, 0);
+      L.r0 = rho0 + L.drho;
+      L.r1 = rho0 + (h(1, 0) + l(1, 0));
+      L.r2 = rho0 + (h(2, 0) + l(2, 0));
+      L.jx0 = h(0, 1) + l(0, 1);
+      L.jy0 = h(0, 2) + l(0, 2);
+      o[i] = prep_point<float, true>(L, a, fex, fey2[i], 0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 15; ++k)
+      *reinterpret_cast<float2 *>(fld<float>(base, kPrepField[k], N) + c) =
+          make_float2(o[0].v[k], o[1].v[k]);
+    m0 = fmaxf(fabsf(o[0].v[12]), fabsf(o[1].v[12]));
+    m3 = fmaxf(fabsf(o[0].v[13]), fabsf(o[1].v[13]));
+    m12 = fmaxf(fabsf(o[0].v[14]), fabsf(o[1].v[14]));
+  }
+  const float mv[3] = {m0, m3, m12};
+  const int mf[3] = {0, 3, 12};
+  block_absmax<float, 3>(mv, mf, J, blk, nblk);
+  if (threadIdx.y == 0 && threadIdx.x < 3 && (blk % nbx) + 1 < nbx)
+    max_part<float>(J)[(size_t)mf[threadIdx.x] * nblk + blk + 1] = 0u;
 }
 
 // Pass 1 (radius 4): vorticity w = D_x u_y - D_y u_x and its level
@@ -1484,13 +1570,17 @@ cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int 
   }
   const int nF = dist ? kNT : 12;  // |u|^2 gets a table only for Ma_V
   const dim3 cb(32, 8), cg((nx + 31) / 32, (ny + 7) / 8, G);
-  if (pairs)
-    k_prep<T, true><<<cg, cb, 0, s>>>(jobs);
-  else
-    k_prep<T, false><<<cg, cb, 0, s>>>(jobs);
   bool quad = sizeof(T) == 4;  // four cells per thread where every job allows
   for (int j = 0; j < G && quad; ++j)
     quad = jobs_host[j].nx % 4 == 0 && (reinterpret_cast<uintptr_t>(jobs_host[j].base) & 15) == 0;
+  bool pair2 = quad && pairs;  // two-cell pass 0: FP32 pairs, force kinds 0 and 1
+  for (int j = 0; j < G && pair2; ++j) pair2 = jobs_host[j].force_kind != 2;
+  if (pair2)
+    k_prep2<<<dim3((nx + 63) / 64, (ny + 7) / 8, G), cb, 0, s>>>(jobs);
+  else if (pairs)
+    k_prep<T, true><<<cg, cb, 0, s>>>(jobs);
+  else
+    k_prep<T, false><<<cg, cb, 0, s>>>(jobs);
   if (quad) {
     const dim3 cg4((nx + 127) / 128, (ny + 7) / 8, G);
     k_grad4<<<cg4, cb, 0, s>>>(jobs);
