@@ -1336,7 +1336,7 @@ __device__ void block_sum_store_pairs(MT (&v)[NQ], double *out0, double *out1) {
 // EXT also a CTA histogram in shared memory, added to the global one with
 // integer atomics (order-free, so deterministic).
 template <typename MT, bool PER_BOX, bool EXT>
-__global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs, int nF,
+__global__ void __launch_bounds__(256, 3) k_query(const DiagJob *__restrict__ jobs, int nF,
                                                const int *__restrict__ origins,
                                                double *per_box, DiagDist ext) {
   constexpr int NZ = EXT ? 2 : 1;
@@ -1398,12 +1398,34 @@ __global__ void __launch_bounds__(256) k_query(const DiagJob *__restrict__ jobs,
     const bool inside = x0 + L <= nx && y0 + L <= ny;
     MT lhs = 0, sum = 0, mx = 0;
     double *o = PER_BOX ? per_box + ((size_t)meta[8 * iL + 3] + b) * 15 : nullptr;
+    // a non-wrapping box of a 12-field table: the six values of a corner are
+    // 48 bytes at a 16-byte boundary, three vector loads per corner
+    unsigned long long vs[6];
+    const bool vec = inside && nF == 12 && nfield == 6;
+    if (vec) {
+      const long long *lo = S + ((size_t)y0 * rs + x0) * 12, *hi = lo + (size_t)L * rs * 12;
+      const size_t dx = (size_t)L * 12;
+      const longlong2 *c00 = reinterpret_cast<const longlong2 *>(lo);
+      const longlong2 *c10 = reinterpret_cast<const longlong2 *>(lo + dx);
+      const longlong2 *c01 = reinterpret_cast<const longlong2 *>(hi);
+      const longlong2 *c11 = reinterpret_cast<const longlong2 *>(hi + dx);
+#pragma unroll
+      for (int h = 0; h < 3; ++h) {
+        const longlong2 a00 = c00[h], a10 = c10[h], a01 = c01[h], a11 = c11[h];
+        vs[2 * h] = (unsigned long long)a11.x - (unsigned long long)a01.x -
+                    (unsigned long long)a10.x + (unsigned long long)a00.x;
+        vs[2 * h + 1] = (unsigned long long)a11.y - (unsigned long long)a01.y -
+                        (unsigned long long)a10.y + (unsigned long long)a00.y;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       if (j >= nfield) break;
       const long long *Sk = S + j;
       unsigned long long bs;
-      if (inside) {  // no periodic wrap: four direct corner loads
+      if (vec) {
+        bs = vs[j];
+      } else if (inside) {  // no periodic wrap: four direct corner loads
         const long long *lo = Sk + ((size_t)y0 * rs + x0) * nF, *hi = lo + (size_t)L * rs * nF;
         const size_t dx = (size_t)L * nF;
         bs = (unsigned long long)hi[dx] - (unsigned long long)hi[0] -
