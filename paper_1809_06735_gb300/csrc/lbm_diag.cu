@@ -808,7 +808,7 @@ __global__ void __launch_bounds__(256, 2) k_grad4(const DiagJob *__restrict__ jo
   block_absmax4<5>(mv, mf, J, blk, nblk, nbx);
 }
 
-__global__ void __launch_bounds__(256) k_flux4(const DiagJob *__restrict__ jobs) {
+__global__ void __launch_bounds__(256, 3) k_flux4(const DiagJob *__restrict__ jobs) {
   JOB_CELLS4;
   float m1 = 0, m5 = 0, m7 = 0, m10 = 0;
   if (valid) {
