@@ -154,9 +154,10 @@ __global__ void __launch_bounds__(128) k3_step_vec(const M3 *__restrict__ ms, in
     while (it >= ms[m].item0 + ms[m].items) ++m;  // items ascend with the member
     const M3 &M = ms[m];
     const int nx = M.nx, ny = M.ny, nz = M.nz;
-    const long long li = it - M.item0;
-    const int gx = (nx + 127) / 128, gy = (ny + 3) / 4;
-    const int xs = (int)(li % gx), yg = (int)((li / gx) % gy), z = (int)(li / ((long long)gx * gy));
+    const unsigned li = (unsigned)(it - M.item0);  // < 2^28 items per member
+    const unsigned gx = (unsigned)(nx + 127) / 128u, gy = (unsigned)(ny + 3) / 4u;
+    const unsigned lx = li / gx;
+    const int xs = (int)(li - lx * gx), yg = (int)(lx % gy), z = (int)(lx / gy);
     const int x = xs * 128 + 4 * lane, y = yg * 4 + threadIdx.y;
     if (y >= ny) continue;  // whole warps
     const bool active = x < nx;
