@@ -146,15 +146,37 @@ __global__ void __launch_bounds__(256) k3_step(const M3 *__restrict__ ms, int me
 // (y - c_y, z - c_z); the -+1 x-shift is a warp shuffle with one scalar
 // load at the segment's edges (the periodic wrap included), as in 2D.
 template <int Q>
-__global__ void __launch_bounds__(128) k3_step_vec(const M3 *__restrict__ ms, int n_members,
+__global__ void __launch_bounds__(128, Q == 19 ? 4 : 3) k3_step_vec(const M3 *__restrict__ ms, int n_members,
                                                    long long n_items, int cur) {
   const int lane = threadIdx.x;
-  int m = 0;
+  // the current member's parameters, reloaded only when the items move on
+  // to the next member (items ascend with the member)
+  int m = -1, nx = 0, ny = 0, nz = 0;
+  long long item0 = 0, item1 = 0;
+  size_t N = 0;
+  const float *src = nullptr, *tab = nullptr;
+  float *dst = nullptr;
+  float rho0 = 0.f, om = 0.f, alpha = 0.f;
   for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
-    while (it >= ms[m].item0 + ms[m].items) ++m;  // items ascend with the member
-    const M3 &M = ms[m];
-    const int nx = M.nx, ny = M.ny, nz = M.nz;
-    const unsigned li = (unsigned)(it - M.item0);  // < 2^28 items per member
+    if (it >= item1) {
+      do {
+        ++m;
+      } while (it >= ms[m].item0 + ms[m].items);
+      const M3 &M = ms[m];
+      nx = M.nx;
+      ny = M.ny;
+      nz = M.nz;
+      item0 = M.item0;
+      item1 = M.item0 + M.items;
+      N = M.N;
+      src = static_cast<const float *>(M.pop[cur]);
+      dst = static_cast<float *>(M.pop[cur ^ 1]);
+      tab = static_cast<const float *>(M.ftab);
+      rho0 = M.rho0_f;
+      om = M.omega_f;
+      alpha = M.alpha_f;
+    }
+    const unsigned li = (unsigned)(it - item0);  // < 2^28 items per member
     const unsigned gx = (unsigned)(nx + 127) / 128u, gy = (unsigned)(ny + 3) / 4u;
     const unsigned lx = li / gx;
     const int xs = (int)(li - lx * gx), yg = (int)(lx % gy), z = (int)(lx / gy);
@@ -165,10 +187,8 @@ __global__ void __launch_bounds__(128) k3_step_vec(const M3 *__restrict__ ms, in
     const int xprev = x == 0 ? nx - 1 : x - 1, xnext = x + 4 >= nx ? 0 : x + 4;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
     const int zm = z == 0 ? nz - 1 : z - 1, zp = z + 1 == nz ? 0 : z + 1;
-    const size_t N = M.N, rowy[3] = {(size_t)yp * nx, (size_t)y * nx, (size_t)ym * nx};
+    const size_t rowy[3] = {(size_t)yp * nx, (size_t)y * nx, (size_t)ym * nx};
     const size_t slab[3] = {(size_t)zp * ny * nx, (size_t)z * ny * nx, (size_t)zm * ny * nx};
-    const float *src = static_cast<const float *>(M.pop[cur]);
-    float *dst = static_cast<float *>(M.pop[cur ^ 1]);
     float v[Q][4];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
@@ -189,7 +209,6 @@ __global__ void __launch_bounds__(128) k3_step_vec(const M3 *__restrict__ ms, in
       }
     }
     if (!active) continue;
-    const float *tab = static_cast<const float *>(M.ftab);
     const float fx = tab[y], fy = tab[ny + z];
     const size_t c = slab[1] + rowy[1] + x;
 #pragma unroll
@@ -197,7 +216,7 @@ __global__ void __launch_bounds__(128) k3_step_vec(const M3 *__restrict__ ms, in
       float g[Q];
 #pragma unroll
       for (int l = 0; l < Q; ++l) g[l] = v[l][i];
-      collide3<float, Q>(g, M.rho0_f, M.omega_f, fx, fy, tab[ny + nz + x + i], M.alpha_f);
+      collide3<float, Q>(g, rho0, om, fx, fy, tab[ny + nz + x + i], alpha);
 #pragma unroll
       for (int l = 0; l < Q; ++l) v[l][i] = g[l];
     }
