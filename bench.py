@@ -288,7 +288,10 @@ def collision_models_leg(P, stream, dev, peak):
         lu = M * n * n * steps
         gbs = BYTES_PER_LU_F32 * lu / secs / 1e9
         out[name] = {"glups": lu / secs / 1e9, "achieved_gbs": gbs, "frac": gbs / peak,
-                     "kernel": "k_step_scalar<float>" if coll == 3 else "k_step_f32_vec (extended)"}
+                     "kernel": "k_step_scalar<float>" if coll == 3 else "k_step_f32_vec (extended)",
+                     # the entropic collision's per-cell root finding keeps the issue
+                     # slots busy (ALU-bound); frac is then only its share of HBM
+                     "bound": "alu" if coll == 3 else "hbm"}
         del lat
     return out
 
