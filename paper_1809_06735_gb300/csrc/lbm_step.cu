@@ -155,16 +155,34 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
   } else {
     T a = fmin(T(2), T(0.5) * (lo + hi));
     for (int it = 0; it < 30; ++it) {
-      T scale;
-      const T g = entropy_gap<T>(f, y, S2, a, &scale);
+      // g(a) and g'(a) = sum Delta ln(1 + a y) - S2 share ln(1 + a y): one
+      // log1p per population (phi as entropy_gap evaluates it)
+      T s = T(0), dg = -S2;
+#pragma unroll
+      for (int l = 0; l < kQ; ++l) {
+        const T z = a * y[l], lz = log1p(z);
+        T ph;
+        if (fabs(z) < T(0.1)) {
+          ph = T(0);
+          T p = z * z;
+#pragma unroll
+          for (int k = 2; k < 10; ++k) {
+            ph += ((k & 1) ? -p : p) * T(1.0 / (k * (k - 1)));
+            p *= z;
+          }
+        } else {
+          ph = (T(1) + z) * lz - z;
+        }
+        s += f[l] * ph;
+        dg += d[l] * lz;
+      }
+      const T scale = s + a * fabs(S2);
+      const T g = s - a * S2;
       const bool conv = fabs(g) <= T(1e-6) * scale;
       if (g < T(0))
         lo = a;
       else
         hi = a;
-      T dg = -S2;
-#pragma unroll
-      for (int l = 0; l < kQ; ++l) dg += d[l] * log1p(a * y[l]);
       T an = a - g / dg;
       const bool inside = an > lo && an < hi;
       if (conv) return inside ? an : a;
