@@ -1045,7 +1045,7 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
       CK(lbm::diag_balance(jobs.data() + j0, jobs_dev + j0, G, h->diag_precision,
                            h->precision == 32, orig_dev, stats_dev, per_box_out,
                            dist ? &dd : nullptr, s));
-      h->launches += 10;  // 4 term passes, scales, 2 scan passes, constants, query, statistics
+      h->launches += 10;  // 4 term passes, scales, strip sums, table builder, constants, query, statistics
     }
   }
   if (async) {

@@ -6,8 +6,9 @@
 //
 // Precision.  Inputs are moment snapshots (rho, j_x, j_y): FP64 [3][ny*nx],
 // or for FP32 storage the compensated FP32 pairs (hi, lo) of rho - rho0,
-// j_x, j_y, [3][2][ny*nx], whose sums are the FP64 moments.  The term fields are computed in T = double (FP64 handles, or
-// on request) or T = float (FP32 handles): GB300 executes FP64 at a small
+// j_x, j_y, [3][2][ny*nx], whose sums are the FP64 moments.  The term
+// fields are computed in T = double (FP64 handles, or on request) or
+// T = float (FP32 handles): GB300 executes FP64 at a small
 // fraction of its FP32 rate, and the FP32 variant keeps its accuracy by
 // forming every cancelling quantity from FP64 differences first -- the time
 // differences u^n - u^{n-1} (so E and Omega differences, hence the eq. (17)
@@ -24,14 +25,15 @@
 // final statistic is FP64 and block-deterministic.
 //
 // Batching.  The balance diagnostic of a group of members runs as ten
-// launches in all (four term passes, scale exponents, two scans, query
-// constants, box query, statistics), blockIdx.z (or the CTA index of the
+// launches in all (four term passes, scale exponents, the strip sums and
+// the table builder, query constants, box query, statistics), blockIdx.z
+// (or the CTA index of the
 // per-job kernels) selecting the member; each member has its own field slot
 // and partials slot.
 //
 // Field slot (doubles of N = nx*ny cells): slots 0..2 a temporary snapshot,
 // slots 3.. the term-stage fields (each slot holds N values of T), then the
-// 12 int64 tables of (nx+1)(ny+1) entries.
+// int64 tables of (nx+1)(ny+1) records of 12 (13) interleaved fields.
 #include <algorithm>
 #include <cstdint>
 #include <cmath>
