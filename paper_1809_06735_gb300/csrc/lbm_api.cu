@@ -290,6 +290,12 @@ int build_tiles(lbm_handle *h) {
     for (int y0 = 0; y0 < c.ny; y0 += rows)
       for (int x0 = 0; x0 < c.nx; x0 += kTileW) tiles.push_back(Tile{m, x0, y0, 0});
   }
+  // With the paper forcing every step first projects the state member by
+  // member in ascending order; the step then takes the members in descending
+  // order, starting on those whose populations the projection read last
+  // (still in L2), and leaves the lowest members freshly written for the
+  // next projection.
+  if (h->has_kind2) std::reverse(tiles.begin(), tiles.end());
   h->ntiles = (int)tiles.size();
   if (!tiles.empty())
     CK(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(),
