@@ -324,12 +324,20 @@ int project(lbm_handle *h, cudaStream_t s, int cur, int slot) {
   return LBM_OK;
 }
 
+// Steps alternate the direction in which they walk the tile table, so each
+// one starts on the tiles the previous one wrote last (still in L2); with
+// the paper forcing the projection walks the members in ascending order and
+// the step always in descending order (the table is built reversed).
+int tile_flip(const lbm_handle *h, int cur) { return h->has_kind2 ? 0 : (cur & 1); }
+
 // One time step of every member on stream s (kind-2 members first get the
 // damping of the state being collided).
 int launch_one_step(lbm_handle *h, cudaStream_t s, int cur) {
   if (h->has_kind2)
     if (int rc = project(h, s, cur, -1)) return rc;
-  if (h->ntiles > 0) CK(lbm::launch_step_f32_vec(h->d_members, h->d_tiles, h->ntiles, cur, h->lc, s));
+  if (h->ntiles > 0)
+    CK(lbm::launch_step_f32_vec(h->d_members, h->d_tiles, h->ntiles, cur, tile_flip(h, cur), h->lc,
+                                s));
   for (int m : h->scalar_members)
     CK(lbm::launch_step_scalar(h->precision, h->d_members, m, h->mcfg[m].nx, h->mcfg[m].ny, cur, s));
   return LBM_OK;
@@ -785,8 +793,8 @@ bool fused_snapshots(const lbm_handle *h) {
 int step_recording(lbm_handle *h) {
   if (int rc = wait_diag(h)) return rc;
   const int slot = (int)(h->t % 3);
-  CK(lbm::launch_step_f32_vec_snap(h->d_members, h->d_tiles, h->ntiles, h->cur, h->lc, slot,
-                                   h->stream));
+  CK(lbm::launch_step_f32_vec_snap(h->d_members, h->d_tiles, h->ntiles, h->cur,
+                                   tile_flip(h, h->cur), h->lc, slot, h->stream));
   h->ring_time[slot] = h->t;
   h->launches += 1;
   h->cur ^= 1;

@@ -144,10 +144,12 @@ struct LaunchCfg {
                       // collision (the extended kernel variant)
 };
 
+// One step of every vector-kernel member (flip: tiles in reverse order).
 cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, int ntiles,
-                                int cur, const LaunchCfg &lc, cudaStream_t s);
+                                int state, int flip, const LaunchCfg &lc, cudaStream_t s);
 cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tiles, int ntiles,
-                                     int state, const LaunchCfg &lc, int slot, cudaStream_t s);
+                                     int state, int flip, const LaunchCfg &lc, int slot,
+                                     cudaStream_t s);
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member,
                                int nx, int ny, int cur, cudaStream_t s);
 // Member indices of one batched launch (kernel parameter).

@@ -406,10 +406,12 @@ __device__ __forceinline__ void paper_force4(const Member &M, int x, int y, floa
 template <int ROWS, int MODE, bool PF, bool SNAP = false>
 __global__ void __launch_bounds__(256, PF ? 3 : (SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
                                                       const Tile *__restrict__ tiles,
-                                                      int ntiles, int cur, int snap_slot) {
+                                                      int ntiles, int cur, int flip, int snap_slot) {
   const int lane = threadIdx.x;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const Tile tl = tiles[t];
+    // flip: the tiles in reverse order, so that a step starts where the
+    // previous one ended (those populations are still in L2)
+    const Tile tl = tiles[flip ? ntiles - 1 - t : t];
     const Member &M = members[tl.member];
     const int nx = M.nx, ny = M.ny, pitch = M.pitch;
     const size_t plane = M.plane;
@@ -575,33 +577,36 @@ __global__ void __launch_bounds__(256, PF ? 3 : (SNAP ? 2 : 1)) k_step_f32_vec(c
 
 template <int ROWS, bool PF, bool SNAP = false>
 static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int ntiles, int state,
-                            int grid, dim3 block, cudaStream_t s, int slot = -1) {
+                            int flip, int grid, dim3 block, cudaStream_t s, int slot = -1) {
   if (state < 2)
-    k_step_f32_vec<ROWS, 0, PF, SNAP><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state, slot);
+    k_step_f32_vec<ROWS, 0, PF, SNAP><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state,
+                                                             flip, slot);
   else if (state == 2)
-    k_step_f32_vec<ROWS, 1, PF, SNAP><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state, slot);
+    k_step_f32_vec<ROWS, 1, PF, SNAP><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state,
+                                                             flip, slot);
   else
-    k_step_f32_vec<ROWS, 2, PF, SNAP><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state, slot);
+    k_step_f32_vec<ROWS, 2, PF, SNAP><<<grid, block, 0, s>>>(d_members, d_tiles, ntiles, state,
+                                                             flip, slot);
 }
 
 template <int ROWS>
 static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int ntiles, int state,
-                            int grid, dim3 block, bool pf, cudaStream_t s) {
+                            int flip, int grid, dim3 block, bool pf, cudaStream_t s) {
   if (pf)
-    launch_vec_rows<ROWS, true>(d_members, d_tiles, ntiles, state, grid, block, s);
+    launch_vec_rows<ROWS, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
   else
-    launch_vec_rows<ROWS, false>(d_members, d_tiles, ntiles, state, grid, block, s);
+    launch_vec_rows<ROWS, false>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
 }
 
 cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, int ntiles,
-                                int state, const LaunchCfg &lc, cudaStream_t s) {
+                                int state, int flip, const LaunchCfg &lc, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   dim3 block(32, lc.block_warps_y);
   int grid = lc.grid_ctas > 0 ? (lc.grid_ctas < ntiles ? lc.grid_ctas : ntiles) : ntiles;
   switch (lc.rows_per_warp) {
-    case 1: launch_vec_rows<1>(d_members, d_tiles, ntiles, state, grid, block, lc.paper_force != 0, s); break;
-    case 2: launch_vec_rows<2>(d_members, d_tiles, ntiles, state, grid, block, lc.paper_force != 0, s); break;
-    case 4: launch_vec_rows<4>(d_members, d_tiles, ntiles, state, grid, block, lc.paper_force != 0, s); break;
+    case 1: launch_vec_rows<1>(d_members, d_tiles, ntiles, state, flip, grid, block, lc.paper_force != 0, s); break;
+    case 2: launch_vec_rows<2>(d_members, d_tiles, ntiles, state, flip, grid, block, lc.paper_force != 0, s); break;
+    case 4: launch_vec_rows<4>(d_members, d_tiles, ntiles, state, flip, grid, block, lc.paper_force != 0, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -610,14 +615,15 @@ cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, in
 // One step with the snapshot of the state it reads recorded into ring slot
 // `slot` (members without the paper forcing or a variable viscosity only).
 cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tiles, int ntiles,
-                                     int state, const LaunchCfg &lc, int slot, cudaStream_t s) {
+                                     int state, int flip, const LaunchCfg &lc, int slot,
+                                     cudaStream_t s) {
   if (ntiles <= 0 || lc.paper_force != 0 || slot < 0 || slot > 2) return cudaErrorInvalidValue;
   dim3 block(32, lc.block_warps_y);
   int grid = lc.grid_ctas > 0 ? (lc.grid_ctas < ntiles ? lc.grid_ctas : ntiles) : ntiles;
   switch (lc.rows_per_warp) {
-    case 1: launch_vec_rows<1, false, true>(d_members, d_tiles, ntiles, state, grid, block, s, slot); break;
-    case 2: launch_vec_rows<2, false, true>(d_members, d_tiles, ntiles, state, grid, block, s, slot); break;
-    case 4: launch_vec_rows<4, false, true>(d_members, d_tiles, ntiles, state, grid, block, s, slot); break;
+    case 1: launch_vec_rows<1, false, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s, slot); break;
+    case 2: launch_vec_rows<2, false, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s, slot); break;
+    case 4: launch_vec_rows<4, false, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s, slot); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
