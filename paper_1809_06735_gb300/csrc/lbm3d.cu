@@ -147,21 +147,22 @@ __global__ void __launch_bounds__(256) k3_step(const M3 *__restrict__ ms, int me
 // load at the segment's edges (the periodic wrap included), as in 2D.
 template <int Q>
 __global__ void __launch_bounds__(128, Q == 19 ? 4 : 3) k3_step_vec(const M3 *__restrict__ ms, int n_members,
-                                                   long long n_items, int cur) {
+                                                   long long n_items, int cur, int flip) {
   const int lane = threadIdx.x;
   // the current member's parameters, reloaded only when the items move on
-  // to the next member (items ascend with the member)
+  // to another member; flip walks the items in reverse order, so that a step
+  // starts where the previous one ended (those populations are still in L2)
   int m = -1, nx = 0, ny = 0, nz = 0;
   long long item0 = 0, item1 = 0;
   size_t N = 0;
   const float *src = nullptr, *tab = nullptr;
   float *dst = nullptr;
   float rho0 = 0.f, om = 0.f, alpha = 0.f;
-  for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
-    if (it >= item1) {
-      do {
-        ++m;
-      } while (it >= ms[m].item0 + ms[m].items);
+  for (long long t = blockIdx.x; t < n_items; t += gridDim.x) {
+    const long long it = flip ? n_items - 1 - t : t;
+    if (it < item0 || it >= item1) {
+      m = 0;
+      while (m + 1 < n_members && it >= ms[m].item0 + ms[m].items) ++m;
       const M3 &M = ms[m];
       nx = M.nx;
       ny = M.ny;
@@ -1110,9 +1111,11 @@ int lbm3d_step(lbm3d_handle *h, int nsteps) {
     if (h->vec_items > 0) {  // every FP32 member with nx % 4 == 0, one launch
       const int n = (int)h->mcfg.size();
       if (h->q == 27)
-        k3_step_vec<27><<<h->vec_grid, dim3(32, 4), 0, h->stream>>>(h->d_m, n, h->vec_items, h->cur);
+        k3_step_vec<27><<<h->vec_grid, dim3(32, 4), 0, h->stream>>>(h->d_m, n, h->vec_items, h->cur,
+                                                                    h->cur & 1);
       else
-        k3_step_vec<19><<<h->vec_grid, dim3(32, 4), 0, h->stream>>>(h->d_m, n, h->vec_items, h->cur);
+        k3_step_vec<19><<<h->vec_grid, dim3(32, 4), 0, h->stream>>>(h->d_m, n, h->vec_items, h->cur,
+                                                                    h->cur & 1);
     }
     for (int m = 0; m < (int)h->mcfg.size(); ++m)
       if (h->hm[m].items == 0)
