@@ -421,8 +421,11 @@ int record(lbm_handle *h) {
     nx = std::max(nx, c.nx);
     ny = std::max(ny, c.ny);
   }
+  // four cells per lane when every member is an FP32 vector-kernel member
+  // with a constant viscosity (no local viscosity to record)
+  const bool quad = h->precision == 32 && h->scalar_members.empty() && !h->has_vv;
   CK(lbm::launch_snapshot_ring(h->precision, h->d_members, (int)h->mcfg.size(), nx, ny, h->cur,
-                               slot, h->stream));
+                               slot, quad, h->stream));
   h->launches += 1;
   if (h->has_kind2) {  // the damping of this state, for the diagnostic
     if (int rc = project(h, h->stream, h->cur, slot)) return rc;

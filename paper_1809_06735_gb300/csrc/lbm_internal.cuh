@@ -177,7 +177,8 @@ cudaError_t launch_projection(int precision, const Member *d_members, int n_memb
                               cudaStream_t s);
 // The ring snapshot of every member in one launch (layout at Member::snap).
 cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_members,
-                                 int nx_max, int ny_max, int state, int slot, cudaStream_t s);
+                                 int nx_max, int ny_max, int state, int slot, bool quad,
+                                 cudaStream_t s);
 cudaError_t launch_snapshot(int precision, const Member *d_members, int member, int nx,
                             int ny, int cur, double *dst, cudaStream_t s);
 cudaError_t launch_status(int precision, const Member *d_members, int member, int nx,

@@ -1157,6 +1157,84 @@ __global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ mem
   project_finalize(M, nblk, slot, tid, lane, wid);
 }
 
+// The snapshot-ring entry of FP32 members with nx % 4 == 0 and a constant
+// viscosity, four cells per lane: CTA (32, 8), a warp per 128-cell row
+// segment, kSnap4Rows rows per thread 8 apart; the state pulled as in
+// k_step_f32_vec (MODE 0: double buffer `state`, 1: AA even, 2: AA odd) and
+// the same compensated pairs as k_snapshot_ring and the recording step.
+constexpr int kSnap4Rows = 4;
+template <int MODE>
+__global__ void __launch_bounds__(256) k_snapshot4(const Member *__restrict__ members, int state,
+                                                   int slot) {
+  const Member &M = members[blockIdx.z];
+  if ((int)(blockIdx.x * 128) >= M.nx || (int)(blockIdx.y * 8 * kSnap4Rows) >= M.ny) return;
+  const int nx = M.nx, ny = M.ny, pitch = M.pitch, lane = threadIdx.x;
+  const size_t plane = M.plane, N = (size_t)nx * ny;
+  const int x = blockIdx.x * 128 + 4 * lane;
+  const bool active = x < nx;
+  const bool last = active && (lane == 31 || x + 4 >= nx);
+  const int xprev = x == 0 ? nx - 1 : x - 1, xnext = x + 4 >= nx ? 0 : x + 4;
+  const float *src = static_cast<const float *>(MODE == 0 ? M.pop[state] : M.pop[0]);
+  float *ring = reinterpret_cast<float *>(M.snap) + (size_t)slot * 6 * N;
+#pragma unroll 1
+  for (int r = 0; r < kSnap4Rows; ++r) {
+    const int y = blockIdx.y * 8 * kSnap4Rows + r * 8 + threadIdx.y;
+    if (y >= ny) break;  // whole warps
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
+    float v[kQ][4];
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const int cxl = cx_of(l), cyl = cy_of(l);
+      if (MODE == 1) {  // own cell, own slot
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (active)
+          o = __ldg(reinterpret_cast<const float4 *>(src + (size_t)l * plane + (size_t)y * pitch + x));
+        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
+        continue;
+      }
+      const int sl = MODE == 2 ? opposite(l) : l;
+      const int ys = cyl == 0 ? y : (cyl > 0 ? ym : yp);  // from y - c_y
+      const float *row = src + (size_t)sl * plane + (size_t)ys * pitch;
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (active) o = __ldg(reinterpret_cast<const float4 *>(row + x));
+      if (cxl == 0) {
+        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
+      } else if (cxl > 0) {  // from x - 1
+        float prev = __shfl_up_sync(0xffffffffu, o.w, 1);
+        if (active && (lane == 0 || x == 0)) prev = __ldg(row + xprev);
+        v[l][0] = prev; v[l][1] = o.x; v[l][2] = o.y; v[l][3] = o.z;
+      } else {  // from x + 1
+        float next = __shfl_down_sync(0xffffffffu, o.x, 1);
+        if (last) next = __ldg(row + xnext);
+        v[l][0] = o.y; v[l][1] = o.z; v[l][2] = o.w; v[l][3] = next;
+      }
+    }
+    if (!active) continue;
+    float hs[3][4], ls[3][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int one[kQ] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+      const int sgn[6] = {1, 1, 1, -1, -1, -1};
+      float f[kQ];
+#pragma unroll
+      for (int l = 0; l < kQ; ++l) f[l] = v[l][c];
+      const float ax[6] = {f[1], f[5], f[8], f[3], f[6], f[7]};
+      const float ay[6] = {f[2], f[5], f[6], f[4], f[7], f[8]};
+      csum_pair(f, one, kQ, hs[0][c], ls[0][c]);
+      csum_pair(ax, sgn, 6, hs[1][c], ls[1][c]);
+      csum_pair(ay, sgn, 6, hs[2][c], ls[2][c]);
+    }
+    float *d = ring + (size_t)y * nx + x;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      __stcs(reinterpret_cast<float4 *>(d + (size_t)(2 * q) * N),
+             make_float4(hs[q][0], hs[q][1], hs[q][2], hs[q][3]));
+      __stcs(reinterpret_cast<float4 *>(d + (size_t)(2 * q + 1) * N),
+             make_float4(ls[q][0], ls[q][1], ls[q][2], ls[q][3]));
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_status(const Member *__restrict__ members, int member, int state) {
   const Member &M = members[member];
@@ -1225,7 +1303,20 @@ cudaError_t launch_snapshot(int precision, const Member *d_members, int member, 
 }
 
 cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_members,
-                                 int nx_max, int ny_max, int state, int slot, cudaStream_t s) {
+                                 int nx_max, int ny_max, int state, int slot, bool quad,
+                                 cudaStream_t s) {
+  if (quad && precision == 32) {  // four cells per lane
+    const dim3 g4((nx_max + 127) / 128, (ny_max + 8 * kSnap4Rows - 1) / (8 * kSnap4Rows),
+                  n_members);
+    const dim3 b4(32, 8);
+    if (state < 2)
+      k_snapshot4<0><<<g4, b4, 0, s>>>(d_members, state, slot);
+    else if (state == 2)
+      k_snapshot4<1><<<g4, b4, 0, s>>>(d_members, state, slot);
+    else
+      k_snapshot4<2><<<g4, b4, 0, s>>>(d_members, state, slot);
+    return cudaGetLastError();
+  }
   const dim3 b(64, 4);
   dim3 g = grid2d(nx_max, ny_max, b);
   g.z = n_members;
