@@ -1114,6 +1114,14 @@ __global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ mem
     if (!active) continue;
     const float cy = tr[4 * nx + y], sy = tr[4 * nx + ny + y];
     const float c2y = tr[4 * nx + 2 * ny + y], s2y = tr[4 * nx + 3 * ny + y];
+    // separable in x and y: the lane's sums of u (1, cos x, sin x, cos 2x,
+    // sin 2x) over its four cells, folded into the mode sums with the row's
+    // y factors (cos(x +- y) = cx cy -+ sx sy, sin(x +- y) = sx cy +- cx sy)
+    float R[2][5];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) R[k][q] = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       float rho = M.rho0_f, jx = 0.f, jy = 0.f;
@@ -1125,15 +1133,30 @@ __global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ mem
       }
       const float ir = 1.0f / rho;
       const float u[2] = {jx * ir, jy * ir};
-      const float cm[6] = {cx[i], cy, cx[i] * cy - sx[i] * sy, cx[i] * cy + sx[i] * sy, c2x[i], c2y};
-      const float sm[6] = {sx[i], sy, sx[i] * cy + cx[i] * sy, sx[i] * cy - cx[i] * sy, s2x[i], s2y};
 #pragma unroll
-      for (int k = 0; k < 2; ++k)
+      for (int k = 0; k < 2; ++k) {
+        R[k][0] += u[k];
+        R[k][1] += u[k] * cx[i];
+        R[k][2] += u[k] * sx[i];
+        R[k][3] += u[k] * c2x[i];
+        R[k][4] += u[k] * s2x[i];
+      }
+    }
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-          acc[12 * k + 2 * m] += u[k] * cm[m];
-          acc[12 * k + 2 * m + 1] += u[k] * sm[m];
-        }
+    for (int k = 0; k < 2; ++k) {
+      float *a = acc + 12 * k;
+      a[0] += R[k][1];                       // cos x
+      a[1] += R[k][2];                       // sin x
+      a[2] += R[k][0] * cy;                  // cos y
+      a[3] += R[k][0] * sy;                  // sin y
+      a[4] += R[k][1] * cy - R[k][2] * sy;   // cos(x + y)
+      a[5] += R[k][2] * cy + R[k][1] * sy;   // sin(x + y)
+      a[6] += R[k][1] * cy + R[k][2] * sy;   // cos(x - y)
+      a[7] += R[k][2] * cy - R[k][1] * sy;   // sin(x - y)
+      a[8] += R[k][3];                       // cos 2x
+      a[9] += R[k][4];                       // sin 2x
+      a[10] += R[k][0] * c2y;                // cos 2y
+      a[11] += R[k][0] * s2y;                // sin 2y
     }
   }
   __shared__ float sh[kDamp][8];
