@@ -26,6 +26,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -430,6 +431,10 @@ def run_ours(args):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
+    # no cyclic garbage collection inside a timed region: a handle destroyed
+    # there (its graphs and streams) would stall the queued work
+    gc.collect()
+    gc.disable()
     clocks.start()
     launches0 = lat.launch_count
     t0, t1 = ev(), ev()
@@ -440,6 +445,7 @@ def run_ours(args):
     lat.diag_synchronize()  # the last period's diagnostic is part of the job
     t1.record(stream)
     torch.cuda.synchronize()
+    gc.enable()
     stats = stats.cpu().numpy()
     clk = clocks.stop()
     launches = lat.launch_count - launches0
@@ -525,13 +531,16 @@ def run_ours(args):
 
     e2e_run(1, host_stats)  # warm-up: the step graph of the storage parity after a restart
     runs = []
+    gc.collect()
+    gc.disable()  # as in the timed steps above
     for _ in range(3):  # median of three pipelined runs: host-side jitter is one-sided
         torch.cuda.synchronize()
         te = time.perf_counter()
         e2e_run(e2e_steps, host_stats)
         torch.cuda.synchronize()
         runs.append(time.perf_counter() - te)
-        assert np.all(np.isfinite(host_stats[:e2e_steps, :, :, 2:, 0].numpy()))
+    gc.enable()
+    assert np.all(np.isfinite(host_stats[:e2e_steps, :, :, 2:, 0].numpy()))
     te = float(np.median(runs))
     if ws > 1:
         te = max_over_ranks(te)
