@@ -498,7 +498,7 @@ def run_ours(args):
     # production caller would: step k's upload (copy stream) and step k-1's
     # statistics read overlap step k's stream-collide; the diagnostic runs
     # on the library's diagnostic stream.
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, args.steps)
     dev_in = torch.empty((3, M, n, n), dtype=torch.float64, device=dev)
     copy_stream = torch.cuda.Stream(device=dev)
     copied, consumed = torch.cuda.Event(), torch.cuda.Event()
@@ -507,12 +507,18 @@ def run_ours(args):
     e2e_buf = [torch.empty((M, len(Ls), 15, 2), dtype=torch.float64, device=dev)
                for _ in range(2)]
 
+    up0, up1 = ev(), ev()  # the first upload: the pipeline fill, not hidden
+
     def e2e_run(nsteps, record):
         for k in range(nsteps):
             copy_stream.wait_event(consumed)  # the previous step's init has read dev_in
+            if k == 0:
+                up0.record(copy_stream)
             with torch.cuda.stream(copy_stream):
                 dev_in.copy_(host, non_blocking=True)
             copied.record(copy_stream)
+            if k == 0:
+                up1.record(copy_stream)
             stream.wait_event(copied)
             lat.init_fields_batch(all_members, dev_in[0], dev_in[1], dev_in[2])
             consumed.record(stream)
@@ -530,7 +536,7 @@ def run_ours(args):
         copy_stream.synchronize()
 
     e2e_run(1, host_stats)  # warm-up: the step graph of the storage parity after a restart
-    runs = []
+    runs, uploads = [], []
     gc.collect()
     gc.disable()  # as in the timed steps above
     for _ in range(3):  # median of three pipelined runs: host-side jitter is one-sided
@@ -539,6 +545,7 @@ def run_ours(args):
         e2e_run(e2e_steps, host_stats)
         torch.cuda.synchronize()
         runs.append(time.perf_counter() - te)
+        uploads.append(up0.elapsed_time(up1))
     gc.enable()
     assert np.all(np.isfinite(host_stats[:e2e_steps, :, :, 2:, 0].numpy()))
     te = float(np.median(runs))
@@ -551,8 +558,9 @@ def run_ours(args):
                    "initialised through lbm_init_fields_batch, 200 steps, Table 1 statistics "
                    "to pinned host memory; step k's upload and step k-1's statistics "
                    "overlap step k; wall clock over %d steps including pipeline fill and "
-                   "drain, median of 3 runs (%s ms)"
-                   % (e2e_steps, ", ".join("%.1f" % (1e3 * r) for r in runs))}
+                   "drain, median of 3 runs (%s ms; the first upload, not overlapped: %s ms)"
+                   % (e2e_steps, ", ".join("%.1f" % (1e3 * r) for r in runs),
+                      ", ".join("%.1f" % u for u in uploads))}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
