@@ -467,11 +467,9 @@ int autotune(lbm_handle *h) {
       for (int rows : {1, 2, 4})
         for (int per : {0, 4, 8})
           cands.push_back({{wy, rows, per * nsm, h->lc.paper_force}, st, 0.f});
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  int best = 0;
-  for (size_t i = 0; i < cands.size(); ++i) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // 2 warm-up and 6 timed steps of candidate i
+  auto time_candidate = [&](size_t i) -> int {
     h->lc = cands[i].lc;
     int rc = build_tiles(h);
     if (rc) return rc;
@@ -488,10 +486,21 @@ int autotune(lbm_handle *h) {
     CK(cudaEventRecord(e1, h->stream));
     CK(cudaEventSynchronize(e1));
     CK(cudaEventElapsedTime(&cands[i].ms, e0, e1));
-    if (cands[i].ms < cands[best].ms) best = (int)i;
+    return LBM_OK;
+  };
+  int best = 0, rc = LBM_OK;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess)
+    rc = fail(h, LBM_ERR_CUDA, std::string("autotune events: ") + cudaGetErrorString(e));
+  for (size_t i = 0; i < cands.size() && rc == LBM_OK; ++i) {
+    rc = time_candidate(i);
+    if (rc == LBM_OK && cands[i].ms < cands[best].ms) best = (int)i;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  // the events are released on every path
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc != LBM_OK) return rc;
   h->lc = cands[best].lc;
   h->cur = cands[best].state;
   h->tuned_ms = cands[best].ms / 6.0f;
