@@ -801,3 +801,54 @@ def test_elbm_cell_conserves_mass_and_adds_the_force(orc):
     assert abs((cx * out).sum() - jx - (Fex - drag * jx)) < 1e-15
     assert abs((cy * out).sum() - jy - (Fey - drag * jy)) < 1e-15
     assert 1.0 < a < 64.0
+
+
+# --------------------------------------------------------------------------
+# Objective of the adjoint: time-window mean of the box-averaged dissipation
+# term RHS^{E,4} of the energy balance (eq. 8)
+# --------------------------------------------------------------------------
+
+def test_objective_closed_form_dissipation(orc):
+    """n0 = n1 = 0: the box mean of -nu rho (2 (du/dx)^2 + (du/dy + dv/dx)^2
+    + 2 (dv/dy)^2) (minus twice nu rho S:S, nu = (tau - 1/2)/3 by eq. 5) of an
+    equilibrium state built from analytic fields whose four velocity
+    derivatives and density all vary.  At the lowest mode of a 256^2 grid the
+    eighth-order stencil of eq. (18) differs from d/dx by about 1e-13 of the
+    derivative, so the exact derivatives fix the value (boxes with and without
+    periodic wrap)."""
+    n, tau = 256, 0.58
+    nu = (tau - 0.5) / 3.0
+    k = 2 * np.pi / n
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    U, V, A, B = 0.02, -0.015, 0.011, 0.007
+    rho = 1.0 + 0.05 * np.sin(k * x + 0.3) * np.cos(k * y - 0.2)
+    ux = U * np.cos(k * y) + A * np.sin(k * x)
+    uy = V * np.cos(k * x) + B * np.sin(k * y)
+    dxu, dyu = A * k * np.cos(k * x), -U * k * np.sin(k * y)
+    dxv, dyv = -V * k * np.sin(k * x), B * k * np.cos(k * y)
+    eps = -nu * rho * (2 * dxu ** 2 + (dyu + dxv) ** 2 + 2 * dyv ** 2)
+    f0 = orc.init(rho, ux, uy)
+    for (bx, by, L) in [(0, 0, n), (10, 200, 16), (250, 3, 32), (100, 240, 64), (7, 9, 1)]:
+        want = np.roll(np.roll(eps, -by, axis=0), -bx, axis=1)[:L, :L].mean()
+        got = orc.objective(f0, tau, orc.NO_FORCE, 0, 0, bx, by, L)
+        assert abs(got - want) <= 1e-10 * abs(want), (bx, by, L, got, want)
+
+
+def test_objective_window_is_the_mean_of_its_steps(orc):
+    """The objective over steps n0..n1 is the plain mean of the single-step
+    objectives, and the single-step objective at step n is the n = 0
+    objective of the state n steps later (forced, sheared flow)."""
+    nx, ny, tau = 24, 20, 0.56
+    force = orc.Force(1, 3e-4, 2, 2e-3)
+    f0 = orc.init(1.0 + li.smooth_fields(nx, ny, 11, amp=0.01),
+                  li.smooth_fields(nx, ny, 12, amp=0.03), li.smooth_fields(nx, ny, 13, amp=0.03))
+    bx, by, L = 19, 15, 8  # wraps in both directions
+    n0, n1 = 3, 7
+    single = [orc.objective(f0, tau, force, n, n, bx, by, L) for n in range(n0, n1 + 1)]
+    J = orc.objective(f0, tau, force, n0, n1, bx, by, L)
+    assert abs(J - np.mean(single)) <= 1e-13 * abs(J)
+    for n, Jn in zip(range(n0, n1 + 1), single):
+        later = orc.run(f0, n, tau, force)
+        assert abs(orc.objective(later, tau, force, 0, 0, bx, by, L) - Jn) <= 1e-14 * abs(Jn)
+    # the window sees the dynamics: the single-step values are not all equal
+    assert np.ptp(single) > 1e-6 * abs(J)
