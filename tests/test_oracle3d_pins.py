@@ -199,3 +199,38 @@ def test_balance_stats3_all_origins_mean_is_global(orc):
         np.testing.assert_allclose(st[iL, 2:, 0], T.reshape(13, -1).mean(axis=1), atol=5e-14)
     assert np.all(np.isnan(st[3]))
     assert np.all(np.abs(st[2, 2:, 1]) < 1e-14)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_d3q_equilibrium_moments(orc, q):
+    """The quadratic equilibrium reproduces rho, rho u and the Euler stress
+    rho (cs^2 I + u u) exactly on lattices with fourth-order isotropy; at rest
+    it is rho t_l."""
+    cx, cy, cz, t = orc.lattice3(q)
+    C = np.stack([cx, cy, cz], 1).astype(float)
+    for rho, u in [(1.0, (0.0, 0.0, 0.0)), (1.04, (0.05, -0.03, 0.02)), (0.96, (-0.1, 0.07, 0.12))]:
+        f = orc.feq3(rho, *u, q=q)
+        u = np.array(u)
+        assert abs(f.sum() - rho) < 1e-15
+        np.testing.assert_allclose(C.T @ f, rho * u, rtol=0, atol=1e-16)
+        np.testing.assert_allclose(np.einsum("la,lb,l->ab", C, C, f),
+                                   rho * (np.eye(3) / 3.0 + np.outer(u, u)), rtol=0, atol=1e-15)
+        if not u.any():
+            np.testing.assert_allclose(f, rho * t, rtol=0, atol=1e-17)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_terms3_from_populations_uniform_states(orc, q):
+    """Uniform states at n, n-1, n-2 with an energy quadratic in time: only
+    LHS^E survives and equals the slope e1 (BDF2 is exact on quadratics),
+    which fixes the order of the three levels."""
+    n, tau, rho0 = 4, 0.6, 0.98
+    e0, e1, e2 = 5e-4, -2e-5, 3e-6
+    states = []
+    for t in (0, -1, -2):
+        sp = np.sqrt(2 * (e0 + e1 * t + e2 * t * t) / rho0)
+        full = lambda v: np.full((n, n, n), v)  # noqa: E731
+        states.append(orc.init3(full(rho0), full(0.48 * sp), full(-0.6 * sp), full(0.64 * sp), q=q))
+    T = orc.terms3_from_populations(*states, tau)
+    np.testing.assert_allclose(T[0], e1, rtol=1e-11, atol=0)
+    assert np.max(np.abs(T[1:])) < 1e-17

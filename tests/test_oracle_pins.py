@@ -852,3 +852,93 @@ def test_objective_window_is_the_mean_of_its_steps(orc):
         assert abs(orc.objective(later, tau, force, 0, 0, bx, by, L) - Jn) <= 1e-14 * abs(Jn)
     # the window sees the dynamics: the single-step values are not all equal
     assert np.ptp(single) > 1e-6 * abs(J)
+
+
+# --------------------------------------------------------------------------
+# Grid-level assembly: collision of a whole grid, the local viscosity field,
+# and the balance terms straight from three population snapshots
+# --------------------------------------------------------------------------
+
+def _perturbed_state(orc, nx, ny, seed):
+    f = orc.init(1.0 + li.smooth_fields(nx, ny, seed, amp=0.02),
+                 li.smooth_fields(nx, ny, seed + 1, amp=0.04),
+                 li.smooth_fields(nx, ny, seed + 2, amp=0.04))
+    rng = np.random.default_rng(seed)
+    return f * (1.0 + 0.01 * rng.standard_normal(f.shape))  # non-equilibrium part
+
+
+@pytest.mark.parametrize("force_args", [(0, 0.0, 0, 0.0), (0, 0.0, 0, 4e-3), (1, 3e-4, 2, 2e-3)])
+def test_grid_collision_at_tau_one_is_the_shifted_equilibrium(orc, force_args):
+    """Eq. (1) with the EDM term at tau = 1 forgets the incoming
+    non-equilibrium part: the post-collision state is f^eq(rho, u + F/rho),
+    u = j/rho, F = F_ext - alpha j (moments by numpy sums)."""
+    nx, ny = 12, 10
+    force = orc.Force(*force_args)
+    f = _perturbed_state(orc, nx, ny, 50)
+    cx, cy, _ = orc.lattice()
+    rho = f.sum(axis=0)
+    jx, jy = np.einsum("l,lyx->yx", cx, f), np.einsum("l,lyx->yx", cy, f)
+    Fex, Fey = orc.force_field(f, force)
+    Fx, Fy = Fex - force.alpha * jx, Fey - force.alpha * jy
+    want = orc.init(rho, (jx + Fx) / rho, (jy + Fy) / rho)
+    np.testing.assert_allclose(orc.collide(f, 1.0, force), want, rtol=0, atol=2e-16)
+
+
+def test_grid_collision_is_affine_in_the_relaxation_rate_and_conserves(orc):
+    """BGK moves f towards the equilibrium by the fraction 1/tau: the changes
+    at two relaxation times, relative to tau = 1, scale as (1/tau - 1); every
+    tau keeps the mass and adds the force F = F_ext - alpha j to the
+    momentum."""
+    nx, ny = 12, 10
+    force = orc.Force(1, 3e-4, 2, 2e-3)
+    f = _perturbed_state(orc, nx, ny, 60)
+    cx, cy, _ = orc.lattice()
+    p1 = orc.collide(f, 1.0, force)
+    d = {tau: (orc.collide(f, tau, force) - p1) / (1.0 / tau - 1.0) for tau in (0.55, 0.8, 1.7)}
+    np.testing.assert_allclose(d[0.55], d[1.7], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(d[0.8], d[1.7], rtol=0, atol=1e-14)
+    jx, jy = np.einsum("l,lyx->yx", cx, f), np.einsum("l,lyx->yx", cy, f)
+    Fex, Fey = orc.force_field(f, force)
+    for tau in (0.55, 0.8, 1.7):
+        p = orc.collide(f, tau, force)
+        np.testing.assert_allclose(p.sum(axis=0), f.sum(axis=0), rtol=0, atol=1e-15)
+        np.testing.assert_allclose(np.einsum("l,lyx->yx", cx, p), jx + Fex - force.alpha * jx,
+                                   rtol=0, atol=1e-16)
+        np.testing.assert_allclose(np.einsum("l,lyx->yx", cy, p), jy + Fey - force.alpha * jy,
+                                   rtol=0, atol=1e-16)
+
+
+def test_nu_field_is_the_local_viscosity_of_each_cell(orc):
+    """BGK: (tau - 1/2)/3 everywhere (eq. 5); Smagorinsky and eq. (7): the
+    viscosity of each cell's own relaxation time, and the Smagorinsky eddy
+    viscosity never lowers it."""
+    nx, ny, tau0 = 8, 6, 0.53
+    f = _perturbed_state(orc, nx, ny, 70)
+    assert np.all(orc.nu_field(f, tau0, orc.Force(0)) == (tau0 - 0.5) / 3.0)
+    for coll, cs in ((1, 0.1), (2, 0.0)):
+        m = orc.Force(0, collision=coll, Cs=cs)
+        nu = orc.nu_field(f, tau0, m)
+        for y in range(ny):
+            for x in range(nx):
+                assert nu[y, x] == pytest.approx((orc.tau_eff(f[:, y, x], tau0, m) - 0.5) / 3.0,
+                                                 rel=0, abs=1e-17)
+        if coll == 1:
+            assert np.all(nu >= (tau0 - 0.5) / 3.0) and np.any(nu > (tau0 - 0.5) / 3.0)
+
+
+def test_terms_from_populations_uniform_states(orc):
+    """Uniform states at levels n, n-1, n-2 whose energy is quadratic in time
+    (E = e0 + e1 t + e2 t^2 at t = 0, -1, -2): no gradient, no vorticity, so
+    every term but LHS^E vanishes, and the BDF2 time derivative of eq. (17)
+    gives LHS^E = e1 exactly (the level order matters: e2 != 0)."""
+    nx, ny, tau, rho0 = 6, 5, 0.6, 1.07
+    e0, e1, e2 = 4e-4, 3e-5, 2e-6
+    states = []
+    for t in (0, -1, -2):
+        E = e0 + e1 * t + e2 * t * t
+        sp = np.sqrt(2 * E / rho0)
+        states.append(orc.init(np.full((ny, nx), rho0), np.full((ny, nx), 0.6 * sp),
+                               np.full((ny, nx), -0.8 * sp)))
+    T = orc.terms_from_populations(*states, tau)
+    np.testing.assert_allclose(T[0], e1, rtol=1e-11, atol=0)
+    assert np.max(np.abs(T[1:])) < 1e-17
