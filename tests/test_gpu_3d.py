@@ -169,3 +169,46 @@ def test_3d_history_required(P):
     with pytest.raises(P.LBMError) as e:
         lat.subvolume_balance(0, [2])
     assert e.value.code == -4
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_3d_edge_cases(P, orc, q):
+    """Zero steps are a no-op and a negative count is rejected; rejected
+    balance arguments leave the handle usable; L = N boxes (the whole
+    periodic cube from every origin) are all equal, with the global means of
+    the oracle's terms; a flow at rest has zero terms and zero balancing
+    errors (eqs. 12, 13 at 0/0)."""
+    n, tau, F0, kf, a = 8, 0.58, 3e-4, 1, 2e-3
+    lat = P.Lattice3D([P.Member3(n, n, n, tau, 1.0, 1, kf, F0, a)], precision=64, diag_every=4,
+                      lattice=q)
+    lat.init_fields(0, *_fields((n, n, n), 70))
+    lat.step(2)
+    f2 = lat.get_populations_host(0)
+    lat.step(0)
+    assert lat.time == 2 and np.array_equal(lat.get_populations_host(0), f2)
+    with pytest.raises(P.LBMError) as e:
+        lat.step(-1)
+    assert e.value.code == -1 and lat.time == 2
+    lat.step(1)
+    f3 = lat.get_populations_host(0)
+    lat.step(1)
+    f4 = lat.get_populations_host(0)
+    for kw in (dict(Ls=[]), dict(Ls=[2], origins=[np.array([[n, 0, 0]])]),
+               dict(Ls=[2], origins=[np.array([[0, 0, -1]])])):
+        with pytest.raises(P.LBMError) as e:
+            lat.subvolume_balance(0, **kw)
+        assert e.value.code == -1, kw
+    stats, pb = lat.subvolume_balance(0, [n], per_box=True)
+    pb = pb.cpu().numpy()
+    T = orc.terms3_from_populations(f4, f3, f2, tau, 1, F0, kf, a)
+    scale = np.max(np.abs(T.reshape(13, -1)), axis=1) + 1e-300
+    assert pb.shape[0] == n ** 3 and np.all(pb[:, 2:] == pb[:1, 2:])
+    np.testing.assert_allclose(stats[0, 2:, 0], T.reshape(13, -1).mean(axis=1), rtol=0,
+                               atol=TERM_TOL * np.max(scale))
+    lat.close()
+    rest = P.Lattice3D([P.Member3(n, n, n, 0.6)], precision=64, diag_every=2, lattice=q)
+    rest.init_fields(0, np.ones((n, n, n)), *(np.zeros((n, n, n)) for _ in range(3)))
+    rest.step(4)
+    st, pbr = rest.subvolume_balance(0, [1, 4, n], per_box=True)
+    assert np.all(st == 0.0) and np.all(pbr.cpu().numpy() == 0.0)
+    rest.close()
