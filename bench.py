@@ -297,6 +297,48 @@ def collision_models_leg(P, stream, dev, peak):
     return out
 
 
+def taylor_green_leg(P, stream, dev):
+    """The plain FP64 Taylor-Green case: 64^2, tau 0.6, u0 0.01, 1000 steps
+    with the balance at L in {4, 8, 16, 32} every 100 steps.  A 64^2 step
+    cannot fill the GPU, so its time is launch latency: reported per step
+    with plain launches and with graph replay, and for the whole workload
+    (steps, snapshots and its ten balance events, host wall clock)."""
+    import torch
+    wl = li.taylor_green_workload()
+    n, tau, D, Ls, steps = wl["n"], wl["tau"], wl["diag_every"], wl["Ls"], wl["steps"]
+    rho, ux, uy = li.taylor_green(n, u0=wl["u0"])
+    out = {"grid": [n, n], "tau": tau, "steps": steps}
+    for key, graph in (("plain", 0), ("graph", 100)):
+        lat = P.Lattice([P.Member(n, n, tau)], precision=64, graph_steps=graph, stream=stream,
+                        device=dev)
+        lat.init_fields(0, rho, ux, uy)
+        lat.step(200)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        lat.step(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        us = a.elapsed_time(b) * 1e3 / steps
+        out["us_per_step_" + key] = us
+        out["glups_" + key] = n * n / us / 1e3
+        lat.close()
+    lat = P.Lattice([P.Member(n, n, tau)], precision=64, diag_every=D, graph_steps=16,
+                    stream=stream, device=dev)
+    lat.init_fields(0, rho, ux, uy)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps // D):
+        lat.step(D)
+        st = lat.subvolume_balance(0, Ls)
+    torch.cuda.synchronize()
+    out["workload_ms"] = (time.perf_counter() - t0) * 1e3
+    out["balance_events"] = steps // D
+    assert np.all(np.isfinite(st[:, 2:, 0]))
+    lat.close()
+    return out
+
+
 def three_d_leg(P, stream, dev, peak):
     """The three-dimensional extension: 2 FP32 members of 128^3 on D3Q19
     (152 algorithmic bytes per update: 19 populations read and written) and
@@ -491,6 +533,7 @@ def run_ours(args):
     paper_forcing = paper_forcing_leg(P, stream, dev, measured_peaks()[0])
     collisions = collision_models_leg(P, stream, dev, measured_peaks()[0])
     three_d = three_d_leg(P, stream, dev, measured_peaks()[0])
+    taylor_green = taylor_green_leg(P, stream, dev)
 
     # end to end through the public API with host buffers: every step uploads
     # the initial fields of all members from pinned host memory, runs the
@@ -593,6 +636,7 @@ def run_ours(args):
             "paper_forcing_ensemble": paper_forcing,
             "collision_models": collisions,
             "three_d": three_d,
+            "fp64_taylor_green_64": taylor_green,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -688,7 +688,10 @@ static dim3 grid2d(int nx, int ny, dim3 b) {
 
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member, int nx,
                                int ny, int state, cudaStream_t s) {
-  dim3 b(64, 4);
+  // one thread per cell; a grid too small to give every SM a 256-thread CTA
+  // gets 64-thread CTAs, so that its FP64 arithmetic (slow on this part)
+  // spreads over four times as many SMs
+  const dim3 b = (long long)nx * ny < (1LL << 15) ? dim3(32, 2) : dim3(64, 4);
   if (precision == 32)
     k_step_scalar<float><<<grid2d(nx, ny, b), b, 0, s>>>(d_members, member, state);
   else
