@@ -234,3 +234,30 @@ def test_terms3_from_populations_uniform_states(orc, q):
     T = orc.terms3_from_populations(*states, tau)
     np.testing.assert_allclose(T[0], e1, rtol=1e-11, atol=0)
     assert np.max(np.abs(T[1:])) < 1e-17
+
+
+def test_balancing_errors3_include_vortex_stretching(orc):
+    """Eqs. (12), (13) in 3D on constant term fields, every box alike: an
+    exact balance gives 0 only when the vortex-stretching term RHS^{O,6}
+    takes part in the enstrophy sum; a known imbalance gives imbalance /
+    max |RHS^i|; all-zero terms give 0 and a zero right-hand side +Inf."""
+    n, L = 4, 2
+    vals = np.zeros(13)
+    vals[0] = 1.0
+    vals[1:6] = [0.5, 0.25, -0.25, 0.75, -0.25]            # sums to LHS^E
+    vals[6] = -2.0
+    vals[7:13] = [-1.0, -0.5, -0.25, 0.0, 0.0, -0.25]       # RHS^{O,6} = -0.25 closes it
+    T = np.broadcast_to(vals[:, None, None, None], (13, n, n, n)).copy()
+    _, pb = orc.balance_stats3(T, [L], per_box=True)
+    assert np.all(pb[0][:, 0] == 0.0) and np.all(pb[0][:, 1] == 0.0)
+    T[12] += 0.5  # RHS^{O,6}: -0.25 -> 0.25; sum -1.5; max |RHS| = 1
+    T[4] -= 0.3   # RHS^{E,4}: 0.75 -> 0.45; sum 0.7; max |RHS| = 0.5
+    _, pb = orc.balance_stats3(T, [L], per_box=True)
+    np.testing.assert_allclose(pb[0][:, 0], 0.3 / 0.5, rtol=1e-14)
+    np.testing.assert_allclose(pb[0][:, 1], 0.5 / 1.0, rtol=1e-14)
+    Z = np.zeros((13, n, n, n))
+    _, pb = orc.balance_stats3(Z, [L], per_box=True)
+    assert np.all(pb[0][:, :2] == 0.0)
+    Z[6] = 1.0
+    _, pb = orc.balance_stats3(Z, [L], per_box=True)
+    assert np.all(pb[0][:, 1] == np.inf) and np.all(pb[0][:, 0] == 0.0)
