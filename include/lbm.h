@@ -149,7 +149,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes,
                lbm_handle **out);
 
 /* Releases the host-side handle and its CUDA graphs; the workspace stays
- * the caller's. */
+ * the caller's.  h == NULL is a no-op (returns 0). */
 int lbm_destroy(lbm_handle *h);
 
 /* Sets member `member` (or every member when member < 0, all sharing the

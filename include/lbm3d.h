@@ -63,6 +63,8 @@ int lbm3d_workspace_size(const lbm3d_config *cfg, size_t *bytes);
  * >= lbm3d_workspace_size bytes, owned by the caller and kept alive until
  * lbm3d_destroy).  *out receives the handle. */
 int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_handle **out);
+/* Waits for the handle's work and releases it (host memory; the workspace
+ * stays the caller's).  h == NULL is a no-op (returns 0). */
 int lbm3d_destroy(lbm3d_handle *h);
 
 /* f(x, 0) = f_eq(rho(x), u(x)) (eq. 2) for one member; rho, ux, uy, uz are

@@ -1073,7 +1073,7 @@ int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_h
 }
 
 int lbm3d_destroy(lbm3d_handle *h) {
-  if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (!h) return LBM_OK;  // like free(NULL)
   cudaStreamSynchronize(h->stream);
   delete h;
   return LBM_OK;

@@ -4,6 +4,7 @@ host-only calls validate configurations (no GPU needed)."""
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -101,3 +102,42 @@ def test_3d_config_checks(P):
     assert size([P.Member3(0, 12, 8, 0.6)]) == -1
     assert size([P.Member3(8, 8, 8, 0.6, force_kind=2)]) == -1
     assert size([P.Member3(8, 8, 8, 0.6)], precision=16) == -1
+
+
+_NULL_SWEEP = r"""
+import ctypes, json, sys
+sys.path.insert(0, sys.argv[1])
+import paper_1809_06735_gb300 as P
+lib = P.load_library()
+out = {}
+for name in json.loads(sys.argv[2]):
+    f = getattr(lib, name)
+    if not f.argtypes:
+        continue
+    args = [0 if t in (ctypes.c_int, ctypes.c_size_t, ctypes.c_longlong) else
+            0.0 if t is ctypes.c_double else None for t in f.argtypes]
+    r = f(*args)
+    out[name] = r.decode() if isinstance(r, bytes) else r
+print(json.dumps(out))
+"""
+
+
+def test_null_handles_and_pointers_are_rejected(P):
+    """Every entry point called with NULL handles and pointers and zero
+    sizes (no GPU work is reached): the argument error -1 from every status
+    call, -1 from the value getters, a message from the error getters, and
+    destroying NULL is a no-op (0).  Run in a child process."""
+    import json
+    names = declared_symbols()
+    r = subprocess.run([sys.executable, "-c", _NULL_SWEEP, ROOT, json.dumps(names)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    assert len(got) >= 30
+    for name, v in got.items():
+        if name.endswith("last_error"):
+            assert v == "handle is NULL", name
+        elif name in ("lbm_destroy", "lbm3d_destroy"):
+            assert v == 0, name
+        else:
+            assert v == -1, (name, v)
