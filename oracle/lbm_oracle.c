@@ -31,7 +31,10 @@
  * identities, conservation, streaming permutation, Taylor-Green decay,
  * Kolmogorov laminar amplitude, stencil modified wavenumber, BDF2
  * exactness, symbolic continuum terms, brute-force box sums, closed-form
- * box Mach numbers, brute-force histogram counts).
+ * box Mach numbers, brute-force histogram counts; the diagnostic velocity
+ * by the midpoint of the momenta before and after the force acts; the ELBM
+ * relaxation by a near-equilibrium shear-wave decay at the BGK viscosity
+ * and by the per-cell relaxation at the tau_eff of its local viscosity).
  */
 #include <math.h>
 #include <stdlib.h>

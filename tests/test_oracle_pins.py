@@ -942,3 +942,105 @@ def test_terms_from_populations_uniform_states(orc):
     T = orc.terms_from_populations(*states, tau)
     np.testing.assert_allclose(T[0], e1, rtol=1e-11, atol=0)
     assert np.max(np.abs(T[1:])) < 1e-17
+
+
+# --------------------------------------------------------------------------
+# Diagnostic velocity of the exact-difference forcing (Sec. 3)
+# --------------------------------------------------------------------------
+
+def test_diagnostic_velocity_is_the_mid_step_velocity_under_uniform_drag(orc):
+    """A uniform state under drag alone stays uniform (streaming a uniform
+    field changes nothing), so one step takes the momentum from j(n) to
+    j(n+1) = j(n) + F = (1 - alpha) j(n) in every cell.  The physical velocity
+    of the exact-difference method is the mean of the momenta before and after
+    the force acts: u(n) = (j(n) + j(n+1)) / (2 rho).  At alpha = 0.1 a dropped
+    or sign-flipped F/2 shift moves u by 5e-2 or 1e-1 of its value."""
+    nx, ny, tau, alpha, rho0 = 5, 4, 0.7, 0.1, 1.04
+    f = orc.init(np.full((ny, nx), rho0), np.full((ny, nx), 0.03), np.full((ny, nx), -0.02))
+    force = orc.Force(0, alpha=alpha)
+    m0 = orc.moments(f, force)
+    m1 = orc.moments(orc.run(f, 1, tau, force), force)
+    np.testing.assert_allclose(m1["rho"], m0["rho"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(m1["jx"], (1 - alpha) * m0["jx"], rtol=0, atol=1e-16)
+    np.testing.assert_allclose(m1["jy"], (1 - alpha) * m0["jy"], rtol=0, atol=1e-16)
+    for u, j in (("ux", "jx"), ("uy", "jy")):
+        np.testing.assert_allclose(m0[u], (m0[j] + m1[j]) / (2 * m0["rho"]), rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("force_args", [dict(kind=0, alpha=5e-3),
+                                        dict(kind=1, F0=3e-4, kf=2, alpha=2e-3),
+                                        dict(kind=2, F0=1e-4, phase=0.4, FR0=0.05, alpha=1e-3)])
+def test_diagnostic_velocity_is_the_mean_of_pre_and_post_collision_velocities(orc, force_args):
+    """Exact-difference forcing (Sec. 3) moves each cell's velocity from
+    u = j/rho to u + F/rho inside the collision; its physical velocity is the
+    midpoint.  So, cell by cell and for every force kind (the Kolmogorov force,
+    the shell force with the eq. (16) damping of the same state, drag),
+    u(n) = (j + j*) / (2 rho) with j* = sum_l c_l f*_l the momentum of the
+    post-collision populations (collision alone; it keeps rho)."""
+    nx, ny = 12, 10
+    force = orc.Force(**force_args)
+    f = _perturbed_state(orc, nx, ny, 60)
+    cx, cy, _ = orc.lattice()
+    post = orc.collide(f, 0.63, force)
+    rho = f.sum(axis=0)
+    m = orc.moments(f, force)
+    for u, c in (("ux", cx), ("uy", cy)):
+        mid = (np.einsum("l,lyx->yx", c, f) + np.einsum("l,lyx->yx", c, post)) / (2 * rho)
+        np.testing.assert_allclose(m[u], mid, rtol=0, atol=1e-16)
+
+
+# --------------------------------------------------------------------------
+# Entropic LBM relaxation (Sec. 1): beta = 1/(2 tau0), tau_eff = 2 tau0/alpha
+# --------------------------------------------------------------------------
+
+def _shear_wave_rate(orc, model, N, U, tau0, t1=50, T=450):
+    y = np.arange(N)
+    basis = np.sin(2 * np.pi * y / N)[:, None]
+    ux = np.tile(U * basis, (1, 4))
+    f1 = orc.run(orc.init(np.ones((N, 4)), ux, np.zeros((N, 4))), t1, tau0, model)
+    f2 = orc.run(f1, T - t1, tau0, model)
+    a1 = np.sum(orc.moments(f1)["ux"] * basis) / np.sum(basis ** 2 * np.ones((1, 4)))
+    a2 = np.sum(orc.moments(f2)["ux"] * basis) / np.sum(basis ** 2 * np.ones((1, 4)))
+    return -np.log(a2 / a1) / (T - t1)
+
+
+def test_elbm_shear_wave_decays_at_the_bgk_viscosity(orc):
+    """Near equilibrium the entropic root tends to alpha = 2, so ELBM's
+    relaxation alpha beta must reduce to BGK's 1/tau0 and its shear viscosity
+    to nu = cs^2 (tau0 - 1/2) (eq. 5).  A small shear wave
+    u_x = U sin(2 pi y / N) then decays at nu k^2 (k = 2 pi / N, up to the
+    lattice's O(k^2) correction) and at the rate of the BGK wave with the same
+    tau0.  A factor beta = 1/tau0 would relax at 2/tau0 (tau_eff = tau0/2,
+    below the stability limit at tau0 = 0.8)."""
+    N, U, tau0 = 64, 1e-3, 0.8
+    k = 2 * np.pi / N
+    nu = (tau0 - 0.5) / 3.0
+    r_elbm = _shear_wave_rate(orc, orc.Force(0, collision=3), N, U, tau0)
+    r_bgk = _shear_wave_rate(orc, orc.Force(0), N, U, tau0)
+    assert abs(r_elbm / (nu * k * k) - 1) < 1e-3
+    assert abs(r_elbm / r_bgk - 1) < 1e-5
+
+
+def test_elbm_relaxes_each_cell_at_the_tau_of_its_viscosity(orc):
+    """Without force the ELBM collision scales each cell's departure from its
+    equilibrium by 1 - alpha beta; the relaxation time that the diagnostic's
+    local viscosity reports (nu_field, eq. 5: tau_eff = 3 nu + 1/2) must be
+    the one the collision applies: f*_l - f^eq_l = (1 - 1/tau_eff)(f_l - f^eq_l)
+    for every population of every cell, on states far enough from equilibrium
+    that alpha differs from 2 (tau_eff differs from tau0)."""
+    nx, ny, tau0 = 6, 5, 0.53
+    model = orc.Force(0, collision=3)
+    cx, cy, _ = orc.lattice()
+    f = orc.init(1.0 + li.smooth_fields(nx, ny, 80, amp=0.02),
+                 li.smooth_fields(nx, ny, 81, amp=0.04), li.smooth_fields(nx, ny, 82, amp=0.04))
+    f = f * (1.0 + 0.05 * np.random.default_rng(80).standard_normal(f.shape))
+    post = orc.collide(f, tau0, model)
+    te = 3.0 * orc.nu_field(f, tau0, model) + 0.5
+    assert np.max(np.abs(te - tau0)) > 5e-3  # alpha is not the BGK value here
+    for y in range(ny):
+        for x in range(nx):
+            a = f[:, y, x]
+            rho = a.sum()
+            feq = orc.feq_entropic(rho, (cx * a).sum() / rho, (cy * a).sum() / rho)
+            np.testing.assert_allclose(post[:, y, x] - feq, (1 - 1 / te[y, x]) * (a - feq),
+                                       rtol=0, atol=1e-15)
