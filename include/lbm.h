@@ -363,9 +363,12 @@ int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx,
  *      collision only (others return LBM_ERR_ARG).
  * out: host pointer to LBM_NGLOBAL doubles; the call synchronises
  *      cuda_stream (NULL = legacy default stream) before returning.
+ * m->tau must be finite and above 1/2, F0 and alpha finite.
  * Calls no cudaMalloc or cudaFree.  The first call on a device looks up the
  * scratch address with cudaGetSymbolAddress; make that first call before
- * any stream capture.  Every call on a device shares the one scratch array
+ * any stream capture.  The address is kept for the rest of the process:
+ * resetting the device (cudaDeviceReset) after that first call is not
+ * supported.  Every call on a device shares the one scratch array
  * (which keeps the last call's contents): calls whose work overlaps on the
  * GPU, e.g. on two streams at once, race and give wrong results.  Errors are
  * reported through lbm_static_last_error(). */

@@ -43,7 +43,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     """Compile every translation unit (in parallel) and link ``liblbm.so``."""
     os.makedirs(OUT, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(ROOT, "include", "lbm.h"))
+    inc = os.path.join(ROOT, "include")
+    headers += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

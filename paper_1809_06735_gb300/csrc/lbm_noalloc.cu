@@ -153,7 +153,8 @@ __global__ void k_static_final(int nblocks, size_t N, double *scratch) {
 }
 
 // Device address of the scratch array on the current device, looked up once
-// per device.
+// per device and kept for the life of the process (a device reset after the
+// first call would leave it stale; the header says so).
 int scratch_address(double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -175,13 +176,15 @@ int scratch_address(double **out) {
 extern "C" int lbm_global_balance_static(const double *f, int nx, int ny,
                                          const lbm_member_cfg *m, double *out,
                                          void *cuda_stream) {
-  if (!f || !m || !out) return fail_static(LBM_ERR_ARG, "f, m and out must not be NULL");
+  if (!f) return fail_static(LBM_ERR_ARG, "f is NULL");
+  if (!m) return fail_static(LBM_ERR_ARG, "m is NULL");
+  if (!out) return fail_static(LBM_ERR_ARG, "out is NULL");
   if (nx < 1 || ny < 1) return fail_static(LBM_ERR_ARG, "grid must be at least 1 x 1");
   if ((long long)nx * ny > (long long)LBM_STATIC_MAX_CELLS)
     return fail_static(LBM_ERR_ARG,
                        "grid larger than LBM_STATIC_MAX_CELLS cells: use lbm_global_balance");
-  if (!(m->tau > 0.5) || (m->force_kind != 0 && m->force_kind != 1) || m->collision != 0 || !std::isfinite(m->F0) ||
-      !std::isfinite(m->alpha))
+  if (!(m->tau > 0.5) || !std::isfinite(m->tau) || (m->force_kind != 0 && m->force_kind != 1) ||
+      m->collision != 0 || !std::isfinite(m->F0) || !std::isfinite(m->alpha))
     return fail_static(LBM_ERR_ARG, "invalid member parameters");
   double *scratch = nullptr;
   int rc = scratch_address(&scratch);

@@ -141,3 +141,51 @@ def test_null_handles_and_pointers_are_rejected(P):
             assert v == 0, name
         else:
             assert v == -1, (name, v)
+
+
+_STATIC_ARGS = r"""
+import ctypes, json, math, sys
+sys.path.insert(0, sys.argv[1])
+import paper_1809_06735_gb300 as P
+lib = P.load_library()
+fn = lib.lbm_global_balance_static
+fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P._MemberCfg),
+               ctypes.c_void_p, ctypes.c_void_p]
+lib.lbm_static_last_error.restype = ctypes.c_char_p
+out = (ctypes.c_double * 7)()
+fake = ctypes.c_void_p(4096)  # never dereferenced: every case fails before any CUDA call
+res = {}
+def call(name, f, nx, ny, m, o):
+    rc = fn(f, nx, ny, ctypes.byref(m.c()) if m is not None else None, o, None)
+    res[name] = [rc, lib.lbm_static_last_error().decode()]
+good = P.Member(8, 8, 0.6)
+call("f", None, 8, 8, good, out)
+call("m", fake, 8, 8, None, out)
+call("out", fake, 8, 8, good, None)
+call("grid", fake, 0, 8, good, out)
+call("size", fake, 1024, 512, good, out)
+call("tau_inf", fake, 8, 8, P.Member(8, 8, math.inf), out)
+call("tau_half", fake, 8, 8, P.Member(8, 8, 0.5), out)
+call("F0_nan", fake, 8, 8, P.Member(8, 8, 0.6, 1.0, 1, 1, math.nan), out)
+call("kind2", fake, 8, 8, P.Member(8, 8, 0.6, 1.0, 2), out)
+print(json.dumps(res))
+"""
+
+
+def test_static_entry_point_rejects_bad_arguments_before_any_cuda_call(P):
+    """lbm_global_balance_static: each NULL pointer, an empty or oversized
+    grid and invalid member parameters (tau infinite or not above 1/2, a
+    non-finite F0, force kind 2) return -1 with a message naming the fault,
+    before any CUDA call (runs without a GPU).  Run in a child process."""
+    import json
+    r = subprocess.run([sys.executable, "-c", _STATIC_ARGS, ROOT],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    for name, (rc, msg) in got.items():
+        assert rc == -1, (name, rc, msg)
+    assert got["f"][1] == "f is NULL" and got["m"][1] == "m is NULL"
+    assert got["out"][1] == "out is NULL"
+    assert "LBM_STATIC_MAX_CELLS" in got["size"][1]
+    for name in ("tau_inf", "tau_half", "F0_nan", "kind2"):
+        assert got[name][1] == "invalid member parameters", name

@@ -130,7 +130,6 @@ def test_state_roundtrip(P):
     lat32.set_populations(0, f0)
     got = lat32.get_populations_host(0)
     assert np.max(np.abs(got - f0)) < 1e-8
-    assert not np.array_equal(got, f0) or True
 
 
 def test_graph_replay_is_bitwise_identical(P):
