@@ -6,7 +6,8 @@ whose host application owns the device memory pool), so it takes no
 workspace and keeps its scratch in a fixed device array.  Two calls in a row
 on different states must each match the handle-based entry point within the
 tolerance the other global-balance tests use (1e-12 relative; the momentum
-sums, which cancel, to 1e-12 per cell).  This file is collected last.
+sums, which cancel, to 1e-12 per cell), and so must one call against the
+FP64 oracle directly.  This file is collected last.
 """
 import ctypes
 
@@ -73,6 +74,25 @@ def test_static_at_the_size_limit_and_unforced(P):
     ref = lat.global_balance(0)
     got = _static_call(P, lat.get_populations(0), m, torch.cuda.current_stream())
     _compare(got, ref, n * n)
+
+
+def test_static_matches_the_oracle_after_a_size_change(P, orc):
+    """The whole-grid quantities straight against the FP64 oracle, and a
+    grid shrinking between calls: a 512^2 call, then 5 x 3 (narrower than the
+    eq. (18) stencil, so every difference wraps).  The second call reads no
+    stale partial of the first."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for nx, ny, seed in ((512, 512, 21), (5, 3, 22), (37, 23, 23)):
+        m = P.Member(nx, ny, 0.61, 1.0, 1, 1, 3e-4, 2e-3)
+        f = li.random_populations(nx, ny, seed=seed, rel_noise=0.03)
+        got = _static_call(P, torch.from_numpy(f).cuda(), m, stream)
+        want = orc.global_quantities(f, 0.61, orc.Force(1, 3e-4, 1, 2e-3))
+        _compare(got, want, nx * ny)
+        lat = P.Lattice([m], precision=64)
+        lat.set_populations(0, f)
+        _compare(got, lat.global_balance(0), nx * ny)
+        lat.close()
 
 
 def test_static_rejects_oversized_grid(P):
