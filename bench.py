@@ -185,6 +185,10 @@ def table1_boxes(n, Ls, scale=1.0):
 
 
 def oracle_period_sample(seed: int, n_steps: int = PERIOD, box_fraction: float = 1.0):
+    """One member of the decaying ensemble through the oracle: n_steps LBM
+    steps, then the diagnostic of the last three levels on the Table 1
+    boxes (a fraction of them).  Returns (updates, step seconds, diagnostic
+    seconds)."""
     import oracle
     wl = li.decaying_ensemble_workload()
     n, tau = wl["n"], wl["tau"]
@@ -195,11 +199,93 @@ def oracle_period_sample(seed: int, n_steps: int = PERIOD, box_fraction: float =
     f_a = oracle.run(f, n_steps - 2, tau)
     f_b = oracle.run(f_a, 1, tau)
     f_c = oracle.run(f_b, 1, tau)
+    t1 = time.perf_counter()
     T = oracle.terms_from_populations(f_c, f_b, f_a, tau)
     for L, o in zip(wl["Ls"], boxes):
         oracle.balance_stats(T, [L], origins=o)
-    dt = time.perf_counter() - t0
-    return n * n * n_steps, dt
+    t2 = time.perf_counter()
+    return n * n * n_steps, t1 - t0, t2 - t1
+
+
+def _oracle_member_task(args):
+    """Pool task (spawned process): one member's oracle period sample."""
+    return oracle_period_sample(*args)
+
+
+def _oracle_strip_task(args):
+    """Pool task: `steps` oracle steps of one 8192 x (rows + 2 steps) strip
+    of the large forced run (random near-rest populations: the oracle's
+    cost does not depend on the values), as a window of the 8192^2 grid
+    (exact in its interior).  Returns (interior updates, seconds)."""
+    import oracle
+    y0, rows, steps = args
+    wl = li.large_forced_workload()
+    n = wl["n"]
+    f = li.random_populations(n, rows + 2 * steps, seed=y0)
+    force = oracle.Force(1, wl["F0"], wl["kf"], wl["alpha"])
+    t0 = time.perf_counter()
+    oracle.run_window(f, steps, wl["tau"], force, 0, y0 - steps, n, n)
+    return n * rows * steps, time.perf_counter() - t0
+
+
+def _oracle_taylor_green_task(_):
+    """Pool task: the whole 64^2 FP64 Taylor-Green workload through the
+    oracle (1000 steps, the balance at L in {4, 8, 16, 32} over every
+    periodic origin every 100 steps).  Returns seconds."""
+    import oracle
+    wl = li.taylor_green_workload()
+    n, tau, D = wl["n"], wl["tau"], wl["diag_every"]
+    f = oracle.init(*li.taylor_green(n, u0=wl["u0"]))
+    t0 = time.perf_counter()
+    for _ in range(wl["steps"] // D):
+        f2 = oracle.run(f, D - 2, tau)
+        f1 = oracle.run(f2, 1, tau)
+        f = oracle.run(f1, 1, tau)
+        oracle.balance_stats(oracle.terms_from_populations(f, f1, f2, tau), wl["Ls"])
+    return time.perf_counter() - t0
+
+
+def oracle_pool(cores: int):
+    """A pool of spawned processes for the oracle (no fork after CUDA use)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()  # compiled once, before the workers load it
+    return mp.get_context("spawn").Pool(cores)
+
+
+def cpu_baseline_all_cores():
+    """The FP64 oracle on every host core, one member per process (the
+    ensemble shards by member with nothing shared): one full 200-step period
+    of the decaying ensemble's 512^2 members, each followed by its Table 1
+    diagnostic; then 2 steps of the 8192^2 large-run shape as one strip per
+    core, and the whole 64^2 Taylor-Green workload on one core."""
+    cores = os.cpu_count() or 1
+    wl = li.decaying_ensemble_workload()
+    with oracle_pool(cores) as pool:
+        pool.map(abs, range(cores))  # workers up (interpreter start, imports)
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_member_task, [(wl["seed0"] + m, PERIOD, 1.0) for m in range(cores)])
+        wall = time.perf_counter() - t0
+        rows = 8192 // cores
+        t1 = time.perf_counter()
+        strips = pool.map(_oracle_strip_task, [(k * rows, rows, 2) for k in range(cores)])
+        wall4 = time.perf_counter() - t1
+        tg = pool.map(_oracle_taylor_green_task, [0])[0]
+    lu = sum(r[0] for r in res)
+    step_s = [r[1] for r in res]
+    return {"value": lu / wall / 1e9, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d members of 512^2 (one per core, processes): the full 200-step "
+                      "period, then the Table 1 diagnostic (L=2..256); GLUPS over the "
+                      "wall clock including the diagnostic" % cores,
+            "seconds": wall,
+            "single_core_step_glups": float(np.median([PERIOD * 512 * 512 / t
+                                                        for t in step_s])) / 1e9,
+            "diagnostic_s_per_event_512sq_member": float(np.median([r[2] for r in res])),
+            "large_8192sq_shape": {"glups": sum(r[0] for r in strips) / wall4 / 1e9,
+                                   "cores": cores,
+                                   "sample": "2 steps of 8192^2 as %d strips of 8192 x %d "
+                                             "(window runs)" % (cores, rows)},
+            "taylor_green_64_workload_s": tg}
 
 
 def run_reference(args):
@@ -210,25 +296,34 @@ def run_reference(args):
         if rank != 0:
             dist.barrier()
             return
-    import oracle
-    oracle.build()
     wl = li.decaying_ensemble_workload()
-    for w in range(args.warmup):
-        oracle_period_sample(wl["seed0"] + w, n_steps=20, box_fraction=0.01)
-    lu, secs = 0, 0.0
-    for k in range(args.steps):
-        a, b = oracle_period_sample(wl["seed0"] + k, n_steps=20, box_fraction=0.01)
-        lu += a
-        secs += b
+    cores = os.cpu_count() or 1
+    with oracle_pool(cores) as pool:
+        pool.map(abs, range(cores))
+
+        def one_step(k):
+            tasks = [(wl["seed0"] + k * cores + m, 20, 0.01) for m in range(cores)]
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_member_task, tasks)
+            return sum(r[0] for r in res), time.perf_counter() - t0
+
+        for w in range(args.warmup):
+            one_step(w)
+        lu, secs = 0, 0.0
+        for k in range(args.steps):
+            a, b = one_step(k)
+            lu += a
+            secs += b
     v = lu / secs / 1e9
-    sample = ("per step: one 512^2 member of the 64, 20 LBM steps of the 200-step period, "
-              "then the diagnostic on 1% of the Table 1 random boxes per L (L=2..256)")
+    sample = ("per step: %d of the 512^2 members at once, one per host core (processes), "
+              "each 20 LBM steps of the 200-step period, then the diagnostic on 1%% of the "
+              "Table 1 random boxes per L (L=2..256)" % cores)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),
-            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -303,15 +398,17 @@ def collision_models_leg(P, stream, dev, peak):
 def taylor_green_leg(P, stream, dev):
     """The plain FP64 Taylor-Green case: 64^2, tau 0.6, u0 0.01, 1000 steps
     with the balance at L in {4, 8, 16, 32} every 100 steps.  A 64^2 step
-    cannot fill the GPU, so its time is launch latency: reported per step
-    with plain launches and with graph replay, and for the whole workload
-    (steps, snapshots and its ten balance events, host wall clock)."""
+    cannot fill the GPU, so its time is latency: reported per step with all
+    the steps of a call in one cooperative launch (grid barrier between
+    steps; graph_steps = 0) and with graph replay of per-step launches, the
+    cost of one grid barrier alone, and the whole workload (steps,
+    snapshots and its ten balance events, host wall clock)."""
     import torch
     wl = li.taylor_green_workload()
     n, tau, D, Ls, steps = wl["n"], wl["tau"], wl["diag_every"], wl["Ls"], wl["steps"]
     rho, ux, uy = li.taylor_green(n, u0=wl["u0"])
     out = {"grid": [n, n], "tau": tau, "steps": steps}
-    for key, graph in (("plain", 0), ("graph", 100)):
+    for key, graph in (("cooperative", 0), ("graph", 100)):
         lat = P.Lattice([P.Member(n, n, tau)], precision=64, graph_steps=graph, stream=stream,
                         device=dev)
         lat.init_fields(0, rho, ux, uy)
@@ -326,8 +423,14 @@ def taylor_green_leg(P, stream, dev):
         out["us_per_step_" + key] = us
         out["glups_" + key] = n * n / us / 1e3
         lat.close()
-    lat = P.Lattice([P.Member(n, n, tau)], precision=64, diag_every=D, graph_steps=16,
-                    stream=stream, device=dev)
+    P.probe_grid_barrier(128, 1000, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.probe_grid_barrier(128, 20000, stream=stream)
+    out["grid_barrier_us_128_ctas"] = (time.perf_counter() - t0) * 1e6 / 20000
+    best = "graph" if out["us_per_step_graph"] <= out["us_per_step_cooperative"] else "cooperative"
+    lat = P.Lattice([P.Member(n, n, tau)], precision=64, diag_every=D,
+                    graph_steps=16 if best == "graph" else 0, stream=stream, device=dev)
     lat.init_fields(0, rho, ux, uy)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -336,6 +439,7 @@ def taylor_green_leg(P, stream, dev):
         st = lat.subvolume_balance(0, Ls)
     torch.cuda.synchronize()
     out["workload_ms"] = (time.perf_counter() - t0) * 1e3
+    out["workload_stepping"] = best
     out["balance_events"] = steps // D
     assert np.all(np.isfinite(st[:, 2:, 0]))
     lat.close()
@@ -401,6 +505,229 @@ def three_d_leg(P, stream, dev, peak):
                       "frac": gbs27 / peak},
             "diagnostic_event_ms_fp64_64cubed_all_origins": 1e3 * diag_s,
             "diagnostic_event_ms_fp32_64cubed_all_origins": 1e3 * diag32_s}
+
+
+def alu_peaks(P, stream):
+    """Measured FMA throughput of this GPU (TFLOP/s, two flops per FMA):
+    the ceiling of the kernels bounded by arithmetic rather than HBM."""
+    return {"fp64_tflops": P.probe_fma_rate(64, stream) / 1e12,
+            "fp32_tflops": P.probe_fma_rate(32, stream) / 1e12,
+            "how": "lbm_probe_fma_rate: 8 independent FMA chains per thread, 8 x 256-thread "
+                   "CTAs per SM, CUDA events"}
+
+
+def fp64_instruction_counts():
+    """FP64 flops per lattice update of the FP64 kernels (dadd + dmul +
+    2 dfma, ncu counters) from the committed summary, valid only while the
+    kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "fp64_flops_per_lu.json")
+    if not os.path.exists(p):
+        return {}
+    with open(p) as fh:
+        d = json.load(fh)
+    out = {}
+    for name, rec in d.get("kernels", {}).items():
+        src = os.path.join(ROOT, "paper_1809_06735_gb300", "csrc", rec["source"])
+        with open(src, "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] == rec.get("source_sha256_16"):
+                out[name] = rec["fp64_flops_per_lu"]
+    return out
+
+
+def fp64_plain_leg(P, stream, dev, peak_hbm, peaks, dev_fields=None):
+    """The plain single-instance FP64 step (double buffer, general kernel)
+    on one 4096^2 member (2 x 1.2 GB of populations: far beyond the L2, so
+    the HBM figure means something), against both bounds: 144 algorithmic
+    bytes per update over the measured copy bandwidth, and the FP64 flops
+    per update (ncu counters) over the measured FP64 FMA rate."""
+    import torch
+    n = 4096
+    lat = P.Lattice([P.Member(n, n, 0.52)], precision=64, graph_steps=10, stream=stream,
+                    device=dev)
+    u = li.smooth_fields(n, n, seed=11, amp=0.02, kmax=16)
+    v = li.smooth_fields(n, n, seed=12, amp=0.02, kmax=16)
+    lat.init_fields(0, np.ones((n, n)), u, v)
+    lat.step(10)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    lat.step(20)
+    b.record(stream)
+    torch.cuda.synchronize()
+    secs = a.elapsed_time(b) / 1e3 / 20
+    lat.close()
+    glups = n * n / secs / 1e9
+    gbs = BYTES_PER_LU_F64 * glups
+    flops = fp64_instruction_counts().get("k_step_scalar<double>")
+    out = {"grid": [n, n], "glups": glups, "bytes_per_lu": BYTES_PER_LU_F64,
+           "achieved_gbs": gbs, "hbm_frac": gbs / peak_hbm}
+    if flops is not None:
+        tf = flops * glups / 1e3
+        out.update({"fp64_flops_per_lu": flops, "achieved_fp64_tflops": tf,
+                    "fp64_peak_tflops": peaks["fp64_tflops"],
+                    "fp64_frac": tf / peaks["fp64_tflops"]})
+        out["bound"] = "fp64" if out["fp64_frac"] > out["hbm_frac"] else "hbm"
+        out["frac"] = max(out["fp64_frac"], out["hbm_frac"])
+    return out
+
+
+def forced_sweep_leg(P, stream, dev, peak):
+    """The forced tau-sweep: 15 FP32 members {256, 512, 1024}^2 x tau
+    {0.505, 0.51, 0.52, 0.55, 0.6}, Kolmogorov kf = 4 with drag 1e-4, all in
+    one launch per step (uneven tile table).  One diagnostic period of 200
+    steps: the stream-collide rate (aggregate, and per member: each member
+    advances the same 200 steps in the batch's time) and its roofline, then
+    the balance event of every member at L = 2..512 (L > N skipped) over
+    every periodic origin, timed on its own."""
+    import torch
+    wl = li.forced_sweep_workload()
+    mem = wl["members"]
+    lat = P.Lattice([P.Member(m["n"], m["n"], m["tau"], 1.0, 1, m["kf"], m["F0"], m["alpha"])
+                     for m in mem], precision=32, diag_every=PERIOD, graph_steps=PURE_STEPS - 1,
+                    stream=stream, device=dev)
+    for i, m in enumerate(mem):
+        lat.init_fields(i, *li.random_phase(m["n"], seed=m["seed"], u_rms=wl["u_rms"]))
+    cells = [m["n"] * m["n"] for m in mem]
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    lat.step(PERIOD)  # warm-up period (graphs, snapshots)
+    lat.subvolume_balance_batch(range(len(mem)), wl["Ls"])
+    a, b, c, d = ev(), ev(), ev(), ev()
+    torch.cuda.synchronize()
+    a.record(stream)
+    lat.step(PURE_STEPS)
+    b.record(stream)
+    lat.step(PERIOD - PURE_STEPS)
+    c.record(stream)
+    st = lat.subvolume_balance_batch(range(len(mem)), wl["Ls"])
+    d.record(stream)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(st[:, 0, 2:, 0]))
+    pure_s = a.elapsed_time(b) / 1e3 / PURE_STEPS
+    period_s = a.elapsed_time(c) / 1e3
+    event_s = c.elapsed_time(d) / 1e3
+    tot = sum(cells)
+    glups = tot / pure_s / 1e9
+    gbs = BYTES_PER_LU_F32 * glups
+    lat.close()
+    return {"members": len(mem), "cells": tot, "glups": glups,
+            "per_member_glups": [{"n": m["n"], "tau": m["tau"], "glups": c_ / pure_s / 1e9}
+                                 for m, c_ in zip(mem, cells)],
+            "bytes_per_lu": BYTES_PER_LU_F32, "achieved_gbs": gbs, "frac": gbs / peak,
+            "diagnostic_event_ms_all_origins": 1e3 * event_s, "sizes": list(wl["Ls"]),
+            "glups_with_diagnostic": tot * PERIOD / (period_s + event_s) / 1e9}
+
+
+def large_grid_leg(P, stream, dev, peak):
+    """The large single forced run: one FP32 member of 8192^2, tau 0.51,
+    Kolmogorov kf = 4, drag 1e-5 (smooth seeded initial fields), its
+    stream-collide rate and roofline, and one balance event at
+    L = 2..4096 over all 67 M periodic origins (FP64 statistics), timed on
+    its own and folded into a 100-step diagnostic period."""
+    import torch
+    wl = li.large_forced_workload()
+    n, D = wl["n"], wl["diag_every"]
+    lat = P.Lattice([P.Member(n, n, wl["tau"], 1.0, 1, wl["kf"], wl["F0"], wl["alpha"])],
+                    precision=32, diag_every=D, graph_steps=D - 4, stream=stream, device=dev)
+    r = 1.0 + li.smooth_fields(n, n, seed=7, amp=1e-3, kmax=16)
+    u = li.smooth_fields(n, n, seed=5, amp=0.03, kmax=16)
+    v = li.smooth_fields(n, n, seed=6, amp=0.03, kmax=16)
+    lat.init_fields(0, r, u, v)
+    del r, u, v
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    lat.step(D)
+    lat.subvolume_balance(0, wl["Ls"])  # warm-up event
+    a, b, c, d = ev(), ev(), ev(), ev()
+    torch.cuda.synchronize()
+    a.record(stream)
+    lat.step(D - 3)
+    b.record(stream)
+    lat.step(3)
+    c.record(stream)
+    st = lat.subvolume_balance(0, wl["Ls"])
+    d.record(stream)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(st[:, 2:, 0]))
+    pure_s = a.elapsed_time(b) / 1e3 / (D - 3)
+    glups = n * n / pure_s / 1e9
+    gbs = BYTES_PER_LU_F32 * glups
+    event_s = c.elapsed_time(d) / 1e3
+    period_s = a.elapsed_time(c) / 1e3
+    lat.close()
+    return {"grid": [n, n], "glups": glups, "bytes_per_lu": BYTES_PER_LU_F32,
+            "achieved_gbs": gbs, "frac": gbs / peak, "sizes": list(wl["Ls"]),
+            "diagnostic_event_ms_all_origins": 1e3 * event_s,
+            "boxes_per_event": n * n * len(wl["Ls"]),
+            "glups_with_diagnostic": n * n * D / (period_s + event_s) / 1e9}
+
+
+def adjoint_leg(P, stream, dev, peaks):
+    """The differentiation workload: 256^2, tau 0.55, Kolmogorov kf = 4
+    (drag 1e-4), J = mean over n in [1000, 2000] of the L = 16 box average
+    of the dissipation term, checkpoints every 100 steps; the forward pass
+    (with checkpoints and the objective) and the reverse pass (recomputation
+    of each interval + adjoint sweep) timed end to end with FP64 and FP32
+    forward states, and the adjoint step kernel alone (216 algorithmic bytes
+    per update: the state, the adjoint pulled from the neighbours, the new
+    adjoint; FP64 arithmetic)."""
+    import torch
+    from paper_1809_06735_gb300.adjoint import ObjectiveSpec, adjoint_objective, forward_objective
+    wl = li.adjoint_workload()
+    n, tau, F0 = wl["n"], wl["tau"], wl["F0"]
+    init = P.Lattice([P.Member(n, n, tau)], precision=64, stream=stream, device=dev)
+    init.init_fields(0, *li.random_phase(n, seed=wl["seed"], u_rms=wl["u_rms"]))
+    f0 = init.get_populations(0).clone()
+    init.close()
+    out = {"grid": [n, n], "window": [wl["n0"], wl["n1"]], "L": wl["L"],
+           "checkpoint_every": wl["checkpoint_every"]}
+    for prec in (64, 32):
+        spec = ObjectiveSpec(nx=n, ny=n, kf=wl["kf"], alpha=wl["alpha"], n0=wl["n0"],
+                             n1=wl["n1"], box=wl["box"], L=wl["L"], precision=prec,
+                             checkpoint_every=wl["checkpoint_every"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, ckpts, lat = forward_objective(spec, tau, F0, f0, keep_checkpoints=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        dtau, dF0, _ = adjoint_objective(spec, tau, F0, lat, ckpts)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        lat.close()
+        out["fp%d_forward" % prec] = {
+            "J": float(J), "dJ_dtau": float(dtau), "dJ_dF0": float(dF0),
+            "forward_ms": 1e3 * (t1 - t0), "forward_us_per_step": 1e6 * (t1 - t0) / wl["n1"],
+            "reverse_ms": 1e3 * (t2 - t1),
+            "reverse_us_per_step": 1e6 * (t2 - t1) / (wl["n1"] + 1)}
+    # the adjoint step kernel alone: a sweep over 100 recorded states
+    lat = P.Lattice([P.Member(n, n, tau, 1.0, 1, wl["kf"], F0, wl["alpha"])], precision=64,
+                    stream=stream, device=dev)
+    lat.set_populations(0, f0)
+    K = 100
+    states = torch.empty((K, 9, n, n), dtype=torch.float64, device=dev)
+    lat.record_trajectory(0, states)
+    lam_in = torch.randn((9, n, n), dtype=torch.float64, device=dev) * 1e-3
+    lam_out, lam_tmp = torch.empty_like(lam_in), torch.empty_like(lam_in)
+    acc = torch.zeros(2, dtype=torch.float64, device=dev)
+    zero = np.zeros(K)
+    lat.adjoint_sweep(0, states, lam_in, lam_out, lam_tmp, zero, (0, 0), 1, acc[0:1], acc[1:2])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    lat.adjoint_sweep(0, states, lam_in, lam_out, lam_tmp, zero, (0, 0), 1, acc[0:1], acc[1:2])
+    b.record(stream)
+    torch.cuda.synchronize()
+    lat.close()
+    step_s = a.elapsed_time(b) / 1e3 / K
+    glups = n * n / step_s / 1e9
+    k = {"us_per_step": 1e6 * step_s, "glups": glups, "bytes_per_lu": 216,
+         "achieved_gbs": 216 * glups,
+         "note": "256^2 FP64: 14 MB per step, L2-resident; launch pair k_adjoint + k_adjoint_final"}
+    flops = fp64_instruction_counts().get("k_adjoint")
+    if flops is not None:
+        tf = flops * glups / 1e3
+        k.update({"fp64_flops_per_lu": flops, "achieved_fp64_tflops": tf,
+                  "fp64_frac": tf / peaks["fp64_tflops"], "bound": "fp64"})
+    out["adjoint_kernel"] = k
+    return out
 
 
 def workload_config():
@@ -585,7 +912,6 @@ def run_ours(args):
         host[0, m].copy_(torch.from_numpy(r))
         host[1, m].copy_(torch.from_numpy(u))
         host[2, m].copy_(torch.from_numpy(v))
-    hnp = host.numpy()
     dev_fields = host.to(dev)
     for m in range(M):
         lat.init_fields(m, dev_fields[0, m], dev_fields[1, m], dev_fields[2, m])
@@ -678,41 +1004,33 @@ def run_ours(args):
     fp64_s = a.elapsed_time(b) / 1e3 / 200
     fp64_glups = n * n / fp64_s / 1e9
     del lat64
+    peaks_alu = alu_peaks(P, stream)
+    fp64_big = fp64_plain_leg(P, stream, dev, peak, peaks_alu)
+    forced_sweep = forced_sweep_leg(P, stream, dev, peak)
+    large_grid = large_grid_leg(P, stream, dev, peak)
+    adjoint = adjoint_leg(P, stream, dev, peaks_alu)
     paper_forcing = paper_forcing_leg(P, stream, dev, measured_peaks()[0])
     collisions = collision_models_leg(P, stream, dev, measured_peaks()[0])
     three_d = three_d_leg(P, stream, dev, measured_peaks()[0])
     taylor_green = taylor_green_leg(P, stream, dev)
 
-    # end to end through the public API with host buffers: every step uploads
-    # the initial fields of all members from pinned host memory, runs the
-    # period and reads its statistics back to the host.  Pipelined as a
-    # production caller would: step k's upload (copy stream) and step k-1's
-    # statistics read overlap step k's stream-collide; the diagnostic runs
-    # on the library's diagnostic stream.
+    # end to end through the public API with host buffers: every step passes
+    # the pinned host initial fields of all members to lbm_init_fields_batch
+    # (the initialisation kernel reads them in place over the host link, no
+    # staging copy), runs the period and reads its statistics back to pinned
+    # host memory.  Pipelined as a production caller would: step k-1's
+    # statistics travel to the host (copy stream) while step k steps; the
+    # diagnostic runs on the library's diagnostic stream.
     e2e_steps = max(1, args.steps)
-    dev_in = torch.empty((3, M, n, n), dtype=torch.float64, device=dev)
     copy_stream = torch.cuda.Stream(device=dev)
-    copied, consumed = torch.cuda.Event(), torch.cuda.Event()
     host_stats = torch.empty((e2e_steps + 1, M, len(Ls), 15, 2), dtype=torch.float64,
                              pin_memory=True)
     e2e_buf = [torch.empty((M, len(Ls), 15, 2), dtype=torch.float64, device=dev)
                for _ in range(2)]
 
-    up0, up1 = ev(), ev()  # the first upload: the pipeline fill, not hidden
-
     def e2e_run(nsteps, record):
         for k in range(nsteps):
-            copy_stream.wait_event(consumed)  # the previous step's init has read dev_in
-            if k == 0:
-                up0.record(copy_stream)
-            with torch.cuda.stream(copy_stream):
-                dev_in.copy_(host, non_blocking=True)
-            copied.record(copy_stream)
-            if k == 0:
-                up1.record(copy_stream)
-            stream.wait_event(copied)
-            lat.init_fields_batch(all_members, dev_in[0], dev_in[1], dev_in[2])
-            consumed.record(stream)
+            lat.init_fields_batch(all_members, host[0], host[1], host[2])
             lat.step(PERIOD)
             if k > 0:  # step k-1's statistics to the host while step k runs
                 lat.diag_synchronize()
@@ -727,7 +1045,7 @@ def run_ours(args):
         copy_stream.synchronize()
 
     e2e_run(1, host_stats)  # warm-up: the step graph of the storage parity after a restart
-    runs, uploads = [], []
+    runs = []
     gc.collect()
     gc.disable()  # as in the timed steps above
     for _ in range(3):  # median of three pipelined runs: host-side jitter is one-sided
@@ -736,7 +1054,6 @@ def run_ours(args):
         e2e_run(e2e_steps, host_stats)
         torch.cuda.synchronize()
         runs.append(time.perf_counter() - te)
-        uploads.append(up0.elapsed_time(up1))
     gc.enable()
     assert np.all(np.isfinite(host_stats[:e2e_steps, :, :, 2:, 0].numpy()))
     te = float(np.median(runs))
@@ -745,23 +1062,16 @@ def run_ours(args):
     e2e = {"value": ws * lu_per_gpu_step * e2e_steps / te / 1e9, "unit": "GLUPS",
            "h2d_bytes_per_step": int(M * 3 * n * n * 8),
            "d2h_bytes_per_step": int(M * len(Ls) * 30 * 8),
-           "note": "per step: pinned host fields of all members uploaded (copy stream) and "
-                   "initialised through lbm_init_fields_batch, 200 steps, Table 1 statistics "
-                   "to pinned host memory; step k's upload and step k-1's statistics "
-                   "overlap step k; wall clock over %d steps including pipeline fill and "
-                   "drain, median of 3 runs (%s ms; the first upload, not overlapped: %s ms)"
-                   % (e2e_steps, ", ".join("%.1f" % (1e3 * r) for r in runs),
-                      ", ".join("%.1f" % u for u in uploads))}
+           "note": "per step: the pinned host fields of all members passed as host pointers "
+                   "to lbm_init_fields_batch (read in place by the initialisation kernel), "
+                   "200 steps, Table 1 statistics to pinned host memory; step k-1's "
+                   "statistics travel while step k runs; wall clock over %d steps including "
+                   "pipeline fill and drain, median of 3 runs (%s ms)"
+                   % (e2e_steps, ", ".join("%.1f" % (1e3 * r) for r in runs))}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        lu, secs = oracle_period_sample(wl["seed0"])
-        cpu = {"value": lu / secs / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-               "sample": "one 512^2 member of the 64: the full 200-step period, then the "
-                         "diagnostic on the same Table 1 random boxes (L=2..256)",
-               "seconds": secs}
+        cpu = cpu_baseline_all_cores()
 
     if rank == 0:
         traffic = profiled_traffic()
@@ -780,7 +1090,12 @@ def run_ours(args):
             "step_only_glups_per_gpu": step_glups,
             "diagnostic_event_ms": dict(diag_ms, members=M, sizes=list(Ls)),
             "fp64_plain_single_instance": {"glups": fp64_glups, "grid": [n, n],
-                                           "ratio_batched_fp32_over_fp64": step_glups / fp64_glups},
+                                           "ratio_batched_fp32_over_fp64": step_glups / fp64_glups,
+                                           "roofline_4096sq": fp64_big},
+            "alu_peaks": peaks_alu,
+            "forced_sweep_15_uneven": forced_sweep,
+            "large_forced_8192sq": large_grid,
+            "adjoint_256sq": adjoint,
             "paper_forcing_ensemble": paper_forcing,
             "collision_models": collisions,
             "three_d": three_d,

@@ -156,23 +156,28 @@ int lbm_destroy(lbm_handle *h);
  * same fields, which then must fit each member's grid) to the equilibrium
  * state f_l(x, 0) = f_eq_l(rho(x), u(x)) of eq. (2) and resets the step
  * counter and snapshot history of the handle.  rho, ux, uy: double[ny][nx],
- * host pointers if on_device == 0 (copied through the workspace; the call
- * synchronises, and first waits for a queued lbm_subvolume_balance_async,
- * whose scratch it reuses), device pointers otherwise (queued on the stream;
- * an asynchronous diagnostic still running is not waited for: it reads the
- * snapshot ring, not the populations). */
+ * host pointers if on_device == 0 (pageable memory is copied through the
+ * workspace: the call synchronises, and first waits for a queued
+ * lbm_subvolume_balance_async, whose scratch it reuses; page-locked memory
+ * is read in place like device memory), device pointers otherwise (queued
+ * on the stream; an asynchronous diagnostic still running is not waited
+ * for: it reads the snapshot ring, not the populations). */
 int lbm_init_fields(lbm_handle *h, int member, const double *rho,
                     const double *ux, const double *uy, int on_device);
 
 /* lbm_init_fields for n members at once (the indices in `members`, host
  * array, each listed once, all with the same grid), each from its own
  * fields: rho, ux, uy are double[n][ny][nx] (member members[i] takes block
- * i).  Host pointers (on_device == 0) are copied through the workspace's
- * diagnostic scratch in chunks of whole members, one copy per field and
- * chunk, with a single synchronisation at the end; device pointers are read
- * in place, without waiting for a queued asynchronous diagnostic (as in
- * lbm_init_fields).  With AA storage at an odd step every member must be
- * listed.
+ * i).  Host pointers (on_device == 0) to pageable memory are copied
+ * through the workspace's diagnostic scratch in chunks of whole members,
+ * one copy per field and chunk, with a single synchronisation at the end;
+ * host pointers to page-locked memory (cudaHostAlloc, cudaHostRegister, a
+ * pinned torch tensor; all three fields) and device pointers are read in
+ * place by the initialisation kernel, queued on the stream without a
+ * synchronisation and without waiting for a queued asynchronous diagnostic
+ * (as in lbm_init_fields): the caller keeps page-locked fields unchanged
+ * until the stream has passed the call.  With AA storage at an odd step
+ * every member must be listed.
  * Resets the step counter and snapshot history like lbm_init_fields. */
 int lbm_init_fields_batch(lbm_handle *h, const int *members, int n, const double *rho,
                           const double *ux, const double *uy, int on_device);
@@ -180,7 +185,12 @@ int lbm_init_fields_batch(lbm_handle *h, const int *members, int n, const double
 /* Advances every member by nsteps time steps of eq. (1): per cell, pull the
  * populations from the neighbours x - c_l, take rho and j, form F, collide
  * with the BGK operator and the EDM term, store.  When diag_every > 0 the
- * snapshots of the required time levels are recorded on the way. */
+ * snapshots of the required time levels are recorded on the way.  A handle
+ * of one member below 32768 cells on the general kernel (without force kind
+ * 2) and with graph_steps == 0 runs the consecutive steps between snapshots
+ * in one cooperative launch with a grid-wide barrier between steps (same
+ * arithmetic, bit-identical results); graph_steps > 0 replays CUDA graphs
+ * of per-step launches instead. */
 int lbm_step(lbm_handle *h, int nsteps);
 
 /* Current time step n of the handle (number of steps since init). */
@@ -312,7 +322,10 @@ int lbm_set_populations(lbm_handle *h, int member, const double *f,
                         int on_device);
 
 /* Divergence check of member `member` at the current time: *status = 1 if
- * any population or density is NaN/Inf or rho <= 0, else 0.  Synchronises. */
+ * any population or density is NaN/Inf or rho <= 0, else 0.  Synchronises.
+ * Returns LBM_ERR_TIMEOUT if a step of a small single-member handle (which
+ * runs all the steps of an lbm_step call in one cooperative launch with a
+ * grid-wide barrier between steps) gave up waiting at that barrier. */
 int lbm_member_status(lbm_handle *h, int member, int *status);
 
 /* Adjoint of one time step of member `member` (no counterpart in the paper;
@@ -337,6 +350,53 @@ int lbm_adjoint_step(lbm_handle *h, int member, const double *f_n,
  * one double. */
 int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx,
                              int by, int L, double *acc);
+
+/* The same objective at nsteps consecutive time levels: acc[0] += weight *
+ * (box average at the current time), then one step of every member, nsteps
+ * times, so the handle ends nsteps steps later.  One call replaces nsteps
+ * pairs of lbm_objective_accumulate and lbm_step(h, 1). */
+int lbm_objective_steps(lbm_handle *h, int member, int nsteps, double weight,
+                        int bx, int by, int L, double *acc);
+
+/* Public states of member `member` at nstates consecutive times: states[k]
+ * (device, double[nstates][9][ny][nx]) receives f(t + k) for the current
+ * time t and k = 0 .. nstates - 1, stepping every member nstates - 1 times
+ * in between (the recomputation of a checkpoint interval for the adjoint).
+ * The handle ends at time t + nstates - 1. */
+int lbm_record_trajectory(lbm_handle *h, int member, int nstates,
+                          double *states);
+
+/* lbm_adjoint_step over nstates consecutive time levels, last to first:
+ * states[k] (device, double[nstates][9][ny][nx]) is the public state
+ * f(n + k), lambda_in = dJ/df(n + nstates) (device; NULL for zero) and, for
+ * k = nstates - 1 down to 0, lambda(n + k) = (dS/df)^T lambda(n + k + 1)
+ * + weights[k] * dJ_{n+k}/df, the objective term as in lbm_adjoint_step
+ * with weights a host array of nstates doubles (0 omits a level).  The
+ * result lambda(n) is written to lambda_out; lambda_tmp (device, same size)
+ * is the other half of the ping-pong; lambda_in, lambda_out and lambda_tmp
+ * must be three distinct buffers.  dJ/dtau and dJ/dF0 contributions are
+ * added to the device accumulators as in lbm_adjoint_step. */
+int lbm_adjoint_sweep(lbm_handle *h, int member, const double *states,
+                      int nstates, const double *lambda_in, double *lambda_out,
+                      double *lambda_tmp, const double *weights, int bx, int by,
+                      int L, double *dJ_dtau, double *dJ_dF0);
+
+/* Measured arithmetic ceiling (no counterpart in the paper; a measurement
+ * helper): FP64 (bits = 64) or FP32 (bits = 32) fused multiply-adds of
+ * independent chains on every SM, timed with CUDA events on cuda_stream
+ * (NULL = legacy default stream); *flops_per_s (host) receives the rate,
+ * two flops per FMA.  Synchronises the stream; about 20 ms. */
+int lbm_probe_fma_rate(int bits, void *cuda_stream, double *flops_per_s);
+
+/* The grid-wide barrier of the small-grid persistent step, alone (no
+ * counterpart in the paper; for testing its failure detection): `rounds`
+ * barriers over `ctas` cooperative 32-thread CTAs (ctas no more than can be
+ * co-resident, else LBM_ERR_CUDA).  If withhold >= 0, CTA `withhold` never
+ * arrives: the others give up after their bounded wait (a second at most)
+ * and set the error word, which *gave_up (host) receives (1), without any
+ * device fault.  Synchronises cuda_stream. */
+int lbm_probe_grid_barrier(int ctas, int rounds, int withhold, void *cuda_stream,
+                           int *gave_up);
 
 /* Largest grid (nx * ny cells) that lbm_global_balance_static accepts. */
 #define LBM_STATIC_MAX_CELLS (512 * 512)

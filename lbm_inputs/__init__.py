@@ -115,14 +115,18 @@ def smooth_fields(nx: int, ny: int, seed: int, amp: float = 0.02, kmax: int = 6)
     rng = _rng(seed)
     x = 2.0 * np.pi * np.arange(nx) / nx
     y = 2.0 * np.pi * np.arange(ny) / ny
-    X, Y = np.meshgrid(x, y)
-    out = np.zeros((ny, nx))
+    # each mode c cos(a x + b y + ph) = c [cos(a x + ph) cos(b y) - sin(a x + ph) sin(b y)],
+    # summed as two rank-one products (separable: fast on large grids)
+    cols, rows = [], []
     for _ in range(12):
         a, b = rng.integers(0, kmax + 1, size=2)
         if a == 0 and b == 0:
             continue
         ph = rng.uniform(0, 2 * np.pi)
-        out += rng.standard_normal() * np.cos(a * X + b * Y + ph)
+        c = rng.standard_normal()
+        cols += [c * np.cos(b * y), -c * np.sin(b * y)]
+        rows += [np.cos(a * x + ph), np.sin(a * x + ph)]
+    out = np.stack(cols, axis=1) @ np.stack(rows, axis=0) if cols else np.zeros((ny, nx))
     m = np.max(np.abs(out))
     return amp * out / (m if m > 0 else 1.0)
 

@@ -103,7 +103,12 @@ def load_library(path: str = LIB_PATH):
         "lbm_member_status": ([P, I, P], I),
         "lbm_adjoint_step": ([P, I, P, P, P, D, I, I, I, P, P], I),
         "lbm_objective_accumulate": ([P, I, D, I, I, I, P], I),
+        "lbm_objective_steps": ([P, I, I, D, I, I, I, P], I),
+        "lbm_record_trajectory": ([P, I, I, P], I),
+        "lbm_adjoint_sweep": ([P, I, P, I, P, P, P, P, I, I, I, P, P], I),
         "lbm_last_error": ([P], ctypes.c_char_p),
+        "lbm_probe_fma_rate": ([I, P, P], I),
+        "lbm_probe_grid_barrier": ([I, I, I, P, P], I),
         "lbm3d_workspace_size": ([ctypes.POINTER(_Config3), ctypes.POINTER(S)], I),
         "lbm3d_create": ([ctypes.POINTER(_Config3), P, S, ctypes.POINTER(P)], I),
         "lbm3d_destroy": ([P], I),
@@ -240,11 +245,20 @@ class Lattice:
     def init_fields_batch(self, members, rho, ux, uy):
         """init_fields for several members (equal grids) from stacked fields
         [n, ny, nx]: numpy arrays go through one host copy per field and a
-        single synchronisation, tensors are read on the device."""
+        single synchronisation; CPU tensors are passed as host pointers
+        (pinned ones are read in place by the kernel, asynchronously: keep
+        them unchanged until the stream has passed the call); CUDA tensors
+        are read on the device."""
         mem = np.ascontiguousarray(members, dtype=np.int32)
         if isinstance(rho, np.ndarray):
             r, u, v = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
             on_dev = 0
+        elif not rho.is_cuda:
+            r, u, v = rho, ux, uy
+            for a in (r, u, v):
+                assert a.dtype == self._torch.float64 and a.is_contiguous()
+            on_dev = 0
+            self._keep = (r, u, v)
         else:
             r, u, v = (self._dev(a) for a in (rho, ux, uy))
             on_dev = 1
@@ -425,6 +439,55 @@ class Lattice:
         self._check(self.lib.lbm_objective_accumulate(self.h, member, float(weight),
                                                       int(box[0]), int(box[1]), int(L),
                                                       _ptr(acc)))
+
+    def objective_steps(self, member: int, nsteps: int, weight: float, box, L: int, acc):
+        """nsteps times: acc += weight * (box average at the current time), then
+        one step of every member."""
+        self._check(self.lib.lbm_objective_steps(self.h, member, int(nsteps), float(weight),
+                                                 int(box[0]), int(box[1]), int(L), _ptr(acc)))
+
+    def record_trajectory(self, member: int, states):
+        """states[k] = public state at the current time + k (device tensor
+        [nstates, 9, ny, nx] float64), stepping nstates - 1 times."""
+        assert states.dtype == self._torch.float64 and states.is_cuda
+        self._check(self.lib.lbm_record_trajectory(self.h, member, int(states.shape[0]),
+                                                   _ptr(states)))
+
+    def adjoint_sweep(self, member: int, states, lam_in, lam_out, lam_tmp, weights, box,
+                      L: int, dJ_dtau, dJ_dF0):
+        """Adjoint steps over the levels of ``states`` (last to first), from
+        lam_in = dJ/df(after the last level; None for zero) to lam_out =
+        dJ/df(first level); ``weights`` holds the objective weight of each
+        level; parameter gradients added into dJ_dtau, dJ_dF0."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        assert w.shape == (states.shape[0],)
+        self._check(self.lib.lbm_adjoint_sweep(self.h, member, _ptr(states), int(states.shape[0]),
+                                               _ptr(lam_in), _ptr(lam_out), _ptr(lam_tmp),
+                                               _ptr(w), int(box[0]), int(box[1]), int(L),
+                                               _ptr(dJ_dtau), _ptr(dJ_dF0)))
+
+
+def probe_fma_rate(bits: int, stream=None) -> float:
+    """Measured FMA throughput of the device in flop/s (bits 64 or 32)."""
+    lib = load_library()
+    out = ctypes.c_double()
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    rc = lib.lbm_probe_fma_rate(int(bits), s, ctypes.byref(out))
+    if rc != LBM_OK:
+        raise LBMError(rc, lib.lbm_last_error(None).decode())
+    return out.value
+
+
+def probe_grid_barrier(ctas: int, rounds: int, withhold: int = -1, stream=None) -> int:
+    """Runs the persistent step's grid barrier alone; returns 1 if the CTAs
+    gave up waiting (CTA ``withhold`` never arriving), else 0."""
+    lib = load_library()
+    out = ctypes.c_int(-1)
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    rc = lib.lbm_probe_grid_barrier(int(ctas), int(rounds), int(withhold), s, ctypes.byref(out))
+    if rc != LBM_OK:
+        raise LBMError(rc, lib.lbm_last_error(None).decode())
+    return out.value
 
 
 def workspace_size(members: Sequence[Member], precision: int = 32, diag_every: int = 0,

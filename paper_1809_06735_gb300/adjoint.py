@@ -53,42 +53,48 @@ def forward_objective(spec: ObjectiveSpec, tau: float, F0: float, f0: torch.Tens
     acc = torch.zeros(1, dtype=torch.float64, device=f0.device)
     ckpts = {}
     K = spec.checkpoint_every
-    for n in range(spec.n1 + 1):
+    n = 0
+    while True:
         if keep_checkpoints and n % K == 0:
             ckpts[n] = lat.get_populations(0).clone()
-        if n >= spec.n0:
+        if n == spec.n1:
             lat.objective_accumulate(0, w, spec.box, spec.L, acc)
-        if n < spec.n1:
-            lat.step(1)
+            break
+        target = min((n // K + 1) * K, spec.n1)
+        if n < spec.n0:  # no objective term before n0
+            target = min(target, spec.n0)
+            lat.step(target - n)
+        else:  # objective at n .. target - 1, stepping to target
+            lat.objective_steps(0, target - n, w, spec.box, spec.L, acc)
+        n = target
     return acc[0], ckpts, lat
 
 
 def adjoint_objective(spec: ObjectiveSpec, tau: float, F0: float, lat: Lattice, ckpts: dict):
-    """Gradients (dJ/dtau, dJ/dF0, dJ/df0) by checkpointed reverse sweeps."""
+    """Gradients (dJ/dtau, dJ/dF0, dJ/df0) by checkpointed reverse sweeps:
+    each interval is recomputed from its checkpoint into a device buffer of
+    states, then swept backwards in one library call."""
     dev = next(iter(ckpts.values())).device
     w = 1.0 / (spec.n1 - spec.n0 + 1)
     shape = (9, spec.ny, spec.nx)
-    lam = torch.zeros(shape, dtype=torch.float64, device=dev)
-    lam_next = torch.empty_like(lam)
+    lam_a = torch.empty(shape, dtype=torch.float64, device=dev)
+    lam_b = torch.empty_like(lam_a)
+    lam_tmp = torch.empty_like(lam_a)
     dtau = torch.zeros(1, dtype=torch.float64, device=dev)
     dF0 = torch.zeros(1, dtype=torch.float64, device=dev)
     K = spec.checkpoint_every
-    starts = sorted(ckpts)
-    first = True
-    for c in reversed(starts):
+    states = torch.empty((K,) + shape, dtype=torch.float64, device=dev)
+    lam_in, lam_out = None, lam_a
+    for c in sorted(ckpts, reverse=True):
         hi = min(c + K - 1, spec.n1)
+        ns = hi - c + 1
         lat.set_populations(0, ckpts[c])
-        states = [ckpts[c]]
-        for _ in range(c + 1, hi + 1):
-            lat.step(1)
-            states.append(lat.get_populations(0).clone())
-        for n in range(hi, c - 1, -1):
-            wn = w if n >= spec.n0 else 0.0
-            lat.adjoint_step(0, states[n - c], None if first else lam, lam_next, wn, spec.box,
-                             spec.L, dtau, dF0)
-            first = False
-            lam, lam_next = lam_next, lam
-    return dtau[0], dF0[0], lam
+        lat.record_trajectory(0, states[:ns])
+        weights = [w if c + k >= spec.n0 else 0.0 for k in range(ns)]
+        lat.adjoint_sweep(0, states[:ns], lam_in, lam_out, lam_tmp, weights, spec.box, spec.L,
+                          dtau, dF0)
+        lam_in, lam_out = lam_out, (lam_b if lam_out is lam_a else lam_a)
+    return dtau[0], dF0[0], lam_in
 
 
 class BoxDissipation(torch.autograd.Function):

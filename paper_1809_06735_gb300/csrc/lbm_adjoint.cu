@@ -27,7 +27,7 @@ namespace lbm {
 namespace {
 
 enum AdjField { A_RHO = 0, A_JX, A_JY, A_U, A_V, GAM_XX, GAM_XY, GAM_YY, D_RHO, D_JX, D_JY,
-                A_NFIELDS };
+                D_TOT, S_TAB, A_NFIELDS };  // S_TAB: sin(2 pi kf y/ny) [ny], then of x [nx]
 static_assert(A_NFIELDS <= kDiagFields, "scratch too small");
 
 struct AGrid {
@@ -68,6 +68,23 @@ __device__ __forceinline__ void force_dir(const AGrid &g, int x, int y, double &
   }
 }
 
+// The direction s of dF_ext/dF0 per row and column, tabulated once per
+// adjoint step (the cell kernel then reads two doubles instead of
+// evaluating two FP64 sines, which the FP64 pipe of this part pays for).
+__global__ void k_sine_tables(AGrid g, double *tab) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.ny + g.nx;
+       i += gridDim.x * blockDim.x) {
+    double sx, sy;
+    if (i < g.ny) {
+      force_dir(g, 0, i, sx, sy);
+      tab[i] = sx;
+    } else {
+      force_dir(g, i - g.ny, 0, sx, sy);
+      tab[i] = sy;
+    }
+  }
+}
+
 template <int NQ>
 __device__ void block_sums(double (&v)[NQ], double *out) {
   __shared__ double sh[NQ][32];
@@ -92,9 +109,35 @@ __device__ void block_sums(double (&v)[NQ], double *out) {
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;             \
        c += (size_t)gridDim.x * blockDim.x)
 
-// rho and j of the public state f[9][ny][nx].
-__global__ void k_public_moments(AGrid g, const double *f, double *F) {
-  FOR_CELLS {
+// The objective touches only the box V0 and the cells within the eq. (18)
+// stencil reach (4 cells) of it: the region R = V0 widened by 4 on each
+// side (the whole axis where that covers it).  u is needed on R, Gamma on
+// V0 and dJ/du = -D^T Gamma on R; every other cell has no objective term.
+struct Region {
+  int x0, y0, w, h;  // lower-left corner (wrapped) and extent, w <= nx, h <= ny
+};
+
+__host__ __device__ inline Region objective_region(int nx, int ny, int bx, int by, int L) {
+  Region r;
+  if (L + 8 >= nx) { r.x0 = 0; r.w = nx; } else { r.x0 = ((bx - 4) % nx + nx) % nx; r.w = L + 8; }
+  if (L + 8 >= ny) { r.y0 = 0; r.h = ny; } else { r.y0 = ((by - 4) % ny + ny) % ny; r.h = L + 8; }
+  return r;
+}
+
+__device__ __forceinline__ bool in_region(int x, int y, const Region &r, const AGrid &g) {
+  return wrapi(x - r.x0, g.nx) < r.w && wrapi(y - r.y0, g.ny) < r.h;
+}
+
+#define FOR_REGION(R)                                                                  \
+  const size_t N = (size_t)g.nx * g.ny;                                                \
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (R).w * (R).h;               \
+       i += gridDim.x * blockDim.x)
+
+// rho, j and u = (j + F/2)/rho of the public state f[9][ny][nx] on R.
+__global__ void k_region_velocity(AGrid g, Region R, const double *f, double *F) {
+  FOR_REGION(R) {
+    const int x = wrapi(R.x0 + i % R.w, g.nx), y = wrapi(R.y0 + i / R.w, g.ny);
+    const size_t c = (size_t)y * g.nx + x;
     double r = 0, a = 0, b = 0;
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
@@ -103,13 +146,14 @@ __global__ void k_public_moments(AGrid g, const double *f, double *F) {
       a += cx_of(l) * v;
       b += cy_of(l) * v;
     }
+    const double Fx = g.fxt[y] - g.alpha * a, Fy = g.fyt[x] - g.alpha * b;
     F[A_RHO * N + c] = r;
-    F[A_JX * N + c] = a;
-    F[A_JY * N + c] = b;
+    F[A_U * N + c] = (a + 0.5 * Fx) / r;
+    F[A_V * N + c] = (b + 0.5 * Fy) / r;
   }
 }
 
-// u = (j + F/2)/rho from (rho, j) fields at F + 0..2N.
+// u = (j + F/2)/rho from (rho, j) fields at F + 0..2N (forward objective).
 __global__ void k_velocity(AGrid g, double *F) {
   FOR_CELLS {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
@@ -120,47 +164,65 @@ __global__ void k_velocity(AGrid g, double *F) {
   }
 }
 
-// Objective pass 1: Gamma_ij = dJ/dG_ij = -2 c nu rho S_ij in the box
-// (c = weight / L^2); direct rho part -c nu Q; explicit dJ/dtau part.
+// Objective pass 1, over V0: Gamma_ij = dJ/dG_ij = -2 c nu rho S_ij
+// (c = weight / L^2); explicit dJ/dtau part -c rho Q / 3 (d nu / d tau = 1/3).
 __global__ void k_obj_gamma(AGrid g, double *F, double cw, int bx, int by, int L,
                             double *partials) {
   double acc[1] = {0.0};
-  FOR_CELLS {
-    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
-    double gxx = 0, gxy = 0, gyy = 0, drho = 0;
-    if (in_box(x, y, bx, by, L, g)) {
-      const double *U = F + A_U * N, *V = F + A_V * N;
-      const double dxu = Dx(U, g, x, y), dyu = Dy(U, g, x, y);
-      const double dxv = Dx(V, g, x, y), dyv = Dy(V, g, x, y);
-      const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
-      const double Q = sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv;
-      const double r = F[A_RHO * N + c];
-      gxx = -2.0 * cw * g.nu * r * sxx;
-      gxy = -2.0 * cw * g.nu * r * sxy;
-      gyy = -2.0 * cw * g.nu * r * syy;
-      drho = -cw * g.nu * Q;
-      acc[0] += -cw * r * Q / 3.0;  // d nu / d tau = 1/3
-    }
-    F[GAM_XX * N + c] = gxx;
-    F[GAM_XY * N + c] = gxy;
-    F[GAM_YY * N + c] = gyy;
-    F[D_RHO * N + c] = drho;
+  const size_t N = (size_t)g.nx * g.ny;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
+    const int x = wrapi(bx + i % L, g.nx), y = wrapi(by + i / L, g.ny);
+    const size_t c = (size_t)y * g.nx + x;
+    const double *U = F + A_U * N, *V = F + A_V * N;
+    const double dxu = Dx(U, g, x, y), dyu = Dy(U, g, x, y);
+    const double dxv = Dx(V, g, x, y), dyv = Dy(V, g, x, y);
+    const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
+    const double Q = sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv;
+    const double r = F[A_RHO * N + c];
+    F[GAM_XX * N + c] = -2.0 * cw * g.nu * r * sxx;
+    F[GAM_XY * N + c] = -2.0 * cw * g.nu * r * sxy;
+    F[GAM_YY * N + c] = -2.0 * cw * g.nu * r * syy;
+    F[D_RHO * N + c] = -cw * g.nu * Q;
+    acc[0] += -cw * r * Q / 3.0;
   }
   block_sums<1>(acc, partials + blockIdx.x);
 }
 
-// Objective pass 2: dJ/du_i = -sum_j D_j Gamma_ij, then dJ/drho, dJ/dj and
-// the explicit dJ/dF0 part through u = ((1 - alpha/2) j + F_ext/2)/rho.
-__global__ void k_obj_velocity_adjoint(AGrid g, double *F, double *partials) {
+// Gamma_ij at (x, y), zero outside V0.
+__device__ __forceinline__ double gam(const double *G, const AGrid &g, int x, int y, int bx,
+                                      int by, int L) {
+  return in_box(x, y, bx, by, L, g) ? G[(size_t)y * g.nx + x] : 0.0;
+}
+
+// Objective pass 2, over R: dJ/du_i = -sum_j D_j Gamma_ij (D^T = -D), then
+// dJ/drho (with the direct part of V0), dJ/dj and the explicit dJ/dF0 part
+// through u = ((1 - alpha/2) j + F_ext/2)/rho.
+__global__ void k_obj_velocity_adjoint(AGrid g, Region R, double *F, int bx, int by, int L,
+                                       double *partials) {
   double acc[1] = {0.0};
-  FOR_CELLS {
-    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
-    const double Ux = -(Dx(F + GAM_XX * N, g, x, y) + Dy(F + GAM_XY * N, g, x, y));
-    const double Uy = -(Dx(F + GAM_XY * N, g, x, y) + Dy(F + GAM_YY * N, g, x, y));
+  FOR_REGION(R) {
+    const int x = wrapi(R.x0 + i % R.w, g.nx), y = wrapi(R.y0 + i / R.w, g.ny);
+    const size_t c = (size_t)y * g.nx + x;
+    const double *Gxx = F + GAM_XX * N, *Gxy = F + GAM_XY * N, *Gyy = F + GAM_YY * N;
+    auto dxg = [&](const double *G) {
+      return 0.8 * (gam(G, g, wr(x + 1, g.nx), y, bx, by, L) - gam(G, g, wr(x - 1, g.nx), y, bx, by, L)) -
+             0.2 * (gam(G, g, wr(x + 2, g.nx), y, bx, by, L) - gam(G, g, wr(x - 2, g.nx), y, bx, by, L)) +
+             (4.0 / 105.0) * (gam(G, g, wr(x + 3, g.nx), y, bx, by, L) - gam(G, g, wr(x - 3, g.nx), y, bx, by, L)) -
+             (1.0 / 280.0) * (gam(G, g, wr(x + 4, g.nx), y, bx, by, L) - gam(G, g, wr(x - 4, g.nx), y, bx, by, L));
+    };
+    auto dyg = [&](const double *G) {
+      return 0.8 * (gam(G, g, x, wr(y + 1, g.ny), bx, by, L) - gam(G, g, x, wr(y - 1, g.ny), bx, by, L)) -
+             0.2 * (gam(G, g, x, wr(y + 2, g.ny), bx, by, L) - gam(G, g, x, wr(y - 2, g.ny), bx, by, L)) +
+             (4.0 / 105.0) * (gam(G, g, x, wr(y + 3, g.ny), bx, by, L) - gam(G, g, x, wr(y - 3, g.ny), bx, by, L)) -
+             (1.0 / 280.0) * (gam(G, g, x, wr(y + 4, g.ny), bx, by, L) - gam(G, g, x, wr(y - 4, g.ny), bx, by, L));
+    };
+    const double Ux = -(dxg(Gxx) + dyg(Gxy));
+    const double Uy = -(dxg(Gxy) + dyg(Gyy));
     const double r = F[A_RHO * N + c], u = F[A_U * N + c], v = F[A_V * N + c];
-    F[D_RHO * N + c] += -(Ux * u + Uy * v) / r;
+    const double direct = in_box(x, y, bx, by, L, g) ? F[D_RHO * N + c] : 0.0;
     F[D_JX * N + c] = Ux * (1.0 - 0.5 * g.alpha) / r;
     F[D_JY * N + c] = Uy * (1.0 - 0.5 * g.alpha) / r;
+    F[D_TOT * N + c] = direct - (Ux * u + Uy * v) / r;
     double sx, sy;
     force_dir(g, x, y, sx, sy);
     acc[0] += (Ux * sx + Uy * sy) / (2.0 * r);
@@ -168,9 +230,34 @@ __global__ void k_obj_velocity_adjoint(AGrid g, double *F, double *partials) {
   block_sums<1>(acc, partials + blockIdx.x);
 }
 
-// Adjoint of one step (see the header comment).  with_obj adds dJ_n/df.
-__global__ void k_adjoint(AGrid g, const double *f, const double *lam_in, double *lam_out,
-                          const double *F, int with_obj, double *partials) {
+// t_l-weighted sums over the populations of the pulled adjoint mu_l and
+// their contractions with the equilibrium's derivatives.  With
+//   feq_l(rho, m) = t_l [rho + 3 c.m + (4.5 (c.m)^2 - 1.5 |m|^2) / rho]
+// and the moments M0 = sum t mu, M_a = sum t c_a mu, M_ab = sum t c_a c_b mu:
+//   sum mu d_rho feq(rho, m) = M0 - (4.5 m.M2.m - 1.5 |m|^2 M0) / rho^2,
+//   sum mu d_m   feq(rho, m) = 3 M1 + (9 M2.m - 3 m M0) / rho,
+//   sum mu feq(rho, m)       = rho M0 + 3 m.M1 + (4.5 m.M2.m - 1.5 |m|^2 M0) / rho.
+struct MuMoments {
+  double m0, mx, my, mxx, mxy, myy;
+};
+
+__device__ __forceinline__ MuMoments mu_moments(const double (&mu)[kQ]) {
+  constexpr double t1 = 1.0 / 9.0, t2 = 1.0 / 36.0;
+  MuMoments M;
+  const double diag = mu[5] + mu[6] + mu[7] + mu[8];
+  M.m0 = (4.0 / 9.0) * mu[0] + t1 * (mu[1] + mu[2] + mu[3] + mu[4]) + t2 * diag;
+  M.mx = t1 * (mu[1] - mu[3]) + t2 * (mu[5] - mu[6] - mu[7] + mu[8]);
+  M.my = t1 * (mu[2] - mu[4]) + t2 * (mu[5] + mu[6] - mu[7] - mu[8]);
+  M.mxx = t1 * (mu[1] + mu[3]) + t2 * diag;
+  M.myy = t1 * (mu[2] + mu[4]) + t2 * diag;
+  M.mxy = t2 * (mu[5] - mu[6] + mu[7] - mu[8]);
+  return M;
+}
+
+// Adjoint of one step (see the header comment).  with_obj adds dJ_n/df on
+// the objective region R.
+__global__ void k_adjoint(AGrid g, Region R, const double *f, const double *lam_in,
+                          double *lam_out, const double *F, int with_obj, double *partials) {
   double acc[2] = {0.0, 0.0};
   FOR_CELLS {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
@@ -188,65 +275,75 @@ __global__ void k_adjoint(AGrid g, const double *f, const double *lam_in, double
     const double ir = 1.0 / rho;
     const double mpx = (1.0 - g.alpha) * jx + g.fxt[y];
     const double mpy = (1.0 - g.alpha) * jy + g.fyt[x];
-    const double jj = jx * jx + jy * jy, mm = mpx * mpx + mpy * mpy;
-    double sx, sy;
-    force_dir(g, x, y, sx, sy);
+    const MuMoments M = mu_moments(mu);
+    // equilibrium at (rho, j): q_a = m.M2.m, p_a = M2.m
+    const double pax = M.mxx * jx + M.mxy * jy, pay = M.mxy * jx + M.myy * jy;
+    const double qa = (4.5 * (jx * pax + jy * pay) - 1.5 * (jx * jx + jy * jy) * M.m0) * ir;
+    // at (rho, m')
+    const double pbx = M.mxx * mpx + M.mxy * mpy, pby = M.mxy * mpx + M.myy * mpy;
+    const double qb = (4.5 * (mpx * pbx + mpy * pby) - 1.5 * (mpx * mpx + mpy * mpy) * M.m0) * ir;
     const double w1 = g.omega - 1.0;
-    double Arho = 0, Ajx = 0, Ajy = 0, dtau = 0, dF0 = 0;
+    const double Sa_rho = M.m0 - qa * ir, Sb_rho = M.m0 - qb * ir;
+    const double Sa_x = 3.0 * M.mx + (9.0 * pax - 3.0 * jx * M.m0) * ir;
+    const double Sa_y = 3.0 * M.my + (9.0 * pay - 3.0 * jy * M.m0) * ir;
+    const double Sb_x = 3.0 * M.mx + (9.0 * pbx - 3.0 * mpx * M.m0) * ir;
+    const double Sb_y = 3.0 * M.my + (9.0 * pby - 3.0 * mpy * M.m0) * ir;
+    double Arho = w1 * Sa_rho + Sb_rho;
+    double Ajx = w1 * Sa_x + (1.0 - g.alpha) * Sb_x;
+    double Ajy = w1 * Sa_y + (1.0 - g.alpha) * Sb_y;
+    // sum mu (f - feq(rho, j)) for dJ/dtau
+    double muf = 0.0;
 #pragma unroll
-    for (int l = 0; l < kQ; ++l) {
-      const double t = w_of(l);
-      const double cxl = cx_of(l), cyl = cy_of(l);
-      const double cj = cxl * jx + cyl * jy, cm = cxl * mpx + cyl * mpy;
-      // equilibrium at (rho, j) and its derivatives
-      const double feq = t * (rho + 3.0 * cj + (4.5 * cj * cj - 1.5 * jj) * ir);
-      const double drho_a = t * (1.0 - (4.5 * cj * cj - 1.5 * jj) * ir * ir);
-      const double dmx_a = t * (3.0 * cxl + (9.0 * cj * cxl - 3.0 * jx) * ir);
-      const double dmy_a = t * (3.0 * cyl + (9.0 * cj * cyl - 3.0 * jy) * ir);
-      // at (rho, m')
-      const double drho_b = t * (1.0 - (4.5 * cm * cm - 1.5 * mm) * ir * ir);
-      const double dmx_b = t * (3.0 * cxl + (9.0 * cm * cxl - 3.0 * mpx) * ir);
-      const double dmy_b = t * (3.0 * cyl + (9.0 * cm * cyl - 3.0 * mpy) * ir);
-      const double m = mu[l];
-      Arho += m * (w1 * drho_a + drho_b);
-      Ajx += m * (w1 * dmx_a + (1.0 - g.alpha) * dmx_b);
-      Ajy += m * (w1 * dmy_a + (1.0 - g.alpha) * dmy_b);
-      dtau += m * (fl[l] - feq);
-      dF0 += m * (dmx_b * sx + dmy_b * sy);
+    for (int l = 0; l < kQ; ++l) muf += mu[l] * fl[l];
+    const double mufeq = rho * M.m0 + 3.0 * (jx * M.mx + jy * M.my) + qa;
+    const double sx = F[S_TAB * N + y], sy = F[S_TAB * N + g.ny + x];
+    acc[0] += (muf - mufeq) * g.omega * g.omega;  // / tau^2
+    acc[1] += Sb_x * sx + Sb_y * sy;
+    if (with_obj && in_region(x, y, R, g)) {
+      Arho += F[D_TOT * N + c];
+      Ajx += F[D_JX * N + c];
+      Ajy += F[D_JY * N + c];
     }
-    double orho = 0, ojx = 0, ojy = 0;
-    if (with_obj) {
-      orho = F[D_RHO * N + c];
-      ojx = F[D_JX * N + c];
-      ojy = F[D_JY * N + c];
-    }
+    const double keep = 1.0 - g.omega;
 #pragma unroll
     for (int l = 0; l < kQ; ++l)
-      lam_out[(size_t)l * N + c] = (1.0 - g.omega) * mu[l] + Arho + cx_of(l) * Ajx +
-                                   cy_of(l) * Ajy + orho + cx_of(l) * ojx + cy_of(l) * ojy;
-    acc[0] += dtau / (g.tau * g.tau);
-    acc[1] += dF0;
+      lam_out[(size_t)l * N + c] = keep * mu[l] + Arho + cx_of(l) * Ajx + cy_of(l) * Ajy;
   }
   block_sums<2>(acc, partials + 2 * blockIdx.x);
 }
 
-// Adds every partial, in block order, into the two accumulators.
-__global__ void k_adjoint_final(const double *p_step, int nb, const double *p_tau,
-                                const double *p_F0, int nbo, int with_obj, double *dJ_dtau,
-                                double *dJ_dF0) {
-  if (threadIdx.x != 0) return;
+// Adds every partial into the two accumulators: thread i sums the partials
+// i, i + 256, ... in order, then a fixed-order tree in shared memory (the
+// same order every call: block-deterministic).
+__global__ void __launch_bounds__(256) k_adjoint_final(const double *p_step, int nb,
+                                                       const double *p_tau, int nbo,
+                                                       const double *p_F0, int nbr, int with_obj,
+                                                       double *dJ_dtau, double *dJ_dF0) {
+  __shared__ double sa[256], sb[256];
+  const int t = threadIdx.x;
   double a = 0.0, b = 0.0;
-  for (int i = 0; i < nb; ++i) {
+  for (int i = t; i < nb; i += 256) {
     a += p_step[2 * i];
     b += p_step[2 * i + 1];
   }
-  if (with_obj)
-    for (int i = 0; i < nbo; ++i) {
-      a += p_tau[i];
-      b += p_F0[i];
+  if (with_obj) {
+    for (int i = t; i < nbo; i += 256) a += p_tau[i];
+    for (int i = t; i < nbr; i += 256) b += p_F0[i];
+  }
+  sa[t] = a;
+  sb[t] = b;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) {
+      sa[t] += sa[t + w];
+      sb[t] += sb[t + w];
     }
-  if (dJ_dtau) *dJ_dtau += a;
-  if (dJ_dF0) *dJ_dF0 += b;
+    __syncthreads();
+  }
+  if (t == 0) {
+    if (dJ_dtau) *dJ_dtau += sa[0];
+    if (dJ_dF0) *dJ_dF0 += sb[0];
+  }
 }
 
 // Forward objective on (rho, j): acc += weight / L^2 * sum_box eps.
@@ -267,11 +364,19 @@ __global__ void k_obj_forward(AGrid g, const double *F, double cw, int bx, int b
   block_sums<1>(acc, partials + blockIdx.x);
 }
 
-__global__ void k_obj_forward_final(const double *partials, int nb, double cw, double *acc) {
-  if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(256) k_obj_forward_final(const double *partials, int nb,
+                                                           double cw, double *acc) {
+  __shared__ double sa[256];
+  const int t = threadIdx.x;
   double a = 0.0;
-  for (int i = 0; i < nb; ++i) a += partials[i];
-  *acc += cw * a;
+  for (int i = t; i < nb; i += 256) a += partials[i];
+  sa[t] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) sa[t] += sa[t + w];
+    __syncthreads();
+  }
+  if (t == 0) *acc += cw * sa[0];
 }
 
 AGrid agrid(const Member &hm) {
@@ -305,22 +410,27 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
   const int nb = nblocks_for(N);
   double *F = sc.f;
   double *p_step = sc.partials;                         // [nb][2]
-  double *p_tau = p_step + 2 * kMaxPartialBlocks;       // [nb]
-  double *p_F0 = p_tau + kMaxPartialBlocks;             // [nb]
+  double *p_tau = p_step + 2 * kMaxPartialBlocks;       // [nbo]
+  double *p_F0 = p_tau + kMaxPartialBlocks;             // [nbr]
   const int with_obj = w != 0.0;
+  const Region R = objective_region(hm.nx, hm.ny, bx, by, L);
+  int nbo = 0, nbr = 0;
   if (with_obj) {
     const double cw = w / ((double)L * (double)L);
-    k_public_moments<<<nb, 256, 0, s>>>(g, f_n, F);
-    k_velocity<<<nb, 256, 0, s>>>(g, F);
-    k_obj_gamma<<<nb, 256, 0, s>>>(g, F, cw, bx, by, L, p_tau);
-    k_obj_velocity_adjoint<<<nb, 256, 0, s>>>(g, F, p_F0);
+    nbr = nblocks_for((size_t)R.w * R.h);
+    nbo = nblocks_for((size_t)L * L);
+    k_region_velocity<<<nbr, 256, 0, s>>>(g, R, f_n, F);
+    k_obj_gamma<<<nbo, 256, 0, s>>>(g, F, cw, bx, by, L, p_tau);
+    k_obj_velocity_adjoint<<<nbr, 256, 0, s>>>(g, R, F, bx, by, L, p_F0);
   }
-  k_adjoint<<<nb, 256, 0, s>>>(g, f_n, lam_in, lam_out, F, with_obj, p_step);
-  k_adjoint_final<<<1, 32, 0, s>>>(p_step, nb, p_tau, p_F0, nb, with_obj, dJ_dtau, dJ_dF0);
+  k_sine_tables<<<(hm.nx + hm.ny + 255) / 256, 256, 0, s>>>(g, F + S_TAB * N);
+  k_adjoint<<<nb, 256, 0, s>>>(g, R, f_n, lam_in, lam_out, F, with_obj, p_step);
+  k_adjoint_final<<<1, 256, 0, s>>>(p_step, nb, p_tau, nbo, p_F0, nbr, with_obj, dJ_dtau,
+                                    dJ_dF0);
   return cudaGetLastError();
 }
 
-int adjoint_kernel_count(double w) { return w != 0.0 ? 6 : 2; }
+int adjoint_kernel_count(double w) { return w != 0.0 ? 6 : 3; }
 
 // Forward objective from the (rho, j) snapshot already written to sc.f[0..2].
 cudaError_t objective_from_snapshot(const Member &hm, double w, int bx, int by, int L,
@@ -331,7 +441,7 @@ cudaError_t objective_from_snapshot(const Member &hm, double w, int bx, int by, 
   k_velocity<<<nblocks_for(N), 256, 0, s>>>(g, F);
   const int nb = nblocks_for((size_t)L * L);
   k_obj_forward<<<nb, 256, 0, s>>>(g, F, 0.0, bx, by, L, sc.partials);
-  k_obj_forward_final<<<1, 32, 0, s>>>(sc.partials, nb, w / ((double)L * (double)L), acc);
+  k_obj_forward_final<<<1, 256, 0, s>>>(sc.partials, nb, w / ((double)L * (double)L), acc);
   return cudaGetLastError();
 }
 

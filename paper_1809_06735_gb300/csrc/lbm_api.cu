@@ -31,7 +31,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 thread_local std::string g_last_error = "no error";
 
 struct Layout {
-  size_t members, tiles, status;
+  size_t members, tiles, status, sync;
   std::vector<size_t> pop0, pop1, fx, fy, fx64, fy64, snap;
   std::vector<size_t> ft, ft64, trig, trig64, damp, damp_f, damp_ring, proj, drows, pcount;
   std::vector<size_t> nu_ring;  // variable viscosity: local viscosity per snapshot slot
@@ -170,6 +170,7 @@ Layout make_layout(const lbm_config *cfg) {
   }
   L.tiles = take(sizeof(Tile) * std::max<size_t>(max_tiles, 1));
   L.status = take(sizeof(int) * n);
+  L.sync = take(4 * sizeof(unsigned));  // persistent small-grid step: count, gen, err
   L.Nmax = 0;
   for (int m = 0; m < n; ++m) {
     const lbm_member_cfg &c = cfg->members[m];
@@ -255,6 +256,8 @@ struct lbm_handle {
   lbm::LaunchCfg lc{8, 1, 0, 0};
   int graph_k = 0;
   cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // by storage state
+  int persist_ctas = 0;  // > 0: one small general-kernel member, steps in one cooperative launch
+  lbm::GridSync gsync{};
   float tuned_ms = 0.f;  // autotuned time of one step, ms (0: not tuned)
   long long launches = 0;  // kernels issued (graph replays count their nodes)
   std::string err = "no error";
@@ -373,6 +376,18 @@ int get_graph(lbm_handle *h, int cur, cudaGraphExec_t *out) {
 }
 
 int run_steps(lbm_handle *h, long long k) {
+  if (h->persist_ctas > 0 && k >= 2) {  // a small grid: the whole run in one launch
+    while (k > 0) {
+      const int n = (int)std::min<long long>(k, 1 << 30);
+      CK(lbm::launch_step_scalar_persistent(h->precision, h->d_members, h->scalar_members[0],
+                                            h->cur, n, h->persist_ctas, h->gsync, h->stream));
+      h->launches += 1;
+      if (n & 1) h->cur ^= 1;
+      h->t += n;
+      k -= n;
+    }
+    return LBM_OK;
+  }
   while (k > 0) {
     if (h->graph_k > 0 && k >= h->graph_k) {
       cudaGraphExec_t g;
@@ -667,11 +682,29 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
     return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
   h->cur = cfg->storage == 1 ? 2 : 0;
   h->lc.paper_force = h->has_kind2 || h->has_vv ? 1 : 0;
+  {
+    unsigned *w = reinterpret_cast<unsigned *>(ws_at(h, lay.sync));
+    h->gsync = lbm::GridSync{w, w + 1, reinterpret_cast<int *>(w + 2)};
+    e = cudaMemsetAsync(w, 0, 4 * sizeof(unsigned), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess)
+      return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
+  }
   rc = build_tiles(h);
   if (rc == LBM_OK) rc = autotune(h);
   if (rc != LBM_OK) {
     std::string msg = h->err;
     return cleanup(fail(nullptr, rc, msg));
+  }
+  // one small member on the general kernel without the paper forcing (whose
+  // damping needs a projection launch per step), no graph replay asked for:
+  // all the steps of a run in one cooperative launch
+  {
+    const lbm_member_cfg &c0 = h->mcfg[0];
+    if (h->cfg.graph_steps == 0 && h->mcfg.size() == 1 && h->ntiles == 0 &&
+        h->scalar_members.size() == 1 && !h->has_kind2 &&
+        (long long)c0.nx * c0.ny < lbm::kPersistMaxCells)
+      h->persist_ctas = lbm::persistent_ctas(h->precision, (long long)c0.nx * c0.ny);
   }
   *out = h;
   return LBM_OK;
@@ -689,6 +722,29 @@ int lbm_destroy(lbm_handle *h) {
   return LBM_OK;
 }
 
+// The device's address of page-locked host memory (cudaHostAlloc /
+// cudaHostRegister, e.g. a pinned torch tensor), or nullptr for pageable
+// memory: init kernels read such fields in place over the host link.
+const double *mapped_host(const double *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // pageable memory on older drivers: not an error here
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return static_cast<const double *>(a.devicePointer);
+}
+
+// Host fields all page-locked: their device addresses, read in place.
+bool map_host_fields(const double *&r, const double *&u, const double *&v) {
+  const double *mr = mapped_host(r), *mu = mapped_host(u), *mv = mapped_host(v);
+  if (!mr || !mu || !mv) return false;
+  r = mr;
+  u = mu;
+  v = mv;
+  return true;
+}
+
 int lbm_init_fields(lbm_handle *h, int member, const double *rho, const double *ux,
                     const double *uy, int on_device) {
   if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
@@ -702,6 +758,7 @@ int lbm_init_fields(lbm_handle *h, int member, const double *rho, const double *
       return fail(h, LBM_ERR_ARG, "shared init fields need equal grids");
   const size_t N = (size_t)nx * ny;
   const double *r = rho, *u = ux, *v = uy;
+  if (!on_device && map_host_fields(r, u, v)) on_device = 1;  // page-locked: read in place
   // host fields are staged in the diagnostic scratch: wait for a queued
   // asynchronous diagnostic; device fields only overwrite the populations,
   // which the diagnostic never reads (it works on the snapshot ring)
@@ -750,6 +807,7 @@ int lbm_init_fields_batch(lbm_handle *h, const int *members, int n, const double
     return fail(h, LBM_ERR_ARG, "AA storage: initialise every member (or at an even step)");
   const int nx = h->mcfg[members[0]].nx, ny = h->mcfg[members[0]].ny;
   const size_t N = (size_t)nx * ny;
+  if (!on_device && map_host_fields(rho, ux, uy)) on_device = 1;  // page-locked: read in place
   if (!on_device)  // staging in the diagnostic scratch (see lbm_init_fields)
     if (int rc = wait_diag(h)) return rc;
   if (h->cur >= 2) h->cur = 2;  // AA storage restarts at its even phase
@@ -1203,7 +1261,11 @@ int lbm_member_status(lbm_handle *h, int member, int *status) {
   CK(lbm::launch_status(h->precision, h->d_members, member, c.nx, c.ny, h->cur, h->stream));
   h->launches += 1;
   CK(cudaMemcpyAsync(status, h->hm[member].status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  int gave_up = 0;
+  CK(cudaMemcpyAsync(&gave_up, h->gsync.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (gave_up)
+    return fail(h, LBM_ERR_TIMEOUT, "a persistent step kernel gave up waiting at its grid barrier");
   return LBM_OK;
 }
 
@@ -1246,6 +1308,74 @@ int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx, i
                           h->stream));
   CK(lbm::objective_from_snapshot(h->hm[member], weight, bx, by, L, acc, h->sc, h->stream));
   h->launches += 4;
+  return LBM_OK;
+}
+
+int lbm_objective_steps(lbm_handle *h, int member, int nsteps, double weight, int bx, int by,
+                        int L, double *acc) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps must be >= 0");
+  for (int k = 0; k < nsteps; ++k) {
+    if (int rc = lbm_objective_accumulate(h, member, weight, bx, by, L, acc)) return rc;
+    if (int rc = lbm_step(h, 1)) return rc;
+  }
+  return LBM_OK;
+}
+
+int lbm_record_trajectory(lbm_handle *h, int member, int nstates, double *states) {
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  if (!states) return fail(h, LBM_ERR_ARG, "states is NULL");
+  if (nstates < 1) return fail(h, LBM_ERR_ARG, "nstates must be >= 1");
+  const lbm_member_cfg &c = h->mcfg[member];
+  const size_t N = (size_t)c.nx * c.ny;
+  for (int k = 0; k < nstates; ++k) {
+    if (k > 0)
+      if ((rc = lbm_step(h, 1))) return rc;
+    if ((rc = lbm_get_populations(h, member, states + (size_t)k * 9 * N, 1))) return rc;
+  }
+  return LBM_OK;
+}
+
+int lbm_adjoint_sweep(lbm_handle *h, int member, const double *states, int nstates,
+                      const double *lambda_in, double *lambda_out, double *lambda_tmp,
+                      const double *weights, int bx, int by, int L, double *dJ_dtau,
+                      double *dJ_dF0) {
+  int rc = check_member(h, member);
+  if (rc) return rc;
+  if (!states || !lambda_out || !lambda_tmp || !weights)
+    return fail(h, LBM_ERR_ARG, "states, lambda_out, lambda_tmp and weights must not be NULL");
+  if (nstates < 1) return fail(h, LBM_ERR_ARG, "nstates must be >= 1");
+  if (lambda_out == lambda_tmp || lambda_in == lambda_out || lambda_in == lambda_tmp)
+    return fail(h, LBM_ERR_ARG, "lambda_in, lambda_out and lambda_tmp must be distinct");
+  const lbm_member_cfg &c = h->mcfg[member];
+  const size_t N = (size_t)c.nx * c.ny;
+  const double *in = lambda_in;
+  for (int k = nstates - 1; k >= 0; --k) {
+    double *out = (k % 2 == 0) ? lambda_out : lambda_tmp;
+    rc = lbm_adjoint_step(h, member, states + (size_t)k * 9 * N, in, out, weights[k], bx, by,
+                          L, dJ_dtau, dJ_dF0);
+    if (rc) return rc;
+    in = out;
+  }
+  return LBM_OK;
+}
+
+int lbm_probe_fma_rate(int bits, void *cuda_stream, double *flops_per_s) {
+  if (bits != 32 && bits != 64) return fail(nullptr, LBM_ERR_ARG, "bits must be 32 or 64");
+  if (!flops_per_s) return fail(nullptr, LBM_ERR_ARG, "flops_per_s is NULL");
+  cudaError_t e = lbm::probe_fma_rate(bits, static_cast<cudaStream_t>(cuda_stream), flops_per_s);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_probe_grid_barrier(int ctas, int rounds, int withhold, void *cuda_stream,
+                           int *gave_up) {
+  if (ctas < 1 || ctas > 4096 || rounds < 0 || withhold >= ctas || !gave_up)
+    return fail(nullptr, LBM_ERR_ARG, "need 1 <= ctas <= 4096, rounds >= 0, withhold < ctas");
+  cudaError_t e = lbm::barrier_probe(ctas, rounds, withhold,
+                                     static_cast<cudaStream_t>(cuda_stream), gave_up);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
   return LBM_OK;
 }
 

@@ -152,6 +152,19 @@ cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tile
                                      cudaStream_t s);
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member,
                                int nx, int ny, int cur, cudaStream_t s);
+// Grid-wide barrier words of the persistent small-grid step (device memory,
+// zeroed by each launch): arrival count, generation, error flag.
+struct GridSync {
+  unsigned *count, *gen;
+  int *err;
+};
+constexpr int kPersistThreads = 32;
+constexpr long long kPersistMaxCells = 1LL << 15;  // grids below this take the persistent path
+int persistent_ctas(int precision, long long ncells);
+cudaError_t barrier_probe(int ctas, int rounds, int withhold, cudaStream_t s, int *gave_up);
+cudaError_t launch_step_scalar_persistent(int precision, const Member *d_members, int member,
+                                          int state, int nsteps, int ctas, GridSync gs,
+                                          cudaStream_t s);
 // Member indices of one batched launch (kernel parameter).
 struct InitList {
   static constexpr int kMax = 256;
@@ -265,4 +278,5 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
 cudaError_t objective_from_snapshot(const Member &hm, double w, int bx, int by, int L,
                                     double *acc, const DiagScratch &sc, cudaStream_t s);
 int adjoint_kernel_count(double w);
+cudaError_t probe_fma_rate(int bits, cudaStream_t s, double *flops_per_s);
 }  // namespace lbm

@@ -142,8 +142,8 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
   }
   if (ymax < (sizeof(T) == 4 ? T(1e-7) : T(1e-12))) return T(2);
   T lo = T(1), hi = amax * (sizeof(T) == 4 ? T(1 - 1e-6) : T(1 - 1e-12));
-  if (entropy_gap<T>(f, y, S2, hi) < T(0)) return T(2);
   if constexpr (sizeof(T) == 8) {
+    if (entropy_gap<T>(f, y, S2, hi) < T(0)) return T(2);
     for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
       const T mid = T(0.5) * (lo + hi);
       if (entropy_gap<T>(f, y, S2, mid) < T(0))
@@ -153,7 +153,24 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
     }
     return T(0.5) * (lo + hi);
   } else {
-    T a = fmin(T(2), T(0.5) * (lo + hi));
+    // Start near the root: the entropy condition g(a) / a = 0 expanded in
+    // powers of y = Delta / f about the BGK value a = 2 (phi(z) = z^2/2 -
+    // z^3/6 + z^4/12 - ..., ln(1 + y) likewise) gives
+    //   a = 2 + (T3 - 2 T4) / (3 T2) + O(y^2),  T_k = sum_l f_l y_l^k,
+    // about y times closer than a = 2; one Newton step from it usually lands
+    // at the FP32 rounding level.  The bracket's upper end is only checked
+    // when that step does not settle.
+    T T2 = T(0), T3 = T(0), T4 = T(0);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const T q = f[l] * y[l] * y[l];
+      T2 += q;
+      T3 += q * y[l];
+      T4 += q * y[l] * y[l];
+    }
+    T a = T(2) + (T3 - T(2) * T4) / (T(3) * T2);
+    if (!(a > lo && a < hi)) a = fmin(T(2), T(0.5) * (lo + hi));
+    bool bracketed = false;
     for (int it = 0; it < 30; ++it) {
       // g(a) and g'(a) = sum Delta ln(1 + a y) - S2 share ln(1 + a y): one
       // log1p per population (phi as entropy_gap evaluates it)
@@ -186,6 +203,13 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
       T an = a - g / dg;
       const bool inside = an > lo && an < hi;
       if (conv) return inside ? an : a;
+      // Newton on the convex g converges quadratically: a step below 1e-3 a
+      // leaves an error of order 1e-6 a, the FP32 rounding level of the root
+      if (inside && fabs(an - a) < T(1e-3) * a) return an;
+      if (!bracketed) {  // no root below the positivity limit: the BGK value
+        bracketed = true;
+        if (entropy_gap<T>(f, y, S2, hi) < T(0)) return T(2);
+      }
       if (!inside) an = T(0.5) * (lo + hi);  // left the bracket: bisect
       const bool done = fabs(an - a) < T(1e-6) * a;
       a = an;
@@ -296,16 +320,30 @@ __device__ __forceinline__ void collide_f32(float g[kQ], float rho0, float om, f
 
 // FP64 plain form on the full populations f_l; coll != 0: omega from the
 // local relaxation time (Pi^neq = sum c c f - rho cs^2 I - rho u u).
+// The populations go in opposite pairs (l, opp(l)), c_opp = -c_l: the
+// equilibrium and the exact-difference term split into a part even in c
+// (the same for both) and an odd part (opposite signs), each formed once:
+//   feq = t rho [1 - 1.5 |u|^2 + 4.5 (c.u)^2] +- 3 t rho |c.u|,
+//   F_l = t rho [9 (c.u)(c.du) + 4.5 (c.du)^2 - 1.5 (2 u.du + |du|^2)] +- 3 t rho |c.du|,
+// (du = F / rho), which halves the FP64 work (FP64 is this part's slow pipe).
+__device__ __forceinline__ void collide_pair_f64(double &fp, double &fm, double cu, double cd,
+                                                 double trho, double base, double dsq,
+                                                 double om, double keep) {
+  const double even_eq = trho * fma(4.5 * cu, cu, base);
+  const double odd_eq = 3.0 * trho * cu;
+  const double even_F = trho * fma(cd, fma(4.5, cd, 9.0 * cu), -1.5 * dsq);
+  const double odd_F = 3.0 * trho * cd;
+  const double e = fma(om, even_eq, even_F), o = fma(om, odd_eq, odd_F);
+  fp = fma(keep, fp, e + o);
+  fm = fma(keep, fm, e - o);
+}
+
 __device__ __forceinline__ void collide_f64(double f[kQ], double om, double Fex, double Fey,
                                             double alpha, int coll = 0, double tau0 = 0.0,
                                             double Cs = 0.0) {
-  double rho = 0.0, jx = 0.0, jy = 0.0;
-#pragma unroll
-  for (int l = 0; l < kQ; ++l) {
-    rho += f[l];
-    jx += cx_of(l) * f[l];
-    jy += cy_of(l) * f[l];
-  }
+  const double rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const double jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
+  const double jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]);
   const double ir = 1.0 / rho;
   const double ux = jx * ir, uy = jy * ir;
   if (coll != 0) om = 1.0 / local_tau_f64(f, rho, ux, uy, tau0, coll, Cs);
@@ -313,15 +351,14 @@ __device__ __forceinline__ void collide_f64(double f[kQ], double om, double Fex,
   const double dux = Fx * ir, duy = Fy * ir;
   const double usq = ux * ux + uy * uy;
   const double dsq = dux * (2.0 * ux + dux) + duy * (2.0 * uy + duy);
-#pragma unroll
-  for (int l = 0; l < kQ; ++l) {
-    const double t = w_of(l);
-    const double cu = cx_of(l) * ux + cy_of(l) * uy;
-    const double cd = cx_of(l) * dux + cy_of(l) * duy;
-    const double feq = t * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-    const double Fl = t * rho * (3.0 * cd + 4.5 * cd * (2.0 * cu + cd) - 1.5 * dsq);
-    f[l] = f[l] - om * (f[l] - feq) + Fl;
-  }
+  const double base = 1.0 - 1.5 * usq, keep = 1.0 - om;
+  const double r0 = (4.0 / 9.0) * rho, r1 = (1.0 / 9.0) * rho, r2 = (1.0 / 36.0) * rho;
+  // rest population: no odd part
+  f[0] = fma(keep, f[0], fma(om, r0 * base, -1.5 * r0 * dsq));
+  collide_pair_f64(f[1], f[3], ux, dux, r1, base, dsq, om, keep);
+  collide_pair_f64(f[2], f[4], uy, duy, r1, base, dsq, om, keep);
+  collide_pair_f64(f[5], f[7], ux + uy, dux + duy, r2, base, dsq, om, keep);
+  collide_pair_f64(f[6], f[8], uy - ux, duy - dux, r2, base, dsq, om, keep);
 }
 
 // One-cell periodic shift.
@@ -634,12 +671,13 @@ cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tile
 // storage state.
 // ---------------------------------------------------------------------------
 
-template <typename T>
-__global__ void k_step_scalar(const Member *__restrict__ members, int member, int state) {
-  const Member &M = members[member];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= M.nx || y >= M.ny) return;
+// One cell (x, y) of one step of member M from storage state `state`.
+// L2ONLY loads the populations past L1 (ld.global.cg): the persistent
+// kernel below reads, at each step, values other SMs wrote at the previous
+// one, which a stale L1 line of this SM could otherwise shadow.  The
+// arithmetic is the same either way.
+template <typename T, bool L2ONLY>
+__device__ __forceinline__ void step_cell(const Member &M, int state, int x, int y) {
   const T *src = static_cast<const T *>(state_buffer(M, state));
   T *dst = static_cast<T *>(state < 2 ? M.pop[state ^ 1] : M.pop[0]);
   T fx = static_cast<const T *>(M.fx_tab)[y];
@@ -656,7 +694,13 @@ __global__ void k_step_scalar(const Member *__restrict__ members, int member, in
   }
   T f[kQ];
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
+  for (int l = 0; l < kQ; ++l) {
+    const T *a = src + pub_index(M, state, l, x, y);
+    if constexpr (L2ONLY)
+      f[l] = __ldcg(a);
+    else
+      f[l] = *a;
+  }
   if (M.collision == 3) {
     if constexpr (sizeof(T) == 4)
       collide_elbm<float>(f, M.rho0_f, M.tau_f, fx, fy, M.alpha_f);
@@ -682,8 +726,139 @@ __global__ void k_step_scalar(const Member *__restrict__ members, int member, in
   }
 }
 
+template <typename T>
+__global__ void k_step_scalar(const Member *__restrict__ members, int member, int state) {
+  const Member &M = members[member];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= M.nx || y >= M.ny) return;
+  step_cell<T, false>(M, state, x, y);
+}
+
+// ---------------------------------------------------------------------------
+// Small grids: every step of a run in one cooperative launch.  A grid of a
+// few thousand cells cannot fill the GPU, so a launch per step costs more in
+// launch latency than in work.  Here one cooperative kernel (all CTAs
+// co-resident, checked at launch) runs nsteps steps, with a grid-wide
+// barrier between steps; each thread owns fixed cells and does exactly the
+// general kernel's arithmetic (step_cell), so results are bit-identical.
+// The barrier waits are bounded: past the limit a CTA sets the error word
+// and returns, and the host reports it (LBM_ERR_TIMEOUT).
+// ---------------------------------------------------------------------------
+
+constexpr long long kBarrierSpinLimit = 1LL << 20;  // polls of ~0.5-1 us: about a second at most
+
+// Grid-wide barrier on a monotonic arrival counter: the k-th barrier (k =
+// 1, 2, ...) completes when the counter reaches k * nblocks.  Thread 0 of
+// each CTA arrives with a release add (its CTA's writes, gathered by the
+// __syncthreads before, become visible first) and polls with acquire loads;
+// no reset, no second word.  Returns false if this CTA gave up (error word
+// set by it or by another CTA).
+__device__ __forceinline__ bool grid_barrier(GridSync gs, unsigned nblocks, unsigned &target) {
+  __shared__ int s_ok;
+  __syncthreads();
+  target += nblocks;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned v;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(v) : "l"(gs.count) : "memory");
+    long long spins = 0;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(gs.count) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if ((++spins & 255) == 0 &&
+          (*(volatile int *)gs.err != 0 || spins > kBarrierSpinLimit)) {
+        atomicExch(gs.err, 1);
+        ok = 0;
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPersistThreads)
+    k_step_scalar_persistent(const Member *__restrict__ members, int member, int state,
+                             int nsteps, GridSync gs) {
+  const Member &M = members[member];
+  const int N = M.nx * M.ny;
+  unsigned target = 0;
+  for (int n = 0; n < nsteps; ++n) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+      step_cell<T, true>(M, state, c % M.nx, c / M.nx);
+    state ^= 1;  // 0 <-> 1 (double buffer), 2 <-> 3 (AA phases)
+    if (n + 1 < nsteps && !grid_barrier(gs, gridDim.x, target)) return;
+  }
+}
+
 static dim3 grid2d(int nx, int ny, dim3 b) {
   return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y);
+}
+
+// CTAs for a persistent run of an N-cell member: one 32-thread CTA per 32
+// cells up to one per SM, never more than can be co-resident (0 if the
+// device cannot launch cooperatively).
+int persistent_ctas(int precision, long long ncells) {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+    return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cudaError_t e = precision == 32
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_scalar_persistent<float>,
+                                                      kPersistThreads, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_scalar_persistent<double>,
+                                                      kPersistThreads, 0);
+  if (e != cudaSuccess || per_sm < 1) return 0;
+  long long want = (ncells + kPersistThreads - 1) / kPersistThreads;
+  if (want > sms) want = sms;
+  return (int)want;
+}
+
+// The barrier alone, for the failure-detection test: `rounds` grid barriers
+// over `ctas` CTAs, of which CTA `withhold` (if >= 0) never arrives, so the
+// others exhaust their bounded wait, set the error word and return.
+__device__ unsigned g_barrier_probe_words[4];
+
+__global__ void k_barrier_probe(int rounds, int withhold, GridSync gs) {
+  if ((int)blockIdx.x == withhold) return;
+  unsigned target = 0;
+  for (int r = 0; r < rounds; ++r)
+    if (!grid_barrier(gs, gridDim.x, target)) return;
+}
+
+cudaError_t barrier_probe(int ctas, int rounds, int withhold, cudaStream_t s, int *gave_up) {
+  unsigned *w = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void **)&w, g_barrier_probe_words);
+  if (e != cudaSuccess) return e;
+  GridSync gs{w, w + 1, reinterpret_cast<int *>(w + 2)};
+  if ((e = cudaMemsetAsync(w, 0, 4 * sizeof(unsigned), s)) != cudaSuccess) return e;
+  void *args[] = {(void *)&rounds, (void *)&withhold, (void *)&gs};
+  e = cudaLaunchCooperativeKernel((const void *)k_barrier_probe, dim3(ctas),
+                                  dim3(kPersistThreads), args, 0, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(gave_up, gs.err, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+      cudaSuccess)
+    return e;
+  return cudaStreamSynchronize(s);
+}
+
+cudaError_t launch_step_scalar_persistent(int precision, const Member *d_members, int member,
+                                          int state, int nsteps, int ctas, GridSync gs,
+                                          cudaStream_t s) {
+  if (ctas < 1 || nsteps < 1) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(gs.count, 0, 3 * sizeof(unsigned), s);  // count, gen, err
+  if (e != cudaSuccess) return e;
+  void *args[] = {(void *)&d_members, (void *)&member, (void *)&state, (void *)&nsteps,
+                  (void *)&gs};
+  if (precision == 32)
+    return cudaLaunchCooperativeKernel((const void *)k_step_scalar_persistent<float>, dim3(ctas),
+                                       dim3(kPersistThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void *)k_step_scalar_persistent<double>, dim3(ctas),
+                                     dim3(kPersistThreads), args, 0, s);
 }
 
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member, int nx,
@@ -926,7 +1101,8 @@ __device__ void project_finalize(const Member &M, int nblk, int slot, int tid, i
   __threadfence();
   // last CTA: one warp per value, two fixed-order chains and a shuffle tree
   __shared__ double coef[kDamp];
-  for (int q = wid; q < kDamp; q += 8) {
+  const int nthreads = blockDim.x * blockDim.y, nwarps = nthreads >> 5;
+  for (int q = wid; q < kDamp; q += nwarps) {
     double a0 = 0.0, a1 = 0.0;
     int b = lane;
     for (; b + 32 < nblk; b += 64) {
@@ -951,16 +1127,21 @@ __device__ void project_finalize(const Member &M, int nblk, int slot, int tid, i
   if (tid == 0) *M.proj_count = 0u;  // ready for the next launch
   if (slot >= 0 || M.damp_rows == nullptr) return;
   __syncthreads();
-  const double *tyd = M.trig64 + 4 * (size_t)nx;
-  for (int y = tid; y < ny; y += 256) {
-    const double cy = tyd[y], sy = tyd[ny + y], c2y = tyd[2 * ny + y], s2y = tyd[3 * ny + y];
+  // per-row factors of the FP32 step in FP32 arithmetic (they are stored as
+  // FP32; FP64 arithmetic here is the slow pipe at the end of the kernel)
+  __shared__ float coef_f[kDamp];
+  if (tid < kDamp) coef_f[tid] = (float)coef[tid];
+  __syncthreads();
+  const float *tyf = static_cast<const float *>(M.trig) + 4 * (size_t)nx;
+  for (int y = tid; y < ny; y += nthreads) {
+    const float cy = tyf[y], sy = tyf[ny + y], c2y = tyf[2 * ny + y], s2y = tyf[3 * ny + y];
     float *row = M.damp_rows + 6 * (size_t)y;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const double *d = coef + 12 * k;
-      row[3 * k] = (float)(d[0] + (d[4] + d[6]) * cy + (d[5] - d[7]) * sy);
-      row[3 * k + 1] = (float)(d[1] + (d[5] + d[7]) * cy - (d[4] - d[6]) * sy);
-      row[3 * k + 2] = (float)(d[2] * cy + d[3] * sy + d[10] * c2y + d[11] * s2y);
+      const float *d = coef_f + 12 * k;
+      row[3 * k] = d[0] + (d[4] + d[6]) * cy + (d[5] - d[7]) * sy;
+      row[3 * k + 1] = d[1] + (d[5] + d[7]) * cy - (d[4] - d[6]) * sy;
+      row[3 * k + 2] = d[2] * cy + d[3] * sy + d[10] * c2y + d[11] * s2y;
     }
   }
 }
@@ -1053,6 +1234,65 @@ __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ memb
 // The populations of the state are pulled as in k_step_f32_vec (MODE 0:
 // double buffer `state`, 1: AA even, 2: AA odd): one float4 per population
 // and lane, the x-shift by shuffles.  Same sums per cell as k_project.
+// One row's contribution to the 24 damping-mode sums: v holds the pulled
+// FP32 deviations of four consecutive cells of row y (lane's cells), cx..s2x
+// their x trig factors.  Shared by the projection kernels.
+__device__ __forceinline__ void proj_row_accumulate(const Member &M, const float (&v)[kQ][4],
+                                                    const float (&cx)[4], const float (&sx)[4],
+                                                    const float (&c2x)[4], const float (&s2x)[4],
+                                                    int y, float (&acc)[kDamp]) {
+  const int nx = M.nx, ny = M.ny;
+  const float *tr = static_cast<const float *>(M.trig);
+  const float cy = tr[4 * nx + y], sy = tr[4 * nx + ny + y];
+  const float c2y = tr[4 * nx + 2 * ny + y], s2y = tr[4 * nx + 3 * ny + y];
+  // separable in x and y: the lane's sums of u (1, cos x, sin x, cos 2x,
+  // sin 2x) over its four cells, folded into the mode sums with the row's
+  // y factors (cos(x +- y) = cx cy -+ sx sy, sin(x +- y) = sx cy +- cx sy)
+  float R[2][5];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) R[k][q] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float rho = M.rho0_f, jx = 0.f, jy = 0.f;
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      rho += v[l][i];
+      jx += (float)cx_of(l) * v[l][i];
+      jy += (float)cy_of(l) * v[l][i];
+    }
+    // approximate reciprocal (2 ulp): u only enters the damping's mode sums,
+    // whose force is F^R_0 ~ 1e-5 times them
+    const float ir = __fdividef(1.0f, rho);
+    const float u[2] = {jx * ir, jy * ir};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      R[k][0] += u[k];
+      R[k][1] += u[k] * cx[i];
+      R[k][2] += u[k] * sx[i];
+      R[k][3] += u[k] * c2x[i];
+      R[k][4] += u[k] * s2x[i];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float *a = acc + 12 * k;
+    a[0] += R[k][1];                       // cos x
+    a[1] += R[k][2];                       // sin x
+    a[2] += R[k][0] * cy;                  // cos y
+    a[3] += R[k][0] * sy;                  // sin y
+    a[4] += R[k][1] * cy - R[k][2] * sy;   // cos(x + y)
+    a[5] += R[k][2] * cy + R[k][1] * sy;   // sin(x + y)
+    a[6] += R[k][1] * cy + R[k][2] * sy;   // cos(x - y)
+    a[7] += R[k][2] * cy - R[k][1] * sy;   // sin(x - y)
+    a[8] += R[k][3];                       // cos 2x
+    a[9] += R[k][4];                       // sin 2x
+    a[10] += R[k][0] * c2y;                // cos 2y
+    a[11] += R[k][0] * s2y;                // sin 2y
+  }
+}
+
 constexpr int kProj4Rows = 8;
 template <int MODE>
 __global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ members, int state,
@@ -1115,52 +1355,7 @@ __global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ mem
       }
     }
     if (!active) continue;
-    const float cy = tr[4 * nx + y], sy = tr[4 * nx + ny + y];
-    const float c2y = tr[4 * nx + 2 * ny + y], s2y = tr[4 * nx + 3 * ny + y];
-    // separable in x and y: the lane's sums of u (1, cos x, sin x, cos 2x,
-    // sin 2x) over its four cells, folded into the mode sums with the row's
-    // y factors (cos(x +- y) = cx cy -+ sx sy, sin(x +- y) = sx cy +- cx sy)
-    float R[2][5];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-#pragma unroll
-      for (int q = 0; q < 5; ++q) R[k][q] = 0.f;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float rho = M.rho0_f, jx = 0.f, jy = 0.f;
-#pragma unroll
-      for (int l = 0; l < kQ; ++l) {
-        rho += v[l][i];
-        jx += (float)cx_of(l) * v[l][i];
-        jy += (float)cy_of(l) * v[l][i];
-      }
-      const float ir = 1.0f / rho;
-      const float u[2] = {jx * ir, jy * ir};
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        R[k][0] += u[k];
-        R[k][1] += u[k] * cx[i];
-        R[k][2] += u[k] * sx[i];
-        R[k][3] += u[k] * c2x[i];
-        R[k][4] += u[k] * s2x[i];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      float *a = acc + 12 * k;
-      a[0] += R[k][1];                       // cos x
-      a[1] += R[k][2];                       // sin x
-      a[2] += R[k][0] * cy;                  // cos y
-      a[3] += R[k][0] * sy;                  // sin y
-      a[4] += R[k][1] * cy - R[k][2] * sy;   // cos(x + y)
-      a[5] += R[k][2] * cy + R[k][1] * sy;   // sin(x + y)
-      a[6] += R[k][1] * cy + R[k][2] * sy;   // cos(x - y)
-      a[7] += R[k][2] * cy - R[k][1] * sy;   // sin(x - y)
-      a[8] += R[k][3];                       // cos 2x
-      a[9] += R[k][4];                       // sin 2x
-      a[10] += R[k][0] * c2y;                // cos 2y
-      a[11] += R[k][0] * s2y;                // sin 2y
-    }
+    proj_row_accumulate(M, v, cx, sx, c2x, s2x, y, acc);
   }
   __shared__ float sh[kDamp][8];
   const int tid = threadIdx.y * 32 + threadIdx.x, wid = threadIdx.y;

@@ -135,3 +135,94 @@ def test_fp32_forward_gradients_close_to_fp64(P):
         grads.append((float(tau.grad), float(F0.grad)))
     for a, b in zip(*grads):
         assert abs(a - b) < 1e-3 * abs(a)
+
+
+# --------------------------------------------------------------------------
+# The differentiation workload at its own configuration: 256^2, tau = 0.55,
+# Kolmogorov forcing kf = 4 with drag 1e-4 and F0 for a laminar u_rms of
+# 0.03, objective = mean over n in [1000, 2000] of the L = 16 box average
+# (origin (0, 0)) of the dissipation term RHS^{E,4} of eq. (8), checkpoints
+# every 100 steps, initial state from the random-phase generator (seed 0,
+# u_rms 0.02).
+# --------------------------------------------------------------------------
+
+C3 = dict(n=256, tau=0.55, kf=4, alpha=1e-4, n0=1000, n1=2000, box=(0, 0), L=16, K=100)
+
+
+def _c3_F0():
+    return li.kolmogorov_F0(C3["n"], C3["tau"], C3["kf"], C3["alpha"], 0.03)
+
+
+def _c3_oracle_J(args):
+    """Oracle objective at (tau, F0) from the C3 initial state (one process)."""
+    import oracle
+    tau, F0 = args
+    n = C3["n"]
+    f0 = oracle.init(*li.random_phase(n, seed=0, u_rms=0.02))
+    return oracle.objective(f0, tau, oracle.Force(1, F0, C3["kf"], C3["alpha"]), C3["n0"],
+                            C3["n1"], *C3["box"], C3["L"])
+
+
+@pytest.fixture(scope="module")
+def c3_fd():
+    """Oracle objective and its central finite differences: dJ/dtau with
+    h = 1e-6, dJ/dF0 by Richardson extrapolation of central differences with
+    relative steps 1e-3 and 5e-4 (seven oracle runs of 2000 steps, in
+    parallel processes)."""
+    import multiprocessing as mp
+    tau, F0, h = C3["tau"], _c3_F0(), 1e-6
+    pts = [(tau, F0), (tau + h, F0), (tau - h, F0)]
+    for hr in (1e-3, 5e-4):
+        pts += [(tau, F0 * (1 + hr)), (tau, F0 * (1 - hr))]
+    with mp.get_context("spawn").Pool(len(pts)) as pool:
+        v = pool.map(_c3_oracle_J, pts)
+    d_tau = (v[1] - v[2]) / (2 * h)
+    dF = [(v[3] - v[4]) / (2 * F0 * 1e-3), (v[5] - v[6]) / (2 * F0 * 5e-4)]
+    return {"J": v[0], "dJ_dtau": d_tau, "dJ_dF0": (4 * dF[1] - dF[0]) / 3}
+
+
+def _c3_gradients(P, precision):
+    import torch
+    from paper_1809_06735_gb300.adjoint import ObjectiveSpec, box_dissipation
+    import oracle
+    n = C3["n"]
+    spec = ObjectiveSpec(nx=n, ny=n, kf=C3["kf"], alpha=C3["alpha"], n0=C3["n0"], n1=C3["n1"],
+                         box=C3["box"], L=C3["L"], precision=precision,
+                         checkpoint_every=C3["K"])
+    f0 = torch.from_numpy(oracle.init(*li.random_phase(n, seed=0, u_rms=0.02))).cuda()
+    tau = torch.tensor(C3["tau"], dtype=torch.float64, requires_grad=True)
+    F0 = torch.tensor(_c3_F0(), dtype=torch.float64, requires_grad=True)
+    J = box_dissipation(tau, F0, f0, spec)
+    J.backward()
+    return float(J), float(tau.grad), float(F0.grad)
+
+
+@pytest.mark.slow
+def test_c3_fp64_gradients_match_oracle_finite_differences(P, c3_fd):
+    """FP64 forward, FP64 adjoint: J within 1e-10 of the oracle's (the FP64
+    trajectories agree to rounding over the 2000 steps: the flow is not
+    chaotic at this Reynolds number, the finite differences agree to 4e-10
+    between h and 2h), dJ/dtau and dJ/dF0 within 1e-6 of the oracle's central
+    finite differences."""
+    J, gt, gF = _c3_gradients(P, 64)
+    print("C3 FP64: J %.12e (oracle %.12e) dJ/dtau %.12e (FD %.12e) dJ/dF0 %.12e (FD %.12e)"
+          % (J, c3_fd["J"], gt, c3_fd["dJ_dtau"], gF, c3_fd["dJ_dF0"]))
+    assert abs(J - c3_fd["J"]) < 1e-10 * abs(c3_fd["J"])
+    assert abs(gt - c3_fd["dJ_dtau"]) < 1e-6 * abs(c3_fd["dJ_dtau"])
+    assert abs(gF - c3_fd["dJ_dF0"]) < 1e-6 * abs(c3_fd["dJ_dF0"])
+
+
+@pytest.mark.slow
+def test_c3_fp32_forward_gradients(P, c3_fd):
+    """FP32 deviation forward, FP64 adjoint on its states: J and both
+    gradients against the FP64 oracle's values.  The FP32 trajectory carries
+    a relative population error of order 1e-6 per hundred steps (the step
+    parity bar), so J (a sum of squared velocity gradients) and its
+    derivatives differ from the FP64 values by the trajectory's relative
+    error; bar 1e-4 over the 2000 steps."""
+    J, gt, gF = _c3_gradients(P, 32)
+    print("C3 FP32: J %.12e (oracle %.12e) dJ/dtau %.12e (FD %.12e) dJ/dF0 %.12e (FD %.12e)"
+          % (J, c3_fd["J"], gt, c3_fd["dJ_dtau"], gF, c3_fd["dJ_dF0"]))
+    assert abs(J - c3_fd["J"]) < 1e-4 * abs(c3_fd["J"])
+    assert abs(gt - c3_fd["dJ_dtau"]) < 1e-4 * abs(c3_fd["dJ_dtau"])
+    assert abs(gF - c3_fd["dJ_dF0"]) < 1e-4 * abs(c3_fd["dJ_dF0"])
