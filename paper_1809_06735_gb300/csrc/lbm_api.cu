@@ -681,7 +681,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
   if (e != cudaSuccess)
     return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
   h->cur = cfg->storage == 1 ? 2 : 0;
-  h->lc.paper_force = h->has_kind2 || h->has_vv ? 1 : 0;
+  h->lc.paper_force = h->has_vv ? 2 : (h->has_kind2 ? 1 : 0);
   {
     unsigned *w = reinterpret_cast<unsigned *>(ws_at(h, lay.sync));
     h->gsync = lbm::GridSync{w, w + 1, reinterpret_cast<int *>(w + 2)};

@@ -140,8 +140,9 @@ struct LaunchCfg {
   int block_warps_y;  // warps per CTA (rows per CTA pass)
   int rows_per_warp;  // rows each warp processes per tile
   int grid_ctas;      // 0: one CTA per tile; else persistent grid size
-  int paper_force;    // 1: some member has force kind 2 or a variable-viscosity
-                      // collision (the extended kernel variant)
+  int paper_force;    // kernel variant: 0 plain; 1 some member has force kind 2
+                      // (BGK collisions); 2 some member has a variable-viscosity
+                      // collision (any force)
 };
 
 // One step of every vector-kernel member (flip: tiles in reverse order).

@@ -440,8 +440,8 @@ __device__ __forceinline__ void paper_force4(const Member &M, int x, int y, floa
 
 // SNAP: the step also records the snapshot-ring entry of the state it
 // reads (slot snap_slot), the same compensated pairs as k_snapshot_ring.
-template <int ROWS, int MODE, bool PF, bool SNAP = false>
-__global__ void __launch_bounds__(256, PF ? 3 : (SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
+template <int ROWS, int MODE, int PF, bool SNAP = false>
+__global__ void __launch_bounds__(256, PF == 2 ? 3 : (PF == 1 || SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
                                                       const Tile *__restrict__ tiles,
                                                       int ntiles, int cur, int flip, int snap_slot) {
   const int lane = threadIdx.x;
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(256, PF ? 3 : (SNAP ? 2 : 1)) k_step_f32_vec(c
       }
       if (active) {
         float fxc[4], fyc[4];
-        if (PF && M.force_kind == 2) {
+        if (PF != 0 && M.force_kind == 2) {
           paper_force4(M, x, y, fxc, fyc);
         } else {
           const float fx = fxt[y];
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(256, PF ? 3 : (SNAP ? 2 : 1)) k_step_f32_vec(c
           float g[kQ];
 #pragma unroll
           for (int l = 0; l < kQ; ++l) g[l] = v[l][c];
-          if constexpr (PF)
+          if constexpr (PF == 2)
             collide_f32<true>(g, rho0, om, fxc[c], fyc[c], alpha, M.collision, M.tau_f, M.Cs_f);
           else
             collide_f32(g, rho0, om, fxc[c], fyc[c], alpha);
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(256, PF ? 3 : (SNAP ? 2 : 1)) k_step_f32_vec(c
   }
 }
 
-template <int ROWS, bool PF, bool SNAP = false>
+template <int ROWS, int PF, bool SNAP = false>
 static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int ntiles, int state,
                             int flip, int grid, dim3 block, cudaStream_t s, int slot = -1) {
   if (state < 2)
@@ -626,13 +626,17 @@ static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int nt
                                                              flip, slot);
 }
 
+// pf: 0 no member with force kind 2 or a variable viscosity; 1 force kind 2
+// with the BGK collision only; 2 variable-viscosity collisions (any force)
 template <int ROWS>
 static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int ntiles, int state,
-                            int flip, int grid, dim3 block, bool pf, cudaStream_t s) {
-  if (pf)
-    launch_vec_rows<ROWS, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
+                            int flip, int grid, dim3 block, int pf, cudaStream_t s) {
+  if (pf == 2)
+    launch_vec_rows<ROWS, 2>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
+  else if (pf == 1)
+    launch_vec_rows<ROWS, 1>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
   else
-    launch_vec_rows<ROWS, false>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
+    launch_vec_rows<ROWS, 0>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
 }
 
 cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, int ntiles,
@@ -641,9 +645,9 @@ cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, in
   dim3 block(32, lc.block_warps_y);
   int grid = lc.grid_ctas > 0 ? (lc.grid_ctas < ntiles ? lc.grid_ctas : ntiles) : ntiles;
   switch (lc.rows_per_warp) {
-    case 1: launch_vec_rows<1>(d_members, d_tiles, ntiles, state, flip, grid, block, lc.paper_force != 0, s); break;
-    case 2: launch_vec_rows<2>(d_members, d_tiles, ntiles, state, flip, grid, block, lc.paper_force != 0, s); break;
-    case 4: launch_vec_rows<4>(d_members, d_tiles, ntiles, state, flip, grid, block, lc.paper_force != 0, s); break;
+    case 1: launch_vec_rows<1>(d_members, d_tiles, ntiles, state, flip, grid, block, lc.paper_force, s); break;
+    case 2: launch_vec_rows<2>(d_members, d_tiles, ntiles, state, flip, grid, block, lc.paper_force, s); break;
+    case 4: launch_vec_rows<4>(d_members, d_tiles, ntiles, state, flip, grid, block, lc.paper_force, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -658,9 +662,9 @@ cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tile
   dim3 block(32, lc.block_warps_y);
   int grid = lc.grid_ctas > 0 ? (lc.grid_ctas < ntiles ? lc.grid_ctas : ntiles) : ntiles;
   switch (lc.rows_per_warp) {
-    case 1: launch_vec_rows<1, false, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s, slot); break;
-    case 2: launch_vec_rows<2, false, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s, slot); break;
-    case 4: launch_vec_rows<4, false, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s, slot); break;
+    case 1: launch_vec_rows<1, 0, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s, slot); break;
+    case 2: launch_vec_rows<2, 0, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s, slot); break;
+    case 4: launch_vec_rows<4, 0, true>(d_members, d_tiles, ntiles, state, flip, grid, block, s, slot); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
