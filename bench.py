@@ -517,9 +517,10 @@ def alu_peaks(P, stream):
 
 
 def fp64_instruction_counts():
-    """FP64 flops per lattice update of the FP64 kernels (dadd + dmul +
-    2 dfma, ncu counters) from the committed summary, valid only while the
-    kernel sources are unchanged."""
+    """FP64 flops and FP64 instructions per lattice update of the FP64
+    kernels (dadd + dmul + 2 dfma, and dadd + dmul + dfma, ncu counters)
+    from the committed summary, valid only while the kernel sources are
+    unchanged."""
     p = os.path.join(ROOT, "profiles", "fp64_flops_per_lu.json")
     if not os.path.exists(p):
         return {}
@@ -530,8 +531,21 @@ def fp64_instruction_counts():
         src = os.path.join(ROOT, "paper_1809_06735_gb300", "csrc", rec["source"])
         with open(src, "rb") as fh:
             if hashlib.sha256(fh.read()).hexdigest()[:16] == rec.get("source_sha256_16"):
-                out[name] = rec["fp64_flops_per_lu"]
+                out[name] = (rec["fp64_flops_per_lu"], rec["fp64_instr_per_lu"])
     return out
+
+
+def fp64_roofline(counts, glups, peaks):
+    """The FP64-pipe roofline of a kernel from its counted flops and
+    instructions per update: achieved flop rate against the measured FMA
+    rate, and the pipe's instruction rate against the FMA chains' (an add or
+    a multiply occupies the pipe like an FMA)."""
+    flops, instr = counts
+    tf = flops * glups / 1e3
+    return {"bound": "fp64", "fp64_flops_per_lu": flops, "fp64_instr_per_lu": instr,
+            "achieved": tf, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": tf / peaks["fp64_tflops"],
+            "pipe_instr_frac": instr * glups * 1e9 / (peaks["fp64_tflops"] * 1e12 / 2)}
 
 
 def fp64_plain_leg(P, stream, dev, peak_hbm, peaks, dev_fields=None):
@@ -558,16 +572,11 @@ def fp64_plain_leg(P, stream, dev, peak_hbm, peaks, dev_fields=None):
     lat.close()
     glups = n * n / secs / 1e9
     gbs = BYTES_PER_LU_F64 * glups
-    flops = fp64_instruction_counts().get("k_step_scalar<double>")
+    counts = fp64_instruction_counts().get("k_step_scalar<double>")
     out = {"grid": [n, n], "glups": glups, "bytes_per_lu": BYTES_PER_LU_F64,
            "achieved_gbs": gbs, "hbm_frac": gbs / peak_hbm}
-    if flops is not None:
-        tf = flops * glups / 1e3
-        out.update({"fp64_flops_per_lu": flops, "achieved_fp64_tflops": tf,
-                    "fp64_peak_tflops": peaks["fp64_tflops"],
-                    "fp64_frac": tf / peaks["fp64_tflops"]})
-        out["bound"] = "fp64" if out["fp64_frac"] > out["hbm_frac"] else "hbm"
-        out["frac"] = max(out["fp64_frac"], out["hbm_frac"])
+    if counts is not None:
+        out["fp64_roofline"] = fp64_roofline(counts, glups, peaks)
     return out
 
 
@@ -721,11 +730,9 @@ def adjoint_leg(P, stream, dev, peaks):
     k = {"us_per_step": 1e6 * step_s, "glups": glups, "bytes_per_lu": 216,
          "achieved_gbs": 216 * glups,
          "note": "256^2 FP64: 14 MB per step, L2-resident; launch pair k_adjoint + k_adjoint_final"}
-    flops = fp64_instruction_counts().get("k_adjoint")
-    if flops is not None:
-        tf = flops * glups / 1e3
-        k.update({"fp64_flops_per_lu": flops, "achieved_fp64_tflops": tf,
-                  "fp64_frac": tf / peaks["fp64_tflops"], "bound": "fp64"})
+    counts = fp64_instruction_counts().get("k_adjoint")
+    if counts is not None:
+        k["fp64_roofline"] = fp64_roofline(counts, glups, peaks)
     out["adjoint_kernel"] = k
     return out
 
