@@ -864,6 +864,25 @@ def case_diag_batch(P, members=16, n=512, events=2):
     print("diag batch case done:", lat.launch_count, "launches")
 
 
+def case_diag_large(P, n=8192, events=2):
+    """The large forced run's balance event: one FP32 member of 8192^2,
+    L = 2..4096 over every periodic origin (805 M boxes), twice (about
+    31 GB of device memory)."""
+    import torch
+    wl = li.large_forced_workload()
+    lat = P.Lattice([P.Member(n, n, wl["tau"], 1.0, 1, wl["kf"], wl["F0"], wl["alpha"])],
+                    precision=32, diag_every=4)
+    lat.init_fields(0, 1.0 + li.smooth_fields(n, n, seed=7, amp=1e-3, kmax=16),
+                    li.smooth_fields(n, n, seed=5, amp=0.03, kmax=16),
+                    li.smooth_fields(n, n, seed=6, amp=0.03, kmax=16))
+    for _ in range(events):
+        lat.step(4)
+        stats = lat.subvolume_balance(0, wl["Ls"])
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(stats[:, 2:, 0]))
+    print("diag_large case done:", lat.launch_count, "launches")
+
+
 def case_fp64(P, n=512, steps=20):
     import torch
     lat = P.Lattice([P.Member(n, n, 0.52)], precision=64)

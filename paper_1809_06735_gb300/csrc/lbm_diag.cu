@@ -1008,23 +1008,27 @@ __global__ void k_global_scale(double *sums, size_t N) {
 // Exact fixed-point summed-area tables
 // ---------------------------------------------------------------------------
 
-// Scale exponents, one CTA per job and one warp per field: e_f with
+// Scale exponents, one CTA of 256 threads per (field, job): e_f with
 // N * max|T_f| * 2^e_f < 2^62 (so every partial sum of the table fits in
 // int64), capped so that 2^e_f is a finite float.  scales[f] = 2^e_f,
 // scales[kNT + f] = 2^-e_f, and the exponent itself at exps_at() as int.
 // nF: the number of fields with a table in this call (12, or 13 with |u|^2).
 template <typename T>
-__global__ void k_scales(const DiagJob *__restrict__ jobs, int nF) {
-  const DiagJob &J = jobs[blockIdx.x];
-  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) k_scales(const DiagJob *__restrict__ jobs, int nF) {
+  const DiagJob &J = jobs[blockIdx.y];
+  const int f = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (f >= nF) return;
   const size_t N = (size_t)J.nx * J.ny;
   const int nblk = ((J.nx + 31) / 32) * ((J.ny + 7) / 8);
   const typename AbsBits<T>::U *mb = max_part<T>(J) + (size_t)f * nblk;
   typename AbsBits<T>::U b = 0;
-  for (int i = lane; i < nblk; i += 32) b = mb[i] > b ? mb[i] : b;
+  for (int i = threadIdx.x; i < nblk; i += 256) b = mb[i] > b ? mb[i] : b;
   b = AbsBits<T>::warp_max(b);
-  if (lane == 0) {
+  __shared__ typename AbsBits<T>::U wmax[8];
+  if (lane == 0) wmax[wid] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) b = wmax[w] > b ? wmax[w] : b;
     const double m = AbsBits<T>::value(b);
     int e = 0;
     if (m > 0.0 && m <= 1.7e308) {
@@ -1151,20 +1155,75 @@ __device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
   return v;
 }
 
-// A CTA of NF warps (warp f = field f) per (strip, job); grid (ns, 1, G).
+// Row blocks: with few strips (a large single member), the rows of a strip
+// are split into nrb blocks of rb_rows rows (a multiple of 32) walked by
+// separate CTAs.  k_col_sums gives each (field, strip, block) the quantised
+// column sums of its rows and the sum of its rows' left parts, after the
+// left parts [field][strip][row] at colsum_base; a block's CTA starts its
+// running column sums at what the blocks above it sum to, exactly (integer
+// arithmetic), so the table is the same whatever the split.
+__device__ __forceinline__ long long *colsum_base(double *base, size_t N, int nF, int ns, int ny) {
+  return strip_base(base, N) + (size_t)nF * ns * ny;
+}
+
+// A CTA of NF warps (warp f = field f) per (strip, row block, job).
+template <typename T, int NF>
+__global__ void __launch_bounds__(NF * 32) k_col_sums(const DiagJob *__restrict__ jobs,
+                                                      int rb_rows) {
+  constexpr int R = sizeof(T) == 4 ? 8 : 4;
+  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31, s = blockIdx.x, rb = blockIdx.y;
+  const int nrb = gridDim.y;
+  const DiagJob &J = jobs[blockIdx.z];
+  const int nx = J.nx, ny = J.ny, ns = (nx + kStrip - 1) / kStrip;
+  const int ya = rb * rb_rows, yb = ya + rb_rows < ny ? ya + rb_rows : ny;
+  if (s >= ns || ya >= ny) return;  // whole CTA
+  const size_t N = (size_t)nx * ny;
+  const T *A = fld<T>(J.base, T0 + f, N);
+  const bool vec = vec_rows(A, nx);
+  const int x = s * kStrip + 4 * lane;
+  const int e = reinterpret_cast<const int *>(J.part + exps_at())[f];
+  const long long *left = strip_base(J.base, N) + ((size_t)f * ns + s) * ny;
+  long long c[4] = {0, 0, 0, 0}, ls = 0;
+  for (int y0 = ya; y0 < yb; y0 += R) {
+    T a[R][4];
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (y0 + k < yb) load4(A + (size_t)(y0 + k) * nx, x, nx, vec, a[k]);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (y0 + k >= yb) break;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) c[j] += quantize(a[k][j], e);
+    }
+  }
+  for (int y = ya + lane; y < yb; y += 32) ls += left[y];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ls += __shfl_down_sync(0xffffffffu, ls, o);
+  long long *cs = colsum_base(J.base, N, NF, ns, ny) + (((size_t)f * ns + s) * nrb + rb) * kStrip;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cs[4 * lane + j] = c[j];
+  long long *lsum = colsum_base(J.base, N, NF, ns, ny) + (size_t)NF * ns * nrb * kStrip;
+  if (lane == 0) lsum[((size_t)f * ns + s) * nrb + rb] = ls;
+}
+
+// A CTA of NF warps (warp f = field f) per (strip, row block, job); grid
+// (ns, nrb, G) (nrb = 1: the whole strip; rb_rows then >= ny).
 // Lane l holds columns x0 + 4l .. x0 + 4l + 3.  Each row is staged in one of
 // two shared tiles [field][129] (column c at (c % 4) 32 + c / 4: conflict-free
 // writes) and copied out as the consecutive words of its records, so one
 // barrier per row suffices.
 template <typename T, int NF>
-__global__ void __launch_bounds__(NF * 32) k_sat_tile(const DiagJob *__restrict__ jobs) {
+__global__ void __launch_bounds__(NF * 32) k_sat_tile(const DiagJob *__restrict__ jobs,
+                                                      int rb_rows) {
   constexpr int R = sizeof(T) == 4 ? 8 : 4;  // rows of loads in flight per warp
   constexpr int NT = NF * 32, TS = kStrip + 1;
   __shared__ long long tile[2][NF][TS];
-  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31, s = blockIdx.x;
+  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31, s = blockIdx.x, rb = blockIdx.y;
+  const int nrb = gridDim.y;
   const DiagJob &J = jobs[blockIdx.z];
   const int nx = J.nx, ny = J.ny, ns = (nx + kStrip - 1) / kStrip;
-  if (s >= ns) return;  // whole CTA
+  const int ya = rb * rb_rows, yb = ya + rb_rows < ny ? ya + rb_rows : ny;
+  if (s >= ns || ya >= ny) return;  // whole CTA
   const int x0 = s * kStrip, x = x0 + 4 * lane;
   const int nw = (nx - x0 < kStrip ? nx - x0 : kStrip) * NF;  // record words per row
   const size_t N = (size_t)nx * ny, rs = (size_t)nx + 1;
@@ -1173,20 +1232,38 @@ __global__ void __launch_bounds__(NF * 32) k_sat_tile(const DiagJob *__restrict_
   const long long *left = strip_base(J.base, N) + ((size_t)f * ns + s) * ny;
   long long *tab = sat_base(J.base, N);
   const int e = reinterpret_cast<const int *>(J.part + exps_at())[f];
-  for (int w = threadIdx.x; w < nw; w += NT) tab[(size_t)(x0 + 1) * NF + w] = 0;  // row 0
-  if (s == 0 && threadIdx.x < NF) tab[threadIdx.x] = 0;
   long long col[4] = {0, 0, 0, 0}, lf = 0;
-  for (int y0 = 0; y0 < ny; y0 += R) {
+  if (rb == 0) {
+    for (int w = threadIdx.x; w < nw; w += NT) tab[(size_t)(x0 + 1) * NF + w] = 0;  // row 0
+    if (s == 0 && threadIdx.x < NF) tab[threadIdx.x] = 0;
+  } else {  // the rows above this block: left parts plus the strip's column prefix
+    const long long *cs = colsum_base(J.base, N, NF, ns, ny) + ((size_t)f * ns + s) * nrb * kStrip;
+    const long long *lsum =
+        colsum_base(J.base, N, NF, ns, ny) + (size_t)NF * ns * nrb * kStrip + ((size_t)f * ns + s) * nrb;
+    long long c[4] = {0, 0, 0, 0}, ls = 0;
+    for (int b = 0; b < rb; ++b) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) c[j] += cs[(size_t)b * kStrip + 4 * lane + j];
+      ls += lsum[b];
+    }
+    c[1] += c[0];
+    c[2] += c[1];
+    c[3] += c[2];
+    const long long off = ls + warp_incl_scan(c[3], lane) - c[3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) col[j] = off + c[j];
+  }
+  for (int y0 = ya; y0 < yb; y0 += R) {
     if ((y0 & 31) == 0) lf = y0 + lane < ny ? left[y0 + lane] : 0;  // 32 rows' left parts
     T a[R][4];
 #pragma unroll
     for (int k = 0; k < R; ++k)
-      if (y0 + k < ny) load4(A + (size_t)(y0 + k) * nx, x, nx, vec, a[k]);
+      if (y0 + k < yb) load4(A + (size_t)(y0 + k) * nx, x, nx, vec, a[k]);
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       const int y = y0 + k;
       const long long l = __shfl_sync(0xffffffffu, lf, (y0 & 31) + k);
-      if (y >= ny) break;  // the same for the whole CTA
+      if (y >= yb) break;  // the same for the whole CTA
       long long v[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) v[j] = quantize(a[k][j], e);
@@ -1615,13 +1692,37 @@ cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int 
     k_flux<T><<<cg, cb, 0, s>>>(jobs);
     k_curl<T><<<cg, cb, 0, s>>>(jobs);
   }
-  k_scales<T><<<G, kNT * 32, 0, s>>>(jobs, nF);
+  k_scales<T><<<dim3(nF, G), 256, 0, s>>>(jobs, nF);
   const int ns = (nx + kStrip - 1) / kStrip;
   k_strip_sums<T><<<dim3((ny + 7) / 8, nF, G), 256, 0, s>>>(jobs);
+  // row blocks when strips x jobs would leave most SMs idle
+  int rb_rows = ny, nrb = 1;
+  {
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    }
+    const long long ctas = (long long)ns * G;
+    if (ctas < 2LL * sms && ny >= 256) {
+      long long want = (2LL * sms + ctas - 1) / ctas;
+      if (want > ny / 64) want = ny / 64;
+      rb_rows = (int)(((ny + want - 1) / want + 31) / 32 * 32);
+      nrb = (ny + rb_rows - 1) / rb_rows;
+    }
+  }
+  if (nrb > 1) {
+    if (nF == kNT)
+      k_col_sums<T, kNT><<<dim3(ns, nrb, G), kNT * 32, 0, s>>>(jobs, rb_rows);
+    else
+      k_col_sums<T, 12><<<dim3(ns, nrb, G), 12 * 32, 0, s>>>(jobs, rb_rows);
+  }
   if (nF == kNT)
-    k_sat_tile<T, kNT><<<dim3(ns, 1, G), kNT * 32, 0, s>>>(jobs);
+    k_sat_tile<T, kNT><<<dim3(ns, nrb, G), kNT * 32, 0, s>>>(jobs, rb_rows);
   else
-    k_sat_tile<T, 12><<<dim3(ns, 1, G), 12 * 32, 0, s>>>(jobs);
+    k_sat_tile<T, 12><<<dim3(ns, nrb, G), 12 * 32, 0, s>>>(jobs, rb_rows);
   k_query_consts<<<G, kDiagMaxL * kNT, 0, s>>>(jobs, nF);
   const DiagDist none{};
   if (dist) {
