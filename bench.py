@@ -333,26 +333,36 @@ def run_reference(args):
         dist.barrier()
 
 
+def median_timed(stream, fn, runs=5):
+    """Median over `runs` calls of fn() of its device time on `stream`
+    (CUDA events, synchronised on both sides), seconds."""
+    import torch
+    times = []
+    for _ in range(runs):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    return float(np.median(times))
+
+
 def paper_forcing_leg(P, stream, dev, peak):
     """The paper's own turbulence forcing (eqs. 14-16, force kind 2) at its
     grid and amplitudes: 64 FP32 members of 256^2, F^T_0 = 8e-4, phase 0,
     F^R_0 = 1e-5, tau = 0.52.  A step is the damping projection (one read of
     the populations, 36 B/LU) plus the stream-collide with the shell-force
-    table (72 + 8 B/LU): 116 algorithmic bytes per lattice update."""
-    import torch
+    table (72 + 8 B/LU): 116 algorithmic bytes per lattice update.  Median of
+    five timed 200-step runs."""
     n2, M2, steps = 256, 64, 200
     lat = P.Lattice([P.Member(n2, n2, 0.52, 1.0, 2, 0, 8e-4, 0.0, 0.0, 1e-5)] * M2,
                     precision=32, graph_steps=50, stream=stream, device=dev)
     for m in range(M2):
         lat.init_fields(m, *li.random_phase(n2, seed=3000 + m, u_rms=0.02))
     lat.step(100)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a.record(stream)
-    lat.step(steps)
-    b.record(stream)
-    torch.cuda.synchronize()
-    secs = a.elapsed_time(b) / 1e3
+    secs = median_timed(stream, lambda: lat.step(steps))
     lu = M2 * n2 * n2 * steps
     gbs = 116.0 * lu / secs / 1e9
     tune = lat.tuning()
@@ -366,8 +376,8 @@ def collision_models_leg(P, stream, dev, peak):
     """The variable-viscosity collisions (Sec. 1) on 16 FP32 members of
     512^2 (tau0 = 0.51): Smagorinsky (Cs = 0.1) and eq. (7) on the extended
     vectorised kernel, the entropic LBM (its per-cell root finding) on the
-    general kernel.  Every step moves 72 algorithmic bytes per update."""
-    import torch
+    general kernel.  Every step moves 72 algorithmic bytes per update.
+    Median of five timed 40-step runs."""
     n, M, steps = 512, 16, 40
     fields = li.random_phase(n, seed=4000, u_rms=0.02)
     out = {"members": M, "grid": [n, n], "tau0": 0.51}
@@ -377,20 +387,21 @@ def collision_models_leg(P, stream, dev, peak):
         for m in range(M):
             lat.init_fields(m, *fields)
         lat.step(20)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        lat.step(steps)
-        b.record(stream)
-        torch.cuda.synchronize()
-        secs = a.elapsed_time(b) / 1e3
+        secs = median_timed(stream, lambda: lat.step(steps))
         lu = M * n * n * steps
         gbs = BYTES_PER_LU_F32 * lu / secs / 1e9
         out[name] = {"glups": lu / secs / 1e9, "achieved_gbs": gbs, "frac": gbs / peak,
                      "kernel": "k_step_scalar<float>" if coll == 3 else "k_step_f32_vec (extended)",
-                     # the entropic collision's per-cell root finding keeps the issue
-                     # slots busy (ALU-bound); frac is then only its share of HBM
-                     "bound": "alu" if coll == 3 else "hbm"}
+                     "bound": "hbm"}
+        if coll == 3:  # the entropic root keeps the issue slots busy: ALU-bound
+            out[name].update({"bound": "alu", "hbm_frac": gbs / peak})
+            wi = issue_counts().get("k_step_scalar<float> (entropic)")
+            if wi is not None:
+                rate = wi * lu / secs
+                pk = issue_peak(dev.index or 0)
+                out[name].update({"warp_instr_per_lu": wi, "achieved": rate / 1e12,
+                                  "peak": pk / 1e12, "unit": "T warp instr/s",
+                                  "frac": rate / pk})
         del lat
     return out
 
@@ -533,6 +544,37 @@ def fp64_instruction_counts():
             if hashlib.sha256(fh.read()).hexdigest()[:16] == rec.get("source_sha256_16"):
                 out[name] = (rec["fp64_flops_per_lu"], rec["fp64_instr_per_lu"])
     return out
+
+
+def issue_counts():
+    """Warp instructions per lattice update of the issue-bound kernels
+    (sm__inst_executed.sum over the launch's cells, ncu) from the committed
+    summary, valid only while the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "elbm_issue.json")
+    if not os.path.exists(p):
+        return {}
+    with open(p) as fh:
+        d = json.load(fh)
+    out = {}
+    for name, rec in d.get("kernels", {}).items():
+        src = os.path.join(ROOT, "paper_1809_06735_gb300", "csrc", rec["source"])
+        with open(src, "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] == rec.get("source_sha256_16"):
+                out[name] = rec["warp_instr_per_lu"]
+    return out
+
+
+def issue_peak(dev_index=0):
+    """Peak instruction issue of the GPU: 4 schedulers per SM, one warp
+    instruction each per clock, at the maximum SM clock (warp instr/s)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
+    return 4.0 * sms * mhz * 1e6
 
 
 def fp64_roofline(counts, glups, peaks):
@@ -752,8 +794,8 @@ def workload_config():
 # each kernel family for Nsight Compute.  Sizes keep the working set above the
 # L2 (so DRAM counters mean something) and below a few GB.  The step cases
 # create their handle with the launch-shape autotuner on: 2 storages x 18
-# shapes x 8 launches = 288 launches of k_step_f32_vec come before the first
-# step of the run.
+# shapes x 8 launches, then the 3 fastest again 3 x 14 launches each, so 414
+# launches of k_step_f32_vec come before the first step of the run.
 # ---------------------------------------------------------------------------
 
 
@@ -770,7 +812,7 @@ def case_step(P, members=16, n=512, steps=25):
 def case_step_full(P, members=64, n=512, steps=200):
     """The ensemble benchmark's stream-collide workload (64 x 512^2, FP32,
     autotuned storage and shape) for single-pass DRAM counters; the
-    autotuner's 288 launches and the 64 initialisations come first."""
+    autotuner's 414 launches and the 64 initialisations come first."""
     import torch
     lat = P.Lattice([P.Member(n, n, 0.52)] * members, precision=32, graph_steps=0, diag_batch=1)
     for m in range(members):

@@ -1695,7 +1695,7 @@ cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int 
   k_scales<T><<<dim3(nF, G), 256, 0, s>>>(jobs, nF);
   const int ns = (nx + kStrip - 1) / kStrip;
   k_strip_sums<T><<<dim3((ny + 7) / 8, nF, G), 256, 0, s>>>(jobs);
-  // row blocks when strips x jobs would leave most SMs idle
+  // row blocks when strips x jobs would leave SMs idle
   int rb_rows = ny, nrb = 1;
   {
     static int sms = 0;
@@ -1706,7 +1706,7 @@ cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int 
         sms = 1;
     }
     const long long ctas = (long long)ns * G;
-    if (ctas < 2LL * sms && ny >= 256) {
+    if (ctas < sms && ny >= 256) {
       long long want = (2LL * sms + ctas - 1) / ctas;
       if (want > ny / 64) want = ny / 64;
       rb_rows = (int)(((ny + want - 1) / want + 31) / 32 * 32);

@@ -153,6 +153,11 @@ cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tile
                                      cudaStream_t s);
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member,
                                int nx, int ny, int cur, cudaStream_t s);
+struct InitList;
+// The general kernel for the members members[0..n) (host array), one launch
+// per 256 members, grid sized for nx_max x ny_max.
+cudaError_t launch_step_scalar_batch(int precision, const Member *d_members, const int *members,
+                                     int n, int nx_max, int ny_max, int state, cudaStream_t s);
 // Grid-wide barrier words of the persistent small-grid step (device memory,
 // zeroed by each launch): arrival count, generation, error flag.
 struct GridSync {

@@ -93,6 +93,51 @@ __device__ __forceinline__ void moments_f64(const double f[kQ], double &rho, dou
 // ---------------------------------------------------------------------------
 
 // phi(z) = (1 + z) ln(1 + z) - z: series where the terms cancel.
+// ln(1 + z) and exp(x) - 1 for the FP32 entropic collision, whose
+// arguments are mostly small (relative populations' departures, velocity
+// factors): their Taylor series in Horner form where |z| < 1/8 (the terms
+// after z^9 / 9 are below 1e-10 of |z|, under the FP32 rounding) and
+// |x| < 1/4 (after x^9 / 9!: below 1e-12), the library functions elsewhere.
+// FP64 keeps the library functions.
+__device__ __forceinline__ float ln1p_series(float z) {
+  float p = 1.0f / 9.0f;
+  p = fmaf(-z, p, 1.0f / 8.0f);
+  p = fmaf(-z, p, 1.0f / 7.0f);
+  p = fmaf(-z, p, 1.0f / 6.0f);
+  p = fmaf(-z, p, 1.0f / 5.0f);
+  p = fmaf(-z, p, 1.0f / 4.0f);
+  p = fmaf(-z, p, 1.0f / 3.0f);
+  p = fmaf(-z, p, 1.0f / 2.0f);
+  p = fmaf(-z, p, 1.0f);
+  return z * p;
+}
+__device__ __forceinline__ float em1_series(float x) {
+  float p = 1.0f / 362880.0f;
+  p = fmaf(x, p, 1.0f / 40320.0f);
+  p = fmaf(x, p, 1.0f / 5040.0f);
+  p = fmaf(x, p, 1.0f / 720.0f);
+  p = fmaf(x, p, 1.0f / 120.0f);
+  p = fmaf(x, p, 1.0f / 24.0f);
+  p = fmaf(x, p, 1.0f / 6.0f);
+  p = fmaf(x, p, 1.0f / 2.0f);
+  p = fmaf(x, p, 1.0f);
+  return x * p;
+}
+template <typename T>
+__device__ __forceinline__ T ln1p_e(T z) {
+  if constexpr (sizeof(T) == 4)
+    return fabsf(z) < 0.125f ? ln1p_series(z) : log1pf(z);
+  else
+    return log1p(z);
+}
+template <typename T>
+__device__ __forceinline__ T expm1_e(T x) {
+  if constexpr (sizeof(T) == 4)
+    return fabsf(x) < 0.25f ? em1_series(x) : expm1f(x);
+  else
+    return expm1(x);
+}
+
 template <typename T>
 __device__ __forceinline__ T phi_entropy(T z) {
   const T lim = sizeof(T) == 4 ? T(0.1) : T(0.1);
@@ -106,7 +151,7 @@ __device__ __forceinline__ T phi_entropy(T z) {
     }
     return s;
   }
-  return (T(1) + z) * log1p(z) - z;
+  return (T(1) + z) * ln1p_e<T>(z) - z;
 }
 
 // g(a) = sum f phi(a y) - a S2, y = Delta / f, S2 = sum Delta ln(1 + y);
@@ -124,11 +169,11 @@ __device__ __forceinline__ T entropy_gap(const T f[kQ], const T y[kQ], T S2, T a
 
 // The root alpha > 1 (alpha = 2 at equilibrium, for non-positive populations
 // or without a root below min(a_max, 64)).  FP64: bisection to 1e-15 (the
-// oracle's procedure); FP32: Newton from 2, g'(a) = sum Delta ln(1 + a y) -
-// S2, kept inside a bisection bracket, until |g| is at the level of its
-// rounding (1e-6 of the terms; then one last Newton step if it stays in the
-// bracket) or the step is below 1e-6 -- about 2-3 iterations, so the lanes
-// of a warp finish together.
+// oracle's procedure); FP32: Newton from the near-equilibrium series start,
+// g'(a) = sum Delta ln(1 + a y) - S2, kept inside a bisection bracket, until
+// |g| is at the level of its rounding (1e-6 of the terms; then one last
+// Newton step if it stays in the bracket) or a step below 1e-3 a (error of
+// order 1e-6 a after it) -- usually one iteration.
 template <typename T>
 __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
   T y[kQ], ymax = T(0), amax = T(64), S2 = T(0);
@@ -138,7 +183,7 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
     y[l] = d[l] / f[l];
     ymax = fmax(ymax, fabs(y[l]));
     if (y[l] < T(0)) amax = fmin(amax, -T(1) / y[l]);
-    S2 += d[l] * log1p(y[l]);
+    S2 += d[l] * ln1p_e<T>(y[l]);
   }
   if (ymax < (sizeof(T) == 4 ? T(1e-7) : T(1e-12))) return T(2);
   T lo = T(1), hi = amax * (sizeof(T) == 4 ? T(1 - 1e-6) : T(1 - 1e-12));
@@ -177,7 +222,7 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
       T s = T(0), dg = -S2;
 #pragma unroll
       for (int l = 0; l < kQ; ++l) {
-        const T z = a * y[l], lz = log1p(z);
+        const T z = a * y[l], lz = ln1p_e<T>(z);
         T ph;
         if (fabs(z) < T(0.1)) {
           ph = T(0);
@@ -227,9 +272,9 @@ template <typename T>
 __device__ __forceinline__ void entropic_logp(T ux, T uy, T lp[kQ]) {
   const T sx = sqrt(T(1) + T(3) * ux * ux), sy = sqrt(T(1) + T(3) * uy * uy);
   const T qx = T(3) * ux * ux / (T(1) + sx), qy = T(3) * uy * uy / (T(1) + sy);
-  const T a0x = log1p(-qx), a0y = log1p(-qy);
-  const T a1x = log1p((T(3) * ux + qx) / (T(1) - ux));
-  const T a1y = log1p((T(3) * uy + qy) / (T(1) - uy));
+  const T a0x = ln1p_e<T>(-qx), a0y = ln1p_e<T>(-qy);
+  const T a1x = ln1p_e<T>((T(3) * ux + qx) / (T(1) - ux));
+  const T a1y = ln1p_e<T>((T(3) * uy + qy) / (T(1) - uy));
 #pragma unroll
   for (int l = 0; l < kQ; ++l)
     lp[l] = a0x + a0y + (T)cx_of(l) * a1x + (T)cy_of(l) * a1y;
@@ -264,7 +309,7 @@ __device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
     const T t = (T)w_of(l);
-    const T em = expm1(lp[l]);  // P_l - 1
+    const T em = expm1_e<T>(lp[l]);  // P_l - 1
     if constexpr (sizeof(T) == 4) {
       f[l] = t * rho0 + v[l];
       d[l] = t * (drho * (T(1) + em) + rho0 * em) - v[l];  // f_eq - f, deviation form
@@ -272,7 +317,7 @@ __device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
       f[l] = v[l];
       d[l] = t * rho * (T(1) + em) - v[l];
     }
-    Fl[l] = t * rho * (T(1) + em) * expm1(lps[l] - lp[l]);
+    Fl[l] = t * rho * (T(1) + em) * expm1_e<T>(lps[l] - lp[l]);
   }
   const T a = elbm_alpha<T>(f, d);
   const T ab = a / (T(2) * tau0);
@@ -798,6 +843,21 @@ __global__ void __launch_bounds__(kPersistThreads)
   }
 }
 
+// The general kernel for several members in one launch: blockIdx.z picks
+// the member from the list (grid sized for the largest; the others' surplus
+// CTAs return at once), so a step of many general-kernel members (the
+// entropic collision, FP64 ensembles, nx % 4 != 0) fills the GPU without a
+// partial wave per member.
+template <typename T>
+__global__ void k_step_scalar_multi(const Member *__restrict__ members, InitList list,
+                                    int state) {
+  const Member &M = members[list.m[blockIdx.z]];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= M.nx || y >= M.ny) return;
+  step_cell<T, false>(M, state, x, y);
+}
+
 static dim3 grid2d(int nx, int ny, dim3 b) {
   return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y);
 }
@@ -863,6 +923,23 @@ cudaError_t launch_step_scalar_persistent(int precision, const Member *d_members
                                        dim3(kPersistThreads), args, 0, s);
   return cudaLaunchCooperativeKernel((const void *)k_step_scalar_persistent<double>, dim3(ctas),
                                      dim3(kPersistThreads), args, 0, s);
+}
+
+cudaError_t launch_step_scalar_batch(int precision, const Member *d_members, const int *members,
+                                     int n, int nx_max, int ny_max, int state, cudaStream_t s) {
+  const dim3 b = (long long)nx_max * ny_max < (1LL << 15) ? dim3(32, 2) : dim3(64, 4);
+  for (int i0 = 0; i0 < n; i0 += InitList::kMax) {
+    InitList list;
+    list.n = n - i0 < InitList::kMax ? n - i0 : InitList::kMax;
+    for (int i = 0; i < list.n; ++i) list.m[i] = members[i0 + i];
+    dim3 g = grid2d(nx_max, ny_max, b);
+    g.z = list.n;
+    if (precision == 32)
+      k_step_scalar_multi<float><<<g, b, 0, s>>>(d_members, list, state);
+    else
+      k_step_scalar_multi<double><<<g, b, 0, s>>>(d_members, list, state);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member, int nx,
