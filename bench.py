@@ -352,24 +352,35 @@ def median_timed(stream, fn, runs=5):
 def paper_forcing_leg(P, stream, dev, peak):
     """The paper's own turbulence forcing (eqs. 14-16, force kind 2) at its
     grid and amplitudes: 64 FP32 members of 256^2, F^T_0 = 8e-4, phase 0,
-    F^R_0 = 1e-5, tau = 0.52.  A step is the damping projection (one read of
-    the populations, 36 B/LU) plus the stream-collide with the shell-force
-    table (72 + 8 B/LU): 116 algorithmic bytes per lattice update.  Median of
-    five timed 200-step runs."""
-    n2, M2, steps = 256, 64, 200
+    F^R_0 = 1e-5, tau = 0.52.  At these amplitudes the flow leaves the
+    low-Mach range within about 250 steps of a u_rms = 0.02 start and then
+    diverges (the FP64 oracle does the same), so every timed run starts
+    from the initial fields again: re-initialisation, 10 untimed steps, 100
+    timed steps (about 0.05 u_rms at the end), median of five; all members
+    are checked finite afterwards.  A step is the damping projection (one
+    read of the populations, 36 B/LU) plus the stream-collide with the
+    shell-force table (72 + 8 B/LU): 116 algorithmic bytes per update."""
+    n2, M2, steps = 256, 64, 100
     lat = P.Lattice([P.Member(n2, n2, 0.52, 1.0, 2, 0, 8e-4, 0.0, 0.0, 1e-5)] * M2,
                     precision=32, graph_steps=50, stream=stream, device=dev)
-    for m in range(M2):
-        lat.init_fields(m, *li.random_phase(n2, seed=3000 + m, u_rms=0.02))
-    lat.step(100)
-    secs = median_timed(stream, lambda: lat.step(steps))
+    fields = [li.random_phase(n2, seed=3000 + m, u_rms=0.02) for m in range(M2)]
+    stacked = [np.stack([f[q] for f in fields]) for q in range(3)]
+    times = []
+    for _ in range(5):
+        lat.init_fields_batch(list(range(M2)), *stacked)
+        lat.step(10)
+        times.append(median_timed(stream, lambda: lat.step(steps), runs=1))
+    secs = float(np.median(times))
+    finite = all(lat.member_status(m) == 0 for m in range(M2))
     lu = M2 * n2 * n2 * steps
-    gbs = 116.0 * lu / secs / 1e9
     tune = lat.tuning()
+    gbs = 116.0 * lu / secs / 1e9
     del lat
     return {"members": M2, "grid": [n2, n2], "FT0": 8e-4, "FR0": 1e-5, "glups": lu / secs / 1e9,
             "bytes_per_lu": 116, "achieved_gbs": gbs, "frac": gbs / peak,
-            "storage": tune["storage"]}
+            "steps_per_run": steps, "fresh_state_runs": True, "finite": finite,
+            "storage": tune["storage"], "projection_rows": tune["projection_rows"],
+            "kernels_per_step": tune["kernels_per_step"]}
 
 
 def collision_models_leg(P, stream, dev, peak):

@@ -202,10 +202,26 @@ long long lbm_launch_count(const lbm_handle *h);
 
 /* Launch configuration the handle uses (host-only; any pointer may be NULL):
  * storage 1 (AA) or 2 (double buffer), warps per CTA and rows per warp of
- * the batched FP32 kernel, persistent grid size (0: one CTA per tile), and
- * the autotuned time of one step in ms (0 when not tuned). */
+ * the batched FP32 kernel, persistent grid size (0: one CTA per tile), the
+ * autotuned time of one step in ms (0 when not tuned), and the rows per
+ * thread of the FP32 eq. (16) projection (force kind 2). */
 int lbm_tuning(const lbm_handle *h, int *storage, int *warps, int *rows,
-               int *grid, float *step_ms);
+               int *grid, float *step_ms, int *proj_rows);
+
+/* Kernels one time step of the handle launches (host-only; -1 for a NULL
+ * handle): 1 for the batched FP32 kernel, plus the general kernel's launches
+ * for members it does not take, plus the damping projection of eq. (16)
+ * when some member has the paper's forcing (force kind 2). */
+long long lbm_kernels_per_step(const lbm_handle *h);
+
+/* Sets the launch configuration in place of the autotuned one (host-side;
+ * the populations and the storage are kept): for the batched FP32 kernel
+ * warps 1..8 per CTA, rows 1, 2 or 4 per warp and grid CTAs (0: one CTA per
+ * tile); proj_rows 1..64 rows per thread of the FP32 eq. (16) projection
+ * (force kind 2, nx % 4 == 0: a CTA covers 128 x 8 proj_rows cells), 0 to
+ * keep the current value.  Results do not depend on any of these.
+ * LBM_ERR_ARG for other values, with the previous configuration kept. */
+int lbm_set_launch(lbm_handle *h, int warps, int rows, int grid, int proj_rows);
 
 /* Records the moment snapshot (rho, j) of every member at the current time
  * into the 3-slot history used by the eq. (17) time derivative. */

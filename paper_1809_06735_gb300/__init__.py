@@ -89,7 +89,9 @@ def load_library(path: str = LIB_PATH):
         "lbm_step": ([P, I], I),
         "lbm_time": ([P], ctypes.c_longlong),
         "lbm_launch_count": ([P], ctypes.c_longlong),
-        "lbm_tuning": ([P, P, P, P, P, P], I),
+        "lbm_kernels_per_step": ([P], ctypes.c_longlong),
+        "lbm_set_launch": ([P, I, I, I, I], I),
+        "lbm_tuning": ([P, P, P, P, P, P, P], I),
         "lbm_record_snapshot": ([P], I),
         "lbm_moments": ([P, I, P, P, P, P], I),
         "lbm_global_balance": ([P, I, P], I),
@@ -282,13 +284,20 @@ class Lattice:
 
     def tuning(self) -> dict:
         """Launch configuration in use (storage 'aa' or 'double_buffer', CTA
-        shape, grid, autotuned ms per step)."""
-        st, w, r, g = (ctypes.c_int() for _ in range(4))
+        shape, grid, autotuned ms per step, kernels per time step)."""
+        st, w, r, g, pr = (ctypes.c_int() for _ in range(5))
         ms = ctypes.c_float()
         self._check(self.lib.lbm_tuning(self.h, ctypes.byref(st), ctypes.byref(w), ctypes.byref(r),
-                                        ctypes.byref(g), ctypes.byref(ms)))
+                                        ctypes.byref(g), ctypes.byref(ms), ctypes.byref(pr)))
         return {"storage": "aa" if st.value == 1 else "double_buffer", "warps_per_cta": w.value,
-                "rows_per_warp": r.value, "grid_ctas": g.value, "tuned_step_ms": ms.value}
+                "rows_per_warp": r.value, "grid_ctas": g.value, "tuned_step_ms": ms.value,
+                "projection_rows": pr.value,
+                "kernels_per_step": int(self.lib.lbm_kernels_per_step(self.h))}
+
+    def set_launch(self, warps: int, rows: int, grid: int = 0, proj_rows: int = 0):
+        """Replace the autotuned launch configuration (see lbm_set_launch);
+        proj_rows 0 keeps the projection's rows per thread."""
+        self._check(self.lib.lbm_set_launch(self.h, warps, rows, grid, proj_rows))
 
     def record_snapshot(self):
         self._check(self.lib.lbm_record_snapshot(self.h))
@@ -584,6 +593,11 @@ class Lattice3D:
     @property
     def time(self) -> int:
         return int(self.lib.lbm3d_time(self.h))
+
+    def set_launch(self, warps: int, rows: int, grid: int = 0, proj_rows: int = 0):
+        """Replace the autotuned launch configuration (see lbm_set_launch);
+        proj_rows 0 keeps the projection's rows per thread."""
+        self._check(self.lib.lbm_set_launch(self.h, warps, rows, grid, proj_rows))
 
     def record_snapshot(self):
         self._check(self.lib.lbm3d_record_snapshot(self.h))

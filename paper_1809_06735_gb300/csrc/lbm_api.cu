@@ -165,8 +165,9 @@ Layout make_layout(const lbm_config *cfg) {
   size_t max_tiles = 0;
   for (int m = 0; m < n; ++m) {
     const lbm_member_cfg &c = cfg->members[m];
-    if (vector_eligible(c, cfg->precision))
+    if (vector_eligible(c, cfg->precision)) {
       max_tiles += (size_t)((c.nx + kTileW - 1) / kTileW) * c.ny;
+    }
   }
   L.tiles = take(sizeof(Tile) * std::max<size_t>(max_tiles, 1));
   L.status = take(sizeof(int) * n);
@@ -253,7 +254,7 @@ struct lbm_handle {
   long long t = 0;
   long long ring_time[3] = {-1, -1, -1};
   lbm::DiagScratch sc{};
-  lbm::LaunchCfg lc{8, 1, 0, 0};
+  lbm::LaunchCfg lc{8, 1, 0, 0, 8};
   int graph_k = 0;
   cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // by storage state
   int persist_ctas = 0;  // > 0: one small general-kernel member, steps in one cooperative launch
@@ -323,7 +324,7 @@ int project(lbm_handle *h, cudaStream_t s, int cur, int slot) {
   int nx, ny;
   max_grid(h, &nx, &ny);
   CK(lbm::launch_projection(h->precision, h->d_members, (int)h->mcfg.size(), nx, ny, cur, slot,
-                            h->proj_quad, s));
+                            h->proj_quad, h->lc.proj_rows, s));
   return LBM_OK;
 }
 
@@ -492,7 +493,7 @@ int autotune(lbm_handle *h) {
     for (int wy : {4, 8})
       for (int rows : {1, 2, 4})
         for (int per : {0, 4, 8})
-          cands.push_back({{wy, rows, per * nsm, h->lc.paper_force}, st, 0.f});
+          cands.push_back({{wy, rows, per * nsm, h->lc.paper_force, h->lc.proj_rows}, st, 0.f});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // 2 warm-up and `steps` timed steps of candidate i: ms per step
   auto time_candidate = [&](size_t i, int steps, float *ms) -> int {
@@ -537,6 +538,25 @@ int autotune(lbm_handle *h) {
     if (t[1] < best_ms) {
       best_ms = t[1];
       best = order[k];
+    }
+  }
+  // with the paper forcing, the rows per thread of the projection (its
+  // pipelining depth and CTA count) on the chosen shape, timed likewise
+  if (rc == LBM_OK && h->has_kind2 && h->proj_quad) {
+    const Cand base = cands[best];
+    for (int pr : {4, 16}) {
+      if (rc != LBM_OK) break;
+      if (pr == base.lc.proj_rows) continue;
+      cands.push_back(base);
+      cands.back().lc.proj_rows = pr;
+      float t[3];
+      for (int r = 0; r < 3 && rc == LBM_OK; ++r) rc = time_candidate(cands.size() - 1, 12, &t[r]);
+      if (rc != LBM_OK) break;
+      std::sort(t, t + 3);
+      if (t[1] < best_ms) {
+        best_ms = t[1];
+        best = (int)cands.size() - 1;
+      }
     }
   }
   // the events are released on every path
@@ -866,9 +886,26 @@ long long lbm_time(const lbm_handle *h) { return h ? h->t : -1; }
 
 long long lbm_launch_count(const lbm_handle *h) { return h ? h->launches : -1; }
 
-int lbm_tuning(const lbm_handle *h, int *storage, int *warps, int *rows, int *grid,
-               float *step_ms) {
+long long lbm_kernels_per_step(const lbm_handle *h) { return h ? kernels_per_step(h) : -1; }
+
+int lbm_set_launch(lbm_handle *h, int warps, int rows, int grid, int proj_rows) {
   if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (rows != 1 && rows != 2 && rows != 4) return fail(h, LBM_ERR_ARG, "rows must be 1, 2 or 4");
+  if (grid < 0) return fail(h, LBM_ERR_ARG, "grid must be >= 0");
+  if (warps < 1 || warps > 8) return fail(h, LBM_ERR_ARG, "warps must be 1..8");
+  if (proj_rows < 0 || proj_rows > 64) return fail(h, LBM_ERR_ARG, "proj_rows must be 0..64");
+  if (int rc = wait_diag(h)) return rc;
+  drop_graphs(h);
+  h->lc = lbm::LaunchCfg{warps, rows, grid, h->lc.paper_force,
+                         proj_rows > 0 ? proj_rows : h->lc.proj_rows};
+  h->tuned_ms = 0.f;
+  return build_tiles(h);
+}
+
+int lbm_tuning(const lbm_handle *h, int *storage, int *warps, int *rows, int *grid,
+               float *step_ms, int *proj_rows) {
+  if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (proj_rows) *proj_rows = h->lc.proj_rows;
   if (storage) *storage = h->cur >= 2 ? 1 : 2;
   if (warps) *warps = h->lc.block_warps_y;
   if (rows) *rows = h->lc.rows_per_warp;
@@ -1292,7 +1329,9 @@ int lbm_member_status(lbm_handle *h, int member, int *status) {
   CK(cudaMemcpyAsync(&gave_up, h->gsync.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (gave_up)
-    return fail(h, LBM_ERR_TIMEOUT, "a persistent step kernel gave up waiting at its grid barrier");
+    return fail(h, LBM_ERR_TIMEOUT,
+                "a persistent step kernel gave up waiting for another CTA (grid barrier or "
+                "damping coefficients)");
   return LBM_OK;
 }
 

@@ -143,6 +143,8 @@ struct LaunchCfg {
   int paper_force;    // kernel variant: 0 plain; 1 some member has force kind 2
                       // (BGK collisions); 2 some member has a variable-viscosity
                       // collision (any force)
+  int proj_rows;      // rows per thread of the FP32 four-cell projection (force
+                      // kind 2): a block covers 128 x 8 proj_rows cells
 };
 
 // One step of every vector-kernel member (flip: tiles in reverse order).
@@ -190,10 +192,14 @@ cudaError_t launch_set_populations(int precision, const Member *d_members, int m
 // state (storage `state`) of every kind-2 member on the 6 mode pairs, then
 // the coefficients (kDamp doubles): slot < 0 into Member::damp / damp_f
 // (the step about to run), slot 0..2 into that ring slot of damp_ring.
-// One launch; members of other kinds are skipped.
+// One launch; members of other kinds are skipped.  quad: the FP32
+// four-cell kernel (every kind-2 member with nx % 4 == 0), prow rows per
+// thread (>= 1).
 cudaError_t launch_projection(int precision, const Member *d_members, int n_members,
-                              int nx_max, int ny_max, int state, int slot, bool quad,
+                              int nx_max, int ny_max, int state, int slot, bool quad, int prow,
                               cudaStream_t s);
+// Resident CTAs per SM of the four-cell projection (0 if unknown).
+int project4_ctas_per_sm();
 // The ring snapshot of every member in one launch (layout at Member::snap).
 cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_members,
                                  int nx_max, int ny_max, int state, int slot, bool quad,

@@ -483,177 +483,184 @@ __device__ __forceinline__ void paper_force4(const Member &M, int x, int y, floa
   }
 }
 
-// SNAP: the step also records the snapshot-ring entry of the state it
-// reads (slot snap_slot), the same compensated pairs as k_snapshot_ring.
-template <int ROWS, int MODE, int PF, bool SNAP = false>
-__global__ void __launch_bounds__(256, PF == 2 ? 3 : (PF == 1 || SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
-                                                      const Tile *__restrict__ tiles,
-                                                      int ntiles, int cur, int flip, int snap_slot) {
+// One tile of the stream-collide: 128 x (blockDim.y * ROWS) cells of one
+// member, 4 consecutive cells per lane.  SNAP: the step also records the
+// snapshot-ring entry of the state it reads (slot snap_slot), the same
+// compensated pairs as k_snapshot_ring.
+template <int ROWS, int MODE, int PF, bool SNAP>
+__device__ __forceinline__ void step_tile(const Member *__restrict__ members, const Tile tl,
+                                          int cur, int snap_slot) {
   const int lane = threadIdx.x;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    // flip: the tiles in reverse order, so that a step starts where the
-    // previous one ended (those populations are still in L2)
-    const Tile tl = tiles[flip ? ntiles - 1 - t : t];
-    const Member &M = members[tl.member];
-    const int nx = M.nx, ny = M.ny, pitch = M.pitch;
-    const size_t plane = M.plane;
-    const float *src = static_cast<const float *>(MODE == 0 ? M.pop[cur] : M.pop[0]);
-    float *dst = static_cast<float *>(MODE == 0 ? M.pop[cur ^ 1] : M.pop[0]);
-    const float *__restrict__ fxt = static_cast<const float *>(M.fx_tab);
-    const float *__restrict__ fyt = static_cast<const float *>(M.fy_tab);
-    const float rho0 = M.rho0_f, om = M.omega_f, alpha = M.alpha_f;
-    const int x = tl.x0 + 4 * lane;
-    const bool active = x < nx;
-    const bool last = active && (lane == 31 || x + 4 >= nx);  // last active lane of the row segment
-    float4 fy4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (active) fy4 = *reinterpret_cast<const float4 *>(fyt + x);
-    const float fy[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
-    const int xprev = (x == 0) ? nx - 1 : x - 1;  // cell left of the chunk
-    const int xnext = (x + 4 >= nx) ? 0 : x + 4;  // cell right of the chunk
+  const Member &M = members[tl.member];
+  const int nx = M.nx, ny = M.ny, pitch = M.pitch;
+  const size_t plane = M.plane;
+  const float *src = static_cast<const float *>(MODE == 0 ? M.pop[cur] : M.pop[0]);
+  float *dst = static_cast<float *>(MODE == 0 ? M.pop[cur ^ 1] : M.pop[0]);
+  const float *__restrict__ fxt = static_cast<const float *>(M.fx_tab);
+  const float *__restrict__ fyt = static_cast<const float *>(M.fy_tab);
+  const float rho0 = M.rho0_f, om = M.omega_f, alpha = M.alpha_f;
+  const int x = tl.x0 + 4 * lane;
+  const bool active = x < nx;
+  const bool last = active && (lane == 31 || x + 4 >= nx);  // last active lane of the row segment
+  float4 fy4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (active) fy4 = *reinterpret_cast<const float4 *>(fyt + x);
+  const float fy[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
+  const int xprev = (x == 0) ? nx - 1 : x - 1;  // cell left of the chunk
+  const int xnext = (x + 4 >= nx) ? 0 : x + 4;  // cell right of the chunk
 
 #pragma unroll 1
-    for (int r = 0; r < ROWS; ++r) {
-      const int y = tl.y0 + threadIdx.y * ROWS + r;
-      if (y >= ny) break;  // uniform per warp
-      const int ym = (y == 0) ? ny - 1 : y - 1;
-      const int yp = (y + 1 == ny) ? 0 : y + 1;
-      float v[kQ][4];
+  for (int r = 0; r < ROWS; ++r) {
+    const int y = tl.y0 + threadIdx.y * ROWS + r;
+    if (y >= ny) break;  // uniform per warp
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y + 1 == ny) ? 0 : y + 1;
+    float v[kQ][4];
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const int cxl = cx_of(l), cyl = cy_of(l);
+      if (MODE == 1) {  // own cell, own slot
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (active)
+          o = __ldg(reinterpret_cast<const float4 *>(src + (size_t)l * plane +
+                                                     (size_t)y * pitch + x));
+        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
+        continue;
+      }
+      const int slot = MODE == 2 ? opposite(l) : l;
+      const int ys = cyl == 0 ? y : (cyl > 0 ? ym : yp);  // pull from y - c_y
+      const float *row = src + (size_t)slot * plane + (size_t)ys * pitch;
+      // read-only (non-coherent) loads only when source and destination
+      // differ; the in-place phase reads what it later overwrites
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (active)
+        o = MODE == 0 ? __ldg(reinterpret_cast<const float4 *>(row + x))
+                      : *reinterpret_cast<const float4 *>(row + x);
+      if (cxl == 0) {
+        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
+      } else if (cxl > 0) {  // pull from x - 1
+        float prev = __shfl_up_sync(0xffffffffu, o.w, 1);
+        if (active && (lane == 0 || x == 0)) prev = MODE == 0 ? __ldg(row + xprev) : row[xprev];
+        v[l][0] = prev; v[l][1] = o.x; v[l][2] = o.y; v[l][3] = o.z;
+      } else {  // pull from x + 1
+        float next = __shfl_down_sync(0xffffffffu, o.x, 1);
+        if (last) next = MODE == 0 ? __ldg(row + xnext) : row[xnext];
+        v[l][0] = o.y; v[l][1] = o.z; v[l][2] = o.w; v[l][3] = next;
+      }
+    }
+    if constexpr (SNAP) {
+      if (active) {  // (rho - rho0, j_x, j_y) of f(., n) as compensated pairs
+        float hs[3][4], ls[3][4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int one[kQ] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+          const int sgn[6] = {1, 1, 1, -1, -1, -1};
+          float f[kQ];
+#pragma unroll
+          for (int l = 0; l < kQ; ++l) f[l] = v[l][c];
+          const float ax[6] = {f[1], f[5], f[8], f[3], f[6], f[7]};
+          const float ay[6] = {f[2], f[5], f[6], f[4], f[7], f[8]};
+          csum_pair(f, one, kQ, hs[0][c], ls[0][c]);
+          csum_pair(ax, sgn, 6, hs[1][c], ls[1][c]);
+          csum_pair(ay, sgn, 6, hs[2][c], ls[2][c]);
+        }
+        const size_t N = (size_t)nx * ny;
+        float *d = reinterpret_cast<float *>(M.snap) + (size_t)snap_slot * 6 * N +
+                   (size_t)y * nx + x;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          __stcs(reinterpret_cast<float4 *>(d + (size_t)(2 * q) * N),
+                 make_float4(hs[q][0], hs[q][1], hs[q][2], hs[q][3]));
+          __stcs(reinterpret_cast<float4 *>(d + (size_t)(2 * q + 1) * N),
+                 make_float4(ls[q][0], ls[q][1], ls[q][2], ls[q][3]));
+        }
+      }
+    }
+    if (active) {
+      float fxc[4], fyc[4];
+      if (PF != 0 && M.force_kind == 2) {
+        paper_force4(M, x, y, fxc, fyc);
+      } else {
+        const float fx = fxt[y];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          fxc[c] = fx;
+          fyc[c] = fy[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float g[kQ];
+#pragma unroll
+        for (int l = 0; l < kQ; ++l) g[l] = v[l][c];
+        if constexpr (PF == 2)
+          collide_f32<true>(g, rho0, om, fxc[c], fyc[c], alpha, M.collision, M.tau_f, M.Cs_f);
+        else
+          collide_f32(g, rho0, om, fxc[c], fyc[c], alpha);
+#pragma unroll
+        for (int l = 0; l < kQ; ++l) v[l][c] = g[l];
+      }
+    }
+    if (MODE == 0 || MODE == 1) {
+      if (active) {
+#pragma unroll
+        for (int l = 0; l < kQ; ++l) {
+          const int slot = MODE == 1 ? opposite(l) : l;
+          __stcs(reinterpret_cast<float4 *>(dst + (size_t)slot * plane + (size_t)y * pitch + x),
+                 make_float4(v[l][0], v[l][1], v[l][2], v[l][3]));
+        }
+      }
+    } else {  // AA odd phase: f*_l(x) goes to slot l at x + c_l
 #pragma unroll
       for (int l = 0; l < kQ; ++l) {
         const int cxl = cx_of(l), cyl = cy_of(l);
-        if (MODE == 1) {  // own cell, own slot
-          float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (active)
-            o = __ldg(reinterpret_cast<const float4 *>(src + (size_t)l * plane +
-                                                       (size_t)y * pitch + x));
-          v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
-          continue;
-        }
-        const int slot = MODE == 2 ? opposite(l) : l;
-        const int ys = cyl == 0 ? y : (cyl > 0 ? ym : yp);  // pull from y - c_y
-        const float *row = src + (size_t)slot * plane + (size_t)ys * pitch;
-        // read-only (non-coherent) loads only when source and destination
-        // differ; the in-place phase reads what it later overwrites
-        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (active)
-          o = MODE == 0 ? __ldg(reinterpret_cast<const float4 *>(row + x))
-                        : *reinterpret_cast<const float4 *>(row + x);
+        const int yd = cyl == 0 ? y : (cyl > 0 ? yp : ym);
+        float *drow = dst + (size_t)l * plane + (size_t)yd * pitch;
         if (cxl == 0) {
-          v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
-        } else if (cxl > 0) {  // pull from x - 1
-          float prev = __shfl_up_sync(0xffffffffu, o.w, 1);
-          if (active && (lane == 0 || x == 0)) prev = MODE == 0 ? __ldg(row + xprev) : row[xprev];
-          v[l][0] = prev; v[l][1] = o.x; v[l][2] = o.y; v[l][3] = o.z;
-        } else {  // pull from x + 1
-          float next = __shfl_down_sync(0xffffffffu, o.x, 1);
-          if (last) next = MODE == 0 ? __ldg(row + xnext) : row[xnext];
-          v[l][0] = o.y; v[l][1] = o.z; v[l][2] = o.w; v[l][3] = next;
-        }
-      }
-      if constexpr (SNAP) {
-        if (active) {  // (rho - rho0, j_x, j_y) of f(., n) as compensated pairs
-          float hs[3][4], ls[3][4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int one[kQ] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
-            const int sgn[6] = {1, 1, 1, -1, -1, -1};
-            float f[kQ];
-#pragma unroll
-            for (int l = 0; l < kQ; ++l) f[l] = v[l][c];
-            const float ax[6] = {f[1], f[5], f[8], f[3], f[6], f[7]};
-            const float ay[6] = {f[2], f[5], f[6], f[4], f[7], f[8]};
-            csum_pair(f, one, kQ, hs[0][c], ls[0][c]);
-            csum_pair(ax, sgn, 6, hs[1][c], ls[1][c]);
-            csum_pair(ay, sgn, 6, hs[2][c], ls[2][c]);
-          }
-          const size_t N = (size_t)nx * ny;
-          float *d = reinterpret_cast<float *>(M.snap) + (size_t)snap_slot * 6 * N +
-                     (size_t)y * nx + x;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            __stcs(reinterpret_cast<float4 *>(d + (size_t)(2 * q) * N),
-                   make_float4(hs[q][0], hs[q][1], hs[q][2], hs[q][3]));
-            __stcs(reinterpret_cast<float4 *>(d + (size_t)(2 * q + 1) * N),
-                   make_float4(ls[q][0], ls[q][1], ls[q][2], ls[q][3]));
-          }
-        }
-      }
-      if (active) {
-        float fxc[4], fyc[4];
-        if (PF != 0 && M.force_kind == 2) {
-          paper_force4(M, x, y, fxc, fyc);
-        } else {
-          const float fx = fxt[y];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            fxc[c] = fx;
-            fyc[c] = fy[c];
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float g[kQ];
-#pragma unroll
-          for (int l = 0; l < kQ; ++l) g[l] = v[l][c];
-          if constexpr (PF == 2)
-            collide_f32<true>(g, rho0, om, fxc[c], fyc[c], alpha, M.collision, M.tau_f, M.Cs_f);
-          else
-            collide_f32(g, rho0, om, fxc[c], fyc[c], alpha);
-#pragma unroll
-          for (int l = 0; l < kQ; ++l) v[l][c] = g[l];
-        }
-      }
-      if (MODE == 0 || MODE == 1) {
-        if (active) {
-#pragma unroll
-          for (int l = 0; l < kQ; ++l) {
-            const int slot = MODE == 1 ? opposite(l) : l;
-            __stcs(reinterpret_cast<float4 *>(dst + (size_t)slot * plane + (size_t)y * pitch + x),
+          if (active)
+            __stcs(reinterpret_cast<float4 *>(drow + x),
                    make_float4(v[l][0], v[l][1], v[l][2], v[l][3]));
-          }
-        }
-      } else {  // AA odd phase: f*_l(x) goes to slot l at x + c_l
-#pragma unroll
-        for (int l = 0; l < kQ; ++l) {
-          const int cxl = cx_of(l), cyl = cy_of(l);
-          const int yd = cyl == 0 ? y : (cyl > 0 ? yp : ym);
-          float *drow = dst + (size_t)l * plane + (size_t)yd * pitch;
-          if (cxl == 0) {
-            if (active)
+        } else if (cxl > 0) {
+          // chunk [x, x+3] receives the cells x-1 .. x+2
+          const float prev = __shfl_up_sync(0xffffffffu, v[l][3], 1);
+          if (active) {
+            if (lane != 0) {
               __stcs(reinterpret_cast<float4 *>(drow + x),
-                     make_float4(v[l][0], v[l][1], v[l][2], v[l][3]));
-          } else if (cxl > 0) {
-            // chunk [x, x+3] receives the cells x-1 .. x+2
-            const float prev = __shfl_up_sync(0xffffffffu, v[l][3], 1);
-            if (active) {
-              if (lane != 0) {
-                __stcs(reinterpret_cast<float4 *>(drow + x),
-                       make_float4(prev, v[l][0], v[l][1], v[l][2]));
-              } else {
-                drow[x + 1] = v[l][0];
-                drow[x + 2] = v[l][1];
-                drow[x + 3] = v[l][2];
-              }
-              if (last) drow[xnext] = v[l][3];
+                     make_float4(prev, v[l][0], v[l][1], v[l][2]));
+            } else {
+              drow[x + 1] = v[l][0];
+              drow[x + 2] = v[l][1];
+              drow[x + 3] = v[l][2];
             }
-          } else {
-            // chunk [x, x+3] receives the cells x+1 .. x+4
-            const float next = __shfl_down_sync(0xffffffffu, v[l][0], 1);
-            if (active) {
-              if (!last) {
-                __stcs(reinterpret_cast<float4 *>(drow + x),
-                       make_float4(v[l][1], v[l][2], v[l][3], next));
-              } else {
-                drow[x] = v[l][1];
-                drow[x + 1] = v[l][2];
-                drow[x + 2] = v[l][3];
-              }
-              if (lane == 0) drow[xprev] = v[l][0];
+            if (last) drow[xnext] = v[l][3];
+          }
+        } else {
+          // chunk [x, x+3] receives the cells x+1 .. x+4
+          const float next = __shfl_down_sync(0xffffffffu, v[l][0], 1);
+          if (active) {
+            if (!last) {
+              __stcs(reinterpret_cast<float4 *>(drow + x),
+                     make_float4(v[l][1], v[l][2], v[l][3], next));
+            } else {
+              drow[x] = v[l][1];
+              drow[x + 1] = v[l][2];
+              drow[x + 2] = v[l][3];
             }
+            if (lane == 0) drow[xprev] = v[l][0];
           }
         }
       }
     }
+  }
+}
+
+template <int ROWS, int MODE, int PF, bool SNAP = false>
+__global__ void __launch_bounds__(256, PF == 2 ? 3 : (PF == 1 || SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
+                                                      const Tile *__restrict__ tiles,
+                                                      int ntiles, int cur, int flip, int snap_slot) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // flip: the tiles in reverse order, so that a step starts where the
+    // previous one ended (those populations are still in L2)
+    step_tile<ROWS, MODE, PF, SNAP>(members, tiles[flip ? ntiles - 1 - t : t], cur, snap_slot);
   }
 }
 
@@ -1315,10 +1322,11 @@ __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ memb
 // The populations of the state are pulled as in k_step_f32_vec (MODE 0:
 // double buffer `state`, 1: AA even, 2: AA odd): one float4 per population
 // and lane, the x-shift by shuffles.  Same sums per cell as k_project.
-// One row's contribution to the 24 damping-mode sums: v holds the pulled
-// FP32 deviations of four consecutive cells of row y (lane's cells), cx..s2x
-// their x trig factors.  Shared by the projection kernels.
-__device__ __forceinline__ void proj_row_accumulate(const Member &M, const float (&v)[kQ][4],
+// One row's contribution to the 24 damping-mode sums: rho, jx, jy are the
+// moments (rho with rho0 added) of four consecutive cells of row y (the
+// lane's cells), cx..s2x their x trig factors.
+__device__ __forceinline__ void proj_row_accumulate(const Member &M, const float (&rho)[4],
+                                                    const float (&jx)[4], const float (&jy)[4],
                                                     const float (&cx)[4], const float (&sx)[4],
                                                     const float (&c2x)[4], const float (&s2x)[4],
                                                     int y, float (&acc)[kDamp]) {
@@ -1336,17 +1344,10 @@ __device__ __forceinline__ void proj_row_accumulate(const Member &M, const float
     for (int q = 0; q < 5; ++q) R[k][q] = 0.f;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float rho = M.rho0_f, jx = 0.f, jy = 0.f;
-#pragma unroll
-    for (int l = 0; l < kQ; ++l) {
-      rho += v[l][i];
-      jx += (float)cx_of(l) * v[l][i];
-      jy += (float)cy_of(l) * v[l][i];
-    }
     // approximate reciprocal (2 ulp): u only enters the damping's mode sums,
     // whose force is F^R_0 ~ 1e-5 times them
-    const float ir = __fdividef(1.0f, rho);
-    const float u[2] = {jx * ir, jy * ir};
+    const float ir = __fdividef(1.0f, rho[i]);
+    const float u[2] = {jx[i] * ir, jy[i] * ir};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       R[k][0] += u[k];
@@ -1374,16 +1375,74 @@ __device__ __forceinline__ void proj_row_accumulate(const Member &M, const float
   }
 }
 
-constexpr int kProj4Rows = 8;
+// The loads of one row of k_project4's pull (MODE 0: double buffer, 1: AA
+// even, 2: AA odd): one float4 per population and lane (o), and e[l] the
+// cell beyond the lane's chunk that the x-shift needs where no neighbouring
+// lane holds it (lane 0 for c_x > 0, the last active lane for c_x < 0).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ members, int state,
-                                                  int slot) {
-  const Member &M = members[blockIdx.z];
-  if (M.force_kind != 2) return;
-  if ((int)(blockIdx.x * 128) >= M.nx || (int)(blockIdx.y * 8 * kProj4Rows) >= M.ny) return;
-  const int nx = M.nx, ny = M.ny, pitch = M.pitch, lane = threadIdx.x;
+__device__ __forceinline__ void proj4_load(const Member &M, const float *src, int y, int x,
+                                           int xprev, int xnext, bool active, bool last,
+                                           int lane, float4 (&o)[kQ], float (&e)[kQ]) {
+  const int ny = M.ny, pitch = M.pitch;
   const size_t plane = M.plane;
-  const int x = blockIdx.x * 128 + 4 * lane;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) {
+    const int cxl = MODE == 1 ? 0 : cx_of(l), cyl = cy_of(l);
+    const int sl = MODE == 2 ? opposite(l) : l;
+    const int ys = MODE == 1 || cyl == 0 ? y : (cyl > 0 ? ym : yp);  // from y - c_y
+    const float *row = src + (size_t)sl * plane + (size_t)ys * pitch;
+    o[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+    e[l] = 0.f;
+    if (active) o[l] = __ldg(reinterpret_cast<const float4 *>(row + x));
+    if (cxl > 0 && active && lane == 0) e[l] = __ldg(row + xprev);
+    if (cxl < 0 && last) e[l] = __ldg(row + xnext);
+  }
+}
+
+// The moments of the lane's four cells from one row's loads: the x-shift of
+// the pull by shuffles, e[l] at the chunk's edge.
+template <int MODE>
+__device__ __forceinline__ void proj4_moments(float rho0, const float4 (&o)[kQ],
+                                              const float (&e)[kQ], bool active, bool last,
+                                              int lane, float (&rho)[4], float (&jx)[4],
+                                              float (&jy)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    rho[i] = rho0;
+    jx[i] = 0.f;
+    jy[i] = 0.f;
+  }
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) {
+    const int cxl = MODE == 1 ? 0 : cx_of(l);
+    float v[4];
+    if (cxl == 0) {
+      v[0] = o[l].x; v[1] = o[l].y; v[2] = o[l].z; v[3] = o[l].w;
+    } else if (cxl > 0) {  // from x - 1
+      float prev = __shfl_up_sync(0xffffffffu, o[l].w, 1);
+      if (active && lane == 0) prev = e[l];
+      v[0] = prev; v[1] = o[l].x; v[2] = o[l].y; v[3] = o[l].z;
+    } else {  // from x + 1
+      float next = __shfl_down_sync(0xffffffffu, o[l].x, 1);
+      if (last) next = e[l];
+      v[0] = o[l].y; v[1] = o[l].z; v[2] = o[l].w; v[3] = next;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      rho[i] += v[i];
+      jx[i] += (float)cx_of(l) * v[i];
+      jy[i] += (float)cy_of(l) * v[i];
+    }
+  }
+}
+// Block (bx, by) of the projection of member M: cells [128 bx, 128 bx + 128)
+// x [8 prow by, 8 prow (by + 1)), CTA (32, 8), prow rows per thread.
+template <int MODE>
+__device__ __forceinline__ void proj4_block(const Member &M, int bx, int by, int state, int slot,
+                                            int prow) {
+  const int nx = M.nx, ny = M.ny, lane = threadIdx.x;
+  const int x = bx * 128 + 4 * lane;
   const bool active = x < nx;
   const bool last = active && (lane == 31 || x + 4 >= nx);
   const int xprev = x == 0 ? nx - 1 : x - 1, xnext = x + 4 >= nx ? 0 : x + 4;
@@ -1402,41 +1461,21 @@ __global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ mem
   float acc[kDamp];
 #pragma unroll
   for (int q = 0; q < kDamp; ++q) acc[q] = 0.f;
+  // software-pipelined over the thread's rows: the loads of the next row are
+  // issued before the mode sums of the current one
+  float4 o[kQ];
+  float e[kQ];
+  const int yb = by * 8 * prow + threadIdx.y;
+  if (yb < ny) proj4_load<MODE>(M, src, yb, x, xprev, xnext, active, last, lane, o, e);
 #pragma unroll 1
-  for (int r = 0; r < kProj4Rows; ++r) {
-    const int y = blockIdx.y * 8 * kProj4Rows + r * 8 + threadIdx.y;
+  for (int r = 0; r < prow; ++r) {
+    const int y = yb + 8 * r;
     if (y >= ny) break;  // whole warps
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
-    float v[kQ][4];
-#pragma unroll
-    for (int l = 0; l < kQ; ++l) {
-      const int cxl = cx_of(l), cyl = cy_of(l);
-      if (MODE == 1) {  // own cell, own slot
-        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (active)
-          o = __ldg(reinterpret_cast<const float4 *>(src + (size_t)l * plane + (size_t)y * pitch + x));
-        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
-        continue;
-      }
-      const int sl = MODE == 2 ? opposite(l) : l;
-      const int ys = cyl == 0 ? y : (cyl > 0 ? ym : yp);  // from y - c_y
-      const float *row = src + (size_t)sl * plane + (size_t)ys * pitch;
-      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (active) o = __ldg(reinterpret_cast<const float4 *>(row + x));
-      if (cxl == 0) {
-        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
-      } else if (cxl > 0) {  // from x - 1
-        float prev = __shfl_up_sync(0xffffffffu, o.w, 1);
-        if (active && (lane == 0 || x == 0)) prev = __ldg(row + xprev);
-        v[l][0] = prev; v[l][1] = o.x; v[l][2] = o.y; v[l][3] = o.z;
-      } else {  // from x + 1
-        float next = __shfl_down_sync(0xffffffffu, o.x, 1);
-        if (last) next = __ldg(row + xnext);
-        v[l][0] = o.y; v[l][1] = o.z; v[l][2] = o.w; v[l][3] = next;
-      }
-    }
-    if (!active) continue;
-    proj_row_accumulate(M, v, cx, sx, c2x, s2x, y, acc);
+    float rho[4], jx[4], jy[4];
+    proj4_moments<MODE>(M.rho0_f, o, e, active, last, lane, rho, jx, jy);
+    if (r + 1 < prow && y + 8 < ny)
+      proj4_load<MODE>(M, src, y + 8, x, xprev, xnext, active, last, lane, o, e);
+    if (active) proj_row_accumulate(M, rho, jx, jy, cx, sx, c2x, s2x, y, acc);
   }
   __shared__ float sh[kDamp][8];
   const int tid = threadIdx.y * 32 + threadIdx.x, wid = threadIdx.y;
@@ -1449,14 +1488,34 @@ __global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ mem
   }
   __syncthreads();
   const int gx = (nx + 127) / 128;
-  const int nblk = gx * ((ny + 8 * kProj4Rows - 1) / (8 * kProj4Rows));
+  const int nblk = gx * ((ny + 8 * prow - 1) / (8 * prow));
   if (tid < kDamp) {
     float a = sh[tid][0];
     for (int w = 1; w < 8; ++w) a += sh[tid][w];
-    M.proj_part[(size_t)(blockIdx.y * gx + blockIdx.x) * kDamp + tid] = (double)a;
+    M.proj_part[(size_t)(by * gx + bx) * kDamp + tid] = (double)a;
     __threadfence();
   }
   project_finalize(M, nblk, slot, tid, lane, wid);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ members, int state,
+                                                  int slot, int prow) {
+  const Member &M = members[blockIdx.z];
+  if (M.force_kind != 2) return;
+  if ((int)(blockIdx.x * 128) >= M.nx || (int)(blockIdx.y * 8 * prow) >= M.ny) return;
+  proj4_block<MODE>(M, blockIdx.x, blockIdx.y, state, slot, prow);
+}
+
+int project4_ctas_per_sm() {
+  static int n = -1;
+  if (n < 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project4<2>, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    n = -1;
+    return 0;
+  }
+  return n;
 }
 
 // The snapshot-ring entry of FP32 members with nx % 4 == 0 and a constant
@@ -1630,17 +1689,18 @@ cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_m
 }
 
 cudaError_t launch_projection(int precision, const Member *d_members, int n_members,
-                              int nx_max, int ny_max, int state, int slot, bool quad,
+                              int nx_max, int ny_max, int state, int slot, bool quad, int prow,
                               cudaStream_t s) {
   if (quad && precision == 32) {  // four cells per lane
-    dim3 g((nx_max + 127) / 128, (ny_max + 8 * kProj4Rows - 1) / (8 * kProj4Rows), n_members);
+    if (prow < 1) return cudaErrorInvalidValue;
+    dim3 g((nx_max + 127) / 128, (ny_max + 8 * prow - 1) / (8 * prow), n_members);
     const dim3 b4(32, 8);
     if (state < 2)
-      k_project4<0><<<g, b4, 0, s>>>(d_members, state, slot);
+      k_project4<0><<<g, b4, 0, s>>>(d_members, state, slot, prow);
     else if (state == 2)
-      k_project4<1><<<g, b4, 0, s>>>(d_members, state, slot);
+      k_project4<1><<<g, b4, 0, s>>>(d_members, state, slot, prow);
     else
-      k_project4<2><<<g, b4, 0, s>>>(d_members, state, slot);
+      k_project4<2><<<g, b4, 0, s>>>(d_members, state, slot, prow);
     return cudaGetLastError();
   }
   const dim3 b(64, 4);

@@ -76,6 +76,66 @@ def test_paper_forcing_trajectories(P, orc, prec, tol, storage):
             assert err < tol, (prec, storage, steps, i, err)
 
 
+def _proj_spec():
+    # kind-2 members on the four-cell projection with heights that leave
+    # ragged last blocks for most rows-per-thread settings (40, 72, 100, 6),
+    # a width (132) with a 4-cell second column, and a Kolmogorov and an
+    # unforced member beside them
+    return [(128, 40, 0.56, 2, FT0, 0, 1e-3), (256, 72, 0.52, 2, FT0, 0, 0.0),
+            (32, 32, 0.55, 1, 2e-4, 2, 1e-3), (48, 40, 0.52, 0, 0.0, 0, 0.0),
+            (132, 100, 0.53, 2, FT0, 0, 0.0), (4, 6, 0.6, 2, FT0, 0, 1e-3)]
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("proj_rows", [1, 3, 5, 13])
+def test_projection_rows_per_thread(P, orc, storage, proj_rows):
+    """The FP32 four-cell projection with 1, 3, 5 and 13 rows per thread
+    (blocks of 8, 24, 40 and 104 rows, software-pipelined over the rows)
+    against the FP64 oracle at the FP32 bar over single launches and graph
+    replays in both AA phases; the result does not depend on the setting
+    beyond the summation order of the mode sums."""
+    spec = _proj_spec()
+    lat = P.Lattice(_members(P, spec), precision=32, storage=storage, graph_steps=6)
+    lat.set_launch(8, 1, 0, proj_rows)
+    assert lat.tuning()["projection_rows"] == proj_rows
+    assert lat.tuning()["kernels_per_step"] == 2
+    init = []
+    for i, (nx, ny, *_r) in enumerate(spec):
+        fields = _fields(nx, ny, 10 * i + 7)
+        lat.init_fields(i, *fields)
+        init.append(orc.init(*fields))
+    done = 0
+    for steps in (1, 8, 31):
+        lat.step(steps - done)
+        done = steps
+        for i, (nx, ny, tau, k, F0, kf, a) in enumerate(spec):
+            ref = orc.run(init[i], steps, tau, _force(orc, k, F0, kf, a))
+            err = rel_err(lat.get_populations_host(i), ref)
+            assert err < FP32_TOL, (storage, proj_rows, steps, i, err)
+            assert lat.member_status(i) == 0
+
+
+def test_set_launch_rejections(P, orc):
+    """lbm_set_launch refuses invalid shapes and keeps the previous
+    configuration; proj_rows 0 keeps the projection setting."""
+    spec = [(64, 48, 0.56, 2, FT0, 0, 1e-3)]
+    lat = P.Lattice(_members(P, spec), precision=32)
+    lat.set_launch(4, 2, 0, 6)
+    for args in ((8, 3, 0, 0), (9, 1, 0, 0), (0, 1, 0, 0), (8, 2, -1, 0), (8, 1, 0, -1),
+                 (8, 1, 0, 65)):
+        with pytest.raises(RuntimeError):
+            lat.set_launch(*args)
+    t = lat.tuning()
+    assert (t["warps_per_cta"], t["rows_per_warp"], t["projection_rows"]) == (4, 2, 6)
+    lat.set_launch(8, 1)
+    assert lat.tuning()["projection_rows"] == 6
+    fields = _fields(64, 48, 3)
+    lat.init_fields(0, *fields)
+    lat.step(3)
+    ref = orc.run(orc.init(*fields), 3, 0.56, _force(orc, 2, FT0, 0, 1e-3))
+    assert rel_err(lat.get_populations_host(0), ref) < FP32_TOL
+
+
 def test_paper_forcing_changes_the_flow(P, orc):
     """The damping is not a no-op: removing it changes the state by far
     more than the parity bar."""
