@@ -383,6 +383,65 @@ def paper_forcing_leg(P, stream, dev, peak):
             "kernels_per_step": tune["kernels_per_step"]}
 
 
+# The forced tau-sweep of the paper's Sec. 5 under its own forcing (eqs.
+# 14-16) at amplitudes for which every tau of the sweep reaches a
+# statistically stationary low-Mach state on 256^2 (the printed
+# F^T_0 = 8e-4, F^R_0 = 1e-5 diverge within about 250 steps under the reading
+# of the forcing used here).
+TREND_TAUS = (0.6, 0.54, 0.53, 0.52, 0.515)
+TREND_FT0, TREND_FR0 = 2e-5, 1e-2
+TREND_LS = (2, 3, 4, 8, 16, 32, 64, 128, 181, 256)
+
+
+def forced_tau_trend(P, members=4, n=256, spin=8000, every=400, events=25, stream=None,
+                     dev=None):
+    """Balancing-error statistics of the forced sweep: for each tau, `members`
+    members of n^2 from random-phase starts (u_rms 0.01, seeds 6000 + m), `spin`
+    steps to the stationary state, then `events` balance events `every` steps
+    apart (the paper samples 25 configurations in time) over all periodic
+    origins at the sizes TREND_LS (L = 3 is l ~ 0.01 and L = 181 l ~ 0.707 on
+    256^2).  Returns {tau: {"urms", "finite", "dE"/"dZ": [nL][mean, std]}},
+    the statistics averaged over members and events."""
+    out = {}
+    for tau in TREND_TAUS:
+        kw = {} if stream is None else {"stream": stream, "device": dev}
+        lat = P.Lattice([P.Member(n, n, tau, 1.0, 2, 0, TREND_FT0, 0.0, 0.0, TREND_FR0)] * members,
+                        precision=32, graph_steps=100, diag_every=every, **kw)
+        for m in range(members):
+            lat.init_fields(m, *li.random_phase(n, seed=6000 + m, u_rms=0.01))
+        lat.step(spin)
+        acc, urms = [], []
+        for _ in range(events):
+            lat.step(every)
+            acc.append(np.asarray(lat.subvolume_balance_batch(range(members), list(TREND_LS)))[:, :, :2, :])
+            urms.append(float(np.sqrt(2 * lat.global_balance(0)[3])))
+        a = np.mean(np.stack(acc), axis=(0, 1))  # [nL, quantity, (mean, std)]
+        out[tau] = {"urms": float(np.mean(urms)),
+                    "finite": all(lat.member_status(m) == 0 for m in range(members)),
+                    "dE": a[:, 0, :].tolist(), "dZ": a[:, 1, :].tolist()}
+        del lat
+    return out
+
+
+def forced_tau_trend_leg(P, stream, dev):
+    """The forced tau-sweep trend (Sec. 5): per tau the mean and std of the
+    energy and enstrophy balancing errors at l ~ 0.01 (L = 3) and l ~ 0.707
+    (L = 181) of 256^2, and the wall time of the whole sweep."""
+    t0 = time.perf_counter()
+    res = forced_tau_trend(P, stream=stream, dev=dev)
+    i_s, i_l = TREND_LS.index(3), TREND_LS.index(181)
+    rows = {}
+    for tau, r in res.items():
+        rows[str(tau)] = {"urms": round(r["urms"], 4), "finite": r["finite"],
+                          "dE_small": r["dE"][i_s], "dE_large": r["dE"][i_l],
+                          "dZ_small": r["dZ"][i_s], "dZ_large": r["dZ"][i_l]}
+    return {"grid": [256, 256], "members": 4, "FT0": TREND_FT0, "FR0": TREND_FR0,
+            "taus": list(TREND_TAUS), "events": 25, "event_every": 400, "spin_up": 8000,
+            "stats": "[mean, std] of delta over all periodic origins, averaged over members "
+                     "and events", "per_tau": rows,
+            "wall_s": time.perf_counter() - t0}
+
+
 def collision_models_leg(P, stream, dev, peak):
     """The variable-viscosity collisions (Sec. 1) on 16 FP32 members of
     512^2 (tau0 = 0.51): Smagorinsky (Cs = 0.1) and eq. (7) on the extended
@@ -483,9 +542,12 @@ def three_d_leg(P, stream, dev, peak):
     uz = 0.005 * np.sin(X - Y)
     rho = np.ones((n, n, n))
 
+    cpl = {}
+
     def timed(q):
         lat = P.Lattice3D([P.Member3(n, n, n, 0.52)] * M, precision=32, stream=stream, device=dev,
                           lattice=q)
+        cpl[q] = lat.tuning()["cells_per_lane"]
         for m in range(M):
             lat.init_fields(m, rho, ux, uy, uz)
         lat.step(10)
@@ -523,8 +585,9 @@ def three_d_leg(P, stream, dev, peak):
     diag32_s = diag_event(32, 32)
     return {"members": M, "grid": [n, n, n], "precision": "fp32", "glups": glups,
             "bytes_per_lu": 152, "achieved_gbs": gbs, "frac": gbs / peak,
+            "cells_per_lane": cpl[19],
             "d3q27": {"glups": glups27, "bytes_per_lu": 216, "achieved_gbs": gbs27,
-                      "frac": gbs27 / peak},
+                      "frac": gbs27 / peak, "cells_per_lane": cpl[27]},
             "diagnostic_event_ms_fp64_64cubed_all_origins": 1e3 * diag_s,
             "diagnostic_event_ms_fp32_64cubed_all_origins": 1e3 * diag32_s}
 
@@ -1089,6 +1152,7 @@ def run_ours(args):
     large_grid = large_grid_leg(P, stream, dev, peak)
     adjoint = adjoint_leg(P, stream, dev, peaks_alu)
     paper_forcing = paper_forcing_leg(P, stream, dev, measured_peaks()[0])
+    tau_trend = forced_tau_trend_leg(P, stream, dev)
     collisions = collision_models_leg(P, stream, dev, measured_peaks()[0])
     three_d = three_d_leg(P, stream, dev, measured_peaks()[0])
     taylor_green = taylor_green_leg(P, stream, dev)
@@ -1176,6 +1240,7 @@ def run_ours(args):
             "large_forced_8192sq": large_grid,
             "adjoint_256sq": adjoint,
             "paper_forcing_ensemble": paper_forcing,
+            "forced_tau_sweep_trend": tau_trend,
             "collision_models": collisions,
             "three_d": three_d,
             "fp64_taylor_green_64": taylor_green,

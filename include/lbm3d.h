@@ -72,9 +72,18 @@ int lbm3d_destroy(lbm3d_handle *h);
 int lbm3d_init_fields(lbm3d_handle *h, int member, const double *rho, const double *ux,
                       const double *uy, const double *uz, int on_device);
 
-/* nsteps steps of eq. (1) for every member (one launch per member and step). */
+/* nsteps steps of eq. (1) for every member: one launch per step for the FP32
+ * members with nx % 4 == 0, one per member and step for the others. */
 int lbm3d_step(lbm3d_handle *h, int nsteps);
 long long lbm3d_time(const lbm3d_handle *h);
+/* Cells per lane of the vectorised FP32 kernel that every FP32 member with
+ * nx % 4 == 0 takes: 4 or 2, the faster on this device, timed at create time
+ * for ensembles above 1 M cells (4 otherwise); 0 when no member takes it; -1
+ * for a NULL handle.  Host-only.  Results do not depend on it. */
+int lbm3d_cells_per_lane(const lbm3d_handle *h);
+/* Sets the cells per lane of that kernel (4 or 2; LBM_ERR_ARG otherwise, the
+ * setting kept).  Host-side: the populations are kept. */
+int lbm3d_set_cells_per_lane(lbm3d_handle *h, int cpl);
 
 /* Public populations double[q][nz][ny][nx] of one member, host or device
  * (index for index the oracle's f(., n)); set accepts the same layout. */

@@ -117,6 +117,8 @@ def load_library(path: str = LIB_PATH):
         "lbm3d_init_fields": ([P, I, P, P, P, P, I], I),
         "lbm3d_step": ([P, I], I),
         "lbm3d_time": ([P], ctypes.c_longlong),
+        "lbm3d_cells_per_lane": ([P], I),
+        "lbm3d_set_cells_per_lane": ([P, I], I),
         "lbm3d_get_populations": ([P, I, P, I], I),
         "lbm3d_set_populations": ([P, I, P, I], I),
         "lbm3d_record_snapshot": ([P], I),
@@ -594,10 +596,14 @@ class Lattice3D:
     def time(self) -> int:
         return int(self.lib.lbm3d_time(self.h))
 
-    def set_launch(self, warps: int, rows: int, grid: int = 0, proj_rows: int = 0):
-        """Replace the autotuned launch configuration (see lbm_set_launch);
-        proj_rows 0 keeps the projection's rows per thread."""
-        self._check(self.lib.lbm_set_launch(self.h, warps, rows, grid, proj_rows))
+    def tuning(self) -> dict:
+        """Cells per lane of the vectorised FP32 kernel (4 or 2, timed at
+        create; 0 when no member takes it)."""
+        return {"cells_per_lane": int(self.lib.lbm3d_cells_per_lane(self.h))}
+
+    def set_cells_per_lane(self, cpl: int):
+        """4 or 2 cells per lane in the vectorised FP32 kernel."""
+        self._check(self.lib.lbm3d_set_cells_per_lane(self.h, int(cpl)))
 
     def record_snapshot(self):
         self._check(self.lib.lbm3d_record_snapshot(self.h))

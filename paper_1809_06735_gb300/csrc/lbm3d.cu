@@ -138,16 +138,44 @@ __global__ void __launch_bounds__(256) k3_step(const M3 *__restrict__ ms, int me
   for (int l = 0; l < Q; ++l) dst[(size_t)l * N + c] = v[l];
 }
 
-// FP32 stream-collide with 4 consecutive cells per lane (nx % 4 == 0), all
-// such members in one persistent launch: a work item is 4 rows (y0 .. y0+3)
-// of a 128-cell x segment of one z plane of one member, a warp per row; the
-// items of every member are numbered consecutively (M3::item0, M3::items).
-// Each population is one aligned 16-byte load per lane from its source row
-// (y - c_y, z - c_z); the -+1 x-shift is a warp shuffle with one scalar
-// load at the segment's edges (the periodic wrap included), as in 2D.
-template <int Q>
-__global__ void __launch_bounds__(128, Q == 19 ? 4 : 3) k3_step_vec(const M3 *__restrict__ ms, int n_members,
-                                                   long long n_items, int cur, int flip) {
+// FP32 stream-collide with CPL = 4 or 2 consecutive cells per lane
+// (nx % 4 == 0), all such members in one persistent launch: a work item is 4
+// rows (y0 .. y0+3) of a 32 CPL-cell x segment of one z plane of one member,
+// a warp per row; the items of every member are numbered consecutively
+// (M3::item0, M3::items).  Each population is one aligned 16- or 8-byte load
+// per lane from its source row (y - c_y, z - c_z); the -+1 x-shift is a
+// warp shuffle with one scalar load at the segment's edges (the periodic
+// wrap included), as in 2D.  Two cells per lane halve the registers that
+// hold the pulled populations (2 Q instead of 4 Q), for more resident warps.
+template <int CPL>
+struct Vec3;
+template <>
+struct Vec3<4> {
+  using V = float4;
+  static __device__ __forceinline__ float first(const V &o) { return o.x; }
+  static __device__ __forceinline__ float lastv(const V &o) { return o.w; }
+  static __device__ __forceinline__ void get(const V &o, float *v) {
+    v[0] = o.x; v[1] = o.y; v[2] = o.z; v[3] = o.w;
+  }
+  static __device__ __forceinline__ V make(const float *v) { return make_float4(v[0], v[1], v[2], v[3]); }
+  static __device__ __forceinline__ V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct Vec3<2> {
+  using V = float2;
+  static __device__ __forceinline__ float first(const V &o) { return o.x; }
+  static __device__ __forceinline__ float lastv(const V &o) { return o.y; }
+  static __device__ __forceinline__ void get(const V &o, float *v) { v[0] = o.x; v[1] = o.y; }
+  static __device__ __forceinline__ V make(const float *v) { return make_float2(v[0], v[1]); }
+  static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
+};
+
+template <int Q, int CPL>
+__global__ void __launch_bounds__(128, CPL == 2 ? (Q == 19 ? 5 : 4) : (Q == 19 ? 4 : 3))
+    k3_step_vec(const M3 *__restrict__ ms, int n_members, long long n_items, int cur, int flip) {
+  using VT = Vec3<CPL>;
+  using V = typename VT::V;
+  constexpr int SEG = 32 * CPL;
   const int lane = threadIdx.x;
   // the current member's parameters, reloaded only when the items move on
   // to another member; flip walks the items in reverse order, so that a step
@@ -178,42 +206,49 @@ __global__ void __launch_bounds__(128, Q == 19 ? 4 : 3) k3_step_vec(const M3 *__
       alpha = M.alpha_f;
     }
     const unsigned li = (unsigned)(it - item0);  // < 2^28 items per member
-    const unsigned gx = (unsigned)(nx + 127) / 128u, gy = (unsigned)(ny + 3) / 4u;
+    const unsigned gx = (unsigned)(nx + SEG - 1) / (unsigned)SEG, gy = (unsigned)(ny + 3) / 4u;
     const unsigned lx = li / gx;
     const int xs = (int)(li - lx * gx), yg = (int)(lx % gy), z = (int)(lx / gy);
-    const int x = xs * 128 + 4 * lane, y = yg * 4 + threadIdx.y;
+    const int x = xs * SEG + CPL * lane, y = yg * 4 + threadIdx.y;
     if (y >= ny) continue;  // whole warps
     const bool active = x < nx;
-    const bool last = active && (lane == 31 || x + 4 >= nx);
-    const int xprev = x == 0 ? nx - 1 : x - 1, xnext = x + 4 >= nx ? 0 : x + 4;
+    const bool last = active && (lane == 31 || x + CPL >= nx);
+    const int xprev = x == 0 ? nx - 1 : x - 1, xnext = x + CPL >= nx ? 0 : x + CPL;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
     const int zm = z == 0 ? nz - 1 : z - 1, zp = z + 1 == nz ? 0 : z + 1;
     const size_t rowy[3] = {(size_t)yp * nx, (size_t)y * nx, (size_t)ym * nx};
     const size_t slab[3] = {(size_t)zp * ny * nx, (size_t)z * ny * nx, (size_t)zm * ny * nx};
-    float v[Q][4];
+    float v[Q][CPL];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       // pull from (y - c_y, z - c_z): entry 1 + c of the (+1, 0, -1) neighbours
       const float *row = src + (size_t)l * N + slab[1 + c3z(l)] + rowy[1 + c3y(l)];
-      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (active) o = __ldg(reinterpret_cast<const float4 *>(row + x));
+      V o = VT::zero();
+      if (active) o = __ldg(reinterpret_cast<const V *>(row + x));
+      float a[CPL];
+      VT::get(o, a);
       if (c3x(l) == 0) {
-        v[l][0] = o.x; v[l][1] = o.y; v[l][2] = o.z; v[l][3] = o.w;
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) v[l][i] = a[i];
       } else if (c3x(l) > 0) {  // from x - 1
-        float prev = __shfl_up_sync(0xffffffffu, o.w, 1);
+        float prev = __shfl_up_sync(0xffffffffu, VT::lastv(o), 1);
         if (active && (lane == 0 || x == 0)) prev = __ldg(row + xprev);
-        v[l][0] = prev; v[l][1] = o.x; v[l][2] = o.y; v[l][3] = o.z;
+        v[l][0] = prev;
+#pragma unroll
+        for (int i = 1; i < CPL; ++i) v[l][i] = a[i - 1];
       } else {  // from x + 1
-        float next = __shfl_down_sync(0xffffffffu, o.x, 1);
+        float next = __shfl_down_sync(0xffffffffu, VT::first(o), 1);
         if (last) next = __ldg(row + xnext);
-        v[l][0] = o.y; v[l][1] = o.z; v[l][2] = o.w; v[l][3] = next;
+#pragma unroll
+        for (int i = 0; i + 1 < CPL; ++i) v[l][i] = a[i + 1];
+        v[l][CPL - 1] = next;
       }
     }
     if (!active) continue;
     const float fx = tab[y], fy = tab[ny + z];
     const size_t c = slab[1] + rowy[1] + x;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < CPL; ++i) {
       float g[Q];
 #pragma unroll
       for (int l = 0; l < Q; ++l) g[l] = v[l][i];
@@ -223,8 +258,7 @@ __global__ void __launch_bounds__(128, Q == 19 ? 4 : 3) k3_step_vec(const M3 *__
     }
 #pragma unroll
     for (int l = 0; l < Q; ++l)
-      __stcs(reinterpret_cast<float4 *>(dst + (size_t)l * N + c),
-             make_float4(v[l][0], v[l][1], v[l][2], v[l][3]));
+      __stcs(reinterpret_cast<V *>(dst + (size_t)l * N + c), VT::make(v[l]));
   }
 }
 
@@ -835,8 +869,9 @@ struct lbm3d_handle {
   int precision = 32;
   int q = 19;  // lattice velocities
   int diag_prec = 64;  // arithmetic of the balance terms
-  long long vec_items = 0;  // work items of the four-cell FP32 kernel
+  long long vec_items = 0;  // work items of the vectorised FP32 kernel
   int vec_grid = 0;         // its persistent grid
+  int cpl = 4;              // its cells per lane (4 or 2, timed at create)
   cudaStream_t stream = nullptr;
   int cur = 0;
   long long t = 0;
@@ -856,6 +891,99 @@ int fail3(lbm3d_handle *h, int code, const std::string &msg) {
   if (h) h->err = msg;
   g_err3 = msg;
   return code;
+}
+
+// Work items of the vectorised kernel at `cpl` cells per lane (M3::item0,
+// M3::items of every FP32 member with nx % 4 == 0), its persistent grid
+// (resident CTAs per SM x SMs), and the member table on the device.
+cudaError_t vec_layout(lbm3d_handle *h, int cpl) {
+  const int seg = 32 * cpl;
+  h->vec_items = 0;
+  for (size_t m = 0; m < h->hm.size(); ++m) {
+    M3 &M = h->hm[m];
+    const lbm3d_member_cfg &c = h->mcfg[m];
+    M.item0 = h->vec_items;
+    M.items = h->precision == 32 && c.nx % 4 == 0
+                  ? (long long)((c.nx + seg - 1) / seg) * ((c.ny + 3) / 4) * c.nz : 0;
+    h->vec_items += M.items;
+  }
+  h->cpl = cpl;
+  h->vec_grid = 0;
+  if (h->vec_items > 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+      const void *k = h->q == 27 ? (cpl == 2 ? (const void *)k3_step_vec<27, 2> : (const void *)k3_step_vec<27, 4>)
+                                 : (cpl == 2 ? (const void *)k3_step_vec<19, 2> : (const void *)k3_step_vec<19, 4>);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0);
+    }
+    if (e != cudaSuccess) return e;
+    const long long g = (long long)std::max(1, sms) * std::max(1, per_sm);
+    h->vec_grid = (int)std::min<long long>(g, h->vec_items);
+  }
+  return cudaMemcpyAsync(h->d_m, h->hm.data(), sizeof(M3) * h->hm.size(), cudaMemcpyHostToDevice,
+                         h->stream);
+}
+
+// One step of the vectorised kernel's members.
+void launch_vec3(lbm3d_handle *h, cudaStream_t s) {
+  const int n = (int)h->mcfg.size();
+  const dim3 b(32, 4);
+  const int flip = h->cur & 1;
+  if (h->q == 27) {
+    if (h->cpl == 2)
+      k3_step_vec<27, 2><<<h->vec_grid, b, 0, s>>>(h->d_m, n, h->vec_items, h->cur, flip);
+    else
+      k3_step_vec<27, 4><<<h->vec_grid, b, 0, s>>>(h->d_m, n, h->vec_items, h->cur, flip);
+  } else {
+    if (h->cpl == 2)
+      k3_step_vec<19, 2><<<h->vec_grid, b, 0, s>>>(h->d_m, n, h->vec_items, h->cur, flip);
+    else
+      k3_step_vec<19, 4><<<h->vec_grid, b, 0, s>>>(h->d_m, n, h->vec_items, h->cur, flip);
+  }
+}
+
+// The faster of four and two cells per lane on this handle's members: each
+// timed over 2 + 4 steps on the live (zeroed) buffers, which are zeroed
+// again afterwards (FP32 ensembles above 1 M cells; smaller ones keep 4).
+cudaError_t tune_vec3(lbm3d_handle *h) {
+  long long cells = 0;
+  for (auto &c : h->mcfg) cells += (long long)c.nx * c.ny * c.nz;
+  if (h->vec_items == 0 || cells < (1LL << 20)) return cudaSuccess;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_cpl = 4;
+  for (int cpl : {4, 2}) {
+    if (e == cudaSuccess) e = vec_layout(h, cpl);
+    for (int r = 0; r < 6 && e == cudaSuccess; ++r) {
+      if (r == 2) e = cudaEventRecord(e0, h->stream);
+      launch_vec3(h, h->stream);
+      h->cur ^= 1;
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && ms < best) {
+      best = ms;
+      best_cpl = cpl;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = vec_layout(h, best_cpl);
+  h->cur = 0;
+  const size_t es = h->precision == 32 ? 4 : 8;
+  for (size_t m = 0; m < h->hm.size() && e == cudaSuccess; ++m) {
+    e = cudaMemsetAsync(h->hm[m].pop[0], 0, es * h->q * h->hm[m].N, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->hm[m].pop[1], 0, es * h->q * h->hm[m].N, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e;
 }
 
 #define CK3(call)                                                                        \
@@ -1014,10 +1142,6 @@ int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_h
     M.alpha_f = (float)c.alpha;
     M.F0_f = (float)c.F0;
     M.N = (size_t)c.nx * c.ny * c.nz;
-    M.item0 = h->vec_items;
-    M.items = cfg->precision == 32 && c.nx % 4 == 0
-                  ? (long long)((c.nx + 127) / 128) * ((c.ny + 3) / 4) * c.nz : 0;
-    h->vec_items += M.items;
     M.pop[0] = h->ws + L.pop0[m];
     M.pop[1] = h->ws + L.pop1[m];
     M.snap = reinterpret_cast<double *>(h->ws + L.snap[m]);
@@ -1047,23 +1171,9 @@ int lbm3d_create(const lbm3d_config *cfg, void *workspace, size_t bytes, lbm3d_h
       return fail3(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
     }
   }
-  if (h->vec_items > 0) {  // persistent grid: resident CTAs per SM x SMs
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = h->q == 27 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_step_vec<27>, 128, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_step_vec<19>, 128, 0);
-    if (e != cudaSuccess) {
-      delete h;
-      return fail3(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
-    }
-    const long long g = (long long)std::max(1, sms) * std::max(1, per_sm);
-    h->vec_grid = (int)std::min<long long>(g, h->vec_items);
-  }
-  cudaError_t e = cudaMemcpyAsync(h->d_m, h->hm.data(), sizeof(M3) * h->hm.size(),
-                                  cudaMemcpyHostToDevice, h->stream);
+  cudaError_t e = vec_layout(h, 4);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = tune_vec3(h);
   if (e != cudaSuccess) {
     delete h;
     return fail3(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
@@ -1108,15 +1218,7 @@ int lbm3d_step(lbm3d_handle *h, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
     if (snap_time3(h, h->t) && h->ring_time[h->t % 3] != h->t)
       if (int rc = record3(h)) return rc;
-    if (h->vec_items > 0) {  // every FP32 member with nx % 4 == 0, one launch
-      const int n = (int)h->mcfg.size();
-      if (h->q == 27)
-        k3_step_vec<27><<<h->vec_grid, dim3(32, 4), 0, h->stream>>>(h->d_m, n, h->vec_items, h->cur,
-                                                                    h->cur & 1);
-      else
-        k3_step_vec<19><<<h->vec_grid, dim3(32, 4), 0, h->stream>>>(h->d_m, n, h->vec_items, h->cur,
-                                                                    h->cur & 1);
-    }
+    if (h->vec_items > 0) launch_vec3(h, h->stream);  // every FP32 member with nx % 4 == 0
     for (int m = 0; m < (int)h->mcfg.size(); ++m)
       if (h->hm[m].items == 0)
         DISPATCH3(h, k3_step, cells3(h->mcfg[m]), dim3(64, 4), h->d_m, m, h->cur);
@@ -1129,6 +1231,18 @@ int lbm3d_step(lbm3d_handle *h, int nsteps) {
 }
 
 long long lbm3d_time(const lbm3d_handle *h) { return h ? h->t : -1; }
+
+int lbm3d_cells_per_lane(const lbm3d_handle *h) {
+  return h ? (h->vec_items > 0 ? h->cpl : 0) : -1;
+}
+
+int lbm3d_set_cells_per_lane(lbm3d_handle *h, int cpl) {
+  if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+  if (cpl != 4 && cpl != 2) return fail3(h, LBM_ERR_ARG, "cells per lane must be 4 or 2");
+  CK3(vec_layout(h, cpl));
+  CK3(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
 
 int lbm3d_get_populations(lbm3d_handle *h, int member, double *f, int on_device) {
   if (int rc = check_member3(h, member)) return rc;

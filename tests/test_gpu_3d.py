@@ -66,6 +66,38 @@ def test_3d_trajectories(P, orc, prec, tol, q):
         done = steps
 
 
+SPEC_VEC = [(12, 10, 8, 0.57, 1, 1, 3e-4, 2e-3), (132, 6, 4, 0.53, 1, 2, 2e-4, 0.0),
+            (64, 5, 3, 0.6, 0, 0, 0.0, 0.0)]
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("cpl", [4, 2])
+def test_3d_cells_per_lane(P, orc, q, cpl):
+    """The vectorised FP32 kernel with 4 and with 2 cells per lane (128- and
+    64-cell row segments: widths 12, 64 and 132 leave partial segments and a
+    4-cell remainder) against the oracle at the FP32 bar over 100 steps."""
+    lat = P.Lattice3D([P.Member3(nx, ny, nz, tau, 1.0, k, kf, F0, a)
+                       for (nx, ny, nz, tau, k, kf, F0, a) in SPEC_VEC], precision=32, lattice=q)
+    lat.set_cells_per_lane(cpl)
+    assert lat.tuning()["cells_per_lane"] == cpl
+    with pytest.raises(RuntimeError):
+        lat.set_cells_per_lane(3)
+    assert lat.tuning()["cells_per_lane"] == cpl
+    ref = []
+    for i, (nx, ny, nz, *_r) in enumerate(SPEC_VEC):
+        fl = _fields((nz, ny, nx), 40 + 10 * i)
+        lat.init_fields(i, *fl)
+        ref.append(orc.init3(*fl, q=q))
+    done = 0
+    for steps in (1, 5, 100):
+        lat.step(steps - done)
+        for i, (nx, ny, nz, tau, k, kf, F0, a) in enumerate(SPEC_VEC):
+            ref[i] = orc.run3(ref[i], steps - done, tau, k, F0, kf, a)
+            err = rel_err(lat.get_populations_host(i), ref[i])
+            assert err < 2e-6, (q, cpl, steps, i, err)
+        done = steps
+
+
 @pytest.mark.parametrize("q", [19, 27])
 def test_3d_state_roundtrip(P, orc, q):
     shape = (6, 5, 7)
