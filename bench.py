@@ -805,6 +805,13 @@ def adjoint_leg(P, stream, dev, peaks):
     out = {"grid": [n, n], "window": [wl["n0"], wl["n1"]], "L": wl["L"],
            "checkpoint_every": wl["checkpoint_every"]}
     for prec in (64, 32):
+        # untimed warm-up on a short window: the first forward of a process
+        # pays one-off set-up (about 0.25 s on the first FP64 one)
+        short = ObjectiveSpec(nx=n, ny=n, kf=wl["kf"], alpha=wl["alpha"], n0=10, n1=20,
+                              box=wl["box"], L=wl["L"], precision=prec, checkpoint_every=10)
+        _, warm_ckpts, warm = forward_objective(short, tau, F0, f0, keep_checkpoints=True)
+        adjoint_objective(short, tau, F0, warm, warm_ckpts)
+        warm.close()
         spec = ObjectiveSpec(nx=n, ny=n, kf=wl["kf"], alpha=wl["alpha"], n0=wl["n0"],
                              n1=wl["n1"], box=wl["box"], L=wl["L"], precision=prec,
                              checkpoint_every=wl["checkpoint_every"])

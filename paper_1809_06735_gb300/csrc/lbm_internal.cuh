@@ -198,8 +198,6 @@ cudaError_t launch_set_populations(int precision, const Member *d_members, int m
 cudaError_t launch_projection(int precision, const Member *d_members, int n_members,
                               int nx_max, int ny_max, int state, int slot, bool quad, int prow,
                               cudaStream_t s);
-// Resident CTAs per SM of the four-cell projection (0 if unknown).
-int project4_ctas_per_sm();
 // The ring snapshot of every member in one launch (layout at Member::snap).
 cudaError_t launch_snapshot_ring(int precision, const Member *d_members, int n_members,
                                  int nx_max, int ny_max, int state, int slot, bool quad,

@@ -1507,16 +1507,6 @@ __global__ void __launch_bounds__(256) k_project4(const Member *__restrict__ mem
   proj4_block<MODE>(M, blockIdx.x, blockIdx.y, state, slot, prow);
 }
 
-int project4_ctas_per_sm() {
-  static int n = -1;
-  if (n < 0 &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project4<2>, 256, 0) != cudaSuccess) {
-    cudaGetLastError();
-    n = -1;
-    return 0;
-  }
-  return n;
-}
 
 // The snapshot-ring entry of FP32 members with nx % 4 == 0 and a constant
 // viscosity, four cells per lane: CTA (32, 8), a warp per 128-cell row

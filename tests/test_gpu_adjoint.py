@@ -194,7 +194,7 @@ def _c3_gradients(P, precision):
     F0 = torch.tensor(_c3_F0(), dtype=torch.float64, requires_grad=True)
     J = box_dissipation(tau, F0, f0, spec)
     J.backward()
-    return float(J), float(tau.grad), float(F0.grad)
+    return float(J.detach()), float(tau.grad), float(F0.grad)
 
 
 @pytest.mark.slow
