@@ -852,7 +852,8 @@ def adjoint_leg(P, stream, dev, peaks):
     glups = n * n / step_s / 1e9
     k = {"us_per_step": 1e6 * step_s, "glups": glups, "bytes_per_lu": 216,
          "achieved_gbs": 216 * glups,
-         "note": "256^2 FP64: 14 MB per step, L2-resident; launch pair k_adjoint + k_adjoint_final"}
+         "note": "256^2 FP64: 14 MB per step, L2-resident; one k_adjoint launch per step, "
+                 "the gradient reduction (k_adjoint_final) once per 100-step sweep"}
     counts = fp64_instruction_counts().get("k_adjoint")
     if counts is not None:
         k["fp64_roofline"] = fp64_roofline(counts, glups, peaks)

@@ -391,7 +391,12 @@ int lbm_record_trajectory(lbm_handle *h, int member, int nstates,
  * result lambda(n) is written to lambda_out; lambda_tmp (device, same size)
  * is the other half of the ping-pong; lambda_in, lambda_out and lambda_tmp
  * must be three distinct buffers.  dJ/dtau and dJ/dF0 contributions are
- * added to the device accumulators as in lbm_adjoint_step. */
+ * added to the device accumulators as in lbm_adjoint_step, summed over the
+ * whole call before they are added (one reduction per call: the adjoint
+ * fields equal those of nstates lbm_adjoint_step calls bit for bit, the two
+ * gradients up to the order of their FP64 sums).  Non-finite weights, or a
+ * box outside the grid when some weight is non-zero, return LBM_ERR_ARG
+ * before any work. */
 int lbm_adjoint_sweep(lbm_handle *h, int member, const double *states,
                       int nstates, const double *lambda_in, double *lambda_out,
                       double *lambda_tmp, const double *weights, int bx, int by,

@@ -86,7 +86,7 @@ __global__ void k_sine_tables(AGrid g, double *tab) {
 }
 
 template <int NQ>
-__device__ void block_sums(double (&v)[NQ], double *out) {
+__device__ void block_sums(double (&v)[NQ], double *out, int add = 0) {
   __shared__ double sh[NQ][32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -100,7 +100,7 @@ __device__ void block_sums(double (&v)[NQ], double *out) {
   if (tid < NQ) {
     double a = 0.0;
     for (int k = 0; k < nw; ++k) a += sh[tid][k];
-    out[tid] = a;
+    out[tid] = add ? out[tid] + a : a;
   }
 }
 
@@ -167,7 +167,7 @@ __global__ void k_velocity(AGrid g, double *F) {
 // Objective pass 1, over V0: Gamma_ij = dJ/dG_ij = -2 c nu rho S_ij
 // (c = weight / L^2); explicit dJ/dtau part -c rho Q / 3 (d nu / d tau = 1/3).
 __global__ void k_obj_gamma(AGrid g, double *F, double cw, int bx, int by, int L,
-                            double *partials) {
+                            double *partials, int add) {
   double acc[1] = {0.0};
   const size_t N = (size_t)g.nx * g.ny;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
@@ -185,7 +185,7 @@ __global__ void k_obj_gamma(AGrid g, double *F, double cw, int bx, int by, int L
     F[D_RHO * N + c] = -cw * g.nu * Q;
     acc[0] += -cw * r * Q / 3.0;
   }
-  block_sums<1>(acc, partials + blockIdx.x);
+  block_sums<1>(acc, partials + blockIdx.x, add);
 }
 
 // Gamma_ij at (x, y), zero outside V0.
@@ -198,7 +198,7 @@ __device__ __forceinline__ double gam(const double *G, const AGrid &g, int x, in
 // dJ/drho (with the direct part of V0), dJ/dj and the explicit dJ/dF0 part
 // through u = ((1 - alpha/2) j + F_ext/2)/rho.
 __global__ void k_obj_velocity_adjoint(AGrid g, Region R, double *F, int bx, int by, int L,
-                                       double *partials) {
+                                       double *partials, int add) {
   double acc[1] = {0.0};
   FOR_REGION(R) {
     const int x = wrapi(R.x0 + i % R.w, g.nx), y = wrapi(R.y0 + i / R.w, g.ny);
@@ -227,7 +227,7 @@ __global__ void k_obj_velocity_adjoint(AGrid g, Region R, double *F, int bx, int
     force_dir(g, x, y, sx, sy);
     acc[0] += (Ux * sx + Uy * sy) / (2.0 * r);
   }
-  block_sums<1>(acc, partials + blockIdx.x);
+  block_sums<1>(acc, partials + blockIdx.x, add);
 }
 
 // t_l-weighted sums over the populations of the pulled adjoint mu_l and
@@ -255,9 +255,12 @@ __device__ __forceinline__ MuMoments mu_moments(const double (&mu)[kQ]) {
 }
 
 // Adjoint of one step (see the header comment).  with_obj adds dJ_n/df on
-// the objective region R.
+// the objective region R.  Each CTA's (dJ/dtau, dJ/dF0) sums go to its slot
+// of `partials`, added to what is there when `add` (a sweep's running sums;
+// steps are stream-ordered, so a slot has one writer at a time).
 __global__ void k_adjoint(AGrid g, Region R, const double *f, const double *lam_in,
-                          double *lam_out, const double *F, int with_obj, double *partials) {
+                          double *lam_out, const double *F, int with_obj, double *partials,
+                          int add) {
   double acc[2] = {0.0, 0.0};
   FOR_CELLS {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
@@ -309,7 +312,7 @@ __global__ void k_adjoint(AGrid g, Region R, const double *f, const double *lam_
     for (int l = 0; l < kQ; ++l)
       lam_out[(size_t)l * N + c] = keep * mu[l] + Arho + cx_of(l) * Ajx + cy_of(l) * Ajy;
   }
-  block_sums<2>(acc, partials + 2 * blockIdx.x);
+  block_sums<2>(acc, partials + 2 * blockIdx.x, add);
 }
 
 // Adds every partial into the two accumulators: thread i sums the partials
@@ -420,17 +423,67 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
     nbr = nblocks_for((size_t)R.w * R.h);
     nbo = nblocks_for((size_t)L * L);
     k_region_velocity<<<nbr, 256, 0, s>>>(g, R, f_n, F);
-    k_obj_gamma<<<nbo, 256, 0, s>>>(g, F, cw, bx, by, L, p_tau);
-    k_obj_velocity_adjoint<<<nbr, 256, 0, s>>>(g, R, F, bx, by, L, p_F0);
+    k_obj_gamma<<<nbo, 256, 0, s>>>(g, F, cw, bx, by, L, p_tau, 0);
+    k_obj_velocity_adjoint<<<nbr, 256, 0, s>>>(g, R, F, bx, by, L, p_F0, 0);
   }
   k_sine_tables<<<(hm.nx + hm.ny + 255) / 256, 256, 0, s>>>(g, F + S_TAB * N);
-  k_adjoint<<<nb, 256, 0, s>>>(g, R, f_n, lam_in, lam_out, F, with_obj, p_step);
+  k_adjoint<<<nb, 256, 0, s>>>(g, R, f_n, lam_in, lam_out, F, with_obj, p_step, 0);
   k_adjoint_final<<<1, 256, 0, s>>>(p_step, nb, p_tau, nbo, p_F0, nbr, with_obj, dJ_dtau,
                                     dJ_dF0);
   return cudaGetLastError();
 }
 
 int adjoint_kernel_count(double w) { return w != 0.0 ? 6 : 3; }
+
+// The adjoint steps of states[nstates - 1] .. states[0] (each [9][ny][nx]),
+// the adjoint ping-ponging between lam_out and lam_tmp so that the last
+// (state 0) lands in lam_out; weights[k] (host) the objective weight of
+// step k.  Each CTA keeps running sums of its (dJ/dtau, dJ/dF0) partials
+// over the whole sweep and one reduction at the end adds them into the
+// accumulators; the force-direction tables are built once.  The adjoint
+// fields are those of per-step adjoint_step calls; the two gradients differ
+// from theirs only by the order of the FP64 sums.
+cudaError_t adjoint_sweep(const Member &hm, const double *states, int nstates,
+                          const double *lam_in, double *lam_out, double *lam_tmp,
+                          const double *weights, int bx, int by, int L, double *dJ_dtau,
+                          double *dJ_dF0, const DiagScratch &sc, cudaStream_t s,
+                          long long *launches) {
+  const AGrid g = agrid(hm);
+  const size_t N = (size_t)hm.nx * hm.ny;
+  const int nb = nblocks_for(N);
+  double *F = sc.f;
+  double *p_step = sc.partials;                    // [nb][2]
+  double *p_tau = p_step + 2 * kMaxPartialBlocks;  // [nbo]
+  double *p_F0 = p_tau + kMaxPartialBlocks;        // [nbr]
+  int any_obj = 0;
+  for (int k = 0; k < nstates; ++k) any_obj |= weights[k] != 0.0;
+  const Region R = objective_region(hm.nx, hm.ny, bx, by, L);
+  const int nbr = any_obj ? nblocks_for((size_t)R.w * R.h) : 0;
+  const int nbo = any_obj ? nblocks_for((size_t)L * L) : 0;
+  cudaError_t e = cudaMemsetAsync(p_step, 0, sizeof(double) * 4 * kMaxPartialBlocks, s);
+  if (e != cudaSuccess) return e;
+  k_sine_tables<<<(hm.nx + hm.ny + 255) / 256, 256, 0, s>>>(g, F + S_TAB * N);
+  long long n = 2;
+  const double *in = lam_in;
+  for (int k = nstates - 1; k >= 0; --k) {
+    double *out = (k % 2 == 0) ? lam_out : lam_tmp;
+    const double *f_k = states + (size_t)k * kQ * N;
+    const int with_obj = weights[k] != 0.0;
+    if (with_obj) {
+      const double cw = weights[k] / ((double)L * (double)L);
+      k_region_velocity<<<nbr, 256, 0, s>>>(g, R, f_k, F);
+      k_obj_gamma<<<nbo, 256, 0, s>>>(g, F, cw, bx, by, L, p_tau, 1);
+      k_obj_velocity_adjoint<<<nbr, 256, 0, s>>>(g, R, F, bx, by, L, p_F0, 1);
+      n += 3;
+    }
+    k_adjoint<<<nb, 256, 0, s>>>(g, R, f_k, in, out, F, with_obj, p_step, 1);
+    n += 1;
+    in = out;
+  }
+  k_adjoint_final<<<1, 256, 0, s>>>(p_step, nb, p_tau, nbo, p_F0, nbr, any_obj, dJ_dtau, dJ_dF0);
+  if (launches) *launches += n;
+  return cudaGetLastError();
+}
 
 // Forward objective from the (rho, j) snapshot already written to sc.f[0..2].
 cudaError_t objective_from_snapshot(const Member &hm, double w, int bx, int by, int L,

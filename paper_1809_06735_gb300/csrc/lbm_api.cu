@@ -1415,15 +1415,21 @@ int lbm_adjoint_sweep(lbm_handle *h, int member, const double *states, int nstat
   if (lambda_out == lambda_tmp || lambda_in == lambda_out || lambda_in == lambda_tmp)
     return fail(h, LBM_ERR_ARG, "lambda_in, lambda_out and lambda_tmp must be distinct");
   const lbm_member_cfg &c = h->mcfg[member];
-  const size_t N = (size_t)c.nx * c.ny;
-  const double *in = lambda_in;
-  for (int k = nstates - 1; k >= 0; --k) {
-    double *out = (k % 2 == 0) ? lambda_out : lambda_tmp;
-    rc = lbm_adjoint_step(h, member, states + (size_t)k * 9 * N, in, out, weights[k], bx, by,
-                          L, dJ_dtau, dJ_dF0);
-    if (rc) return rc;
-    in = out;
+  if (c.force_kind == 2)
+    return fail(h, LBM_ERR_ARG, "the adjoint supports force kinds 0 and 1 (the damping of "
+                                "kind 2 couples every cell)");
+  if (c.collision != 0)
+    return fail(h, LBM_ERR_ARG, "the adjoint supports the BGK collision only");
+  bool any_obj = false;
+  for (int k = 0; k < nstates; ++k) {
+    if (!std::isfinite(weights[k])) return fail(h, LBM_ERR_ARG, "weights must be finite");
+    any_obj = any_obj || weights[k] != 0.0;
   }
+  if (any_obj && (L < 1 || L > c.nx || L > c.ny || bx < 0 || bx >= c.nx || by < 0 || by >= c.ny))
+    return fail(h, LBM_ERR_ARG, "objective box outside the grid");
+  if ((rc = wait_diag(h))) return rc;
+  CK(lbm::adjoint_sweep(h->hm[member], states, nstates, lambda_in, lambda_out, lambda_tmp,
+                        weights, bx, by, L, dJ_dtau, dJ_dF0, h->sc, h->stream, &h->launches));
   return LBM_OK;
 }
 

@@ -288,5 +288,12 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
 cudaError_t objective_from_snapshot(const Member &hm, double w, int bx, int by, int L,
                                     double *acc, const DiagScratch &sc, cudaStream_t s);
 int adjoint_kernel_count(double w);
+// The adjoint steps of a recorded interval, last state first, with one
+// gradient reduction per call (weights: host array of nstates).
+cudaError_t adjoint_sweep(const Member &hm, const double *states, int nstates,
+                          const double *lam_in, double *lam_out, double *lam_tmp,
+                          const double *weights, int bx, int by, int L, double *dJ_dtau,
+                          double *dJ_dF0, const DiagScratch &sc, cudaStream_t s,
+                          long long *launches);
 cudaError_t probe_fma_rate(int bits, cudaStream_t s, double *flops_per_s);
 }  // namespace lbm

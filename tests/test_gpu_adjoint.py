@@ -60,6 +60,47 @@ def test_adjoint_step_dot_product(P):
     assert abs(float((lam * dS_dF0).sum()) - float(dF)) < 1e-6 * abs(float(dF))
 
 
+@pytest.mark.parametrize("nstates,weighted", [(7, (2, 3, 5)), (6, ()), (1, (0,))])
+def test_adjoint_sweep_matches_single_steps(P, nstates, weighted):
+    """lbm_adjoint_sweep over a recorded interval (one gradient reduction per
+    call, force-direction tables built once) against nstates single
+    lbm_adjoint_step calls, last level first: the adjoint fields bit for
+    bit, dJ/dtau and dJ/dF0 to the rounding of their FP64 sums (1e-13);
+    objective weights on some levels, on none, and a one-level sweep with a
+    zero incoming adjoint."""
+    import torch
+    nx, ny, tau, F0, kf, alpha = 40, 28, 0.56, 2e-4, 2, 1e-3
+    box, L = (35, 24), 8  # wraps around both edges
+    lat = P.Lattice([P.Member(nx, ny, tau, 1.0, 1, kf, F0, alpha)], precision=64)
+    lat.set_populations(0, torch.from_numpy(li.random_populations(nx, ny, seed=4)).cuda())
+    states = torch.empty((nstates, 9, ny, nx), dtype=torch.float64, device="cuda")
+    lat.record_trajectory(0, states)
+    rng = np.random.default_rng(5)
+    lam0 = None if nstates == 1 else torch.from_numpy(rng.standard_normal((9, ny, nx))).cuda()
+    w = np.zeros(nstates)
+    for k in weighted:
+        w[k] = 0.1 * (k + 1)
+    acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+    out, tmp = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda"), \
+        torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+    lat.adjoint_sweep(0, states, lam0, out, tmp, w, box, L, acc[0:1], acc[1:2])
+    lam = lam0
+    for k in range(nstates - 1, -1, -1):
+        nxt = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+        lat.adjoint_step(0, states[k], lam, nxt, float(w[k]), box, L, acc[2:3], acc[3:4])
+        lam = nxt
+    assert torch.equal(out, lam)
+    a = acc.cpu().numpy()
+    assert abs(a[0] - a[2]) <= 1e-13 * abs(a[2]), (a[0], a[2])
+    assert abs(a[1] - a[3]) <= 1e-13 * abs(a[3]), (a[1], a[3])
+    with pytest.raises(RuntimeError):  # weights must be finite
+        lat.adjoint_sweep(0, states, lam0, out, tmp, np.full(nstates, np.nan), box, L,
+                          acc[0:1], acc[1:2])
+    with pytest.raises(RuntimeError):  # box outside the grid with a weighted level
+        lat.adjoint_sweep(0, states, lam0, out, tmp, np.ones(nstates), (nx, 0), L,
+                          acc[0:1], acc[1:2])
+
+
 def _small_spec(precision=64):
     from paper_1809_06735_gb300.adjoint import ObjectiveSpec
     return ObjectiveSpec(nx=32, ny=32, kf=2, alpha=1e-3, n0=20, n1=44, box=(5, 3), L=8,
