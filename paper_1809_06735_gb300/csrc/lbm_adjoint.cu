@@ -382,6 +382,70 @@ __global__ void __launch_bounds__(256) k_obj_forward_final(const double *partial
   if (t == 0) *acc += cw * sa[0];
 }
 
+// The forward objective in one launch of one CTA when the region R (the
+// box and the 4 cells of the eq. (18) stencil around it) has at most
+// kObjFusedCells cells: (rho, j) of R from the storage state `state` (the
+// snapshot's arithmetic), u = (j + F/2)/rho into shared memory, the box's
+// dissipation terms summed per thread, per warp and over the warps in a
+// fixed order, acc += cw * sum (the sum of k_obj_forward + k_obj_forward_final).
+constexpr int kObjFusedCells = 1600;  // a 40 x 40 region: boxes up to 32 x 32
+constexpr int kObjFusedThreads = 512;
+template <typename T>
+__global__ void __launch_bounds__(kObjFusedThreads)
+    k_obj_fused(const Member *__restrict__ members, int member, int state, AGrid g, Region R,
+                int bx, int by, int L, double cw, double *acc) {
+  __shared__ double sr[kObjFusedCells], su[kObjFusedCells], sv[kObjFusedCells];
+  __shared__ double sw[kObjFusedThreads / 32];
+  const Member &M = members[member];
+  const T *src = static_cast<const T *>(state_buffer(M, state));
+  const int tid = threadIdx.x, ncell = R.w * R.h;
+  for (int i = tid; i < ncell; i += kObjFusedThreads) {
+    const int x = wrapi(R.x0 + i % R.w, g.nx), y = wrapi(R.y0 + i / R.w, g.ny);
+    T f[kQ];
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
+    double r, jx, jy;
+    pub_moments<T>(f, M.rho0, r, jx, jy);
+    const double Fx = g.fxt[y] - g.alpha * jx, Fy = g.fyt[x] - g.alpha * jy;
+    sr[i] = r;
+    su[i] = (jx + 0.5 * Fx) / r;
+    sv[i] = (jy + 0.5 * Fy) / r;
+  }
+  __syncthreads();
+  // index in R of the grid cell (x + dx, y + dy): R holds every cell the
+  // stencil of a box cell reaches (the whole axis where it wraps onto itself)
+  auto at = [&](const double *A, int x, int y) {
+    return A[wrapi(y - R.y0, g.ny) * R.w + wrapi(x - R.x0, g.nx)];
+  };
+  auto dx = [&](const double *A, int x, int y) {
+    return 0.8 * (at(A, x + 1, y) - at(A, x - 1, y)) - 0.2 * (at(A, x + 2, y) - at(A, x - 2, y)) +
+           (4.0 / 105.0) * (at(A, x + 3, y) - at(A, x - 3, y)) -
+           (1.0 / 280.0) * (at(A, x + 4, y) - at(A, x - 4, y));
+  };
+  auto dy = [&](const double *A, int x, int y) {
+    return 0.8 * (at(A, x, y + 1) - at(A, x, y - 1)) - 0.2 * (at(A, x, y + 2) - at(A, x, y - 2)) +
+           (4.0 / 105.0) * (at(A, x, y + 3) - at(A, x, y - 3)) -
+           (1.0 / 280.0) * (at(A, x, y + 4) - at(A, x, y - 4));
+  };
+  double a = 0.0;
+  for (int i = tid; i < L * L; i += kObjFusedThreads) {
+    const int x = wrapi(bx + i % L, g.nx), y = wrapi(by + i / L, g.ny);
+    const double dxu = dx(su, x, y), dyu = dy(su, x, y);
+    const double dxv = dx(sv, x, y), dyv = dy(sv, x, y);
+    const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
+    a += -g.nu * at(sr, x, y) * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if ((tid & 31) == 0) sw[tid >> 5] = a;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kObjFusedThreads / 32; ++w) t += sw[w];
+    *acc += cw * t;
+  }
+}
+
 AGrid agrid(const Member &hm) {
   AGrid g;
   g.nx = hm.nx;
@@ -482,6 +546,25 @@ cudaError_t adjoint_sweep(const Member &hm, const double *states, int nstates,
   }
   k_adjoint_final<<<1, 256, 0, s>>>(p_step, nb, p_tau, nbo, p_F0, nbr, any_obj, dJ_dtau, dJ_dF0);
   if (launches) *launches += n;
+  return cudaGetLastError();
+}
+
+// Forward objective of the state in storage `state` in one single-CTA
+// launch when the box's region is small (returns cudaErrorNotSupported
+// otherwise, launching nothing).
+cudaError_t objective_fused(int precision, const Member *d_members, int member,
+                            const Member &hm, int state, double w, int bx, int by, int L,
+                            double *acc, cudaStream_t s) {
+  const Region R = objective_region(hm.nx, hm.ny, bx, by, L);
+  if ((long long)R.w * R.h > kObjFusedCells) return cudaErrorNotSupported;
+  const AGrid g = agrid(hm);
+  const double cw = w / ((double)L * (double)L);
+  if (precision == 32)
+    k_obj_fused<float><<<1, kObjFusedThreads, 0, s>>>(d_members, member, state, g, R, bx, by, L,
+                                                      cw, acc);
+  else
+    k_obj_fused<double><<<1, kObjFusedThreads, 0, s>>>(d_members, member, state, g, R, bx, by,
+                                                       L, cw, acc);
   return cudaGetLastError();
 }
 

@@ -1370,6 +1370,13 @@ int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx, i
   if (L < 1 || L > c.nx || L > c.ny || bx < 0 || bx >= c.nx || by < 0 || by >= c.ny)
     return fail(h, LBM_ERR_ARG, "objective box outside the grid");
   if ((rc = wait_diag(h))) return rc;
+  const cudaError_t e = lbm::objective_fused(h->precision, h->d_members, member, h->hm[member],
+                                             h->cur, weight, bx, by, L, acc, h->stream);
+  if (e == cudaSuccess) {  // small box: one launch
+    h->launches += 1;
+    return LBM_OK;
+  }
+  if (e != cudaErrorNotSupported) CK(e);
   CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, h->sc.f,
                           h->stream));
   CK(lbm::objective_from_snapshot(h->hm[member], weight, bx, by, L, acc, h->sc, h->stream));

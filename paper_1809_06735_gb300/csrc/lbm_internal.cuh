@@ -127,6 +127,71 @@ struct Tile {
   int member, x0, y0, pad;
 };
 
+#ifdef __CUDACC__
+// One-cell periodic shift.
+__device__ __forceinline__ int wrap1(int i, int n) {
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Storage index of the public population f_l(x, y) in a given state.
+__device__ __forceinline__ size_t pub_index(const Member &M, int state, int l, int x, int y) {
+  if (state == 2) return (size_t)l * M.plane + (size_t)y * M.pitch + x;
+  const int xs = wrap1(x - cx_of(l), M.nx), ys = wrap1(y - cy_of(l), M.ny);
+  const int slot = state == 3 ? opposite(l) : l;
+  return (size_t)slot * M.plane + (size_t)ys * M.pitch + xs;
+}
+__device__ __forceinline__ void *state_buffer(const Member &M, int state) {
+  return state < 2 ? M.pop[state] : M.pop[0];
+}
+
+// Error-free addition (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated FP32 sum of FP32 values, returned in FP64: the value of a
+// double-precision sum at FP32 arithmetic cost (GB300 runs FP64 at a small
+// fraction of its FP32 rate).
+__device__ __forceinline__ double csum(const float *v, const int *sign, int n) {
+  float s = sign[0] * v[0], c = 0.f;
+  for (int k = 1; k < n; ++k) {
+    float e;
+    two_sum(s, sign[k] * v[k], s, e);
+    c += e;
+  }
+  return (double)s + (double)c;
+}
+
+// (rho, j_x, j_y) in FP64 of one cell's public populations: FP32 deviations
+// g = f - t rho0 by compensated sums (rho = rho0 + sum g: the weights sum to
+// 1), FP64 populations by plain sums in index order.
+template <typename T>
+__device__ __forceinline__ void pub_moments(const T (&f)[kQ], double rho0, double &r, double &jx,
+                                            double &jy) {
+  if constexpr (sizeof(T) == 4) {
+    const int one[kQ] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    const float ax[6] = {f[1], f[5], f[8], f[3], f[6], f[7]};
+    const float ay[6] = {f[2], f[5], f[6], f[4], f[7], f[8]};
+    const int sgn[6] = {1, 1, 1, -1, -1, -1};
+    r = rho0 + csum(f, one, kQ);
+    jx = csum(ax, sgn, 6);
+    jy = csum(ay, sgn, 6);
+  } else {
+    r = 0.0;
+    jx = 0.0;
+    jy = 0.0;
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      r += f[l];
+      jx += cx_of(l) * f[l];
+      jy += cy_of(l) * f[l];
+    }
+  }
+}
+#endif
+
 __host__ __device__ inline int wrapi(int i, int n) {
   int r = i % n;
   return r < 0 ? r + n : r;
@@ -287,6 +352,13 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
                          cudaStream_t s);
 cudaError_t objective_from_snapshot(const Member &hm, double w, int bx, int by, int L,
                                     double *acc, const DiagScratch &sc, cudaStream_t s);
+// The forward objective of the state in storage `state` (acc += w times the
+// box average of the dissipation term) in one single-CTA launch, for boxes
+// whose region (the box widened by the 4-cell stencil reach) has at most
+// 1600 cells; cudaErrorNotSupported (nothing launched) for larger ones.
+cudaError_t objective_fused(int precision, const Member *d_members, int member,
+                            const Member &hm, int state, double w, int bx, int by, int L,
+                            double *acc, cudaStream_t s);
 int adjoint_kernel_count(double w);
 // The adjoint steps of a recorded interval, last state first, with one
 // gradient reduction per call (weights: host array of nstates).

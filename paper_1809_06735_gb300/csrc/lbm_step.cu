@@ -406,29 +406,6 @@ __device__ __forceinline__ void collide_f64(double f[kQ], double om, double Fex,
   collide_pair_f64(f[6], f[8], uy - ux, duy - dux, r2, base, dsq, om, keep);
 }
 
-// One-cell periodic shift.
-__device__ __forceinline__ int wrap1(int i, int n) {
-  return i < 0 ? i + n : (i >= n ? i - n : i);
-}
-
-// Storage index of the public population f_l(x, y) in a given state.
-__device__ __forceinline__ size_t pub_index(const Member &M, int state, int l, int x, int y) {
-  if (state == 2) return (size_t)l * M.plane + (size_t)y * M.pitch + x;
-  const int xs = wrap1(x - cx_of(l), M.nx), ys = wrap1(y - cy_of(l), M.ny);
-  const int slot = state == 3 ? opposite(l) : l;
-  return (size_t)slot * M.plane + (size_t)ys * M.pitch + xs;
-}
-__device__ __forceinline__ void *state_buffer(const Member &M, int state) {
-  return state < 2 ? M.pop[state] : M.pop[0];
-}
-
-// Error-free addition (Knuth's TwoSum): s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
 // Compensated FP32 sum of FP32 values as the unevaluated pair (s, c): the
 // FP64 sum is (double)s + (double)c (the csum value) and differences of
 // nearby sums can be formed in FP32 as (s - s') + (c - c').
@@ -1036,19 +1013,6 @@ __global__ void k_set_pop(const Member *__restrict__ members, int member, int st
   }
 }
 
-// Compensated FP32 sum of FP32 values, returned in FP64: the value of a
-// double-precision sum at FP32 arithmetic cost (GB300 runs FP64 at a small
-// fraction of its FP32 rate).
-__device__ __forceinline__ double csum(const float *v, const int *sign, int n) {
-  float s = sign[0] * v[0], c = 0.f;
-  for (int k = 1; k < n; ++k) {
-    float e;
-    two_sum(s, sign[k] * v[k], s, e);
-    c += e;
-  }
-  return (double)s + (double)c;
-}
-
 // (rho, j_x, j_y) of the pre-collision state, FP64, into d[3][ny*nx]; with a
 // variable-viscosity collision also the local viscosity as d[3][ny*nx].
 template <typename T>
@@ -1063,26 +1027,7 @@ __global__ void k_snapshot(const Member *__restrict__ members, int member, int s
 #pragma unroll
   for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
   double r, jx, jy;
-  if constexpr (sizeof(T) == 4) {
-    // deviations: rho = rho0 + sum g (weights sum to 1), j = sum c g
-    const int one[kQ] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
-    const float ax[6] = {f[1], f[5], f[8], f[3], f[6], f[7]};
-    const float ay[6] = {f[2], f[5], f[6], f[4], f[7], f[8]};
-    const int sgn[6] = {1, 1, 1, -1, -1, -1};
-    r = M.rho0 + csum(f, one, kQ);
-    jx = csum(ax, sgn, 6);
-    jy = csum(ay, sgn, 6);
-  } else {
-    r = 0.0;
-    jx = 0.0;
-    jy = 0.0;
-#pragma unroll
-    for (int l = 0; l < kQ; ++l) {
-      r += f[l];
-      jx += cx_of(l) * f[l];
-      jy += cy_of(l) * f[l];
-    }
-  }
+  pub_moments<T>(f, M.rho0, r, jx, jy);
   const size_t N = (size_t)M.nx * M.ny, c = (size_t)y * M.nx + x;
   d[c] = r;
   d[N + c] = jx;
