@@ -1007,6 +1007,26 @@ def case_diag_large(P, n=8192, events=2):
     print("diag_large case done:", lat.launch_count, "launches")
 
 
+def case_diag_query(P, n=2048, events=2):
+    """The all-origins box query on tables larger than L2: one FP32 member of
+    2048^2 (12 corner tables of 4.2 M records, 400 MB), L = 2..2048 over
+    every periodic origin (46 M boxes per event)."""
+    import torch
+    wl = li.large_forced_workload()
+    lat = P.Lattice([P.Member(n, n, wl["tau"], 1.0, 1, wl["kf"] * n // wl["n"], wl["F0"],
+                              wl["alpha"])], precision=32, diag_every=4)
+    lat.init_fields(0, 1.0 + li.smooth_fields(n, n, seed=7, amp=1e-3, kmax=32),
+                    li.smooth_fields(n, n, seed=5, amp=0.03, kmax=32),
+                    li.smooth_fields(n, n, seed=6, amp=0.03, kmax=32))
+    Ls = [L for L in wl["Ls"] if L <= n]
+    for _ in range(events):
+        lat.step(4)
+        stats = lat.subvolume_balance(0, Ls)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(stats[:, 2:, 0]))
+    print("diag_query case done:", lat.launch_count, "launches")
+
+
 def case_fp64(P, n=512, steps=20):
     import torch
     lat = P.Lattice([P.Member(n, n, 0.52)], precision=64)

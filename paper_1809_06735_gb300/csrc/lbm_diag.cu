@@ -1344,24 +1344,23 @@ __device__ __forceinline__ double to_mt<double>(long long v) {
 }
 template <>
 __device__ __forceinline__ float to_mt<float>(long long v) {
-  const unsigned long long sgn = (unsigned long long)v >> 63;
-  const unsigned long long a = sgn ? 0ull - (unsigned long long)v : (unsigned long long)v;
-  if (a == 0ull) return 0.0f;
-  int e = 63 - __clzll((long long)a);  // index of the leading one
-  unsigned long long m;
-  if (e <= 23) {
-    m = a << (23 - e);
-  } else {
-    const int sh = e - 23;
-    m = (a + (1ull << (sh - 1))) >> sh;
-    if (m >> 24) {  // rounding carried into a new leading bit
-      m >>= 1;
-      ++e;
-    }
-  }
-  const unsigned bits = ((unsigned)sgn << 31) | ((unsigned)(e + 127) << 23) |
-                        ((unsigned)m & 0x7fffffu);
-  return __uint_as_float(bits);
+  // |v| = h 2^42 + m 2^21 + l with l, m < 2^21 and h <= 2^22: each piece is
+  // exact in FP32 once its bits are placed in the mantissa of 2^23 and that
+  // constant is subtracted; two fused multiply-adds of non-negative terms
+  // combine them (at most one unit in the last place from the correctly
+  // rounded value, the same for every call), the sign is applied last.  No
+  // integer-to-float instruction: GB300 issues those at a small fraction of
+  // the FP32 rate.
+  const bool neg = v < 0;
+  const unsigned long long a = neg ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const unsigned l = (unsigned)a & 0x1FFFFFu;
+  const unsigned m = (unsigned)(a >> 21) & 0x1FFFFFu;
+  const unsigned h = (unsigned)(a >> 42);
+  const float fl = __uint_as_float(0x4B000000u | l) - 8388608.0f;
+  const float fm = __uint_as_float(0x4B000000u | m) - 8388608.0f;
+  const float fh = __uint_as_float(0x4B000000u | h) - 8388608.0f;
+  const float r = fmaf(fh, 4398046511104.0f, fmaf(fm, 2097152.0f, fl));
+  return neg ? -r : r;
 }
 
 // Bin of v among ne ascending edges: the number of edges <= v.
@@ -1471,17 +1470,57 @@ __global__ void __launch_bounds__(256, 3) k_query(const DiagJob *__restrict__ jo
   };
   int x0 = 0, y0 = 0;
   if (b < nb) origin(b, x0, y0);
+  // all periodic origins in row-major order: the next origin is this one
+  // advanced by the stride (no division per box)
+  const int sdx = ooff < 0 ? stride % nx : 0, sdy = ooff < 0 ? stride / nx : 0;
   for (; b < nb; b += stride) {
     int xn = 0, yn = 0;  // the next box's origin, loaded ahead
-    if (b + stride < nb) origin(b + stride, xn, yn);
+    if (ooff < 0) {
+      xn = x0 + sdx;
+      yn = y0 + sdy;
+      if (xn >= nx) {
+        xn -= nx;
+        ++yn;
+      }
+    } else if (b + stride < nb) {
+      origin(b + stride, xn, yn);
+    }
     const bool inside = x0 + L <= nx && y0 + L <= ny;
     MT lhs = 0, sum = 0, mx = 0;
     double *o = PER_BOX ? per_box + ((size_t)meta[8 * iL + 3] + b) * 15 : nullptr;
     // a non-wrapping box of a 12-field table: the six values of a corner are
     // 48 bytes at a 16-byte boundary, three vector loads per corner
     unsigned long long vs[6];
-    const bool vec = inside && nF == 12 && nfield == 6;
-    if (vec) {
+    const bool vec = nF == 12 && nfield == 6;
+    if (vec && !inside) {
+      // a box across the periodic edge: the prefix sum extended periodically
+      // is a signed sum of at most 3 x 3 table corners, columns
+      // {x0 + L, x0} or {nx, x0, x0 + L - nx} (and rows likewise); each
+      // corner's six values are three 16-byte loads
+      const int wx = x0 + L > nx, wy = y0 + L > ny;
+      const int X[3] = {wx ? nx : x0 + L, x0, x0 + L - nx};
+      const int Y[3] = {wy ? ny : y0 + L, y0, y0 + L - ny};
+#pragma unroll
+      for (int j = 0; j < 6; ++j) vs[j] = 0ull;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (k == 2 && !wy) break;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          if (i == 2 && !wx) break;
+          const bool neg = (i == 1) != (k == 1);  // the x0 column and the y0 row subtract
+          const longlong2 *c =
+              reinterpret_cast<const longlong2 *>(S + ((size_t)Y[k] * rs + X[i]) * 12);
+#pragma unroll
+          for (int h = 0; h < 3; ++h) {
+            const longlong2 a = c[h];
+            const unsigned long long ax = (unsigned long long)a.x, ay = (unsigned long long)a.y;
+            vs[2 * h] = neg ? vs[2 * h] - ax : vs[2 * h] + ax;
+            vs[2 * h + 1] = neg ? vs[2 * h + 1] - ay : vs[2 * h + 1] + ay;
+          }
+        }
+      }
+    } else if (vec) {
       const long long *lo = S + ((size_t)y0 * rs + x0) * 12, *hi = lo + (size_t)L * rs * 12;
       const size_t dx = (size_t)L * 12;
       const longlong2 *c00 = reinterpret_cast<const longlong2 *>(lo);
