@@ -225,13 +225,12 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
         const T z = a * y[l], lz = ln1p_e<T>(z);
         T ph;
         if (fabs(z) < T(0.1)) {
-          ph = T(0);
-          T p = z * z;
+          // phi(z) = sum_{k>=2} (-1)^k z^k / (k (k - 1)), terms to z^9, in
+          // Horner form
+          T p = T(1.0 / 72.0);
 #pragma unroll
-          for (int k = 2; k < 10; ++k) {
-            ph += ((k & 1) ? -p : p) * T(1.0 / (k * (k - 1)));
-            p *= z;
-          }
+          for (int k = 8; k >= 2; --k) p = fma(-z, p, T(1.0 / (k * (k - 1))));
+          ph = z * z * p;
         } else {
           ph = (T(1) + z) * lz - z;
         }
@@ -304,7 +303,10 @@ __device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
   const T Fx = Fex - alpha_drag * jx, Fy = Fey - alpha_drag * jy;
   T lp[kQ], lps[kQ];
   entropic_logp<T>(ux, uy, lp);
-  entropic_logp<T>(ux + Fx / rho, uy + Fy / rho, lps);
+  // without force the shifted velocity is u itself and the EDM term is
+  // exactly zero: its second set of logarithms and exponentials is skipped
+  const bool forced = Fx != T(0) || Fy != T(0);
+  if (forced) entropic_logp<T>(ux + Fx / rho, uy + Fy / rho, lps);
   T f[kQ], d[kQ], Fl[kQ];
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
@@ -317,7 +319,7 @@ __device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
       f[l] = v[l];
       d[l] = t * rho * (T(1) + em) - v[l];
     }
-    Fl[l] = t * rho * (T(1) + em) * expm1_e<T>(lps[l] - lp[l]);
+    Fl[l] = forced ? t * rho * (T(1) + em) * expm1_e<T>(lps[l] - lp[l]) : T(0);
   }
   const T a = elbm_alpha<T>(f, d);
   const T ab = a / (T(2) * tau0);
