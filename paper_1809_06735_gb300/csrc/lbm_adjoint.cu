@@ -143,8 +143,8 @@ __global__ void k_region_velocity(AGrid g, Region R, const double *f, double *F)
     for (int l = 0; l < kQ; ++l) {
       const double v = f[(size_t)l * N + c];
       r += v;
-      a += cx_of(l) * v;
-      b += cy_of(l) * v;
+      if (cx_of(l) != 0) a += cx_of(l) * v;
+      if (cy_of(l) != 0) b += cy_of(l) * v;
     }
     const double Fx = g.fxt[y] - g.alpha * a, Fy = g.fyt[x] - g.alpha * b;
     F[A_RHO * N + c] = r;
@@ -270,8 +270,8 @@ __global__ void k_adjoint(AGrid g, Region R, const double *f, const double *lam_
     for (int l = 0; l < kQ; ++l) {
       fl[l] = f[(size_t)l * N + c];
       rho += fl[l];
-      jx += cx_of(l) * fl[l];
-      jy += cy_of(l) * fl[l];
+      if (cx_of(l) != 0) jx += cx_of(l) * fl[l];
+      if (cy_of(l) != 0) jy += cy_of(l) * fl[l];
       const int xd = wr(x + cx_of(l), g.nx), yd = wr(y + cy_of(l), g.ny);
       mu[l] = lam_in ? lam_in[(size_t)l * N + (size_t)yd * g.nx + xd] : 0.0;
     }
@@ -309,8 +309,12 @@ __global__ void k_adjoint(AGrid g, Region R, const double *f, const double *lam_
     }
     const double keep = 1.0 - g.omega;
 #pragma unroll
-    for (int l = 0; l < kQ; ++l)
-      lam_out[(size_t)l * N + c] = keep * mu[l] + Arho + cx_of(l) * Ajx + cy_of(l) * Ajy;
+    for (int l = 0; l < kQ; ++l) {  // the terms with c = 0 skipped: a product by 0
+      double o = keep * mu[l] + Arho;  // still costs an FMA under IEEE arithmetic
+      if (cx_of(l) != 0) o += cx_of(l) * Ajx;
+      if (cy_of(l) != 0) o += cy_of(l) * Ajy;
+      lam_out[(size_t)l * N + c] = o;
+    }
   }
   block_sums<2>(acc, partials + 2 * blockIdx.x, add);
 }

@@ -185,8 +185,8 @@ __device__ __forceinline__ void pub_moments(const T (&f)[kQ], double rho0, doubl
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       r += f[l];
-      jx += cx_of(l) * f[l];
-      jy += cy_of(l) * f[l];
+      if (cx_of(l) != 0) jx += cx_of(l) * f[l];
+      if (cy_of(l) != 0) jy += cy_of(l) * f[l];
     }
   }
 }

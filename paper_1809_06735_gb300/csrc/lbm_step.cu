@@ -64,9 +64,9 @@ __device__ __forceinline__ double local_tau_f64(const double f[kQ], double rho, 
   double sxx = 0.0, sxy = 0.0, syy = 0.0;
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
-    sxx += cx_of(l) * cx_of(l) * f[l];
-    sxy += cx_of(l) * cy_of(l) * f[l];
-    syy += cy_of(l) * cy_of(l) * f[l];
+    if (cx_of(l) != 0) sxx += f[l];
+    if (cx_of(l) * cy_of(l) != 0) sxy += cx_of(l) * cy_of(l) * f[l];
+    if (cy_of(l) != 0) syy += f[l];
   }
   return tau_from_stress<double>(sxx - rho / 3.0 - rho * ux * ux, sxy - rho * ux * uy,
                                  syy - rho / 3.0 - rho * uy * uy, rho, tau0, coll, Cs);
@@ -75,10 +75,10 @@ __device__ __forceinline__ void moments_f64(const double f[kQ], double &rho, dou
                                             double &uy) {
   double r = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) {
-    r += f[l];
-    jx += cx_of(l) * f[l];
-    jy += cy_of(l) * f[l];
+  for (int l = 0; l < kQ; ++l) {  // terms with c = 0 skipped (a product by 0 is not
+    r += f[l];                       // dropped by IEEE arithmetic: it costs an FMA)
+    if (cx_of(l) != 0) jx += cx_of(l) * f[l];
+    if (cy_of(l) != 0) jy += cy_of(l) * f[l];
   }
   rho = r;
   const double ir = 1.0 / r;
@@ -294,8 +294,8 @@ __device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       rho += v[l];
-      jx += cx_of(l) * v[l];
-      jy += cy_of(l) * v[l];
+      if (cx_of(l) != 0) jx += cx_of(l) * v[l];
+      if (cy_of(l) != 0) jy += cy_of(l) * v[l];
     }
     drho = T(0);
   }
@@ -1100,8 +1100,8 @@ __global__ void k_snapshot_ring(const Member *__restrict__ members, int state, i
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       r += f[l];
-      jx += cx_of(l) * f[l];
-      jy += cy_of(l) * f[l];
+      if (cx_of(l) != 0) jx += cx_of(l) * f[l];
+      if (cy_of(l) != 0) jy += cy_of(l) * f[l];
     }
     double *d = M.snap + (size_t)slot * 3 * N;
     d[c] = r;
@@ -1223,8 +1223,8 @@ __global__ void __launch_bounds__(256) k_project(const Member *__restrict__ memb
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       rho += f[l];
-      jx += (T)cx_of(l) * f[l];
-      jy += (T)cy_of(l) * f[l];
+      if (cx_of(l) != 0) jx += (T)cx_of(l) * f[l];
+      if (cy_of(l) != 0) jy += (T)cy_of(l) * f[l];
     }
     const T ir = T(1) / rho;
     const T u[2] = {jx * ir, jy * ir};
@@ -1378,8 +1378,8 @@ __device__ __forceinline__ void proj4_moments(float rho0, const float4 (&o)[kQ],
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       rho[i] += v[i];
-      jx[i] += (float)cx_of(l) * v[i];
-      jy[i] += (float)cy_of(l) * v[i];
+      if (cx_of(l) != 0) jx[i] += (float)cx_of(l) * v[i];
+      if (cy_of(l) != 0) jy[i] += (float)cy_of(l) * v[i];
     }
   }
 }
