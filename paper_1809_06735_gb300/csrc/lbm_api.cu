@@ -1402,6 +1402,21 @@ int lbm_record_trajectory(lbm_handle *h, int member, int nstates, double *states
   if (nstates < 1) return fail(h, LBM_ERR_ARG, "nstates must be >= 1");
   const lbm_member_cfg &c = h->mcfg[member];
   const size_t N = (size_t)c.nx * c.ny;
+  // one member on the general kernel, no snapshot cadence, no projection:
+  // each step writes the public state it starts from (one launch and one
+  // read of the state per level instead of a step and an export)
+  if (h->mcfg.size() == 1 && h->scalar_members.size() == 1 && h->ntiles == 0 &&
+      h->cfg.diag_every == 0 && !h->has_kind2) {
+    if ((rc = wait_diag(h))) return rc;
+    for (int k = 0; k + 1 < nstates; ++k) {
+      CK(lbm::launch_step_scalar(h->precision, h->d_members, member, c.nx, c.ny, h->cur,
+                                 h->stream, states + (size_t)k * 9 * N));
+      h->launches += 1;
+      h->cur ^= 1;
+      h->t += 1;
+    }
+    return lbm_get_populations(h, member, states + (size_t)(nstates - 1) * 9 * N, 1);
+  }
   for (int k = 0; k < nstates; ++k) {
     if (k > 0)
       if ((rc = lbm_step(h, 1))) return rc;

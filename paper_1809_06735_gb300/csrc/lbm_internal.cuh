@@ -218,8 +218,10 @@ cudaError_t launch_step_f32_vec(const Member *d_members, const Tile *d_tiles, in
 cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tiles, int ntiles,
                                      int state, int flip, const LaunchCfg &lc, int slot,
                                      cudaStream_t s);
+// rec (optional): the member's public state before the step, FP64
+// [9][ny][nx] (the values lbm_get_populations returns), written by the step.
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member,
-                               int nx, int ny, int cur, cudaStream_t s);
+                               int nx, int ny, int cur, cudaStream_t s, double *rec = nullptr);
 struct InitList;
 // The general kernel for the members members[0..n) (host array), one launch
 // per 256 members, grid sized for nx_max x ny_max.

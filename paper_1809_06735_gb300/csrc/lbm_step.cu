@@ -710,9 +710,11 @@ cudaError_t launch_step_f32_vec_snap(const Member *d_members, const Tile *d_tile
 // L2ONLY loads the populations past L1 (ld.global.cg): the persistent
 // kernel below reads, at each step, values other SMs wrote at the previous
 // one, which a stale L1 line of this SM could otherwise shadow.  The
-// arithmetic is the same either way.
+// arithmetic is the same either way.  rec (optional): the public state
+// before the step, FP64 [9][ny][nx], as k_get_pop writes it.
 template <typename T, bool L2ONLY>
-__device__ __forceinline__ void step_cell(const Member &M, int state, int x, int y) {
+__device__ __forceinline__ void step_cell(const Member &M, int state, int x, int y,
+                                          double *rec = nullptr) {
   const T *src = static_cast<const T *>(state_buffer(M, state));
   T *dst = static_cast<T *>(state < 2 ? M.pop[state ^ 1] : M.pop[0]);
   T fx = static_cast<const T *>(M.fx_tab)[y];
@@ -735,6 +737,15 @@ __device__ __forceinline__ void step_cell(const Member &M, int state, int x, int
       f[l] = __ldcg(a);
     else
       f[l] = *a;
+  }
+  if (rec) {
+    const size_t N = (size_t)M.nx * M.ny;
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      double v = (double)f[l];
+      if (sizeof(T) == 4) v += w_of(l) * M.rho0;
+      rec[(size_t)l * N + (size_t)y * M.nx + x] = v;
+    }
   }
   if (M.collision == 3) {
     if constexpr (sizeof(T) == 4)
@@ -762,12 +773,13 @@ __device__ __forceinline__ void step_cell(const Member &M, int state, int x, int
 }
 
 template <typename T>
-__global__ void k_step_scalar(const Member *__restrict__ members, int member, int state) {
+__global__ void k_step_scalar(const Member *__restrict__ members, int member, int state,
+                              double *rec) {
   const Member &M = members[member];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= M.nx || y >= M.ny) return;
-  step_cell<T, false>(M, state, x, y);
+  step_cell<T, false>(M, state, x, y, rec);
 }
 
 // ---------------------------------------------------------------------------
@@ -929,15 +941,16 @@ cudaError_t launch_step_scalar_batch(int precision, const Member *d_members, con
 }
 
 cudaError_t launch_step_scalar(int precision, const Member *d_members, int member, int nx,
-                               int ny, int state, cudaStream_t s) {
-  // one thread per cell; a grid too small to give every SM a 256-thread CTA
-  // gets 64-thread CTAs, so that its FP64 arithmetic (slow on this part)
-  // spreads over four times as many SMs
-  const dim3 b = (long long)nx * ny < (1LL << 15) ? dim3(32, 2) : dim3(64, 4);
+                               int ny, int state, cudaStream_t s, double *rec) {
+  // one thread per cell; grids below 2^17 cells get 64-thread CTAs, so that
+  // their FP64 arithmetic (slow on this part) spreads evenly over the SMs
+  // (256^2 FP64: 16.9 against 18.2 us per step with 256-thread CTAs in 1.7
+  // waves; no difference from 384^2 up)
+  const dim3 b = (long long)nx * ny < (1LL << 17) ? dim3(32, 2) : dim3(64, 4);
   if (precision == 32)
-    k_step_scalar<float><<<grid2d(nx, ny, b), b, 0, s>>>(d_members, member, state);
+    k_step_scalar<float><<<grid2d(nx, ny, b), b, 0, s>>>(d_members, member, state, rec);
   else
-    k_step_scalar<double><<<grid2d(nx, ny, b), b, 0, s>>>(d_members, member, state);
+    k_step_scalar<double><<<grid2d(nx, ny, b), b, 0, s>>>(d_members, member, state, rec);
   return cudaGetLastError();
 }
 

@@ -101,6 +101,39 @@ def test_adjoint_sweep_matches_single_steps(P, nstates, weighted):
                           acc[0:1], acc[1:2])
 
 
+@pytest.mark.parametrize("prec,grids", [(64, [(37, 23)]), (32, [(37, 23)]), (32, [(40, 24)]),
+                                         (64, [(37, 23), (16, 12)])])
+def test_record_trajectory_matches_steps(P, prec, grids):
+    """lbm_record_trajectory against single steps and exports (lbm_step(1) +
+    lbm_get_populations), bit for bit, and the handle's time afterwards: one
+    member on the general kernel (each step writes the state it starts from,
+    FP64 and FP32), one on the FP32 vector kernel and two members (step and
+    export per level)."""
+    import torch
+    members = [P.Member(nx, ny, 0.57, 1.0, 1, 1, 2e-4, 1e-3) for (nx, ny) in grids]
+    a = P.Lattice(members, precision=prec)
+    b = P.Lattice(members, precision=prec)
+    for i, (nx, ny) in enumerate(grids):
+        f0 = torch.from_numpy(li.random_populations(nx, ny, seed=20 + i)).cuda()
+        a.set_populations(i, f0)
+        b.set_populations(i, f0)
+    a.step(3)
+    b.step(3)
+    K = 9
+    nx, ny = grids[0]
+    states = torch.empty((K, 9, ny, nx), dtype=torch.float64, device="cuda")
+    a.record_trajectory(0, states)
+    for k in range(K):
+        if k:
+            b.step(1)
+        assert torch.equal(states[k], b.get_populations(0)), k
+    assert a.time == b.time == 3 + K - 1
+    a.step(2)
+    b.step(2)
+    for i in range(len(grids)):
+        assert torch.equal(a.get_populations(i), b.get_populations(i))
+
+
 def _small_spec(precision=64):
     from paper_1809_06735_gb300.adjoint import ObjectiveSpec
     return ObjectiveSpec(nx=32, ny=32, kf=2, alpha=1e-3, n0=20, n1=44, box=(5, 3), L=8,
