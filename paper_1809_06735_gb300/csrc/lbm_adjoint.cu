@@ -466,10 +466,23 @@ AGrid agrid(const Member &hm) {
   return g;
 }
 
-int nblocks_for(size_t N) {
-  size_t b = (N + 255) / 256;
+int nblocks_for(size_t N, int threads = 256) {
+  size_t b = (N + threads - 1) / threads;
   return (int)(b > (size_t)kMaxPartialBlocks ? kMaxPartialBlocks : (b < 1 ? 1 : b));
 }
+
+// CTA size of the objective kernels of an adjoint step: their few hundred
+// to few thousand cells of FP64 work spread over as many SMs as possible
+// (GB300 issues about 1.7 FP64 FMAs per clock per SM).  A 100-level sweep
+// of 256^2 with every other level weighted (L = 16): 42.8 us per level with
+// 32-thread CTAs, 44.4 with 256 threads, 52.0 with the three kernels in one
+// single-CTA launch.
+constexpr int kObjThreads = 32;
+
+// CTA size of k_adjoint: 64 threads below 2^17 cells, so that a small
+// grid's FP64 work spreads evenly over the SMs (256^2: 44.3 against 46.2 us
+// per adjoint step with 256-thread CTAs in 1.7 waves), 256 above.
+int adjoint_threads(size_t N) { return N < ((size_t)1 << 17) ? 64 : 256; }
 
 }  // namespace
 
@@ -478,7 +491,7 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
                          double *dJ_dF0, const DiagScratch &sc, cudaStream_t s) {
   const AGrid g = agrid(hm);
   const size_t N = (size_t)hm.nx * hm.ny;
-  const int nb = nblocks_for(N);
+  const int tpb = adjoint_threads(N), nb = nblocks_for(N, tpb);
   double *F = sc.f;
   double *p_step = sc.partials;                         // [nb][2]
   double *p_tau = p_step + 2 * kMaxPartialBlocks;       // [nbo]
@@ -488,14 +501,14 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
   int nbo = 0, nbr = 0;
   if (with_obj) {
     const double cw = w / ((double)L * (double)L);
-    nbr = nblocks_for((size_t)R.w * R.h);
-    nbo = nblocks_for((size_t)L * L);
-    k_region_velocity<<<nbr, 256, 0, s>>>(g, R, f_n, F);
-    k_obj_gamma<<<nbo, 256, 0, s>>>(g, F, cw, bx, by, L, p_tau, 0);
-    k_obj_velocity_adjoint<<<nbr, 256, 0, s>>>(g, R, F, bx, by, L, p_F0, 0);
+    nbr = nblocks_for((size_t)R.w * R.h, kObjThreads);
+    nbo = nblocks_for((size_t)L * L, kObjThreads);
+    k_region_velocity<<<nbr, kObjThreads, 0, s>>>(g, R, f_n, F);
+    k_obj_gamma<<<nbo, kObjThreads, 0, s>>>(g, F, cw, bx, by, L, p_tau, 0);
+    k_obj_velocity_adjoint<<<nbr, kObjThreads, 0, s>>>(g, R, F, bx, by, L, p_F0, 0);
   }
   k_sine_tables<<<(hm.nx + hm.ny + 255) / 256, 256, 0, s>>>(g, F + S_TAB * N);
-  k_adjoint<<<nb, 256, 0, s>>>(g, R, f_n, lam_in, lam_out, F, with_obj, p_step, 0);
+  k_adjoint<<<nb, tpb, 0, s>>>(g, R, f_n, lam_in, lam_out, F, with_obj, p_step, 0);
   k_adjoint_final<<<1, 256, 0, s>>>(p_step, nb, p_tau, nbo, p_F0, nbr, with_obj, dJ_dtau,
                                     dJ_dF0);
   return cudaGetLastError();
@@ -518,7 +531,7 @@ cudaError_t adjoint_sweep(const Member &hm, const double *states, int nstates,
                           long long *launches) {
   const AGrid g = agrid(hm);
   const size_t N = (size_t)hm.nx * hm.ny;
-  const int nb = nblocks_for(N);
+  const int tpb = adjoint_threads(N), nb = nblocks_for(N, tpb);
   double *F = sc.f;
   double *p_step = sc.partials;                    // [nb][2]
   double *p_tau = p_step + 2 * kMaxPartialBlocks;  // [nbo]
@@ -526,8 +539,8 @@ cudaError_t adjoint_sweep(const Member &hm, const double *states, int nstates,
   int any_obj = 0;
   for (int k = 0; k < nstates; ++k) any_obj |= weights[k] != 0.0;
   const Region R = objective_region(hm.nx, hm.ny, bx, by, L);
-  const int nbr = any_obj ? nblocks_for((size_t)R.w * R.h) : 0;
-  const int nbo = any_obj ? nblocks_for((size_t)L * L) : 0;
+  const int nbr = any_obj ? nblocks_for((size_t)R.w * R.h, kObjThreads) : 0;
+  const int nbo = any_obj ? nblocks_for((size_t)L * L, kObjThreads) : 0;
   cudaError_t e = cudaMemsetAsync(p_step, 0, sizeof(double) * 4 * kMaxPartialBlocks, s);
   if (e != cudaSuccess) return e;
   k_sine_tables<<<(hm.nx + hm.ny + 255) / 256, 256, 0, s>>>(g, F + S_TAB * N);
@@ -539,12 +552,12 @@ cudaError_t adjoint_sweep(const Member &hm, const double *states, int nstates,
     const int with_obj = weights[k] != 0.0;
     if (with_obj) {
       const double cw = weights[k] / ((double)L * (double)L);
-      k_region_velocity<<<nbr, 256, 0, s>>>(g, R, f_k, F);
-      k_obj_gamma<<<nbo, 256, 0, s>>>(g, F, cw, bx, by, L, p_tau, 1);
-      k_obj_velocity_adjoint<<<nbr, 256, 0, s>>>(g, R, F, bx, by, L, p_F0, 1);
+      k_region_velocity<<<nbr, kObjThreads, 0, s>>>(g, R, f_k, F);
+      k_obj_gamma<<<nbo, kObjThreads, 0, s>>>(g, F, cw, bx, by, L, p_tau, 1);
+      k_obj_velocity_adjoint<<<nbr, kObjThreads, 0, s>>>(g, R, F, bx, by, L, p_F0, 1);
       n += 3;
     }
-    k_adjoint<<<nb, 256, 0, s>>>(g, R, f_k, in, out, F, with_obj, p_step, 1);
+    k_adjoint<<<nb, tpb, 0, s>>>(g, R, f_k, in, out, F, with_obj, p_step, 1);
     n += 1;
     in = out;
   }

@@ -60,8 +60,10 @@ def test_adjoint_step_dot_product(P):
     assert abs(float((lam * dS_dF0).sum()) - float(dF)) < 1e-6 * abs(float(dF))
 
 
-@pytest.mark.parametrize("nstates,weighted", [(7, (2, 3, 5)), (6, ()), (1, (0,))])
-def test_adjoint_sweep_matches_single_steps(P, nstates, weighted):
+@pytest.mark.parametrize("nstates,weighted,box,L", [(7, (2, 3, 5), (35, 24), 8), (6, (), (35, 24), 8),
+                                                   (1, (0,), (35, 24), 8),
+                                                   (5, (1, 3), (30, 20), 24)])
+def test_adjoint_sweep_matches_single_steps(P, nstates, weighted, box, L):
     """lbm_adjoint_sweep over a recorded interval (one gradient reduction per
     call, force-direction tables built once) against nstates single
     lbm_adjoint_step calls, last level first: the adjoint fields bit for
@@ -70,7 +72,7 @@ def test_adjoint_sweep_matches_single_steps(P, nstates, weighted):
     zero incoming adjoint."""
     import torch
     nx, ny, tau, F0, kf, alpha = 40, 28, 0.56, 2e-4, 2, 1e-3
-    box, L = (35, 24), 8  # wraps around both edges
+    # boxes wrapping around both edges; L = 24: a region of 32 x 28 cells
     lat = P.Lattice([P.Member(nx, ny, tau, 1.0, 1, kf, F0, alpha)], precision=64)
     lat.set_populations(0, torch.from_numpy(li.random_populations(nx, ny, seed=4)).cuda())
     states = torch.empty((nstates, 9, ny, nx), dtype=torch.float64, device="cuda")
@@ -164,13 +166,17 @@ def test_objective_forward_matches_oracle(P, orc, n, box, L, precision, tol):
     assert abs(float(J) - Jo) < tol * abs(Jo), (float(J), Jo)
 
 
-def test_gradients_match_oracle_finite_differences(P, orc):
+@pytest.mark.parametrize("box,L", [((5, 3), 8), ((20, 27), 24)])
+def test_gradients_match_oracle_finite_differences(P, orc, box, L):
     """dJ/dtau (h = 1e-6), dJ/dF0 (1e-3 relative step, Richardson) and a
     directional derivative in f0 against central differences of the FP64
-    oracle objective."""
+    oracle objective; a box whose region (box plus stencil reach) fits the
+    single-CTA forward objective (8 x 8) and one that does not (24 x 24 on
+    32^2: the region is the whole grid)."""
+    import dataclasses
     import torch
     from paper_1809_06735_gb300.adjoint import box_dissipation
-    spec = _small_spec()
+    spec = dataclasses.replace(_small_spec(), box=box, L=L)
     tau0, kf, alpha = 0.6, 2, 1e-3
     F00 = li.kolmogorov_F0(32, tau0, kf, alpha, 0.02)
     r, u, v = li.random_phase(32, seed=4, u_rms=0.02, k_peak=3.0)
