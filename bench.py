@@ -1041,10 +1041,11 @@ def case_adjoint(P, n=256, steps=6):
     F0 = li.kolmogorov_F0(n, 0.55, 4, 1e-4, 0.03)
     lat = P.Lattice([P.Member(n, n, 0.55, 1.0, 1, 4, F0, 1e-4)], precision=64)
     lat.init_fields(0, *li.random_phase(n, seed=0, u_rms=0.02))
+    acc = torch.zeros(2, dtype=torch.float64, device="cuda")
+    lat.objective_steps(0, steps, 1e-3, (0, 0), 16, acc[0:1])  # forward objective levels
     f = lat.get_populations(0)
     lam = torch.zeros_like(f)
     out = torch.empty_like(f)
-    acc = torch.zeros(2, dtype=torch.float64, device=f.device)
     for _ in range(steps):
         lat.adjoint_step(0, f, lam, out, 1e-3, (0, 0), 16, acc[0:1], acc[1:2])
         lam, out = out, lam

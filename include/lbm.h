@@ -363,9 +363,9 @@ int lbm_adjoint_step(lbm_handle *h, int member, const double *f_n,
 /* acc[0] += weight * (L x L box average, origin (bx, by), of the dissipation
  * term RHS^{E,4} of eq. (8) of member `member` at the current time): the
  * forward objective matching lbm_adjoint_step.  acc is a device pointer to
- * one double.  One kernel launch when the box widened by the 4-cell reach of
- * the eq. (18) stencils covers at most 1600 cells (L <= 32 away from the
- * whole-axis case), four otherwise. */
+ * one double.  One kernel launch (the moments of the box widened by the
+ * 4-cell reach of the eq. (18) stencils only, per tile of the box, and a
+ * fixed-order sum: the result does not depend on the launch order). */
 int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx,
                              int by, int L, double *acc);
 

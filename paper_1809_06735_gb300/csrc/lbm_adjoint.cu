@@ -20,6 +20,8 @@
 //   u = (j + F/2)/rho, F = F_ext - alpha j, nu = (tau - 1/2)/3,
 // whose adjoint uses D^T = -D (antisymmetric periodic eq. (18) stencil).
 // All arithmetic is FP64; reductions are block-deterministic.
+#include <algorithm>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -40,23 +42,6 @@ __device__ __forceinline__ int wrapn(int i, int n) {
   return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 __device__ __forceinline__ int wr(int i, int n) { return n >= 4 ? wrapn(i, n) : wrapi(i, n); }
-
-__device__ __forceinline__ double Dx(const double *A, const AGrid &g, int x, int y) {
-  const double *r = A + (size_t)y * g.nx;
-  return 0.8 * (r[wr(x + 1, g.nx)] - r[wr(x - 1, g.nx)]) -
-         0.2 * (r[wr(x + 2, g.nx)] - r[wr(x - 2, g.nx)]) +
-         (4.0 / 105.0) * (r[wr(x + 3, g.nx)] - r[wr(x - 3, g.nx)]) -
-         (1.0 / 280.0) * (r[wr(x + 4, g.nx)] - r[wr(x - 4, g.nx)]);
-}
-__device__ __forceinline__ double Dy(const double *A, const AGrid &g, int x, int y) {
-  auto at = [&](int d) { return A[(size_t)wr(y + d, g.ny) * g.nx + x]; };
-  return 0.8 * (at(1) - at(-1)) - 0.2 * (at(2) - at(-2)) + (4.0 / 105.0) * (at(3) - at(-3)) -
-         (1.0 / 280.0) * (at(4) - at(-4));
-}
-
-__device__ __forceinline__ bool in_box(int x, int y, int bx, int by, int L, const AGrid &g) {
-  return wrapi(x - bx, g.nx) < L && wrapi(y - by, g.ny) < L;
-}
 
 __device__ __forceinline__ void force_dir(const AGrid &g, int x, int y, double &sx, double &sy) {
   if (g.force == 1) {
@@ -147,85 +132,124 @@ __global__ void k_region_velocity(AGrid g, Region R, const double *f, double *F)
       if (cy_of(l) != 0) b += cy_of(l) * v;
     }
     const double Fx = g.fxt[y] - g.alpha * a, Fy = g.fyt[x] - g.alpha * b;
+    const double ir = 1.0 / r;
     F[A_RHO * N + c] = r;
-    F[A_U * N + c] = (a + 0.5 * Fx) / r;
-    F[A_V * N + c] = (b + 0.5 * Fy) / r;
+    F[A_U * N + c] = (a + 0.5 * Fx) * ir;
+    F[A_V * N + c] = (b + 0.5 * Fy) * ir;
   }
 }
 
-// u = (j + F/2)/rho from (rho, j) fields at F + 0..2N (forward objective).
-__global__ void k_velocity(AGrid g, double *F) {
-  FOR_CELLS {
-    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
-    const double r = F[A_RHO * N + c], jx = F[A_JX * N + c], jy = F[A_JY * N + c];
-    const double Fx = g.fxt[y] - g.alpha * jx, Fy = g.fyt[x] - g.alpha * jy;
-    F[A_U * N + c] = (jx + 0.5 * Fx) / r;
-    F[A_V * N + c] = (jy + 0.5 * Fy) / r;
-  }
+// Four lanes per cell: lanes 4q .. 4q + 3 of a warp share cell q of the
+// warp's group of eight, lane part p = lane & 3 evaluates one of the cell's
+// four stencil derivatives and the quad exchanges them by shuffles (a
+// quarter of the dependent FP64 chain per lane, four times the SMs).  The
+// loop runs in whole warps: a lane past the last cell works on the last
+// cell and writes nothing, so every shuffle has the full warp.
+#define FOR_QUADS(NCELLS)                                                      \
+  const int lane = threadIdx.x & 31, p = lane & 3, qb = lane & ~3;             \
+  const int wglob = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);       \
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);                     \
+  for (int i0 = wglob * 8; i0 < (NCELLS); i0 += nwarps * 8)
+
+__device__ __forceinline__ double quad_get(double v, int qb, int k) {
+  return __shfl_sync(0xffffffffu, v, qb + k);
+}
+
+// The eq. (18) stencil derivative of A along x (dir 0) or y (dir 1) at (x, y),
+// one code path for both directions (no divergence within a quad).
+__device__ __forceinline__ double D_dir(const double *A, const AGrid &g, int x, int y, int dir) {
+  auto at = [&](int k) {
+    return dir ? A[(size_t)wr(y + k, g.ny) * g.nx + x] : A[(size_t)y * g.nx + wr(x + k, g.nx)];
+  };
+  return 0.8 * (at(1) - at(-1)) - 0.2 * (at(2) - at(-2)) + (4.0 / 105.0) * (at(3) - at(-3)) -
+         (1.0 / 280.0) * (at(4) - at(-4));
 }
 
 // Objective pass 1, over V0: Gamma_ij = dJ/dG_ij = -2 c nu rho S_ij
 // (c = weight / L^2); explicit dJ/dtau part -c rho Q / 3 (d nu / d tau = 1/3).
+// Four lanes per cell (FOR_QUADS): d/dx u, d/dy u, d/dx v, d/dy v.
 __global__ void k_obj_gamma(AGrid g, double *F, double cw, int bx, int by, int L,
                             double *partials, int add) {
   double acc[1] = {0.0};
   const size_t N = (size_t)g.nx * g.ny;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
+  const int nc = L * L;
+  FOR_QUADS(nc) {
+    const int iq = i0 + (lane >> 2), i = iq < nc ? iq : nc - 1;
     const int x = wrapi(bx + i % L, g.nx), y = wrapi(by + i / L, g.ny);
     const size_t c = (size_t)y * g.nx + x;
-    const double *U = F + A_U * N, *V = F + A_V * N;
-    const double dxu = Dx(U, g, x, y), dyu = Dy(U, g, x, y);
-    const double dxv = Dx(V, g, x, y), dyv = Dy(V, g, x, y);
-    const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
-    const double Q = sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv;
-    const double r = F[A_RHO * N + c];
-    F[GAM_XX * N + c] = -2.0 * cw * g.nu * r * sxx;
-    F[GAM_XY * N + c] = -2.0 * cw * g.nu * r * sxy;
-    F[GAM_YY * N + c] = -2.0 * cw * g.nu * r * syy;
-    F[D_RHO * N + c] = -cw * g.nu * Q;
-    acc[0] += -cw * r * Q / 3.0;
+    const double d = D_dir(F + (p < 2 ? A_U : A_V) * N, g, x, y, p & 1);
+    const double dxu = quad_get(d, qb, 0), dyu = quad_get(d, qb, 1);
+    const double dxv = quad_get(d, qb, 2), dyv = quad_get(d, qb, 3);
+    if (iq < nc) {
+      const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
+      const double r = F[A_RHO * N + c];
+      if (p < 3) {  // Gamma_xx, Gamma_xy, Gamma_yy: one per lane
+        const double sp = p == 0 ? sxx : (p == 1 ? sxy : syy);
+        F[(GAM_XX + p) * N + c] = -2.0 * cw * g.nu * r * sp;
+      } else {
+        const double Q = sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv;
+        F[D_RHO * N + c] = -cw * g.nu * Q;
+        acc[0] += -cw * r * Q / 3.0;
+      }
+    }
   }
   block_sums<1>(acc, partials + blockIdx.x, add);
 }
 
-// Gamma_ij at (x, y), zero outside V0.
-__device__ __forceinline__ double gam(const double *G, const AGrid &g, int x, int y, int bx,
-                                      int by, int L) {
-  return in_box(x, y, bx, by, L, g) ? G[(size_t)y * g.nx + x] : 0.0;
-}
-
 // Objective pass 2, over R: dJ/du_i = -sum_j D_j Gamma_ij (D^T = -D), then
 // dJ/drho (with the direct part of V0), dJ/dj and the explicit dJ/dF0 part
-// through u = ((1 - alpha/2) j + F_ext/2)/rho.
+// through u = ((1 - alpha/2) j + F_ext/2)/rho.  Four lanes per cell
+// (FOR_QUADS): D_x Gamma_xx, D_y Gamma_xy, D_x Gamma_xy, D_y Gamma_yy, Gamma
+// zero outside V0; then one quotient per lane (dJ/djx, dJ/djy, the velocity
+// part of dJ/drho, the dJ/dF0 term) and the force direction s from the
+// sine tables at F[S_TAB].
 __global__ void k_obj_velocity_adjoint(AGrid g, Region R, double *F, int bx, int by, int L,
                                        double *partials, int add) {
   double acc[1] = {0.0};
-  FOR_REGION(R) {
+  const size_t N = (size_t)g.nx * g.ny;
+  const int nc = R.w * R.h;
+  FOR_QUADS(nc) {
+    const int iq = i0 + (lane >> 2), i = iq < nc ? iq : nc - 1;
     const int x = wrapi(R.x0 + i % R.w, g.nx), y = wrapi(R.y0 + i / R.w, g.ny);
     const size_t c = (size_t)y * g.nx + x;
-    const double *Gxx = F + GAM_XX * N, *Gxy = F + GAM_XY * N, *Gyy = F + GAM_YY * N;
-    auto dxg = [&](const double *G) {
-      return 0.8 * (gam(G, g, wr(x + 1, g.nx), y, bx, by, L) - gam(G, g, wr(x - 1, g.nx), y, bx, by, L)) -
-             0.2 * (gam(G, g, wr(x + 2, g.nx), y, bx, by, L) - gam(G, g, wr(x - 2, g.nx), y, bx, by, L)) +
-             (4.0 / 105.0) * (gam(G, g, wr(x + 3, g.nx), y, bx, by, L) - gam(G, g, wr(x - 3, g.nx), y, bx, by, L)) -
-             (1.0 / 280.0) * (gam(G, g, wr(x + 4, g.nx), y, bx, by, L) - gam(G, g, wr(x - 4, g.nx), y, bx, by, L));
+    // box-relative coordinates: the stencil point k along dir is in V0 when
+    // its along coordinate wraps into [0, L) and the cross one already is
+    const int rx = wrapi(x - bx, g.nx), ry = wrapi(y - by, g.ny);
+    const int dir = p & 1;
+    const double *G = F + (p == 0 ? GAM_XX : (p == 3 ? GAM_YY : GAM_XY)) * N;
+    const int ra = dir ? ry : rx, na = dir ? g.ny : g.nx;
+    const bool cross_in = (dir ? rx : ry) < L;
+    auto at = [&](int k) {
+      const int t = wr(ra + k, na);
+      const size_t e = dir ? (size_t)wr(y + k, g.ny) * g.nx + x : (size_t)y * g.nx + wr(x + k, g.nx);
+      return (cross_in && t < L) ? G[e] : 0.0;
     };
-    auto dyg = [&](const double *G) {
-      return 0.8 * (gam(G, g, x, wr(y + 1, g.ny), bx, by, L) - gam(G, g, x, wr(y - 1, g.ny), bx, by, L)) -
-             0.2 * (gam(G, g, x, wr(y + 2, g.ny), bx, by, L) - gam(G, g, x, wr(y - 2, g.ny), bx, by, L)) +
-             (4.0 / 105.0) * (gam(G, g, x, wr(y + 3, g.ny), bx, by, L) - gam(G, g, x, wr(y - 3, g.ny), bx, by, L)) -
-             (1.0 / 280.0) * (gam(G, g, x, wr(y + 4, g.ny), bx, by, L) - gam(G, g, x, wr(y - 4, g.ny), bx, by, L));
-    };
-    const double Ux = -(dxg(Gxx) + dyg(Gxy));
-    const double Uy = -(dxg(Gxy) + dyg(Gyy));
-    const double r = F[A_RHO * N + c], u = F[A_U * N + c], v = F[A_V * N + c];
-    const double direct = in_box(x, y, bx, by, L, g) ? F[D_RHO * N + c] : 0.0;
-    F[D_JX * N + c] = Ux * (1.0 - 0.5 * g.alpha) / r;
-    F[D_JY * N + c] = Uy * (1.0 - 0.5 * g.alpha) / r;
-    F[D_TOT * N + c] = direct - (Ux * u + Uy * v) / r;
-    double sx, sy;
-    force_dir(g, x, y, sx, sy);
-    acc[0] += (Ux * sx + Uy * sy) / (2.0 * r);
+    const double d = 0.8 * (at(1) - at(-1)) - 0.2 * (at(2) - at(-2)) +
+                     (4.0 / 105.0) * (at(3) - at(-3)) - (1.0 / 280.0) * (at(4) - at(-4));
+    const double Ux = -(quad_get(d, qb, 0) + quad_get(d, qb, 1));
+    const double Uy = -(quad_get(d, qb, 2) + quad_get(d, qb, 3));
+    const double r = F[A_RHO * N + c];
+    double num;
+    if (p == 0) {
+      num = Ux * (1.0 - 0.5 * g.alpha);
+    } else if (p == 1) {
+      num = Uy * (1.0 - 0.5 * g.alpha);
+    } else if (p == 2) {
+      num = Ux * F[A_U * N + c] + Uy * F[A_V * N + c];
+    } else {
+      num = Ux * F[S_TAB * N + y] + Uy * F[S_TAB * N + g.ny + x];
+    }
+    const double q = num / (p == 3 ? 2.0 * r : r);
+    if (iq < nc) {
+      if (p < 2) {
+        F[(D_JX + p) * N + c] = q;
+      } else if (p == 2) {
+        const double direct = (rx < L && ry < L) ? F[D_RHO * N + c] : 0.0;
+        F[D_TOT * N + c] = direct - q;
+      } else {
+        acc[0] += q;
+      }
+    }
   }
   block_sums<1>(acc, partials + blockIdx.x, add);
 }
@@ -353,101 +377,119 @@ __global__ void __launch_bounds__(256) k_adjoint_final(const double *p_step, int
   }
 }
 
-// Forward objective on (rho, j): acc += weight / L^2 * sum_box eps.
-__global__ void k_obj_forward(AGrid g, const double *F, double cw, int bx, int by, int L,
-                              double *partials) {
-  double acc[1] = {0.0};
-  const size_t nbox = (size_t)L * L;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nbox;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int x = wrapi(bx + (int)(i % L), g.nx), y = wrapi(by + (int)(i / L), g.ny);
-    const size_t N = (size_t)g.nx * g.ny, c = (size_t)y * g.nx + x;
-    const double *U = F + A_U * N, *V = F + A_V * N;
-    const double dxu = Dx(U, g, x, y), dyu = Dy(U, g, x, y);
-    const double dxv = Dx(V, g, x, y), dyv = Dy(V, g, x, y);
-    const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
-    acc[0] += -g.nu * F[A_RHO * N + c] * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
-  }
-  block_sums<1>(acc, partials + blockIdx.x);
-}
-
-__global__ void __launch_bounds__(256) k_obj_forward_final(const double *partials, int nb,
-                                                           double cw, double *acc) {
-  __shared__ double sa[256];
-  const int t = threadIdx.x;
-  double a = 0.0;
-  for (int i = t; i < nb; i += 256) a += partials[i];
-  sa[t] = a;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (t < w) sa[t] += sa[t + w];
-    __syncthreads();
-  }
-  if (t == 0) *acc += cw * sa[0];
-}
-
-// The forward objective in one launch of one CTA when the region R (the
-// box and the 4 cells of the eq. (18) stencil around it) has at most
-// kObjFusedCells cells: (rho, j) of R from the storage state `state` (the
-// snapshot's arithmetic), u = (j + F/2)/rho into shared memory, the box's
-// dissipation terms summed per thread, per warp and over the warps in a
-// fixed order, acc += cw * sum (the sum of k_obj_forward + k_obj_forward_final).
-constexpr int kObjFusedCells = 1600;  // a 40 x 40 region: boxes up to 32 x 32
-constexpr int kObjFusedThreads = 512;
-template <typename T>
-__global__ void __launch_bounds__(kObjFusedThreads)
-    k_obj_fused(const Member *__restrict__ members, int member, int state, AGrid g, Region R,
-                int bx, int by, int L, double cw, double *acc) {
-  __shared__ double sr[kObjFusedCells], su[kObjFusedCells], sv[kObjFusedCells];
-  __shared__ double sw[kObjFusedThreads / 32];
+// The forward objective in one launch of many CTAs.  The box is cut into
+// TB x TB tiles; for each of its tiles a CTA computes rho and u = (j +
+// F/2)/rho from the storage state `state` (the snapshot's moment arithmetic)
+// on the tile widened by the 4-cell reach of the eq. (18) stencils (cells of
+// the overlaps computed once per tile that needs them), keeps them in shared
+// memory and sums the dissipation terms of the tile's box cells.  Each CTA
+// writes one partial; the last CTA to finish (the arrival counter `count`,
+// zero before the launch and reset by that CTA) sums the partials in a fixed
+// order and adds cw times the sum to acc.  Small tiles for small boxes, a
+// thread per cell of the widened tile and four lanes per box cell: the FP64
+// work spreads over more SMs and its dependent chains stay short (GB300
+// issues about 1.7 FP64 FMAs per clock per SM).
+template <typename T, int TB, int NT>
+__global__ void __launch_bounds__(NT)
+    k_obj_tiles(const Member *__restrict__ members, int member, int state, AGrid g, int bx,
+                int by, int L, double cw, double *partials, unsigned *count, double *acc) {
+  constexpr int W = TB + 8, NC = W * W;
+  __shared__ double sr[NC], su[NC], sv[NC];
+  __shared__ double sw[NT / 32];
+  __shared__ int is_last;
   const Member &M = members[member];
   const T *src = static_cast<const T *>(state_buffer(M, state));
-  const int tid = threadIdx.x, ncell = R.w * R.h;
-  for (int i = tid; i < ncell; i += kObjFusedThreads) {
-    const int x = wrapi(R.x0 + i % R.w, g.nx), y = wrapi(R.y0 + i / R.w, g.ny);
-    T f[kQ];
-#pragma unroll
-    for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
-    double r, jx, jy;
-    pub_moments<T>(f, M.rho0, r, jx, jy);
-    const double Fx = g.fxt[y] - g.alpha * jx, Fy = g.fyt[x] - g.alpha * jy;
-    sr[i] = r;
-    su[i] = (jx + 0.5 * Fx) / r;
-    sv[i] = (jy + 0.5 * Fy) / r;
-  }
-  __syncthreads();
-  // index in R of the grid cell (x + dx, y + dy): R holds every cell the
-  // stencil of a box cell reaches (the whole axis where it wraps onto itself)
-  auto at = [&](const double *A, int x, int y) {
-    return A[wrapi(y - R.y0, g.ny) * R.w + wrapi(x - R.x0, g.nx)];
-  };
-  auto dx = [&](const double *A, int x, int y) {
-    return 0.8 * (at(A, x + 1, y) - at(A, x - 1, y)) - 0.2 * (at(A, x + 2, y) - at(A, x - 2, y)) +
-           (4.0 / 105.0) * (at(A, x + 3, y) - at(A, x - 3, y)) -
-           (1.0 / 280.0) * (at(A, x + 4, y) - at(A, x - 4, y));
-  };
-  auto dy = [&](const double *A, int x, int y) {
-    return 0.8 * (at(A, x, y + 1) - at(A, x, y - 1)) - 0.2 * (at(A, x, y + 2) - at(A, x, y - 2)) +
-           (4.0 / 105.0) * (at(A, x, y + 3) - at(A, x, y - 3)) -
-           (1.0 / 280.0) * (at(A, x, y + 4) - at(A, x, y - 4));
-  };
+  const int tid = threadIdx.x, ntx = (L + TB - 1) / TB, nt = ntx * ntx;
   double a = 0.0;
-  for (int i = tid; i < L * L; i += kObjFusedThreads) {
-    const int x = wrapi(bx + i % L, g.nx), y = wrapi(by + i / L, g.ny);
-    const double dxu = dx(su, x, y), dyu = dy(su, x, y);
-    const double dxv = dx(sv, x, y), dyv = dy(sv, x, y);
-    const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
-    a += -g.nu * at(sr, x, y) * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int ox = (t % ntx) * TB, oy = (t / ntx) * TB;  // tile origin within the box
+    __syncthreads();  // the previous tile's reads of shared memory are done
+    for (int i = tid; i < NC; i += NT) {
+      const int x = wrapi(bx + ox - 4 + i % W, g.nx), y = wrapi(by + oy - 4 + i / W, g.ny);
+      T f[kQ];
+#pragma unroll
+      for (int l = 0; l < kQ; ++l) f[l] = src[pub_index(M, state, l, x, y)];
+      double r, jx, jy;
+      pub_moments<T>(f, M.rho0, r, jx, jy);
+      const double Fx = g.fxt[y] - g.alpha * jx, Fy = g.fyt[x] - g.alpha * jy;
+      const double ir = 1.0 / r;
+      sr[i] = r;
+      su[i] = (jx + 0.5 * Fx) * ir;
+      sv[i] = (jy + 0.5 * Fy) * ir;
+    }
+    __syncthreads();
+    // the tile's box cells, four lanes per cell (d/dx u, d/dy u, d/dx v,
+    // d/dy v), whole warps per pass so that every shuffle has the full warp
+    const int lane = tid & 31, p = lane & 3, qb = lane & ~3;
+    for (int i0 = (tid >> 5) * 8; i0 < TB * TB; i0 += (NT / 32) * 8) {
+      const int iq = i0 + (lane >> 2), i = iq < TB * TB ? iq : TB * TB - 1;
+      const int lx = i % TB, ly = i / TB;
+      const int c = (ly + 4) * W + lx + 4, s = (p & 1) ? W : 1;
+      const double *A = p < 2 ? su : sv;
+      const double d = 0.8 * (A[c + s] - A[c - s]) - 0.2 * (A[c + 2 * s] - A[c - 2 * s]) +
+                       (4.0 / 105.0) * (A[c + 3 * s] - A[c - 3 * s]) -
+                       (1.0 / 280.0) * (A[c + 4 * s] - A[c - 4 * s]);
+      const double dxu = __shfl_sync(0xffffffffu, d, qb), dyu = __shfl_sync(0xffffffffu, d, qb + 1);
+      const double dxv = __shfl_sync(0xffffffffu, d, qb + 2), dyv = __shfl_sync(0xffffffffu, d, qb + 3);
+      if (p == 0 && iq < TB * TB && ox + lx < L && oy + ly < L) {
+        const double sxx = 2 * dxu, sxy = dyu + dxv, syy = 2 * dyv;
+        a += -g.nu * sr[c] * (sxx * dxu + sxy * dyu + sxy * dxv + syy * dyv);
+      }
+    }
   }
+  // the CTA's partial: shuffle tree per warp, warps in order
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
   if ((tid & 31) == 0) sw[tid >> 5] = a;
   __syncthreads();
   if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kObjFusedThreads / 32; ++w) t += sw[w];
-    *acc += cw * t;
+    double p = 0.0;
+    for (int w = 0; w < NT / 32; ++w) p += sw[w];
+    partials[blockIdx.x] = p;
+    __threadfence();
+    is_last = atomicAdd(count, 1u) == gridDim.x - 1;
   }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // last CTA: strided fixed-order chains, the same tree
+  double b = 0.0;
+  for (int k = tid; k < (int)gridDim.x; k += NT) b += __ldcg(partials + k);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+  __syncthreads();
+  if ((tid & 31) == 0) sw[tid >> 5] = b;
+  __syncthreads();
+  if (tid == 0) {
+    double p = 0.0;
+    for (int w = 0; w < NT / 32; ++w) p += sw[w];
+    *acc += cw * p;
+    *count = 0u;
+  }
+}
+
+template <typename T>
+cudaError_t launch_obj_tiles(const Member *d_members, int member, int state, const AGrid &g,
+                             int bx, int by, int L, double cw, double *partials,
+                             unsigned *count, double *acc, cudaStream_t s) {
+  // the largest tile that still gives a CTA to every SM, 4 x 4 at least;
+  // a thread per cell of the widened tile ((TB + 8)^2 rounded up to warps)
+  // for the latency-bound small tiles, 256 threads for 16 x 16 tiles, whose
+  // many CTAs keep the FP64 pipes busy (L = 256 on 256^2: 28.8 us against
+  // 30.8 with 576 threads)
+  auto tiles = [&](int tb) { return (long long)((L + tb - 1) / tb) * ((L + tb - 1) / tb); };
+  const int tb = tiles(16) >= 152 ? 16 : tiles(8) >= 152 ? 8 : 4;
+  const int grid = (int)std::min<long long>(tiles(tb), kMaxPartialBlocks);
+  if (tb == 16)
+    k_obj_tiles<T, 16, 256><<<grid, 256, 0, s>>>(d_members, member, state, g, bx, by, L, cw,
+                                                 partials, count, acc);
+  else if (tb == 8)
+    k_obj_tiles<T, 8, 256><<<grid, 256, 0, s>>>(d_members, member, state, g, bx, by, L, cw,
+                                                partials, count, acc);
+  else
+    k_obj_tiles<T, 4, 160><<<grid, 160, 0, s>>>(d_members, member, state, g, bx, by, L, cw,
+                                                partials, count, acc);
+  return cudaGetLastError();
 }
 
 AGrid agrid(const Member &hm) {
@@ -499,15 +541,16 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
   const int with_obj = w != 0.0;
   const Region R = objective_region(hm.nx, hm.ny, bx, by, L);
   int nbo = 0, nbr = 0;
+  k_sine_tables<<<(hm.nx + hm.ny + 255) / 256, 256, 0, s>>>(g, F + S_TAB * N);
   if (with_obj) {
     const double cw = w / ((double)L * (double)L);
-    nbr = nblocks_for((size_t)R.w * R.h, kObjThreads);
-    nbo = nblocks_for((size_t)L * L, kObjThreads);
-    k_region_velocity<<<nbr, kObjThreads, 0, s>>>(g, R, f_n, F);
+    const size_t nreg = (size_t)R.w * R.h;
+    nbr = nblocks_for(4 * nreg, kObjThreads);  // four lanes per cell
+    nbo = nblocks_for(4 * (size_t)L * L, kObjThreads);
+    k_region_velocity<<<nblocks_for(nreg, kObjThreads), kObjThreads, 0, s>>>(g, R, f_n, F);
     k_obj_gamma<<<nbo, kObjThreads, 0, s>>>(g, F, cw, bx, by, L, p_tau, 0);
     k_obj_velocity_adjoint<<<nbr, kObjThreads, 0, s>>>(g, R, F, bx, by, L, p_F0, 0);
   }
-  k_sine_tables<<<(hm.nx + hm.ny + 255) / 256, 256, 0, s>>>(g, F + S_TAB * N);
   k_adjoint<<<nb, tpb, 0, s>>>(g, R, f_n, lam_in, lam_out, F, with_obj, p_step, 0);
   k_adjoint_final<<<1, 256, 0, s>>>(p_step, nb, p_tau, nbo, p_F0, nbr, with_obj, dJ_dtau,
                                     dJ_dF0);
@@ -539,8 +582,10 @@ cudaError_t adjoint_sweep(const Member &hm, const double *states, int nstates,
   int any_obj = 0;
   for (int k = 0; k < nstates; ++k) any_obj |= weights[k] != 0.0;
   const Region R = objective_region(hm.nx, hm.ny, bx, by, L);
-  const int nbr = any_obj ? nblocks_for((size_t)R.w * R.h, kObjThreads) : 0;
-  const int nbo = any_obj ? nblocks_for((size_t)L * L, kObjThreads) : 0;
+  const size_t nreg = (size_t)R.w * R.h;
+  const int nbv = nblocks_for(nreg, kObjThreads);
+  const int nbr = any_obj ? nblocks_for(4 * nreg, kObjThreads) : 0;  // four lanes per cell
+  const int nbo = any_obj ? nblocks_for(4 * (size_t)L * L, kObjThreads) : 0;
   cudaError_t e = cudaMemsetAsync(p_step, 0, sizeof(double) * 4 * kMaxPartialBlocks, s);
   if (e != cudaSuccess) return e;
   k_sine_tables<<<(hm.nx + hm.ny + 255) / 256, 256, 0, s>>>(g, F + S_TAB * N);
@@ -552,7 +597,7 @@ cudaError_t adjoint_sweep(const Member &hm, const double *states, int nstates,
     const int with_obj = weights[k] != 0.0;
     if (with_obj) {
       const double cw = weights[k] / ((double)L * (double)L);
-      k_region_velocity<<<nbr, kObjThreads, 0, s>>>(g, R, f_k, F);
+      k_region_velocity<<<nbv, kObjThreads, 0, s>>>(g, R, f_k, F);
       k_obj_gamma<<<nbo, kObjThreads, 0, s>>>(g, F, cw, bx, by, L, p_tau, 1);
       k_obj_velocity_adjoint<<<nbr, kObjThreads, 0, s>>>(g, R, F, bx, by, L, p_F0, 1);
       n += 3;
@@ -566,36 +611,17 @@ cudaError_t adjoint_sweep(const Member &hm, const double *states, int nstates,
   return cudaGetLastError();
 }
 
-// Forward objective of the state in storage `state` in one single-CTA
-// launch when the box's region is small (returns cudaErrorNotSupported
-// otherwise, launching nothing).
-cudaError_t objective_fused(int precision, const Member *d_members, int member,
+// Forward objective of the state in storage `state`: one launch.
+cudaError_t objective_tiles(int precision, const Member *d_members, int member,
                             const Member &hm, int state, double w, int bx, int by, int L,
-                            double *acc, cudaStream_t s) {
-  const Region R = objective_region(hm.nx, hm.ny, bx, by, L);
-  if ((long long)R.w * R.h > kObjFusedCells) return cudaErrorNotSupported;
+                            double *acc, const DiagScratch &sc, cudaStream_t s) {
   const AGrid g = agrid(hm);
   const double cw = w / ((double)L * (double)L);
   if (precision == 32)
-    k_obj_fused<float><<<1, kObjFusedThreads, 0, s>>>(d_members, member, state, g, R, bx, by, L,
-                                                      cw, acc);
-  else
-    k_obj_fused<double><<<1, kObjFusedThreads, 0, s>>>(d_members, member, state, g, R, bx, by,
-                                                       L, cw, acc);
-  return cudaGetLastError();
-}
-
-// Forward objective from the (rho, j) snapshot already written to sc.f[0..2].
-cudaError_t objective_from_snapshot(const Member &hm, double w, int bx, int by, int L,
-                                    double *acc, const DiagScratch &sc, cudaStream_t s) {
-  const AGrid g = agrid(hm);
-  const size_t N = (size_t)hm.nx * hm.ny;
-  double *F = sc.f;
-  k_velocity<<<nblocks_for(N), 256, 0, s>>>(g, F);
-  const int nb = nblocks_for((size_t)L * L);
-  k_obj_forward<<<nb, 256, 0, s>>>(g, F, 0.0, bx, by, L, sc.partials);
-  k_obj_forward_final<<<1, 256, 0, s>>>(sc.partials, nb, w / ((double)L * (double)L), acc);
-  return cudaGetLastError();
+    return launch_obj_tiles<float>(d_members, member, state, g, bx, by, L, cw, sc.partials,
+                                   sc.count, acc, s);
+  return launch_obj_tiles<double>(d_members, member, state, g, bx, by, L, cw, sc.partials,
+                                  sc.count, acc, s);
 }
 
 }  // namespace lbm

@@ -35,7 +35,7 @@ struct Layout {
   std::vector<size_t> pop0, pop1, fx, fy, fx64, fy64, snap;
   std::vector<size_t> ft, ft64, trig, trig64, damp, damp_f, damp_ring, proj, drows, pcount;
   std::vector<size_t> nu_ring;  // variable viscosity: local viscosity per snapshot slot
-  size_t scratch, partials, jpart, jobs, stats, Ls, out7, origins;
+  size_t scratch, partials, count, jpart, jobs, stats, Ls, out7, origins;
   size_t edges, hist, mach;  // distributions: bin edges, histograms, Ma_V statistics
   int diag_slots;          // members per batched diagnostic launch
   size_t slot_doubles, jpart_doubles;
@@ -214,6 +214,7 @@ Layout make_layout(const lbm_config *cfg) {
   L.diag_slots = (int)std::min<size_t>(slots, (size_t)n);
   L.scratch = take(8 * L.slot_doubles * L.diag_slots);
   L.partials = take(8 * (size_t)lbm::kGeneralPartials);
+  L.count = take(sizeof(unsigned));
   L.jpart = take(8 * L.jpart_doubles * L.diag_slots);
   L.jobs = take(sizeof(lbm::DiagJob) * n);
   L.stats = take(8 * (size_t)n * kMaxL * 30);
@@ -609,6 +610,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
   h->sc.f = reinterpret_cast<double *>(ws_at(h, lay.scratch));
   h->sc.N = lay.Nmax;
   h->sc.partials = reinterpret_cast<double *>(ws_at(h, lay.partials));
+  h->sc.count = reinterpret_cast<unsigned *>(ws_at(h, lay.count));
   h->sc.slots = lay.diag_slots;
   h->sc.slot_doubles = lay.slot_doubles;
   h->sc.jpart = reinterpret_cast<double *>(ws_at(h, lay.jpart));
@@ -724,6 +726,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
   cudaError_t e = cudaMemcpyAsync(h->d_members, h->hm.data(), sizeof(Member) * h->hm.size(),
                                   cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws_at(h, lay.status), 0, sizeof(int) * cfg->n_members, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->sc.count, 0, sizeof(unsigned), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess)
     return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
@@ -1370,17 +1373,9 @@ int lbm_objective_accumulate(lbm_handle *h, int member, double weight, int bx, i
   if (L < 1 || L > c.nx || L > c.ny || bx < 0 || bx >= c.nx || by < 0 || by >= c.ny)
     return fail(h, LBM_ERR_ARG, "objective box outside the grid");
   if ((rc = wait_diag(h))) return rc;
-  const cudaError_t e = lbm::objective_fused(h->precision, h->d_members, member, h->hm[member],
-                                             h->cur, weight, bx, by, L, acc, h->stream);
-  if (e == cudaSuccess) {  // small box: one launch
-    h->launches += 1;
-    return LBM_OK;
-  }
-  if (e != cudaErrorNotSupported) CK(e);
-  CK(lbm::launch_snapshot(h->precision, h->d_members, member, c.nx, c.ny, h->cur, h->sc.f,
-                          h->stream));
-  CK(lbm::objective_from_snapshot(h->hm[member], weight, bx, by, L, acc, h->sc, h->stream));
-  h->launches += 4;
+  CK(lbm::objective_tiles(h->precision, h->d_members, member, h->hm[member], h->cur, weight, bx,
+                          by, L, acc, h->sc, h->stream));
+  h->launches += 1;
   return LBM_OK;
 }
 

@@ -279,6 +279,7 @@ struct DiagScratch {
   double *f;          // slot 0: [nfields][N] field scratch (also general staging)
   size_t N;           // cells of the largest member
   double *partials;   // general reduction partials (kGeneralPartials doubles)
+  unsigned *count;    // arrival counter of last-CTA reductions (zero between launches)
   int slots;          // members one batched diagnostic launch covers
   size_t slot_doubles;   // stride of the field slots (slot j at f + j * slot_doubles)
   double *jpart;      // per-slot partials (slot j at jpart + j * jpart_doubles)
@@ -352,15 +353,11 @@ cudaError_t adjoint_step(const Member &hm, const double *f_n, const double *lam_
                          double *lam_out, double w, int bx, int by, int L,
                          double *dJ_dtau, double *dJ_dF0, const DiagScratch &sc,
                          cudaStream_t s);
-cudaError_t objective_from_snapshot(const Member &hm, double w, int bx, int by, int L,
-                                    double *acc, const DiagScratch &sc, cudaStream_t s);
 // The forward objective of the state in storage `state` (acc += w times the
-// box average of the dissipation term) in one single-CTA launch, for boxes
-// whose region (the box widened by the 4-cell stencil reach) has at most
-// 1600 cells; cudaErrorNotSupported (nothing launched) for larger ones.
-cudaError_t objective_fused(int precision, const Member *d_members, int member,
+// box average of the dissipation term) in one launch (lbm_adjoint.cu).
+cudaError_t objective_tiles(int precision, const Member *d_members, int member,
                             const Member &hm, int state, double w, int bx, int by, int L,
-                            double *acc, cudaStream_t s);
+                            double *acc, const DiagScratch &sc, cudaStream_t s);
 int adjoint_kernel_count(double w);
 // The adjoint steps of a recorded interval, last state first, with one
 // gradient reduction per call (weights: host array of nstates).

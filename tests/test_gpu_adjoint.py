@@ -143,17 +143,21 @@ def _small_spec(precision=64):
 
 
 @pytest.mark.parametrize("n,box,L,precision,tol", [
-    (32, (5, 3), 8, 64, 1e-12),     # region 16 x 16: the single-CTA objective
-    (32, (29, 30), 8, 64, 1e-12),   # the same, box wrapping around both edges
-    (48, (3, 40), 32, 64, 1e-12),   # region 40 x 40 = 1600 cells, the largest fused
-    (48, (10, 2), 34, 64, 1e-12),   # region 42 x 42 > 1600: snapshot + 3 kernels
-    (32, (5, 3), 8, 32, 1e-5),      # FP32 populations, single CTA
-    (48, (10, 2), 34, 32, 1e-5)])   # FP32, snapshot path
+    (32, (5, 3), 8, 64, 1e-12),       # 4 x 4 tiles: 2 x 2 CTAs
+    (32, (29, 30), 8, 64, 1e-12),     # the same, box wrapping around both edges
+    (48, (3, 40), 30, 64, 1e-12),     # ragged last tiles (30 = 7 x 4 + 2)
+    (48, (10, 2), 45, 64, 1e-12),     # the stencil reach wraps onto the box itself
+    (128, (100, 7), 101, 64, 1e-12),  # 8 x 8 tiles (13 x 13 CTAs), ragged, wrapping
+    (200, (150, 190), 197, 64, 1e-12),  # 16 x 16 tiles (13 x 13 CTAs), ragged, wrapping
+    (520, (7, 500), 515, 64, 1e-12),  # 33 x 33 tiles on 1024 CTAs (a CTA does two)
+    (32, (5, 3), 8, 32, 1e-5),        # FP32 populations
+    (200, (150, 190), 197, 32, 1e-5)])  # FP32, 16 x 16 tiles
 def test_objective_forward_matches_oracle(P, orc, n, box, L, precision, tol):
-    """J over n in [20, 44] against the oracle's objective, for boxes whose
-    region (the box widened by the stencil reach) fits one CTA's shared
-    memory and for larger ones (the two paths of lbm_objective_accumulate).
-    FP32 populations: the storage rounding of a 44-step trajectory."""
+    """J over n in [20, 44] against the oracle's objective: every tile size
+    of the one-launch objective (4, 8, 16), ragged last tiles, boxes across
+    the periodic edges, a stencil reach that wraps onto the box, more tiles
+    than CTAs.  FP32 populations: the storage rounding of a 44-step
+    trajectory."""
     import dataclasses
     import torch
     from paper_1809_06735_gb300.adjoint import forward_objective
@@ -170,9 +174,8 @@ def test_objective_forward_matches_oracle(P, orc, n, box, L, precision, tol):
 def test_gradients_match_oracle_finite_differences(P, orc, box, L):
     """dJ/dtau (h = 1e-6), dJ/dF0 (1e-3 relative step, Richardson) and a
     directional derivative in f0 against central differences of the FP64
-    oracle objective; a box whose region (box plus stencil reach) fits the
-    single-CTA forward objective (8 x 8) and one that does not (24 x 24 on
-    32^2: the region is the whole grid)."""
+    oracle objective; an 8 x 8 box and a 24 x 24 box on 32^2 (its stencil
+    reach wraps onto the box: the adjoint's region is the whole grid)."""
     import dataclasses
     import torch
     from paper_1809_06735_gb300.adjoint import box_dissipation
