@@ -93,12 +93,11 @@ __device__ __forceinline__ void moments_f64(const double f[kQ], double &rho, dou
 // ---------------------------------------------------------------------------
 
 // phi(z) = (1 + z) ln(1 + z) - z: series where the terms cancel.
-// ln(1 + z) and exp(x) - 1 for the FP32 entropic collision, whose
-// arguments are mostly small (relative populations' departures, velocity
-// factors): their Taylor series in Horner form where |z| < 1/8 (the terms
-// after z^9 / 9 are below 1e-10 of |z|, under the FP32 rounding) and
-// |x| < 1/4 (after x^9 / 9!: below 1e-12), the library functions elsewhere.
-// FP64 keeps the library functions.
+// ln(1 + z) for the FP32 entropic collision, whose arguments are mostly
+// small (relative populations' departures): its Taylor series in Horner
+// form where |z| < 1/8 (the terms after z^9 / 9 are below 1e-10 of |z|,
+// under the FP32 rounding), the library function elsewhere.  FP64 keeps the
+// library functions.
 __device__ __forceinline__ float ln1p_series(float z) {
   float p = 1.0f / 9.0f;
   p = fmaf(-z, p, 1.0f / 8.0f);
@@ -111,18 +110,6 @@ __device__ __forceinline__ float ln1p_series(float z) {
   p = fmaf(-z, p, 1.0f);
   return z * p;
 }
-__device__ __forceinline__ float em1_series(float x) {
-  float p = 1.0f / 362880.0f;
-  p = fmaf(x, p, 1.0f / 40320.0f);
-  p = fmaf(x, p, 1.0f / 5040.0f);
-  p = fmaf(x, p, 1.0f / 720.0f);
-  p = fmaf(x, p, 1.0f / 120.0f);
-  p = fmaf(x, p, 1.0f / 24.0f);
-  p = fmaf(x, p, 1.0f / 6.0f);
-  p = fmaf(x, p, 1.0f / 2.0f);
-  p = fmaf(x, p, 1.0f);
-  return x * p;
-}
 template <typename T>
 __device__ __forceinline__ T ln1p_e(T z) {
   if constexpr (sizeof(T) == 4)
@@ -130,12 +117,16 @@ __device__ __forceinline__ T ln1p_e(T z) {
   else
     return log1p(z);
 }
+
+// a / b for the entropic collision: FP32 with the fast division intrinsic
+// (at most 2 ulp; every denominator here is a population, a density or a
+// sum of order one), FP64 exact.
 template <typename T>
-__device__ __forceinline__ T expm1_e(T x) {
+__device__ __forceinline__ T div_e(T a, T b) {
   if constexpr (sizeof(T) == 4)
-    return fabsf(x) < 0.25f ? em1_series(x) : expm1f(x);
+    return __fdividef(a, b);
   else
-    return expm1(x);
+    return a / b;
 }
 
 template <typename T>
@@ -169,25 +160,35 @@ __device__ __forceinline__ T entropy_gap(const T f[kQ], const T y[kQ], T S2, T a
 
 // The root alpha > 1 (alpha = 2 at equilibrium, for non-positive populations
 // or without a root below min(a_max, 64)).  FP64: bisection to 1e-15 (the
-// oracle's procedure); FP32: Newton from the near-equilibrium series start,
-// g'(a) = sum Delta ln(1 + a y) - S2, kept inside a bisection bracket, until
-// |g| is at the level of its rounding (1e-6 of the terms; then one last
-// Newton step if it stays in the bracket) or a step below 1e-3 a (error of
-// order 1e-6 a after it) -- usually one iteration.
+// oracle's procedure); FP32: the third-order series of the root in the
+// populations' relative departures y when every |y| < 0.02 (error below
+// 1e-7), otherwise Newton from that series, g'(a) = sum Delta ln(1 + a y) -
+// S2, kept inside a bisection bracket, until |g| is at the level of its
+// rounding (1e-6 of the terms; then one last Newton step if it stays in the
+// bracket) or a step below 1e-3 a (error of order 1e-6 a after it).
 template <typename T>
 __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
-  T y[kQ], ymax = T(0), amax = T(64), S2 = T(0);
+  T y[kQ], ymax = T(0), S2 = T(0);
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
     if (!(f[l] > T(0))) return T(2);
-    y[l] = d[l] / f[l];
+    y[l] = div_e<T>(d[l], f[l]);
     ymax = fmax(ymax, fabs(y[l]));
-    if (y[l] < T(0)) amax = fmin(amax, -T(1) / y[l]);
-    S2 += d[l] * ln1p_e<T>(y[l]);
   }
   if (ymax < (sizeof(T) == 4 ? T(1e-7) : T(1e-12))) return T(2);
-  T lo = T(1), hi = amax * (sizeof(T) == 4 ? T(1 - 1e-6) : T(1 - 1e-12));
+  // the bracket (1, a_max): f + a Delta stays positive below a_max
+  auto upper = [&]() {
+    T amax = T(64);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l)
+      if (y[l] < T(0)) amax = fmin(amax, div_e<T>(-T(1), y[l]));
+    return amax * (sizeof(T) == 4 ? T(1 - 1e-6) : T(1 - 1e-12));
+  };
+  T lo = T(1), hi;
   if constexpr (sizeof(T) == 8) {
+    hi = upper();
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) S2 += d[l] * ln1p_e<T>(y[l]);
     if (entropy_gap<T>(f, y, S2, hi) < T(0)) return T(2);
     for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
       const T mid = T(0.5) * (lo + hi);
@@ -198,22 +199,35 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
     }
     return T(0.5) * (lo + hi);
   } else {
-    // Start near the root: the entropy condition g(a) / a = 0 expanded in
-    // powers of y = Delta / f about the BGK value a = 2 (phi(z) = z^2/2 -
-    // z^3/6 + z^4/12 - ..., ln(1 + y) likewise) gives
-    //   a = 2 + (T3 - 2 T4) / (3 T2) + O(y^2),  T_k = sum_l f_l y_l^k,
-    // about y times closer than a = 2; one Newton step from it usually lands
-    // at the FP32 rounding level.  The bracket's upper end is only checked
-    // when that step does not settle.
-    T T2 = T(0), T3 = T(0), T4 = T(0);
+    // The root as a series in y = Delta / f about the BGK value a = 2: with
+    // T_k = sum_l f_l y_l^k (of order y^k), the entropy condition g(a) / a
+    // = sum_{k>=2} (-1)^k T_k (a^(k-1) - k) / (k (k - 1)) = 0 solved order
+    // by order in y gives a = 2 + c1 + c2 + c3 + O(y^4),
+    //   c1 = u / 3, c2 = 4 u^2 / 9 - 2 q4 / 3,
+    //   c3 = 11 q5 / 10 - 14 u q4 / 9 + 17 u^3 / 27,
+    // u = T3 / T2, q4 = T4 / T2, q5 = T5 / T2.  Against the root of the
+    // entropy condition to 40 digits its error is below 1e-7 (under the FP32
+    // rounding of a) while max |y| < 0.02: the series is then the root.
+    // Otherwise it starts Newton's iteration on g.
+    T T2 = T(0), T3 = T(0), T4 = T(0), T5 = T(0);
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
-      const T q = f[l] * y[l] * y[l];
+      T q = f[l] * y[l] * y[l];
       T2 += q;
-      T3 += q * y[l];
-      T4 += q * y[l] * y[l];
+      q *= y[l];
+      T3 += q;
+      q *= y[l];
+      T4 += q;
+      T5 += q * y[l];
     }
-    T a = T(2) + (T3 - T(2) * T4) / (T(3) * T2);
+    const T r2 = div_e<T>(T(1), T2), u = T3 * r2, q4 = T4 * r2, q5 = T5 * r2;
+    T a = T(2) + (u * T(1.0 / 3.0) + (T(4.0 / 9.0) * u * u - T(2.0 / 3.0) * q4 +
+                                      T(1.1) * q5 - T(14.0 / 9.0) * u * q4 +
+                                      T(17.0 / 27.0) * u * u * u));
+    if (ymax < T(0.02)) return a;
+    hi = upper();
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) S2 += d[l] * ln1p_e<T>(y[l]);
     if (!(a > lo && a < hi)) a = fmin(T(2), T(0.5) * (lo + hi));
     bool bracketed = false;
     for (int it = 0; it < 30; ++it) {
@@ -244,7 +258,7 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
         lo = a;
       else
         hi = a;
-      T an = a - g / dg;
+      T an = a - div_e<T>(g, dg);
       const bool inside = an > lo && an < hi;
       if (conv) return inside ? an : a;
       // Newton on the convex g converges quadratically: a step below 1e-3 a
@@ -263,29 +277,55 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
   }
 }
 
-// ln of the entropic equilibrium's velocity factor, per population:
+// ln of the entropic equilibrium's velocity factor, per population (FP64):
 // ln P_l(u) = sum_a [ln(2 - s_a) + c_la ln((2 u_a + s_a) / (1 - u_a))],
 // s_a = sqrt(1 + 3 u_a^2), each logarithm as log1p of a cancellation-free
 // argument (s - 1 = 3 u^2 / (1 + s)).
 template <typename T>
 __device__ __forceinline__ void entropic_logp(T ux, T uy, T lp[kQ]) {
   const T sx = sqrt(T(1) + T(3) * ux * ux), sy = sqrt(T(1) + T(3) * uy * uy);
-  const T qx = T(3) * ux * ux / (T(1) + sx), qy = T(3) * uy * uy / (T(1) + sy);
+  const T qx = div_e<T>(T(3) * ux * ux, T(1) + sx), qy = div_e<T>(T(3) * uy * uy, T(1) + sy);
   const T a0x = ln1p_e<T>(-qx), a0y = ln1p_e<T>(-qy);
-  const T a1x = ln1p_e<T>((T(3) * ux + qx) / (T(1) - ux));
-  const T a1y = ln1p_e<T>((T(3) * uy + qy) / (T(1) - uy));
+  const T a1x = ln1p_e<T>(div_e<T>(T(3) * ux + qx, T(1) - ux));
+  const T a1y = ln1p_e<T>(div_e<T>(T(3) * uy + qy, T(1) - uy));
 #pragma unroll
   for (int l = 0; l < kQ; ++l)
     lp[l] = a0x + a0y + (T)cx_of(l) * a1x + (T)cy_of(l) * a1y;
+}
+
+// P_l(u) - 1 for FP32 from the product form of the same factor,
+// P_l = prod_a (2 - s_a) ((2 u_a + s_a) / (1 - u_a))^(c_la): with
+// q = s - 1 = 3 u^2 / (1 + s), the factor of an axis is 1 + Z_c for
+// c = 0, +1, -1: Z_0 = -q, Z_(+1) = b - q - q b with b = (3 u + q) / (1 - u),
+// Z_(-1) = b' - q - q b' with b' = -(3 u + q) / (1 + 2 u + q), and
+// P - 1 = X + Y + X Y: no logarithm or exponential, no cancellation.
+__device__ __forceinline__ void entropic_em_f32(float ux, float uy, float em[kQ]) {
+  float X[3], Y[3];  // indexed by c + 1
+  auto axis = [](float u, float (&Z)[3]) {
+    const float s = sqrtf(1.0f + 3.0f * u * u);
+    const float q = __fdividef(3.0f * u * u, 1.0f + s);
+    const float n = 3.0f * u + q;
+    const float b = __fdividef(n, 1.0f - u), bm = -__fdividef(n, 1.0f + 2.0f * u + q);
+    Z[0] = fmaf(-q, bm, bm - q);
+    Z[1] = -q;
+    Z[2] = fmaf(-q, b, b - q);
+  };
+  axis(ux, X);
+  axis(uy, Y);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) {
+    const float x = X[cx_of(l) + 1], y = Y[cy_of(l) + 1];
+    em[l] = fmaf(x, y, x + y);
+  }
 }
 
 // One ELBM collision in storage form (FP32: deviations g = f - t rho0, FP64:
 // f); returns alpha.
 template <typename T>
 __device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
-  T rho, jx, jy, drho;
+  T rho, jx, jy, drho, ux, uy;
   if constexpr (sizeof(T) == 4) {
-    float ir, ux, uy;
+    float ir;
     moments_f32(v, rho0, drho, rho, jx, jy, ir, ux, uy);
   } else {
     rho = T(0);
@@ -298,31 +338,40 @@ __device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
       if (cy_of(l) != 0) jy += cy_of(l) * v[l];
     }
     drho = T(0);
+    ux = jx / rho;
+    uy = jy / rho;
   }
-  const T ux = jx / rho, uy = jy / rho;
   const T Fx = Fex - alpha_drag * jx, Fy = Fey - alpha_drag * jy;
-  T lp[kQ], lps[kQ];
-  entropic_logp<T>(ux, uy, lp);
   // without force the shifted velocity is u itself and the EDM term is
-  // exactly zero: its second set of logarithms and exponentials is skipped
+  // exactly zero: its second equilibrium is skipped
   const bool forced = Fx != T(0) || Fy != T(0);
-  if (forced) entropic_logp<T>(ux + Fx / rho, uy + Fy / rho, lps);
   T f[kQ], d[kQ], Fl[kQ];
+  if constexpr (sizeof(T) == 4) {
+    float em[kQ], ems[kQ];  // P_l - 1 at u and at the shifted velocity
+    entropic_em_f32(ux, uy, em);
+    if (forced) entropic_em_f32(ux + div_e<T>(Fx, rho), uy + div_e<T>(Fy, rho), ems);
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) {
-    const T t = (T)w_of(l);
-    const T em = expm1_e<T>(lp[l]);  // P_l - 1
-    if constexpr (sizeof(T) == 4) {
+    for (int l = 0; l < kQ; ++l) {
+      const float t = w_of(l);
       f[l] = t * rho0 + v[l];
-      d[l] = t * (drho * (T(1) + em) + rho0 * em) - v[l];  // f_eq - f, deviation form
-    } else {
+      d[l] = t * (drho * (1.0f + em[l]) + rho0 * em[l]) - v[l];  // f_eq - f, deviation form
+      Fl[l] = forced ? t * rho * (ems[l] - em[l]) : 0.0f;
+    }
+  } else {
+    T lp[kQ], lps[kQ];
+    entropic_logp<T>(ux, uy, lp);
+    if (forced) entropic_logp<T>(ux + div_e<T>(Fx, rho), uy + div_e<T>(Fy, rho), lps);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const T t = (T)w_of(l);
+      const T em = expm1(lp[l]);  // P_l - 1
       f[l] = v[l];
       d[l] = t * rho * (T(1) + em) - v[l];
+      Fl[l] = forced ? t * rho * (T(1) + em) * expm1(lps[l] - lp[l]) : T(0);
     }
-    Fl[l] = forced ? t * rho * (T(1) + em) * expm1_e<T>(lps[l] - lp[l]) : T(0);
   }
   const T a = elbm_alpha<T>(f, d);
-  const T ab = a / (T(2) * tau0);
+  const T ab = div_e<T>(a, T(2) * tau0);
 #pragma unroll
   for (int l = 0; l < kQ; ++l) v[l] = v[l] + ab * d[l] + Fl[l];
   return a;

@@ -91,6 +91,40 @@ def test_collision_trajectories(P, oracle_trajectories, prec, tol, storage):
             assert err < tol, (prec, storage, steps, i, err)
 
 
+@pytest.mark.parametrize("prec,tol", [(64, FP64_TOL), (32, FP32_TOL)])
+def test_elbm_far_from_equilibrium(P, orc, prec, tol):
+    """ELBM steps from a state with half its cells departing from the
+    entropic equilibrium by up to 12% (relative departures y above 0.02: the
+    FP32 root takes Newton's iteration) and half near it (y below 0.01: the
+    root's series alone), one and three steps against the oracle, without
+    and with the force and drag."""
+    nx, ny, tau = 32, 24, 0.52
+    rng = np.random.default_rng(5)
+    f0 = orc.init(*_fields(nx, ny, 11))
+    hit = rng.uniform(size=(1, ny, nx)) < 0.5
+    f0 = f0 * (1.0 + 0.12 * rng.uniform(-1.0, 1.0, size=f0.shape) * hit)
+    cx, cy, _ = orc.lattice()
+    ymax = np.empty((ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            f = f0[:, j, i]
+            rho = f.sum()
+            d = orc.feq_entropic(rho, (cx * f).sum() / rho, (cy * f).sum() / rho) - f
+            ymax[j, i] = np.abs(d / f).max()
+    assert (ymax > 0.03).mean() > 0.3 and (ymax < 0.01).mean() > 0.3
+    for kind, F0, alpha in ((0, 0.0, 0.0), (1, 2e-4, 1e-3)):
+        lat = P.Lattice([P.Member(nx, ny, tau, 1.0, kind, 2, F0, alpha, 0.0, 0.0, 3, 0.0)],
+                        precision=prec)
+        lat.set_populations(0, f0)
+        model = orc.Force(kind, F0, 2, alpha, collision=3)
+        done = 0
+        for steps in (1, 3):
+            lat.step(steps - done)
+            done = steps
+            err = rel_err(lat.get_populations_host(0), orc.run(f0, steps, tau, model))
+            assert err < tol, (prec, kind, steps, err)
+
+
 def test_collision_models_change_the_flow(P, orc):
     """Both models move the state by far more than the parity bar relative to
     BGK (eq. (7) through the compressible part of the strain)."""
