@@ -444,10 +444,10 @@ def forced_tau_trend_leg(P, stream, dev):
 
 def collision_models_leg(P, stream, dev, peak):
     """The variable-viscosity collisions (Sec. 1) on 16 FP32 members of
-    512^2 (tau0 = 0.51): Smagorinsky (Cs = 0.1) and eq. (7) on the extended
-    vectorised kernel, the entropic LBM (its per-cell root finding) on the
-    general kernel.  Every step moves 72 algorithmic bytes per update.
-    Median of five timed 40-step runs."""
+    512^2 (tau0 = 0.51): Smagorinsky (Cs = 0.1), eq. (7) and the entropic
+    LBM (its per-cell root of the entropy condition) on the vectorised
+    kernel.  Every step moves 72 algorithmic bytes per update.  Median of
+    five timed 40-step runs."""
     n, M, steps = 512, 16, 40
     fields = li.random_phase(n, seed=4000, u_rms=0.02)
     out = {"members": M, "grid": [n, n], "tau0": 0.51}
@@ -461,11 +461,11 @@ def collision_models_leg(P, stream, dev, peak):
         lu = M * n * n * steps
         gbs = BYTES_PER_LU_F32 * lu / secs / 1e9
         out[name] = {"glups": lu / secs / 1e9, "achieved_gbs": gbs, "frac": gbs / peak,
-                     "kernel": "k_step_scalar<float>" if coll == 3 else "k_step_f32_vec (extended)",
+                     "kernel": "k_step_f32_vec (entropic)" if coll == 3 else "k_step_f32_vec (extended)",
                      "bound": "hbm"}
         if coll == 3:  # the entropic root keeps the issue slots busy: ALU-bound
             out[name].update({"bound": "alu", "hbm_frac": gbs / peak})
-            wi = issue_counts().get("k_step_scalar<float> (entropic)")
+            wi = issue_counts().get("k_step_f32_vec (entropic)")
             if wi is not None:
                 rate = wi * lu / secs
                 pk = issue_peak(dev.index or 0)

@@ -112,10 +112,9 @@ void shell_force_tables(const lbm_member_cfg &c, int pitch, std::vector<double> 
   }
 }
 
-// The vectorised FP32 kernel serves nx % 4 == 0 with every collision but
-// the entropic one (its per-cell root finding runs in the general kernel).
+// The vectorised FP32 kernel serves nx % 4 == 0 with every collision.
 bool vector_eligible(const lbm_member_cfg &m, int precision) {
-  return precision == 32 && m.nx % 4 == 0 && m.collision != 3;
+  return precision == 32 && m.nx % 4 == 0;
 }
 
 int check_config(const lbm_config *cfg, std::string &err) {
@@ -251,6 +250,7 @@ struct lbm_handle {
   bool has_kind2 = false;  // some member uses the paper's forcing (kind 2)
   bool proj_quad = true;   // every kind-2 member allows the four-cell projection
   bool has_vv = false;     // some member has a variable-viscosity collision
+  bool has_elbm = false;   // some member has the entropic collision
   int cur = 0;
   long long t = 0;
   long long ring_time[3] = {-1, -1, -1};
@@ -665,6 +665,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
     if (c.collision != 0) {
       M.nu_ring = ws_at(h, lay.nu_ring[m]);
       h->has_vv = true;
+      if (c.collision == 3) h->has_elbm = true;
     }
     if (c.force_kind == 2) {
       M.FR0 = c.FR0;
@@ -731,7 +732,7 @@ int lbm_create(const lbm_config *cfg, void *workspace, size_t bytes, lbm_handle 
   if (e != cudaSuccess)
     return cleanup(fail(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
   h->cur = cfg->storage == 1 ? 2 : 0;
-  h->lc.paper_force = h->has_vv ? 2 : (h->has_kind2 ? 1 : 0);
+  h->lc.paper_force = h->has_elbm ? 3 : (h->has_vv ? 2 : (h->has_kind2 ? 1 : 0));
   {
     unsigned *w = reinterpret_cast<unsigned *>(ws_at(h, lay.sync));
     h->gsync = lbm::GridSync{w, w + 1, reinterpret_cast<int *>(w + 2)};

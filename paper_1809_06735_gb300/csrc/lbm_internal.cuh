@@ -207,7 +207,8 @@ struct LaunchCfg {
   int grid_ctas;      // 0: one CTA per tile; else persistent grid size
   int paper_force;    // kernel variant: 0 plain; 1 some member has force kind 2
                       // (BGK collisions); 2 some member has a variable-viscosity
-                      // collision (any force)
+                      // collision (any force); 3 some member has the entropic
+                      // collision (with any other collision and force)
   int proj_rows;      // rows per thread of the FP32 four-cell projection (force
                       // kind 2): a block covers 128 x 8 proj_rows cells
 };

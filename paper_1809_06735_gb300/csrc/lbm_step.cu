@@ -211,14 +211,12 @@ __device__ T elbm_alpha(const T f[kQ], const T d[kQ]) {
     // Otherwise it starts Newton's iteration on g.
     T T2 = T(0), T3 = T(0), T4 = T(0), T5 = T(0);
 #pragma unroll
-    for (int l = 0; l < kQ; ++l) {
-      T q = f[l] * y[l] * y[l];
-      T2 += q;
-      q *= y[l];
-      T3 += q;
-      q *= y[l];
-      T4 += q;
-      T5 += q * y[l];
+    for (int l = 0; l < kQ; ++l) {  // f y^k = Delta y^(k-1)
+      const T y2 = y[l] * y[l], dy2 = d[l] * y2;
+      T2 = fma(d[l], y[l], T2);
+      T3 = fma(d[l], y2, T3);
+      T4 = fma(dy2, y[l], T4);
+      T5 = fma(dy2, y2, T5);
     }
     const T r2 = div_e<T>(T(1), T2), u = T3 * r2, q4 = T4 * r2, q5 = T5 * r2;
     T a = T(2) + (u * T(1.0 / 3.0) + (T(4.0 / 9.0) * u * u - T(2.0 / 3.0) * q4 +
@@ -353,8 +351,9 @@ __device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       const float t = w_of(l);
-      f[l] = t * rho0 + v[l];
-      d[l] = t * (drho * (1.0f + em[l]) + rho0 * em[l]) - v[l];  // f_eq - f, deviation form
+      f[l] = fmaf(t, rho0, v[l]);
+      // f_eq - f = t rho (1 + em) - t rho0 - v = t (drho + rho em) - v
+      d[l] = fmaf(t, fmaf(rho, em[l], drho), -v[l]);
       Fl[l] = forced ? t * rho * (ems[l] - em[l]) : 0.0f;
     }
   } else {
@@ -372,8 +371,13 @@ __device__ T collide_elbm(T v[kQ], T rho0, T tau0, T Fex, T Fey, T alpha_drag) {
   }
   const T a = elbm_alpha<T>(f, d);
   const T ab = div_e<T>(a, T(2) * tau0);
+  if (forced) {
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) v[l] = v[l] + ab * d[l] + Fl[l];
+    for (int l = 0; l < kQ; ++l) v[l] = v[l] + ab * d[l] + Fl[l];
+  } else {
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) v[l] = v[l] + ab * d[l];
+  }
   return a;
 }
 
@@ -620,7 +624,12 @@ __device__ __forceinline__ void step_tile(const Member *__restrict__ members, co
         float g[kQ];
 #pragma unroll
         for (int l = 0; l < kQ; ++l) g[l] = v[l][c];
-        if constexpr (PF == 2)
+        if constexpr (PF == 3) {
+          if (M.collision == 3)
+            collide_elbm<float>(g, rho0, M.tau_f, fxc[c], fyc[c], alpha);
+          else
+            collide_f32<true>(g, rho0, om, fxc[c], fyc[c], alpha, M.collision, M.tau_f, M.Cs_f);
+        } else if constexpr (PF == 2)
           collide_f32<true>(g, rho0, om, fxc[c], fyc[c], alpha, M.collision, M.tau_f, M.Cs_f);
         else
           collide_f32(g, rho0, om, fxc[c], fyc[c], alpha);
@@ -682,7 +691,7 @@ __device__ __forceinline__ void step_tile(const Member *__restrict__ members, co
 }
 
 template <int ROWS, int MODE, int PF, bool SNAP = false>
-__global__ void __launch_bounds__(256, PF == 2 ? 3 : (PF == 1 || SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
+__global__ void __launch_bounds__(256, PF == 2 ? 3 : (PF == 1 || PF == 3 || SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
                                                       const Tile *__restrict__ tiles,
                                                       int ntiles, int cur, int flip, int snap_slot) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -707,11 +716,14 @@ static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int nt
 }
 
 // pf: 0 no member with force kind 2 or a variable viscosity; 1 force kind 2
-// with the BGK collision only; 2 variable-viscosity collisions (any force)
+// with the BGK collision only; 2 variable-viscosity collisions (any force);
+// 3 some member with the entropic collision (any other collision, any force)
 template <int ROWS>
 static void launch_vec_rows(const Member *d_members, const Tile *d_tiles, int ntiles, int state,
                             int flip, int grid, dim3 block, int pf, cudaStream_t s) {
-  if (pf == 2)
+  if (pf == 3)
+    launch_vec_rows<ROWS, 3>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
+  else if (pf == 2)
     launch_vec_rows<ROWS, 2>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
   else if (pf == 1)
     launch_vec_rows<ROWS, 1>(d_members, d_tiles, ntiles, state, flip, grid, block, s);
