@@ -426,14 +426,15 @@ __device__ __forceinline__ void collide_f32(float g[kQ], float rho0, float om, f
 //   feq = t rho [1 - 1.5 |u|^2 + 4.5 (c.u)^2] +- 3 t rho |c.u|,
 //   F_l = t rho [9 (c.u)(c.du) + 4.5 (c.du)^2 - 1.5 (2 u.du + |du|^2)] +- 3 t rho |c.du|,
 // (du = F / rho), which halves the FP64 work (FP64 is this part's slow pipe).
+// The relaxed sums om feq + F are formed before the common factor t rho:
+//   e = t rho [om (base + 4.5 (c.u)^2) + (c.du) (4.5 c.du + 9 c.u) + mdsq],
+//   o = 3 t rho (om c.u + c.du),  mdsq = -1.5 (2 u.du + |du|^2),
+// 13 FP64 operations per pair.
 __device__ __forceinline__ void collide_pair_f64(double &fp, double &fm, double cu, double cd,
-                                                 double trho, double base, double dsq,
-                                                 double om, double keep) {
-  const double even_eq = trho * fma(4.5 * cu, cu, base);
-  const double odd_eq = 3.0 * trho * cu;
-  const double even_F = trho * fma(cd, fma(4.5, cd, 9.0 * cu), -1.5 * dsq);
-  const double odd_F = 3.0 * trho * cd;
-  const double e = fma(om, even_eq, even_F), o = fma(om, odd_eq, odd_F);
+                                                 double trho, double trho3, double base,
+                                                 double mdsq, double om, double keep) {
+  const double e = trho * fma(om, fma(4.5 * cu, cu, base), fma(cd, fma(4.5, cd, 9.0 * cu), mdsq));
+  const double o = trho3 * fma(om, cu, cd);
   fp = fma(keep, fp, e + o);
   fm = fma(keep, fm, e - o);
 }
@@ -451,14 +452,15 @@ __device__ __forceinline__ void collide_f64(double f[kQ], double om, double Fex,
   const double dux = Fx * ir, duy = Fy * ir;
   const double usq = ux * ux + uy * uy;
   const double dsq = dux * (2.0 * ux + dux) + duy * (2.0 * uy + duy);
-  const double base = 1.0 - 1.5 * usq, keep = 1.0 - om;
+  const double base = 1.0 - 1.5 * usq, keep = 1.0 - om, mdsq = -1.5 * dsq;
   const double r0 = (4.0 / 9.0) * rho, r1 = (1.0 / 9.0) * rho, r2 = (1.0 / 36.0) * rho;
+  const double r13 = (1.0 / 3.0) * rho, r23 = (1.0 / 12.0) * rho;  // 3 t rho
   // rest population: no odd part
-  f[0] = fma(keep, f[0], fma(om, r0 * base, -1.5 * r0 * dsq));
-  collide_pair_f64(f[1], f[3], ux, dux, r1, base, dsq, om, keep);
-  collide_pair_f64(f[2], f[4], uy, duy, r1, base, dsq, om, keep);
-  collide_pair_f64(f[5], f[7], ux + uy, dux + duy, r2, base, dsq, om, keep);
-  collide_pair_f64(f[6], f[8], uy - ux, duy - dux, r2, base, dsq, om, keep);
+  f[0] = fma(keep, f[0], r0 * fma(om, base, mdsq));
+  collide_pair_f64(f[1], f[3], ux, dux, r1, r13, base, mdsq, om, keep);
+  collide_pair_f64(f[2], f[4], uy, duy, r1, r13, base, mdsq, om, keep);
+  collide_pair_f64(f[5], f[7], ux + uy, dux + duy, r2, r23, base, mdsq, om, keep);
+  collide_pair_f64(f[6], f[8], uy - ux, duy - dux, r2, r23, base, mdsq, om, keep);
 }
 
 // Compensated FP32 sum of FP32 values as the unevaluated pair (s, c): the
