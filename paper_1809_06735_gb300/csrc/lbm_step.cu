@@ -693,7 +693,7 @@ __device__ __forceinline__ void step_tile(const Member *__restrict__ members, co
 }
 
 template <int ROWS, int MODE, int PF, bool SNAP = false>
-__global__ void __launch_bounds__(256, PF == 2 ? 3 : (PF == 1 || PF == 3 || SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
+__global__ void __launch_bounds__(256, PF == 1 || PF == 2 ? 3 : (PF == 3 || SNAP ? 2 : 1)) k_step_f32_vec(const Member *__restrict__ members,
                                                       const Tile *__restrict__ tiles,
                                                       int ntiles, int cur, int flip, int snap_slot) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
