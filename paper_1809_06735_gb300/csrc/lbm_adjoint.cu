@@ -267,14 +267,17 @@ struct MuMoments {
 
 __device__ __forceinline__ MuMoments mu_moments(const double (&mu)[kQ]) {
   constexpr double t1 = 1.0 / 9.0, t2 = 1.0 / 36.0;
+  // sums and differences of the opposite pairs (1, 3), (2, 4), (5, 7), (6, 8)
+  const double s13 = mu[1] + mu[3], d13 = mu[1] - mu[3], s24 = mu[2] + mu[4], d24 = mu[2] - mu[4];
+  const double s57 = mu[5] + mu[7], d57 = mu[5] - mu[7], s68 = mu[6] + mu[8], d68 = mu[6] - mu[8];
+  const double diag = s57 + s68;
   MuMoments M;
-  const double diag = mu[5] + mu[6] + mu[7] + mu[8];
-  M.m0 = (4.0 / 9.0) * mu[0] + t1 * (mu[1] + mu[2] + mu[3] + mu[4]) + t2 * diag;
-  M.mx = t1 * (mu[1] - mu[3]) + t2 * (mu[5] - mu[6] - mu[7] + mu[8]);
-  M.my = t1 * (mu[2] - mu[4]) + t2 * (mu[5] + mu[6] - mu[7] - mu[8]);
-  M.mxx = t1 * (mu[1] + mu[3]) + t2 * diag;
-  M.myy = t1 * (mu[2] + mu[4]) + t2 * diag;
-  M.mxy = t2 * (mu[5] - mu[6] + mu[7] - mu[8]);
+  M.m0 = fma(4.0 / 9.0, mu[0], fma(t1, s13 + s24, t2 * diag));
+  M.mx = fma(t1, d13, t2 * (d57 - d68));
+  M.my = fma(t1, d24, t2 * (d57 + d68));
+  M.mxx = fma(t1, s13, t2 * diag);
+  M.myy = fma(t1, s24, t2 * diag);
+  M.mxy = t2 * (s57 - s68);
   return M;
 }
 
@@ -289,16 +292,16 @@ __global__ void k_adjoint(AGrid g, Region R, const double *f, const double *lam_
   FOR_CELLS {
     const int x = (int)(c % g.nx), y = (int)(c / g.nx);
     double fl[kQ], mu[kQ];
-    double rho = 0, jx = 0, jy = 0;
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       fl[l] = f[(size_t)l * N + c];
-      rho += fl[l];
-      if (cx_of(l) != 0) jx += cx_of(l) * fl[l];
-      if (cy_of(l) != 0) jy += cy_of(l) * fl[l];
       const int xd = wr(x + cx_of(l), g.nx), yd = wr(y + cy_of(l), g.ny);
       mu[l] = lam_in ? lam_in[(size_t)l * N + (size_t)yd * g.nx + xd] : 0.0;
     }
+    // moments from the opposite pairs' sums and differences
+    const double d57 = fl[5] - fl[7], d68 = fl[6] - fl[8];
+    const double rho = fl[0] + ((fl[1] + fl[3]) + (fl[2] + fl[4])) + ((fl[5] + fl[7]) + (fl[6] + fl[8]));
+    const double jx = (fl[1] - fl[3]) + (d57 - d68), jy = (fl[2] - fl[4]) + (d57 + d68);
     const double ir = 1.0 / rho;
     const double mpx = (1.0 - g.alpha) * jx + g.fxt[y];
     const double mpy = (1.0 - g.alpha) * jy + g.fyt[x];
@@ -332,12 +335,15 @@ __global__ void k_adjoint(AGrid g, Region R, const double *f, const double *lam_
       Ajy += F[D_JY * N + c];
     }
     const double keep = 1.0 - g.omega;
+    // lambda_l = keep mu_l + Arho + c_l . A, by opposite pairs (c . A once
+    // per pair; a product by c = 0 still costs an FMA under IEEE arithmetic)
+    const double cA[4] = {Ajx, Ajy, Ajx + Ajy, Ajy - Ajx};  // c of 1, 2, 5, 6
+    lam_out[c] = fma(keep, mu[0], Arho);
 #pragma unroll
-    for (int l = 0; l < kQ; ++l) {  // the terms with c = 0 skipped: a product by 0
-      double o = keep * mu[l] + Arho;  // still costs an FMA under IEEE arithmetic
-      if (cx_of(l) != 0) o += cx_of(l) * Ajx;
-      if (cy_of(l) != 0) o += cy_of(l) * Ajy;
-      lam_out[(size_t)l * N + c] = o;
+    for (int k = 0; k < 4; ++k) {
+      const int l = k < 2 ? 1 + k : 5 + (k - 2), m = opposite(l);
+      lam_out[(size_t)l * N + c] = fma(keep, mu[l], Arho + cA[k]);
+      lam_out[(size_t)m * N + c] = fma(keep, mu[m], Arho - cA[k]);
     }
   }
   block_sums<2>(acc, partials + 2 * blockIdx.x, add);
