@@ -314,10 +314,13 @@ __global__ void k_adjoint(AGrid g, Region R, const double *f, const double *lam_
     const double qb = (4.5 * (mpx * pbx + mpy * pby) - 1.5 * (mpx * mpx + mpy * mpy) * M.m0) * ir;
     const double w1 = g.omega - 1.0;
     const double Sa_rho = M.m0 - qa * ir, Sb_rho = M.m0 - qb * ir;
-    const double Sa_x = 3.0 * M.mx + (9.0 * pax - 3.0 * jx * M.m0) * ir;
-    const double Sa_y = 3.0 * M.my + (9.0 * pay - 3.0 * jy * M.m0) * ir;
-    const double Sb_x = 3.0 * M.mx + (9.0 * pbx - 3.0 * mpx * M.m0) * ir;
-    const double Sb_y = 3.0 * M.my + (9.0 * pby - 3.0 * mpy * M.m0) * ir;
+    // S_a = 3 M_a + 9 p_a / rho - 3 m_a M0 / rho with 9 / rho and 3 M0 / rho
+    // formed once
+    const double ir9 = 9.0 * ir, k0 = 3.0 * M.m0 * ir, mx3 = 3.0 * M.mx, my3 = 3.0 * M.my;
+    const double Sa_x = fma(ir9, pax, fma(-jx, k0, mx3));
+    const double Sa_y = fma(ir9, pay, fma(-jy, k0, my3));
+    const double Sb_x = fma(ir9, pbx, fma(-mpx, k0, mx3));
+    const double Sb_y = fma(ir9, pby, fma(-mpy, k0, my3));
     double Arho = w1 * Sa_rho + Sb_rho;
     double Ajx = w1 * Sa_x + (1.0 - g.alpha) * Sb_x;
     double Ajy = w1 * Sa_y + (1.0 - g.alpha) * Sb_y;
