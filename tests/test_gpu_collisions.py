@@ -38,11 +38,12 @@ def _fields(nx, ny, seed, amp=0.05):
 
 
 # (nx, ny, tau, force kind, F0, kf, alpha, collision): vector and general
-# kernels, every force kind
+# kernels, every force kind (the entropic collision with each of them)
 SPEC = [(64, 48, 0.51, 0, 0.0, 0, 0.0, 1), (37, 23, 0.53, 1, 2e-4, 2, 1e-3, 1),
         (48, 40, 0.52, 2, 2e-5, 0, 0.0, 2), (32, 32, 0.55, 1, 2e-4, 2, 0.0, 2),
         (40, 40, 0.56, 0, 0.0, 0, 0.0, 0), (48, 40, 0.505, 0, 0.0, 0, 0.0, 3),
-        (37, 23, 0.51, 1, 2e-4, 2, 1e-3, 3)]
+        (37, 23, 0.51, 1, 2e-4, 2, 1e-3, 3), (48, 40, 0.51, 2, 2e-5, 0, 0.0, 3),
+        (37, 23, 0.52, 2, 2e-5, 0, 0.0, 3)]
 
 
 def _member(P, spec):
