@@ -1171,7 +1171,8 @@ int balance_members(lbm_handle *h, const int *members, int nm, const int *L, int
     J.meta = meta_dev + (size_t)i * kMaxL * 8;
     J.nL = (int)where[i].size();
     J.max_boxes = maxb[i];
-    J.qblocks = lbm::diag_query_blocks(maxb[i], origins != nullptr);
+    J.qblocks = lbm::diag_query_blocks(maxb[i], origins != nullptr,
+                                       std::min(nm, h->sc.slots));
     J.force_kind = hm.force_kind;
     if (hm.collision != 0) {  // local viscosity recorded with the snapshot at n
       const size_t N = (size_t)hm.nx * hm.ny;

@@ -1063,8 +1063,18 @@ __device__ __forceinline__ long long quantize(float v, int e) {
   return w < 0.0f ? -q : q;
 }
 __device__ __forceinline__ long long quantize(double v, int e) {
-  return __double2ll_rn(ldexp(v, e));
+  // v 2^e (a product by a power of two: exact, as ldexp), 2^e from its bits
+  return __double2ll_rn(v * __longlong_as_double((long long)(e + 1023) << 52));
 }
+// FP64 terms are quantised once, by k_strip_sums, which stores each value's
+// integer over the value itself (the same width); the later passes of the
+// table read the integers (no FP64 work there: with one strip a small grid
+// has few CTAs, and the FP64 pipe of an SM is narrow).  FP32 terms are
+// quantised on the fly (integer arithmetic only).
+template <typename T> struct QTerm { using type = T; };
+template <> struct QTerm<double> { using type = long long; };
+__device__ __forceinline__ long long q_term(float v, int e) { return quantize(v, e); }
+__device__ __forceinline__ long long q_term(long long v, int) { return v; }
 
 // Summed-area tables by strips of kStrip = 128 columns, 4 consecutive cells
 // per lane (each term field read twice, each table record written once):
@@ -1105,6 +1115,18 @@ __device__ __forceinline__ void load4(const double *r, int x, int nx, bool vec, 
   }
 }
 
+__device__ __forceinline__ void load4(const long long *r, int x, int nx, bool vec,
+                                      long long (&v)[4]) {
+  if (vec && x + 3 < nx) {
+    const longlong2 a = *reinterpret_cast<const longlong2 *>(r + x);
+    const longlong2 b = *reinterpret_cast<const longlong2 *>(r + x + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = x + k < nx ? r[x + k] : 0ll;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ bool vec_rows(const T *A, int nx) {
   return nx % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
@@ -1119,7 +1141,7 @@ __global__ void __launch_bounds__(256) k_strip_sums(const DiagJob *__restrict__ 
   const int lane = threadIdx.x & 31, y = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (y >= ny) return;  // whole warps
   const size_t N = (size_t)nx * ny;
-  const T *A = fld<T>(J.base, T0 + f, N);
+  T *A = fld<T>(J.base, T0 + f, N);
   const bool vec = vec_rows(A, nx);
   A += (size_t)y * nx;
   const int e = reinterpret_cast<const int *>(J.part + exps_at())[f];
@@ -1133,9 +1155,24 @@ __global__ void __launch_bounds__(256) k_strip_sums(const DiagJob *__restrict__ 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (s0 + u >= ns) break;
-      long long v = 0;
+      long long v = 0, q[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) v += quantize(a[u][k], e);
+      for (int k = 0; k < 4; ++k) {
+        q[k] = quantize(a[u][k], e);
+        v += q[k];
+      }
+      if constexpr (sizeof(T) == 8) {  // the integers over the values
+        long long *r = reinterpret_cast<long long *>(A);
+        const int x = (s0 + u) * kStrip + 4 * lane;
+        if (vec && x + 3 < nx) {
+          *reinterpret_cast<longlong2 *>(r + x) = make_longlong2(q[0], q[1]);
+          *reinterpret_cast<longlong2 *>(r + x + 2) = make_longlong2(q[2], q[3]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (x + k < nx) r[x + k] = q[k];
+        }
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       if (lane == 0) {
@@ -1178,14 +1215,15 @@ __global__ void __launch_bounds__(NF * 32) k_col_sums(const DiagJob *__restrict_
   const int ya = rb * rb_rows, yb = ya + rb_rows < ny ? ya + rb_rows : ny;
   if (s >= ns || ya >= ny) return;  // whole CTA
   const size_t N = (size_t)nx * ny;
-  const T *A = fld<T>(J.base, T0 + f, N);
+  using Q = typename QTerm<T>::type;
+  const Q *A = reinterpret_cast<const Q *>(fld<T>(J.base, T0 + f, N));
   const bool vec = vec_rows(A, nx);
   const int x = s * kStrip + 4 * lane;
   const int e = reinterpret_cast<const int *>(J.part + exps_at())[f];
   const long long *left = strip_base(J.base, N) + ((size_t)f * ns + s) * ny;
   long long c[4] = {0, 0, 0, 0}, ls = 0;
   for (int y0 = ya; y0 < yb; y0 += R) {
-    T a[R][4];
+    Q a[R][4];
 #pragma unroll
     for (int k = 0; k < R; ++k)
       if (y0 + k < yb) load4(A + (size_t)(y0 + k) * nx, x, nx, vec, a[k]);
@@ -1193,7 +1231,7 @@ __global__ void __launch_bounds__(NF * 32) k_col_sums(const DiagJob *__restrict_
     for (int k = 0; k < R; ++k) {
       if (y0 + k >= yb) break;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) c[j] += quantize(a[k][j], e);
+      for (int j = 0; j < 4; ++j) c[j] += q_term(a[k][j], e);
     }
   }
   for (int y = ya + lane; y < yb; y += 32) ls += left[y];
@@ -1227,7 +1265,8 @@ __global__ void __launch_bounds__(NF * 32) k_sat_tile(const DiagJob *__restrict_
   const int x0 = s * kStrip, x = x0 + 4 * lane;
   const int nw = (nx - x0 < kStrip ? nx - x0 : kStrip) * NF;  // record words per row
   const size_t N = (size_t)nx * ny, rs = (size_t)nx + 1;
-  const T *A = fld<T>(J.base, T0 + f, N);
+  using Q = typename QTerm<T>::type;
+  const Q *A = reinterpret_cast<const Q *>(fld<T>(J.base, T0 + f, N));
   const bool vec = vec_rows(A, nx);
   const long long *left = strip_base(J.base, N) + ((size_t)f * ns + s) * ny;
   long long *tab = sat_base(J.base, N);
@@ -1255,7 +1294,7 @@ __global__ void __launch_bounds__(NF * 32) k_sat_tile(const DiagJob *__restrict_
   }
   for (int y0 = ya; y0 < yb; y0 += R) {
     if ((y0 & 31) == 0) lf = y0 + lane < ny ? left[y0 + lane] : 0;  // 32 rows' left parts
-    T a[R][4];
+    Q a[R][4];
 #pragma unroll
     for (int k = 0; k < R; ++k)
       if (y0 + k < yb) load4(A + (size_t)(y0 + k) * nx, x, nx, vec, a[k]);
@@ -1266,7 +1305,7 @@ __global__ void __launch_bounds__(NF * 32) k_sat_tile(const DiagJob *__restrict_
       if (y >= yb) break;  // the same for the whole CTA
       long long v[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = quantize(a[k][j], e);
+      for (int j = 0; j < 4; ++j) v[j] = q_term(a[k][j], e);
       v[1] += v[0];
       v[2] += v[1];
       v[3] += v[2];
@@ -1811,10 +1850,17 @@ cudaError_t diag_global(const Member &hm, const double *snap3, const DiagScratch
 }
 
 // Box lists: about 8 boxes per thread pair; every periodic origin: about 32
-// per thread pair; at most kMaxQueryBlocks CTAs per (job, size, part).
-int diag_query_blocks(int max_boxes, bool origin_list) {
+// per thread pair; at most kMaxQueryBlocks CTAs per (job, size, part).  A
+// batch of few jobs with few boxes (a small grid) gets smaller CTAs, down to
+// one pass of 128 boxes, about 256 per size over the batch: its FP64
+// statistics then spread over the SMs instead of queueing on a few (GB300
+// issues about 1.7 FP64 FMAs per clock per SM).
+int diag_query_blocks(int max_boxes, bool origin_list, int batch_jobs) {
   const int per_cta = origin_list ? 1024 : 4096;
-  return std::min(kMaxQueryBlocks, std::max(1, (max_boxes + per_cta - 1) / per_cta));
+  int qb = (max_boxes + per_cta - 1) / per_cta;
+  const int want = (256 + std::max(1, batch_jobs) - 1) / std::max(1, batch_jobs);
+  qb = std::max(qb, std::min(want, (max_boxes + 127) / 128));
+  return std::min(kMaxQueryBlocks, std::max(1, qb));
 }
 
 size_t diag_slot_doubles(size_t Nmax, size_t pad) {

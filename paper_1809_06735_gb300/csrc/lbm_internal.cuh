@@ -324,7 +324,7 @@ struct DiagJob {
 };
 // Query CTAs for a job: a fixed function of its own box count, so that the
 // statistics do not depend on which members share a batch.
-int diag_query_blocks(int max_boxes, bool origin_list);
+int diag_query_blocks(int max_boxes, bool origin_list, int batch_jobs);
 // Doubles of one field slot and of one partials slot for members of at most
 // Nmax cells and nx + ny + 1 <= pad.
 size_t diag_slot_doubles(size_t Nmax, size_t pad);
