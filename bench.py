@@ -1036,6 +1036,22 @@ def case_fp64(P, n=512, steps=20):
     print("fp64 case done")
 
 
+def case_taylor_green(P, events=3):
+    """The FP64 Taylor-Green workload (64^2, tau 0.6) for a few of its
+    balance events: 100 steps, then the balance at L in {4, 8, 16, 32} over
+    every origin, per event."""
+    import torch
+    wl = li.taylor_green_workload()
+    n, tau, D, Ls = wl["n"], wl["tau"], wl["diag_every"], wl["Ls"]
+    lat = P.Lattice([P.Member(n, n, tau)], precision=64, diag_every=D, graph_steps=16)
+    lat.init_fields(0, *li.taylor_green(n, u0=wl["u0"]))
+    for _ in range(events):
+        lat.step(D)
+        lat.subvolume_balance(0, Ls)
+    torch.cuda.synchronize()
+    print("taylor green case done:", lat.launch_count, "launches")
+
+
 def case_adjoint(P, n=256, steps=6):
     import torch
     F0 = li.kolmogorov_F0(n, 0.55, 4, 1e-4, 0.03)

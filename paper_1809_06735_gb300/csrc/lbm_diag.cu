@@ -1784,9 +1784,9 @@ cudaError_t balance_launches(const DiagJob *jobs_host, const DiagJob *jobs, int 
         sms = 1;
     }
     const long long ctas = (long long)ns * G;
-    if (ctas < sms && ny >= 256) {
+    if (ctas < sms && ny >= 64) {
       long long want = (2LL * sms + ctas - 1) / ctas;
-      if (want > ny / 64) want = ny / 64;
+      if (want > ny / (ny >= 256 ? 64 : 32)) want = ny / (ny >= 256 ? 64 : 32);
       rb_rows = (int)(((ny + want - 1) / want + 31) / 32 * 32);
       nrb = (ny + rb_rows - 1) / rb_rows;
     }
