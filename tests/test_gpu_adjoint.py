@@ -150,6 +150,7 @@ def _small_spec(precision=64):
     (128, (100, 7), 101, 64, 1e-12),  # 8 x 8 tiles (13 x 13 CTAs), ragged, wrapping
     (200, (150, 190), 197, 64, 1e-12),  # 16 x 16 tiles (13 x 13 CTAs), ragged, wrapping
     (520, (7, 500), 515, 64, 1e-12),  # 33 x 33 tiles on 1024 CTAs (a CTA does two)
+    (6, (4, 5), 6, 64, 1e-12),        # a grid smaller than one widened tile: halos wrap twice
     (32, (5, 3), 8, 32, 1e-5),        # FP32 populations
     (200, (150, 190), 197, 32, 1e-5)])  # FP32, 16 x 16 tiles
 def test_objective_forward_matches_oracle(P, orc, n, box, L, precision, tol):
