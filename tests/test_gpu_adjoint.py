@@ -171,19 +171,20 @@ def test_objective_forward_matches_oracle(P, orc, n, box, L, precision, tol):
     assert abs(float(J) - Jo) < tol * abs(Jo), (float(J), Jo)
 
 
-@pytest.mark.parametrize("box,L", [((5, 3), 8), ((20, 27), 24)])
-def test_gradients_match_oracle_finite_differences(P, orc, box, L):
+@pytest.mark.parametrize("n,box,L", [(32, (5, 3), 8), (32, (20, 27), 24), (6, (4, 5), 6)])
+def test_gradients_match_oracle_finite_differences(P, orc, n, box, L):
     """dJ/dtau (h = 1e-6), dJ/dF0 (1e-3 relative step, Richardson) and a
     directional derivative in f0 against central differences of the FP64
     oracle objective; an 8 x 8 box and a 24 x 24 box on 32^2 (its stencil
-    reach wraps onto the box: the adjoint's region is the whole grid)."""
+    reach wraps onto the box: the adjoint's region is the whole grid), and
+    the whole 6^2 grid as the box (the reach wraps around it twice)."""
     import dataclasses
     import torch
     from paper_1809_06735_gb300.adjoint import box_dissipation
-    spec = dataclasses.replace(_small_spec(), box=box, L=L)
+    spec = dataclasses.replace(_small_spec(), nx=n, ny=n, box=box, L=L)
     tau0, kf, alpha = 0.6, 2, 1e-3
-    F00 = li.kolmogorov_F0(32, tau0, kf, alpha, 0.02)
-    r, u, v = li.random_phase(32, seed=4, u_rms=0.02, k_peak=3.0)
+    F00 = li.kolmogorov_F0(n, tau0, kf, alpha, 0.02)
+    r, u, v = li.random_phase(n, seed=4, u_rms=0.02, k_peak=3.0)
     f0 = orc.init(r, u, v)
     tau = torch.tensor(tau0, dtype=torch.float64, requires_grad=True)
     F0 = torch.tensor(F00, dtype=torch.float64, requires_grad=True)
